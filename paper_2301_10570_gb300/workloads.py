@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs for the synapse search.
+
+This module only draws random inputs; it holds none of the method's
+arithmetic.  It is the one piece shared by the CUDA path's tests/benchmark
+and the oracle.  The paper's own networks are not public: these generators
+stand in for them with the sizes and structure of the workloads the paper and
+the benchmark describe (a Poisson-like uniform cube at the paper's density,
+and clustered networks), with sigma = 750 um (Table 1) and vacant element
+counts small integers as in the model of structural plasticity (Section 3.1).
+All generators use numpy's PCG64 with the given seed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SIGMA_UM = 750.0
+
+
+def default_params(side: float, **kw) -> dict:
+    """Search parameters: kernel width, expansion order, octree and pair rule."""
+    p = dict(sigma=SIGMA_UM, p=4, leaf_capacity=32, max_depth=21,
+             origin=(0.0, 0.0, 0.0), side=float(side), seed=0,
+             rho_max=0.25, cutoff=4.0, m2l_min_pairs=0, boundary_tol=1e-5)
+    p.update(kw)
+    return p
+
+
+@dataclass
+class Workload:
+    name: str
+    pos: np.ndarray          # (3, n) float32, SoA x/y/z in um
+    type: np.ndarray         # (n,) uint8, 0 = excitatory, 1 = inhibitory
+    vac_axon: np.ndarray     # (n,) uint8 vacant axonal elements
+    vac_dend_e: np.ndarray   # (n,) uint8 vacant excitatory dendritic elements
+    vac_dend_i: np.ndarray   # (n,) uint8 vacant inhibitory dendritic elements
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[1])
+
+    def arrays(self):
+        return self.pos, self.type, self.vac_axon, self.vac_dend_e, self.vac_dend_i
+
+
+def _counts(rng, n, frac_exc=0.8, vmax=3):
+    type_ = (rng.random(n) >= frac_exc).astype(np.uint8)
+    va = rng.integers(0, vmax + 1, n, dtype=np.uint8)
+    ve = rng.integers(0, vmax + 1, n, dtype=np.uint8)
+    vi = rng.integers(0, vmax + 1, n, dtype=np.uint8)
+    return type_, va, ve, vi
+
+
+def _clamp_cube(pos, side):
+    hi = np.nextafter(np.float32(side), np.float32(0))
+    return np.clip(pos, np.float32(0), hi).astype(np.float32)
+
+
+def uniform_cube(n: int, side: float, seed: int, name: str = "uniform", **kw) -> Workload:
+    rng = np.random.default_rng(seed)
+    pos = _clamp_cube(rng.random((3, n), dtype=np.float64).astype(np.float32) *
+                      np.float32(side), side)
+    t, a, e, i = _counts(rng, n)
+    return Workload(name, pos, t, a, e, i, default_params(side, **kw))
+
+
+def clustered(n_clusters: int, per_cluster: int, side: float, std: float, margin: float,
+              seed: int, name: str = "clustered", **kw) -> Workload:
+    """Isotropic Gaussian clusters; centres uniform in [margin, side - margin)^3."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(margin, side - margin, (n_clusters, 3))
+    pts = centres[:, None, :] + rng.normal(0.0, std, (n_clusters, per_cluster, 3))
+    pos = _clamp_cube(pts.reshape(-1, 3).T.astype(np.float32), side)
+    n = n_clusters * per_cluster
+    t, a, e, i = _counts(rng, n)
+    return Workload(name, np.ascontiguousarray(pos), t, a, e, i,
+                    default_params(side, **kw))
+
+
+# -- the named workloads ----------------------------------------------------
+def uniform_4k(**kw) -> Workload:
+    """4,096 neurons uniform in a 10,000 um cube, p = 4, leaf capacity 32."""
+    return uniform_cube(4096, 10_000.0, seed=1, name="uniform_4k", **kw)
+
+
+def uniform_256k(**kw) -> Workload:
+    """262,144 neurons uniform in a 40,000 um cube (same density as uniform_4k)."""
+    return uniform_cube(262_144, 40_000.0, seed=2, name="uniform_256k", **kw)
+
+
+def clustered_1m(**kw) -> Workload:
+    """1,048,576 neurons in 64 Gaussian clusters (std 1,500 um), 100,000 um cube."""
+    return clustered(64, 16_384, 100_000.0, 1500.0, 4500.0, seed=3, name="clustered_1m",
+                     **kw)
+
+
+def clustered_small(n_clusters: int = 2, per_cluster: int = 4096, seed: int = 7,
+                    **kw) -> Workload:
+    """A few clusters at the density of clustered_1m, small enough for the oracle."""
+    side = 100_000.0 * (n_clusters / 64.0) ** (1.0 / 3.0)
+    return clustered(n_clusters, per_cluster, side, 1500.0, min(4500.0, side / 4), seed=seed,
+                     name=f"clustered_{n_clusters}x{per_cluster}", **kw)
+
+
+def subset(w: Workload, idx: np.ndarray, name: str | None = None) -> Workload:
+    """The neurons idx of w (same parameters)."""
+    idx = np.asarray(idx)
+    return Workload(name or w.name + "_sub", np.ascontiguousarray(w.pos[:, idx]),
+                    w.type[idx].copy(), w.vac_axon[idx].copy(), w.vac_dend_e[idx].copy(),
+                    w.vac_dend_i[idx].copy(), dict(w.params))

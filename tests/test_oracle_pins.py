@@ -1,0 +1,614 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, textbook identities, brute force on tiny inputs, the paper's printed
+accuracy bound, invariants of the model, or an independent Python restatement
+of a bit-level definition.  None of these tests touches the GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import hermite as npherm
+
+from paper_2301_10570_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# Hermite functions (the h(alpha, x) of Eq. 6 / Eq. 7)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("x", [-2.7, -1.0, -0.3, 0.0, 0.45, 1.3, 3.1])
+def test_hermite_matches_physicists_polynomials(oracle_mod, x):
+    """h_n(x) = H_n(x) exp(-x^2) with numpy's physicists' Hermite series."""
+    h = oracle_mod.hermite(16, x)
+    for n in range(17):
+        c = np.zeros(n + 1)
+        c[n] = 1.0
+        ref = npherm.hermval(x, c) * math.exp(-x * x)
+        assert h[n] == pytest.approx(ref, rel=1e-11, abs=1e-11 * math.sqrt(math.factorial(n)) * 2 ** n)
+
+
+def test_hermite_parity_and_derivative(oracle_mod):
+    """h_n(-x) = (-1)^n h_n(x) and h_n'(x) = -h_{n+1}(x)."""
+    for x in (0.2, 0.9, 1.7):
+        hp, hm = oracle_mod.hermite(12, x), oracle_mod.hermite(12, -x)
+        for n in range(13):
+            assert hm[n] == pytest.approx((-1) ** n * hp[n], rel=1e-13, abs=1e-300)
+        eps = 1e-6
+        ha, hb = oracle_mod.hermite(12, x + eps), oracle_mod.hermite(12, x - eps)
+        for n in range(12):
+            deriv = (ha[n] - hb[n]) / (2 * eps)
+            assert deriv == pytest.approx(-hp[n + 1], rel=1e-6, abs=1e-6)
+
+
+def test_hermite_generating_function(oracle_mod):
+    """exp(-(t - s)^2) = sum_n s^n / n! h_n(t)."""
+    for t in (-1.1, 0.0, 0.6, 2.0):
+        h = oracle_mod.hermite(40, t)
+        for s in (-0.7, 0.25, 0.9):
+            series = sum(s ** n / math.factorial(n) * h[n] for n in range(41))
+            assert series == pytest.approx(math.exp(-(t - s) ** 2), rel=1e-12, abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Expansions (Eq. 6, Eq. 7 and their composition)
+# --------------------------------------------------------------------------
+def _cramer_tail(rho, p, nmax=80):
+    """sum_{n>=p} rho^n / sqrt(n!) (the 1-D tail of Cramer's inequality)."""
+    return sum(rho ** n / math.sqrt(math.factorial(n)) for n in range(p, nmax))
+
+
+def test_m2l_of_point_source_is_s2l(oracle_mod):
+    """A single source at the box centre has A_0 = w, A_alpha = 0 otherwise; its
+    translation must be the direct Taylor coefficients of Eq. 6 with the sign
+    fixed by the Taylor expansion: B_beta = w / beta! h_beta((s - t_C)/sigma)."""
+    p, sigma, w = 6, 750.0, 2.0
+    s = np.array([100.0, -250.0, 40.0])
+    cA = np.array([700.0, 300.0, -500.0])
+    A = oracle_mod.p2m(p, sigma, s[None, :], np.array([w]), s)
+    B = oracle_mod.m2l(p, sigma, A, cA, s)
+    H = [oracle_mod.hermite(p, (s[d] - cA[d]) / sigma) for d in range(3)]
+    for b0 in range(p):
+        for b1 in range(p):
+            for b2 in range(p):
+                ref = w * H[0][b0] * H[1][b1] * H[2][b2] / (
+                    math.factorial(b0) * math.factorial(b1) * math.factorial(b2))
+                assert B[(b0 * p + b1) * p + b2] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+
+
+def test_single_pair_converges_to_closed_form(oracle_mod):
+    """One source and one target: P2M -> M2L -> L2P tends to w exp(-r^2/sigma^2)
+    as p grows, and stays inside the Cramer bound of both truncations."""
+    sigma, w = 750.0, 3.0
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        cD = rng.uniform(-1000, 1000, 3)
+        cA = cD + rng.uniform(-1500, 1500, 3)
+        s = cD + rng.uniform(-0.25, 0.25, 3) * sigma
+        t = cA + rng.uniform(-0.25, 0.25, 3) * sigma
+        exact = w * math.exp(-np.sum((t - s) ** 2) / sigma ** 2)
+        errs = []
+        for p in range(1, 9):
+            A = oracle_mod.p2m(p, sigma, s[None, :], np.array([w]), cD)
+            B = oracle_mod.m2l(p, sigma, A, cA, cD)
+            errs.append(abs(oracle_mod.l2p(p, sigma, B, cA, t) - exact))
+            rho = math.sqrt(2) * 0.25 * math.sqrt(3)
+            kappa = 1.0865
+            full = sum(rho ** n / math.sqrt(math.factorial(n)) for n in range(80))
+            part = full - _cramer_tail(rho, p)
+            bound = w * kappa ** 3 * 2 * (full ** 3 - part ** 3) * full ** 3
+            assert errs[-1] <= bound
+        assert errs[-1] < 1e-6 * w
+        assert errs[-1] <= errs[2]
+
+
+def test_hermite_m2p_truncation_bound(oracle_mod):
+    """Eq. 7 on a box of sources vs direct sums, within W kappa^3 (F^3 - F_p^3)."""
+    sigma = 750.0
+    rng = np.random.default_rng(5)
+    for half in (0.2, 0.35):
+        pts = rng.uniform(-half, half, (40, 3)) * sigma
+        w = rng.integers(0, 4, 40).astype(float)
+        c = np.zeros(3)
+        prev = None
+        for p in range(1, 9):
+            A = oracle_mod.p2m(p, sigma, pts, w, c)
+            rho = math.sqrt(2) * half
+            F = sum(rho ** n / math.sqrt(math.factorial(n)) for n in range(80))
+            Fp = F - _cramer_tail(rho, p)
+            bound = w.sum() * 1.0865 ** 3 * (F ** 3 - Fp ** 3)
+            worst = 0.0
+            for t in rng.uniform(-2.5, 2.5, (30, 3)) * sigma:
+                exact = np.sum(w * np.exp(-np.sum((t - pts) ** 2, 1) / sigma ** 2))
+                worst = max(worst, abs(oracle_mod.m2p(p, sigma, A, c, t) - exact))
+            assert worst <= bound
+            if prev is not None and p >= 3:
+                assert worst <= prev * 1.5
+            prev = worst
+
+
+# --------------------------------------------------------------------------
+# Morton keys and the octree (Section 3.2)
+# --------------------------------------------------------------------------
+def _interleave(qx, qy, qz):
+    key = 0
+    for k in range(21):
+        key |= ((qx >> k) & 1) << (3 * k + 2)
+        key |= ((qy >> k) & 1) << (3 * k + 1)
+        key |= ((qz >> k) & 1) << (3 * k)
+    return key
+
+
+def test_morton_hand_examples(oracle_mod):
+    side = float(2 ** 21)            # one grid cell per unit
+    o = (0.0, 0.0, 0.0)
+    assert oracle_mod.morton(1.5, 0.5, 0.5, o, side) == 0b100
+    assert oracle_mod.morton(0.5, 1.5, 0.5, o, side) == 0b010
+    assert oracle_mod.morton(0.5, 0.5, 1.5, o, side) == 0b001
+    assert oracle_mod.morton(3.5, 3.5, 3.5, o, side) == 0b111111
+    assert oracle_mod.morton(2.5, 0.5, 1.5, o, side) == 0b100001
+    top = 2 ** 21 - 1
+    assert oracle_mod.morton(top + 0.5, top + 0.5, top + 0.5, o, side) == 2 ** 63 - 1
+    assert oracle_mod.morton(-5.0, 1e30, float("nan"), o, side) == _interleave(0, top, 0)
+
+
+def _quantise(v, o, side):
+    scale = np.float32(np.float64(2 ** 21) / np.float64(side))
+    f = np.floor((np.float32(v) - np.float32(o)) * scale)
+    f = np.where(np.isnan(f), -1.0, f)
+    return np.clip(f, 0, 2 ** 21 - 1).astype(np.int64)
+
+
+def _python_tree(w, C, maxd):
+    """Recursive subdivision written independently of the oracle."""
+    q = [_quantise(w.pos[d], w.params["origin"][d], w.params["side"]) for d in range(3)]
+    keys = np.array([_interleave(int(a), int(b), int(c)) for a, b, c in zip(*q)], dtype=np.uint64)
+    order = np.argsort(keys, kind="stable")
+    ks = keys[order]
+    nodes = []
+
+    def rec(level, prefix, lo, hi):
+        nodes.append((level, prefix, lo, hi - lo))
+        if hi - lo <= C or level >= maxd:
+            return
+        shift = 3 * (21 - level - 1)
+        for o in range(8):
+            sel = [i for i in range(lo, hi) if (int(ks[i]) >> shift) & 7 == o]
+            if sel:
+                rec(level + 1, (prefix << 3) | o, sel[0], sel[-1] + 1)
+
+    rec(0, 0, 0, len(ks))
+    nodes.sort(key=lambda t: (t[0], t[1]))
+    return ks, order, nodes
+
+
+@pytest.mark.parametrize("n,C,maxd", [(300, 4, 21), (257, 8, 3), (1, 4, 21), (64, 64, 21)])
+def test_octree_matches_recursive_subdivision(oracle_mod, n, C, maxd):
+    w = W.uniform_cube(n, 10_000.0, seed=n, leaf_capacity=C, max_depth=maxd)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    ks, order, ref_nodes = _python_tree(w, C, maxd)
+    keys, perm = o.keys()
+    assert np.array_equal(keys, ks)
+    assert np.array_equal(perm, order)
+    nd = o.nodes()
+    got = list(zip(nd["level"].tolist(), nd["prefix"].tolist(), nd["first"].tolist(),
+                   nd["count"].tolist()))
+    assert got == ref_nodes
+
+
+def test_octree_with_coincident_points(oracle_mod):
+    """Points in one grid cell cannot be separated: the leaf at max depth overfills."""
+    w = W.uniform_cube(50, 1000.0, seed=3, leaf_capacity=4)
+    w.pos[:, :20] = w.pos[:, :1]
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    nd = o.nodes()
+    leaf = nd["child_first"] < 0
+    assert nd["count"][leaf].sum() == 50
+    assert nd["count"][leaf].max() >= 20
+    assert nd["level"][leaf][np.argmax(nd["count"][leaf])] == 21
+
+
+def test_box_aggregates(oracle_mod):
+    w = W.uniform_cube(500, 10_000.0, seed=9, leaf_capacity=8)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    _, perm = o.keys()
+    nd = o.nodes()
+    pos = w.pos[:, perm].astype(np.float64)
+    t, a, e, i = (v[perm].astype(np.int64) for v in (w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i))
+    for k in range(len(nd["level"])):
+        s = slice(nd["first"][k], nd["first"][k] + nd["count"][k])
+        assert nd["sums"][k].tolist() == [int((a[s] * (t[s] == 0)).sum()), int((a[s] * (t[s] == 1)).sum()),
+                                          int(e[s].sum()), int(i[s].sum())]
+        wa, wd = a[s], e[s] + i[s]
+        if wa.sum() > 0:
+            assert np.allclose(nd["centroids"][k, :3], (pos[:, s] * wa).sum(1) / wa.sum(), rtol=1e-12)
+        if wd.sum() > 0:
+            assert np.allclose(nd["centroids"][k, 3:], (pos[:, s] * wd).sum(1) / wd.sum(), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Dual traversal and the FMM sum (Eq. 8)
+# --------------------------------------------------------------------------
+def _terminal_cover(o, w):
+    """For every (target point, source point) count the terminal traversal pairs
+    (far, near-leaf or pruned) whose boxes contain them."""
+    nd, pr = o.nodes(), o.pairs()
+    n = w.n
+    cover = np.zeros((n, n), np.int32)
+    for X, Y, kind in zip(pr["X"], pr["Y"], pr["kind"]):
+        if kind == 0:
+            continue
+        xs = slice(nd["first"][X], nd["first"][X] + nd["count"][X])
+        ys = slice(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+        cover[xs, ys] += 1
+    return cover
+
+
+@pytest.mark.parametrize("params", [dict(leaf_capacity=4, rho_max=0.0, cutoff=2.0),
+                                    dict(leaf_capacity=4, rho_max=0.6, cutoff=3.0),
+                                    dict(leaf_capacity=2, rho_max=1.0, cutoff=50.0)])
+def test_traversal_covers_every_point_pair_once(oracle_mod, params):
+    w = W.clustered_small(1, 160, seed=4, **params)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    cover = _terminal_cover(o, w)
+    nd = o.nodes()
+    sa = nd["sums"][0, 0] + nd["sums"][0, 1]
+    if sa > 0:
+        assert cover.min() == 1 and cover.max() == 1
+
+
+def test_pruned_and_far_pairs_respect_geometry(oracle_mod):
+    w = W.clustered_small(1, 600, seed=8, leaf_capacity=4, rho_max=0.4, cutoff=2.5)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    _, perm = o.keys()
+    nd, pr = o.nodes(), o.pairs()
+    pos = w.pos[:, perm].astype(np.float64)
+    sigma, lf = w.params["sigma"], o.far_level()
+    n_far = 0
+    for X, Y, kind in zip(pr["X"], pr["Y"], pr["kind"]):
+        if kind not in (1, 3):
+            continue
+        xs = pos[:, nd["first"][X]: nd["first"][X] + nd["count"][X]]
+        ys = pos[:, nd["first"][Y]: nd["first"][Y] + nd["count"][Y]]
+        dmin = np.sqrt(((xs[:, :, None] - ys[:, None, :]) ** 2).sum(0)).min()
+        if kind == 3 and nd["sums"][X, :2].sum() > 0 and nd["sums"][Y, 2:].sum() > 0:
+            assert dmin >= w.params["cutoff"] * sigma * (1 - 1e-6)
+        if kind == 1:
+            n_far += 1
+            assert min(nd["level"][X], nd["level"][Y]) >= lf
+            assert X != Y and dmin > 0
+    assert n_far > 0
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_fmm_matches_brute_force_tiny(oracle_mod, p):
+    """N <= 64 with far pairs forced: FMM within its truncation, brute force exact."""
+    w = W.uniform_cube(64, 1500.0, seed=21, leaf_capacity=2, rho_max=0.3, cutoff=6.0, p=p)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    u = o.attraction()
+    assert o.stats()["far_pairs"] > 0
+    # brute force written here, independently of the oracle
+    x = w.pos.astype(np.float64)
+    d2 = ((x[:, :, None] - x[:, None, :]) ** 2).sum(0)
+    K = np.exp(-d2 / w.params["sigma"] ** 2)
+    np.fill_diagonal(K, 0.0)
+    wt = np.where(w.type[:, None] == 0, w.vac_dend_e[None, :], w.vac_dend_i[None, :])
+    ref = np.where(w.vac_axon > 0, (K * wt).sum(1), 0.0)
+    m = ref > 1e-3 * ref.max()
+    tol = {4: 5e-3, 6: 2e-4}[p]
+    assert np.max(np.abs(u[m] - ref[m]) / ref[m]) < tol
+    assert np.allclose(oracle_mod.direct(*w.arrays(), w.params["sigma"]), ref, rtol=1e-12, atol=1e-300)
+
+
+def test_paper_cutoff_meets_paper_accuracy(oracle_mod):
+    """With the paper's cut-off alpha = beta = (3,3,3) (p = 4) the expansions
+    stay within the paper's largest outlier, 0.125 %, of direct evaluation
+    when boxes carrying an expansion are at most 0.2 sigma across half."""
+    k = _paper()
+    p = k["cutoff_multi_index"]["value"][0] + 1
+    w = W.clustered_small(1, 2048, seed=2, leaf_capacity=4, rho_max=0.2, p=p,
+                          sigma=k["sigma_um"]["value"])
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    u = o.attraction()
+    assert o.stats()["far_pairs"] > 1000
+    ref = oracle_mod.direct(*w.arrays(), w.params["sigma"])
+    m = ref > 0
+    assert np.max(np.abs(u[m] - ref[m]) / ref[m]) < k["max_expansion_deviation"]["value"]
+
+
+def test_pair_table_total_equals_weighted_attraction(oracle_mod):
+    """W(root, root) of each channel = sum over that channel's targets of a_t u(t)."""
+    w = W.clustered_small(1, 1500, seed=12, leaf_capacity=4, rho_max=0.3, p=4)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    u = o.attraction()
+    pr = o.pairs()
+    for ch, name in ((0, "wE"), (1, "wI")):
+        ref = np.sum(w.vac_axon * u * (w.type == ch))
+        assert pr[name][0] == pytest.approx(ref, rel=1e-10)
+
+
+def test_kernel_symmetry(oracle_mod):
+    """sum_t a_t u_w(t) = sum_s w_s u_a(s): the Gaussian is symmetric."""
+    w = W.uniform_cube(700, 8000.0, seed=13)
+    t0 = np.zeros(w.n, np.uint8)
+    lhs = np.sum(w.vac_axon * oracle_mod.direct(w.pos, t0, w.vac_axon, w.vac_dend_e, w.vac_dend_i, 750.0))
+    rhs = np.sum(w.vac_dend_e * oracle_mod.direct(w.pos, t0, w.vac_dend_e, w.vac_axon, w.vac_dend_i, 750.0))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_mean_field_of_uniform_density(oracle_mod):
+    """Deep inside a uniform cloud u ~ rho pi^{3/2} sigma^3 E[w] (Eq. 8 with
+    the exp(-r^2/sigma^2) reading; the exp(-r^2/sigma) reading would give ~0)."""
+    side, n, sigma = 10_000.0, 20_000, 750.0
+    w = W.uniform_cube(n, side, seed=17)
+    inner = np.all((w.pos > 4 * sigma) & (w.pos < side - 4 * sigma), axis=0) & (w.vac_axon > 0)
+    idx = np.nonzero(inner)[0]
+    u = oracle_mod.direct(*w.arrays(), sigma, targets=idx)
+    ew = np.where(w.type[idx] == 0, w.vac_dend_e.mean(), w.vac_dend_i.mean())
+    ref = n / side ** 3 * math.pi ** 1.5 * sigma ** 3 * ew
+    assert np.mean(u / ref) == pytest.approx(1.0, abs=0.03)
+
+
+# --------------------------------------------------------------------------
+# Selection: Algorithm 1 / Algorithm 2 and the request resolution
+# --------------------------------------------------------------------------
+def test_single_leaf_descent_is_inverse_cdf(oracle_mod):
+    """With one leaf (N <= C) every element draws s != t with probability
+    proportional to w_s K(t,s): inverse CDF of the element's uniform."""
+    w = W.uniform_cube(40, 3000.0, seed=31, leaf_capacity=64)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    for step in (0, 5):
+        r = o.select_partners(step)
+        x = w.pos.astype(np.float64)
+        e = 0
+        for t in range(w.n):
+            wt = w.vac_dend_i if w.type[t] else w.vac_dend_e
+            d2 = ((x - x[:, t:t + 1]) ** 2).sum(0)
+            ws = wt * np.exp(-d2 / 750.0 ** 2)
+            ws[t] = 0.0
+            _, perm = o.keys()
+            ws_sorted = ws[perm]
+            cdf = np.cumsum(ws_sorted)
+            for k in range(w.vac_axon[t]):
+                if cdf[-1] <= 0:
+                    assert r["partner"][e] == -1
+                else:
+                    U = oracle_mod.uniform(0, t, k | (int(w.type[t]) << 8) | (2 << 16), step)
+                    j = int(np.searchsorted(cdf, U * cdf[-1], side="right"))
+                    if not r["near_boundary"][e]:
+                        assert r["partner"][e] == perm[j]
+                e += 1
+
+
+def _leaf_of(nd, point):
+    k = 0
+    while nd["child_first"][k] >= 0:
+        for c in range(nd["child_first"][k], nd["child_first"][k] + nd["nchild"][k]):
+            if nd["first"][c] <= point < nd["first"][c] + nd["count"][c]:
+                k = c
+                break
+    return k
+
+
+def _exact_partner_distribution(o, w, t_orig):
+    """Product of the per-level choice probabilities of Algorithm 2 along every
+    path of Algorithm 1, times the leaf probability, for one neuron."""
+    nd, pr = o.nodes(), o.pairs()
+    keys, perm = o.keys()
+    inv = np.argsort(perm)
+    t = int(inv[t_orig])
+    ch = int(w.type[t_orig])
+    wkey = "wI" if ch else "wE"
+    leaf = _leaf_of(nd, t)
+    anc = set()
+    k = leaf
+    while k >= 0:
+        anc.add(k)
+        k = nd["parent"][k]
+    x = w.pos[:, perm].astype(np.float64)
+    wt = (w.vac_dend_i if ch else w.vac_dend_e)[perm].astype(np.float64)
+    out = np.zeros(w.n)
+
+    def is_leaf(k):
+        return nd["child_first"][k] < 0
+
+    def kids(k):
+        return list(range(nd["child_first"][k], nd["child_first"][k] + nd["nchild"][k]))
+
+    def visit(X, Y, q, prob):
+        if is_leaf(X) and is_leaf(Y):
+            ys = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+            ws = wt[ys] * np.exp(-((x[:, ys] - x[:, t:t + 1]) ** 2).sum(0) / 750.0 ** 2)
+            ws[ys == t] = 0.0
+            if ws.sum() > 0:
+                out[ys] += prob * ws / ws.sum()
+            return
+        cf = pr["child_first"][q]
+        if is_leaf(X):
+            wk = np.maximum(pr[wkey][cf: cf + nd["nchild"][Y]], 0)
+            for kk, Yc in enumerate(kids(Y)):
+                if wk[kk] > 0:
+                    visit(X, Yc, cf + kk, prob * wk[kk] / wk.sum())
+            return
+        i = [j for j, Xc in enumerate(kids(X)) if Xc in anc][0]
+        Xc = kids(X)[i]
+        if is_leaf(Y):
+            if pr[wkey][cf + i] > 0:
+                visit(Xc, Y, cf + i, prob)
+            return
+        ny = nd["nchild"][Y]
+        wk = np.maximum(pr[wkey][cf + i * ny: cf + (i + 1) * ny], 0)
+        for kk, Yc in enumerate(kids(Y)):
+            if wk[kk] > 0:
+                visit(Xc, Yc, cf + i * ny + kk, prob * wk[kk] / wk.sum())
+
+    visit(0, 0, 0, 1.0)
+    res = np.zeros(w.n)
+    res[perm] = out
+    return res
+
+
+def test_descent_distribution_chi2(oracle_mod):
+    """Empirical partner frequencies over many steps follow the exact
+    product-of-levels probabilities (near field only, so every level is in the
+    pair table)."""
+    from scipy import stats
+    w = W.uniform_cube(48, 2500.0, seed=41, leaf_capacity=4, rho_max=0.0, cutoff=50.0)
+    w.vac_axon[:] = 1
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    nsteps = 3000
+    counts = {t: np.zeros(w.n) for t in (0, 7, 23)}
+    for step in range(nsteps):
+        part = o.select_partners(step)["partner"]
+        for t in counts:
+            if part[t] >= 0:
+                counts[t][part[t]] += 1
+    for t, c in counts.items():
+        p = _exact_partner_distribution(o, w, t)
+        assert p.sum() == pytest.approx(1.0, abs=1e-9)
+        assert c[p == 0].sum() == 0
+        big = p * nsteps >= 5
+        obs = np.append(c[big], c[~big].sum())
+        exp = np.append(p[big], p[~big].sum()) * nsteps
+        keep = exp > 0
+        chi2 = ((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+        assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+
+
+def test_shared_choices_within_a_box(oracle_mod):
+    """All axons of a leaf reach the same dendrite leaf (Section 5: neighbours
+    share their choices), so their partners lie in one leaf."""
+    w = W.uniform_cube(600, 6000.0, seed=43, leaf_capacity=8, rho_max=0.0)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    r = o.select_partners(3)
+    nd = o.nodes()
+    _, perm = o.keys()
+    inv = np.argsort(perm)
+    leaf_of_sorted = np.zeros(w.n, np.int64)
+    for k in np.nonzero(nd["child_first"] < 0)[0]:
+        leaf_of_sorted[nd["first"][k]: nd["first"][k] + nd["count"][k]] = k
+    off = np.concatenate([[0], np.cumsum(w.vac_axon.astype(np.int64))])
+    groups = {}
+    for t in range(w.n):
+        for e in range(off[t], off[t + 1]):
+            if r["partner"][e] >= 0:
+                key = (leaf_of_sorted[inv[t]], int(w.type[t]))
+                groups.setdefault(key, set()).add(leaf_of_sorted[inv[r["partner"][e]]])
+    assert groups and all(len(v) == 1 for v in groups.values())
+
+
+def _recount_resolution(oracle_mod, w, partner, step):
+    off = np.concatenate([[0], np.cumsum(w.vac_axon.astype(np.int64))])
+    reqs = []
+    for t in range(w.n):
+        for k in range(w.vac_axon[t]):
+            e = off[t] + k
+            if partner[e] >= 0:
+                prio = oracle_mod.philox([t, k | (3 << 16), step & 0xFFFFFFFF, step >> 32], [0, 0])[0]
+                reqs.append((int(partner[e]), int(w.type[t]), int(prio), int(e)))
+    reqs.sort()
+    acc = np.zeros(len(partner), bool)
+    used = {}
+    for s, ch, _, e in reqs:
+        cap = (w.vac_dend_i if ch else w.vac_dend_e)[s]
+        if used.get((s, ch), 0) < cap:
+            acc[e] = True
+            used[(s, ch)] = used.get((s, ch), 0) + 1
+    return acc
+
+
+def test_resolution_brute_force_recount(oracle_mod):
+    w = W.uniform_cube(900, 5000.0, seed=47, leaf_capacity=8)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    r = o.select_partners(11)
+    acc = _recount_resolution(oracle_mod, w, r["partner"], 11)
+    assert np.array_equal(acc, r["accepted"])
+    assert r["n_syn"] == acc.sum()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_synapse_invariants(oracle_mod, seed):
+    """Formed synapses never exceed min(vacant axonal, vacant dendritic) per
+    type, nor any neuron's vacancies; no autapses; every partner has w > 0."""
+    w = W.clustered_small(1, 3000, seed=seed, leaf_capacity=8, rho_max=0.3)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    r = o.select_partners(seed)
+    pre, post, ty = r["syn_pre"], r["syn_post"], r["syn_type"]
+    for ch in (0, 1):
+        dend = w.vac_dend_i if ch else w.vac_dend_e
+        axons = w.vac_axon[w.type == ch].sum()
+        assert (ty == ch).sum() <= min(int(axons), int(dend.sum()))
+        np.testing.assert_array_less(np.bincount(post[ty == ch], minlength=w.n) - 1, dend.astype(int))
+    assert np.all(np.bincount(pre, minlength=w.n) <= w.vac_axon)
+    assert np.all(pre != post)
+    assert np.all(w.type[pre] == ty)
+    off = np.concatenate([[0], np.cumsum(w.vac_axon.astype(np.int64))])
+    owner = np.repeat(np.arange(w.n), w.vac_axon)
+    ok = r["partner"] >= 0
+    s = r["partner"][ok]
+    wt = np.where(w.type[owner[ok]] == 0, w.vac_dend_e[s], w.vac_dend_i[s])
+    assert np.all(wt > 0)
+    assert len(off) == w.n + 1
+
+
+def test_vacancy_walk_and_commit(oracle_mod):
+    rng = np.random.default_rng(0)
+    a, e, i = (rng.integers(0, 6, 2000).astype(np.uint8) for _ in range(3))
+    a2, e2, i2 = oracle_mod.vacancy_walk(0, 4, a, e, i)
+    for before, after in ((a, a2), (e, e2), (i, i2)):
+        d = after.astype(int) - before.astype(int)
+        assert set(np.unique(d)) <= {-1, 0, 1}
+        assert np.all((after >= 0) & (after <= 5))
+        assert np.all((d == 0) == (((before == 0) & (d == 0)) | ((before == 5) & (d == 0))))
+        assert abs(np.mean(d[(before > 0) & (before < 5)])) < 0.1
+    pre = np.array([0, 0, 3], np.int32)
+    post = np.array([5, 6, 5], np.int32)
+    ty = np.array([0, 1, 0], np.uint8)
+    a3, e3, i3 = oracle_mod.commit_synapses(pre, post, ty, a2, e2, i2)
+    a2, e2, i2 = (v.astype(int) for v in (a2, e2, i2))
+    assert a3[0] == max(a2[0] - 2, 0) and a3[3] == max(a2[3] - 1, 0)
+    assert e3[5] == max(e2[5] - 2, 0) and i3[6] == max(i2[6] - 1, 0)
+
+
+def test_philox_statistics(oracle_mod):
+    """Counter-based uniforms: U in [0,1), flat (chi^2), distinct counters give
+    distinct outputs (the block is a bijection of the counter)."""
+    from scipy import stats
+    us = np.array([oracle_mod.uniform(123, i, 7, 9) for i in range(20000)])
+    assert us.min() >= 0 and us.max() < 1
+    h, _ = np.histogram(us, bins=50, range=(0, 1))
+    assert stats.chisquare(h).pvalue > 1e-4
+    outs = {tuple(oracle_mod.philox([i, 0, 0, 0], [5, 6]).tolist()) for i in range(5000)}
+    assert len(outs) == 5000
+    a = oracle_mod.philox([1, 2, 3, 4], [5, 6])
+    b = oracle_mod.philox([1, 2, 3, 4], [5, 7])
+    assert not np.array_equal(a, b)
