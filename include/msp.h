@@ -1,0 +1,230 @@
+/*
+ * msp.h -- C ABI of the GB300 synapse-search library (libmsp).
+ *
+ * The library computes, on one GPU, the structural-plasticity synapse search
+ * of "Accelerating Brain Simulations with the Fast Multipole Method"
+ * (Noettgen, Czappa, Wolf; arXiv 2301.10570):
+ *
+ *   u(t) = sum_{s != t} w_s exp(-|t - s|^2 / sigma^2)              (Eq. 8)
+ *
+ * for every neuron t with vacant axonal elements, where w_s is the number of
+ * vacant dendritic elements of s of t's type.  The sum is organised on an
+ * octree (Section 3.2) as a fast multipole method: Hermite coefficients of
+ * source boxes (Eq. 7), their translation into Taylor coefficients about a
+ * target box (Eq. 6), evaluation at the targets, and the exact near field.
+ * The same pass yields the attraction between every pair of boxes the
+ * descent of Algorithm 1 can visit; the descent then draws, per axon box and
+ * level, a dendrite box with probability proportional to its attraction
+ * (Algorithm 2) down to a dendrite neuron, and the requests are resolved at
+ * the dendrite side (Section 4).
+ *
+ * Conventions (all entry points):
+ *   - Every pointer named *_dev is a device pointer, *_host a host pointer.
+ *     The caller owns every buffer it passes; the context owns its own
+ *     workspace and frees it in msp_destroy.
+ *   - Neuron arrays are in the caller's order (index 0..n-1); outputs are in
+ *     the same order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; the calls marked "synchronous" wait
+ *     for it before returning.
+ *   - Errors are returned as msp_status; msp_last_error() gives a message
+ *     for the calling thread.  No call throws or aborts.
+ *   - Channels: 0 = excitatory, 1 = inhibitory.  An axon of a type-T neuron
+ *     connects only to vacant dendritic elements of channel T.
+ *   - Results are deterministic for fixed inputs, configuration and step,
+ *     except that the near-field and L2P sums of u may differ in the last
+ *     bits between runs when far pairs are present.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msp_ctx msp_ctx;
+
+typedef enum {
+    MSP_OK = 0,
+    MSP_ERR_INVALID_ARG = 1,  /* bad pointer, size or configuration value    */
+    MSP_ERR_CUDA = 2,         /* a CUDA runtime call failed                  */
+    MSP_ERR_OOM = 3,          /* device allocation failed                    */
+    MSP_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up          */
+    MSP_ERR_NOT_BUILT = 5,    /* call order violated (e.g. no tree yet)      */
+    MSP_ERR_CHECK = 6,        /* a device-side consistency check failed      */
+    MSP_ERR_CAPACITY = 7      /* a size exceeds an index range (> 2^31-1)    */
+} msp_status;
+
+/* Search configuration.
+ *   sigma          kernel width in the units of the positions (Table 1: 750)
+ *   p              expansion terms per dimension, 1..8; multi-indices
+ *                  0 <= alpha_d < p (the paper's alpha=beta=(3,3,3) is p=4)
+ *   leaf_capacity  an octree box is split while it holds more points
+ *   max_depth      deepest octree level, <= 21 (boxes at max_depth never split)
+ *   origin, side   the cube [origin, origin+side)^3 quantised to 2^21 cells
+ *                  per dimension; positions outside are clamped to its faces
+ *   seed           Philox key of every random draw
+ *   rho_max        an expansion is used only for boxes whose half-width is at
+ *                  most rho_max*sigma
+ *   cutoff         box pairs whose minimum distance is at least cutoff*sigma
+ *                  contribute nothing (their kernel is below exp(-cutoff^2))
+ *   m2l_min_pairs  a well-separated pair is translated only if
+ *                  count(X)*count(Y) >= m2l_min_pairs; otherwise it is
+ *                  refined down to the near field                          */
+typedef struct {
+    double    sigma;
+    int       p;
+    int       leaf_capacity;
+    int       max_depth;
+    float     origin[3];
+    float     side;
+    uint64_t  seed;
+    double    rho_max;
+    double    cutoff;
+    long long m2l_min_pairs;
+} msp_config;
+
+/* Sizes and operation counts of the last build / attraction / selection. */
+typedef struct {
+    int64_t n;                 /* neurons                                   */
+    int64_t n_nodes;           /* octree boxes                              */
+    int64_t n_leaves;
+    int32_t tree_depth;        /* deepest level present                     */
+    int32_t far_level;         /* shallowest level allowed to carry expansions */
+    int64_t n_pairs;           /* box pairs visited by the dual traversal   */
+    int32_t pair_depths;
+    int64_t n_far;             /* translated (M2L) pairs                    */
+    int64_t n_p2p;             /* near-field leaf pairs                     */
+    int64_t p2p_interactions;  /* target-source evaluations in the near field */
+    int64_t n_elements;        /* vacant axonal elements (sum of vac_axon)  */
+    int64_t n_draws;           /* tree-level + leaf draws of the last selection */
+    int64_t n_requests;        /* elements that drew a partner              */
+    int64_t n_synapses;        /* accepted requests                         */
+    int64_t expansion_nodes;   /* boxes carrying expansions                 */
+} msp_stats;
+
+/* Create a context on CUDA device `device` (cudaSetDevice is called).
+ * Ownership: the caller destroys it with msp_destroy.  Errors:
+ * MSP_ERR_INVALID_ARG for a configuration outside the ranges above. */
+msp_status msp_create(msp_ctx **out, const msp_config *cfg, int device);
+msp_status msp_destroy(msp_ctx *ctx);
+
+/* Steps a1-a4 (Section 3.2): Morton keys of the positions, a stable radix
+ * sort, the adaptive octree (level by level; a box with more than
+ * leaf_capacity points is split into its non-empty octants) and, per box,
+ * the sums of vacant axonal elements per channel, vacant dendritic elements
+ * per channel, and the axon- and dendrite-weighted centroids.
+ *   x_dev,y_dev,z_dev    n floats each (SoA positions)
+ *   type_dev             n bytes, 0/1
+ *   vac_axon_dev         n bytes, vacant axonal elements of the neuron's type
+ *   vac_dend_e_dev/_i    n bytes, vacant dendritic elements per channel
+ * The inputs are read during the call's stream work only; the context keeps
+ * its own sorted copy.  Synchronous (the per-level node counts are read
+ * back).  n may be 0.  Errors: MSP_ERR_INVALID_ARG (n < 0, n > 2^31-2, null
+ * pointer with n > 0), MSP_ERR_OOM. */
+msp_status msp_build_tree(msp_ctx *ctx, int64_t n, const float *x_dev, const float *y_dev,
+                          const float *z_dev, const uint8_t *type_dev,
+                          const uint8_t *vac_axon_dev, const uint8_t *vac_dend_e_dev,
+                          const uint8_t *vac_dend_i_dev, void *stream);
+
+/* Steps a5-a10: dual traversal (Algorithm 1's pairing of axon and dendrite
+ * boxes, refined until a pair is pruned by the cutoff, translated, or a
+ * near-field leaf pair), Hermite coefficients (Eq. 7), Hermite-to-Taylor
+ * translation (composition of Eq. 7 and Eq. 6), Taylor evaluation (Eq. 6),
+ * exact near field (Eq. 8), and the box-pair attraction table.
+ *   u_dev   n floats out: u(t) of the neuron's own channel if vac_axon > 0,
+ *           else 0.  May be NULL (only the pair table is produced).
+ * Requires msp_build_tree.  Synchronous (per-depth pair counts are read
+ * back).  Errors: MSP_ERR_NOT_BUILT, MSP_ERR_OOM, MSP_ERR_CAPACITY. */
+msp_status msp_attraction(msp_ctx *ctx, float *u_dev, void *stream);
+
+/* The comparison path: Eq. 8 by all-pairs evaluation over every neuron, on
+ * the tree's sorted copy (no cutoff, no expansion).  Same output convention
+ * as msp_attraction.  Requires msp_build_tree.  Asynchronous. */
+msp_status msp_direct(msp_ctx *ctx, float *u_dev, void *stream);
+
+/* Steps a11-a12: Algorithm 1 with Algorithm 2's choice at every level, a
+ * per-element draw inside the chosen dendrite leaf, and request resolution.
+ *   step            plasticity step number, part of every Philox counter
+ *   partner_dev     n_elements int32 out: the dendrite neuron drawn by each
+ *                   vacant axonal element (elements ordered by neuron, then
+ *                   element index; n_elements = sum of vac_axon), -1 if none
+ *   syn_pre_dev, syn_post_dev (int32), syn_type_dev (uint8): capacity
+ *                   n_elements; the accepted synapses in element order
+ *   n_syn_dev       one int64 out: number of synapses written
+ * Requires msp_attraction.  Synchronous.  Errors: MSP_ERR_NOT_BUILT. */
+msp_status msp_select_partners(msp_ctx *ctx, uint64_t step, int32_t *partner_dev,
+                               int32_t *syn_pre_dev, int32_t *syn_post_dev,
+                               uint8_t *syn_type_dev, int64_t *n_syn_dev, void *stream);
+
+/* One whole plasticity step (build + attraction + selection) from HOST
+ * buffers: copies the inputs to the device, runs the path, and copies
+ * u, partner and the synapse list back.  Host buffers should be pinned for
+ * full copy bandwidth.  partner_host and syn_* have capacity sum(vac_axon).
+ * u_host may be NULL.  Returns the synapse count in *n_syn_host.
+ * Synchronous. */
+msp_status msp_plasticity_step_host(msp_ctx *ctx, int64_t n, uint64_t step,
+                                    const float *x_host, const float *y_host,
+                                    const float *z_host, const uint8_t *type_host,
+                                    const uint8_t *vac_axon_host,
+                                    const uint8_t *vac_dend_e_host,
+                                    const uint8_t *vac_dend_i_host, float *u_host,
+                                    int32_t *partner_host, int32_t *syn_pre_host,
+                                    int32_t *syn_post_host, uint8_t *syn_type_host,
+                                    int64_t *n_syn_host);
+
+/* Vacancy random walk used by the 100-step clustered run: every neuron's
+ * vacant axonal and dendritic counts move by +1 or -1 (Philox, tag WALK,
+ * counter (neuron, channel, step)), clamped to [0,5].  In place, n bytes
+ * each.  Asynchronous. */
+msp_status msp_vacancy_walk(msp_ctx *ctx, int64_t n, uint64_t step, uint8_t *vac_axon_dev,
+                            uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev, void *stream);
+
+/* Formed synapses occupy their elements (Section 3.1: vacant = elements -
+ * synapses): decrement vac_axon of each pre neuron and the dendritic count
+ * of the synapse's channel of each post neuron, saturating at 0.
+ * n_syn_dev is read on the device.  Asynchronous. */
+msp_status msp_commit_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t capacity,
+                               const int32_t *syn_pre_dev, const int32_t *syn_post_dev,
+                               const uint8_t *syn_type_dev, uint8_t *vac_axon_dev,
+                               uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev,
+                               void *stream);
+
+/* Sizes and counts of the last calls.  Synchronous. */
+msp_status msp_get_stats(msp_ctx *ctx, msp_stats *out);
+
+/* Copies of internal arrays for parity tests (all HOST pointers, sizes from
+ * msp_get_stats; any pointer may be NULL to skip that array).  Synchronous.
+ *   keys (n uint64, sorted Morton keys), perm (n int32, caller index of each
+ *   sorted position); per box: level, prefix (Morton code at its level),
+ *   first, count, parent, child_first (-1 for a leaf), nchild,
+ *   sums4 (n_nodes x {axon E, axon I, dendrite E, dendrite I}),
+ *   cent6 (n_nodes x {axon centroid xyz, dendrite centroid xyz}). */
+msp_status msp_export_tree(msp_ctx *ctx, uint64_t *keys, int32_t *perm, uint8_t *level,
+                           uint64_t *prefix, int32_t *first, int32_t *count, int32_t *parent,
+                           int32_t *child_first, uint8_t *nchild, int32_t *sums4,
+                           float *cent6);
+
+/* Box pairs of the dual traversal (HOST pointers, n_pairs each; depth_start
+ * has pair_depths+1 entries): kind 0 split, 1 far (translated), 2 near-field
+ * leaf pair, 3 pruned; w_e / w_i the pair attraction per channel. */
+msp_status msp_export_pairs(msp_ctx *ctx, int32_t *X, int32_t *Y, uint8_t *kind,
+                            int32_t *child_first, double *w_e, double *w_i,
+                            int64_t *depth_start);
+
+/* Expansions of the boxes at level >= far_level, HOST float arrays of
+ * expansion_nodes x 2 x p^3 each (channel-major): A (Hermite coefficients of
+ * the dendritic weights), M (axon moments), B (accumulated Taylor
+ * coefficients); first_node receives the index of the first such box. */
+msp_status msp_export_expansions(msp_ctx *ctx, float *A, float *M, float *B,
+                                 int64_t *first_node);
+
+/* Message of the last error of the calling thread ("" if none). */
+const char *msp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

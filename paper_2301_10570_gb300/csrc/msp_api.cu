@@ -1,0 +1,357 @@
+// msp_api.cu -- the C ABI of include/msp.h: argument checks, context
+// lifetime, error conversion, and the host-buffer plasticity step.
+#include <cmath>
+#include <cstring>
+
+#include "msp_internal.cuh"
+
+namespace msp {
+void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const float* z,
+                const uint8_t* type, const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
+                cudaStream_t s);
+void attraction(msp_ctx& c, float* u_dev, cudaStream_t s);
+void direct(msp_ctx& c, float* u_dev, cudaStream_t s);
+void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const uint8_t* va_dev,
+                     const uint8_t* vde_dev, const uint8_t* vdi_dev, int32_t* partner,
+                     int32_t* syn_pre, int32_t* syn_post, uint8_t* syn_type, int64_t* n_syn,
+                     cudaStream_t s);
+void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde, uint8_t* vdi,
+                  cudaStream_t s);
+void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const int32_t* pre,
+                     const int32_t* post, const uint8_t* styp, uint8_t* va, uint8_t* vde,
+                     uint8_t* vdi, cudaStream_t s);
+}  // namespace msp
+
+namespace {
+
+thread_local std::string g_last_error;
+
+msp_status fail(msp_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+template <class F>
+msp_status guarded(msp_ctx* c, F&& f) {
+    if (!c) return fail(MSP_ERR_INVALID_ARG, "null context");
+    try {
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return fail(MSP_ERR_CUDA, cudaGetErrorString(e));
+        f();
+        g_last_error.clear();
+        return MSP_OK;
+    } catch (const msp::Error& e) {
+        return fail(e.code, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(MSP_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(MSP_ERR_CUDA, e.what());
+    }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void require(bool ok, const char* msg) {
+    if (!ok) throw msp::Error(MSP_ERR_INVALID_ARG, msg);
+}
+
+void derive(msp_ctx& c) {
+    const msp_config& cfg = c.cfg;
+    c.morton_scale = (float)((double)(1u << msp::kMortonBits) / (double)cfg.side);
+    // boxes whose half-width is at most rho_max * sigma may carry expansions
+    c.l_far = cfg.max_depth + 1;
+    for (int l = 0; l <= cfg.max_depth; ++l)
+        if ((double)cfg.side / std::ldexp(1.0, l + 1) <= cfg.rho_max * cfg.sigma) {
+            c.l_far = l;
+            break;
+        }
+    // prune a pair when (sum of squared gaps in boxes of level l) * side_l^2
+    // >= (cutoff * sigma)^2
+    for (int l = 0; l <= msp::kMortonBits; ++l) {
+        double bl = (double)cfg.side / std::ldexp(1.0, l);
+        double r = cfg.cutoff * cfg.sigma / bl;
+        c.g2[l] = (long long)std::ceil(r * r);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* msp_last_error(void) { return g_last_error.c_str(); }
+
+msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
+    if (!out || !cfg) return fail(MSP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(cfg->sigma > 0.0) || cfg->p < 1 || cfg->p > msp::kMaxP || cfg->leaf_capacity < 1 ||
+        cfg->max_depth < 0 || cfg->max_depth > msp::kMortonBits || !(cfg->side > 0.0f) ||
+        !(cfg->rho_max >= 0.0) || !(cfg->cutoff > 0.0) || cfg->m2l_min_pairs < 0 ||
+        !std::isfinite(cfg->origin[0]) || !std::isfinite(cfg->origin[1]) ||
+        !std::isfinite(cfg->origin[2]) || !std::isfinite(cfg->side))
+        return fail(MSP_ERR_INVALID_ARG, "configuration value out of range");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(MSP_ERR_CUDA, cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(MSP_ERR_INVALID_ARG, "no such CUDA device");
+    msp_ctx* c = new (std::nothrow) msp_ctx();
+    if (!c) return fail(MSP_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->device = device;
+    msp_status st = guarded(c, [&] {
+        MSP_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+        MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->small_host), 16 * sizeof(int64_t)));
+        derive(*c);
+    });
+    if (st != MSP_OK) {
+        msp_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MSP_OK;
+}
+
+msp_status msp_destroy(msp_ctx* c) {
+    if (!c) return MSP_OK;
+    cudaSetDevice(c->device);
+    msp::DBuf* bufs[] = {&c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->perm, &c->inv, &c->pts,
+                         &c->wts, &c->lw, &c->elem_off, &c->leaf_of, &c->nd_level, &c->nd_prefix,
+                         &c->nd_first, &c->nd_count, &c->nd_parent, &c->nd_child_first,
+                         &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
+                         &c->pr_kind, &c->pr_cf, &c->pr_w, &c->far_q, &c->p2p_key0,
+                         &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
+                         &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
+                         &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
+                         &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
+                         &c->small_dev, &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
+                         &c->h_post, &c->h_type, &c->h_nsyn, &c->c_type, &c->c_va,
+                         &c->c_vde, &c->c_vdi};
+    for (msp::DBuf* b : bufs) b->release();
+    for (auto& b : c->h_in) b.release();
+    if (c->small_host) cudaFreeHost(c->small_host);
+    delete c;
+    return MSP_OK;
+}
+
+msp_status msp_build_tree(msp_ctx* c, int64_t n, const float* x, const float* y, const float* z,
+                          const uint8_t* type, const uint8_t* va, const uint8_t* vde,
+                          const uint8_t* vdi, void* stream) {
+    return guarded(c, [&] {
+        require(n >= 0 && n < 0x7ffffffell, "n out of range");
+        require(n == 0 || (x && y && z && type && va && vde && vdi), "null input pointer");
+        cudaStream_t s = as_stream(stream);
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        uint8_t* ct = c->c_type.ensure<uint8_t>(nn);
+        uint8_t* ca = c->c_va.ensure<uint8_t>(nn);
+        uint8_t* ce = c->c_vde.ensure<uint8_t>(nn);
+        uint8_t* ci = c->c_vdi.ensure<uint8_t>(nn);
+        if (n > 0) {
+            MSP_CUDA(cudaMemcpyAsync(ct, type, n, cudaMemcpyDeviceToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(ca, va, n, cudaMemcpyDeviceToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(ce, vde, n, cudaMemcpyDeviceToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(ci, vdi, n, cudaMemcpyDeviceToDevice, s));
+        }
+        c->in_type = ct; c->in_va = ca; c->in_vde = ce; c->in_vdi = ci;
+        msp::build_tree(*c, n, x, y, z, ct, ca, ce, ci, s);
+    });
+}
+
+msp_status msp_attraction(msp_ctx* c, float* u, void* stream) {
+    return guarded(c, [&] { msp::attraction(*c, u, as_stream(stream)); });
+}
+
+msp_status msp_direct(msp_ctx* c, float* u, void* stream) {
+    return guarded(c, [&] {
+        require(u || (c && c->n == 0), "null output pointer");
+        msp::direct(*c, u, as_stream(stream));
+    });
+}
+
+msp_status msp_select_partners(msp_ctx* c, uint64_t step, int32_t* partner, int32_t* pre,
+                               int32_t* post, uint8_t* styp, int64_t* n_syn, void* stream) {
+    return guarded(c, [&] {
+        require(n_syn != nullptr, "null n_syn");
+        require(c->n_elem == 0 || (partner && pre && post && styp), "null output pointer");
+        require(c->in_type != nullptr || c->n == 0, "inputs of the build are not available");
+        msp::select_partners(*c, step, c->in_type, c->in_va, c->in_vde, c->in_vdi, partner, pre,
+                             post, styp, n_syn, as_stream(stream));
+    });
+}
+
+msp_status msp_plasticity_step_host(msp_ctx* c, int64_t n, uint64_t step, const float* x,
+                                    const float* y, const float* z, const uint8_t* type,
+                                    const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
+                                    float* u, int32_t* partner, int32_t* pre, int32_t* post,
+                                    uint8_t* styp, int64_t* n_syn) {
+    return guarded(c, [&] {
+        require(n >= 0 && n < 0x7ffffffell, "n out of range");
+        require(n == 0 || (x && y && z && type && va && vde && vdi), "null input pointer");
+        require(n_syn != nullptr, "null n_syn");
+        cudaStream_t s = 0;
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        float* dx = c->h_in[0].ensure<float>(nn);
+        float* dy = c->h_in[1].ensure<float>(nn);
+        float* dz = c->h_in[2].ensure<float>(nn);
+        uint8_t* dt = c->h_in[3].ensure<uint8_t>(nn);
+        uint8_t* da = c->h_in[4].ensure<uint8_t>(nn);
+        uint8_t* de = c->h_in[5].ensure<uint8_t>(nn);
+        uint8_t* di = c->h_in[6].ensure<uint8_t>(nn);
+        if (n > 0) {
+            MSP_CUDA(cudaMemcpyAsync(dx, x, n * 4, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(dy, y, n * 4, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(dz, z, n * 4, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(dt, type, n, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(da, va, n, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(de, vde, n, cudaMemcpyHostToDevice, s));
+            MSP_CUDA(cudaMemcpyAsync(di, vdi, n, cudaMemcpyHostToDevice, s));
+        }
+        c->in_type = dt; c->in_va = da; c->in_vde = de; c->in_vdi = di;
+        msp::build_tree(*c, n, dx, dy, dz, dt, da, de, di, s);
+        float* du = u ? c->h_u.ensure<float>(nn) : nullptr;
+        msp::attraction(*c, du, s);
+        size_t ne = (size_t)(c->n_elem > 0 ? c->n_elem : 1);
+        require(c->n_elem == 0 || (partner && pre && post && styp), "null output pointer");
+        int32_t* dp = c->h_partner.ensure<int32_t>(ne);
+        int32_t* dpre = c->h_pre.ensure<int32_t>(ne);
+        int32_t* dpost = c->h_post.ensure<int32_t>(ne);
+        uint8_t* dst = c->h_type.ensure<uint8_t>(ne);
+        int64_t* dn = c->h_nsyn.ensure<int64_t>(1);
+        msp::select_partners(*c, step, dt, da, de, di, dp, dpre, dpost, dst, dn, s);
+        int64_t ns = c->n_synapses;
+        if (u && n > 0) MSP_CUDA(cudaMemcpyAsync(u, du, n * 4, cudaMemcpyDeviceToHost, s));
+        if (c->n_elem > 0) {
+            MSP_CUDA(cudaMemcpyAsync(partner, dp, c->n_elem * 4, cudaMemcpyDeviceToHost, s));
+            if (ns > 0) {
+                MSP_CUDA(cudaMemcpyAsync(pre, dpre, ns * 4, cudaMemcpyDeviceToHost, s));
+                MSP_CUDA(cudaMemcpyAsync(post, dpost, ns * 4, cudaMemcpyDeviceToHost, s));
+                MSP_CUDA(cudaMemcpyAsync(styp, dst, ns, cudaMemcpyDeviceToHost, s));
+            }
+        }
+        MSP_CUDA(cudaStreamSynchronize(s));
+        *n_syn = ns;
+    });
+}
+
+msp_status msp_vacancy_walk(msp_ctx* c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde,
+                            uint8_t* vdi, void* stream) {
+    return guarded(c, [&] {
+        require(n >= 0, "n out of range");
+        require(n == 0 || (va && vde && vdi), "null pointer");
+        msp::vacancy_walk(*c, n, step, va, vde, vdi, as_stream(stream));
+    });
+}
+
+msp_status msp_commit_synapses(msp_ctx* c, const int64_t* n_syn, int64_t capacity,
+                               const int32_t* pre, const int32_t* post, const uint8_t* styp,
+                               uint8_t* va, uint8_t* vde, uint8_t* vdi, void* stream) {
+    return guarded(c, [&] {
+        require(capacity >= 0, "capacity out of range");
+        require(capacity == 0 || (n_syn && pre && post && styp && va && vde && vdi),
+                "null pointer");
+        msp::commit_synapses(*c, n_syn, capacity, pre, post, styp, va, vde, vdi,
+                             as_stream(stream));
+    });
+}
+
+msp_status msp_get_stats(msp_ctx* c, msp_stats* out) {
+    return guarded(c, [&] {
+        require(out != nullptr, "null output");
+        MSP_CUDA(cudaDeviceSynchronize());
+        std::memset(out, 0, sizeof(*out));
+        out->n = c->n;
+        out->n_nodes = c->n_nodes;
+        out->tree_depth = c->tree_depth;
+        out->far_level = c->l_far;
+        out->n_pairs = c->n_pairs;
+        out->pair_depths = (int32_t)(c->depth_start.empty() ? 0 : c->depth_start.size() - 1);
+        out->n_far = c->n_far;
+        out->n_p2p = c->n_p2p;
+        out->p2p_interactions = c->p2p_interactions;
+        out->n_elements = c->n_elem;
+        out->n_draws = c->n_draws;
+        out->n_requests = c->n_requests;
+        out->n_synapses = c->n_synapses;
+        out->expansion_nodes = c->exp_nodes;
+        if (c->n_nodes > 0) {
+            std::vector<int32_t> cf((size_t)c->n_nodes);
+            MSP_CUDA(cudaMemcpy(cf.data(), c->nd_child_first.p, cf.size() * 4,
+                                cudaMemcpyDeviceToHost));
+            int64_t leaves = 0;
+            for (int32_t v : cf) leaves += v < 0;
+            out->n_leaves = leaves;
+        }
+    });
+}
+
+msp_status msp_export_tree(msp_ctx* c, uint64_t* keys, int32_t* perm, uint8_t* level,
+                           uint64_t* prefix, int32_t* first, int32_t* count, int32_t* parent,
+                           int32_t* child_first, uint8_t* nchild, int32_t* sums4, float* cent6) {
+    return guarded(c, [&] {
+        if (!c->tree_built) throw msp::Error(MSP_ERR_NOT_BUILT, "no tree");
+        MSP_CUDA(cudaDeviceSynchronize());
+        const size_t n = (size_t)c->n, m = (size_t)c->n_nodes;
+        auto cp = [](void* dst, const void* src, size_t bytes) {
+            if (dst && bytes) MSP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        };
+        cp(keys, c->keys0.p, n * 8);
+        cp(perm, c->perm.p, n * 4);
+        cp(level, c->nd_level.p, m);
+        cp(prefix, c->nd_prefix.p, m * 8);
+        cp(first, c->nd_first.p, m * 4);
+        cp(count, c->nd_count.p, m * 4);
+        cp(parent, c->nd_parent.p, m * 4);
+        cp(child_first, c->nd_child_first.p, m * 4);
+        cp(nchild, c->nd_nchild.p, m);
+        cp(sums4, c->nd_sums.p, m * 16);
+        if (cent6 && m) {
+            std::vector<float> a(4 * m), d(4 * m);
+            cp(a.data(), c->nd_ca.p, m * 16);
+            cp(d.data(), c->nd_cd.p, m * 16);
+            for (size_t i = 0; i < m; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    cent6[6 * i + k] = a[4 * i + k];
+                    cent6[6 * i + 3 + k] = d[4 * i + k];
+                }
+        }
+    });
+}
+
+msp_status msp_export_pairs(msp_ctx* c, int32_t* X, int32_t* Y, uint8_t* kind,
+                            int32_t* child_first, double* w_e, double* w_i,
+                            int64_t* depth_start) {
+    return guarded(c, [&] {
+        if (!c->attraction_done) throw msp::Error(MSP_ERR_NOT_BUILT, "no attraction");
+        MSP_CUDA(cudaDeviceSynchronize());
+        const size_t m = (size_t)c->n_pairs;
+        auto cp = [](void* dst, const void* src, size_t bytes) {
+            if (dst && bytes) MSP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        };
+        cp(X, c->pr_X.p, m * 4);
+        cp(Y, c->pr_Y.p, m * 4);
+        cp(kind, c->pr_kind.p, m);
+        cp(child_first, c->pr_cf.p, m * 4);
+        if ((w_e || w_i) && m) {
+            std::vector<double> w(2 * m);
+            cp(w.data(), c->pr_w.p, m * 16);
+            for (size_t i = 0; i < m; ++i) {
+                if (w_e) w_e[i] = w[2 * i];
+                if (w_i) w_i[i] = w[2 * i + 1];
+            }
+        }
+        if (depth_start)
+            for (size_t d = 0; d < c->depth_start.size(); ++d) depth_start[d] = c->depth_start[d];
+    });
+}
+
+msp_status msp_export_expansions(msp_ctx* c, float* A, float* M, float* B, int64_t* first_node) {
+    return guarded(c, [&] {
+        if (!c->attraction_done) throw msp::Error(MSP_ERR_NOT_BUILT, "no attraction");
+        MSP_CUDA(cudaDeviceSynchronize());
+        size_t m = (size_t)c->exp_nodes * 2 * c->cfg.p * c->cfg.p * c->cfg.p * sizeof(float);
+        if (A && m) MSP_CUDA(cudaMemcpy(A, c->expA.p, m, cudaMemcpyDeviceToHost));
+        if (M && m) MSP_CUDA(cudaMemcpy(M, c->expM.p, m, cudaMemcpyDeviceToHost));
+        if (B && m) MSP_CUDA(cudaMemcpy(B, c->expB.p, m, cudaMemcpyDeviceToHost));
+        if (first_node) *first_node = c->exp_first;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,785 @@
+// msp_fmm.cu -- steps a5-a10: dual traversal with the separation / cutoff
+// rule, Hermite coefficients (Eq. 7), Hermite-to-Taylor translation (Eq. 7
+// composed with the Taylor expansion of Eq. 6), Taylor evaluation (Eq. 6), the
+// exact near field (Eq. 8) and the box-pair attraction table; plus the
+// all-pairs comparison path.
+#include <cmath>
+
+#include "msp_internal.cuh"
+
+namespace msp {
+
+struct Geo {
+    long long g2[kMortonBits + 1];   // prune when sum of squared box gaps >= g2[level]
+    int l_far;                       // boxes at level >= l_far may carry expansions
+    long long m2l_min_pairs;
+};
+
+__device__ inline float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__constant__ float c_inv_fact[kMaxP] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f,
+                                        1.f / 720.f, 1.f / 5040.f};
+
+namespace {
+
+struct NodeView {
+    const uint8_t* level;
+    const uint64_t* prefix;
+    const int32_t* first;
+    const int32_t* count;
+    const int32_t* child_first;
+    const uint8_t* nchild;
+    const int4* sums;
+};
+
+__device__ inline uint8_t classify(const NodeView& nv, const Geo& geo, int32_t X, int32_t Y) {
+    int4 sx = nv.sums[X], sy = nv.sums[Y];
+    if (sx.x + sx.y == 0 || sy.z + sy.w == 0) return kPruned;
+    int lx = nv.level[X], ly = nv.level[Y];
+    int lf = lx > ly ? lx : ly;
+    uint64_t px = nv.prefix[X], py = nv.prefix[Y];
+    long long gsum = 0, gmax = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        long long lox = (long long)compact_by3(px >> (2 - d)) << (lf - lx);
+        long long hix = lox + (1ll << (lf - lx));
+        long long loy = (long long)compact_by3(py >> (2 - d)) << (lf - ly);
+        long long hiy = loy + (1ll << (lf - ly));
+        long long g = 0;
+        if (loy - hix > g) g = loy - hix;
+        if (lox - hiy > g) g = lox - hiy;
+        gsum += g * g;
+        if (g > gmax) gmax = g;
+    }
+    if (gsum >= geo.g2[lf]) return kPruned;
+    int lmin = lx < ly ? lx : ly;
+    if (lmin >= geo.l_far && gmax >= 1 &&
+        (long long)nv.count[X] * (long long)nv.count[Y] >= geo.m2l_min_pairs)
+        return kFar;
+    if (nv.child_first[X] < 0 && nv.child_first[Y] < 0) return kP2P;
+    return kSplit;
+}
+
+__device__ inline int block_size(const NodeView& nv, int32_t X, int32_t Y) {
+    bool lx = nv.child_first[X] < 0, ly = nv.child_first[Y] < 0;
+    return (lx ? 1 : nv.nchild[X]) * (ly ? 1 : nv.nchild[Y]);
+}
+
+__global__ void k_classify(int64_t q0, int64_t nq, NodeView nv, Geo geo,
+                           const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+                           uint8_t* __restrict__ kind, int32_t* __restrict__ cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = q0 + k;
+        int32_t X = pX[q], Y = pY[q];
+        uint8_t kd = classify(nv, geo, X, Y);
+        kind[q] = kd;
+        cnt[k] = kd == kSplit ? block_size(nv, X, Y) : 0;
+    }
+}
+
+// children of a split pair, one contiguous block, axon-child major
+__global__ void k_emit_pairs(int64_t q0, int64_t nq, int64_t next0, NodeView nv,
+                             const uint8_t* __restrict__ kind, const int32_t* __restrict__ off,
+                             int32_t* __restrict__ pX, int32_t* __restrict__ pY,
+                             int32_t* __restrict__ pcf, double2* __restrict__ pw) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = q0 + k;
+        pw[q] = make_double2(0.0, 0.0);
+        if (kind[q] != kSplit) {
+            pcf[q] = -1;
+            continue;
+        }
+        int32_t X = pX[q], Y = pY[q];
+        int64_t cf = next0 + off[k];
+        pcf[q] = (int32_t)cf;
+        int32_t cx = nv.child_first[X], cy = nv.child_first[Y];
+        if (cx >= 0 && cy >= 0) {
+            int nx = nv.nchild[X], ny = nv.nchild[Y];
+            for (int i = 0; i < nx; ++i)
+                for (int j = 0; j < ny; ++j) {
+                    pX[cf + i * ny + j] = cx + i;
+                    pY[cf + i * ny + j] = cy + j;
+                }
+        } else if (cx < 0) {
+            int ny = nv.nchild[Y];
+            for (int j = 0; j < ny; ++j) {
+                pX[cf + j] = X;
+                pY[cf + j] = cy + j;
+            }
+        } else {
+            int nx = nv.nchild[X];
+            for (int i = 0; i < nx; ++i) {
+                pX[cf + i] = cx + i;
+                pY[cf + i] = Y;
+            }
+        }
+    }
+}
+
+__global__ void k_flag_kind(const uint8_t* __restrict__ kind, int64_t n, uint8_t K,
+                            int32_t* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = kind[i] == K;
+}
+
+__global__ void k_compact_kind(const uint8_t* __restrict__ kind, int64_t n, uint8_t K,
+                               const int32_t* __restrict__ off, const int32_t* __restrict__ pX,
+                               int32_t* __restrict__ out_q, uint64_t* __restrict__ out_key) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (kind[i] == K) {
+            int32_t o = off[i];
+            out_q[o] = (int32_t)i;
+            if (out_key) out_key[o] = (uint64_t)pX[i];
+        }
+}
+
+__global__ void k_seg_flags(const uint64_t* __restrict__ key, int64_t n, int32_t* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_first(const int32_t* __restrict__ flag, const int32_t* __restrict__ off,
+                            int64_t n, int32_t* __restrict__ seg_first) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) seg_first[off[i]] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// a6: Hermite coefficients of the dendritic weights (Eq. 7) and axon moments
+// M_beta = sum_t a_t ((t - c_A)/sigma)^beta, per channel, one block per box
+// ---------------------------------------------------------------------------
+constexpr int kP2MThreads = 128;
+constexpr int kP2MChunk = 32;
+
+__global__ void __launch_bounds__(kP2MThreads)
+k_p2m(int64_t first_node, int p, float inv_sigma, const float4* __restrict__ pts,
+      const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
+      const float4* __restrict__ ca, const float4* __restrict__ cd, float* __restrict__ A,
+      float* __restrict__ M) {
+    __shared__ float ypow[kP2MChunk][3][kMaxP];
+    __shared__ float xpow[kP2MChunk][3][kMaxP];
+    __shared__ float wgt[kP2MChunk][4];
+    const int64_t node = first_node + blockIdx.x;
+    const int p3 = p * p * p;
+    const float4 cD = cd[node], cA = ca[node];
+    const int32_t f = nfirst[node], c = ncount[node];
+    constexpr int kMaxAcc = (4 * kMaxP * kMaxP * kMaxP + kP2MThreads - 1) / kP2MThreads;
+    float acc[kMaxAcc];
+#pragma unroll
+    for (int r = 0; r < kMaxAcc; ++r) acc[r] = 0.f;
+    for (int base = 0; base < c; base += kP2MChunk) {
+        int m = min(kP2MChunk, c - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * 3; t += kP2MThreads) {
+            int j = t / 3, d = t % 3;
+            float4 P = pts[f + base + j];
+            float pv = d == 0 ? P.x : (d == 1 ? P.y : P.z);
+            float yv = (pv - (d == 0 ? cD.x : (d == 1 ? cD.y : cD.z))) * inv_sigma;
+            float xv = (pv - (d == 0 ? cA.x : (d == 1 ? cA.y : cA.z))) * inv_sigma;
+            float py = 1.f, px = 1.f;
+            for (int k = 0; k < p; ++k) {
+                ypow[j][d][k] = py;
+                xpow[j][d][k] = px;
+                py *= yv;
+                px *= xv;
+            }
+            if (d == 0) {
+                uint32_t w = __float_as_uint(P.w);
+                float a = (float)pk_axon(w);
+                bool inh = pk_type(w) != 0;
+                wgt[j][0] = (float)pk_de(w);
+                wgt[j][1] = (float)pk_di(w);
+                wgt[j][2] = inh ? 0.f : a;
+                wgt[j][3] = inh ? a : 0.f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kMaxAcc; ++r) {
+            int idx = threadIdx.x + r * kP2MThreads;
+            if (idx >= 4 * p3) continue;
+            int which = idx / p3, a = idx - which * p3;
+            int a0 = a / (p * p), a1 = (a / p) % p, a2 = a % p;
+            float s = acc[r];
+            if (which < 2) {
+                for (int j = 0; j < m; ++j)
+                    s = fmaf(wgt[j][which] * ypow[j][0][a0], ypow[j][1][a1] * ypow[j][2][a2], s);
+            } else {
+                for (int j = 0; j < m; ++j)
+                    s = fmaf(wgt[j][which] * xpow[j][0][a0], xpow[j][1][a1] * xpow[j][2][a2], s);
+            }
+            acc[r] = s;
+        }
+    }
+    const int64_t e = (int64_t)blockIdx.x;
+#pragma unroll
+    for (int r = 0; r < kMaxAcc; ++r) {
+        int idx = threadIdx.x + r * kP2MThreads;
+        if (idx >= 4 * p3) continue;
+        int which = idx / p3, a = idx - which * p3;
+        int a0 = a / (p * p), a1 = (a / p) % p, a2 = a % p;
+        if (which < 2)
+            A[(e * 2 + which) * p3 + a] = acc[r] * c_inv_fact[a0] * c_inv_fact[a1] * c_inv_fact[a2];
+        else
+            M[(e * 2 + which - 2) * p3 + a] = acc[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7: translation of one channel, cooperatively by a warp.  With
+// Delta = (c_A - c_D)/sigma and H_d[n] = h_n(Delta_d):
+//   B_beta = (-1)^|beta| / beta!  sum_alpha A_alpha H0[a0+b0] H1[a1+b1] H2[a2+b2]
+// done as three passes over one dimension each (p^4 multiply-adds per pass).
+// On return Bout (shared) holds B; the return value is sum_beta B_beta M_beta.
+// ---------------------------------------------------------------------------
+__device__ inline void hermite_table(float x, int nmax, float* h) {
+    float h0 = __expf(-x * x);
+    h[0] = h0;
+    if (nmax >= 1) h[1] = 2.f * x * h0;
+    for (int k = 1; k < nmax; ++k) h[k + 1] = 2.f * x * h[k] - 2.f * (float)k * h[k - 1];
+}
+
+__device__ float warp_m2l(int p, const float* __restrict__ Ag, const float* __restrict__ Mg,
+                          const float* H /*smem 3 x 16*/, float* src, float* t1, float* Bout) {
+    const int lane = threadIdx.x & 31;
+    const int p2 = p * p, p3 = p2 * p;
+    for (int i = lane; i < p3; i += 32) src[i] = Ag[i];
+    __syncwarp();
+    for (int o = lane; o < p3; o += 32) {        // (b0, a1, a2)
+        int b0 = o / p2, r = o - b0 * p2;
+        float s = 0.f;
+        for (int a0 = 0; a0 < p; ++a0) s = fmaf(H[a0 + b0], src[a0 * p2 + r], s);
+        t1[o] = s;
+    }
+    __syncwarp();
+    for (int o = lane; o < p3; o += 32) {        // (b0, b1, a2)
+        int b0 = o / p2, b1 = (o / p) % p, a2 = o % p;
+        float s = 0.f;
+        for (int a1 = 0; a1 < p; ++a1) s = fmaf(H[16 + a1 + b1], t1[b0 * p2 + a1 * p + a2], s);
+        src[o] = s;
+    }
+    __syncwarp();
+    float w = 0.f;
+    for (int o = lane; o < p3; o += 32) {        // (b0, b1, b2)
+        int b0 = o / p2, b1 = (o / p) % p, b2 = o % p;
+        float s = 0.f;
+        for (int a2 = 0; a2 < p; ++a2) s = fmaf(H[32 + a2 + b2], src[b0 * p2 + b1 * p + a2], s);
+        float sc = c_inv_fact[b0] * c_inv_fact[b1] * c_inv_fact[b2];
+        if ((b0 + b1 + b2) & 1) sc = -sc;
+        s *= sc;
+        Bout[o] = s;
+        w = fmaf(s, Mg[o], w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    __syncwarp();
+    return w;
+}
+
+constexpr int kM2LWarps = 4;
+
+__global__ void __launch_bounds__(kM2LWarps * 32)
+k_m2l(const int32_t* __restrict__ far_q, int64_t nfar, int64_t exp_first, int p, float inv_sigma,
+      const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+      const float4* __restrict__ ca, const float4* __restrict__ cd, const float* __restrict__ A,
+      const float* __restrict__ M, float* __restrict__ B, double2* __restrict__ pw) {
+    __shared__ float sH[kM2LWarps][48];
+    __shared__ float sbuf[kM2LWarps][3][kMaxP * kMaxP * kMaxP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p3 = p * p * p;
+    for (int64_t k = (int64_t)blockIdx.x * kM2LWarps + w; k < nfar;
+         k += (int64_t)gridDim.x * kM2LWarps) {
+        int32_t q = far_q[k];
+        int32_t X = pX[q], Y = pY[q];
+        float4 a = ca[X], d = cd[Y];
+        if (lane < 3) {
+            float dl = (lane == 0 ? a.x - d.x : (lane == 1 ? a.y - d.y : a.z - d.z)) * inv_sigma;
+            hermite_table(dl, 2 * p - 2, &sH[w][16 * lane]);
+        }
+        __syncwarp();
+        int64_t ex = X - exp_first, ey = Y - exp_first;
+        float wch[2];
+        for (int ch = 0; ch < 2; ++ch) {
+            wch[ch] = warp_m2l(p, A + (ey * 2 + ch) * p3, M + (ex * 2 + ch) * p3, sH[w],
+                               sbuf[w][0], sbuf[w][1], sbuf[w][2]);
+            for (int i = lane; i < p3; i += 32) atomicAdd(&B[(ex * 2 + ch) * p3 + i], sbuf[w][2][i]);
+            __syncwarp();
+        }
+        if (lane == 0) pw[q] = make_double2((double)wch[0], (double)wch[1]);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: Taylor evaluation (Eq. 6) at every target from each of its boxes that
+// carries an expansion; initialises u_sorted.
+// ---------------------------------------------------------------------------
+__global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
+                      const float4* __restrict__ pts, const int32_t* __restrict__ leaf_of,
+                      const int32_t* __restrict__ parent, const float4* __restrict__ ca,
+                      const float* __restrict__ B, float* __restrict__ u) {
+    const int p3 = p * p * p;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        float4 P = pts[j];
+        uint32_t pw = __float_as_uint(P.w);
+        float acc = 0.f;
+        if (pk_axon(pw) > 0) {
+            int ch = pk_type(pw) ? 1 : 0;
+            int32_t node = leaf_of[j];
+            while (node >= exp_first) {
+                float4 c = ca[node];
+                float x[3] = {(P.x - c.x) * inv_sigma, (P.y - c.y) * inv_sigma,
+                              (P.z - c.z) * inv_sigma};
+                float px[3][kMaxP];
+                for (int d = 0; d < 3; ++d) {
+                    float v = 1.f;
+                    for (int k = 0; k < p; ++k) {
+                        px[d][k] = v;
+                        v *= x[d];
+                    }
+                }
+                const float* Bn = B + ((int64_t)(node - exp_first) * 2 + ch) * p3;
+                int i = 0;
+                for (int b0 = 0; b0 < p; ++b0)
+                    for (int b1 = 0; b1 < p; ++b1) {
+                        float s = 0.f;
+                        float f01 = px[0][b0] * px[1][b1];
+                        for (int b2 = 0; b2 < p; ++b2) s = fmaf(Bn[i++], px[2][b2], s);
+                        acc = fmaf(f01, s, acc);
+                    }
+                node = parent[node];
+            }
+        }
+        u[j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a9: exact near field (Eq. 8) over the near-field leaf pairs, grouped by
+// target leaf X: one warp per X.  The warp's lanes are split into
+// (target, source-slice) groups so that small leaves still fill the warp: a
+// chunk of up to 32 targets with vacant axons is padded to T = 2^k targets and
+// each target gets 32/T lanes that walk interleaved slices of the sources.
+//
+// With k = log2(e)/sigma^2 and hats denoting sqrt(k)*(position - c) for the
+// geometric centre c of X,
+//   w_s K(t,s) = 2^( 2 t^.s^ - |s^|^2 + log2 w_s ) * 2^(-|t^|^2),
+// so a source is staged once per warp as (s^, -|s^|^2 + log2 w_s) per channel
+// and one evaluation costs three FMAs, one EX2 on the SFU and one add.
+// Per partner leaf the warp also reduces W(X,Y) = sum_t a_t sum_s w_s K(t,s).
+// ---------------------------------------------------------------------------
+constexpr int kP2PWarps = 4;
+constexpr int kP2PStage = 128;
+
+__global__ void __launch_bounds__(kP2PWarps * 32)
+k_p2p(const int32_t* __restrict__ seg_first, int64_t nseg, const int32_t* __restrict__ list_q,
+      const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+      const uint8_t* __restrict__ nlevel, const uint64_t* __restrict__ nprefix,
+      const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
+      const float4* __restrict__ pts, const float2* __restrict__ lw, float sqk, float ox,
+      float oy, float oz, float side, float* __restrict__ u, double2* __restrict__ pw,
+      unsigned long long* __restrict__ work) {
+    __shared__ float4 stE[kP2PWarps][kP2PStage];
+    __shared__ float4 stI[kP2PWarps][kP2PStage];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* sE = stE[w];
+    float4* sI = stI[w];
+    for (int64_t sg = (int64_t)blockIdx.x * kP2PWarps + w; sg < nseg;
+         sg += (int64_t)gridDim.x * kP2PWarps) {
+        const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
+        const int32_t X = pX[list_q[i0]];
+        const int32_t tf = nfirst[X], tc = ncount[X];
+        const int lvl = nlevel[X];
+        const uint64_t pre = nprefix[X];
+        const float bs = ldexpf(side, -lvl);
+        const float cx = ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs;
+        const float cy = oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs;
+        const float cz = oz + ((float)compact_by3(pre) + 0.5f) * bs;
+        // the expanded exponent needs |t^|^2 <= 4 for every target of X
+        const bool fast = 0.75f * sqk * sqk * bs * bs <= 4.f;
+        unsigned long long evals = 0;
+        for (int32_t tb = 0; tb < tc; tb += 32) {
+            // compact the targets of this chunk that have vacant axons
+            const int32_t tl = tf + tb + lane;
+            float4 T = tb + lane < tc ? pts[tl] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const uint32_t twl = __float_as_uint(T.w);
+            const bool act = tb + lane < tc && pk_axon(twl) > 0;
+            const unsigned mask = __ballot_sync(0xffffffffu, act);
+            const int nact = __popc(mask);
+            if (nact == 0) continue;
+            int lg = 0;
+            while ((1 << lg) < nact) ++lg;
+            const int ntp = 1 << lg, slices = 32 >> lg;
+            const int j = lane & (ntp - 1), ksl = lane >> lg;
+            const bool valid = j < nact;
+            // lane holding the j-th active target
+            int src_lane = 0;
+            for (int b = 0, r = 0; b < 32; ++b)
+                if ((mask >> b) & 1u) {
+                    if (r == j) src_lane = b;
+                    ++r;
+                }
+            const float tx = __shfl_sync(0xffffffffu, T.x, src_lane);
+            const float ty = __shfl_sync(0xffffffffu, T.y, src_lane);
+            const float tz = __shfl_sync(0xffffffffu, T.z, src_lane);
+            const uint32_t tw = __shfl_sync(0xffffffffu, twl, src_lane);
+            const int32_t t = tf + tb + src_lane;
+            const bool inh = pk_type(tw) != 0;
+            const float hx = (tx - cx) * sqk, hy = (ty - cy) * sqk, hz = (tz - cz) * sqk;
+            const float h2x = fast ? 2.f * hx : hx, h2y = fast ? 2.f * hy : hy,
+                        h2z = fast ? 2.f * hz : hz;
+            const float scale = fast ? ex2_approx(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
+            const float fa = valid ? (float)pk_axon(tw) * scale : 0.f;
+            const float4* src = inh ? sI : sE;
+            float acc = 0.f;
+            for (int32_t ib = i0; ib < i1; ib += 32) {
+                // metadata of up to 32 partner pairs, one per lane
+                int32_t mq = 0, msf = 0, msc = 0;
+                if (ib + lane < i1) {
+                    mq = list_q[ib + lane];
+                    int32_t Y = pY[mq];
+                    msf = nfirst[Y];
+                    msc = ncount[Y];
+                }
+                const int nb = min(32, i1 - ib);
+                for (int r = 0; r < nb; ++r) {
+                    const int32_t q = __shfl_sync(0xffffffffu, mq, r);
+                    const int32_t sf = __shfl_sync(0xffffffffu, msf, r);
+                    const int32_t sc = __shfl_sync(0xffffffffu, msc, r);
+                    const bool self = sf == tf;
+                    float part = 0.f;
+                    for (int32_t sb = 0; sb < sc; sb += kP2PStage) {
+                        const int m = min(kP2PStage, sc - sb);
+                        __syncwarp();
+                        for (int e = lane; e < m; e += 32) {
+                            float4 S = pts[sf + sb + e];
+                            float2 L = lw[sf + sb + e];
+                            float sx = (S.x - cx) * sqk, sy = (S.y - cy) * sqk,
+                                  sz = (S.z - cz) * sqk;
+                            float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
+                            sE[e] = make_float4(sx, sy, sz, n2 + L.x);
+                            sI[e] = make_float4(sx, sy, sz, n2 + L.y);
+                        }
+                        __syncwarp();
+                        if (fast && !self) {
+                            for (int e = ksl; e < m; e += slices) {
+                                float4 S = src[e];
+                                part += ex2_approx(fmaf(h2x, S.x, fmaf(h2y, S.y, fmaf(h2z, S.z, S.w))));
+                            }
+                        } else if (fast) {
+                            for (int e = ksl; e < m; e += slices) {
+                                float4 S = src[e];
+                                float arg = fmaf(h2x, S.x, fmaf(h2y, S.y, fmaf(h2z, S.z, S.w)));
+                                part += sf + sb + e == t ? 0.f : ex2_approx(arg);
+                            }
+                        } else {
+                            // boxes wider than ~2 sigma: the expanded form would
+                            // overflow, use the difference form
+                            for (int e = ksl; e < m; e += slices) {
+                                float4 S = src[e];
+                                float dx = h2x - S.x, dy = h2y - S.y, dz = h2z - S.z;
+                                float arg = S.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                part += sf + sb + e == t ? 0.f : ex2_approx(arg);
+                            }
+                        }
+                    }
+                    acc += part;
+                    float v = fa * part;
+                    float vE = inh ? 0.f : v, vI = inh ? v : 0.f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        vE += __shfl_xor_sync(0xffffffffu, vE, o);
+                        vI += __shfl_xor_sync(0xffffffffu, vI, o);
+                    }
+                    if (lane == 0) {
+                        double2 cur = pw[q];
+                        pw[q] = make_double2(cur.x + (double)vE, cur.y + (double)vI);
+                    }
+                    evals += (unsigned long long)sc * (unsigned long long)nact;
+                }
+            }
+            // sum the slices of each target
+            for (int o = ntp; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (valid && ksl == 0) u[t] += acc * scale;
+        }
+        if (lane == 0) atomicAdd(work, evals);
+    }
+}
+
+// a10: attraction of a split pair = sum over its child block (double)
+__global__ void k_reduce_pairs(int64_t q0, int64_t nq, NodeView nv,
+                               const uint8_t* __restrict__ kind, const int32_t* __restrict__ pX,
+                               const int32_t* __restrict__ pY, const int32_t* __restrict__ pcf,
+                               double2* __restrict__ pw) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = q0 + k;
+        if (kind[q] != kSplit) continue;
+        int nb = block_size(nv, pX[q], pY[q]);
+        int32_t cf = pcf[q];
+        double e = 0.0, i = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            double2 v = pw[cf + j];
+            e += v.x;
+            i += v.y;
+        }
+        pw[q] = make_double2(e, i);
+    }
+}
+
+__global__ void k_scatter_u(const float* __restrict__ us, const int32_t* __restrict__ perm,
+                            int64_t n, float* __restrict__ u) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        u[perm[j]] = us[j];
+}
+
+// ---------------------------------------------------------------------------
+// all-pairs comparison path: every target against every source, sources
+// staged through shared memory in tiles
+// ---------------------------------------------------------------------------
+constexpr int kDirThreads = 256;
+
+__global__ void __launch_bounds__(kDirThreads)
+k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ wts, float k2,
+         float* __restrict__ u) {
+    __shared__ float4 sp[kDirThreads];
+    __shared__ float2 sw[kDirThreads];
+    for (int64_t tb = (int64_t)blockIdx.x * kDirThreads; tb < n;
+         tb += (int64_t)gridDim.x * kDirThreads) {
+        int64_t t = tb + threadIdx.x;
+        bool active = t < n;
+        float4 T = active ? pts[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t tw = __float_as_uint(T.w);
+        bool inh = pk_type(tw) != 0;
+        float acc = 0.f;
+        for (int64_t sb = 0; sb < n; sb += kDirThreads) {
+            __syncthreads();
+            int64_t s = sb + threadIdx.x;
+            sp[threadIdx.x] = s < n ? pts[s] : make_float4(3e30f, 3e30f, 3e30f, 0.f);
+            sw[threadIdx.x] = s < n ? wts[s] : make_float2(0.f, 0.f);
+            __syncthreads();
+#pragma unroll 8
+            for (int j = 0; j < kDirThreads; ++j) {
+                float4 S = sp[j];
+                float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float e = ex2_approx(-r2 * k2);
+                acc = fmaf(inh ? sw[j].y : sw[j].x, e, acc);
+            }
+        }
+        if (active) {
+            float2 self = wts[t];
+            acc -= inh ? self.y : self.x;       // the j == t term contributed w_t * 2^0
+            u[t] = pk_axon(tw) > 0 ? acc : 0.f;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static NodeView node_view(msp_ctx& c) {
+    NodeView nv;
+    nv.level = c.nd_level.get<uint8_t>();
+    nv.prefix = c.nd_prefix.get<uint64_t>();
+    nv.first = c.nd_first.get<int32_t>();
+    nv.count = c.nd_count.get<int32_t>();
+    nv.child_first = c.nd_child_first.get<int32_t>();
+    nv.nchild = c.nd_nchild.get<uint8_t>();
+    nv.sums = c.nd_sums.get<int4>();
+    return nv;
+}
+
+static int bits_for(int64_t v) {
+    int b = 1;
+    while (b < 63 && (1ll << b) <= v) ++b;
+    return b;
+}
+
+void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
+    if (!c.tree_built) throw Error(MSP_ERR_NOT_BUILT, "msp_build_tree must run first");
+    c.attraction_done = false;
+    const msp_config& cfg = c.cfg;
+    const int64_t n = c.n;
+    const int B = 256;
+    NodeView nv = node_view(c);
+    Geo geo;
+    for (int l = 0; l <= kMortonBits; ++l) geo.g2[l] = c.g2[l];
+    geo.l_far = c.l_far;
+    geo.m2l_min_pairs = cfg.m2l_min_pairs;
+    const int p = cfg.p, p3 = p * p * p;
+    const float inv_sigma = (float)(1.0 / cfg.sigma);
+    const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
+
+    // a5: breadth-first dual traversal from (root, root)
+    c.depth_start.assign(1, 0);
+    int64_t total = n > 0 ? 1 : 0;
+    size_t cap = (size_t)std::max<int64_t>(64 * c.n_nodes, 1024);
+    auto grow_pairs = [&](size_t need, size_t keep) {
+        c.pr_X.grow<int32_t>(need, keep, s);
+        c.pr_Y.grow<int32_t>(need, keep, s);
+        c.pr_kind.grow<uint8_t>(need, keep, s);
+        c.pr_cf.grow<int32_t>(need, keep, s);
+        c.pr_w.grow<double2>(need, keep, s);
+    };
+    grow_pairs(cap, 0);
+    if (total) {
+        int32_t zero = 0;
+        MSP_CUDA(cudaMemcpyAsync(c.pr_X.get<int32_t>(), &zero, 4, cudaMemcpyHostToDevice, s));
+        MSP_CUDA(cudaMemcpyAsync(c.pr_Y.get<int32_t>(), &zero, 4, cudaMemcpyHostToDevice, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+    }
+    c.depth_start.push_back(total);
+    int d = 0;
+    while (c.depth_start[d + 1] > c.depth_start[d]) {
+        int64_t q0 = c.depth_start[d], nq = c.depth_start[d + 1] - q0;
+        int32_t* cnt = c.cnt.ensure<int32_t>((size_t)nq);
+        int32_t* off = c.off.ensure<int32_t>((size_t)nq);
+        k_classify<<<grid_for(nq, B), B, 0, s>>>(q0, nq, nv, geo, c.pr_X.get<int32_t>(),
+                                                 c.pr_Y.get<int32_t>(), c.pr_kind.get<uint8_t>(),
+                                                 cnt);
+        MSP_LAUNCH("classify");
+        int64_t nnext = scan_exclusive(c, cnt, off, nq, s);
+        if (total + nnext > 0x7fffffffll) throw Error(MSP_ERR_CAPACITY, "pair count exceeds int32");
+        if ((size_t)(total + nnext) > c.pr_X.bytes / sizeof(int32_t))
+            grow_pairs((size_t)(total + nnext), (size_t)total);
+        k_emit_pairs<<<grid_for(nq, B), B, 0, s>>>(q0, nq, total, nv, c.pr_kind.get<uint8_t>(), off,
+                                                   c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
+                                                   c.pr_cf.get<int32_t>(), c.pr_w.get<double2>());
+        MSP_LAUNCH("emit_pairs");
+        total += nnext;
+        c.depth_start.push_back(total);
+        ++d;
+    }
+    if (c.depth_start.size() > 1) c.depth_start.pop_back();   // the last depth is empty
+    c.n_pairs = total;
+    const int n_depths = (int)c.depth_start.size() - 1;
+    uint8_t* kind = c.pr_kind.get<uint8_t>();
+
+    // far and near-field lists
+    int32_t* flag = c.cnt.ensure<int32_t>((size_t)std::max<int64_t>(total, 1));
+    int32_t* off = c.off.ensure<int32_t>((size_t)std::max<int64_t>(total, 1));
+    k_flag_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kFar, flag);
+    MSP_LAUNCH("flag_far");
+    c.n_far = scan_exclusive(c, flag, off, total, s);
+    int32_t* far_q = c.far_q.ensure<int32_t>((size_t)std::max<int64_t>(c.n_far, 1));
+    k_compact_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kFar, off, c.pr_X.get<int32_t>(),
+                                                    far_q, nullptr);
+    MSP_LAUNCH("compact_far");
+    k_flag_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kP2P, flag);
+    MSP_LAUNCH("flag_p2p");
+    c.n_p2p = scan_exclusive(c, flag, off, total, s);
+    size_t np = (size_t)std::max<int64_t>(c.n_p2p, 1);
+    uint64_t* pk0 = c.p2p_key0.ensure<uint64_t>(np);
+    uint64_t* pk1 = c.p2p_key1.ensure<uint64_t>(np);
+    int32_t* pv0 = c.p2p_val0.ensure<int32_t>(np);
+    int32_t* pv1 = c.p2p_val1.ensure<int32_t>(np);
+    k_compact_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kP2P, off, c.pr_X.get<int32_t>(),
+                                                    pv0, pk0);
+    MSP_LAUNCH("compact_p2p");
+    radix_sort(c, pk0, pv0, pk1, pv1, c.n_p2p, bits_for(c.n_nodes), s);
+    int32_t* sflag = c.seg_flag.ensure<int32_t>(np);
+    int32_t* soff = c.cnt.ensure<int32_t>(np);
+    k_seg_flags<<<grid_for(c.n_p2p, B), B, 0, s>>>(pk0, c.n_p2p, sflag);
+    MSP_LAUNCH("seg_flags");
+    int64_t nseg = scan_exclusive(c, sflag, soff, c.n_p2p, s);
+    int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)nseg + 1);
+    k_seg_first<<<grid_for(c.n_p2p, B), B, 0, s>>>(sflag, soff, c.n_p2p, seg_first);
+    MSP_LAUNCH("seg_first");
+    {
+        int32_t last = (int32_t)c.n_p2p;
+        MSP_CUDA(cudaMemcpyAsync(seg_first + nseg, &last, 4, cudaMemcpyHostToDevice, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+    }
+    c.n_p2p_targets = nseg;
+
+    // a6: expansions of every box at level >= l_far
+    c.exp_first = c.l_far <= c.tree_depth ? c.level_start[c.l_far] : c.n_nodes;
+    c.exp_nodes = c.n_nodes - c.exp_first;
+    size_t ecount = (size_t)std::max<int64_t>(c.exp_nodes, 1) * 2 * p3;
+    float* eA = c.expA.ensure<float>(ecount);
+    float* eM = c.expM.ensure<float>(ecount);
+    float* eB = c.expB.ensure<float>(ecount);
+    if (c.exp_nodes > 0) {
+        MSP_CUDA(cudaMemsetAsync(eB, 0, ecount * sizeof(float), s));
+        k_p2m<<<(unsigned)c.exp_nodes, kP2MThreads, 0, s>>>(
+            c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.nd_first.get<int32_t>(),
+            c.nd_count.get<int32_t>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM);
+        MSP_LAUNCH("p2m");
+    }
+    // a7: translations, accumulating B(X) and W(X,Y)
+    if (c.n_far > 0) {
+        int g = grid_for(c.n_far, kM2LWarps, (int64_t)c.sm_count * 32);
+        k_m2l<<<g, kM2LWarps * 32, 0, s>>>(far_q, c.n_far, c.exp_first, p, inv_sigma,
+                                           c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
+                                           c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM,
+                                           eB, c.pr_w.get<double2>());
+        MSP_LAUNCH("m2l");
+    }
+    // a8: Taylor evaluation initialises u in sorted order; a9 adds the near field
+    float* us = c.u_sorted.ensure<float>((size_t)std::max<int64_t>(n, 1));
+    unsigned long long* work = c.small_dev.ensure<unsigned long long>(8) + 1;
+    MSP_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        k_l2p<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
+            n, c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.leaf_of.get<int32_t>(),
+            c.nd_parent.get<int32_t>(), c.nd_ca.get<float4>(), eB, us);
+        MSP_LAUNCH("l2p");
+    }
+    if (nseg > 0) {
+        int g = grid_for(nseg, kP2PWarps, (int64_t)c.sm_count * 64);
+        const float sqk = (float)std::sqrt(1.4426950408889634 / (cfg.sigma * cfg.sigma));
+        k_p2p<<<g, kP2PWarps * 32, 0, s>>>(
+            seg_first, nseg, pv0, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
+            c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
+            c.nd_count.get<int32_t>(), c.pts.get<float4>(), c.lw.get<float2>(), sqk,
+            cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, us, c.pr_w.get<double2>(), work);
+        MSP_LAUNCH("p2p");
+    }
+    // a10: pair table, deepest pairs first
+    for (int dd = n_depths - 1; dd >= 0; --dd) {
+        int64_t q0 = c.depth_start[dd], nq = c.depth_start[dd + 1] - q0;
+        if (nq == 0) continue;
+        k_reduce_pairs<<<grid_for(nq, B), B, 0, s>>>(q0, nq, nv, kind, c.pr_X.get<int32_t>(),
+                                                     c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
+                                                     c.pr_w.get<double2>());
+        MSP_LAUNCH("reduce_pairs");
+    }
+    if (u_dev && n > 0) {
+        k_scatter_u<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
+            us, c.perm.get<int32_t>(), n, u_dev);
+        MSP_LAUNCH("scatter_u");
+    }
+    c.p2p_interactions = read_i64(c, reinterpret_cast<const int64_t*>(work), s);
+    c.attraction_done = true;
+}
+
+void direct(msp_ctx& c, float* u_dev, cudaStream_t s) {
+    if (!c.tree_built) throw Error(MSP_ERR_NOT_BUILT, "msp_build_tree must run first");
+    const int64_t n = c.n;
+    if (n == 0) return;
+    const float k2 = (float)(1.4426950408889634 / (c.cfg.sigma * c.cfg.sigma));
+    float* us = c.u_sorted.ensure<float>((size_t)n);
+    k_direct<<<grid_for(n, kDirThreads), kDirThreads, 0, s>>>(n, c.pts.get<float4>(),
+                                                              c.wts.get<float2>(), k2, us);
+    MSP_LAUNCH("direct");
+    k_scatter_u<<<grid_for(n, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
+        us, c.perm.get<int32_t>(), n, u_dev);
+    MSP_LAUNCH("scatter_u");
+}
+
+}  // namespace msp

@@ -1,0 +1,227 @@
+// msp_internal.cuh -- context, device buffers and device helpers shared by the
+// translation units of libmsp.  Not part of the public ABI (include/msp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "msp.h"
+
+namespace msp {
+
+constexpr int kMortonBits = 21;
+constexpr int kMaxP = 8;
+constexpr uint32_t kTagDescend = 1u, kTagLeaf = 2u, kTagAccept = 3u, kTagWalk = 4u;
+enum PairKind : uint8_t { kSplit = 0, kFar = 1, kP2P = 2, kPruned = 3 };
+
+// ---------------------------------------------------------------------------
+// errors: internal code throws; every C entry point converts to msp_status
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    msp_status code;
+    Error(msp_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+inline void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    msp_status c = (e == cudaErrorMemoryAllocation) ? MSP_ERR_OOM : MSP_ERR_CUDA;
+    throw Error(c, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define MSP_CUDA(x) ::msp::cuda_check((x), #x)
+#define MSP_LAUNCH(what) ::msp::cuda_check(cudaGetLastError(), what)
+
+// grow-only device buffer
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T* get() const { return static_cast<T*>(p); }
+    template <class T>
+    T* ensure(size_t count) {
+        size_t need = count * sizeof(T);
+        if (need == 0) need = sizeof(T);
+        if (need > bytes) {
+            if (p) cudaFree(p);
+            p = nullptr;
+            bytes = 0;
+            size_t alloc = need + need / 4 + 256;
+            cuda_check(cudaMalloc(&p, alloc), "cudaMalloc");
+            bytes = alloc;
+        }
+        return static_cast<T*>(p);
+    }
+    // grow to `count` elements keeping the first `keep` (stream-ordered copy)
+    template <class T>
+    T* grow(size_t count, size_t keep, cudaStream_t s) {
+        size_t need = count * sizeof(T);
+        if (need == 0) need = sizeof(T);
+        if (need <= bytes) return static_cast<T*>(p);
+        size_t alloc = need + need / 2 + 256;
+        void* q = nullptr;
+        cuda_check(cudaMalloc(&q, alloc), "cudaMalloc");
+        if (p && keep)
+            cuda_check(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s),
+                       "cudaMemcpyAsync");
+        cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        if (p) cudaFree(p);
+        p = q;
+        bytes = alloc;
+        return static_cast<T*>(p);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// one item of the level-synchronous descent (Algorithm 1)
+struct Item {
+    int32_t X, Y, q, ch;   // axon box, dendrite box, traversal pair (-1 below a far pair), channel
+};
+
+}  // namespace msp
+
+struct msp_ctx {
+    msp_config cfg;
+    int device = 0;
+    int sm_count = 0;
+    // derived constants
+    float morton_scale = 0.f;
+    int l_far = 0;
+    long long g2[msp::kMortonBits + 1];
+    // sizes
+    int64_t n = 0;
+    int64_t n_elem = 0;
+    int64_t n_nodes = 0, n_leaves = 0;
+    int tree_depth = 0;
+    std::vector<int64_t> level_start;   // level l nodes: [level_start[l], level_start[l+1])
+    std::vector<int64_t> depth_start;   // pair depth d: [depth_start[d], depth_start[d+1])
+    int64_t n_pairs = 0, n_far = 0, n_p2p = 0, p2p_interactions = 0;
+    int64_t n_draws = 0, n_requests = 0, n_synapses = 0;
+    int64_t exp_first = 0, exp_nodes = 0;
+    int64_t n_p2p_targets = 0;
+    bool tree_built = false, attraction_done = false;
+    // sorted points
+    msp::DBuf keys0, keys1, vals0, vals1;
+    msp::DBuf perm, inv, pts, wts, lw, elem_off, leaf_of;
+    // octree (SoA)
+    msp::DBuf nd_level, nd_prefix, nd_first, nd_count, nd_parent, nd_child_first, nd_nchild;
+    msp::DBuf nd_sums, nd_ca, nd_cd;
+    // dual traversal
+    msp::DBuf pr_X, pr_Y, pr_kind, pr_cf, pr_w;
+    // lists
+    msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag;
+    // expansions
+    msp::DBuf expA, expM, expB;
+    msp::DBuf u_sorted;
+    // descent
+    msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
+    // generic scratch
+    msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist;
+    int64_t* small_host = nullptr;     // pinned, for count readbacks
+    // per-neuron inputs of the last build in caller order (context-owned
+    // copies; the selection reads them again)
+    msp::DBuf c_type, c_va, c_vde, c_vdi;
+    const uint8_t *in_type = nullptr, *in_va = nullptr, *in_vde = nullptr, *in_vdi = nullptr;
+    // host-buffer step staging
+    msp::DBuf h_in[7];
+    msp::DBuf h_u, h_partner, h_pre, h_post, h_type, h_nsyn;
+};
+
+namespace msp {
+
+// ---------------------------------------------------------------------------
+// primitives (msp_prims.cu)
+// ---------------------------------------------------------------------------
+// Exclusive scan of n int32 values into out (may alias in); returns the total
+// (synchronous: reads it back).  Throws MSP_ERR_CAPACITY if the total does not
+// fit in int32.
+int64_t scan_exclusive(msp_ctx& c, const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) by the low `bits` bits of key.  The
+// result ends in (keys, vals); (keys_tmp, vals_tmp) are scratch of n entries.
+void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                int32_t* vals_tmp, int64_t n, int bits, cudaStream_t s);
+// Read an int64 from device memory (synchronous).
+int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s);
+
+inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications, key bumped by the Weyl constants between rounds.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        c[1] = (uint32_t)p1;
+        c[3] = (uint32_t)p0;
+        c[0] = n0;
+        c[2] = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// counter (c0, c1, step_lo, step_hi), key = seed; returns the 4 output words
+__host__ __device__ inline void philox_draw(uint64_t seed, uint32_t c0, uint32_t c1,
+                                            uint64_t step, uint32_t out[4]) {
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = (uint32_t)step;
+    out[3] = (uint32_t)(step >> 32);
+    philox4x32_10(out, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// U in [0,1) from the top 53 bits of the first two output words
+__host__ __device__ inline double philox_uniform(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                 uint64_t step) {
+    uint32_t o[4];
+    philox_draw(seed, c0, c1, step, o);
+    uint64_t bits = (((uint64_t)o[0] << 32) | o[1]) >> 11;
+    return (double)bits * (1.0 / 9007199254740992.0);
+}
+
+// every third bit of v (bits 0,3,6,...) packed into the low bits
+__host__ __device__ inline uint32_t compact_by3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return (uint32_t)v;
+}
+
+// spread the low 21 bits of v to bits 0,3,6,...
+__host__ __device__ inline uint64_t spread_by3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// packed per-point bytes: type | vac_axon << 8 | vac_dend_e << 16 | vac_dend_i << 24
+__device__ inline uint32_t pk_type(uint32_t w) { return w & 0xffu; }
+__device__ inline uint32_t pk_axon(uint32_t w) { return (w >> 8) & 0xffu; }
+__device__ inline uint32_t pk_de(uint32_t w) { return (w >> 16) & 0xffu; }
+__device__ inline uint32_t pk_di(uint32_t w) { return w >> 24; }
+
+}  // namespace msp

@@ -1,0 +1,245 @@
+// msp_prims.cu -- device-wide exclusive scan and stable LSD radix sort used by
+// the tree build, the pair lists, the descent and the request resolution.
+#include "msp_internal.cuh"
+
+namespace msp {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ inline long long warp_incl_scan(long long v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan over the block of one value per thread; returns the block total
+__device__ inline long long block_excl_scan(long long v, long long* total) {
+    __shared__ long long warp_sums[kScanThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+        long long si = warp_incl_scan(s);
+        if (lane < kScanThreads / 32) warp_sums[lane] = si - s;
+        if (lane == kScanThreads / 32 - 1) *total = si;
+    }
+    __syncthreads();
+    long long r = inc - v + warp_sums[w];
+    __syncthreads();
+    return r;
+}
+
+// per-tile sums (int64)
+template <class T>
+__global__ void k_scan_reduce(const T* __restrict__ in, int64_t n, long long* __restrict__ bsum) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    long long s = 0;
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+        int64_t i = base + j;
+        if (i < n) s += (long long)in[i];
+    }
+    __shared__ long long tot;
+    long long dummy = block_excl_scan(s, &tot);
+    (void)dummy;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// exclusive scan of one tile, plus the tile's offset; the last tile writes the
+// grand total to *total
+template <class Tin, class Tout>
+__global__ void k_scan_tile(const Tin* in, Tout* out, int64_t n,   // may alias
+                            const long long* __restrict__ boff, long long* __restrict__ total) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int64_t i = base + j;
+        v[j] = i < n ? (long long)in[i] : 0;
+        s += v[j];
+    }
+    __shared__ long long tile_total;
+    long long pre = block_excl_scan(s, &tile_total);
+    long long off = boff ? boff[blockIdx.x] : 0;
+    pre += off;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int64_t i = base + j;
+        if (i < n) out[i] = (Tout)pre;
+        pre += v[j];
+    }
+    if (threadIdx.x == 0 && blockIdx.x == gridDim.x - 1 && total) *total = off + tile_total;
+}
+
+// recursive scan of n int64 block sums in place (out may alias in)
+void scan_i64(msp_ctx& c, long long* data, int64_t n, long long* total, long long* scratch,
+              cudaStream_t s) {
+    if (n <= kScanTile) {
+        k_scan_tile<long long, long long><<<1, kScanThreads, 0, s>>>(data, data, n, nullptr, total);
+        MSP_LAUNCH("scan_tile_i64");
+        return;
+    }
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    long long* bsum = scratch;
+    k_scan_reduce<long long><<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, bsum);
+    MSP_LAUNCH("scan_reduce_i64");
+    scan_i64(c, bsum, nb, nullptr, scratch + nb, s);
+    k_scan_tile<long long, long long><<<(unsigned)nb, kScanThreads, 0, s>>>(data, data, n, bsum,
+                                                                          total);
+    MSP_LAUNCH("scan_tile_i64");
+}
+
+// ---------------------------------------------------------------------------
+// radix sort
+// ---------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;
+constexpr int kRsWarps = kRsThreads / 32;
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             int32_t* __restrict__ hist, int nb) {
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int j = threadIdx.x; j < kRsTile; j += kRsThreads) {
+        int64_t i = base + j;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: items of a tile are ranked in index order within their
+// digit.  Round r covers tile positions [r*256, r*256+256), thread order =
+// index order; within a warp the rank comes from the lanes with the same digit,
+// across warps from the per-warp digit counts of the round.
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                                int64_t n, int shift, const int32_t* __restrict__ offs, int nb,
+                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout) {
+    __shared__ int32_t running[256];
+    __shared__ int32_t wcnt[kRsWarps][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    running[t] = offs[(int64_t)t * nb + blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kRsWarps; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsItems; ++r) {
+        int64_t i = base + (int64_t)r * kRsThreads + t;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        int32_t val = valid ? vin[i] : 0;
+        int d = valid ? (int)((key >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = running[d] + rank;
+            for (int k = 0; k < w; ++k) pos += wcnt[k][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        int add = 0;
+#pragma unroll
+        for (int k = 0; k < kRsWarps; ++k) {
+            add += wcnt[k][t];
+            wcnt[k][t] = 0;
+        }
+        running[t] += add;
+        __syncthreads();
+    }
+}
+
+__global__ void k_copy_kv(const uint64_t* __restrict__ ks, const int32_t* __restrict__ vs,
+                          int64_t n, uint64_t* __restrict__ kd, int32_t* __restrict__ vd) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        kd[i] = ks[i];
+        vd[i] = vs[i];
+    }
+}
+
+}  // namespace
+
+int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s) {
+    MSP_CUDA(cudaMemcpyAsync(c.small_host, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    return c.small_host[0];
+}
+
+int64_t scan_exclusive(msp_ctx& c, const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return 0;
+    long long* total = c.small_dev.ensure<long long>(8);
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        k_scan_tile<int32_t, int32_t><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
+        MSP_LAUNCH("scan_tile");
+    } else {
+        long long* scratch = c.scan_tmp.ensure<long long>((size_t)(2 * nb + 64));
+        k_scan_reduce<int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch);
+        MSP_LAUNCH("scan_reduce");
+        scan_i64(c, scratch, nb, nullptr, scratch + nb, s);
+        k_scan_tile<int32_t, int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, scratch,
+                                                                          total);
+        MSP_LAUNCH("scan_tile");
+    }
+    int64_t t = read_i64(c, reinterpret_cast<int64_t*>(total), s);
+    if (t > 0x7fffffffll) throw Error(MSP_ERR_CAPACITY, "scan total exceeds int32 range");
+    return t;
+}
+
+void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp, int32_t* vals_tmp,
+                int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return;
+    int nb = (int)((n + kRsTile - 1) / kRsTile);
+    int32_t* hist = c.rs_hist.ensure<int32_t>((size_t)256 * nb);
+    int passes = (bits + 7) / 8;
+    uint64_t *ka = keys, *kb = keys_tmp;
+    int32_t *va = vals, *vb = vals_tmp;
+    for (int ps = 0; ps < passes; ++ps) {
+        int shift = 8 * ps;
+        k_radix_hist<<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
+        MSP_LAUNCH("radix_hist");
+        // exclusive scan of the digit-major histogram: offsets of (digit, tile)
+        {
+            int64_t m = (int64_t)256 * nb;
+            int64_t tb = (m + kScanTile - 1) / kScanTile;
+            long long* scratch = c.scan_tmp.ensure<long long>((size_t)(2 * tb + 64));
+            if (tb == 1) {
+                k_scan_tile<int32_t, int32_t><<<1, kScanThreads, 0, s>>>(hist, hist, m, nullptr,
+                                                                      nullptr);
+            } else {
+                k_scan_reduce<int32_t><<<(unsigned)tb, kScanThreads, 0, s>>>(hist, m, scratch);
+                scan_i64(c, scratch, tb, nullptr, scratch + tb, s);
+                k_scan_tile<int32_t, int32_t><<<(unsigned)tb, kScanThreads, 0, s>>>(
+                    hist, hist, m, scratch, nullptr);
+            }
+            MSP_LAUNCH("radix_scan");
+        }
+        k_radix_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, n, shift, hist, nb, kb, vb);
+        MSP_LAUNCH("radix_scatter");
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        k_copy_kv<<<grid_for(n, 256, 4096), 256, 0, s>>>(ka, va, n, keys, vals);
+        MSP_LAUNCH("radix_copy");
+    }
+}
+
+}  // namespace msp

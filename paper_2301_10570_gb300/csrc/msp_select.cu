@@ -1,0 +1,523 @@
+// msp_select.cu -- steps a11-a12: the level-synchronous descent of
+// Algorithm 1 with Algorithm 2's choice (candidate attractions, total, uniform
+// draw, upper_bound over the inclusive prefix sums), the per-element draw of a
+// dendrite neuron inside the chosen leaf, and the resolution of the requests
+// at the dendrite side (Section 4).  Also the vacancy random walk and the
+// consumption of formed synapses.
+#include "msp_internal.cuh"
+
+namespace msp {
+
+__device__ inline float ex2_approx_sel(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__constant__ float c_inv_fact_sel[kMaxP] = {1.f, 1.f, 0.5f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f,
+                                            1.f / 720.f, 1.f / 5040.f};
+
+namespace {
+
+struct Tree {
+    const uint8_t* level;
+    const int32_t* first;
+    const int32_t* count;
+    const int32_t* child_first;
+    const uint8_t* nchild;
+    const int4* sums;
+    const float4* ca;
+    const float4* cd;
+};
+
+struct Exps {
+    const float* A;
+    const float* M;
+    int64_t first;
+    int p;
+    float inv_sigma;
+};
+
+// W(X, Y) of one channel from the expansions (pairs below a translated
+// pair): M2L of A(Y) about c_A(X), dotted with the axon moments M(X).  Whole
+// warp; the result is returned to every lane.
+__device__ float warp_far_w(const Tree& tr, const Exps& ex, int32_t X, int32_t Y, int ch,
+                            float* H, float* b0, float* b1) {
+    const int lane = threadIdx.x & 31;
+    const int p = ex.p, p2 = p * p, p3 = p2 * p;
+    if (X < ex.first || Y < ex.first) return 0.f;
+    float4 a = tr.ca[X], d = tr.cd[Y];
+    if (lane < 3) {
+        float x = (lane == 0 ? a.x - d.x : (lane == 1 ? a.y - d.y : a.z - d.z)) * ex.inv_sigma;
+        float* h = H + 16 * lane;
+        float h0 = __expf(-x * x);
+        h[0] = h0;
+        if (2 * p - 2 >= 1) h[1] = 2.f * x * h0;
+        for (int k = 1; k < 2 * p - 2; ++k) h[k + 1] = 2.f * x * h[k] - 2.f * (float)k * h[k - 1];
+    }
+    const float* Ag = ex.A + ((int64_t)(Y - ex.first) * 2 + ch) * p3;
+    const float* Mg = ex.M + ((int64_t)(X - ex.first) * 2 + ch) * p3;
+    for (int i = lane; i < p3; i += 32) b0[i] = Ag[i];
+    __syncwarp();
+    for (int o = lane; o < p3; o += 32) {
+        int c0 = o / p2, r = o - c0 * p2;
+        float s = 0.f;
+        for (int k = 0; k < p; ++k) s = fmaf(H[k + c0], b0[k * p2 + r], s);
+        b1[o] = s;
+    }
+    __syncwarp();
+    for (int o = lane; o < p3; o += 32) {
+        int c0 = o / p2, c1 = (o / p) % p, k2 = o % p;
+        float s = 0.f;
+        for (int k = 0; k < p; ++k) s = fmaf(H[16 + k + c1], b1[c0 * p2 + k * p + k2], s);
+        b0[o] = s;
+    }
+    __syncwarp();
+    float w = 0.f;
+    for (int o = lane; o < p3; o += 32) {
+        int c0 = o / p2, c1 = (o / p) % p, c2 = o % p;
+        float s = 0.f;
+        for (int k = 0; k < p; ++k) s = fmaf(H[32 + k + c2], b0[c0 * p2 + c1 * p + k], s);
+        float sc = c_inv_fact_sel[c0] * c_inv_fact_sel[c1] * c_inv_fact_sel[c2];
+        if ((c0 + c1 + c2) & 1) sc = -sc;
+        w = fmaf(s * sc, Mg[o], w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    __syncwarp();
+    return w;
+}
+
+// Algorithm 2's last steps: negative candidates (truncation) count as zero;
+// -1 when the total is zero; upper_bound over the inclusive prefix sums, and
+// the last positive candidate when rounding puts r at the total.
+__device__ inline int draw_index(const double* w, int k, double U) {
+    double pre[8];
+    double tot = 0.0;
+    for (int i = 0; i < k; ++i) {
+        tot += w[i] > 0.0 ? w[i] : 0.0;
+        pre[i] = tot;
+    }
+    if (!(tot > 0.0)) return -1;
+    double r = U * tot;
+    for (int i = 0; i < k; ++i)
+        if (pre[i] > r) return i;
+    for (int i = k - 1; i >= 0; --i)
+        if (w[i] > 0.0) return i;
+    return -1;
+}
+
+constexpr int kDescWarps = 4;
+
+__global__ void __launch_bounds__(kDescWarps * 32)
+k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
+          const uint8_t* __restrict__ kind, const int32_t* __restrict__ pcf,
+          const double2* __restrict__ pw, uint64_t seed, uint64_t step, Item* __restrict__ out,
+          int64_t cap_out, Item* __restrict__ leaf_out, int64_t cap_leaf,
+          unsigned long long* __restrict__ counters /* [0] next, [1] leaf, [2] draws, [3] overflow */) {
+    __shared__ float sH[kDescWarps][48];
+    __shared__ float sb[kDescWarps][2][kMaxP * kMaxP * kMaxP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t k = (int64_t)blockIdx.x * kDescWarps + w; k < n_in;
+         k += (int64_t)gridDim.x * kDescWarps) {
+        Item it = in[k];
+        const int32_t X = it.X, Y = it.Y;
+        const int ch = it.ch;
+        const bool lx = tr.child_first[X] < 0, ly = tr.child_first[Y] < 0;
+        const bool split = it.q >= 0 && kind[it.q] == kSplit;
+        const int32_t cf = split ? pcf[it.q] : -1;
+        if (lx && ly) {
+            // form_synapse: the leaf pair goes to the per-element draw
+            if (lane == 0) {
+                unsigned long long slot = atomicAdd(&counters[1], 1ull);
+                if ((int64_t)slot < cap_leaf) leaf_out[slot] = it;
+                else atomicAdd(&counters[3], 1ull);
+            }
+            continue;
+        }
+        if (!lx && ly) {
+            // the dendrite side is a leaf: every axon child with vacancies of
+            // this channel keeps it, without a draw
+            int nx = tr.nchild[X];
+            int32_t cx = tr.child_first[X];
+            if (lane < nx) {
+                int32_t xc = cx + lane;
+                int4 sm = tr.sums[xc];
+                int sa = ch ? sm.y : sm.x;
+                bool keep = sa > 0;
+                if (keep && split) keep = (ch ? pw[cf + lane].y : pw[cf + lane].x) > 0.0;
+                if (keep) {
+                    unsigned long long slot = atomicAdd(&counters[0], 1ull);
+                    Item nx_it = {xc, Y, split ? cf + lane : -1, ch};
+                    if ((int64_t)slot < cap_out) out[slot] = nx_it;
+                    else atomicAdd(&counters[3], 1ull);
+                }
+            }
+            continue;
+        }
+        // a draw among the children of Y, for X itself (X a leaf) or for each
+        // axon child of X (both inner)
+        const int ny = tr.nchild[Y];
+        const int32_t cy = tr.child_first[Y];
+        const int nsrc = lx ? 1 : tr.nchild[X];
+        for (int i = 0; i < nsrc; ++i) {
+            const int32_t xc = lx ? X : tr.child_first[X] + i;
+            if (!lx) {
+                int4 sm = tr.sums[xc];
+                if ((ch ? sm.y : sm.x) == 0) continue;
+            }
+            double wk[8];
+            for (int j = 0; j < ny; ++j) {
+                if (split) {
+                    double2 v = pw[cf + (int64_t)i * ny + j];
+                    wk[j] = ch ? v.y : v.x;
+                } else {
+                    wk[j] = (double)warp_far_w(tr, ex, xc, cy + j, ch, sH[w], sb[w][0], sb[w][1]);
+                }
+            }
+            if (lane == 0) {
+                uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
+                double U = philox_uniform(seed, (uint32_t)xc, c1, step);
+                int kk = draw_index(wk, ny, U);
+                atomicAdd(&counters[2], 1ull);
+                if (kk >= 0) {
+                    unsigned long long slot = atomicAdd(&counters[0], 1ull);
+                    Item nx_it = {xc, cy + kk, split ? cf + i * ny + kk : -1, ch};
+                    if ((int64_t)slot < cap_out) out[slot] = nx_it;
+                    else atomicAdd(&counters[3], 1ull);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// per-element draw inside a chosen dendrite leaf: weights w_s K(t,s) in
+// single precision, inclusive prefix sums in double precision
+__global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
+                            const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
+                            const float4* __restrict__ pts, const float2* __restrict__ wts,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
+                            float k2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
+                            unsigned long long* __restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = wid; k < n_items; k += nw) {
+        Item it = items[k];
+        const int32_t tf = nfirst[it.X], tc = ncount[it.X];
+        const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
+        unsigned long long draws = 0;
+        for (int32_t tb = 0; tb < tc; tb += 32) {
+            int32_t t = tf + tb + lane;
+            if (tb + lane >= tc) continue;
+            float4 T = pts[t];
+            uint32_t tw = __float_as_uint(T.w);
+            int ch = pk_type(tw) ? 1 : 0;
+            int a = (int)pk_axon(tw);
+            if (ch != it.ch || a == 0) continue;
+            double tot = 0.0;
+            for (int32_t s = sf; s < sf + sc; ++s) {
+                if (s == t) continue;
+                float4 S = pts[s];
+                float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ws = (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2);
+                tot += (double)ws;
+            }
+            const int32_t to = perm[t];
+            if (!(tot > 0.0)) continue;
+            for (int e = 0; e < a; ++e) {
+                uint32_t c1 = (uint32_t)e | ((uint32_t)ch << 8) | (kTagLeaf << 16);
+                double r = philox_uniform(seed, (uint32_t)to, c1, step) * tot;
+                double pre = 0.0;
+                int32_t pick = -1, last_pos = -1;
+                for (int32_t s = sf; s < sf + sc; ++s) {
+                    if (s == t) continue;
+                    float4 S = pts[s];
+                    float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float ws = (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2);
+                    pre += (double)ws;
+                    if (ws > 0.f) last_pos = s;
+                    if (pre > r) {
+                        pick = s;
+                        break;
+                    }
+                }
+                if (pick < 0) pick = last_pos;
+                partner[eoff[to] + e] = pick >= 0 ? perm[pick] : -1;
+                ++draws;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
+        if (lane == 0 && draws) atomicAdd(&counters[2], draws);
+    }
+}
+
+// requests in element order: flag, then key = (dendrite*2 + channel) << 32 | priority
+__global__ void k_request_flags(const int32_t* __restrict__ partner, int64_t n_elem,
+                                int32_t* __restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
+         e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = partner[e] >= 0;
+}
+
+__global__ void k_request_emit(int64_t n, const uint8_t* __restrict__ type,
+                               const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
+                               const int32_t* __restrict__ partner, const int32_t* __restrict__ roff,
+                               uint64_t seed, uint64_t step, uint64_t* __restrict__ key,
+                               int32_t* __restrict__ val) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int a = va[t];
+        int32_t e0 = eoff[t];
+        uint32_t ch = type[t] ? 1u : 0u;
+        for (int k = 0; k < a; ++k) {
+            int32_t s = partner[e0 + k];
+            if (s < 0) continue;
+            uint32_t o[4];
+            philox_draw(seed, (uint32_t)t, (uint32_t)k | (kTagAccept << 16), step, o);
+            int32_t r = roff[e0 + k];
+            key[r] = ((uint64_t)((uint32_t)s * 2u + ch) << 32) | o[0];
+            val[r] = e0 + k;
+        }
+    }
+}
+
+// a dendrite neuron accepts, per channel, its first `capacity` requests in
+// (priority, element) order: request i is accepted unless request i - cap
+// belongs to the same (dendrite, channel) group
+__global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                         int64_t nr, const uint8_t* __restrict__ vde,
+                         const uint8_t* __restrict__ vdi, uint8_t* __restrict__ accepted) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t g = (uint32_t)(key[i] >> 32);
+        uint32_t s = g >> 1;
+        int cap = (g & 1u) ? vdi[s] : vde[s];
+        bool ok = cap > 0 && (i < cap || (uint32_t)(key[i - cap] >> 32) != g);
+        accepted[val[i]] = ok ? 1 : 0;
+    }
+}
+
+__global__ void k_acc_flags(const uint8_t* __restrict__ acc, int64_t n_elem,
+                            int32_t* __restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
+         e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = acc[e];
+}
+
+__global__ void k_emit_synapses(int64_t n, const uint8_t* __restrict__ type,
+                                const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
+                                const int32_t* __restrict__ partner,
+                                const uint8_t* __restrict__ acc, const int32_t* __restrict__ soff,
+                                int32_t* __restrict__ pre, int32_t* __restrict__ post,
+                                uint8_t* __restrict__ styp) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int a = va[t];
+        int32_t e0 = eoff[t];
+        for (int k = 0; k < a; ++k) {
+            if (!acc[e0 + k]) continue;
+            int32_t r = soff[e0 + k];
+            pre[r] = (int32_t)t;
+            post[r] = partner[e0 + k];
+            styp[r] = type[t] ? 1 : 0;
+        }
+    }
+}
+
+__global__ void k_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t* __restrict__ va,
+                       uint8_t* __restrict__ vde, uint8_t* __restrict__ vdi) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t* v[3] = {va, vde, vdi};
+        for (int ch = 0; ch < 3; ++ch) {
+            uint32_t o[4];
+            philox_draw(seed, (uint32_t)i, (uint32_t)ch | (kTagWalk << 16), step, o);
+            int nv = (int)v[ch][i] + ((o[0] & 1u) ? 1 : -1);
+            nv = nv < 0 ? 0 : (nv > 5 ? 5 : nv);
+            v[ch][i] = (uint8_t)nv;
+        }
+    }
+}
+
+__device__ inline void sat_dec(uint8_t* p) {
+    // byte-wise saturating decrement through the containing 32-bit word
+    uintptr_t addr = reinterpret_cast<uintptr_t>(p);
+    unsigned int* word = reinterpret_cast<unsigned int*>(addr & ~uintptr_t(3));
+    unsigned int sh = (unsigned int)(addr & 3u) * 8u;
+    unsigned int old = *word, assumed;
+    do {
+        assumed = old;
+        unsigned int b = (assumed >> sh) & 0xffu;
+        if (b == 0) return;
+        old = atomicCAS(word, assumed, assumed - (1u << sh));
+    } while (old != assumed);
+}
+
+__global__ void k_commit(const int64_t* __restrict__ n_syn, int64_t capacity,
+                         const int32_t* __restrict__ pre, const int32_t* __restrict__ post,
+                         const uint8_t* __restrict__ styp, uint8_t* va, uint8_t* vde, uint8_t* vdi) {
+    int64_t m = *n_syn;
+    if (m > capacity) m = capacity;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        sat_dec(va + pre[k]);
+        sat_dec((styp[k] ? vdi : vde) + post[k]);
+    }
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+static int bits_for_sel(int64_t v) {
+    int b = 1;
+    while (b < 63 && (1ll << b) <= v) ++b;
+    return b;
+}
+
+void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const uint8_t* va_dev,
+                     const uint8_t* vde_dev, const uint8_t* vdi_dev, int32_t* partner,
+                     int32_t* syn_pre, int32_t* syn_post, uint8_t* syn_type, int64_t* n_syn,
+                     cudaStream_t s) {
+    if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
+    const msp_config& cfg = c.cfg;
+    const int64_t n = c.n, ne = c.n_elem;
+    const int B = 256;
+    const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
+    c.n_draws = c.n_requests = c.n_synapses = 0;
+    if (ne == 0) {
+        MSP_CUDA(cudaMemsetAsync(n_syn, 0, sizeof(int64_t), s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
+    k_fill_i32<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(partner, ne, -1);
+    MSP_LAUNCH("fill_partner");
+
+    Tree tr;
+    tr.level = c.nd_level.get<uint8_t>();
+    tr.first = c.nd_first.get<int32_t>();
+    tr.count = c.nd_count.get<int32_t>();
+    tr.child_first = c.nd_child_first.get<int32_t>();
+    tr.nchild = c.nd_nchild.get<uint8_t>();
+    tr.sums = c.nd_sums.get<int4>();
+    tr.ca = c.nd_ca.get<float4>();
+    tr.cd = c.nd_cd.get<float4>();
+    Exps ex;
+    ex.A = c.expA.get<float>();
+    ex.M = c.expM.get<float>();
+    ex.first = c.exp_first;
+    ex.p = cfg.p;
+    ex.inv_sigma = (float)(1.0 / cfg.sigma);
+
+    // a11: items of both channels start at (root, root) if the root pair has
+    // vacancies and attraction in that channel
+    int64_t cap_items = 2 * c.n_nodes + 64, cap_leaf = 2 * c.n_nodes + 64;
+    Item* it0 = c.items0.ensure<Item>((size_t)cap_items);
+    Item* it1 = c.items1.ensure<Item>((size_t)cap_items);
+    Item* lit = c.leaf_items.ensure<Item>((size_t)cap_leaf);
+    unsigned long long* ctr = c.small_dev.ensure<unsigned long long>(8) + 2;
+    int4 root_sums;
+    double2 root_w;
+    MSP_CUDA(cudaMemcpyAsync(&root_sums, c.nd_sums.get<int4>(), sizeof(int4), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaMemcpyAsync(&root_w, c.pr_w.get<double2>(), sizeof(double2), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    std::vector<Item> init;
+    if (root_sums.x > 0 && root_w.x > 0.0) init.push_back(Item{0, 0, 0, 0});
+    if (root_sums.y > 0 && root_w.y > 0.0) init.push_back(Item{0, 0, 0, 1});
+    int64_t n_in = (int64_t)init.size();
+    if (n_in) MSP_CUDA(cudaMemcpyAsync(it0, init.data(), n_in * sizeof(Item), cudaMemcpyHostToDevice, s));
+    MSP_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+    Item *cur = it0, *nxt = it1;
+    int guard = 0;
+    while (n_in > 0) {
+        MSP_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
+        int g = grid_for(n_in, kDescWarps, (int64_t)c.sm_count * 32);
+        k_descend<<<g, kDescWarps * 32, 0, s>>>(cur, n_in, tr, ex, c.pr_kind.get<uint8_t>(),
+                                                c.pr_cf.get<int32_t>(), c.pr_w.get<double2>(),
+                                                cfg.seed, step, nxt, cap_items, lit, cap_leaf, ctr);
+        MSP_LAUNCH("descend");
+        MSP_CUDA(cudaMemcpyAsync(c.small_host, ctr, 4 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        if (c.small_host[3] != 0) throw Error(MSP_ERR_CHECK, "descent item capacity exceeded");
+        n_in = c.small_host[0];
+        std::swap(cur, nxt);
+        if (++guard > 4 * kMortonBits + 8) throw Error(MSP_ERR_CHECK, "descent did not terminate");
+    }
+    int64_t n_leaf = c.small_host[1];
+    c.n_draws = c.small_host[2];
+    if (n_leaf > 0) {
+        int g = grid_for(n_leaf * 32, 256, (int64_t)c.sm_count * 32);
+        k_leaf_draw<<<g, 256, 0, s>>>(lit, n_leaf, c.nd_first.get<int32_t>(),
+                                      c.nd_count.get<int32_t>(), c.pts.get<float4>(),
+                                      c.wts.get<float2>(), c.perm.get<int32_t>(),
+                                      c.elem_off.get<int32_t>(), k2, cfg.seed, step, partner, ctr);
+        MSP_LAUNCH("leaf_draw");
+    }
+
+    // a12: requests, sorted by (dendrite, channel, priority, element)
+    int32_t* flag = c.cnt.ensure<int32_t>((size_t)ne);
+    int32_t* roff = c.off.ensure<int32_t>((size_t)ne);
+    k_request_flags<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(partner, ne, flag);
+    MSP_LAUNCH("request_flags");
+    int64_t nr = scan_exclusive(c, flag, roff, ne, s);
+    c.n_requests = nr;
+    uint8_t* acc = c.accepted.ensure<uint8_t>((size_t)ne);
+    MSP_CUDA(cudaMemsetAsync(acc, 0, (size_t)ne, s));
+    if (nr > 0) {
+        size_t m = (size_t)nr;
+        uint64_t* k0 = c.rq_key0.ensure<uint64_t>(m);
+        uint64_t* k1 = c.rq_key1.ensure<uint64_t>(m);
+        int32_t* v0 = c.rq_val0.ensure<int32_t>(m);
+        int32_t* v1 = c.rq_val1.ensure<int32_t>(m);
+        k_request_emit<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
+            n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff, cfg.seed, step, k0, v0);
+        MSP_LAUNCH("request_emit");
+        radix_sort(c, k0, v0, k1, v1, nr, 32 + bits_for_sel(2 * n), s);
+        k_accept<<<grid_for(nr, B, (int64_t)c.sm_count * 16), B, 0, s>>>(k0, v0, nr, vde_dev,
+                                                                         vdi_dev, acc);
+        MSP_LAUNCH("accept");
+    }
+    k_acc_flags<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(acc, ne, flag);
+    MSP_LAUNCH("acc_flags");
+    int32_t* soff = c.acc_off.ensure<int32_t>((size_t)ne);
+    int64_t nsyn = scan_exclusive(c, flag, soff, ne, s);
+    c.n_synapses = nsyn;
+    k_emit_synapses<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
+        n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, acc, soff, syn_pre, syn_post,
+        syn_type);
+    MSP_LAUNCH("emit_synapses");
+    c.small_host[4] = nsyn;
+    MSP_CUDA(cudaMemcpyAsync(n_syn, &c.small_host[4], sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MSP_CUDA(cudaMemcpyAsync(c.small_host, ctr + 2, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    c.n_draws = c.small_host[0];
+}
+
+void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde, uint8_t* vdi,
+                  cudaStream_t s) {
+    if (n <= 0) return;
+    k_walk<<<grid_for(n, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(n, c.cfg.seed, step, va,
+                                                                        vde, vdi);
+    MSP_LAUNCH("walk");
+}
+
+void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const int32_t* pre,
+                     const int32_t* post, const uint8_t* styp, uint8_t* va, uint8_t* vde,
+                     uint8_t* vdi, cudaStream_t s) {
+    if (capacity <= 0) return;
+    k_commit<<<grid_for(capacity, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
+        n_syn, capacity, pre, post, styp, va, vde, vdi);
+    MSP_LAUNCH("commit");
+}
+
+}  // namespace msp

@@ -1,0 +1,314 @@
+// msp_tree.cu -- steps a1-a4: Morton keys, stable sort + gather into a
+// Morton-ordered float4 array, the adaptive octree (Section 3.2) built level
+// by level, and the per-box sums of vacant elements and centroids.
+#include "msp_internal.cuh"
+
+namespace msp {
+
+namespace {
+
+// q = floor((v - o) * scale) in single precision with round-to-nearest, then
+// clamped to the 2^21 grid; NaN maps to 0.
+__device__ inline uint32_t quantise(float v, float o, float scale) {
+    float f = floorf(__fmul_rn(__fsub_rn(v, o), scale));
+    if (!(f >= 0.0f)) return 0u;
+    if (f >= 2097152.0f) return 2097151u;
+    return (uint32_t)f;
+}
+
+__global__ void k_morton(const float* __restrict__ x, const float* __restrict__ y,
+                         const float* __restrict__ z, int64_t n, float ox, float oy, float oz,
+                         float scale, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t qx = quantise(x[i], ox, scale);
+        uint32_t qy = quantise(y[i], oy, scale);
+        uint32_t qz = quantise(z[i], oz, scale);
+        keys[i] = (spread_by3(qx) << 2) | (spread_by3(qy) << 1) | spread_by3(qz);
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_gather(const int32_t* __restrict__ order, int64_t n, const float* __restrict__ x,
+                         const float* __restrict__ y, const float* __restrict__ z,
+                         const uint8_t* __restrict__ type, const uint8_t* __restrict__ va,
+                         const uint8_t* __restrict__ vde, const uint8_t* __restrict__ vdi,
+                         int32_t* __restrict__ perm, int32_t* __restrict__ inv,
+                         float4* __restrict__ pts, float2* __restrict__ wts,
+                         float2* __restrict__ lw) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = order[j];
+        perm[j] = i;
+        inv[i] = (int32_t)j;
+        uint32_t packed = (uint32_t)(type[i] ? 1u : 0u) | ((uint32_t)va[i] << 8) |
+                          ((uint32_t)vde[i] << 16) | ((uint32_t)vdi[i] << 24);
+        pts[j] = make_float4(x[i], y[i], z[i], __uint_as_float(packed));
+        wts[j] = make_float2((float)vde[i], (float)vdi[i]);
+        // log2 of the dendrite weights (-inf for none), added in the exponent
+        lw[j] = make_float2(vde[i] ? log2f((float)vde[i]) : -INFINITY,
+                            vdi[i] ? log2f((float)vdi[i]) : -INFINITY);
+    }
+}
+
+__global__ void k_u8_to_i32(const uint8_t* __restrict__ a, int64_t n, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i];
+}
+
+__global__ void k_init_root(int64_t n, uint8_t* level, uint64_t* prefix, int32_t* first,
+                            int32_t* count, int32_t* parent, int32_t* child_first,
+                            uint8_t* nchild) {
+    level[0] = 0;
+    prefix[0] = 0;
+    first[0] = 0;
+    count[0] = (int32_t)n;
+    parent[0] = -1;
+    child_first[0] = -1;
+    nchild[0] = 0;
+}
+
+// first index in [lo, hi) whose octant (at shift) is >= o; octants are
+// non-decreasing inside a box because the higher bits are the box prefix
+__device__ inline int32_t octant_lower_bound(const uint64_t* __restrict__ keys, int32_t lo,
+                                             int32_t hi, int shift, uint32_t o) {
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if (((keys[mid] >> shift) & 7u) < o)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// number of non-empty octants of every box at this level that is split
+__global__ void k_count_children(int64_t l0, int64_t nl, int level, int leaf_capacity,
+                                 int max_depth, const uint64_t* __restrict__ keys,
+                                 const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+                                 int32_t* __restrict__ cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = l0 + k;
+        int32_t c = count[i];
+        int nch = 0;
+        if (c > leaf_capacity && level < max_depth) {
+            int shift = 3 * (kMortonBits - (level + 1));
+            int32_t lo = first[i], hi = first[i] + c;
+            int32_t b = lo;
+            for (uint32_t o = 0; o < 8; ++o) {
+                int32_t e = octant_lower_bound(keys, b, hi, shift, o + 1);
+                nch += (e > b);
+                b = e;
+            }
+        }
+        cnt[k] = nch;
+    }
+}
+
+__global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level,
+                                const uint64_t* __restrict__ keys, const int32_t* __restrict__ cnt,
+                                const int32_t* __restrict__ off, uint8_t* __restrict__ nd_level,
+                                uint64_t* __restrict__ nd_prefix, int32_t* __restrict__ nd_first,
+                                int32_t* __restrict__ nd_count, int32_t* __restrict__ nd_parent,
+                                int32_t* __restrict__ nd_child_first,
+                                uint8_t* __restrict__ nd_nchild) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = l0 + k;
+        int nch = cnt[k];
+        if (nch == 0) continue;
+        int64_t cf = next0 + off[k];
+        nd_child_first[i] = (int32_t)cf;
+        nd_nchild[i] = (uint8_t)nch;
+        int shift = 3 * (kMortonBits - (level + 1));
+        int32_t lo = nd_first[i], hi = nd_first[i] + nd_count[i];
+        uint64_t pre = nd_prefix[i];
+        int32_t b = lo;
+        int j = 0;
+        for (uint32_t o = 0; o < 8; ++o) {
+            int32_t e = octant_lower_bound(keys, b, hi, shift, o + 1);
+            if (e > b) {
+                int64_t ci = cf + j++;
+                nd_level[ci] = (uint8_t)(level + 1);
+                nd_prefix[ci] = (pre << 3) | o;
+                nd_first[ci] = b;
+                nd_count[ci] = e - b;
+                nd_parent[ci] = (int32_t)i;
+                nd_child_first[ci] = -1;
+                nd_nchild[ci] = 0;
+            }
+            b = e;
+        }
+    }
+}
+
+// Box aggregates, deepest level first.  A leaf sums its points; an inner box
+// combines its children.  Centroids are accumulated as weighted offsets from
+// the box's geometric centre so that single precision keeps them accurate.
+__global__ void k_aggregate(int64_t l0, int64_t nl, int level, float ox, float oy, float oz,
+                            float side, const float4* __restrict__ pts,
+                            const uint64_t* __restrict__ prefix, const int32_t* __restrict__ first,
+                            const int32_t* __restrict__ count,
+                            const int32_t* __restrict__ child_first,
+                            const uint8_t* __restrict__ nchild, int4* __restrict__ sums,
+                            float4* __restrict__ ca, float4* __restrict__ cd,
+                            int32_t* __restrict__ leaf_of) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = l0 + k;
+        uint64_t pre = prefix[i];
+        float bs = ldexpf(side, -level);
+        float g[3] = {ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs,
+                      oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs,
+                      oz + ((float)compact_by3(pre) + 0.5f) * bs};
+        int aE = 0, aI = 0, wE = 0, wI = 0;
+        float sa[3] = {0.f, 0.f, 0.f}, sd[3] = {0.f, 0.f, 0.f};
+        int32_t cf = child_first[i];
+        if (cf < 0) {
+            int32_t f = first[i], c = count[i];
+            for (int32_t j = f; j < f + c; ++j) {
+                float4 p = pts[j];
+                uint32_t w = __float_as_uint(p.w);
+                int a = (int)pk_axon(w), de = (int)pk_de(w), di = (int)pk_di(w);
+                if (pk_type(w)) aI += a; else aE += a;
+                wE += de;
+                wI += di;
+                float fa = (float)a, fd = (float)(de + di);
+                float dx = p.x - g[0], dy = p.y - g[1], dz = p.z - g[2];
+                sa[0] = fmaf(fa, dx, sa[0]); sa[1] = fmaf(fa, dy, sa[1]); sa[2] = fmaf(fa, dz, sa[2]);
+                sd[0] = fmaf(fd, dx, sd[0]); sd[1] = fmaf(fd, dy, sd[1]); sd[2] = fmaf(fd, dz, sd[2]);
+                leaf_of[j] = (int32_t)i;
+            }
+        } else {
+            int nc = nchild[i];
+            for (int j = 0; j < nc; ++j) {
+                int4 s = sums[cf + j];
+                float4 a4 = ca[cf + j], d4 = cd[cf + j];
+                aE += s.x; aI += s.y; wE += s.z; wI += s.w;
+                float fa = (float)(s.x + s.y), fd = (float)(s.z + s.w);
+                sa[0] = fmaf(fa, a4.x - g[0], sa[0]); sa[1] = fmaf(fa, a4.y - g[1], sa[1]);
+                sa[2] = fmaf(fa, a4.z - g[2], sa[2]);
+                sd[0] = fmaf(fd, d4.x - g[0], sd[0]); sd[1] = fmaf(fd, d4.y - g[1], sd[1]);
+                sd[2] = fmaf(fd, d4.z - g[2], sd[2]);
+            }
+        }
+        sums[i] = make_int4(aE, aI, wE, wI);
+        float ta = (float)(aE + aI), td = (float)(wE + wI);
+        ca[i] = ta > 0.f ? make_float4(g[0] + sa[0] / ta, g[1] + sa[1] / ta, g[2] + sa[2] / ta, ta)
+                         : make_float4(g[0], g[1], g[2], 0.f);
+        cd[i] = td > 0.f ? make_float4(g[0] + sd[0] / td, g[1] + sd[1] / td, g[2] + sd[2] / td, td)
+                         : make_float4(g[0], g[1], g[2], 0.f);
+    }
+}
+
+}  // namespace
+
+void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const float* z,
+                const uint8_t* type, const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
+                cudaStream_t s) {
+    c.tree_built = false;
+    c.attraction_done = false;
+    c.n = n;
+    const msp_config& cfg = c.cfg;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    uint64_t* k0 = c.keys0.ensure<uint64_t>(nn);
+    uint64_t* k1 = c.keys1.ensure<uint64_t>(nn);
+    int32_t* v0 = c.vals0.ensure<int32_t>(nn);
+    int32_t* v1 = c.vals1.ensure<int32_t>(nn);
+    int32_t* perm = c.perm.ensure<int32_t>(nn);
+    int32_t* inv = c.inv.ensure<int32_t>(nn);
+    float4* pts = c.pts.ensure<float4>(nn);
+    float2* wts = c.wts.ensure<float2>(nn);
+    float2* lw = c.lw.ensure<float2>(nn);
+    int32_t* eoff = c.elem_off.ensure<int32_t>(nn + 1);
+    int32_t* leaf_of = c.leaf_of.ensure<int32_t>(nn);
+    const int B = 256;
+    const int G = grid_for(n, B, (int64_t)c.sm_count * 16);
+
+    // a1 + a2: keys, stable sort, gather into Morton order
+    if (n > 0) {
+        k_morton<<<G, B, 0, s>>>(x, y, z, n, cfg.origin[0], cfg.origin[1], cfg.origin[2],
+                                 c.morton_scale, k0, v0);
+        MSP_LAUNCH("morton");
+        radix_sort(c, k0, v0, k1, v1, n, 3 * kMortonBits, s);
+        k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
+        MSP_LAUNCH("gather");
+        // element offsets: exclusive prefix of the vacant axonal counts
+        int32_t* tmp = c.cnt.ensure<int32_t>(nn);
+        k_u8_to_i32<<<G, B, 0, s>>>(va, n, tmp);
+        MSP_LAUNCH("u8_to_i32");
+        c.n_elem = scan_exclusive(c, tmp, eoff, n, s);
+        int32_t ne = (int32_t)c.n_elem;
+        MSP_CUDA(cudaMemcpyAsync(eoff + n, &ne, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        // the host value must outlive the copy
+        MSP_CUDA(cudaStreamSynchronize(s));
+    } else {
+        c.n_elem = 0;
+    }
+
+    // a3: level-synchronous octree
+    size_t cap = (size_t)(2 * nn / (size_t)std::max(cfg.leaf_capacity, 1) + 64);
+    auto grow_nodes = [&](size_t need, size_t keep) {
+        c.nd_level.grow<uint8_t>(need, keep, s);
+        c.nd_prefix.grow<uint64_t>(need, keep, s);
+        c.nd_first.grow<int32_t>(need, keep, s);
+        c.nd_count.grow<int32_t>(need, keep, s);
+        c.nd_parent.grow<int32_t>(need, keep, s);
+        c.nd_child_first.grow<int32_t>(need, keep, s);
+        c.nd_nchild.grow<uint8_t>(need, keep, s);
+    };
+    grow_nodes(cap, 0);
+    k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
+                                c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+                                c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
+                                c.nd_nchild.get<uint8_t>());
+    MSP_LAUNCH("init_root");
+    c.level_start.assign(1, 0);
+    c.level_start.push_back(1);
+    int64_t total = 1;
+    int depth = 0;
+    for (int l = 0; l < cfg.max_depth && n > 0; ++l) {
+        int64_t l0 = c.level_start[l], nl = c.level_start[l + 1] - l0;
+        int32_t* cnt = c.cnt.ensure<int32_t>((size_t)nl);
+        int32_t* off = c.off.ensure<int32_t>((size_t)nl);
+        k_count_children<<<grid_for(nl, B), B, 0, s>>>(l0, nl, l, cfg.leaf_capacity,
+                                                       cfg.max_depth, k0,
+                                                       c.nd_first.get<int32_t>(),
+                                                       c.nd_count.get<int32_t>(), cnt);
+        MSP_LAUNCH("count_children");
+        int64_t nnext = scan_exclusive(c, cnt, off, nl, s);
+        if (nnext == 0) break;
+        if ((size_t)(total + nnext) > c.nd_first.bytes / sizeof(int32_t))
+            grow_nodes((size_t)(total + nnext), (size_t)total);
+        k_emit_children<<<grid_for(nl, B), B, 0, s>>>(
+            l0, nl, total, l, k0, cnt, off, c.nd_level.get<uint8_t>(),
+            c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+            c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
+            c.nd_nchild.get<uint8_t>());
+        MSP_LAUNCH("emit_children");
+        total += nnext;
+        c.level_start.push_back(total);
+        depth = l + 1;
+    }
+    c.n_nodes = total;
+    c.tree_depth = depth;
+
+    // a4: aggregates, deepest level first
+    int4* sums = c.nd_sums.ensure<int4>((size_t)total);
+    float4* ca = c.nd_ca.ensure<float4>((size_t)total);
+    float4* cd = c.nd_cd.ensure<float4>((size_t)total);
+    for (int l = depth; l >= 0; --l) {
+        int64_t l0 = c.level_start[l], nl = c.level_start[l + 1] - l0;
+        k_aggregate<<<grid_for(nl, 128), 128, 0, s>>>(
+            l0, nl, l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
+            c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+            c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
+        MSP_LAUNCH("aggregate");
+    }
+    MSP_CUDA(cudaStreamSynchronize(s));
+    c.tree_built = true;
+}
+
+}  // namespace msp

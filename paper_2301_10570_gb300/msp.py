@@ -1,0 +1,266 @@
+"""Python binding of libmsp (include/msp.h): argument marshalling only.
+
+Every step of the synapse search runs in the CUDA library; this module only
+turns torch tensors into device pointers and the current torch stream into a
+cudaStream_t.  There is no fallback: if the library is missing or fails to
+load, constructing :class:`MSP` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmsp.so")
+_lock = threading.Lock()
+_lib = None
+
+SPLIT, FAR, P2P, PRUNED = 0, 1, 2, 3
+STATUS = {0: "MSP_OK", 1: "MSP_ERR_INVALID_ARG", 2: "MSP_ERR_CUDA", 3: "MSP_ERR_OOM",
+          4: "MSP_ERR_TIMEOUT", 5: "MSP_ERR_NOT_BUILT", 6: "MSP_ERR_CHECK",
+          7: "MSP_ERR_CAPACITY"}
+
+EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "msp_direct",
+            "msp_select_partners", "msp_plasticity_step_host", "msp_vacancy_walk",
+            "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
+            "msp_export_expansions", "msp_last_error")
+
+
+class MSPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("p", C.c_int), ("leaf_capacity", C.c_int),
+                ("max_depth", C.c_int), ("origin", C.c_float * 3), ("side", C.c_float),
+                ("seed", C.c_uint64), ("rho_max", C.c_double), ("cutoff", C.c_double),
+                ("m2l_min_pairs", C.c_longlong)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
+                ("tree_depth", C.c_int32), ("far_level", C.c_int32), ("n_pairs", C.c_int64),
+                ("pair_depths", C.c_int32), ("n_far", C.c_int64), ("n_p2p", C.c_int64),
+                ("p2p_interactions", C.c_int64), ("n_elements", C.c_int64),
+                ("n_draws", C.c_int64), ("n_requests", C.c_int64), ("n_synapses", C.c_int64),
+                ("expansion_nodes", C.c_int64)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libmsp.so (built by paper_2301_10570_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2301_10570_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        vp, i64, u64 = C.c_void_p, C.c_int64, C.c_uint64
+        L.msp_create.argtypes = [C.POINTER(vp), C.POINTER(Config), C.c_int]
+        L.msp_destroy.argtypes = [vp]
+        L.msp_build_tree.argtypes = [vp, i64] + [vp] * 7 + [vp]
+        L.msp_attraction.argtypes = [vp, vp, vp]
+        L.msp_direct.argtypes = [vp, vp, vp]
+        L.msp_select_partners.argtypes = [vp, u64] + [vp] * 5 + [vp]
+        L.msp_plasticity_step_host.argtypes = [vp, i64, u64] + [vp] * 13
+        L.msp_vacancy_walk.argtypes = [vp, i64, u64, vp, vp, vp, vp]
+        L.msp_commit_synapses.argtypes = [vp, vp, i64] + [vp] * 6 + [vp]
+        L.msp_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.msp_export_tree.argtypes = [vp] * 12
+        L.msp_export_pairs.argtypes = [vp] * 8
+        L.msp_export_expansions.argtypes = [vp] * 5
+        L.msp_last_error.restype = C.c_char_p
+        for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
+                     "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
+                     "msp_vacancy_walk", "msp_commit_synapses", "msp_get_stats",
+                     "msp_export_tree", "msp_export_pairs", "msp_export_expansions"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(code):
+    if code != 0:
+        raise MSPError(code, load().msp_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _np(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_config(params: dict) -> Config:
+    c = Config()
+    c.sigma = float(params["sigma"])
+    c.p = int(params["p"])
+    c.leaf_capacity = int(params["leaf_capacity"])
+    c.max_depth = int(params.get("max_depth", 21))
+    for d in range(3):
+        c.origin[d] = float(params["origin"][d])
+    c.side = float(params["side"])
+    c.seed = int(params.get("seed", 0))
+    c.rho_max = float(params["rho_max"])
+    c.cutoff = float(params["cutoff"])
+    c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
+    return c
+
+
+class MSP:
+    """One libmsp context on a CUDA device."""
+
+    def __init__(self, params: dict, device: int = 0):
+        L = load()
+        self.params = dict(params)
+        self.device = device
+        self._cfg = make_config(params)
+        h = C.c_void_p()
+        _check(L.msp_create(C.byref(h), C.byref(self._cfg), int(device)))
+        self._h = h
+        self.n = 0
+        self._inputs = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().msp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the path -----------------------------------------------------------
+    def build_tree(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, stream=None):
+        """pos: (3, n) float32 CUDA tensor; the rest (n,) uint8 CUDA tensors."""
+        pos = pos.contiguous()
+        ins = [pos[0].contiguous(), pos[1].contiguous(), pos[2].contiguous(),
+               type_.contiguous(), vac_axon.contiguous(), vac_dend_e.contiguous(),
+               vac_dend_i.contiguous()]
+        for t, dt in zip(ins, [torch.float32] * 3 + [torch.uint8] * 4):
+            if not t.is_cuda or t.dtype != dt:
+                raise TypeError("build_tree expects CUDA float32 positions and uint8 counts")
+        self.n = int(pos.shape[1])
+        self._inputs = ins
+        _check(load().msp_build_tree(self._h, self.n, *[_ptr(t) for t in ins], _stream(stream)))
+
+    def attraction(self, out=None, stream=None):
+        u = out if out is not None else torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(load().msp_attraction(self._h, _ptr(u), _stream(stream)))
+        return u
+
+    def direct(self, out=None, stream=None):
+        u = out if out is not None else torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(load().msp_direct(self._h, _ptr(u), _stream(stream)))
+        return u
+
+    def num_elements(self) -> int:
+        return self.stats()["n_elements"]
+
+    def select_partners(self, step: int, out=None, stream=None):
+        ne = max(self.num_elements(), 1)
+        if out is None:
+            dev = "cuda"
+            out = dict(partner=torch.empty(ne, dtype=torch.int32, device=dev),
+                       syn_pre=torch.empty(ne, dtype=torch.int32, device=dev),
+                       syn_post=torch.empty(ne, dtype=torch.int32, device=dev),
+                       syn_type=torch.empty(ne, dtype=torch.uint8, device=dev),
+                       n_syn=torch.zeros(1, dtype=torch.int64, device=dev))
+        _check(load().msp_select_partners(self._h, int(step), _ptr(out["partner"]),
+                                          _ptr(out["syn_pre"]), _ptr(out["syn_post"]),
+                                          _ptr(out["syn_type"]), _ptr(out["n_syn"]),
+                                          _stream(stream)))
+        return out
+
+    def plasticity_step_host(self, step, pos, type_, vac_axon, vac_dend_e, vac_dend_i,
+                             out=None, want_u=True):
+        """Whole step from host (numpy, ideally pinned) buffers; returns host results."""
+        n = int(pos.shape[1])
+        x, y, z = (np.ascontiguousarray(pos[d], dtype=np.float32) for d in range(3))
+        t, a, e, i = (np.ascontiguousarray(v, dtype=np.uint8) for v in
+                      (type_, vac_axon, vac_dend_e, vac_dend_i))
+        ne = max(int(a.sum(dtype=np.int64)), 1)
+        if out is None:
+            out = dict(u=np.zeros(max(n, 1), np.float32), partner=np.zeros(ne, np.int32),
+                       syn_pre=np.zeros(ne, np.int32), syn_post=np.zeros(ne, np.int32),
+                       syn_type=np.zeros(ne, np.uint8), n_syn=np.zeros(1, np.int64))
+        _check(load().msp_plasticity_step_host(
+            self._h, n, int(step), _np(x), _np(y), _np(z), _np(t), _np(a), _np(e), _np(i),
+            _np(out["u"]) if want_u else None, _np(out["partner"]), _np(out["syn_pre"]),
+            _np(out["syn_post"]), _np(out["syn_type"]), _np(out["n_syn"])))
+        return out
+
+    def vacancy_walk(self, step, vac_axon, vac_dend_e, vac_dend_i, stream=None):
+        _check(load().msp_vacancy_walk(self._h, int(vac_axon.numel()), int(step),
+                                       _ptr(vac_axon), _ptr(vac_dend_e), _ptr(vac_dend_i),
+                                       _stream(stream)))
+
+    def commit_synapses(self, sel, vac_axon, vac_dend_e, vac_dend_i, stream=None):
+        _check(load().msp_commit_synapses(self._h, _ptr(sel["n_syn"]), int(sel["syn_pre"].numel()),
+                                          _ptr(sel["syn_pre"]), _ptr(sel["syn_post"]),
+                                          _ptr(sel["syn_type"]), _ptr(vac_axon),
+                                          _ptr(vac_dend_e), _ptr(vac_dend_i), _stream(stream)))
+
+    # -- introspection ------------------------------------------------------
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().msp_get_stats(self._h, C.byref(s)))
+        return {name: int(getattr(s, name)) for name, _ in Stats._fields_}
+
+    def export_tree(self):
+        st = self.stats()
+        n, m = st["n"], st["n_nodes"]
+        out = dict(keys=np.zeros(max(n, 1), np.uint64), perm=np.zeros(max(n, 1), np.int32),
+                   level=np.zeros(m, np.uint8), prefix=np.zeros(m, np.uint64),
+                   first=np.zeros(m, np.int32), count=np.zeros(m, np.int32),
+                   parent=np.zeros(m, np.int32), child_first=np.zeros(m, np.int32),
+                   nchild=np.zeros(m, np.uint8), sums=np.zeros((m, 4), np.int32),
+                   centroids=np.zeros((m, 6), np.float32))
+        _check(load().msp_export_tree(self._h, *[_np(out[k]) for k in
+                                                 ("keys", "perm", "level", "prefix", "first",
+                                                  "count", "parent", "child_first", "nchild",
+                                                  "sums", "centroids")]))
+        out["keys"], out["perm"] = out["keys"][:n], out["perm"][:n]
+        return out
+
+    def export_pairs(self):
+        st = self.stats()
+        m, nd = st["n_pairs"], st["pair_depths"]
+        out = dict(X=np.zeros(m, np.int32), Y=np.zeros(m, np.int32), kind=np.zeros(m, np.uint8),
+                   child_first=np.zeros(m, np.int32), wE=np.zeros(m), wI=np.zeros(m),
+                   depth_start=np.zeros(nd + 1, np.int64))
+        _check(load().msp_export_pairs(self._h, *[_np(out[k]) for k in
+                                                  ("X", "Y", "kind", "child_first", "wE", "wI",
+                                                   "depth_start")]))
+        return out
+
+    def export_expansions(self):
+        st = self.stats()
+        p3 = self._cfg.p ** 3
+        m = st["expansion_nodes"]
+        A, M, B = (np.zeros((max(m, 1), 2, p3), np.float32) for _ in range(3))
+        first = np.zeros(1, np.int64)
+        _check(load().msp_export_expansions(self._h, _np(A), _np(M), _np(B), _np(first)))
+        return A[:m], M[:m], B[:m], int(first[0])
+
+
+def to_device(w, device="cuda"):
+    """Move a workload's arrays to the GPU (pos (3,n) f32, counts u8)."""
+    return (torch.from_numpy(np.ascontiguousarray(w.pos)).to(device),
+            torch.from_numpy(w.type).to(device), torch.from_numpy(w.vac_axon).to(device),
+            torch.from_numpy(w.vac_dend_e).to(device), torch.from_numpy(w.vac_dend_i).to(device))
