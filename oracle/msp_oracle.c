@@ -34,6 +34,12 @@
 #define TAG_ACCEPT  3u
 #define TAG_WALK    4u
 #define MAXP 8
+/* A draw whose total attraction is at or below this counts as having no
+ * candidate (no partner is drawn).  Every attraction inside the cutoff radius
+ * is many orders of magnitude larger (exp(-cutoff^2) times an integer
+ * weight); the threshold only keeps sums of terms far below single precision
+ * range from deciding a draw. */
+#define ORC_MIN_ATTRACTION 1e-30
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as    */
@@ -664,7 +670,8 @@ static double far_w(const orc_ctx *c, int32_t X, int32_t Y, int ch)
 
 /* Algorithm 2's last three steps: total, uniform draw in [0,total),
  * upper_bound over the inclusive prefix sums.  Negative candidates (possible
- * only through truncation) count as zero.  Returns -1 when total is zero.
+ * only through truncation) count as zero.  Returns -1 when the total is at
+ * most ORC_MIN_ATTRACTION.
  * *nb is set when r falls within tol*total of an inner boundary. */
 static int draw_index(const double *w, int k, double U, double tol, uint8_t *nb)
 {
@@ -674,7 +681,7 @@ static int draw_index(const double *w, int k, double U, double tol, uint8_t *nb)
         tot += w[i] > 0.0 ? w[i] : 0.0;
         pre[i] = tot;
     }
-    if (!(tot > 0.0)) return -1;
+    if (!(tot > ORC_MIN_ATTRACTION)) return -1;
     double r = U * tot;
     int pick = -1;
     for (int i = 0; i < k; ++i)
@@ -715,6 +722,7 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
     const orc_config *cfg = &c->cfg;
     const double tol = cfg->boundary_tol;
     const double inv_s2 = 1.0 / (cfg->sigma * cfg->sigma);
+    const double rc2 = (cfg->cutoff * cfg->sigma) * (cfg->cutoff * cfg->sigma);
     int64_t n_elem = c->n_elem;
     for (int64_t e = 0; e < n_elem; ++e) { partner[e] = -1; near_boundary[e] = 0; accepted[e] = 0; }
     int64_t draws = 0, bdraws = 0;
@@ -722,7 +730,7 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
     for (int ch = 0; ch < 2; ++ch) {
         item_t *cur = NULL, *nxt = NULL;
         int64_t ncur = 0, ccur = 0, nnxt = 0, cnxt = 0;
-        if (c->n > 0 && c->nodes[0].sa[ch] > 0 && c->pairs[0].w[ch] > 0.0) {
+        if (c->n > 0 && c->nodes[0].sa[ch] > 0 && c->pairs[0].w[ch] > ORC_MIN_ATTRACTION) {
             item_t it = {0, 0, 0, 0};
             push_item(&cur, &ncur, &ccur, it);
         }
@@ -736,7 +744,8 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
                 if (is_leaf(X) && is_leaf(Y)) {
                     /* form_synapse: every vacant element of channel ch in X
                      * draws one dendrite neuron of Y, s != t, with weight
-                     * w_s K(t, s) (Eq. 8) */
+                     * w_s K(t, s) (Eq. 8), the kernel truncated at the same
+                     * cutoff radius that prunes box pairs */
                     double w[1024];
                     double *wp = Y->count <= 1024 ? w : (double *)malloc(Y->count * sizeof(double));
                     for (int64_t t = X->first; t < (int64_t)X->first + X->count; ++t) {
@@ -750,7 +759,7 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
                                     double e = c->pos[3 * t + d] - c->pos[3 * s + d];
                                     d2 += e * e;
                                 }
-                                ws = (ch ? c->vdi[s] : c->vde[s]) * exp(-d2 * inv_s2);
+                                ws = d2 < rc2 ? (ch ? c->vdi[s] : c->vde[s]) * exp(-d2 * inv_s2) : 0.0;
                             }
                             wp[s - Y->first] = ws;
                             tot += ws;
@@ -759,7 +768,7 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
                         for (int k = 0; k < c->va[t]; ++k) {
                             int64_t e = c->elem_off[to] + k;
                             near_boundary[e] = it.nb;
-                            if (!(tot > 0.0)) continue;
+                            if (!(tot > ORC_MIN_ATTRACTION)) continue;
                             double U = orc_uniform(cfg->seed, (uint32_t)to,
                                                    (uint32_t)k | ((uint32_t)ch << 8) | (TAG_LEAF << 16),
                                                    step);
@@ -804,7 +813,7 @@ int64_t orc_select_partners(orc_ctx *c, uint64_t step, int32_t *partner,
                     for (int i = 0; i < X->nchild; ++i) {
                         int32_t xc = X->child_first + i;
                         if (c->nodes[xc].sa[ch] == 0) continue;
-                        if (split && !(c->pairs[cf + i].w[ch] > 0.0)) continue;
+                        if (split && !(c->pairs[cf + i].w[ch] > ORC_MIN_ATTRACTION)) continue;
                         item_t nx = {xc, it.Y, split ? cf + i : -1, it.nb};
                         push_item(&nxt, &nnxt, &cnxt, nx);
                     }

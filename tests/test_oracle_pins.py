@@ -385,13 +385,14 @@ def test_single_leaf_descent_is_inverse_cdf(oracle_mod):
         for t in range(w.n):
             wt = w.vac_dend_i if w.type[t] else w.vac_dend_e
             d2 = ((x - x[:, t:t + 1]) ** 2).sum(0)
-            ws = wt * np.exp(-d2 / 750.0 ** 2)
+            # kernel truncated at the pruning radius (same reading as the pairs)
+            ws = np.where(d2 < (w.params["cutoff"] * 750.0) ** 2, wt * np.exp(-d2 / 750.0 ** 2), 0.0)
             ws[t] = 0.0
             _, perm = o.keys()
             ws_sorted = ws[perm]
             cdf = np.cumsum(ws_sorted)
             for k in range(w.vac_axon[t]):
-                if cdf[-1] <= 0:
+                if cdf[-1] <= 1e-30:
                     assert r["partner"][e] == -1
                 else:
                     U = oracle_mod.uniform(0, t, k | (int(w.type[t]) << 8) | (2 << 16), step)
@@ -439,9 +440,10 @@ def _exact_partner_distribution(o, w, t_orig):
     def visit(X, Y, q, prob):
         if is_leaf(X) and is_leaf(Y):
             ys = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
-            ws = wt[ys] * np.exp(-((x[:, ys] - x[:, t:t + 1]) ** 2).sum(0) / 750.0 ** 2)
+            d2 = ((x[:, ys] - x[:, t:t + 1]) ** 2).sum(0)
+            ws = np.where(d2 < (w.params["cutoff"] * 750.0) ** 2, wt[ys] * np.exp(-d2 / 750.0 ** 2), 0.0)
             ws[ys == t] = 0.0
-            if ws.sum() > 0:
+            if ws.sum() > 1e-30:
                 out[ys] += prob * ws / ws.sum()
             return
         cf = pr["child_first"][q]
