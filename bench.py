@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Plasticity-step throughput of the GB300 synapse search.
+
+One step = the whole hot path on one network: vacancy update (seeded +-1 walk),
+Morton keys + sort + octree + box sums, dual traversal, expansions and near
+field (the attraction u of every neuron with vacant axons, and the box-pair
+attraction table), the Algorithm 1/2 descent to a partner per vacant axonal
+element, request resolution, and the consumption of the formed synapses.
+
+Workload: 1,048,576 neurons in 64 isotropic Gaussian clusters (std 1,500 um)
+inside a 100,000 um cube, sigma = 750 um, 80/20 excitatory/inhibitory, vacant
+counts uniform in {0..3} (synthetic, seeded).
+
+  python bench.py [--gpus N --steps K --warmup W]          # this library
+  python bench.py --impl reference [...]                    # the FP64 CPU oracle
+Multi-GPU runs are independent replicas (one network per GPU, no exchange).
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "plasticity-step neurons/s at 1M neurons, FMM vs direct on GB300, rel.err<=1e-4"
+UNIT = "neurons/s"
+SM_COUNT = 152
+EX2_PER_SM_CLK = 16          # MUFU.EX2 results per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
+    return ap.parse_args()
+
+
+def tuned_params():
+    """Plan chosen by the autotuner for this workload (leaf capacity, cutoff,
+    expansions): see paper_2301_10570_gb300/autotune.py."""
+    return dict(leaf_capacity=128, cutoff=4.0, rho_max=0.0, p=4, m2l_min_pairs=0)
+
+
+def workload():
+    from paper_2301_10570_gb300 import workloads as W
+    return W.clustered_1m(**tuned_params())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# -- clocks ------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(prefix="msp_clocks_", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# -- our arm -------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2301_10570_gb300 import msp, replicas
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workload()
+    n = w.n
+    g = msp.MSP(w.params, device=dev.index)
+    pos, typ, va0, ve0, vi0 = msp.to_device(w, dev)
+    va, ve, vi = va0.clone(), ve0.clone(), vi0.clone()
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    ne_cap = 5 * n          # vacancies are clamped to [0, 5]
+    sel = dict(partner=torch.empty(ne_cap, dtype=torch.int32, device=dev),
+               syn_pre=torch.empty(ne_cap, dtype=torch.int32, device=dev),
+               syn_post=torch.empty(ne_cap, dtype=torch.int32, device=dev),
+               syn_type=torch.empty(ne_cap, dtype=torch.uint8, device=dev),
+               n_syn=torch.zeros(1, dtype=torch.int64, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(k):
+        g.vacancy_walk(k, va, ve, vi)
+        g.build_tree(pos, typ, va, ve, vi)
+        g.attraction(out=u)
+        g.select_partners(k, out=sel)
+        g.commit_synapses(sel, va, ve, vi)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    launches0 = g.stats()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    nf_ms, inter, synapses = [], [], []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps (untimed)
+        ev[i][0].record()
+        step(args.warmup + i)
+        ev[i][1].record()
+        st = g.stats()                     # synchronises; outside the step's events
+        nf_ms.append(st["near_field_ms"])
+        inter.append(st["p2p_interactions"])
+        synapses.append(st["n_synapses"])
+    torch.cuda.synchronize()
+    replicas.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = g.stats()["kernel_launches"] - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    agg = replicas.aggregate_throughput(n, sum(step_ms) / len(step_ms), dev)
+    ms = agg["ms"]
+    value = agg["per_s"]
+
+    # end to end through the public host-buffer entry point (pinned buffers)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hp = pinned(w.pos)
+    ht, ha, he, hi = (pinned(a) for a in (w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i))
+    ne = int(ha.sum(dtype=np.int64))
+    hout = dict(u=pinned(np.zeros(n, np.float32)), partner=pinned(np.zeros(ne, np.int32)),
+                syn_pre=pinned(np.zeros(ne, np.int32)), syn_post=pinned(np.zeros(ne, np.int32)),
+                syn_type=pinned(np.zeros(ne, np.uint8)), n_syn=np.zeros(1, np.int64))
+    g.plasticity_step_host(0, hp, ht, ha, he, hi, out=hout)
+    torch.cuda.synchronize()
+    e2e_t, d2h = [], []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.plasticity_step_host(i, hp, ht, ha, he, hi, out=hout)
+        e2e_t.append(time.perf_counter() - t0)
+        ns = int(hout["n_syn"][0])
+        d2h.append(4 * n + 4 * ne + 9 * ns + 8)
+    e2e = replicas.aggregate_throughput(n, 1e3 * sum(e2e_t) / len(e2e_t), dev)
+    e2e_ms = e2e["ms"]
+
+    # the attraction of the unwalked inputs (accuracy checks below)
+    g.build_tree(pos, typ, va0, ve0, vi0)
+    uf = g.attraction()
+    torch.cuda.synchronize()
+    # direct all-pairs evaluation of the attraction on the same GPU
+    direct = None
+    if not args.no_direct:
+        ud = torch.empty(n, dtype=torch.float32, device=dev)
+        g.direct(out=ud)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record()
+        g.direct(out=ud)
+        e1.record()
+        torch.cuda.synchronize()
+        d_ms = e0.elapsed_time(e1)
+        m = ud > 1e-6 * ud.max()
+        rel = ((uf[m] - ud[m]).abs() / ud[m]).max().item()
+        direct = {"direct_attraction_ms": round(d_ms, 3),
+                  "direct_neurons_per_s": n / (d_ms / 1e3),
+                  "speedup_step_vs_direct_attraction": round(d_ms / ms, 2),
+                  "max_rel_err_vs_direct_fp32": rel}
+
+    # roofline of the dominant kernel (near field: one EX2 per interaction)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gex2 = SM_COUNT * EX2_PER_SM_CLK * sm_max * 1e6 / 1e9
+    nf = statistics.mean(nf_ms)
+    achieved = statistics.mean(inter) / (nf / 1e3) / 1e9 if nf > 0 else 0.0
+    roofline = {"kernel": "k_p2p (near field)", "bound": "alu", "achieved": round(achieved, 1),
+                "peak": round(peak_gex2, 1), "unit": "Gex2/s", "frac": round(achieved / peak_gex2, 4),
+                "traffic": None, "near_field_ms": round(nf, 3),
+                "near_field_share_of_step": round(nf / ms, 3),
+                "interactions_per_step": int(statistics.mean(inter)),
+                "peak_basis": f"{SM_COUNT} SMs x {EX2_PER_SM_CLK} ex2/clk x {sm_max:.0f} MHz"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "clustered_1m: 1,048,576 neurons, 64 Gaussian clusters (std 1500 um), "
+                                  "100,000 um cube, sigma 750 um, 80/20 E/I, vacancies U{0..3} + walk",
+                      "plan": tuned_params(), "parallelism": f"replicas x{world}",
+                      "l2": "flushed (256 MB write) between timed steps",
+                      "timing": "CUDA events per step, mean over steps",
+                      "wall_s_timed_loop": round(t_wall, 3),
+                      "synapses_per_step": int(statistics.mean(synapses)),
+                      **(direct or {})},
+           "clocks": clk,
+           "e2e": {"value": e2e["per_s"], "unit": UNIT,
+                   "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": int(statistics.mean(d2h)),
+                   "ms_per_step": round(e2e_ms, 3),
+                   "path": "msp_plasticity_step_host (pinned host buffers)"},
+           "gpu_launches": int(launches),
+           "roofline": roofline}
+    return out, w, g, uf
+
+
+def cpu_baseline(w, u_gpu=None, sample_clusters=4):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
+    workload (the first few clusters), plus the GPU's accuracy on sampled
+    targets against the oracle's brute force."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2301_10570_gb300 import workloads as W
+    O.build()
+    m = sample_clusters * 16_384
+    sub = W.subset(w, np.arange(m), name="first_clusters")
+    o = O.Oracle(sub.params)
+    t0 = time.perf_counter()
+    o.build_tree(*sub.arrays())
+    o.attraction()
+    o.select_partners(0)
+    dt = time.perf_counter() - t0
+    res = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {sample_clusters} clusters ({m} neurons) of the workload, one full step "
+                     f"(tree, attraction, selection) in {dt:.1f} s"}
+    if u_gpu is not None:
+        rng = np.random.default_rng(0)
+        idx = rng.choice(w.n, 256, replace=False)
+        ref = O.direct(*w.arrays(), w.params["sigma"], targets=idx)
+        ug = u_gpu[idx]
+        k = ref > 0
+        res["max_rel_err_vs_fp64_256_sampled_targets"] = float(np.max(np.abs(ug[k] - ref[k]) / ref[k]))
+    return res
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, on a bounded sample of the workload."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2301_10570_gb300 import workloads as W
+    O.build()
+    w = workload()
+    m = 16_384
+    sub = W.subset(w, np.arange(m), name="first_cluster")
+    o = O.Oracle(sub.params)
+
+    def step(k):
+        a, e, i = O.vacancy_walk(0, k, sub.vac_axon, sub.vac_dend_e, sub.vac_dend_i)
+        o.build_tree(sub.pos, sub.type, a, e, i)
+        o.attraction()
+        o.select_partners(k)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = m / dt
+    sample = f"first cluster ({m} neurons) of the 1M clustered workload per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "clustered_1m (bounded sample)", "plan": tuned_params()},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2301_10570_gb300 import build as B
+    B.build()
+    out, w, g, u = run_ours(args, rank, world)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

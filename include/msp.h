@@ -103,6 +103,11 @@ typedef struct {
     int64_t n_requests;        /* elements that drew a partner              */
     int64_t n_synapses;        /* accepted requests                         */
     int64_t expansion_nodes;   /* boxes carrying expansions                 */
+    int64_t kernel_launches;   /* kernels launched by this library in this
+                                  process so far (all contexts)             */
+    double  near_field_ms;     /* device time of the near-field kernel of the
+                                  last msp_attraction (CUDA events on its
+                                  stream); 0 if it had no near-field pairs  */
 } msp_stats;
 
 /* Create a context on CUDA device `device` (cudaSetDevice is called).

@@ -22,6 +22,10 @@ void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const i
                      uint8_t* vdi, cudaStream_t s);
 }  // namespace msp
 
+namespace msp {
+std::atomic<long long> g_kernel_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -100,6 +104,8 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
     msp_status st = guarded(c, [&] {
         MSP_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
         MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->small_host), 16 * sizeof(int64_t)));
+        MSP_CUDA(cudaEventCreate(&c->ev_nf0));
+        MSP_CUDA(cudaEventCreate(&c->ev_nf1));
         derive(*c);
     });
     if (st != MSP_OK) {
@@ -119,6 +125,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
                          &c->pr_kind, &c->pr_cf, &c->pr_w, &c->far_q, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
+                         &c->nf_w32,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
                          &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
@@ -128,6 +135,8 @@ msp_status msp_destroy(msp_ctx* c) {
     for (msp::DBuf* b : bufs) b->release();
     for (auto& b : c->h_in) b.release();
     if (c->small_host) cudaFreeHost(c->small_host);
+    if (c->ev_nf0) cudaEventDestroy(c->ev_nf0);
+    if (c->ev_nf1) cudaEventDestroy(c->ev_nf1);
     delete c;
     return MSP_OK;
 }
@@ -271,6 +280,13 @@ msp_status msp_get_stats(msp_ctx* c, msp_stats* out) {
         out->n_requests = c->n_requests;
         out->n_synapses = c->n_synapses;
         out->expansion_nodes = c->exp_nodes;
+        out->kernel_launches = msp::g_kernel_launches.load();
+        out->near_field_ms = 0.0;
+        if (c->nf_timed) {
+            float ms = 0.f;
+            MSP_CUDA(cudaEventElapsedTime(&ms, c->ev_nf0, c->ev_nf1));
+            out->near_field_ms = ms;
+        }
         if (c->n_nodes > 0) {
             std::vector<int32_t> cf((size_t)c->n_nodes);
             MSP_CUDA(cudaMemcpy(cf.data(), c->nd_child_first.p, cf.size() * 4,

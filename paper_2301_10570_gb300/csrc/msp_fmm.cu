@@ -365,158 +365,6 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
     }
 }
 
-// ---------------------------------------------------------------------------
-// a9: exact near field (Eq. 8) over the near-field leaf pairs, grouped by
-// target leaf X: one warp per X.  The warp's lanes are split into
-// (target, source-slice) groups so that small leaves still fill the warp: a
-// chunk of up to 32 targets with vacant axons is padded to T = 2^k targets and
-// each target gets 32/T lanes that walk interleaved slices of the sources.
-//
-// With k = log2(e)/sigma^2 and hats denoting sqrt(k)*(position - c) for the
-// geometric centre c of X,
-//   w_s K(t,s) = 2^( 2 t^.s^ - |s^|^2 + log2 w_s ) * 2^(-|t^|^2),
-// so a source is staged once per warp as (s^, -|s^|^2 + log2 w_s) per channel
-// and one evaluation costs three FMAs, one EX2 on the SFU and one add.
-// Per partner leaf the warp also reduces W(X,Y) = sum_t a_t sum_s w_s K(t,s).
-// ---------------------------------------------------------------------------
-constexpr int kP2PWarps = 4;
-constexpr int kP2PStage = 128;
-
-__global__ void __launch_bounds__(kP2PWarps * 32)
-k_p2p(const int32_t* __restrict__ seg_first, int64_t nseg, const int32_t* __restrict__ list_q,
-      const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
-      const uint8_t* __restrict__ nlevel, const uint64_t* __restrict__ nprefix,
-      const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
-      const float4* __restrict__ pts, const float2* __restrict__ lw, float sqk, float ox,
-      float oy, float oz, float side, float* __restrict__ u, double2* __restrict__ pw,
-      unsigned long long* __restrict__ work) {
-    __shared__ float4 stE[kP2PWarps][kP2PStage];
-    __shared__ float4 stI[kP2PWarps][kP2PStage];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* sE = stE[w];
-    float4* sI = stI[w];
-    for (int64_t sg = (int64_t)blockIdx.x * kP2PWarps + w; sg < nseg;
-         sg += (int64_t)gridDim.x * kP2PWarps) {
-        const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
-        const int32_t X = pX[list_q[i0]];
-        const int32_t tf = nfirst[X], tc = ncount[X];
-        const int lvl = nlevel[X];
-        const uint64_t pre = nprefix[X];
-        const float bs = ldexpf(side, -lvl);
-        const float cx = ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs;
-        const float cy = oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs;
-        const float cz = oz + ((float)compact_by3(pre) + 0.5f) * bs;
-        // the expanded exponent needs |t^|^2 <= 4 for every target of X
-        const bool fast = 0.75f * sqk * sqk * bs * bs <= 4.f;
-        unsigned long long evals = 0;
-        for (int32_t tb = 0; tb < tc; tb += 32) {
-            // compact the targets of this chunk that have vacant axons
-            const int32_t tl = tf + tb + lane;
-            float4 T = tb + lane < tc ? pts[tl] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const uint32_t twl = __float_as_uint(T.w);
-            const bool act = tb + lane < tc && pk_axon(twl) > 0;
-            const unsigned mask = __ballot_sync(0xffffffffu, act);
-            const int nact = __popc(mask);
-            if (nact == 0) continue;
-            int lg = 0;
-            while ((1 << lg) < nact) ++lg;
-            const int ntp = 1 << lg, slices = 32 >> lg;
-            const int j = lane & (ntp - 1), ksl = lane >> lg;
-            const bool valid = j < nact;
-            // lane holding the j-th active target
-            int src_lane = 0;
-            for (int b = 0, r = 0; b < 32; ++b)
-                if ((mask >> b) & 1u) {
-                    if (r == j) src_lane = b;
-                    ++r;
-                }
-            const float tx = __shfl_sync(0xffffffffu, T.x, src_lane);
-            const float ty = __shfl_sync(0xffffffffu, T.y, src_lane);
-            const float tz = __shfl_sync(0xffffffffu, T.z, src_lane);
-            const uint32_t tw = __shfl_sync(0xffffffffu, twl, src_lane);
-            const int32_t t = tf + tb + src_lane;
-            const bool inh = pk_type(tw) != 0;
-            const float hx = (tx - cx) * sqk, hy = (ty - cy) * sqk, hz = (tz - cz) * sqk;
-            const float h2x = fast ? 2.f * hx : hx, h2y = fast ? 2.f * hy : hy,
-                        h2z = fast ? 2.f * hz : hz;
-            const float scale = fast ? ex2_approx(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
-            const float fa = valid ? (float)pk_axon(tw) * scale : 0.f;
-            const float4* src = inh ? sI : sE;
-            float acc = 0.f;
-            for (int32_t ib = i0; ib < i1; ib += 32) {
-                // metadata of up to 32 partner pairs, one per lane
-                int32_t mq = 0, msf = 0, msc = 0;
-                if (ib + lane < i1) {
-                    mq = list_q[ib + lane];
-                    int32_t Y = pY[mq];
-                    msf = nfirst[Y];
-                    msc = ncount[Y];
-                }
-                const int nb = min(32, i1 - ib);
-                for (int r = 0; r < nb; ++r) {
-                    const int32_t q = __shfl_sync(0xffffffffu, mq, r);
-                    const int32_t sf = __shfl_sync(0xffffffffu, msf, r);
-                    const int32_t sc = __shfl_sync(0xffffffffu, msc, r);
-                    const bool self = sf == tf;
-                    float part = 0.f;
-                    for (int32_t sb = 0; sb < sc; sb += kP2PStage) {
-                        const int m = min(kP2PStage, sc - sb);
-                        __syncwarp();
-                        for (int e = lane; e < m; e += 32) {
-                            float4 S = pts[sf + sb + e];
-                            float2 L = lw[sf + sb + e];
-                            float sx = (S.x - cx) * sqk, sy = (S.y - cy) * sqk,
-                                  sz = (S.z - cz) * sqk;
-                            float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
-                            sE[e] = make_float4(sx, sy, sz, n2 + L.x);
-                            sI[e] = make_float4(sx, sy, sz, n2 + L.y);
-                        }
-                        __syncwarp();
-                        if (fast && !self) {
-                            for (int e = ksl; e < m; e += slices) {
-                                float4 S = src[e];
-                                part += ex2_approx(fmaf(h2x, S.x, fmaf(h2y, S.y, fmaf(h2z, S.z, S.w))));
-                            }
-                        } else if (fast) {
-                            for (int e = ksl; e < m; e += slices) {
-                                float4 S = src[e];
-                                float arg = fmaf(h2x, S.x, fmaf(h2y, S.y, fmaf(h2z, S.z, S.w)));
-                                part += sf + sb + e == t ? 0.f : ex2_approx(arg);
-                            }
-                        } else {
-                            // boxes wider than ~2 sigma: the expanded form would
-                            // overflow, use the difference form
-                            for (int e = ksl; e < m; e += slices) {
-                                float4 S = src[e];
-                                float dx = h2x - S.x, dy = h2y - S.y, dz = h2z - S.z;
-                                float arg = S.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                part += sf + sb + e == t ? 0.f : ex2_approx(arg);
-                            }
-                        }
-                    }
-                    acc += part;
-                    float v = fa * part;
-                    float vE = inh ? 0.f : v, vI = inh ? v : 0.f;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        vE += __shfl_xor_sync(0xffffffffu, vE, o);
-                        vI += __shfl_xor_sync(0xffffffffu, vI, o);
-                    }
-                    if (lane == 0) {
-                        double2 cur = pw[q];
-                        pw[q] = make_double2(cur.x + (double)vE, cur.y + (double)vI);
-                    }
-                    evals += (unsigned long long)sc * (unsigned long long)nact;
-                }
-            }
-            // sum the slices of each target
-            for (int o = ntp; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (valid && ksl == 0) u[t] += acc * scale;
-        }
-        if (lane == 0) atomicAdd(work, evals);
-    }
-}
-
 // a10: attraction of a split pair = sum over its child block (double)
 __global__ void k_reduce_pairs(int64_t q0, int64_t nq, NodeView nv,
                                const uint8_t* __restrict__ kind, const int32_t* __restrict__ pX,
@@ -570,20 +418,28 @@ k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ w
             sp[threadIdx.x] = s < n ? pts[s] : make_float4(3e30f, 3e30f, 3e30f, 0.f);
             sw[threadIdx.x] = s < n ? wts[s] : make_float2(0.f, 0.f);
             __syncthreads();
+            if (sb != tb) {
 #pragma unroll 8
-            for (int j = 0; j < kDirThreads; ++j) {
-                float4 S = sp[j];
-                float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float e = ex2_approx(-r2 * k2);
-                acc = fmaf(inh ? sw[j].y : sw[j].x, e, acc);
+                for (int j = 0; j < kDirThreads; ++j) {
+                    float4 S = sp[j];
+                    float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float e = ex2_approx(-r2 * k2);
+                    acc = fmaf(inh ? sw[j].y : sw[j].x, e, acc);
+                }
+            } else {
+                // the tile holding the targets themselves: skip j == t
+                for (int j = 0; j < kDirThreads; ++j) {
+                    float4 S = sp[j];
+                    float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float e = ex2_approx(-r2 * k2);
+                    float wj = j == (int)threadIdx.x ? 0.f : (inh ? sw[j].y : sw[j].x);
+                    acc = fmaf(wj, e, acc);
+                }
             }
         }
-        if (active) {
-            float2 self = wts[t];
-            acc -= inh ? self.y : self.x;       // the j == t term contributed w_t * 2^0
-            u[t] = pk_axon(tw) > 0 ? acc : 0.f;
-        }
+        if (active) u[t] = pk_axon(tw) > 0 ? acc : 0.f;
     }
 }
 
@@ -741,15 +597,11 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
         MSP_LAUNCH("l2p");
     }
     if (nseg > 0) {
-        int g = grid_for(nseg, kP2PWarps, (int64_t)c.sm_count * 64);
-        const float sqk = (float)std::sqrt(1.4426950408889634 / (cfg.sigma * cfg.sigma));
-        k_p2p<<<g, kP2PWarps * 32, 0, s>>>(
-            seg_first, nseg, pv0, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
-            c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
-            c.nd_count.get<int32_t>(), c.pts.get<float4>(), c.lw.get<float2>(), sqk,
-            cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, us, c.pr_w.get<double2>(), work);
-        MSP_LAUNCH("p2p");
+        MSP_CUDA(cudaEventRecord(c.ev_nf0, s));
+        launch_near_field(c, seg_first, nseg, pv0, c.n_p2p, us, work, s);
+        MSP_CUDA(cudaEventRecord(c.ev_nf1, s));
     }
+    c.nf_timed = nseg > 0;
     // a10: pair table, deepest pairs first
     for (int dd = n_depths - 1; dd >= 0; --dd) {
         int64_t q0 = c.depth_start[dd], nq = c.depth_start[dd + 1] - q0;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -17,6 +18,9 @@ constexpr int kMortonBits = 21;
 constexpr int kMaxP = 8;
 constexpr uint32_t kTagDescend = 1u, kTagLeaf = 2u, kTagAccept = 3u, kTagWalk = 4u;
 enum PairKind : uint8_t { kSplit = 0, kFar = 1, kP2P = 2, kPruned = 3 };
+// A draw whose total attraction is at or below this has no candidate; every
+// attraction inside the cutoff radius is many orders of magnitude larger.
+constexpr double kMinAttraction = 1e-30;
 
 // ---------------------------------------------------------------------------
 // errors: internal code throws; every C entry point converts to msp_status
@@ -31,8 +35,12 @@ inline void cuda_check(cudaError_t e, const char* what) {
     msp_status c = (e == cudaErrorMemoryAllocation) ? MSP_ERR_OOM : MSP_ERR_CUDA;
     throw Error(c, std::string(what) + ": " + cudaGetErrorString(e));
 }
+// kernels launched by the library (process-wide), counted at each launch check
+extern std::atomic<long long> g_kernel_launches;
 #define MSP_CUDA(x) ::msp::cuda_check((x), #x)
-#define MSP_LAUNCH(what) ::msp::cuda_check(cudaGetLastError(), what)
+#define MSP_LAUNCH(what) \
+    (::msp::g_kernel_launches.fetch_add(1, std::memory_order_relaxed), \
+     ::msp::cuda_check(cudaGetLastError(), what))
 
 // grow-only device buffer
 struct DBuf {
@@ -115,7 +123,7 @@ struct msp_ctx {
     // dual traversal
     msp::DBuf pr_X, pr_Y, pr_kind, pr_cf, pr_w;
     // lists
-    msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag;
+    msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
     // expansions
     msp::DBuf expA, expM, expB;
     msp::DBuf u_sorted;
@@ -124,6 +132,8 @@ struct msp_ctx {
     // generic scratch
     msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist;
     int64_t* small_host = nullptr;     // pinned, for count readbacks
+    cudaEvent_t ev_nf0 = nullptr, ev_nf1 = nullptr;   // around the near-field kernel
+    bool nf_timed = false;
     // per-neuron inputs of the last build in caller order (context-owned
     // copies; the selection reads them again)
     msp::DBuf c_type, c_va, c_vde, c_vdi;
@@ -146,6 +156,11 @@ int64_t scan_exclusive(msp_ctx& c, const int32_t* in, int32_t* out, int64_t n, c
 // result ends in (keys, vals); (keys_tmp, vals_tmp) are scratch of n entries.
 void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                 int32_t* vals_tmp, int64_t n, int bits, cudaStream_t s);
+// Step a9, the near field over the leaf pairs grouped by target leaf
+// (msp_nearfield.cu); accumulates into u_sorted and the pair table.
+void launch_near_field(msp_ctx& c, const int32_t* seg_first, int64_t nseg, const int32_t* list_q,
+                       int64_t n_list, float* u_sorted, unsigned long long* work,
+                       cudaStream_t s);
 // Read an int64 from device memory (synchronous).
 int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s);
 

@@ -89,7 +89,8 @@ __device__ float warp_far_w(const Tree& tr, const Exps& ex, int32_t X, int32_t Y
 }
 
 // Algorithm 2's last steps: negative candidates (truncation) count as zero;
-// -1 when the total is zero; upper_bound over the inclusive prefix sums, and
+// -1 when the total is at most kMinAttraction; upper_bound over the inclusive
+// prefix sums, and
 // the last positive candidate when rounding puts r at the total.
 __device__ inline int draw_index(const double* w, int k, double U) {
     double pre[8];
@@ -98,7 +99,7 @@ __device__ inline int draw_index(const double* w, int k, double U) {
         tot += w[i] > 0.0 ? w[i] : 0.0;
         pre[i] = tot;
     }
-    if (!(tot > 0.0)) return -1;
+    if (!(tot > kMinAttraction)) return -1;
     double r = U * tot;
     for (int i = 0; i < k; ++i)
         if (pre[i] > r) return i;
@@ -145,7 +146,7 @@ k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
                 int4 sm = tr.sums[xc];
                 int sa = ch ? sm.y : sm.x;
                 bool keep = sa > 0;
-                if (keep && split) keep = (ch ? pw[cf + lane].y : pw[cf + lane].x) > 0.0;
+                if (keep && split) keep = (ch ? pw[cf + lane].y : pw[cf + lane].x) > kMinAttraction;
                 if (keep) {
                     unsigned long long slot = atomicAdd(&counters[0], 1ull);
                     Item nx_it = {xc, Y, split ? cf + lane : -1, ch};
@@ -198,7 +199,7 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                             const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
                             const float4* __restrict__ pts, const float2* __restrict__ wts,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
-                            float k2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
+                            float k2, float rc2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
                             unsigned long long* __restrict__ counters) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -222,32 +223,61 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                 float4 S = pts[s];
                 float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ws = (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2);
+                float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
                 tot += (double)ws;
             }
             const int32_t to = perm[t];
-            if (!(tot > 0.0)) continue;
-            for (int e = 0; e < a; ++e) {
-                uint32_t c1 = (uint32_t)e | ((uint32_t)ch << 8) | (kTagLeaf << 16);
-                double r = philox_uniform(seed, (uint32_t)to, c1, step) * tot;
+            if (!(tot > kMinAttraction)) continue;
+            // the element draws r_e = U_e * tot, in groups of up to 8 sorted
+            // thresholds; one prefix walk over the leaf serves a whole group
+            constexpr int kGroup = 8;
+            for (int e0 = 0; e0 < a; e0 += kGroup) {
+                const int ng = min(kGroup, a - e0);
+                double r[kGroup];
+                int ord[kGroup];
+                for (int e = 0; e < ng; ++e) {
+                    uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
+                    double v = philox_uniform(seed, (uint32_t)to, c1, step) * tot;
+                    int j = e;
+                    while (j > 0 && r[j - 1] > v) {
+                        r[j] = r[j - 1];
+                        ord[j] = ord[j - 1];
+                        --j;
+                    }
+                    r[j] = v;
+                    ord[j] = e;
+                }
+                int32_t pick[kGroup];
+                for (int e = 0; e < ng; ++e) pick[e] = -1;
                 double pre = 0.0;
-                int32_t pick = -1, last_pos = -1;
-                for (int32_t s = sf; s < sf + sc; ++s) {
+                int32_t last_pos = -1;
+                int next = 0;
+                for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
                     if (s == t) continue;
                     float4 S = pts[s];
                     float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float ws = (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2);
+                    float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
                     pre += (double)ws;
                     if (ws > 0.f) last_pos = s;
-                    if (pre > r) {
-                        pick = s;
-                        break;
-                    }
+                    while (next < ng && pre > r[next]) pick[ord[next++]] = s;
                 }
-                if (pick < 0) pick = last_pos;
-                partner[eoff[to] + e] = pick >= 0 ? perm[pick] : -1;
-                ++draws;
+                if (next < ng) {
+                    // rounding left r at the total: the last source with weight
+                    for (int32_t s = sf + sc - 1; s >= sf && last_pos < 0; --s) {
+                        if (s == t) continue;
+                        float4 S = pts[s];
+                        float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 < rc2 && (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) > 0.f)
+                            last_pos = s;
+                    }
+                    while (next < ng) pick[ord[next++]] = last_pos;
+                }
+                for (int e = 0; e < ng; ++e) {
+                    partner[eoff[to] + e0 + e] = pick[e] >= 0 ? perm[pick[e]] : -1;
+                    ++draws;
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
@@ -392,6 +422,8 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     const int64_t n = c.n, ne = c.n_elem;
     const int B = 256;
     const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
+    // inside a leaf the kernel is truncated at the radius that prunes box pairs
+    const float rc2 = (float)((cfg.cutoff * cfg.sigma) * (cfg.cutoff * cfg.sigma));
     c.n_draws = c.n_requests = c.n_synapses = 0;
     if (ne == 0) {
         MSP_CUDA(cudaMemsetAsync(n_syn, 0, sizeof(int64_t), s));
@@ -430,8 +462,8 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     MSP_CUDA(cudaMemcpyAsync(&root_w, c.pr_w.get<double2>(), sizeof(double2), cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaStreamSynchronize(s));
     std::vector<Item> init;
-    if (root_sums.x > 0 && root_w.x > 0.0) init.push_back(Item{0, 0, 0, 0});
-    if (root_sums.y > 0 && root_w.y > 0.0) init.push_back(Item{0, 0, 0, 1});
+    if (root_sums.x > 0 && root_w.x > kMinAttraction) init.push_back(Item{0, 0, 0, 0});
+    if (root_sums.y > 0 && root_w.y > kMinAttraction) init.push_back(Item{0, 0, 0, 1});
     int64_t n_in = (int64_t)init.size();
     if (n_in) MSP_CUDA(cudaMemcpyAsync(it0, init.data(), n_in * sizeof(Item), cudaMemcpyHostToDevice, s));
     MSP_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
@@ -459,7 +491,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         k_leaf_draw<<<g, 256, 0, s>>>(lit, n_leaf, c.nd_first.get<int32_t>(),
                                       c.nd_count.get<int32_t>(), c.pts.get<float4>(),
                                       c.wts.get<float2>(), c.perm.get<int32_t>(),
-                                      c.elem_off.get<int32_t>(), k2, cfg.seed, step, partner, ctr);
+                                      c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, step, partner, ctr);
         MSP_LAUNCH("leaf_draw");
     }
 

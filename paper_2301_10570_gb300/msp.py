@@ -49,7 +49,8 @@ class Stats(C.Structure):
                 ("pair_depths", C.c_int32), ("n_far", C.c_int64), ("n_p2p", C.c_int64),
                 ("p2p_interactions", C.c_int64), ("n_elements", C.c_int64),
                 ("n_draws", C.c_int64), ("n_requests", C.c_int64), ("n_synapses", C.c_int64),
-                ("expansion_nodes", C.c_int64)]
+                ("expansion_nodes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("near_field_ms", C.c_double)]
 
 
 def load(path: str = LIB_PATH):
@@ -220,7 +221,8 @@ class MSP:
     def stats(self) -> dict:
         s = Stats()
         _check(load().msp_get_stats(self._h, C.byref(s)))
-        return {name: int(getattr(s, name)) for name, _ in Stats._fields_}
+        return {name: (float if name.endswith("_ms") else int)(getattr(s, name))
+                for name, _ in Stats._fields_}
 
     def export_tree(self):
         st = self.stats()
