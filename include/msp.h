@@ -229,6 +229,35 @@ msp_status msp_export_expansions(msp_ctx *ctx, float *A, float *M, float *B,
 /* Message of the last error of the calling thread ("" if none). */
 const char *msp_last_error(void);
 
+/* Largest n accepted by msp_direct_noalloc (the size of its fixed scratch). */
+#define MSP_NOALLOC_MAX_N 65536
+
+/* The all-pairs attraction of msp_direct for callers that cannot allocate
+ * device memory: a simulation loop that must never block on cudaMalloc (which
+ * can synchronise the device), or a host framework that owns all device
+ * memory and forbids libraries to allocate.  The paper has no counterpart;
+ * this is a service of this library.
+ *   n                    number of neurons, 0..MSP_NOALLOC_MAX_N; larger n is
+ *                        rejected with MSP_ERR_INVALID_ARG and nothing runs
+ *   x,y,z,type,vac_*     device inputs as for msp_build_tree (caller order)
+ *   sigma                kernel width
+ *   u                    device output, n floats: u(t) of the neuron's own
+ *                        channel if vac_axon > 0, else 0
+ *   stream               cudaStream_t as void* (NULL = legacy default stream)
+ * It allocates nothing and needs no context.  Its scratch is one fixed
+ * file-scope device array of MSP_NOALLOC_MAX_N * 24 bytes that every GPU
+ * loading this library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call rewrites
+ * the part it reads before reading it), so calls whose work overlaps on the
+ * same GPU (for example on two streams) race on it: the caller must
+ * serialise them.  Asynchronous on `stream`. */
+msp_status msp_direct_noalloc(int64_t n, const float *x, const float *y, const float *z,
+                              const uint8_t *type, const uint8_t *vac_axon,
+                              const uint8_t *vac_dend_e, const uint8_t *vac_dend_i,
+                              double sigma, float *u, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

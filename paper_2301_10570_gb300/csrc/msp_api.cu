@@ -22,13 +22,16 @@ void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const i
                      uint8_t* vdi, cudaStream_t s);
 }  // namespace msp
 
+namespace {
+thread_local std::string g_last_error;
+}
+
 namespace msp {
 std::atomic<long long> g_kernel_launches{0};
+void set_last_error(const char* msg) { g_last_error = msg; }
 }
 
 namespace {
-
-thread_local std::string g_last_error;
 
 msp_status fail(msp_status code, const std::string& msg) {
     g_last_error = msg;

@@ -27,7 +27,8 @@ STATUS = {0: "MSP_OK", 1: "MSP_ERR_INVALID_ARG", 2: "MSP_ERR_CUDA", 3: "MSP_ERR_
 EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "msp_direct",
             "msp_select_partners", "msp_plasticity_step_host", "msp_vacancy_walk",
             "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
-            "msp_export_expansions", "msp_last_error")
+            "msp_export_expansions", "msp_last_error", "msp_direct_noalloc")
+NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
 
 class MSPError(RuntimeError):
@@ -78,6 +79,8 @@ def load(path: str = LIB_PATH):
         L.msp_export_pairs.argtypes = [vp] * 8
         L.msp_export_expansions.argtypes = [vp] * 5
         L.msp_last_error.restype = C.c_char_p
+        L.msp_direct_noalloc.argtypes = [i64] + [vp] * 7 + [C.c_double, vp, vp]
+        L.msp_direct_noalloc.restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
                      "msp_vacancy_walk", "msp_commit_synapses", "msp_get_stats",
@@ -259,6 +262,19 @@ class MSP:
         first = np.zeros(1, np.int64)
         _check(load().msp_export_expansions(self._h, _np(A), _np(M), _np(B), _np(first)))
         return A[:m], M[:m], B[:m], int(first[0])
+
+
+def direct_noalloc(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, out=None, stream=None):
+    """msp_direct_noalloc: all-pairs attraction without any device allocation
+    by the library, for callers that cannot allocate (n <= NOALLOC_MAX_N).
+    `out` (n float32, CUDA) may be preallocated by the caller."""
+    n = int(pos.shape[1])
+    xs = [pos[d].contiguous() for d in range(3)]
+    u = out if out is not None else torch.empty(n, dtype=torch.float32, device=pos.device)
+    _check(load().msp_direct_noalloc(n, *[_ptr(t) for t in xs], _ptr(type_), _ptr(vac_axon),
+                                     _ptr(vac_dend_e), _ptr(vac_dend_i), float(sigma), _ptr(u),
+                                     _stream(stream)))
+    return u
 
 
 def to_device(w, device="cuda"):
