@@ -4,6 +4,8 @@
 // dendrite neuron inside the chosen leaf, and the resolution of the requests
 // at the dendrite side (Section 4).  Also the vacancy random walk and the
 // consumption of formed synapses.
+#include <algorithm>
+
 #include "msp_internal.cuh"
 
 namespace msp {
@@ -201,15 +203,16 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
                             float k2, float rc2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
                             unsigned long long* __restrict__ counters) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = wid; k < n_items; k += nw) {
+    // one block of kLeafWarps warps per leaf item; the warps take interleaved
+    // chunks of 32 targets of the axon leaf
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int64_t k = blockIdx.x; k < n_items; k += gridDim.x) {
         Item it = items[k];
         const int32_t tf = nfirst[it.X], tc = ncount[it.X];
         const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
         unsigned long long draws = 0;
-        for (int32_t tb = 0; tb < tc; tb += 32) {
+        for (int32_t tb = 32 * w; tb < tc; tb += 32 * nwarps) {
             int32_t t = tf + tb + lane;
             if (tb + lane >= tc) continue;
             float4 T = pts[t];
@@ -217,15 +220,21 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
             int ch = pk_type(tw) ? 1 : 0;
             int a = (int)pk_axon(tw);
             if (ch != it.ch || a == 0) continue;
-            double tot = 0.0;
+            // the total in single precision with compensated summation; the
+            // walk below accumulates the prefix in double precision
+            float tsum = 0.f, tcomp = 0.f;
             for (int32_t s = sf; s < sf + sc; ++s) {
                 if (s == t) continue;
                 float4 S = pts[s];
                 float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                tot += (double)ws;
+                float yv = ws - tcomp;
+                float tv = tsum + yv;
+                tcomp = (tv - tsum) - yv;
+                tsum = tv;
             }
+            const double tot = (double)tsum - (double)tcomp;
             const int32_t to = perm[t];
             if (!(tot > kMinAttraction)) continue;
             // the element draws r_e = U_e * tot, in groups of up to 8 sorted
@@ -252,6 +261,7 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                 double pre = 0.0;
                 int32_t last_pos = -1;
                 int next = 0;
+                double rn = r[0];            // the smallest threshold not yet crossed
                 for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
                     if (s == t) continue;
                     float4 S = pts[s];
@@ -260,7 +270,12 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                     float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
                     pre += (double)ws;
                     if (ws > 0.f) last_pos = s;
-                    while (next < ng && pre > r[next]) pick[ord[next++]] = s;
+                    if (pre > rn) {
+                        do {
+                            pick[ord[next++]] = s;
+                            rn = next < ng ? r[next] : 0.0;
+                        } while (next < ng && pre > rn);
+                    }
                 }
                 if (next < ng) {
                     // rounding left r at the total: the last source with weight
@@ -487,8 +502,8 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     int64_t n_leaf = c.small_host[1];
     c.n_draws = c.small_host[2];
     if (n_leaf > 0) {
-        int g = grid_for(n_leaf * 32, 256, (int64_t)c.sm_count * 32);
-        k_leaf_draw<<<g, 256, 0, s>>>(lit, n_leaf, c.nd_first.get<int32_t>(),
+        int g = (int)std::min<int64_t>(n_leaf, 1 << 30);
+        k_leaf_draw<<<g, 128, 0, s>>>(lit, n_leaf, c.nd_first.get<int32_t>(),
                                       c.nd_count.get<int32_t>(), c.pts.get<float4>(),
                                       c.wts.get<float2>(), c.perm.get<int32_t>(),
                                       c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, step, partner, ctr);
