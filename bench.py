@@ -58,6 +58,29 @@ def workload():
     return W.clustered_1m(**tuned_params())
 
 
+def near_field_traffic():
+    """DRAM bytes of one near-field launch on this workload, from the ncu
+    capture summarised in profiles/ (null once the kernel source changed)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "near_field_traffic_clustered_1m.md")
+    src = os.path.join(ROOT, "paper_2301_10570_gb300", "csrc", "msp_nearfield.cu")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.split(":")[0].strip() in ("dram_bytes_per_launch",
+                                                                    "kernel_source_sha256"):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if fields.get("kernel_source_sha256") != sha:
+            return None
+        return int(float(fields["dram_bytes_per_launch"]))
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -232,7 +255,7 @@ def run_ours(args, rank, world):
     achieved = statistics.mean(inter) / (nf / 1e3) / 1e9 if nf > 0 else 0.0
     roofline = {"kernel": "k_p2p (near field)", "bound": "alu", "achieved": round(achieved, 1),
                 "peak": round(peak_gex2, 1), "unit": "Gex2/s", "frac": round(achieved / peak_gex2, 4),
-                "traffic": None, "near_field_ms": round(nf, 3),
+                "traffic": near_field_traffic(), "near_field_ms": round(nf, 3),
                 "near_field_share_of_step": round(nf / ms, 3),
                 "interactions_per_step": int(statistics.mean(inter)),
                 "peak_basis": f"{SM_COUNT} SMs x {EX2_PER_SM_CLK} ex2/clk x {sm_max:.0f} MHz"}

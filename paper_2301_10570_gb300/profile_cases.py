@@ -1,0 +1,58 @@
+"""Small, named workloads for profiling the CUDA path under ncu.
+
+    python -m paper_2301_10570_gb300.profile_cases near_field_131k
+    python -m paper_2301_10570_gb300.profile_cases step_1m --steps 2
+
+Each case builds the library, runs a few plasticity steps (tree, attraction,
+selection) and prints the library's statistics; it exits non-zero on any
+error.  The cases are sized for the profiling rules of the pool: the full
+capture case holds well under 1 GB on the device.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+
+def _plan():
+    # the benchmark's plan (leaf capacity, cutoff, no translations)
+    return dict(leaf_capacity=128, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+
+
+def near_field_131k():
+    from . import workloads as W
+    return W.clustered(8, 16_384, 100_000.0 * (8 / 64) ** (1 / 3), 1500.0, 4500.0, seed=3,
+                       name="clustered_131k", **_plan())
+
+
+def step_1m():
+    from . import workloads as W
+    return W.clustered_1m(**_plan())
+
+
+CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=sorted(CASES))
+    ap.add_argument("--steps", type=int, default=2)
+    args = ap.parse_args(argv)
+    import torch
+
+    from . import build, msp
+    build.build()
+    w = CASES[args.case]()
+    g = msp.MSP(w.params)
+    dev = msp.to_device(w)
+    for k in range(args.steps):
+        g.build_tree(*dev)
+        g.attraction()
+        g.select_partners(k)
+    torch.cuda.synchronize()
+    print(args.case, g.stats())
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
