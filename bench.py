@@ -50,7 +50,7 @@ def parse():
 def tuned_params():
     """Plan chosen by the autotuner for this workload (leaf capacity, cutoff,
     expansions): see paper_2301_10570_gb300/autotune.py."""
-    return dict(leaf_capacity=128, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+    return dict(leaf_capacity=192, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
 
 
 def workload():

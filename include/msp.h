@@ -69,7 +69,10 @@ typedef enum {
  *   rho_max        an expansion is used only for boxes whose half-width is at
  *                  most rho_max*sigma
  *   cutoff         box pairs whose minimum distance is at least cutoff*sigma
- *                  contribute nothing (their kernel is below exp(-cutoff^2))
+ *                  contribute nothing (their kernel is below exp(-cutoff^2)),
+ *                  and inside a chosen leaf sources beyond cutoff*sigma have
+ *                  weight zero; 0 < cutoff <= 5 (exp(-25) ~ 1e-11 is below
+ *                  single precision relative resolution of any sum)
  *   m2l_min_pairs  a well-separated pair is translated only if
  *                  count(X)*count(Y) >= m2l_min_pairs; otherwise it is
  *                  refined down to the near field                          */

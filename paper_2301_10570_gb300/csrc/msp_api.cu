@@ -92,7 +92,8 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
     *out = nullptr;
     if (!(cfg->sigma > 0.0) || cfg->p < 1 || cfg->p > msp::kMaxP || cfg->leaf_capacity < 1 ||
         cfg->max_depth < 0 || cfg->max_depth > msp::kMortonBits || !(cfg->side > 0.0f) ||
-        !(cfg->rho_max >= 0.0) || !(cfg->cutoff > 0.0) || cfg->m2l_min_pairs < 0 ||
+        !(cfg->rho_max >= 0.0) || !(cfg->cutoff > 0.0) || !(cfg->cutoff <= 5.0) ||
+        cfg->m2l_min_pairs < 0 ||
         !std::isfinite(cfg->origin[0]) || !std::isfinite(cfg->origin[1]) ||
         !std::isfinite(cfg->origin[2]) || !std::isfinite(cfg->side))
         return fail(MSP_ERR_INVALID_ARG, "configuration value out of range");

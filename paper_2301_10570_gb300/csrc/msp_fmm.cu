@@ -370,19 +370,30 @@ __global__ void k_reduce_pairs(int64_t q0, int64_t nq, NodeView nv,
                                const uint8_t* __restrict__ kind, const int32_t* __restrict__ pX,
                                const int32_t* __restrict__ pY, const int32_t* __restrict__ pcf,
                                double2* __restrict__ pw) {
+    // four interleaved partial sums (children c = j mod 4), combined in a fixed
+    // order: deterministic, and four independent add chains
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t q = q0 + k;
+        const int64_t q = q0 + k;
         if (kind[q] != kSplit) continue;
-        int nb = block_size(nv, pX[q], pY[q]);
-        int32_t cf = pcf[q];
-        double e = 0.0, i = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            double2 v = pw[cf + j];
-            e += v.x;
-            i += v.y;
+        const int nb = block_size(nv, pX[q], pY[q]);
+        const int32_t cf = pcf[q];
+        double e[4] = {0.0, 0.0, 0.0, 0.0}, i[4] = {0.0, 0.0, 0.0, 0.0};
+        int c = 0;
+        for (; c + 3 < nb; c += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                double2 v = pw[cf + c + u];
+                e[u] += v.x;
+                i[u] += v.y;
+            }
         }
-        pw[q] = make_double2(e, i);
+        for (; c < nb; ++c) {
+            double2 v = pw[cf + c];
+            e[c & 3] += v.x;
+            i[c & 3] += v.y;
+        }
+        pw[q] = make_double2((e[0] + e[1]) + (e[2] + e[3]), (i[0] + i[1]) + (i[2] + i[3]));
     }
 }
 

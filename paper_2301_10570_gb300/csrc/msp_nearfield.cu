@@ -3,15 +3,17 @@
 //
 // Work unit: one target leaf X (one block of 4 warps) and all its partner
 // leaves Y (a contiguous segment of the pair list sorted by X).  The block
-// first collects the targets of X with vacant axons (up to 128 per pass); the
+// first collects the targets of X with vacant axons (up to 64 per pass); the
 // warps then take the partner pairs round-robin.  Each warp stages the sources
 // of its current pair in its own shared memory and every lane evaluates them
 // against its targets:
 //   up to 32 targets: padded to T = 2^k, 32/T lanes per target walking
 //                     interleaved slices of the sources (small leaves still
 //                     fill the warp);
-//   33..128 targets:  R = 2 or 4 targets per lane, every lane walks all
-//                     sources (each staged source is used R times).
+//   33..64 targets:   2 targets per lane, every lane walks all sources (each
+//                     staged source is used twice).
+// Capping a pass at 64 targets keeps the kernel at 64 registers (8 blocks of
+// 4 warps per SM); larger leaves take several passes.
 // The per-target sums of the 4 warps are added in a fixed order, so u is
 // reproducible run to run.  Per pair, the warp reduces the box-pair
 // attraction W(X,Y) = sum_t a_t sum_s w_s K(t,s) of each channel in single
@@ -34,9 +36,14 @@ namespace msp {
 
 namespace {
 
+// the block's transposed per-pair W buffer (16 pairs x 32 lanes per warp, one
+// padding column), set by the kernel before use
+__shared__ float2* s_wt;
+__shared__ int32_t* s_wii;
+
 constexpr int kNFWarps = 4;
 constexpr int kNFStage = 64;
-constexpr int kNFMaxT = 32 * 4;
+constexpr int kNFMaxT = 32 * 2;    // targets per pass (at most 2 per lane: 64 registers)
 
 __device__ inline float nf_ex2(float x) {
     float y;
@@ -134,6 +141,8 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                                          int slices, const Tgt (&tg)[R], float (&acc)[R],
                                          float4* stw, unsigned long long& evals, int nt) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 (*wt)[33] = reinterpret_cast<float2 (*)[33]>(s_wt + w * 16 * 33);
+    int32_t* wii = s_wii + w * 16;
     for (int32_t cb = i0 + w; cb < i1; cb += 32 * kNFWarps) {
         // metadata of the warp's next 32 pairs, one per lane
         int32_t mi = cb + kNFWarps * lane, msf = 0, msc = 0;
@@ -177,14 +186,30 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 float v = tg[k].fa * part[k];
                 if (tg[k].ch) vI += v; else vE += v;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vE += __shfl_xor_sync(0xffffffffu, vE, o);
-                vI += __shfl_xor_sync(0xffffffffu, vI, o);
-            }
-            if (lane == 0) {
-                float2 cur = a.w32[ii];
-                a.w32[ii] = make_float2(cur.x + vE, cur.y + vI);
+            // W(X,Y) of each channel: every lane's term goes into a transposed
+            // buffer; every 16 pairs the warp sums the rows (half a row per
+            // lane, then one shuffle) and adds them to the pairs' slots
+            const int slot = r & 15;
+            wt[slot][lane] = make_float2(vE, vI);
+            if (lane == 0) wii[slot] = ii;
+            if (slot == 15 || r == nb - 1) {
+                __syncwarp();
+                const int row = lane & 15, half = lane >> 4;
+                float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll 4
+                for (int c = 0; c < 16; ++c) {
+                    float2 v2 = wt[row][half * 16 + c];
+                    s2.x += v2.x;
+                    s2.y += v2.y;
+                }
+                s2.x += __shfl_down_sync(0xffffffffu, s2.x, 16);
+                s2.y += __shfl_down_sync(0xffffffffu, s2.y, 16);
+                if (lane <= slot) {
+                    const int32_t pi = wii[lane];
+                    float2 cur = a.w32[pi];
+                    a.w32[pi] = make_float2(cur.x + s2.x, cur.y + s2.y);
+                }
+                __syncwarp();
             }
             evals += (unsigned long long)sc * (unsigned long long)nt;
         }
@@ -249,11 +274,15 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kNFWarps * 32, 6) k_near_field(NFArgs a) {
+__global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
     __shared__ float4 st[kNFWarps][2 * kNFStage];
     __shared__ float red[kNFWarps][kNFMaxT];
     __shared__ int32_t tl[kNFMaxT];
     __shared__ int s_nt, s_pos;
+    __shared__ float2 wt_all[kNFWarps][16][33];
+    __shared__ int32_t wii_all[kNFWarps][16];
+    s_wt = &wt_all[0][0][0];
+    s_wii = &wii_all[0][0];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stw = st[w];
     for (int64_t sg = blockIdx.x; sg < a.nseg; sg += gridDim.x) {
@@ -309,10 +338,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 6) k_near_field(NFArgs a) {
             if (nt == 0) break;
             if (nt <= 32)
                 nf_targets<1>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-            else if (nt <= 64)
-                nf_targets<2>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             else
-                nf_targets<4>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                nf_targets<2>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             if (pos >= tc) break;
         }
         if (lane == 0 && evals) atomicAdd(a.work, evals);

@@ -211,6 +211,10 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
         Item it = items[k];
         const int32_t tf = nfirst[it.X], tc = ncount[it.X];
         const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
+        // fixed-point scale: sc weights of at most 2^8 must stay below 2^63
+        int lg = 0;
+        while ((1 << lg) < sc + 1 && lg < 30) ++lg;
+        const int shift = min(40, 55 - lg);
         unsigned long long draws = 0;
         for (int32_t tb = 32 * w; tb < tc; tb += 32 * nwarps) {
             int32_t t = tf + tb + lane;
@@ -220,33 +224,37 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
             int ch = pk_type(tw) ? 1 : 0;
             int a = (int)pk_axon(tw);
             if (ch != it.ch || a == 0) continue;
-            // the total in single precision with compensated summation; the
-            // walk below accumulates the prefix in double precision
-            float tsum = 0.f, tcomp = 0.f;
+            // Prefix sums of the weights in exact 64-bit fixed point (scale
+            // 2^shift; a weight is at most 255): integer adds are exact and
+            // full rate, where double precision adds are scarce on this GPU.
+            // Weights below 2^-shift (far below exp(-cutoff^2) for the cutoffs
+            // the library accepts) count as zero.
+            uint64_t tot = 0;
             for (int32_t s = sf; s < sf + sc; ++s) {
                 if (s == t) continue;
                 float4 S = pts[s];
                 float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                float yv = ws - tcomp;
-                float tv = tsum + yv;
-                tcomp = (tv - tsum) - yv;
-                tsum = tv;
+                tot += __float2ull_rz(ldexpf(ws, shift));
             }
-            const double tot = (double)tsum - (double)tcomp;
             const int32_t to = perm[t];
-            if (!(tot > kMinAttraction)) continue;
-            // the element draws r_e = U_e * tot, in groups of up to 8 sorted
-            // thresholds; one prefix walk over the leaf serves a whole group
+            if (tot == 0) continue;
+            // the element draws r_e = floor(U_e * tot) (U_e with 53 bits), in
+            // groups of up to 8 sorted thresholds; one prefix walk over the
+            // leaf serves a whole group: the first source whose inclusive
+            // prefix exceeds r_e
             constexpr int kGroup = 8;
             for (int e0 = 0; e0 < a; e0 += kGroup) {
                 const int ng = min(kGroup, a - e0);
-                double r[kGroup];
+                uint64_t r[kGroup];
                 int ord[kGroup];
                 for (int e = 0; e < ng; ++e) {
                     uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
-                    double v = philox_uniform(seed, (uint32_t)to, c1, step) * tot;
+                    uint32_t o4[4];
+                    philox_draw(seed, (uint32_t)to, c1, step, o4);
+                    uint64_t u53 = (((uint64_t)o4[0] << 32) | o4[1]) >> 11;
+                    uint64_t v = __umul64hi(u53 << 11, tot);     // floor(u53 * tot / 2^53)
                     int j = e;
                     while (j > 0 && r[j - 1] > v) {
                         r[j] = r[j - 1];
@@ -257,40 +265,26 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
                     ord[j] = e;
                 }
                 int32_t pick[kGroup];
-                for (int e = 0; e < ng; ++e) pick[e] = -1;
-                double pre = 0.0;
-                int32_t last_pos = -1;
+                uint64_t pre = 0;
                 int next = 0;
-                double rn = r[0];            // the smallest threshold not yet crossed
+                uint64_t rn = r[0];          // the smallest threshold not yet crossed
                 for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
                     if (s == t) continue;
                     float4 S = pts[s];
                     float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                    pre += (double)ws;
-                    if (ws > 0.f) last_pos = s;
+                    pre += __float2ull_rz(ldexpf(ws, shift));
                     if (pre > rn) {
                         do {
                             pick[ord[next++]] = s;
-                            rn = next < ng ? r[next] : 0.0;
+                            rn = next < ng ? r[next] : 0;
                         } while (next < ng && pre > rn);
                     }
                 }
-                if (next < ng) {
-                    // rounding left r at the total: the last source with weight
-                    for (int32_t s = sf + sc - 1; s >= sf && last_pos < 0; --s) {
-                        if (s == t) continue;
-                        float4 S = pts[s];
-                        float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (r2 < rc2 && (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) > 0.f)
-                            last_pos = s;
-                    }
-                    while (next < ng) pick[ord[next++]] = last_pos;
-                }
+                // r < tot = the final prefix, so every threshold was crossed
                 for (int e = 0; e < ng; ++e) {
-                    partner[eoff[to] + e0 + e] = pick[e] >= 0 ? perm[pick[e]] : -1;
+                    partner[eoff[to] + e0 + e] = perm[pick[e]];
                     ++draws;
                 }
             }

@@ -83,63 +83,90 @@ __device__ inline int32_t octant_lower_bound(const uint64_t* __restrict__ keys, 
     return lo;
 }
 
+// Octant boundaries of the boxes of one level, 8 lanes per box (one binary
+// search per octant): lane o of a box's group returns the end of octant o and
+// the start of octant o (its neighbour's end, or the box start for o = 0).
+// Whole warps take part (4 boxes per warp per round).
+struct OctantSplit {
+    int64_t k;         // box index within the level (valid if < nl)
+    bool valid, split;
+    int32_t lo, end, start;
+};
+
+__device__ inline OctantSplit octant_split(int64_t base, int64_t l0, int64_t nl, int level,
+                                           int leaf_capacity, int max_depth,
+                                           const uint64_t* __restrict__ keys,
+                                           const int32_t* __restrict__ first,
+                                           const int32_t* __restrict__ count) {
+    const int lane = threadIdx.x & 31, o = lane & 7;
+    OctantSplit r;
+    r.k = base + (lane >> 3);
+    r.valid = r.k < nl;
+    r.split = false;
+    r.lo = 0;
+    int32_t e = 0;
+    if (r.valid) {
+        const int64_t i = l0 + r.k;
+        const int32_t c = count[i];
+        r.lo = first[i];
+        r.split = c > leaf_capacity && level < max_depth;
+        if (r.split)
+            e = octant_lower_bound(keys, r.lo, r.lo + c, 3 * (kMortonBits - (level + 1)),
+                                   (uint32_t)o + 1);
+    }
+    int32_t prev = __shfl_up_sync(0xffffffffu, e, 1);
+    r.end = e;
+    r.start = o == 0 ? r.lo : prev;
+    return r;
+}
+
 // number of non-empty octants of every box at this level that is split
 __global__ void k_count_children(int64_t l0, int64_t nl, int level, int leaf_capacity,
                                  int max_depth, const uint64_t* __restrict__ keys,
                                  const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                                  int32_t* __restrict__ cnt) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = l0 + k;
-        int32_t c = count[i];
-        int nch = 0;
-        if (c > leaf_capacity && level < max_depth) {
-            int shift = 3 * (kMortonBits - (level + 1));
-            int32_t lo = first[i], hi = first[i] + c;
-            int32_t b = lo;
-            for (uint32_t o = 0; o < 8; ++o) {
-                int32_t e = octant_lower_bound(keys, b, hi, shift, o + 1);
-                nch += (e > b);
-                b = e;
-            }
-        }
-        cnt[k] = nch;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = wid * 4; base < nl; base += nw * 4) {
+        OctantSplit r = octant_split(base, l0, nl, level, leaf_capacity, max_depth, keys, first, count);
+        const unsigned m = __ballot_sync(0xffffffffu, r.split && r.end > r.start);
+        if (r.valid && (lane & 7) == 0) cnt[r.k] = __popc((m >> (lane & ~7)) & 0xffu);
     }
 }
 
-__global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level,
-                                const uint64_t* __restrict__ keys, const int32_t* __restrict__ cnt,
+__global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level, int leaf_capacity,
+                                int max_depth, const uint64_t* __restrict__ keys,
                                 const int32_t* __restrict__ off, uint8_t* __restrict__ nd_level,
                                 uint64_t* __restrict__ nd_prefix, int32_t* __restrict__ nd_first,
                                 int32_t* __restrict__ nd_count, int32_t* __restrict__ nd_parent,
                                 int32_t* __restrict__ nd_child_first,
                                 uint8_t* __restrict__ nd_nchild) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = l0 + k;
-        int nch = cnt[k];
-        if (nch == 0) continue;
-        int64_t cf = next0 + off[k];
-        nd_child_first[i] = (int32_t)cf;
-        nd_nchild[i] = (uint8_t)nch;
-        int shift = 3 * (kMortonBits - (level + 1));
-        int32_t lo = nd_first[i], hi = nd_first[i] + nd_count[i];
-        uint64_t pre = nd_prefix[i];
-        int32_t b = lo;
-        int j = 0;
-        for (uint32_t o = 0; o < 8; ++o) {
-            int32_t e = octant_lower_bound(keys, b, hi, shift, o + 1);
-            if (e > b) {
-                int64_t ci = cf + j++;
-                nd_level[ci] = (uint8_t)(level + 1);
-                nd_prefix[ci] = (pre << 3) | o;
-                nd_first[ci] = b;
-                nd_count[ci] = e - b;
-                nd_parent[ci] = (int32_t)i;
-                nd_child_first[ci] = -1;
-                nd_nchild[ci] = 0;
-            }
-            b = e;
+    const int lane = threadIdx.x & 31, o = lane & 7;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = wid * 4; base < nl; base += nw * 4) {
+        OctantSplit r = octant_split(base, l0, nl, level, leaf_capacity, max_depth, keys, nd_first,
+                                     nd_count);
+        const bool ne = r.split && r.end > r.start;
+        const unsigned m = __ballot_sync(0xffffffffu, ne);
+        const unsigned grp = (m >> (lane & ~7)) & 0xffu;
+        if (!r.valid || grp == 0) continue;
+        const int64_t i = l0 + r.k;
+        const int64_t cf = next0 + off[r.k];
+        if (o == 0) {
+            nd_child_first[i] = (int32_t)cf;
+            nd_nchild[i] = (uint8_t)__popc(grp);
+        }
+        if (ne) {
+            const int64_t ci = cf + __popc(grp & ((1u << o) - 1u));
+            nd_level[ci] = (uint8_t)(level + 1);
+            nd_prefix[ci] = (nd_prefix[i] << 3) | (uint64_t)o;
+            nd_first[ci] = r.start;
+            nd_count[ci] = r.end - r.start;
+            nd_parent[ci] = (int32_t)i;
+            nd_child_first[ci] = -1;
+            nd_nchild[ci] = 0;
         }
     }
 }
@@ -273,7 +300,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         int64_t l0 = c.level_start[l], nl = c.level_start[l + 1] - l0;
         int32_t* cnt = c.cnt.ensure<int32_t>((size_t)nl);
         int32_t* off = c.off.ensure<int32_t>((size_t)nl);
-        k_count_children<<<grid_for(nl, B), B, 0, s>>>(l0, nl, l, cfg.leaf_capacity,
+        k_count_children<<<grid_for(8 * nl, B), B, 0, s>>>(l0, nl, l, cfg.leaf_capacity,
                                                        cfg.max_depth, k0,
                                                        c.nd_first.get<int32_t>(),
                                                        c.nd_count.get<int32_t>(), cnt);
@@ -282,8 +309,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         if (nnext == 0) break;
         if ((size_t)(total + nnext) > c.nd_first.bytes / sizeof(int32_t))
             grow_nodes((size_t)(total + nnext), (size_t)total);
-        k_emit_children<<<grid_for(nl, B), B, 0, s>>>(
-            l0, nl, total, l, k0, cnt, off, c.nd_level.get<uint8_t>(),
+        k_emit_children<<<grid_for(8 * nl, B), B, 0, s>>>(
+            l0, nl, total, l, cfg.leaf_capacity, cfg.max_depth, k0, off, c.nd_level.get<uint8_t>(),
             c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
             c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
             c.nd_nchild.get<uint8_t>());
