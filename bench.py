@@ -44,12 +44,20 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="rerun the plan chooser on this workload and bench its plan")
     return ap.parse_args()
+
+
+_PLAN_OVERRIDE = None
 
 
 def tuned_params():
     """Plan chosen by the autotuner for this workload (leaf capacity, cutoff,
-    expansions): see paper_2301_10570_gb300/autotune.py."""
+    expansions; `python bench.py --autotune` reruns it, see
+    paper_2301_10570_gb300/autotune.py and profiles/autotune_clustered_1m.md)."""
+    if _PLAN_OVERRIDE is not None:
+        return dict(_PLAN_OVERRIDE)
     return dict(leaf_capacity=192, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
 
 
@@ -365,6 +373,13 @@ def main():
         torch.cuda.set_device(0)
     from paper_2301_10570_gb300 import build as B
     B.build()
+    if args.autotune:
+        global _PLAN_OVERRIDE
+        from paper_2301_10570_gb300 import autotune
+        best, table = autotune.tune(workload(), device=torch.cuda.current_device())
+        for row in table:
+            print(json.dumps(row), file=sys.stderr)
+        _PLAN_OVERRIDE = best
     out, w, g, u = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy())

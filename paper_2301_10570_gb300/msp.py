@@ -7,9 +7,11 @@ load, constructing :class:`MSP` raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import threading
+import weakref
 
 import numpy as np
 import torch
@@ -124,6 +126,21 @@ def make_config(params: dict) -> Config:
     return c
 
 
+_live = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    """Destroy the contexts still alive at interpreter exit, while the CUDA
+    runtime is still up (registered after torch, so it runs before torch's
+    own exit handlers)."""
+    for ctx in list(_live):
+        try:
+            ctx.close()
+        except Exception:
+            pass
+
+
 class MSP:
     """One libmsp context on a CUDA device."""
 
@@ -137,9 +154,11 @@ class MSP:
         self._h = h
         self.n = 0
         self._inputs = None
+        _live.add(self)
 
     def close(self):
         if getattr(self, "_h", None):
+            torch.cuda.synchronize(self.device)
             load().msp_destroy(self._h)
             self._h = None
 
