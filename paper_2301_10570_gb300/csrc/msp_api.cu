@@ -110,6 +110,9 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
         MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->small_host), 16 * sizeof(int64_t)));
         MSP_CUDA(cudaEventCreate(&c->ev_nf0));
         MSP_CUDA(cudaEventCreate(&c->ev_nf1));
+        MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->hcount), sizeof(msp::DevCounts)));
+        std::memset(c->hcount, 0, sizeof(msp::DevCounts));
+        MSP_CUDA(cudaMemset(c->dcount.ensure<msp::DevCounts>(1), 0, sizeof(msp::DevCounts)));
         derive(*c);
     });
     if (st != MSP_OK) {
@@ -139,6 +142,9 @@ msp_status msp_destroy(msp_ctx* c) {
     for (msp::DBuf* b : bufs) b->release();
     for (auto& b : c->h_in) b.release();
     if (c->small_host) cudaFreeHost(c->small_host);
+    if (c->hcount) cudaFreeHost(c->hcount);
+    c->dcount.release();
+    c->sd_tmp.release();
     if (c->ev_nf0) cudaEventDestroy(c->ev_nf0);
     if (c->ev_nf1) cudaEventDestroy(c->ev_nf1);
     delete c;

@@ -69,9 +69,26 @@ __device__ inline int block_size(const NodeView& nv, int32_t X, int32_t Y) {
     return (lx ? 1 : nv.nchild[X]) * (ly ? 1 : nv.nchild[Y]);
 }
 
-__global__ void k_classify(int64_t q0, int64_t nq, NodeView nv, Geo geo,
+// the root pair (root, root) at depth 0
+__global__ void k_init_pairs(int64_t n, int32_t* pX, int32_t* pY, DevCounts* dc) {
+    dc->depth_start[0] = 0;
+    dc->depth_start[1] = n > 0 ? 1 : 0;
+    dc->overflow = 0;
+    dc->need_pairs = 0;
+    dc->interactions = 0;
+    if (n > 0) {
+        pX[0] = 0;
+        pY[0] = 0;
+    }
+}
+
+// pairs of one depth: [db[0], db[1]); their count goes to *scan_n
+__global__ void k_classify(const int64_t* __restrict__ db, NodeView nv, Geo geo,
                            const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
-                           uint8_t* __restrict__ kind, int32_t* __restrict__ cnt) {
+                           uint8_t* __restrict__ kind, int32_t* __restrict__ cnt,
+                           int64_t* __restrict__ scan_n) {
+    const int64_t q0 = db[0], nq = db[1] - db[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scan_n = nq;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = q0 + k;
@@ -82,11 +99,18 @@ __global__ void k_classify(int64_t q0, int64_t nq, NodeView nv, Geo geo,
     }
 }
 
-// children of a split pair, one contiguous block, axon-child major
-__global__ void k_emit_pairs(int64_t q0, int64_t nq, int64_t next0, NodeView nv,
+// Children of the split pairs of one depth, one contiguous block per pair,
+// axon-child major, from db[1] on.  When the children do not fit in the table
+// (overflow bit 0, set by the scan that also left the next depth empty) no
+// child is written and the traversal ends here; the caller grows the table
+// and redoes it.
+__global__ void k_emit_pairs(const int64_t* __restrict__ db, NodeView nv,
                              const uint8_t* __restrict__ kind, const int32_t* __restrict__ off,
                              int32_t* __restrict__ pX, int32_t* __restrict__ pY,
-                             int32_t* __restrict__ pcf, double2* __restrict__ pw) {
+                             int32_t* __restrict__ pcf, double2* __restrict__ pw, int64_t cap,
+                             const int64_t* __restrict__ overflow) {
+    const int64_t q0 = db[0], nq = db[1] - db[0], next0 = db[1];
+    const bool full = (*overflow & 1) != 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = q0 + k;
@@ -97,6 +121,10 @@ __global__ void k_emit_pairs(int64_t q0, int64_t nq, int64_t next0, NodeView nv,
         }
         int32_t X = pX[q], Y = pY[q];
         int64_t cf = next0 + off[k];
+        if (full || cf + block_size(nv, X, Y) > cap) {
+            pcf[q] = -1;
+            continue;
+        }
         pcf[q] = (int32_t)cf;
         int32_t cx = nv.child_first[X], cy = nv.child_first[Y];
         if (cx >= 0 && cy >= 0) {
@@ -122,16 +150,19 @@ __global__ void k_emit_pairs(int64_t q0, int64_t nq, int64_t next0, NodeView nv,
     }
 }
 
-__global__ void k_flag_kind(const uint8_t* __restrict__ kind, int64_t n, uint8_t K,
-                            int32_t* __restrict__ flag) {
+__global__ void k_flag_kind(const uint8_t* __restrict__ kind, const int64_t* __restrict__ n_dev,
+                            uint8_t K, int32_t* __restrict__ flag) {
+    const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         flag[i] = kind[i] == K;
 }
 
-__global__ void k_compact_kind(const uint8_t* __restrict__ kind, int64_t n, uint8_t K,
-                               const int32_t* __restrict__ off, const int32_t* __restrict__ pX,
-                               int32_t* __restrict__ out_q, uint64_t* __restrict__ out_key) {
+__global__ void k_compact_kind(const uint8_t* __restrict__ kind, const int64_t* __restrict__ n_dev,
+                               uint8_t K, const int32_t* __restrict__ off,
+                               const int32_t* __restrict__ pX, int32_t* __restrict__ out_q,
+                               uint64_t* __restrict__ out_key) {
+    const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         if (kind[i] == K) {
@@ -141,14 +172,20 @@ __global__ void k_compact_kind(const uint8_t* __restrict__ kind, int64_t n, uint
         }
 }
 
-__global__ void k_seg_flags(const uint64_t* __restrict__ key, int64_t n, int32_t* __restrict__ flag) {
+__global__ void k_seg_flags(const uint64_t* __restrict__ key, const int64_t* __restrict__ n_dev,
+                            int32_t* __restrict__ flag) {
+    const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
 }
 
+// segment starts, and seg_first[nseg] = n
 __global__ void k_seg_first(const int32_t* __restrict__ flag, const int32_t* __restrict__ off,
-                            int64_t n, int32_t* __restrict__ seg_first) {
+                            const int64_t* __restrict__ n_dev, const int64_t* __restrict__ nseg_dev,
+                            int32_t* __restrict__ seg_first) {
+    const int64_t n = *n_dev;
+    if (blockIdx.x == 0 && threadIdx.x == 0) seg_first[*nseg_dev] = (int32_t)n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         if (flag[i]) seg_first[off[i]] = (int32_t)i;
@@ -289,14 +326,15 @@ __device__ float warp_m2l(int p, const float* __restrict__ Ag, const float* __re
 constexpr int kM2LWarps = 4;
 
 __global__ void __launch_bounds__(kM2LWarps * 32)
-k_m2l(const int32_t* __restrict__ far_q, int64_t nfar, int64_t exp_first, int p, float inv_sigma,
-      const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+k_m2l(const int32_t* __restrict__ far_q, const int64_t* __restrict__ nfar_dev, int64_t exp_first,
+      int p, float inv_sigma, const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
       const float4* __restrict__ ca, const float4* __restrict__ cd, const float* __restrict__ A,
       const float* __restrict__ M, float* __restrict__ B, double2* __restrict__ pw) {
     __shared__ float sH[kM2LWarps][48];
     __shared__ float sbuf[kM2LWarps][3][kMaxP * kMaxP * kMaxP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p3 = p * p * p;
+    const int64_t nfar = *nfar_dev;
     for (int64_t k = (int64_t)blockIdx.x * kM2LWarps + w; k < nfar;
          k += (int64_t)gridDim.x * kM2LWarps) {
         int32_t q = far_q[k];
@@ -366,18 +404,19 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
 }
 
 // a10: attraction of a split pair = sum over its child block (double)
-__global__ void k_reduce_pairs(int64_t q0, int64_t nq, NodeView nv,
+__global__ void k_reduce_pairs(const int64_t* __restrict__ db, NodeView nv,
                                const uint8_t* __restrict__ kind, const int32_t* __restrict__ pX,
                                const int32_t* __restrict__ pY, const int32_t* __restrict__ pcf,
                                double2* __restrict__ pw) {
     // four interleaved partial sums (children c = j mod 4), combined in a fixed
     // order: deterministic, and four independent add chains
+    const int64_t q0 = db[0], nq = db[1] - db[0];
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = q0 + k;
-        if (kind[q] != kSplit) continue;
-        const int nb = block_size(nv, pX[q], pY[q]);
         const int32_t cf = pcf[q];
+        if (kind[q] != kSplit || cf < 0) continue;     // cf < 0: children not stored (overflow)
+        const int nb = block_size(nv, pX[q], pY[q]);
         double e[4] = {0.0, 0.0, 0.0, 0.0}, i[4] = {0.0, 0.0, 0.0, 0.0};
         int c = 0;
         for (; c + 3 < nb; c += 4) {
@@ -492,87 +531,68 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     const float inv_sigma = (float)(1.0 / cfg.sigma);
     const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
 
-    // a5: breadth-first dual traversal from (root, root)
-    c.depth_start.assign(1, 0);
-    int64_t total = n > 0 ? 1 : 0;
-    size_t cap = (size_t)std::max<int64_t>(64 * c.n_nodes, 1024);
-    auto grow_pairs = [&](size_t need, size_t keep) {
-        c.pr_X.grow<int32_t>(need, keep, s);
-        c.pr_Y.grow<int32_t>(need, keep, s);
-        c.pr_kind.grow<uint8_t>(need, keep, s);
-        c.pr_cf.grow<int32_t>(need, keep, s);
-        c.pr_w.grow<double2>(need, keep, s);
-    };
-    grow_pairs(cap, 0);
-    if (total) {
-        int32_t zero = 0;
-        MSP_CUDA(cudaMemcpyAsync(c.pr_X.get<int32_t>(), &zero, 4, cudaMemcpyHostToDevice, s));
-        MSP_CUDA(cudaMemcpyAsync(c.pr_Y.get<int32_t>(), &zero, 4, cudaMemcpyHostToDevice, s));
-        MSP_CUDA(cudaStreamSynchronize(s));
-    }
-    c.depth_start.push_back(total);
-    int d = 0;
-    while (c.depth_start[d + 1] > c.depth_start[d]) {
-        int64_t q0 = c.depth_start[d], nq = c.depth_start[d + 1] - q0;
-        int32_t* cnt = c.cnt.ensure<int32_t>((size_t)nq);
-        int32_t* off = c.off.ensure<int32_t>((size_t)nq);
-        k_classify<<<grid_for(nq, B), B, 0, s>>>(q0, nq, nv, geo, c.pr_X.get<int32_t>(),
-                                                 c.pr_Y.get<int32_t>(), c.pr_kind.get<uint8_t>(),
-                                                 cnt);
-        MSP_LAUNCH("classify");
-        int64_t nnext = scan_exclusive(c, cnt, off, nq, s);
-        if (total + nnext > 0x7fffffffll) throw Error(MSP_ERR_CAPACITY, "pair count exceeds int32");
-        if ((size_t)(total + nnext) > c.pr_X.bytes / sizeof(int32_t))
-            grow_pairs((size_t)(total + nnext), (size_t)total);
-        k_emit_pairs<<<grid_for(nq, B), B, 0, s>>>(q0, nq, total, nv, c.pr_kind.get<uint8_t>(), off,
-                                                   c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
-                                                   c.pr_cf.get<int32_t>(), c.pr_w.get<double2>());
-        MSP_LAUNCH("emit_pairs");
-        total += nnext;
-        c.depth_start.push_back(total);
-        ++d;
-    }
-    if (c.depth_start.size() > 1) c.depth_start.pop_back();   // the last depth is empty
-    c.n_pairs = total;
-    const int n_depths = (int)c.depth_start.size() - 1;
+    DevCounts* dc = dcounts(c);
+    // traversal depth d holds the pairs whose finer box is at level d, so the
+    // tree depth bounds the number of depths
+    const int D = c.tree_depth + 1;
+    if (c.pair_cap <= 0) c.pair_cap = std::max<int64_t>(64 * c.n_nodes, 1 << 16);
+    const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
+    for (int attempt = 0;; ++attempt) {
+    const int64_t cap = c.pair_cap;
+    if (cap > 0x7fffffffll) throw Error(MSP_ERR_CAPACITY, "pair count exceeds int32");
+    c.pr_X.ensure<int32_t>((size_t)cap);
+    c.pr_Y.ensure<int32_t>((size_t)cap);
+    c.pr_kind.ensure<uint8_t>((size_t)cap);
+    c.pr_cf.ensure<int32_t>((size_t)cap);
+    c.pr_w.ensure<double2>((size_t)cap);
+    int32_t* cnt = c.cnt.ensure<int32_t>((size_t)cap);
+    int32_t* off = c.off.ensure<int32_t>((size_t)cap);
     uint8_t* kind = c.pr_kind.get<uint8_t>();
 
-    // far and near-field lists
-    int32_t* flag = c.cnt.ensure<int32_t>((size_t)std::max<int64_t>(total, 1));
-    int32_t* off = c.off.ensure<int32_t>((size_t)std::max<int64_t>(total, 1));
-    k_flag_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kFar, flag);
-    MSP_LAUNCH("flag_far");
-    c.n_far = scan_exclusive(c, flag, off, total, s);
-    int32_t* far_q = c.far_q.ensure<int32_t>((size_t)std::max<int64_t>(c.n_far, 1));
-    k_compact_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kFar, off, c.pr_X.get<int32_t>(),
-                                                    far_q, nullptr);
-    MSP_LAUNCH("compact_far");
-    k_flag_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kP2P, flag);
-    MSP_LAUNCH("flag_p2p");
-    c.n_p2p = scan_exclusive(c, flag, off, total, s);
-    size_t np = (size_t)std::max<int64_t>(c.n_p2p, 1);
-    uint64_t* pk0 = c.p2p_key0.ensure<uint64_t>(np);
-    uint64_t* pk1 = c.p2p_key1.ensure<uint64_t>(np);
-    int32_t* pv0 = c.p2p_val0.ensure<int32_t>(np);
-    int32_t* pv1 = c.p2p_val1.ensure<int32_t>(np);
-    k_compact_kind<<<grid_for(total, B), B, 0, s>>>(kind, total, kP2P, off, c.pr_X.get<int32_t>(),
-                                                    pv0, pk0);
-    MSP_LAUNCH("compact_p2p");
-    radix_sort(c, pk0, pv0, pk1, pv1, c.n_p2p, bits_for(c.n_nodes), s);
-    int32_t* sflag = c.seg_flag.ensure<int32_t>(np);
-    int32_t* soff = c.cnt.ensure<int32_t>(np);
-    k_seg_flags<<<grid_for(c.n_p2p, B), B, 0, s>>>(pk0, c.n_p2p, sflag);
-    MSP_LAUNCH("seg_flags");
-    int64_t nseg = scan_exclusive(c, sflag, soff, c.n_p2p, s);
-    int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)nseg + 1);
-    k_seg_first<<<grid_for(c.n_p2p, B), B, 0, s>>>(sflag, soff, c.n_p2p, seg_first);
-    MSP_LAUNCH("seg_first");
-    {
-        int32_t last = (int32_t)c.n_p2p;
-        MSP_CUDA(cudaMemcpyAsync(seg_first + nseg, &last, 4, cudaMemcpyHostToDevice, s));
-        MSP_CUDA(cudaStreamSynchronize(s));
+    // a5: breadth-first dual traversal from (root, root)
+    k_init_pairs<<<1, 1, 0, s>>>(n, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(), dc);
+    MSP_LAUNCH("init_pairs");
+    for (int d = 0; d < D; ++d) {
+        k_classify<<<Gt, B, 0, s>>>(&dc->depth_start[d], nv, geo, c.pr_X.get<int32_t>(),
+                                    c.pr_Y.get<int32_t>(), kind, cnt, &dc->scan_n);
+        MSP_LAUNCH("classify");
+        scan_dev(c, cnt, off, &dc->scan_n, cap, &dc->depth_start[d + 2], &dc->depth_start[d + 1], s,
+                 cap, &dc->overflow, &dc->need_pairs);
+        k_emit_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[d], nv, kind, off, c.pr_X.get<int32_t>(),
+                                      c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
+                                      c.pr_w.get<double2>(), cap, &dc->overflow);
+        MSP_LAUNCH("emit_pairs");
     }
-    c.n_p2p_targets = nseg;
+    const int64_t* n_pairs_dev = &dc->depth_start[D];
+
+    // far and near-field lists
+    int32_t* flag = cnt;
+    k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kFar, flag);
+    MSP_LAUNCH("flag_far");
+    scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_far, nullptr, s);
+    int32_t* far_q = c.far_q.ensure<int32_t>((size_t)cap);
+    k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kFar, off, c.pr_X.get<int32_t>(), far_q,
+                                    nullptr);
+    MSP_LAUNCH("compact_far");
+    k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kP2P, flag);
+    MSP_LAUNCH("flag_p2p");
+    scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_p2p, nullptr, s);
+    uint64_t* pk0 = c.p2p_key0.ensure<uint64_t>((size_t)cap);
+    uint64_t* pk1 = c.p2p_key1.ensure<uint64_t>((size_t)cap);
+    int32_t* pv0 = c.p2p_val0.ensure<int32_t>((size_t)cap);
+    int32_t* pv1 = c.p2p_val1.ensure<int32_t>((size_t)cap);
+    k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kP2P, off, c.pr_X.get<int32_t>(), pv0, pk0);
+    MSP_LAUNCH("compact_p2p");
+    radix_sort_dev(c, pk0, pv0, pk1, pv1, &dc->n_p2p, cap, bits_for(c.n_nodes), s);
+    int32_t* sflag = c.seg_flag.ensure<int32_t>((size_t)cap);
+    int32_t* soff = cnt;
+    k_seg_flags<<<Gt, B, 0, s>>>(pk0, &dc->n_p2p, sflag);
+    MSP_LAUNCH("seg_flags");
+    scan_dev(c, sflag, soff, &dc->n_p2p, cap, &dc->nseg, nullptr, s);
+    // at most one segment per box
+    int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)c.n_nodes + 2);
+    k_seg_first<<<Gt, B, 0, s>>>(sflag, soff, &dc->n_p2p, &dc->nseg, seg_first);
+    MSP_LAUNCH("seg_first");
 
     // a6: expansions of every box at level >= l_far
     c.exp_first = c.l_far <= c.tree_depth ? c.level_start[c.l_far] : c.n_nodes;
@@ -589,37 +609,31 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
         MSP_LAUNCH("p2m");
     }
     // a7: translations, accumulating B(X) and W(X,Y)
-    if (c.n_far > 0) {
-        int g = grid_for(c.n_far, kM2LWarps, (int64_t)c.sm_count * 32);
-        k_m2l<<<g, kM2LWarps * 32, 0, s>>>(far_q, c.n_far, c.exp_first, p, inv_sigma,
-                                           c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
-                                           c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM,
-                                           eB, c.pr_w.get<double2>());
+    if (c.exp_nodes > 0) {
+        k_m2l<<<(int)c.sm_count * 8, kM2LWarps * 32, 0, s>>>(
+            far_q, &dc->n_far, c.exp_first, p, inv_sigma, c.pr_X.get<int32_t>(),
+            c.pr_Y.get<int32_t>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM, eB,
+            c.pr_w.get<double2>());
         MSP_LAUNCH("m2l");
     }
     // a8: Taylor evaluation initialises u in sorted order; a9 adds the near field
     float* us = c.u_sorted.ensure<float>((size_t)std::max<int64_t>(n, 1));
-    unsigned long long* work = c.small_dev.ensure<unsigned long long>(8) + 1;
-    MSP_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(&dc->interactions);
     if (n > 0) {
         k_l2p<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
             n, c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.leaf_of.get<int32_t>(),
             c.nd_parent.get<int32_t>(), c.nd_ca.get<float4>(), eB, us);
         MSP_LAUNCH("l2p");
-    }
-    if (nseg > 0) {
         MSP_CUDA(cudaEventRecord(c.ev_nf0, s));
-        launch_near_field(c, seg_first, nseg, pv0, c.n_p2p, us, work, s);
+        launch_near_field(c, seg_first, &dc->nseg, c.n_nodes, pv0, &dc->n_p2p, cap, us, work, s);
         MSP_CUDA(cudaEventRecord(c.ev_nf1, s));
     }
-    c.nf_timed = nseg > 0;
+    c.nf_timed = n > 0;
     // a10: pair table, deepest pairs first
-    for (int dd = n_depths - 1; dd >= 0; --dd) {
-        int64_t q0 = c.depth_start[dd], nq = c.depth_start[dd + 1] - q0;
-        if (nq == 0) continue;
-        k_reduce_pairs<<<grid_for(nq, B), B, 0, s>>>(q0, nq, nv, kind, c.pr_X.get<int32_t>(),
-                                                     c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
-                                                     c.pr_w.get<double2>());
+    for (int dd = D - 1; dd >= 0; --dd) {
+        k_reduce_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[dd], nv, kind, c.pr_X.get<int32_t>(),
+                                        c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
+                                        c.pr_w.get<double2>());
         MSP_LAUNCH("reduce_pairs");
     }
     if (u_dev && n > 0) {
@@ -627,7 +641,28 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
             us, c.perm.get<int32_t>(), n, u_dev);
         MSP_LAUNCH("scatter_u");
     }
-    c.p2p_interactions = read_i64(c, reinterpret_cast<const int64_t*>(work), s);
+    pull_counts(c, s);              // the one synchronisation of the attraction
+    const DevCounts& hc = *c.hcount;
+    if (hc.overflow & 1) {
+        // the pair table was too small: the traversal stopped at the first depth
+        // that did not fit, so its count is a lower bound; grow and redo
+        if (attempt >= 8) throw Error(MSP_ERR_CAPACITY, "pair table overflow after growth");
+        c.pair_cap = std::max(2 * cap, hc.need_pairs + hc.need_pairs / 2 + 1024);
+        continue;
+    }
+    int nd = 0;
+    for (int d = 0; d < D; ++d)
+        if (hc.depth_start[d + 1] > hc.depth_start[d]) nd = d + 1;
+    c.depth_start.assign(hc.depth_start, hc.depth_start + nd + 1);
+    c.n_pairs = hc.depth_start[D];
+    c.n_far = hc.n_far;
+    c.n_p2p = hc.n_p2p;
+    c.n_p2p_targets = hc.nseg;
+    c.p2p_interactions = hc.interactions;
+    // keep a quarter of headroom for the next call
+    c.pair_cap = std::max(c.pair_cap, c.n_pairs + c.n_pairs / 4 + 1024);
+    break;
+    }
     c.attraction_done = true;
 }
 

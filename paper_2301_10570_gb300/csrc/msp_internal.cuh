@@ -92,6 +92,29 @@ struct Item {
     int32_t X, Y, q, ch;   // axon box, dendrite box, traversal pair (-1 below a far pair), channel
 };
 
+constexpr int kMaxLevels = kMortonBits + 1;   // octree levels 0..21
+
+// Sizes that the kernels produce and consume, kept in device memory so that
+// a whole step runs without waiting for the host; copied to pinned host
+// memory once at the end of each public call.
+struct DevCounts {
+    int64_t n;                               // neurons of the last build
+    int64_t level_start[kMaxLevels + 2];     // level l boxes: [level_start[l], level_start[l+1])
+    int64_t depth_start[kMaxLevels + 3];     // traversal depth d pairs
+    int64_t n_elem;                          // vacant axonal elements
+    int64_t more_levels;                     // boxes still to split below the last built level
+    int64_t n_far, n_p2p, nseg;
+    int64_t items[3];                        // descent items, rotating: in / out / reset
+    int64_t n_leaf;                          // leaf pairs reached by the descent
+    int64_t draws;
+    int64_t n_req, n_syn;
+    int64_t interactions;
+    int64_t overflow;                        // bit 0 pairs, 1 items, 2 leaf items, 3 steps
+    int64_t need_pairs;                      // largest pair-table end asked for (before clamping)
+    int64_t need_items;                      // largest descent item count asked for
+    int64_t scan_n;                          // element count of the next scan
+};
+
 }  // namespace msp
 
 struct msp_ctx {
@@ -130,7 +153,12 @@ struct msp_ctx {
     // descent
     msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
     // generic scratch
-    msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist;
+    msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist, sd_tmp;
+    // device-resident sizes and their pinned host mirror
+    msp::DBuf dcount;
+    msp::DevCounts* hcount = nullptr;
+    int depth_hint = -1;                 // tree depth of the last build (-1: none)
+    int64_t pair_cap = 0;                // capacity of the pair table
     int64_t* small_host = nullptr;     // pinned, for count readbacks
     cudaEvent_t ev_nf0 = nullptr, ev_nf1 = nullptr;   // around the near-field kernel
     bool nf_timed = false;
@@ -158,11 +186,32 @@ void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                 int32_t* vals_tmp, int64_t n, int bits, cudaStream_t s);
 // Step a9, the near field over the leaf pairs grouped by target leaf
 // (msp_nearfield.cu); accumulates into u_sorted and the pair table.
-void launch_near_field(msp_ctx& c, const int32_t* seg_first, int64_t nseg, const int32_t* list_q,
-                       int64_t n_list, float* u_sorted, unsigned long long* work,
+// Segment and list counts live in device memory (*nseg_dev <= nseg_cap,
+// *nlist_dev <= nlist_cap); no host synchronisation.
+void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
+                       int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
+                       int64_t nlist_cap, float* u_sorted, unsigned long long* work,
                        cudaStream_t s);
 // Read an int64 from device memory (synchronous).
 int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s);
+// Exclusive scan of in[0, *n_dev) (n_dev in device memory, at most n_cap)
+// into out; *total_dst = total (+ *base if base).  No host synchronisation.
+// With overflow given, an end above clamp_cap sets bit 0 of *overflow, raises
+// *need to it and stores *base instead.
+void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev, int64_t n_cap,
+              int64_t* total_dst, const int64_t* base, cudaStream_t s, int64_t clamp_cap = 0,
+              int64_t* overflow = nullptr, int64_t* need = nullptr);
+// Stable radix sort of the first *n_dev (<= n_cap) pairs.  No host sync.
+void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                    int32_t* vals_tmp, const int64_t* n_dev, int64_t n_cap, int bits,
+                    cudaStream_t s);
+// small device-side bookkeeping (msp_prims.cu)
+void dev_set(int64_t* dst, int64_t v, cudaStream_t s);
+void dev_sub(int64_t* dst, const int64_t* a, const int64_t* b, cudaStream_t s);   // *dst = *b - *a
+void dev_store_i32(int32_t* dst, const int64_t* src, cudaStream_t s);
+// device counts of a context and their host mirror (synchronous)
+inline DevCounts* dcounts(msp_ctx& c) { return c.dcount.get<DevCounts>(); }
+void pull_counts(msp_ctx& c, cudaStream_t s);
 
 inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
     int64_t g = (n + block - 1) / block;

@@ -53,7 +53,7 @@ __device__ inline float nf_ex2(float x) {
 
 struct NFArgs {
     const int32_t* seg_first;
-    int64_t nseg;
+    const int64_t* nseg;         // segment count (device memory)
     const int32_t* list_q;
     const int32_t* pX;
     const int32_t* pY;
@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
     s_wii = &wii_all[0][0];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stw = st[w];
-    for (int64_t sg = blockIdx.x; sg < a.nseg; sg += gridDim.x) {
+    const int64_t nseg = *a.nseg;
+    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t i0 = a.seg_first[sg], i1 = a.seg_first[sg + 1];
         const int32_t X = a.pX[a.list_q[i0]];
         const int32_t tf = a.nfirst[X], tc = a.ncount[X];
@@ -346,9 +347,17 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
     }
 }
 
+__global__ void k_zero_w(float2* __restrict__ w32, const int64_t* __restrict__ n_dev) {
+    const int64_t n = *n_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        w32[i] = make_float2(0.f, 0.f);
+}
+
 // the single precision per-pair attractions into the double precision table
 __global__ void k_widen_w(const int32_t* __restrict__ list_q, const float2* __restrict__ w32,
-                          int64_t n, double2* __restrict__ pw) {
+                          const int64_t* __restrict__ n_dev, double2* __restrict__ pw) {
+    const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float2 v = w32[i];
@@ -358,15 +367,19 @@ __global__ void k_widen_w(const int32_t* __restrict__ list_q, const float2* __re
 
 }  // namespace
 
-void launch_near_field(msp_ctx& c, const int32_t* seg_first, int64_t nseg, const int32_t* list_q,
-                       int64_t n_list, float* u_sorted, unsigned long long* work, cudaStream_t s) {
-    if (nseg <= 0) return;
+void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
+                       int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
+                       int64_t nlist_cap, float* u_sorted, unsigned long long* work,
+                       cudaStream_t s) {
+    if (nseg_cap <= 0 || nlist_cap <= 0) return;
     const msp_config& cfg = c.cfg;
-    float2* w32 = c.nf_w32.ensure<float2>((size_t)n_list);
-    MSP_CUDA(cudaMemsetAsync(w32, 0, (size_t)n_list * sizeof(float2), s));
+    float2* w32 = c.nf_w32.ensure<float2>((size_t)nlist_cap);
+    const int gl = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
+    k_zero_w<<<gl, 256, 0, s>>>(w32, nlist_dev);
+    MSP_LAUNCH("zero_w");
     NFArgs a;
     a.seg_first = seg_first;
-    a.nseg = nseg;
+    a.nseg = nseg_dev;
     a.list_q = list_q;
     a.pX = c.pr_X.get<int32_t>();
     a.pY = c.pr_Y.get<int32_t>();
@@ -384,11 +397,11 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, int64_t nseg, const
     a.u = u_sorted;
     a.w32 = w32;
     a.work = work;
-    int grid = (int)std::min<int64_t>(nseg, 1 << 30);
+    // one block per segment; blocks past the device count return at once
+    int grid = (int)std::min<int64_t>(nseg_cap, 1 << 30);
     k_near_field<<<grid, kNFWarps * 32, 0, s>>>(a);
     MSP_LAUNCH("near_field");
-    k_widen_w<<<grid_for(n_list, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
-        list_q, w32, n_list, c.pr_w.get<double2>());
+    k_widen_w<<<gl, 256, 0, s>>>(list_q, w32, nlist_dev, c.pr_w.get<double2>());
     MSP_LAUNCH("widen_w");
 }
 

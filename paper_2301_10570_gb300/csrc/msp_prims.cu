@@ -242,4 +242,240 @@ void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// the same primitives with the element count in device memory (no host sync;
+// launch shapes come from a host-side capacity bound)
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_sd_reduce(const int32_t* __restrict__ in, const int64_t* __restrict__ n_dev,
+                            long long* __restrict__ bsum) {
+    const int64_t n = *n_dev;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    __shared__ long long tot;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long s = 0;
+        for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+            int64_t i = t * kScanTile + j;
+            if (i < n) s += in[i];
+        }
+        long long d = block_excl_scan(s, &tot);
+        (void)d;
+        if (threadIdx.x == 0) bsum[t] = tot;
+        __syncthreads();
+    }
+}
+
+// one block: exclusive scan of the tile sums in chunks, total (+ *base) to
+// *dst.  With a clamp, an end beyond clamp_cap is recorded (overflow bit 0,
+// need = the largest end asked for) and *dst gets *base instead: the next
+// range is empty.
+__global__ void k_sd_spine(long long* __restrict__ bsum, const int64_t* __restrict__ n_dev,
+                           int64_t* __restrict__ dst, const int64_t* __restrict__ base,
+                           int64_t clamp_cap, int64_t* __restrict__ overflow,
+                           int64_t* __restrict__ need) {
+    const int64_t n = *n_dev;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    __shared__ long long chunk_total;
+    long long carry = 0;
+    for (int64_t c0 = 0; c0 < ntiles; c0 += (int64_t)kScanThreads * kScanItems) {
+        long long v[kScanItems];
+        long long s = 0;
+        const int64_t b = c0 + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            v[j] = b + j < ntiles ? bsum[b + j] : 0;
+            s += v[j];
+        }
+        long long pre = block_excl_scan(s, &chunk_total) + carry;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (b + j < ntiles) bsum[b + j] = pre;
+            pre += v[j];
+        }
+        carry += chunk_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && dst) {
+        const int64_t b = base ? *base : 0;
+        int64_t end = carry + b;
+        if (overflow && end > clamp_cap) {
+            atomicOr(reinterpret_cast<unsigned long long*>(overflow), 1ull);
+            atomicMax(reinterpret_cast<unsigned long long*>(need), (unsigned long long)end);
+            end = b;
+        }
+        *dst = end;
+    }
+}
+
+__global__ void k_sd_apply(const int32_t* in, int32_t* out, const int64_t* __restrict__ n_dev,
+                           const long long* __restrict__ bsum) {
+    const int64_t n = *n_dev;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    __shared__ long long tot;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t base = t * kScanTile + (int64_t)threadIdx.x * kScanItems;
+        long long v[kScanItems];
+        long long s = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            v[j] = base + j < n ? in[base + j] : 0;
+            s += v[j];
+        }
+        long long pre = block_excl_scan(s, &tot) + bsum[t];
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (base + j < n) out[base + j] = (int32_t)pre;
+            pre += v[j];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_radix_hist_dev(const uint64_t* __restrict__ keys, const int64_t* __restrict__ n_dev,
+                                 int shift, int32_t* __restrict__ hist, int nb) {
+    __shared__ int32_t h[256];
+    const int64_t n = *n_dev;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int j = threadIdx.x; j < kRsTile; j += kRsThreads) {
+        int64_t i = base + j;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_radix_scatter_dev(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                                    const int64_t* __restrict__ n_dev, int shift,
+                                    const int32_t* __restrict__ offs, int nb,
+                                    uint64_t* __restrict__ kout, int32_t* __restrict__ vout) {
+    const int64_t n = *n_dev;
+    if ((int64_t)blockIdx.x * kRsTile >= n) return;       // whole block idle
+    __shared__ int32_t running[256];
+    __shared__ int32_t wcnt[kRsWarps][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    running[t] = offs[(int64_t)t * nb + blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kRsWarps; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsItems; ++r) {
+        int64_t i = base + (int64_t)r * kRsThreads + t;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        int32_t val = valid ? vin[i] : 0;
+        int d = valid ? (int)((key >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = running[d] + rank;
+            for (int k = 0; k < w; ++k) pos += wcnt[k][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        int add = 0;
+#pragma unroll
+        for (int k = 0; k < kRsWarps; ++k) {
+            add += wcnt[k][t];
+            wcnt[k][t] = 0;
+        }
+        running[t] += add;
+        __syncthreads();
+    }
+}
+
+__global__ void k_copy_kv_dev(const uint64_t* __restrict__ ks, const int32_t* __restrict__ vs,
+                              const int64_t* __restrict__ n_dev, uint64_t* __restrict__ kd,
+                              int32_t* __restrict__ vd) {
+    const int64_t n = *n_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        kd[i] = ks[i];
+        vd[i] = vs[i];
+    }
+}
+
+}  // namespace
+
+namespace {
+__global__ void k_dev_set(int64_t* dst, int64_t v) { *dst = v; }
+__global__ void k_dev_sub(int64_t* dst, const int64_t* a, const int64_t* b) { *dst = *b - *a; }
+__global__ void k_dev_store_i32(int32_t* dst, const int64_t* src) { *dst = (int32_t)*src; }
+}  // namespace
+
+void dev_set(int64_t* dst, int64_t v, cudaStream_t s) {
+    k_dev_set<<<1, 1, 0, s>>>(dst, v);
+    MSP_LAUNCH("dev_set");
+}
+void dev_sub(int64_t* dst, const int64_t* a, const int64_t* b, cudaStream_t s) {
+    k_dev_sub<<<1, 1, 0, s>>>(dst, a, b);
+    MSP_LAUNCH("dev_sub");
+}
+void dev_store_i32(int32_t* dst, const int64_t* src, cudaStream_t s) {
+    k_dev_store_i32<<<1, 1, 0, s>>>(dst, src);
+    MSP_LAUNCH("dev_store_i32");
+}
+void pull_counts(msp_ctx& c, cudaStream_t s) {
+    MSP_CUDA(cudaMemcpyAsync(c.hcount, c.dcount.p, sizeof(DevCounts), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+}
+
+void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev, int64_t n_cap,
+              int64_t* total_dst, const int64_t* base, cudaStream_t s, int64_t clamp_cap,
+              int64_t* overflow, int64_t* need) {
+    const int64_t tiles_cap = std::max<int64_t>((n_cap + kScanTile - 1) / kScanTile, 1);
+    long long* bsum = c.sd_tmp.ensure<long long>((size_t)tiles_cap);
+    const int G = (int)std::min<int64_t>(tiles_cap, (int64_t)c.sm_count * 8);
+    k_sd_reduce<<<G, kScanThreads, 0, s>>>(in, n_dev, bsum);
+    MSP_LAUNCH("scan_dev_reduce");
+    k_sd_spine<<<1, kScanThreads, 0, s>>>(bsum, n_dev, total_dst, base, clamp_cap, overflow,
+                                          need);
+    MSP_LAUNCH("scan_dev_spine");
+    k_sd_apply<<<G, kScanThreads, 0, s>>>(in, out, n_dev, bsum);
+    MSP_LAUNCH("scan_dev_apply");
+}
+
+void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                    int32_t* vals_tmp, const int64_t* n_dev, int64_t n_cap, int bits,
+                    cudaStream_t s) {
+    if (n_cap <= 1 || bits <= 0) return;
+    const int nb = (int)((n_cap + kRsTile - 1) / kRsTile);
+    int32_t* hist = c.rs_hist.ensure<int32_t>((size_t)256 * nb);
+    const int passes = (bits + 7) / 8;
+    uint64_t *ka = keys, *kb = keys_tmp;
+    int32_t *va = vals, *vb = vals_tmp;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = 8 * ps;
+        k_radix_hist_dev<<<nb, kRsThreads, 0, s>>>(ka, n_dev, shift, hist, nb);
+        MSP_LAUNCH("radix_hist_dev");
+        const int64_t m = (int64_t)256 * nb;
+        const int64_t tb = (m + kScanTile - 1) / kScanTile;
+        long long* scratch = c.scan_tmp.ensure<long long>((size_t)(2 * tb + 64));
+        if (tb == 1) {
+            k_scan_tile<int32_t, int32_t><<<1, kScanThreads, 0, s>>>(hist, hist, m, nullptr, nullptr);
+        } else {
+            k_scan_reduce<int32_t><<<(unsigned)tb, kScanThreads, 0, s>>>(hist, m, scratch);
+            scan_i64(c, scratch, tb, nullptr, scratch + tb, s);
+            k_scan_tile<int32_t, int32_t><<<(unsigned)tb, kScanThreads, 0, s>>>(hist, hist, m,
+                                                                              scratch, nullptr);
+        }
+        MSP_LAUNCH("radix_scan_dev");
+        k_radix_scatter_dev<<<nb, kRsThreads, 0, s>>>(ka, va, n_dev, shift, hist, nb, kb, vb);
+        MSP_LAUNCH("radix_scatter_dev");
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        k_copy_kv_dev<<<grid_for(n_cap, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
+            ka, va, n_dev, keys, vals);
+        MSP_LAUNCH("radix_copy_dev");
+    }
+}
+
 }  // namespace msp

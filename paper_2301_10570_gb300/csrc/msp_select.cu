@@ -112,15 +112,46 @@ __device__ inline int draw_index(const double* w, int k, double U) {
 
 constexpr int kDescWarps = 4;
 
+// Descent counters of one level step.  The item counts rotate through three
+// slots: the step reads its input count from one, appends to the next (zeroed
+// by the step before) and zeroes the third for the step after.
+struct DescCtr {
+    const int64_t* n_in;
+    unsigned long long* n_out;
+    int64_t* n_reset;
+    unsigned long long* n_leaf;
+    unsigned long long* draws;
+    unsigned long long* overflow;     // bit 1: items, bit 2: leaf items
+};
+
+// the items of both channels start at (root, root) where the root has
+// vacancies and attraction in that channel
+__global__ void k_init_items(const int4* __restrict__ sums, const double2* __restrict__ pw,
+                             Item* __restrict__ items, DevCounts* dc) {
+    const int4 rs = sums[0];
+    const double2 rw = pw[0];
+    int64_t k = 0;
+    if (rs.x > 0 && rw.x > kMinAttraction) items[k++] = Item{0, 0, 0, 0};
+    if (rs.y > 0 && rw.y > kMinAttraction) items[k++] = Item{0, 0, 0, 1};
+    dc->items[0] = k;
+    dc->items[1] = 0;
+    dc->n_leaf = 0;
+    dc->draws = 0;
+    dc->overflow = 0;
+}
+
 __global__ void __launch_bounds__(kDescWarps * 32)
-k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
+k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
           const uint8_t* __restrict__ kind, const int32_t* __restrict__ pcf,
           const double2* __restrict__ pw, uint64_t seed, uint64_t step, Item* __restrict__ out,
-          int64_t cap_out, Item* __restrict__ leaf_out, int64_t cap_leaf,
-          unsigned long long* __restrict__ counters /* [0] next, [1] leaf, [2] draws, [3] overflow */) {
+          int64_t cap_out, Item* __restrict__ leaf_out, int64_t cap_leaf, DescCtr ct) {
     __shared__ float sH[kDescWarps][48];
     __shared__ float sb[kDescWarps][2][kMaxP * kMaxP * kMaxP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the count may exceed the buffer (items past it were not stored and the
+    // overflow bit is set)
+    const int64_t n_in = min(*ct.n_in, cap_out);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ct.n_reset = 0;
     for (int64_t k = (int64_t)blockIdx.x * kDescWarps + w; k < n_in;
          k += (int64_t)gridDim.x * kDescWarps) {
         Item it = in[k];
@@ -132,9 +163,9 @@ k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
         if (lx && ly) {
             // form_synapse: the leaf pair goes to the per-element draw
             if (lane == 0) {
-                unsigned long long slot = atomicAdd(&counters[1], 1ull);
+                unsigned long long slot = atomicAdd(ct.n_leaf, 1ull);
                 if ((int64_t)slot < cap_leaf) leaf_out[slot] = it;
-                else atomicAdd(&counters[3], 1ull);
+                else atomicOr(ct.overflow, 4ull);
             }
             continue;
         }
@@ -150,10 +181,10 @@ k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
                 bool keep = sa > 0;
                 if (keep && split) keep = (ch ? pw[cf + lane].y : pw[cf + lane].x) > kMinAttraction;
                 if (keep) {
-                    unsigned long long slot = atomicAdd(&counters[0], 1ull);
+                    unsigned long long slot = atomicAdd(ct.n_out, 1ull);
                     Item nx_it = {xc, Y, split ? cf + lane : -1, ch};
                     if ((int64_t)slot < cap_out) out[slot] = nx_it;
-                    else atomicAdd(&counters[3], 1ull);
+                    else atomicOr(ct.overflow, 2ull);
                 }
             }
             continue;
@@ -182,12 +213,12 @@ k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
                 uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
                 double U = philox_uniform(seed, (uint32_t)xc, c1, step);
                 int kk = draw_index(wk, ny, U);
-                atomicAdd(&counters[2], 1ull);
+                atomicAdd(ct.draws, 1ull);
                 if (kk >= 0) {
-                    unsigned long long slot = atomicAdd(&counters[0], 1ull);
+                    unsigned long long slot = atomicAdd(ct.n_out, 1ull);
                     Item nx_it = {xc, cy + kk, split ? cf + i * ny + kk : -1, ch};
                     if ((int64_t)slot < cap_out) out[slot] = nx_it;
-                    else atomicAdd(&counters[3], 1ull);
+                    else atomicOr(ct.overflow, 2ull);
                 }
             }
             __syncwarp();
@@ -197,16 +228,18 @@ k_descend(const Item* __restrict__ in, int64_t n_in, Tree tr, Exps ex,
 
 // per-element draw inside a chosen dendrite leaf: weights w_s K(t,s) in
 // single precision, inclusive prefix sums in double precision
-__global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
+__global__ void k_leaf_draw(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf,
+                            int64_t cap_leaf,
                             const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
                             const float4* __restrict__ pts, const float2* __restrict__ wts,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
                             float k2, float rc2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
-                            unsigned long long* __restrict__ counters) {
+                            unsigned long long* __restrict__ draw_ctr) {
     // one block of kLeafWarps warps per leaf item; the warps take interleaved
     // chunks of 32 targets of the axon leaf
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    const int64_t n_items = min(*n_leaf, cap_leaf);
     for (int64_t k = blockIdx.x; k < n_items; k += gridDim.x) {
         Item it = items[k];
         const int32_t tf = nfirst[it.X], tc = ncount[it.X];
@@ -290,7 +323,7 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, int64_t n_items,
             }
         }
         for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
-        if (lane == 0 && draws) atomicAdd(&counters[2], draws);
+        if (lane == 0 && draws) atomicAdd(draw_ctr, draws);
     }
 }
 
@@ -328,8 +361,9 @@ __global__ void k_request_emit(int64_t n, const uint8_t* __restrict__ type,
 // (priority, element) order: request i is accepted unless request i - cap
 // belongs to the same (dendrite, channel) group
 __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
-                         int64_t nr, const uint8_t* __restrict__ vde,
+                         const int64_t* __restrict__ nr_dev, const uint8_t* __restrict__ vde,
                          const uint8_t* __restrict__ vdi, uint8_t* __restrict__ accepted) {
+    const int64_t nr = *nr_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t g = (uint32_t)(key[i] >> 32);
@@ -458,90 +492,75 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     ex.p = cfg.p;
     ex.inv_sigma = (float)(1.0 / cfg.sigma);
 
-    // a11: items of both channels start at (root, root) if the root pair has
-    // vacancies and attraction in that channel
-    int64_t cap_items = 2 * c.n_nodes + 64, cap_leaf = 2 * c.n_nodes + 64;
-    Item* it0 = c.items0.ensure<Item>((size_t)cap_items);
-    Item* it1 = c.items1.ensure<Item>((size_t)cap_items);
+    // a11: the level steps of the descent.  At step k every inner box of an
+    // item is at level k (inner boxes always go one level down; a leaf stays),
+    // and an item of two leaves goes to the per-element draw, so depth + 1
+    // steps empty the item list.
+    const int64_t cap_items = 2 * c.n_nodes + 64, cap_leaf = 2 * c.n_nodes + 64;
+    Item* ib[2] = {c.items0.ensure<Item>((size_t)cap_items), c.items1.ensure<Item>((size_t)cap_items)};
     Item* lit = c.leaf_items.ensure<Item>((size_t)cap_leaf);
-    unsigned long long* ctr = c.small_dev.ensure<unsigned long long>(8) + 2;
-    int4 root_sums;
-    double2 root_w;
-    MSP_CUDA(cudaMemcpyAsync(&root_sums, c.nd_sums.get<int4>(), sizeof(int4), cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaMemcpyAsync(&root_w, c.pr_w.get<double2>(), sizeof(double2), cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaStreamSynchronize(s));
-    std::vector<Item> init;
-    if (root_sums.x > 0 && root_w.x > kMinAttraction) init.push_back(Item{0, 0, 0, 0});
-    if (root_sums.y > 0 && root_w.y > kMinAttraction) init.push_back(Item{0, 0, 0, 1});
-    int64_t n_in = (int64_t)init.size();
-    if (n_in) MSP_CUDA(cudaMemcpyAsync(it0, init.data(), n_in * sizeof(Item), cudaMemcpyHostToDevice, s));
-    MSP_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
-    Item *cur = it0, *nxt = it1;
-    int guard = 0;
-    while (n_in > 0) {
-        MSP_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
-        int g = grid_for(n_in, kDescWarps, (int64_t)c.sm_count * 32);
-        k_descend<<<g, kDescWarps * 32, 0, s>>>(cur, n_in, tr, ex, c.pr_kind.get<uint8_t>(),
-                                                c.pr_cf.get<int32_t>(), c.pr_w.get<double2>(),
-                                                cfg.seed, step, nxt, cap_items, lit, cap_leaf, ctr);
+    DevCounts* dc = dcounts(c);
+    k_init_items<<<1, 1, 0, s>>>(c.nd_sums.get<int4>(), c.pr_w.get<double2>(), ib[0], dc);
+    MSP_LAUNCH("init_items");
+    auto ull = [](int64_t* p) { return reinterpret_cast<unsigned long long*>(p); };
+    const int n_steps = c.tree_depth + 1;
+    const int gd = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 16);
+    for (int k = 0; k < n_steps; ++k) {
+        DescCtr ct;
+        ct.n_in = &dc->items[k % 3];
+        ct.n_out = ull(&dc->items[(k + 1) % 3]);
+        ct.n_reset = &dc->items[(k + 2) % 3];
+        ct.n_leaf = ull(&dc->n_leaf);
+        ct.draws = ull(&dc->draws);
+        ct.overflow = ull(&dc->overflow);
+        k_descend<<<gd, kDescWarps * 32, 0, s>>>(ib[k & 1], tr, ex, c.pr_kind.get<uint8_t>(),
+                                                 c.pr_cf.get<int32_t>(), c.pr_w.get<double2>(),
+                                                 cfg.seed, step, ib[(k + 1) & 1], cap_items, lit,
+                                                 cap_leaf, ct);
         MSP_LAUNCH("descend");
-        MSP_CUDA(cudaMemcpyAsync(c.small_host, ctr, 4 * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, s));
-        MSP_CUDA(cudaStreamSynchronize(s));
-        if (c.small_host[3] != 0) throw Error(MSP_ERR_CHECK, "descent item capacity exceeded");
-        n_in = c.small_host[0];
-        std::swap(cur, nxt);
-        if (++guard > 4 * kMortonBits + 8) throw Error(MSP_ERR_CHECK, "descent did not terminate");
     }
-    int64_t n_leaf = c.small_host[1];
-    c.n_draws = c.small_host[2];
-    if (n_leaf > 0) {
-        int g = (int)std::min<int64_t>(n_leaf, 1 << 30);
-        k_leaf_draw<<<g, 128, 0, s>>>(lit, n_leaf, c.nd_first.get<int32_t>(),
-                                      c.nd_count.get<int32_t>(), c.pts.get<float4>(),
-                                      c.wts.get<float2>(), c.perm.get<int32_t>(),
-                                      c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, step, partner, ctr);
-        MSP_LAUNCH("leaf_draw");
-    }
+    // one block per leaf item; blocks past the device count return at once
+    k_leaf_draw<<<(unsigned)std::min<int64_t>(cap_leaf, 1 << 30), 128, 0, s>>>(
+        lit, &dc->n_leaf, cap_leaf, c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+        c.pts.get<float4>(), c.wts.get<float2>(), c.perm.get<int32_t>(),
+        c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, step, partner, ull(&dc->draws));
+    MSP_LAUNCH("leaf_draw");
 
     // a12: requests, sorted by (dendrite, channel, priority, element)
     int32_t* flag = c.cnt.ensure<int32_t>((size_t)ne);
     int32_t* roff = c.off.ensure<int32_t>((size_t)ne);
-    k_request_flags<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(partner, ne, flag);
+    const int ge = grid_for(ne, B, (int64_t)c.sm_count * 16);
+    const int gn = grid_for(n, B, (int64_t)c.sm_count * 16);
+    k_request_flags<<<ge, B, 0, s>>>(partner, ne, flag);
     MSP_LAUNCH("request_flags");
-    int64_t nr = scan_exclusive(c, flag, roff, ne, s);
-    c.n_requests = nr;
+    scan_dev(c, flag, roff, &dc->n_elem, ne, &dc->n_req, nullptr, s);
     uint8_t* acc = c.accepted.ensure<uint8_t>((size_t)ne);
     MSP_CUDA(cudaMemsetAsync(acc, 0, (size_t)ne, s));
-    if (nr > 0) {
-        size_t m = (size_t)nr;
-        uint64_t* k0 = c.rq_key0.ensure<uint64_t>(m);
-        uint64_t* k1 = c.rq_key1.ensure<uint64_t>(m);
-        int32_t* v0 = c.rq_val0.ensure<int32_t>(m);
-        int32_t* v1 = c.rq_val1.ensure<int32_t>(m);
-        k_request_emit<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
-            n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff, cfg.seed, step, k0, v0);
-        MSP_LAUNCH("request_emit");
-        radix_sort(c, k0, v0, k1, v1, nr, 32 + bits_for_sel(2 * n), s);
-        k_accept<<<grid_for(nr, B, (int64_t)c.sm_count * 16), B, 0, s>>>(k0, v0, nr, vde_dev,
-                                                                         vdi_dev, acc);
-        MSP_LAUNCH("accept");
-    }
-    k_acc_flags<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(acc, ne, flag);
+    uint64_t* k0 = c.rq_key0.ensure<uint64_t>((size_t)ne);
+    uint64_t* k1 = c.rq_key1.ensure<uint64_t>((size_t)ne);
+    int32_t* v0 = c.rq_val0.ensure<int32_t>((size_t)ne);
+    int32_t* v1 = c.rq_val1.ensure<int32_t>((size_t)ne);
+    k_request_emit<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff,
+                                    cfg.seed, step, k0, v0);
+    MSP_LAUNCH("request_emit");
+    radix_sort_dev(c, k0, v0, k1, v1, &dc->n_req, ne, 32 + bits_for_sel(2 * n), s);
+    k_accept<<<ge, B, 0, s>>>(k0, v0, &dc->n_req, vde_dev, vdi_dev, acc);
+    MSP_LAUNCH("accept");
+    k_acc_flags<<<ge, B, 0, s>>>(acc, ne, flag);
     MSP_LAUNCH("acc_flags");
     int32_t* soff = c.acc_off.ensure<int32_t>((size_t)ne);
-    int64_t nsyn = scan_exclusive(c, flag, soff, ne, s);
-    c.n_synapses = nsyn;
-    k_emit_synapses<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
-        n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, acc, soff, syn_pre, syn_post,
-        syn_type);
+    scan_dev(c, flag, soff, &dc->n_elem, ne, &dc->n_syn, nullptr, s);
+    k_emit_synapses<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, acc,
+                                     soff, syn_pre, syn_post, syn_type);
     MSP_LAUNCH("emit_synapses");
-    c.small_host[4] = nsyn;
-    MSP_CUDA(cudaMemcpyAsync(n_syn, &c.small_host[4], sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MSP_CUDA(cudaMemcpyAsync(c.small_host, ctr + 2, sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaStreamSynchronize(s));
-    c.n_draws = c.small_host[0];
+    MSP_CUDA(cudaMemcpyAsync(n_syn, &dc->n_syn, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    pull_counts(c, s);              // the one synchronisation of the selection
+    const DevCounts& hc = *c.hcount;
+    if (hc.overflow & 6) throw Error(MSP_ERR_CHECK, "descent item capacity exceeded");
+    if (hc.items[n_steps % 3] != 0) throw Error(MSP_ERR_CHECK, "descent did not terminate");
+    c.n_draws = hc.draws;
+    c.n_requests = hc.n_req;
+    c.n_synapses = hc.n_syn;
 }
 
 void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde, uint8_t* vdi,

@@ -59,7 +59,9 @@ __global__ void k_u8_to_i32(const uint8_t* __restrict__ a, int64_t n, int32_t* _
 
 __global__ void k_init_root(int64_t n, uint8_t* level, uint64_t* prefix, int32_t* first,
                             int32_t* count, int32_t* parent, int32_t* child_first,
-                            uint8_t* nchild) {
+                            uint8_t* nchild, int64_t* level_start) {
+    level_start[0] = 0;
+    level_start[1] = 1;
     level[0] = 0;
     prefix[0] = 0;
     first[0] = 0;
@@ -120,12 +122,15 @@ __device__ inline OctantSplit octant_split(int64_t base, int64_t l0, int64_t nl,
     return r;
 }
 
-// number of non-empty octants of every box at this level that is split
-__global__ void k_count_children(int64_t l0, int64_t nl, int level, int leaf_capacity,
+// number of non-empty octants of every box at this level that is split; the
+// level's boxes are [lb[0], lb[1]), their count goes to *scan_n for the scan
+__global__ void k_count_children(const int64_t* __restrict__ lb, int level, int leaf_capacity,
                                  int max_depth, const uint64_t* __restrict__ keys,
                                  const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-                                 int32_t* __restrict__ cnt) {
+                                 int32_t* __restrict__ cnt, int64_t* __restrict__ scan_n) {
     const int lane = threadIdx.x & 31;
+    const int64_t l0 = lb[0], nl = lb[1] - lb[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scan_n = nl;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 4; base < nl; base += nw * 4) {
@@ -135,7 +140,8 @@ __global__ void k_count_children(int64_t l0, int64_t nl, int level, int leaf_cap
     }
 }
 
-__global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level, int leaf_capacity,
+// children of the level's boxes [lb[0], lb[1]); the next level starts at lb[1]
+__global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int leaf_capacity,
                                 int max_depth, const uint64_t* __restrict__ keys,
                                 const int32_t* __restrict__ off, uint8_t* __restrict__ nd_level,
                                 uint64_t* __restrict__ nd_prefix, int32_t* __restrict__ nd_first,
@@ -143,6 +149,7 @@ __global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level
                                 int32_t* __restrict__ nd_child_first,
                                 uint8_t* __restrict__ nd_nchild) {
     const int lane = threadIdx.x & 31, o = lane & 7;
+    const int64_t l0 = lb[0], nl = lb[1] - lb[0], next0 = lb[1];
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 4; base < nl; base += nw * 4) {
@@ -174,7 +181,7 @@ __global__ void k_emit_children(int64_t l0, int64_t nl, int64_t next0, int level
 // Box aggregates, deepest level first.  A leaf sums its points; an inner box
 // combines its children.  Centroids are accumulated as weighted offsets from
 // the box's geometric centre so that single precision keeps them accurate.
-__global__ void k_aggregate(int64_t l0, int64_t nl, int level, float ox, float oy, float oz,
+__global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox, float oy, float oz,
                             float side, const float4* __restrict__ pts,
                             const uint64_t* __restrict__ prefix, const int32_t* __restrict__ first,
                             const int32_t* __restrict__ count,
@@ -182,6 +189,7 @@ __global__ void k_aggregate(int64_t l0, int64_t nl, int level, float ox, float o
                             const uint8_t* __restrict__ nchild, int4* __restrict__ sums,
                             float4* __restrict__ ca, float4* __restrict__ cd,
                             int32_t* __restrict__ leaf_of) {
+    const int64_t l0 = lb[0], nl = lb[1] - lb[0];
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = l0 + k;
@@ -239,6 +247,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     c.attraction_done = false;
     c.n = n;
     const msp_config& cfg = c.cfg;
+    DevCounts* dc = dcounts(c);
+    dev_set(&dc->n, n, s);
     size_t nn = (size_t)(n > 0 ? n : 1);
     uint64_t* k0 = c.keys0.ensure<uint64_t>(nn);
     uint64_t* k1 = c.keys1.ensure<uint64_t>(nn);
@@ -266,75 +276,96 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         int32_t* tmp = c.cnt.ensure<int32_t>(nn);
         k_u8_to_i32<<<G, B, 0, s>>>(va, n, tmp);
         MSP_LAUNCH("u8_to_i32");
-        c.n_elem = scan_exclusive(c, tmp, eoff, n, s);
-        int32_t ne = (int32_t)c.n_elem;
-        MSP_CUDA(cudaMemcpyAsync(eoff + n, &ne, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        // the host value must outlive the copy
-        MSP_CUDA(cudaStreamSynchronize(s));
+        scan_dev(c, tmp, eoff, &dc->n, n, &dc->n_elem, nullptr, s);
+        dev_store_i32(eoff + n, &dc->n_elem, s);
     } else {
-        c.n_elem = 0;
+        dev_set(&dc->n_elem, 0, s);
     }
 
-    // a3: level-synchronous octree
-    size_t cap = (size_t)(2 * nn / (size_t)std::max(cfg.leaf_capacity, 1) + 64);
-    auto grow_nodes = [&](size_t need, size_t keep) {
-        c.nd_level.grow<uint8_t>(need, keep, s);
-        c.nd_prefix.grow<uint64_t>(need, keep, s);
-        c.nd_first.grow<int32_t>(need, keep, s);
-        c.nd_count.grow<int32_t>(need, keep, s);
-        c.nd_parent.grow<int32_t>(need, keep, s);
-        c.nd_child_first.grow<int32_t>(need, keep, s);
-        c.nd_nchild.grow<uint8_t>(need, keep, s);
-    };
-    grow_nodes(cap, 0);
-    k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
-                                c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-                                c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
-                                c.nd_nchild.get<uint8_t>());
-    MSP_LAUNCH("init_root");
-    c.level_start.assign(1, 0);
-    c.level_start.push_back(1);
-    int64_t total = 1;
+    // a3: level-synchronous octree; the level sizes stay in device memory.
+    // Levels are built down to the previous tree's depth + 1 (a first guess
+    // from n and the leaf capacity otherwise); if a box of the last built level
+    // would still split, the tree is rebuilt with all levels.
+    int L = c.depth_hint;
+    if (L < 0) {
+        L = 3;
+        for (int64_t m = std::max<int64_t>(n / std::max(cfg.leaf_capacity, 1), 1); m > 1; m >>= 3) ++L;
+    } else {
+        L += 1;
+    }
+    L = std::min(std::max(L, 0), cfg.max_depth);
+    const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
+    int32_t* cnt = c.cnt.ensure<int32_t>(nn + 8);
+    int32_t* off = c.off.ensure<int32_t>(nn + 8);
+    for (;;) {
+        // node capacity: at most min(8^l, n) boxes per level
+        int64_t cap = 0;
+        for (int l = 0; l <= L; ++l) cap += l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
+        cap += 8;
+        c.nd_level.ensure<uint8_t>((size_t)cap);
+        c.nd_prefix.ensure<uint64_t>((size_t)cap);
+        c.nd_first.ensure<int32_t>((size_t)cap);
+        c.nd_count.ensure<int32_t>((size_t)cap);
+        c.nd_parent.ensure<int32_t>((size_t)cap);
+        c.nd_child_first.ensure<int32_t>((size_t)cap);
+        c.nd_nchild.ensure<uint8_t>((size_t)cap);
+        int4* sums = c.nd_sums.ensure<int4>((size_t)cap);
+        float4* ca = c.nd_ca.ensure<float4>((size_t)cap);
+        float4* cd = c.nd_cd.ensure<float4>((size_t)cap);
+        k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
+                                    c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+                                    c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
+                                    c.nd_nchild.get<uint8_t>(), dc->level_start);
+        MSP_LAUNCH("init_root");
+        for (int l = 0; l < L; ++l) {
+            const int64_t lcap = l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
+            k_count_children<<<Gt, B, 0, s>>>(&dc->level_start[l], l, cfg.leaf_capacity,
+                                              cfg.max_depth, k0, c.nd_first.get<int32_t>(),
+                                              c.nd_count.get<int32_t>(), cnt, &dc->scan_n);
+            MSP_LAUNCH("count_children");
+            scan_dev(c, cnt, off, &dc->scan_n, lcap, &dc->level_start[l + 2],
+                     &dc->level_start[l + 1], s);
+            k_emit_children<<<Gt, B, 0, s>>>(
+                &dc->level_start[l], l, cfg.leaf_capacity, cfg.max_depth, k0, off,
+                c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
+                c.nd_count.get<int32_t>(), c.nd_parent.get<int32_t>(),
+                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>());
+            MSP_LAUNCH("emit_children");
+        }
+        // would a box of the last built level still split?
+        if (L < cfg.max_depth) {
+            k_count_children<<<Gt, B, 0, s>>>(&dc->level_start[L], L, cfg.leaf_capacity,
+                                              cfg.max_depth, k0, c.nd_first.get<int32_t>(),
+                                              c.nd_count.get<int32_t>(), cnt, &dc->scan_n);
+            MSP_LAUNCH("count_children");
+            scan_dev(c, cnt, off, &dc->scan_n, (int64_t)nn, &dc->more_levels, nullptr, s);
+        } else {
+            dev_set(&dc->more_levels, 0, s);
+        }
+        // a4: aggregates, deepest level first (empty levels are no-ops)
+        for (int l = L; l >= 0; --l) {
+            k_aggregate<<<Gt, 128, 0, s>>>(
+                &dc->level_start[l], l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
+                c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
+            MSP_LAUNCH("aggregate");
+        }
+        pull_counts(c, s);          // the one synchronisation of the build
+        if (c.hcount->more_levels > 0 && L < cfg.max_depth) {
+            L = cfg.max_depth;
+            continue;
+        }
+        break;
+    }
+    const DevCounts& hc = *c.hcount;
     int depth = 0;
-    for (int l = 0; l < cfg.max_depth && n > 0; ++l) {
-        int64_t l0 = c.level_start[l], nl = c.level_start[l + 1] - l0;
-        int32_t* cnt = c.cnt.ensure<int32_t>((size_t)nl);
-        int32_t* off = c.off.ensure<int32_t>((size_t)nl);
-        k_count_children<<<grid_for(8 * nl, B), B, 0, s>>>(l0, nl, l, cfg.leaf_capacity,
-                                                       cfg.max_depth, k0,
-                                                       c.nd_first.get<int32_t>(),
-                                                       c.nd_count.get<int32_t>(), cnt);
-        MSP_LAUNCH("count_children");
-        int64_t nnext = scan_exclusive(c, cnt, off, nl, s);
-        if (nnext == 0) break;
-        if ((size_t)(total + nnext) > c.nd_first.bytes / sizeof(int32_t))
-            grow_nodes((size_t)(total + nnext), (size_t)total);
-        k_emit_children<<<grid_for(8 * nl, B), B, 0, s>>>(
-            l0, nl, total, l, cfg.leaf_capacity, cfg.max_depth, k0, off, c.nd_level.get<uint8_t>(),
-            c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-            c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
-            c.nd_nchild.get<uint8_t>());
-        MSP_LAUNCH("emit_children");
-        total += nnext;
-        c.level_start.push_back(total);
-        depth = l + 1;
-    }
-    c.n_nodes = total;
+    for (int l = 1; l <= L; ++l)
+        if (hc.level_start[l + 1] > hc.level_start[l]) depth = l;
+    c.level_start.assign(hc.level_start, hc.level_start + depth + 2);
+    c.n_nodes = hc.level_start[depth + 1];
     c.tree_depth = depth;
-
-    // a4: aggregates, deepest level first
-    int4* sums = c.nd_sums.ensure<int4>((size_t)total);
-    float4* ca = c.nd_ca.ensure<float4>((size_t)total);
-    float4* cd = c.nd_cd.ensure<float4>((size_t)total);
-    for (int l = depth; l >= 0; --l) {
-        int64_t l0 = c.level_start[l], nl = c.level_start[l + 1] - l0;
-        k_aggregate<<<grid_for(nl, 128), 128, 0, s>>>(
-            l0, nl, l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
-            c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-            c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
-        MSP_LAUNCH("aggregate");
-    }
-    MSP_CUDA(cudaStreamSynchronize(s));
+    c.depth_hint = depth;
+    c.n_elem = hc.n_elem;
     c.tree_built = true;
 }
 
