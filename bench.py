@@ -171,14 +171,23 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(k):
+        # the same step as separate calls (one host synchronisation each)
         g.vacancy_walk(k, va, ve, vi)
         g.build_tree(pos, typ, va, ve, vi)
         g.attraction(out=u)
         g.select_partners(k, out=sel)
         g.commit_synapses(sel, va, ve, vi)
 
+    # eager warm-up: sizes the tree levels and the pair table for the graph
     for k in range(args.warmup):
         step(k)
+    torch.cuda.synchronize()
+    # the whole step as one CUDA graph, replayed once per step; its own
+    # warm-up replays, then the timed ones
+    k0 = args.warmup
+    gout = g.step_graph_capture(pos, typ, va, ve, vi, first_step=k0,
+                                history_len=args.warmup + 2 * args.steps)
+    k0 = g.run_steps(k0, args.warmup)
     torch.cuda.synchronize()
     replicas.barrier()
     torch.cuda.synchronize()
@@ -187,27 +196,46 @@ def run_ours(args, rank, world):
     launches0 = g.stats()["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    nf_ms, inter, synapses = [], [], []
     t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()                      # L2 flushed between timed steps (untimed)
-        ev[i][0].record()
-        step(args.warmup + i)
-        ev[i][1].record()
-        st = g.stats()                     # synchronises; outside the step's events
-        nf_ms.append(st["near_field_ms"])
-        inter.append(st["p2p_interactions"])
-        synapses.append(st["n_synapses"])
+    halted = 0
+    for attempt in range(2):
+        for i in range(args.steps):
+            flush.zero_()                  # L2 flushed between timed steps (untimed)
+            ev[i][0].record()
+            g.step_graph_launch(1)
+            ev[i][1].record()
+        nxt, halted = g.step_graph_finish()
+        if not halted:                     # a halted step was finished eagerly: time again
+            break
+    first_timed = nxt - args.steps
     torch.cuda.synchronize()
     replicas.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
-    launches = g.stats()["kernel_launches"] - launches0
+    st = g.stats()
+    launches = st["kernel_launches"] - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     agg = replicas.aggregate_throughput(n, sum(step_ms) / len(step_ms), dev)
     ms = agg["ms"]
     value = agg["per_s"]
+    hist = gout["history"].cpu().numpy()
+    synapses = [int(v) for v in hist[first_timed - args.warmup:nxt - args.warmup]]
+    nf_ms, inter = [st["near_field_ms"]], [st["p2p_interactions"]]
+
+    # the same steps as separate calls, for comparison
+    for k in range(nxt, nxt + 2):
+        step(k)                            # fresh build after the graph, and warm
+    torch.cuda.synchronize()
+    eager_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(nxt + 2 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        eager_ms.append(e0.elapsed_time(e1))
 
     # end to end through the public host-buffer entry point (pinned buffers)
     pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -276,7 +304,10 @@ def run_ours(args, rank, world):
                                   "100,000 um cube, sigma 750 um, 80/20 E/I, vacancies U{0..3} + walk",
                       "plan": tuned_params(), "parallelism": f"replicas x{world}",
                       "l2": "flushed (256 MB write) between timed steps",
-                      "timing": "CUDA events per step, mean over steps",
+                      "timing": "CUDA events per step (one graph replay each), mean over steps",
+                      "step_path": "whole step captured as one CUDA graph (msp_step_graph_*)",
+                      "graph_halted": int(halted),
+                      "eager_ms_per_step": round(statistics.mean(eager_ms), 3),
                       "wall_s_timed_loop": round(t_wall, 3),
                       "synapses_per_step": int(statistics.mean(synapses)),
                       **(direct or {})},

@@ -200,6 +200,62 @@ msp_status msp_commit_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t c
                                uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev,
                                void *stream);
 
+/* ---- The whole plasticity step as one CUDA graph ---------------------------
+ * A plasticity step of the 100-step run is: vacancy walk (step k), octree
+ * build (Section 3.2), attraction (Section 3.3, Eq. 6-8), selection
+ * (Algorithm 1, Algorithm 2, Section 4) with Philox step k, commit of the
+ * formed synapses.  msp_step_graph_capture records that sequence once, on
+ * the device buffers given, as a CUDA graph; msp_step_graph_launch replays
+ * it, one replay per step, with the step index kept and advanced in device
+ * memory, so a run of many steps needs no host work per step.
+ *
+ * Capture requirements: msp_build_tree and msp_attraction have run on the
+ * same positions x/y/z (their tree depth and pair-table size give the
+ * graph's capacities).  The positions and types must not change while the
+ * graph is in use (neurons do not move in the model); the vacant counts are
+ * the run's state, changed only by the graph (walk and commit).
+ *   x/y/z/type_dev     n neurons, read every replay
+ *   vac_*_dev          the state, updated in place every replay
+ *   partner_dev        capacity 5*n int32 (the walk keeps counts <= 5)
+ *   syn_*_dev          capacity syn_capacity >= 5*n
+ *   n_syn_dev          one int64: the last replay's synapse count
+ *   history_dev        optional (NULL): int64[history_len], entry i receives
+ *                      the synapse count of step first_step + i
+ *   first_step         the step index of the first replay
+ * The capture runs one dry pass (nothing of the state changes) to size the
+ * workspace, then records; it synchronises `stream`.
+ *
+ * A replay that would exceed a capacity (pair table, descent items, tree
+ * depth) sets a device-side halt flag before its commit; that step's and all
+ * later replays' walk and commit then change nothing.  msp_step_graph_finish
+ * waits for the replays, finishes a halted step eagerly (growing what
+ * overflowed), captures the graph again from the next step, and returns the
+ * index of the next step to run in *next_step (so the caller replays the
+ * remaining steps) and the halt bits in *halted (0: none).
+ * Errors: MSP_ERR_NOT_BUILT (capture before build/attraction, launch without
+ * a graph), MSP_ERR_INVALID_ARG. */
+msp_status msp_step_graph_capture(msp_ctx *ctx, int64_t n, const float *x_dev,
+                                  const float *y_dev, const float *z_dev,
+                                  const uint8_t *type_dev, uint8_t *vac_axon_dev,
+                                  uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev,
+                                  int32_t *partner_dev, int32_t *syn_pre_dev,
+                                  int32_t *syn_post_dev, uint8_t *syn_type_dev,
+                                  int64_t syn_capacity, int64_t *n_syn_dev,
+                                  int64_t *history_dev, int64_t history_len,
+                                  uint64_t first_step, void *stream);
+/* Enqueues n_steps replays on `stream`.  Asynchronous. */
+msp_status msp_step_graph_launch(msp_ctx *ctx, int64_t n_steps, void *stream);
+/* Waits for the replays (see above).  msp_get_stats then reports the last
+ * replay's sizes and, in near_field_ms and p2p_interactions, the means over
+ * the replays of the last launch.  Synchronous. */
+msp_status msp_step_graph_finish(msp_ctx *ctx, void *stream, uint64_t *next_step,
+                                 int64_t *halted);
+/* Capacity of the pair table (box pairs of the dual traversal).  The table
+ * grows on demand in the eager calls; inside the step graph it cannot, and a
+ * step that needs more halts (see above).  Values below the current use are
+ * allowed (the next eager attraction grows the table again). */
+msp_status msp_set_pair_capacity(msp_ctx *ctx, int64_t pairs);
+
 /* Sizes and counts of the last calls.  Synchronous. */
 msp_status msp_get_stats(msp_ctx *ctx, msp_stats *out);
 

@@ -20,6 +20,10 @@ void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vd
 void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const int32_t* pre,
                      const int32_t* post, const uint8_t* styp, uint8_t* va, uint8_t* vde,
                      uint8_t* vdi, cudaStream_t s);
+void graph_release(msp_ctx& c);
+void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s);
+void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s);
+void graph_finish(msp_ctx& c, cudaStream_t s, uint64_t* next_step, int64_t* halted);
 }  // namespace msp
 
 namespace {
@@ -147,6 +151,8 @@ msp_status msp_destroy(msp_ctx* c) {
     c->sd_tmp.release();
     if (c->ev_nf0) cudaEventDestroy(c->ev_nf0);
     if (c->ev_nf1) cudaEventDestroy(c->ev_nf1);
+    msp::graph_release(*c);
+    for (cudaEvent_t e : c->g_events) cudaEventDestroy(e);
     delete c;
     return MSP_OK;
 }
@@ -271,6 +277,53 @@ msp_status msp_commit_synapses(msp_ctx* c, const int64_t* n_syn, int64_t capacit
     });
 }
 
+msp_status msp_step_graph_capture(msp_ctx* c, int64_t n, const float* x, const float* y,
+                                  const float* z, const uint8_t* type, uint8_t* va, uint8_t* vde,
+                                  uint8_t* vdi, int32_t* partner, int32_t* pre, int32_t* post,
+                                  uint8_t* styp, int64_t syn_capacity, int64_t* n_syn,
+                                  int64_t* history, int64_t history_len, uint64_t first_step,
+                                  void* stream) {
+    return guarded(c, [&] {
+        require(n > 0 && n < 0x7ffffffell / msp::kMaxVacancy, "n out of range");
+        require(x && y && z && type && va && vde && vdi && partner && pre && post && styp && n_syn,
+                "null pointer");
+        require(syn_capacity >= (int64_t)msp::kMaxVacancy * n, "synapse capacity below 5*n");
+        require(history_len >= 0 && (history_len == 0 || history), "bad history buffer");
+        msp_ctx::GraphArgs g;
+        g.x = x; g.y = y; g.z = z; g.type = type;
+        g.va = va; g.vde = vde; g.vdi = vdi;
+        g.n = n;
+        g.partner = partner; g.pre = pre; g.post = post; g.styp = styp;
+        g.capacity = syn_capacity;
+        g.n_syn = n_syn;
+        g.history = history_len ? history : nullptr;
+        g.history_len = history_len;
+        g.first_step = first_step;
+        msp::graph_capture(*c, g, as_stream(stream));
+    });
+}
+
+msp_status msp_step_graph_launch(msp_ctx* c, int64_t n_steps, void* stream) {
+    return guarded(c, [&] {
+        require(n_steps >= 0, "n_steps out of range");
+        msp::graph_launch(*c, n_steps, as_stream(stream));
+    });
+}
+
+msp_status msp_step_graph_finish(msp_ctx* c, void* stream, uint64_t* next_step, int64_t* halted) {
+    return guarded(c, [&] {
+        require(next_step && halted, "null output");
+        msp::graph_finish(*c, as_stream(stream), next_step, halted);
+    });
+}
+
+msp_status msp_set_pair_capacity(msp_ctx* c, int64_t pairs) {
+    return guarded(c, [&] {
+        require(pairs >= 1 && pairs <= 0x7fffffffll, "capacity out of range");
+        c->pair_cap = pairs;
+    });
+}
+
 msp_status msp_get_stats(msp_ctx* c, msp_stats* out) {
     return guarded(c, [&] {
         require(out != nullptr, "null output");
@@ -292,7 +345,9 @@ msp_status msp_get_stats(msp_ctx* c, msp_stats* out) {
         out->expansion_nodes = c->exp_nodes;
         out->kernel_launches = msp::g_kernel_launches.load();
         out->near_field_ms = 0.0;
-        if (c->nf_timed) {
+        if (c->last_was_graph) {
+            out->near_field_ms = c->g_nf_ms_mean;
+        } else if (c->nf_timed) {
             float ms = 0.f;
             MSP_CUDA(cudaEventElapsedTime(&ms, c->ev_nf0, c->ev_nf1));
             out->near_field_ms = ms;

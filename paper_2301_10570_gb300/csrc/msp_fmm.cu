@@ -518,10 +518,17 @@ static int bits_for(int64_t v) {
 
 void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     if (!c.tree_built) throw Error(MSP_ERR_NOT_BUILT, "msp_build_tree must run first");
-    c.attraction_done = false;
+    if (!c.graph_mode) {
+        c.attraction_done = false;
+        c.last_was_graph = false;
+    }
     const msp_config& cfg = c.cfg;
     const int64_t n = c.n;
     const int B = 256;
+    // inside a stream capture the near-field events become graph nodes
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    MSP_CUDA(cudaStreamIsCapturing(s, &cst));
+    const unsigned ev_flags = cst == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     NodeView nv = node_view(c);
     Geo geo;
     for (int l = 0; l <= kMortonBits; ++l) geo.g2[l] = c.g2[l];
@@ -624,9 +631,9 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
             n, c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.leaf_of.get<int32_t>(),
             c.nd_parent.get<int32_t>(), c.nd_ca.get<float4>(), eB, us);
         MSP_LAUNCH("l2p");
-        MSP_CUDA(cudaEventRecord(c.ev_nf0, s));
+        MSP_CUDA(cudaEventRecordWithFlags(c.ev_nf0, s, ev_flags));
         launch_near_field(c, seg_first, &dc->nseg, c.n_nodes, pv0, &dc->n_p2p, cap, us, work, s);
-        MSP_CUDA(cudaEventRecord(c.ev_nf1, s));
+        MSP_CUDA(cudaEventRecordWithFlags(c.ev_nf1, s, ev_flags));
     }
     c.nf_timed = n > 0;
     // a10: pair table, deepest pairs first
@@ -641,6 +648,9 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
             us, c.perm.get<int32_t>(), n, u_dev);
         MSP_LAUNCH("scatter_u");
     }
+    // inside the whole-step graph the table does not grow: an overflow halts
+    // the graph (checked on the device after the selection)
+    if (c.graph_mode) return;
     pull_counts(c, s);              // the one synchronisation of the attraction
     const DevCounts& hc = *c.hcount;
     if (hc.overflow & 1) {

@@ -113,6 +113,24 @@ struct DevCounts {
     int64_t need_pairs;                      // largest pair-table end asked for (before clamping)
     int64_t need_items;                      // largest descent item count asked for
     int64_t scan_n;                          // element count of the next scan
+    // whole-step graph: the step index its kernels draw with, the halt flag
+    // (nonzero: a capacity was exceeded; the state-changing kernels stop) and
+    // the steps completed
+    uint64_t step;
+    int64_t halt;
+    int64_t steps_run;
+    int64_t interactions_run;                // near-field interactions over the replays
+};
+
+// the vacancy walk keeps every vacant count in [0, kMaxVacancy]
+constexpr int kMaxVacancy = 5;
+
+// The step index of the Philox counters: a value, or (inside the whole-step
+// graph) read from device memory.
+struct StepRef {
+    uint64_t v;
+    const uint64_t* p;
+    __device__ uint64_t get() const { return p ? *p : v; }
 };
 
 }  // namespace msp
@@ -166,6 +184,32 @@ struct msp_ctx {
     // copies; the selection reads them again)
     msp::DBuf c_type, c_va, c_vde, c_vdi;
     const uint8_t *in_type = nullptr, *in_va = nullptr, *in_vde = nullptr, *in_vdi = nullptr;
+    // whole-step CUDA graph (msp_graph.cu).  graph_mode: sizes come from
+    // capacity bounds and no call synchronises (set while capturing and for
+    // the dry run that sizes the buffers before it).
+    bool graph_mode = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t g_template = nullptr;
+    int64_t graph_kernels = 0;                 // kernel launches per replay
+    cudaGraphNode_t g_nf0 = nullptr, g_nf1 = nullptr;   // event records around the near field
+    std::vector<cudaEvent_t> g_events;         // two per replay of the last launch
+    int64_t g_replays = 0;                     // replays of the last launch
+    int g_left_slot = 0;                       // descent counter slot that must end empty
+    double g_nf_ms_mean = 0.0;                 // mean near-field time over them
+    bool last_was_graph = false;               // statistics come from graph replays
+    struct GraphArgs {
+        const float *x = nullptr, *y = nullptr, *z = nullptr;
+        const uint8_t* type = nullptr;
+        uint8_t *va = nullptr, *vde = nullptr, *vdi = nullptr;
+        int64_t n = 0;
+        int32_t *partner = nullptr, *pre = nullptr, *post = nullptr;
+        uint8_t* styp = nullptr;
+        int64_t capacity = 0;
+        int64_t* n_syn = nullptr;
+        int64_t* history = nullptr;
+        int64_t history_len = 0;
+        uint64_t first_step = 0;
+    } gargs;
     // host-buffer step staging
     msp::DBuf h_in[7];
     msp::DBuf h_u, h_partner, h_pre, h_post, h_type, h_nsyn;

@@ -137,14 +137,15 @@ __global__ void k_init_items(const int4* __restrict__ sums, const double2* __res
     dc->items[1] = 0;
     dc->n_leaf = 0;
     dc->draws = 0;
-    dc->overflow = 0;
+    dc->overflow &= ~6ll;       // the descent's bits; bit 0 (pair table) stays
 }
 
 __global__ void __launch_bounds__(kDescWarps * 32)
 k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
           const uint8_t* __restrict__ kind, const int32_t* __restrict__ pcf,
-          const double2* __restrict__ pw, uint64_t seed, uint64_t step, Item* __restrict__ out,
+          const double2* __restrict__ pw, uint64_t seed, StepRef stp, Item* __restrict__ out,
           int64_t cap_out, Item* __restrict__ leaf_out, int64_t cap_leaf, DescCtr ct) {
+    const uint64_t step = stp.get();
     __shared__ float sH[kDescWarps][48];
     __shared__ float sb[kDescWarps][2][kMaxP * kMaxP * kMaxP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -160,6 +161,9 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
         const bool lx = tr.child_first[X] < 0, ly = tr.child_first[Y] < 0;
         const bool split = it.q >= 0 && kind[it.q] == kSplit;
         const int32_t cf = split ? pcf[it.q] : -1;
+        // a split pair whose children did not fit in the pair table (the step
+        // is halted and redone with a larger table): nothing to read
+        if (split && cf < 0) continue;
         if (lx && ly) {
             // form_synapse: the leaf pair goes to the per-element draw
             if (lane == 0) {
@@ -233,8 +237,11 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, const int64_t* __res
                             const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
                             const float4* __restrict__ pts, const float2* __restrict__ wts,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
-                            float k2, float rc2, uint64_t seed, uint64_t step, int32_t* __restrict__ partner,
-                            unsigned long long* __restrict__ draw_ctr) {
+                            float k2, float rc2, uint64_t seed, StepRef stp,
+                            int32_t* __restrict__ partner, unsigned long long* __restrict__ draw_ctr,
+                            const int64_t* __restrict__ n_elem) {
+    const uint64_t step = stp.get();
+    const int64_t ne = *n_elem;
     // one block of kLeafWarps warps per leaf item; the warps take interleaved
     // chunks of 32 targets of the axon leaf
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -272,7 +279,7 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, const int64_t* __res
                 tot += __float2ull_rz(ldexpf(ws, shift));
             }
             const int32_t to = perm[t];
-            if (tot == 0) continue;
+            if (tot == 0 || (int64_t)eoff[to] + a > ne) continue;
             // the element draws r_e = floor(U_e * tot) (U_e with 53 bits), in
             // groups of up to 8 sorted thresholds; one prefix walk over the
             // leaf serves a whole group: the first source whose inclusive
@@ -328,8 +335,9 @@ __global__ void k_leaf_draw(const Item* __restrict__ items, const int64_t* __res
 }
 
 // requests in element order: flag, then key = (dendrite*2 + channel) << 32 | priority
-__global__ void k_request_flags(const int32_t* __restrict__ partner, int64_t n_elem,
-                                int32_t* __restrict__ flag) {
+__global__ void k_request_flags(const int32_t* __restrict__ partner,
+                                const int64_t* __restrict__ n_dev, int32_t* __restrict__ flag) {
+    const int64_t n_elem = *n_dev;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
          e += (int64_t)gridDim.x * blockDim.x)
         flag[e] = partner[e] >= 0;
@@ -338,12 +346,15 @@ __global__ void k_request_flags(const int32_t* __restrict__ partner, int64_t n_e
 __global__ void k_request_emit(int64_t n, const uint8_t* __restrict__ type,
                                const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
                                const int32_t* __restrict__ partner, const int32_t* __restrict__ roff,
-                               uint64_t seed, uint64_t step, uint64_t* __restrict__ key,
-                               int32_t* __restrict__ val) {
+                               uint64_t seed, StepRef stp, uint64_t* __restrict__ key,
+                               int32_t* __restrict__ val, const int64_t* __restrict__ n_elem) {
+    const uint64_t step = stp.get();
+    const int64_t ne = *n_elem;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         int a = va[t];
         int32_t e0 = eoff[t];
+        if ((int64_t)e0 + a > ne) continue;
         uint32_t ch = type[t] ? 1u : 0u;
         for (int k = 0; k < a; ++k) {
             int32_t s = partner[e0 + k];
@@ -374,8 +385,9 @@ __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __rest
     }
 }
 
-__global__ void k_acc_flags(const uint8_t* __restrict__ acc, int64_t n_elem,
+__global__ void k_acc_flags(const uint8_t* __restrict__ acc, const int64_t* __restrict__ n_dev,
                             int32_t* __restrict__ flag) {
+    const int64_t n_elem = *n_dev;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
          e += (int64_t)gridDim.x * blockDim.x)
         flag[e] = acc[e];
@@ -386,11 +398,13 @@ __global__ void k_emit_synapses(int64_t n, const uint8_t* __restrict__ type,
                                 const int32_t* __restrict__ partner,
                                 const uint8_t* __restrict__ acc, const int32_t* __restrict__ soff,
                                 int32_t* __restrict__ pre, int32_t* __restrict__ post,
-                                uint8_t* __restrict__ styp) {
+                                uint8_t* __restrict__ styp, const int64_t* __restrict__ n_elem) {
+    const int64_t ne = *n_elem;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         int a = va[t];
         int32_t e0 = eoff[t];
+        if ((int64_t)e0 + a > ne) continue;
         for (int k = 0; k < a; ++k) {
             if (!acc[e0 + k]) continue;
             int32_t r = soff[e0 + k];
@@ -401,8 +415,11 @@ __global__ void k_emit_synapses(int64_t n, const uint8_t* __restrict__ type,
     }
 }
 
-__global__ void k_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t* __restrict__ va,
-                       uint8_t* __restrict__ vde, uint8_t* __restrict__ vdi) {
+__global__ void k_walk(int64_t n, uint64_t seed, StepRef stp, uint8_t* __restrict__ va,
+                       uint8_t* __restrict__ vde, uint8_t* __restrict__ vdi,
+                       const int64_t* __restrict__ halt) {
+    if (halt && *halt) return;
+    const uint64_t step = stp.get();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint8_t* v[3] = {va, vde, vdi};
@@ -410,7 +427,7 @@ __global__ void k_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t* __restr
             uint32_t o[4];
             philox_draw(seed, (uint32_t)i, (uint32_t)ch | (kTagWalk << 16), step, o);
             int nv = (int)v[ch][i] + ((o[0] & 1u) ? 1 : -1);
-            nv = nv < 0 ? 0 : (nv > 5 ? 5 : nv);
+            nv = nv < 0 ? 0 : (nv > kMaxVacancy ? kMaxVacancy : nv);
             v[ch][i] = (uint8_t)nv;
         }
     }
@@ -432,7 +449,9 @@ __device__ inline void sat_dec(uint8_t* p) {
 
 __global__ void k_commit(const int64_t* __restrict__ n_syn, int64_t capacity,
                          const int32_t* __restrict__ pre, const int32_t* __restrict__ post,
-                         const uint8_t* __restrict__ styp, uint8_t* va, uint8_t* vde, uint8_t* vdi) {
+                         const uint8_t* __restrict__ styp, uint8_t* va, uint8_t* vde, uint8_t* vdi,
+                         const int64_t* __restrict__ halt) {
+    if (halt && *halt) return;
     int64_t m = *n_syn;
     if (m > capacity) m = capacity;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
@@ -442,7 +461,8 @@ __global__ void k_commit(const int64_t* __restrict__ n_syn, int64_t capacity,
     }
 }
 
-__global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v) {
+__global__ void k_fill_i32(int32_t* __restrict__ p, const int64_t* __restrict__ n_dev, int32_t v) {
+    const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
@@ -462,7 +482,10 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
                      cudaStream_t s) {
     if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
     const msp_config& cfg = c.cfg;
-    const int64_t n = c.n, ne = c.n_elem;
+    // the element count: exact from the build, or (whole-step graph) the
+    // bound that the vacancy walk keeps; kernels read the exact count from
+    // device memory and never index past it
+    const int64_t n = c.n, ne = c.graph_mode ? (int64_t)kMaxVacancy * n : c.n_elem;
     const int B = 256;
     const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
     // inside a leaf the kernel is truncated at the radius that prunes box pairs
@@ -470,10 +493,13 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     c.n_draws = c.n_requests = c.n_synapses = 0;
     if (ne == 0) {
         MSP_CUDA(cudaMemsetAsync(n_syn, 0, sizeof(int64_t), s));
-        MSP_CUDA(cudaStreamSynchronize(s));
+        if (!c.graph_mode) MSP_CUDA(cudaStreamSynchronize(s));
         return;
     }
-    k_fill_i32<<<grid_for(ne, B, (int64_t)c.sm_count * 16), B, 0, s>>>(partner, ne, -1);
+    DevCounts* dc = dcounts(c);
+    const StepRef stp{step, c.graph_mode ? &dc->step : nullptr};
+    const int ge = grid_for(ne, B, (int64_t)c.sm_count * 16);
+    k_fill_i32<<<ge, B, 0, s>>>(partner, &dc->n_elem, -1);
     MSP_LAUNCH("fill_partner");
 
     Tree tr;
@@ -499,7 +525,6 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     const int64_t cap_items = 2 * c.n_nodes + 64, cap_leaf = 2 * c.n_nodes + 64;
     Item* ib[2] = {c.items0.ensure<Item>((size_t)cap_items), c.items1.ensure<Item>((size_t)cap_items)};
     Item* lit = c.leaf_items.ensure<Item>((size_t)cap_leaf);
-    DevCounts* dc = dcounts(c);
     k_init_items<<<1, 1, 0, s>>>(c.nd_sums.get<int4>(), c.pr_w.get<double2>(), ib[0], dc);
     MSP_LAUNCH("init_items");
     auto ull = [](int64_t* p) { return reinterpret_cast<unsigned long long*>(p); };
@@ -515,7 +540,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         ct.overflow = ull(&dc->overflow);
         k_descend<<<gd, kDescWarps * 32, 0, s>>>(ib[k & 1], tr, ex, c.pr_kind.get<uint8_t>(),
                                                  c.pr_cf.get<int32_t>(), c.pr_w.get<double2>(),
-                                                 cfg.seed, step, ib[(k + 1) & 1], cap_items, lit,
+                                                 cfg.seed, stp, ib[(k + 1) & 1], cap_items, lit,
                                                  cap_leaf, ct);
         MSP_LAUNCH("descend");
     }
@@ -523,15 +548,14 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     k_leaf_draw<<<(unsigned)std::min<int64_t>(cap_leaf, 1 << 30), 128, 0, s>>>(
         lit, &dc->n_leaf, cap_leaf, c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
         c.pts.get<float4>(), c.wts.get<float2>(), c.perm.get<int32_t>(),
-        c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, step, partner, ull(&dc->draws));
+        c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, stp, partner, ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
 
     // a12: requests, sorted by (dendrite, channel, priority, element)
     int32_t* flag = c.cnt.ensure<int32_t>((size_t)ne);
     int32_t* roff = c.off.ensure<int32_t>((size_t)ne);
-    const int ge = grid_for(ne, B, (int64_t)c.sm_count * 16);
     const int gn = grid_for(n, B, (int64_t)c.sm_count * 16);
-    k_request_flags<<<ge, B, 0, s>>>(partner, ne, flag);
+    k_request_flags<<<ge, B, 0, s>>>(partner, &dc->n_elem, flag);
     MSP_LAUNCH("request_flags");
     scan_dev(c, flag, roff, &dc->n_elem, ne, &dc->n_req, nullptr, s);
     uint8_t* acc = c.accepted.ensure<uint8_t>((size_t)ne);
@@ -541,19 +565,24 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     int32_t* v0 = c.rq_val0.ensure<int32_t>((size_t)ne);
     int32_t* v1 = c.rq_val1.ensure<int32_t>((size_t)ne);
     k_request_emit<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff,
-                                    cfg.seed, step, k0, v0);
+                                    cfg.seed, stp, k0, v0, &dc->n_elem);
     MSP_LAUNCH("request_emit");
     radix_sort_dev(c, k0, v0, k1, v1, &dc->n_req, ne, 32 + bits_for_sel(2 * n), s);
     k_accept<<<ge, B, 0, s>>>(k0, v0, &dc->n_req, vde_dev, vdi_dev, acc);
     MSP_LAUNCH("accept");
-    k_acc_flags<<<ge, B, 0, s>>>(acc, ne, flag);
+    k_acc_flags<<<ge, B, 0, s>>>(acc, &dc->n_elem, flag);
     MSP_LAUNCH("acc_flags");
     int32_t* soff = c.acc_off.ensure<int32_t>((size_t)ne);
     scan_dev(c, flag, soff, &dc->n_elem, ne, &dc->n_syn, nullptr, s);
     k_emit_synapses<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, acc,
-                                     soff, syn_pre, syn_post, syn_type);
+                                     soff, syn_pre, syn_post, syn_type, &dc->n_elem);
     MSP_LAUNCH("emit_synapses");
     MSP_CUDA(cudaMemcpyAsync(n_syn, &dc->n_syn, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (c.graph_mode) {
+        // checked on the device at the end of the graph's step
+        c.g_left_slot = n_steps % 3;
+        return;
+    }
     pull_counts(c, s);              // the one synchronisation of the selection
     const DevCounts& hc = *c.hcount;
     if (hc.overflow & 6) throw Error(MSP_ERR_CHECK, "descent item capacity exceeded");
@@ -566,8 +595,10 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
 void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde, uint8_t* vdi,
                   cudaStream_t s) {
     if (n <= 0) return;
-    k_walk<<<grid_for(n, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(n, c.cfg.seed, step, va,
-                                                                        vde, vdi);
+    DevCounts* dc = dcounts(c);
+    const StepRef stp{step, c.graph_mode ? &dc->step : nullptr};
+    k_walk<<<grid_for(n, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
+        n, c.cfg.seed, stp, va, vde, vdi, c.graph_mode ? &dc->halt : nullptr);
     MSP_LAUNCH("walk");
 }
 
@@ -576,7 +607,8 @@ void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const i
                      uint8_t* vdi, cudaStream_t s) {
     if (capacity <= 0) return;
     k_commit<<<grid_for(capacity, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
-        n_syn, capacity, pre, post, styp, va, vde, vdi);
+        n_syn, capacity, pre, post, styp, va, vde, vdi,
+        c.graph_mode ? &dcounts(c)->halt : nullptr);
     MSP_LAUNCH("commit");
 }
 

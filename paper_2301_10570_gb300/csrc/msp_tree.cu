@@ -243,8 +243,10 @@ __global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox,
 void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const float* z,
                 const uint8_t* type, const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
                 cudaStream_t s) {
-    c.tree_built = false;
-    c.attraction_done = false;
+    if (!c.graph_mode) {
+        c.tree_built = false;
+        c.attraction_done = false;
+    }
     c.n = n;
     const msp_config& cfg = c.cfg;
     DevCounts* dc = dcounts(c);
@@ -350,6 +352,9 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
                 c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
             MSP_LAUNCH("aggregate");
         }
+        // inside the whole-step graph the tree of the same positions has the
+        // same levels; a deeper one sets more_levels, which halts the graph
+        if (c.graph_mode) return;
         pull_counts(c, s);          // the one synchronisation of the build
         if (c.hcount->more_levels > 0 && L < cfg.max_depth) {
             L = cfg.max_depth;

@@ -29,7 +29,10 @@ STATUS = {0: "MSP_OK", 1: "MSP_ERR_INVALID_ARG", 2: "MSP_ERR_CUDA", 3: "MSP_ERR_
 EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "msp_direct",
             "msp_select_partners", "msp_plasticity_step_host", "msp_vacancy_walk",
             "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
-            "msp_export_expansions", "msp_last_error", "msp_direct_noalloc")
+            "msp_export_expansions", "msp_last_error", "msp_direct_noalloc",
+            "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
+            "msp_set_pair_capacity")
+MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
 
@@ -83,6 +86,13 @@ def load(path: str = LIB_PATH):
         L.msp_last_error.restype = C.c_char_p
         L.msp_direct_noalloc.argtypes = [i64] + [vp] * 7 + [C.c_double, vp, vp]
         L.msp_direct_noalloc.restype = C.c_int
+        L.msp_step_graph_capture.argtypes = [vp, i64] + [vp] * 11 + [i64, vp, vp, i64, u64, vp]
+        L.msp_step_graph_launch.argtypes = [vp, i64, vp]
+        L.msp_step_graph_finish.argtypes = [vp, vp, C.POINTER(u64), C.POINTER(i64)]
+        L.msp_set_pair_capacity.argtypes = [vp, i64]
+        for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
+                     "msp_set_pair_capacity"):
+            getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
                      "msp_vacancy_walk", "msp_commit_synapses", "msp_get_stats",
@@ -238,6 +248,59 @@ class MSP:
                                           _ptr(sel["syn_pre"]), _ptr(sel["syn_post"]),
                                           _ptr(sel["syn_type"]), _ptr(vac_axon),
                                           _ptr(vac_dend_e), _ptr(vac_dend_i), _stream(stream)))
+
+    # -- the whole step as a CUDA graph ---------------------------------------
+    def step_graph_capture(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, first_step,
+                           history_len=0, stream=None):
+        """Captures walk + build + attraction + selection + commit on these CUDA
+        tensors (the vacant counts are updated in place by every replay).
+        build_tree and attraction must have run on the same positions.  Returns
+        the output tensors the replays write."""
+        pos = pos.contiguous()
+        n = int(pos.shape[1])
+        cap = max(MAX_VACANCY * n, 1)
+        dev = pos.device
+        xs = [pos[0].contiguous(), pos[1].contiguous(), pos[2].contiguous()]
+        st = [type_.contiguous(), vac_axon, vac_dend_e, vac_dend_i]
+        for t in st[1:]:
+            if not t.is_contiguous():
+                raise ValueError("vacant counts must be contiguous (updated in place)")
+        out = dict(partner=torch.empty(cap, dtype=torch.int32, device=dev),
+                   syn_pre=torch.empty(cap, dtype=torch.int32, device=dev),
+                   syn_post=torch.empty(cap, dtype=torch.int32, device=dev),
+                   syn_type=torch.empty(cap, dtype=torch.uint8, device=dev),
+                   n_syn=torch.zeros(1, dtype=torch.int64, device=dev),
+                   history=torch.full((max(int(history_len), 1),), -1, dtype=torch.int64,
+                                      device=dev))
+        self._graph_inputs = xs + st + [out]
+        _check(load().msp_step_graph_capture(
+            self._h, n, *[_ptr(t) for t in xs], *[_ptr(t) for t in st], _ptr(out["partner"]),
+            _ptr(out["syn_pre"]), _ptr(out["syn_post"]), _ptr(out["syn_type"]), cap,
+            _ptr(out["n_syn"]), _ptr(out["history"]) if history_len else None, int(history_len),
+            int(first_step), _stream(stream)))
+        return out
+
+    def step_graph_launch(self, n_steps, stream=None):
+        _check(load().msp_step_graph_launch(self._h, int(n_steps), _stream(stream)))
+
+    def step_graph_finish(self, stream=None):
+        """Waits for the replays; returns (next step index, halt bits)."""
+        nxt, halted = C.c_uint64(0), C.c_int64(0)
+        _check(load().msp_step_graph_finish(self._h, _stream(stream), C.byref(nxt),
+                                            C.byref(halted)))
+        return int(nxt.value), int(halted.value)
+
+    def run_steps(self, first_step, n_steps, stream=None):
+        """Replays the captured step until steps first_step .. first_step+n_steps-1
+        have run (a halted step is finished eagerly and the graph re-captured)."""
+        step, end = int(first_step), int(first_step) + int(n_steps)
+        while step < end:
+            self.step_graph_launch(end - step, stream)
+            step, _ = self.step_graph_finish(stream)
+        return step
+
+    def set_pair_capacity(self, pairs):
+        _check(load().msp_set_pair_capacity(self._h, int(pairs)))
 
     # -- introspection ------------------------------------------------------
     def stats(self) -> dict:

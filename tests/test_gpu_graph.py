@@ -1,0 +1,155 @@
+"""The whole plasticity step as one CUDA graph (walk, build, attraction,
+selection, commit) against the same steps issued as separate eager calls.
+
+Both sides run the same kernels; the graph takes its launch shapes from
+capacity bounds and its step index from device memory, neither of which
+changes a result, so the per-step synapse counts, the final vacancy state
+and the last step's partners and synapse lists must be identical.  The halt
+test forces a pair-table overflow inside a replay (a capacity far below the
+pairs of a step with vacancies) and checks that the halted step is finished
+eagerly with the same result.
+"""
+import numpy as np
+import pytest
+
+from paper_2301_10570_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_10570_gb300 import msp  # noqa: E402
+
+
+def _state(w):
+    pos, t, a, e, i = msp.to_device(w)
+    return pos, t, a.clone(), e.clone(), i.clone()
+
+
+def _eager(w, first, k_steps):
+    """Steps first .. first+k_steps-1 as separate calls; returns per-step
+    synapse counts, the final state and the last step's selection."""
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    counts = []
+    sel = None
+    for k in range(first, first + k_steps):
+        g.vacancy_walk(k, a, e, i)
+        g.build_tree(pos, t, a, e, i)
+        g.attraction()
+        sel = g.select_partners(k)
+        g.commit_synapses(sel, a, e, i)
+        counts.append(int(sel["n_syn"].item()))
+    ne = g.num_elements()
+    last = dict(partner=sel["partner"][:ne].cpu().numpy(), n_syn=counts[-1],
+                pre=sel["syn_pre"][:counts[-1]].cpu().numpy(),
+                post=sel["syn_post"][:counts[-1]].cpu().numpy(),
+                typ=sel["syn_type"][:counts[-1]].cpu().numpy())
+    g.close()
+    return counts, [v.cpu().numpy() for v in (a, e, i)], last
+
+
+def _graph(w, first, k_steps, pair_capacity=None, manual=False):
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    if pair_capacity is not None:
+        g.set_pair_capacity(pair_capacity)
+    out = g.step_graph_capture(pos, t, a, e, i, first_step=first, history_len=k_steps)
+    halts = []
+    if manual:
+        step, end = first, first + k_steps
+        while step < end:
+            g.step_graph_launch(end - step)
+            step, h = g.step_graph_finish()
+            halts.append(h)
+    else:
+        assert g.run_steps(first, k_steps) == first + k_steps
+    st = g.stats()
+    counts = out["history"].cpu().numpy().tolist()
+    ns = counts[-1]
+    last = dict(n_syn=ns, pre=out["syn_pre"][:ns].cpu().numpy(),
+                post=out["syn_post"][:ns].cpu().numpy(), typ=out["syn_type"][:ns].cpu().numpy(),
+                partner_all=out["partner"].cpu().numpy(), n_elem=st["n_elements"])
+    res = (counts, [v.cpu().numpy() for v in (a, e, i)], last, st, halts)
+    g.close()
+    return res
+
+
+def _workload():
+    return W.clustered_small(2, 2048, seed=11, leaf_capacity=32)
+
+
+def test_graph_replays_equal_eager_steps():
+    w = _workload()
+    k_steps = 6
+    ce, se, le = _eager(w, 3, k_steps)
+    cg, sg, lg, st, _ = _graph(w, 3, k_steps)
+    assert cg == ce
+    for x, y in zip(sg, se):
+        assert np.array_equal(x, y)
+    assert lg["n_elem"] == len(le["partner"])
+    assert np.array_equal(lg["partner_all"][:lg["n_elem"]], le["partner"])
+    for key in ("pre", "post", "typ"):
+        assert np.array_equal(lg[key], le[key])
+    assert st["near_field_ms"] > 0.0 and st["p2p_interactions"] > 0
+
+
+def test_graph_halt_finishes_the_step_eagerly():
+    # no vacant axons at capture: the dry run needs one pair, so a capacity of
+    # 8 pairs fits it; the first replay's walk gives axons and overflows it
+    w = _workload()
+    w.vac_axon[:] = 0
+    k_steps = 4
+    ce, se, _ = _eager(w, 0, k_steps)
+    cg, sg, _, _, halts = _graph(w, 0, k_steps, pair_capacity=8, manual=True)
+    assert halts and halts[0] & 1, halts          # pair-table overflow reported
+    assert cg == ce
+    for x, y in zip(sg, se):
+        assert np.array_equal(x, y)
+
+
+def test_graph_counts_its_kernel_launches():
+    w = _workload()
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    g.step_graph_capture(pos, t, a, e, i, first_step=0)
+    k0 = g.stats()["kernel_launches"]
+    g.step_graph_launch(3)
+    nxt, halted = g.step_graph_finish()
+    assert (nxt, halted) == (3, 0)
+    per = (g.stats()["kernel_launches"] - k0) / 3
+    assert per > 50 and per == int(per)
+    g.close()
+
+
+def test_graph_call_order_errors():
+    w = _workload()
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    with pytest.raises(msp.MSPError):
+        g.step_graph_capture(pos, t, a, e, i, first_step=0)     # no build yet
+    with pytest.raises(msp.MSPError):
+        g.step_graph_launch(1)                                  # nothing captured
+    with pytest.raises(msp.MSPError):
+        g.set_pair_capacity(0)
+    g.close()
+
+
+def test_full_size_graph_replays_equal_eager_steps():
+    """The benchmark workload (1,048,576 neurons) in the configuration the
+    benchmark times: two graph replays against the same two eager steps."""
+    import bench
+    w = bench.workload()
+    ce, se, le = _eager(w, 5, 2)
+    cg, sg, lg, _, _ = _graph(w, 5, 2)
+    assert cg == ce
+    for x, y in zip(sg, se):
+        assert np.array_equal(x, y)
+    for key in ("pre", "post", "typ"):
+        assert np.array_equal(lg[key], le[key])
