@@ -136,7 +136,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
                          &c->pr_kind, &c->pr_cf, &c->pr_w, &c->far_q, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
-                         &c->nf_w32,
+                         &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
                          &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,

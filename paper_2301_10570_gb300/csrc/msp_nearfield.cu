@@ -2,18 +2,22 @@
 // near-field leaf pairs of the dual traversal, which dominates the step.
 //
 // Work unit: one target leaf X (one block of 4 warps) and all its partner
-// leaves Y (a contiguous segment of the pair list sorted by X).  The block
-// first collects the targets of X with vacant axons (up to 64 per pass); the
-// warps then take the partner pairs round-robin.  Each warp stages the sources
-// of its current pair in its own shared memory and every lane evaluates them
-// against its targets:
+// leaves Y (a contiguous segment of the pair list sorted by X).  Blocks take
+// the segments longest first (the order comes from an estimate of each
+// segment's work), so the last wave of blocks is short.  The block collects
+// the targets of X with vacant axons, up to 128 at a time, excitatory ones
+// first (their count padded to even), and evaluates them in passes of up to
+// 64; the warps take the partner pairs round-robin.  Each warp stages the
+// sources of its current pair in its own shared memory and every lane
+// evaluates them against its targets:
 //   up to 32 targets: padded to T = 2^k, 32/T lanes per target walking
 //                     interleaved slices of the sources (small leaves still
 //                     fill the warp);
-//   33..64 targets:   2 targets per lane, every lane walks all sources (each
-//                     staged source is used twice).
+//   33..64 targets:   2 targets per lane, both of one channel (the E-first
+//                     order with even padding guarantees it), so one staged
+//                     source serves both with one shared-memory load.
 // Capping a pass at 64 targets keeps the kernel at 64 registers (8 blocks of
-// 4 warps per SM); larger leaves take several passes.
+// 4 warps per SM).
 // The per-target sums of the 4 warps are added in a fixed order, so u is
 // reproducible run to run.  Per pair, the warp reduces the box-pair
 // attraction W(X,Y) = sum_t a_t sum_s w_s K(t,s) of each channel in single
@@ -25,8 +29,10 @@
 //   w_s K(t,s) = 2^( 2 t^.s^ - |s^|^2 + log2 w_s ) * 2^(-|t^|^2),
 // so a source is staged once per warp as (s^, -|s^|^2 + log2 w_s) for each
 // channel and one evaluation is three FMAs, one EX2 on the SFU and one add.
-// For leaves wider than about 2 sigma the expanded exponent could overflow,
-// and the difference form (s^, log2 w_s) with |t^ - s^|^2 is used instead.
+// The first factor is at most 2^(|t^|^2 + 8), so the expanded form is used
+// while |t^|^2 <= 20 for every target of X (leaves up to about 4.3 sigma
+// wide; the exponent's rounding then stays near 1e-6 relative); wider leaves
+// use the difference form (s^, log2 w_s) with |t^ - s^|^2.
 #include <algorithm>
 #include <cmath>
 
@@ -44,6 +50,8 @@ __shared__ int32_t* s_wii;
 constexpr int kNFWarps = 4;
 constexpr int kNFStage = 64;
 constexpr int kNFMaxT = 32 * 2;    // targets per pass (at most 2 per lane: 64 registers)
+constexpr int kNFList = 128;       // targets collected per round
+constexpr float kNFFastT2 = 20.f;  // largest |t^|^2 of the expanded form
 
 __device__ inline float nf_ex2(float x) {
     float y;
@@ -54,6 +62,7 @@ __device__ inline float nf_ex2(float x) {
 struct NFArgs {
     const int32_t* seg_first;
     const int64_t* nseg;         // segment count (device memory)
+    const int32_t* order;        // segments, longest first
     const int32_t* list_q;
     const int32_t* pX;
     const int32_t* pY;
@@ -69,59 +78,60 @@ struct NFArgs {
     unsigned long long* work;
 };
 
-// one target of a lane
-struct Tgt {
-    float x, y, z;     // 2 t^ (expanded form) or t^ (difference form)
-    float scale;       // 2^(-|t^|^2) or 1
-    float fa;          // a_t * scale, 0 for padding
-    int32_t t;         // sorted index, -1 for padding
-    int ch;            // 0 excitatory, 1 inhibitory
+// the targets of a lane (R of them, one channel)
+template <int R>
+struct Tgts {
+    float x[R], y[R], z[R];   // 2 t^ (expanded form) or t^ (difference form)
+    float scale[R];           // 2^(-|t^|^2) or 1
+    float fa[R];              // a_t * scale, 0 for padding
+    int32_t t[R];             // sorted index, -1 for padding
+    int ch;                   // 0 excitatory, 1 inhibitory
 };
 
 // Evaluate the staged sources [0, m) (lane slice ksl of `slices`) against the
 // lane's R targets.  MODE 0: expanded exponent; 1: expanded, skipping the
-// target itself; 2: difference form, skipping the target itself.
+// target itself; 2: difference form; 3: difference form, skipping the target.
 template <int R, int MODE>
 __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int slices,
-                                        const Tgt (&tg)[R], int32_t base, float (&part)[R]) {
-    constexpr int U = R == 1 ? 4 : (R == 2 ? 2 : 1);
+                                        const Tgts<R>& tg, int32_t base, float (&part)[R]) {
+    constexpr int U = R == 1 ? 4 : 2;
     float p[R][U];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int v = 0; v < U; ++v) p[r][v] = 0.f;
+    const float4* sc = st + tg.ch;
     int e = ksl;
     if (MODE == 0) {
         for (; e + (U - 1) * slices < m; e += U * slices) {
 #pragma unroll
             for (int v = 0; v < U; ++v) {
+                const float4 A = sc[2 * (e + v * slices)];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float4 A = st[2 * (e + v * slices) + tg[r].ch];
-                    p[r][v] += nf_ex2(fmaf(tg[r].x, A.x, fmaf(tg[r].y, A.y, fmaf(tg[r].z, A.z, A.w))));
-                }
+                for (int r = 0; r < R; ++r)
+                    p[r][v] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
             }
         }
         for (; e < m; e += slices) {
+            const float4 A = sc[2 * e];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float4 A = st[2 * e + tg[r].ch];
-                p[r][0] += nf_ex2(fmaf(tg[r].x, A.x, fmaf(tg[r].y, A.y, fmaf(tg[r].z, A.z, A.w))));
-            }
+            for (int r = 0; r < R; ++r)
+                p[r][0] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
         }
     } else {
         for (; e < m; e += slices) {
+            const float4 A = sc[2 * e];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float4 A = st[2 * e + tg[r].ch];
                 float v;
-                if (MODE == 1) {
-                    v = nf_ex2(fmaf(tg[r].x, A.x, fmaf(tg[r].y, A.y, fmaf(tg[r].z, A.z, A.w))));
+                if (MODE == 0 || MODE == 1) {
+                    v = nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
                 } else {
-                    float dx = tg[r].x - A.x, dy = tg[r].y - A.y, dz = tg[r].z - A.z;
+                    const float dx = tg.x[r] - A.x, dy = tg.y[r] - A.y, dz = tg.z[r] - A.z;
                     v = nf_ex2(A.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 }
-                p[r][0] += base + e == tg[r].t ? 0.f : v;
+                if (MODE == 1 || MODE == 3) v = base + e == tg.t[r] ? 0.f : v;
+                p[r][0] += v;
             }
         }
     }
@@ -138,8 +148,8 @@ __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int sl
 template <int R>
 __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1, int32_t tf,
                                          bool fast, float cx, float cy, float cz, int ksl,
-                                         int slices, const Tgt (&tg)[R], float (&acc)[R],
-                                         float4* stw, unsigned long long& evals, int nt) {
+                                         int slices, const Tgts<R>& tg, float (&acc)[R],
+                                         float4* stw, unsigned long long& evals, int nreal) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 (*wt)[33] = reinterpret_cast<float2 (*)[33]>(s_wt + w * 16 * 33);
     int32_t* wii = s_wii + w * 16;
@@ -172,25 +182,25 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                     stw[2 * e + 1] = make_float4(sx, sy, sz, n2 + L.y);
                 }
                 __syncwarp();
-                if (fast && !self)
-                    nf_eval<R, 0>(stw, m, ksl, slices, tg, sf + sb, part);
-                else if (fast)
-                    nf_eval<R, 1>(stw, m, ksl, slices, tg, sf + sb, part);
-                else
-                    nf_eval<R, 2>(stw, m, ksl, slices, tg, sf + sb, part);
+                if (fast) {
+                    if (self) nf_eval<R, 1>(stw, m, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval<R, 0>(stw, m, ksl, slices, tg, sf + sb, part);
+                } else {
+                    if (self) nf_eval<R, 3>(stw, m, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval<R, 2>(stw, m, ksl, slices, tg, sf + sb, part);
+                }
             }
-            float vE = 0.f, vI = 0.f;
+            float v = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 acc[k] += part[k];
-                float v = tg[k].fa * part[k];
-                if (tg[k].ch) vI += v; else vE += v;
+                v = fmaf(tg.fa[k], part[k], v);
             }
             // W(X,Y) of each channel: every lane's term goes into a transposed
             // buffer; every 16 pairs the warp sums the rows (half a row per
             // lane, then one shuffle) and adds them to the pairs' slots
             const int slot = r & 15;
-            wt[slot][lane] = make_float2(vE, vI);
+            wt[slot][lane] = tg.ch ? make_float2(0.f, v) : make_float2(v, 0.f);
             if (lane == 0) wii[slot] = ii;
             if (slot == 15 || r == nb - 1) {
                 __syncwarp();
@@ -211,16 +221,18 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 }
                 __syncwarp();
             }
-            evals += (unsigned long long)sc * (unsigned long long)nt;
+            evals += (unsigned long long)sc * (unsigned long long)nreal;
         }
     }
 }
 
+// one pass over the targets tl[0, nt) (nt <= 64; tl[k] < 0 is padding);
+// nreal of them are real
 template <int R>
-__device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, int nt, int32_t i0,
-                                           int32_t i1, int32_t tf, bool fast, float cx, float cy,
-                                           float cz, float4* stw, float (*red)[kNFMaxT],
-                                           unsigned long long& evals) {
+__device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, int nt, int nreal,
+                                           int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
+                                           float cy, float cz, float4* stw,
+                                           float (*red)[kNFMaxT], unsigned long long& evals) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0, ntp = 32;
     if (R == 1) {
@@ -230,44 +242,51 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
     const int slices = R == 1 ? 32 >> lg : 1;
     const int j = R == 1 ? (lane & (ntp - 1)) : lane;
     const int ksl = R == 1 ? lane >> lg : 0;
-    Tgt tg[R];
+    // slot of target r of this lane: j (R = 1) or 2j + r (R = 2)
+    Tgts<R> tg;
     float acc[R];
+    {
+        // the channel of the lane's first slot (both slots share it)
+        const int s0 = R == 1 ? j : 2 * j;
+        const int32_t t0 = s0 < nt ? tl[s0] : -1;
+        tg.ch = t0 >= 0 ? (pk_type(__float_as_uint(a.pts[t0].w)) ? 1 : 0) : 0;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int slot = j + 32 * r;
-        const bool valid = slot < nt;
-        const int32_t t = valid ? tl[slot] : tl[0];
+        const int slot = R == 1 ? j : 2 * j + r;
+        const int32_t ts = slot < nt ? tl[slot] : -1;
+        const bool valid = ts >= 0;
+        const int32_t t = valid ? ts : tl[0];          // tl[0] is always a real target
         const float4 T = a.pts[t];
         const uint32_t tw = __float_as_uint(T.w);
         const float hx = (T.x - cx) * a.sqk, hy = (T.y - cy) * a.sqk, hz = (T.z - cz) * a.sqk;
-        tg[r].x = fast ? 2.f * hx : hx;
-        tg[r].y = fast ? 2.f * hy : hy;
-        tg[r].z = fast ? 2.f * hz : hz;
-        tg[r].scale = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
-        tg[r].fa = valid ? (float)pk_axon(tw) * tg[r].scale : 0.f;
-        tg[r].t = valid ? t : -1;
-        tg[r].ch = pk_type(tw) ? 1 : 0;
+        tg.x[r] = fast ? 2.f * hx : hx;
+        tg.y[r] = fast ? 2.f * hy : hy;
+        tg.z[r] = fast ? 2.f * hz : hz;
+        tg.scale[r] = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
+        tg.fa[r] = valid ? (float)pk_axon(tw) * tg.scale[r] : 0.f;
+        tg.t[r] = valid ? t : -1;
         acc[r] = 0.f;
     }
-    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nt);
+    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nreal);
     // slices of a target (R == 1), then the 4 warps in a fixed order
 #pragma unroll
     for (int r = 0; r < R; ++r)
         for (int o = ntp; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     if (ksl == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) red[w][j + 32 * r] = acc[r];
+        for (int r = 0; r < R; ++r) red[w][R == 1 ? j : 2 * j + r] = acc[r];
     }
     __syncthreads();
     if (w == 0 && ksl == 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int slot = j + 32 * r;
-            if (slot < nt) {
+            const int slot = R == 1 ? j : 2 * j + r;
+            if (tg.t[r] >= 0) {
                 float s = red[0][slot];
 #pragma unroll
                 for (int k = 1; k < kNFWarps; ++k) s += red[k][slot];
-                a.u[tg[r].t] += s * tg[r].scale;
+                a.u[tg.t[r]] += s * tg.scale[r];
             }
         }
     }
@@ -277,8 +296,8 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
 __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
     __shared__ float4 st[kNFWarps][2 * kNFStage];
     __shared__ float red[kNFWarps][kNFMaxT];
-    __shared__ int32_t tl[kNFMaxT];
-    __shared__ int s_nt, s_pos;
+    __shared__ int32_t tl[kNFList];
+    __shared__ int s_nt, s_nreal, s_pos;
     __shared__ float2 wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
     s_wt = &wt_all[0][0][0];
@@ -286,7 +305,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stw = st[w];
     const int64_t nseg = *a.nseg;
-    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    for (int64_t b = blockIdx.x; b < nseg; b += gridDim.x) {
+        const int32_t sg = a.order[b];
         const int32_t i0 = a.seg_first[sg], i1 = a.seg_first[sg + 1];
         const int32_t X = a.pX[a.list_q[i0]];
         const int32_t tf = a.nfirst[X], tc = a.ncount[X];
@@ -295,55 +315,109 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
         const float cx = a.ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs;
         const float cy = a.oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs;
         const float cz = a.oz + ((float)compact_by3(pre) + 0.5f) * bs;
-        // the expanded exponent needs |t^|^2 <= 4 for every target of X
-        const bool fast = 0.75f * a.sqk * a.sqk * bs * bs <= 4.f;
+        // the expanded exponent needs |t^|^2 <= kNFFastT2 for every target of X
+        const bool fast = 0.75f * a.sqk * a.sqk * bs * bs <= kNFFastT2;
         unsigned long long evals = 0;
         int32_t pos = 0;
         for (;;) {
-            // warp 0 collects up to 128 targets with vacant axons, from pos on
+            // warp 0 collects up to kNFList - 1 targets with vacant axons from
+            // pos on: first walk counts them per channel and finds where the
+            // round ends, second walk writes the excitatory ones, a padding
+            // entry if their count is odd and inhibitory ones follow, then the
+            // inhibitory ones
             if (w == 0) {
-                int nt = 0;
+                int nt = 0, nE = 0;
                 int32_t p = pos;
-                while (p < tc && nt < kNFMaxT) {
+                while (p < tc && nt < kNFList - 1) {
                     const int32_t t = tf + p + lane;
-                    const bool act = p + lane < tc && pk_axon(__float_as_uint(a.pts[t].w)) > 0;
+                    const uint32_t tw = p + lane < tc ? __float_as_uint(a.pts[t].w) : 0u;
+                    const bool act = pk_axon(tw) > 0;
                     const unsigned mask = __ballot_sync(0xffffffffu, act);
-                    const int room = kNFMaxT - nt;
-                    const int take = min(__popc(mask), room);
-                    const int rank = __popc(mask & ((1u << lane) - 1u));
-                    if (act && rank < take) tl[nt + rank] = t;
-                    if (take < __popc(mask)) {
-                        // stop after the lane of the last taken target
+                    const unsigned emask = __ballot_sync(0xffffffffu, act && !pk_type(tw));
+                    const int room = kNFList - 1 - nt;
+                    if (__popc(mask) > room) {
+                        // stop after the lane of the room-th target
                         int last = 0;
-                        for (int b = 0, c = 0; b < 32; ++b)
-                            if ((mask >> b) & 1u) {
-                                if (c == take - 1) last = b;
+                        for (int bb = 0, c = 0; bb < 32; ++bb)
+                            if ((mask >> bb) & 1u) {
+                                if (c == room - 1) last = bb;
                                 ++c;
                             }
+                        const unsigned keep = last == 31 ? 0xffffffffu : ((1u << (last + 1)) - 1u);
+                        nt += room;
+                        nE += __popc(emask & keep);
                         p += last + 1;
-                        nt += take;
                         break;
                     }
-                    nt += take;
+                    nt += __popc(mask);
+                    nE += __popc(emask);
                     p += 32;
                 }
+                const int32_t pend = min(p, tc);
+                const int nI = nt - nE;
+                const int pad = (nE & 1) && nI > 0 ? 1 : 0;
+                int we = 0, wi = nE + pad;
+                for (int32_t q = pos; q < pend; q += 32) {
+                    const int32_t t = tf + q + lane;
+                    const uint32_t tw = q + lane < pend ? __float_as_uint(a.pts[t].w) : 0u;
+                    const bool act = pk_axon(tw) > 0;
+                    const bool isE = act && !pk_type(tw);
+                    const bool isI = act && pk_type(tw);
+                    const unsigned me = __ballot_sync(0xffffffffu, isE);
+                    const unsigned mI = __ballot_sync(0xffffffffu, isI);
+                    const unsigned lt = (1u << lane) - 1u;
+                    if (isE) tl[we + __popc(me & lt)] = t;
+                    if (isI) tl[wi + __popc(mI & lt)] = t;
+                    we += __popc(me);
+                    wi += __popc(mI);
+                }
+                if (pad && lane == 0) tl[nE] = -1;
                 if (lane == 0) {
-                    s_nt = nt;
-                    s_pos = p;
+                    s_nt = nt + pad;
+                    s_nreal = nt;
+                    s_pos = pend;
                 }
             }
             __syncthreads();
-            const int nt = s_nt;
+            const int ntl = s_nt;
             pos = s_pos;
             __syncthreads();
-            if (nt == 0) break;
-            if (nt <= 32)
-                nf_targets<1>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-            else
-                nf_targets<2>(a, tl, nt, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+            if (ntl == 0) break;
+            for (int c0 = 0; c0 < ntl; c0 += kNFMaxT) {
+                const int m = min(kNFMaxT, ntl - c0);
+                int nreal = 0;
+                for (int k = 0; k < m; ++k) nreal += tl[c0 + k] >= 0;
+                if (m <= 32)
+                    nf_targets<1>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                else
+                    nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+            }
             if (pos >= tc) break;
         }
         if (lane == 0 && evals) atomicAdd(a.work, evals);
+    }
+}
+
+// Segment order, longest first: key = 16-bit complement of 1024 log2(work),
+// work = targets of X times the sources of its partner leaves (an estimate:
+// every neuron of X counts as a target).
+__global__ void k_seg_order_keys(const int32_t* __restrict__ seg_first,
+                                 const int64_t* __restrict__ nseg_dev,
+                                 const int32_t* __restrict__ list_q,
+                                 const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+                                 const int32_t* __restrict__ ncount, uint64_t* __restrict__ key,
+                                 int32_t* __restrict__ val) {
+    const int64_t nseg = *nseg_dev;
+    for (int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sg < nseg;
+         sg += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
+        double srcs = 0.0;
+        for (int32_t i = i0; i < i1; ++i) srcs += (double)ncount[pY[list_q[i]]];
+        const double work = srcs * (double)ncount[pX[list_q[i0]]];
+        const float lg = log2f((float)work + 1.f);
+        const uint32_t q = min(0xffffu, (uint32_t)(lg * 1024.f));
+        key[sg] = (uint64_t)(0xffffu - q);
+        val[sg] = (int32_t)sg;
     }
 }
 
@@ -377,9 +451,20 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     const int gl = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
     k_zero_w<<<gl, 256, 0, s>>>(w32, nlist_dev);
     MSP_LAUNCH("zero_w");
+    // longest segments first
+    uint64_t* ok0 = c.nf_okey0.ensure<uint64_t>((size_t)nseg_cap);
+    uint64_t* ok1 = c.nf_okey1.ensure<uint64_t>((size_t)nseg_cap);
+    int32_t* ov0 = c.nf_oval0.ensure<int32_t>((size_t)nseg_cap);
+    int32_t* ov1 = c.nf_oval1.ensure<int32_t>((size_t)nseg_cap);
+    k_seg_order_keys<<<grid_for(nseg_cap, 128, (int64_t)c.sm_count * 4), 128, 0, s>>>(
+        seg_first, nseg_dev, list_q, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
+        c.nd_count.get<int32_t>(), ok0, ov0);
+    MSP_LAUNCH("seg_order_keys");
+    radix_sort_dev(c, ok0, ov0, ok1, ov1, nseg_dev, nseg_cap, 16, s);
     NFArgs a;
     a.seg_first = seg_first;
     a.nseg = nseg_dev;
+    a.order = ov0;
     a.list_q = list_q;
     a.pX = c.pr_X.get<int32_t>();
     a.pY = c.pr_Y.get<int32_t>();
