@@ -138,7 +138,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
                          &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
-                         &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
+                         &c->leaf_items, &c->leaf_map, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
                          &c->small_dev, &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
                          &c->h_post, &c->h_type, &c->h_nsyn, &c->c_type, &c->c_va,

@@ -170,7 +170,8 @@ struct msp_ctx {
     msp::DBuf expA, expM, expB;
     msp::DBuf u_sorted;
     // descent
-    msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
+    msp::DBuf items0, items1, leaf_items, leaf_map, rq_key0, rq_key1, rq_val0, rq_val1, accepted,
+        acc_off;
     // generic scratch
     msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist, sd_tmp;
     // device-resident sizes and their pinned host mirror

@@ -407,17 +407,23 @@ __global__ void k_seg_order_keys(const int32_t* __restrict__ seg_first,
                                  const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
                                  const int32_t* __restrict__ ncount, uint64_t* __restrict__ key,
                                  int32_t* __restrict__ val) {
+    // one warp per segment, lanes over its pairs
     const int64_t nseg = *nseg_dev;
-    for (int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sg < nseg;
-         sg += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sg = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); sg < nseg;
+         sg += nw) {
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
-        double srcs = 0.0;
-        for (int32_t i = i0; i < i1; ++i) srcs += (double)ncount[pY[list_q[i]]];
-        const double work = srcs * (double)ncount[pX[list_q[i0]]];
-        const float lg = log2f((float)work + 1.f);
-        const uint32_t q = min(0xffffu, (uint32_t)(lg * 1024.f));
-        key[sg] = (uint64_t)(0xffffu - q);
-        val[sg] = (int32_t)sg;
+        float srcs = 0.f;
+        for (int32_t i = i0 + lane; i < i1; i += 32) srcs += (float)ncount[pY[list_q[i]]];
+        for (int o = 16; o > 0; o >>= 1) srcs += __shfl_xor_sync(0xffffffffu, srcs, o);
+        if (lane == 0) {
+            const float work = srcs * (float)ncount[pX[list_q[i0]]];
+            const float lg = log2f(work + 1.f);
+            const uint32_t q = min(0xffffu, (uint32_t)(lg * 1024.f));
+            key[sg] = (uint64_t)(0xffffu - q);
+            val[sg] = (int32_t)sg;
+        }
     }
 }
 
@@ -456,7 +462,7 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     uint64_t* ok1 = c.nf_okey1.ensure<uint64_t>((size_t)nseg_cap);
     int32_t* ov0 = c.nf_oval0.ensure<int32_t>((size_t)nseg_cap);
     int32_t* ov1 = c.nf_oval1.ensure<int32_t>((size_t)nseg_cap);
-    k_seg_order_keys<<<grid_for(nseg_cap, 128, (int64_t)c.sm_count * 4), 128, 0, s>>>(
+    k_seg_order_keys<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 16), 128, 0, s>>>(
         seg_first, nseg_dev, list_q, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
         c.nd_count.get<int32_t>(), ok0, ov0);
     MSP_LAUNCH("seg_order_keys");

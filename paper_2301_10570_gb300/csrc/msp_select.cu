@@ -230,108 +230,114 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
     }
 }
 
-// per-element draw inside a chosen dendrite leaf: weights w_s K(t,s) in
-// single precision, inclusive prefix sums in double precision
-__global__ void k_leaf_draw(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf,
-                            int64_t cap_leaf,
-                            const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
-                            const float4* __restrict__ pts, const float2* __restrict__ wts,
-                            const int32_t* __restrict__ perm, const int32_t* __restrict__ eoff,
-                            float k2, float rc2, uint64_t seed, StepRef stp,
-                            int32_t* __restrict__ partner, unsigned long long* __restrict__ draw_ctr,
+// The leaf pair reached by each (axon leaf, channel): the descent's items
+// partition the axon boxes of a channel, so every axon leaf has at most one.
+__global__ void k_leaf_map(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf,
+                           int64_t cap_leaf, int32_t* __restrict__ map) {
+    const int64_t n = min(*n_leaf, cap_leaf);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const Item it = items[k];
+        map[2 * (int64_t)it.X + it.ch] = it.Y;
+    }
+}
+
+// Per-element draw inside the chosen dendrite leaf, one thread per axon
+// neuron t (sorted order): weights w_s K(t,s) of the sources s != t of the
+// leaf, truncated at the cutoff, and the inclusive prefix sums over the
+// leaf's order.
+__global__ void k_leaf_draw(int64_t n, const int32_t* __restrict__ leaf_of,
+                            const int32_t* __restrict__ map, const int32_t* __restrict__ nfirst,
+                            const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
+                            const float2* __restrict__ wts, const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ eoff, float k2, float rc2, uint64_t seed,
+                            StepRef stp, int32_t* __restrict__ partner,
+                            unsigned long long* __restrict__ draw_ctr,
                             const int64_t* __restrict__ n_elem) {
     const uint64_t step = stp.get();
     const int64_t ne = *n_elem;
-    // one block of kLeafWarps warps per leaf item; the warps take interleaved
-    // chunks of 32 targets of the axon leaf
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int64_t n_items = min(*n_leaf, cap_leaf);
-    for (int64_t k = blockIdx.x; k < n_items; k += gridDim.x) {
-        Item it = items[k];
-        const int32_t tf = nfirst[it.X], tc = ncount[it.X];
-        const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
+    unsigned long long draws = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float4 T = pts[t];
+        const uint32_t tw = __float_as_uint(T.w);
+        const int ch = pk_type(tw) ? 1 : 0;
+        const int a = (int)pk_axon(tw);
+        if (a == 0) continue;
+        const int32_t Y = map[2 * (int64_t)leaf_of[t] + ch];
+        if (Y < 0) continue;
+        const int32_t sf = nfirst[Y], sc = ncount[Y];
         // fixed-point scale: sc weights of at most 2^8 must stay below 2^63
         int lg = 0;
         while ((1 << lg) < sc + 1 && lg < 30) ++lg;
         const int shift = min(40, 55 - lg);
-        unsigned long long draws = 0;
-        for (int32_t tb = 32 * w; tb < tc; tb += 32 * nwarps) {
-            int32_t t = tf + tb + lane;
-            if (tb + lane >= tc) continue;
-            float4 T = pts[t];
-            uint32_t tw = __float_as_uint(T.w);
-            int ch = pk_type(tw) ? 1 : 0;
-            int a = (int)pk_axon(tw);
-            if (ch != it.ch || a == 0) continue;
-            // Prefix sums of the weights in exact 64-bit fixed point (scale
-            // 2^shift; a weight is at most 255): integer adds are exact and
-            // full rate, where double precision adds are scarce on this GPU.
-            // Weights below 2^-shift (far below exp(-cutoff^2) for the cutoffs
-            // the library accepts) count as zero.
-            uint64_t tot = 0;
-            for (int32_t s = sf; s < sf + sc; ++s) {
-                if (s == t) continue;
-                float4 S = pts[s];
-                float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                tot += __float2ull_rz(ldexpf(ws, shift));
+        // Prefix sums of the weights in exact 64-bit fixed point (scale
+        // 2^shift; a weight is at most 255): integer adds are exact and full
+        // rate, where double precision adds are scarce on this GPU.  Weights
+        // below 2^-shift (far below exp(-cutoff^2) for the cutoffs the library
+        // accepts) count as zero.
+        uint64_t tot = 0;
+        for (int32_t s = sf; s < sf + sc; ++s) {
+            if (s == t) continue;
+            const float4 S = pts[s];
+            const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
+            tot += __float2ull_rz(ldexpf(ws, shift));
+        }
+        const int32_t to = perm[t];
+        if (tot == 0 || (int64_t)eoff[to] + a > ne) continue;
+        // the element draws r_e = floor(U_e * tot) (U_e with 53 bits), in
+        // groups of up to 8 sorted thresholds; one prefix walk over the leaf
+        // serves a whole group: the first source whose inclusive prefix
+        // exceeds r_e
+        constexpr int kGroup = 8;
+        for (int e0 = 0; e0 < a; e0 += kGroup) {
+            const int ng = min(kGroup, a - e0);
+            uint64_t r[kGroup];
+            int ord[kGroup];
+            for (int e = 0; e < ng; ++e) {
+                uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
+                uint32_t o4[4];
+                philox_draw(seed, (uint32_t)to, c1, step, o4);
+                uint64_t u53 = (((uint64_t)o4[0] << 32) | o4[1]) >> 11;
+                uint64_t v = __umul64hi(u53 << 11, tot);     // floor(u53 * tot / 2^53)
+                int j = e;
+                while (j > 0 && r[j - 1] > v) {
+                    r[j] = r[j - 1];
+                    ord[j] = ord[j - 1];
+                    --j;
+                }
+                r[j] = v;
+                ord[j] = e;
             }
-            const int32_t to = perm[t];
-            if (tot == 0 || (int64_t)eoff[to] + a > ne) continue;
-            // the element draws r_e = floor(U_e * tot) (U_e with 53 bits), in
-            // groups of up to 8 sorted thresholds; one prefix walk over the
-            // leaf serves a whole group: the first source whose inclusive
-            // prefix exceeds r_e
-            constexpr int kGroup = 8;
-            for (int e0 = 0; e0 < a; e0 += kGroup) {
-                const int ng = min(kGroup, a - e0);
-                uint64_t r[kGroup];
-                int ord[kGroup];
-                for (int e = 0; e < ng; ++e) {
-                    uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
-                    uint32_t o4[4];
-                    philox_draw(seed, (uint32_t)to, c1, step, o4);
-                    uint64_t u53 = (((uint64_t)o4[0] << 32) | o4[1]) >> 11;
-                    uint64_t v = __umul64hi(u53 << 11, tot);     // floor(u53 * tot / 2^53)
-                    int j = e;
-                    while (j > 0 && r[j - 1] > v) {
-                        r[j] = r[j - 1];
-                        ord[j] = ord[j - 1];
-                        --j;
-                    }
-                    r[j] = v;
-                    ord[j] = e;
+            int32_t pick[kGroup];
+            uint64_t pre = 0;
+            int next = 0;
+            uint64_t rn = r[0];          // the smallest threshold not yet crossed
+            for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
+                if (s == t) continue;
+                const float4 S = pts[s];
+                const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
+                pre += __float2ull_rz(ldexpf(ws, shift));
+                if (pre > rn) {
+                    do {
+                        pick[ord[next++]] = s;
+                        rn = next < ng ? r[next] : 0;
+                    } while (next < ng && pre > rn);
                 }
-                int32_t pick[kGroup];
-                uint64_t pre = 0;
-                int next = 0;
-                uint64_t rn = r[0];          // the smallest threshold not yet crossed
-                for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
-                    if (s == t) continue;
-                    float4 S = pts[s];
-                    float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                    pre += __float2ull_rz(ldexpf(ws, shift));
-                    if (pre > rn) {
-                        do {
-                            pick[ord[next++]] = s;
-                            rn = next < ng ? r[next] : 0;
-                        } while (next < ng && pre > rn);
-                    }
-                }
-                // r < tot = the final prefix, so every threshold was crossed
-                for (int e = 0; e < ng; ++e) {
-                    partner[eoff[to] + e0 + e] = perm[pick[e]];
-                    ++draws;
-                }
+            }
+            // r < tot = the final prefix, so every threshold was crossed
+            for (int e = 0; e < ng; ++e) {
+                partner[eoff[to] + e0 + e] = perm[pick[e]];
+                ++draws;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
-        if (lane == 0 && draws) atomicAdd(draw_ctr, draws);
     }
+    for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
+    if ((threadIdx.x & 31) == 0 && draws) atomicAdd(draw_ctr, draws);
 }
 
 // requests in element order: flag, then key = (dendrite*2 + channel) << 32 | priority
@@ -544,9 +550,14 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
                                                  cap_leaf, ct);
         MSP_LAUNCH("descend");
     }
-    // one block per leaf item; blocks past the device count return at once
-    k_leaf_draw<<<(unsigned)std::min<int64_t>(cap_leaf, 1 << 30), 128, 0, s>>>(
-        lit, &dc->n_leaf, cap_leaf, c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+    // the leaf pair of each (axon leaf, channel), then one thread per neuron
+    int32_t* lmap = c.leaf_map.ensure<int32_t>((size_t)(2 * c.n_nodes));
+    MSP_CUDA(cudaMemsetAsync(lmap, 0xff, (size_t)(2 * c.n_nodes) * sizeof(int32_t), s));
+    k_leaf_map<<<grid_for(cap_leaf, B, (int64_t)c.sm_count * 4), B, 0, s>>>(lit, &dc->n_leaf,
+                                                                           cap_leaf, lmap);
+    MSP_LAUNCH("leaf_map");
+    k_leaf_draw<<<grid_for(n, 128, (int64_t)c.sm_count * 64), 128, 0, s>>>(
+        n, c.leaf_of.get<int32_t>(), lmap, c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
         c.pts.get<float4>(), c.wts.get<float2>(), c.perm.get<int32_t>(),
         c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, stp, partner, ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
