@@ -10,12 +10,11 @@
 // 64; the warps take the partner pairs round-robin.  Each warp stages the
 // sources of its current pair in its own shared memory and every lane
 // evaluates them against its targets:
-//   up to 32 targets: padded to T = 2^k, 32/T lanes per target walking
-//                     interleaved slices of the sources (small leaves still
-//                     fill the warp);
-//   33..64 targets:   2 targets per lane, both of one channel (the E-first
-//                     order with even padding guarantees it), so one staged
-//                     source serves both with one shared-memory load.
+// every lane holds 2 targets of one channel (the E-first order with even
+// padding guarantees it), so one staged source serves both with one
+// shared-memory load; passes of up to 32 targets pad their target pairs to
+// P = 2^k and 32/P lanes share a pair, walking interleaved slices of the
+// sources (small leaves still fill the warp).
 // Capping a pass at 64 targets keeps the kernel at 64 registers (8 blocks of
 // 4 warps per SM).
 // The per-target sums of the 4 warps are added in a fixed order, so u is
@@ -94,22 +93,23 @@ struct Tgts {
 template <int R, int MODE>
 __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int slices,
                                         const Tgts<R>& tg, int32_t base, float (&part)[R]) {
-    constexpr int U = R == 1 ? 4 : 2;
-    float p[R][U];
+    // U sources per iteration, two partial sums per target
+    constexpr int U = 4;
+    float p[R][2];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int v = 0; v < U; ++v) p[r][v] = 0.f;
+    for (int r = 0; r < R; ++r) p[r][0] = p[r][1] = 0.f;
     const float4* sc = st + tg.ch;
     int e = ksl;
     if (MODE == 0) {
-        for (; e + (U - 1) * slices < m; e += U * slices) {
+        const int step = 2 * slices;
+        const float4* q = sc + 2 * e;
+        for (; e + (U - 1) * slices < m; e += U * slices, q += U * step) {
 #pragma unroll
             for (int v = 0; v < U; ++v) {
-                const float4 A = sc[2 * (e + v * slices)];
+                const float4 A = q[v * step];
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    p[r][v] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
+                    p[r][v & 1] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
             }
         }
         for (; e < m; e += slices) {
@@ -136,12 +136,7 @@ __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int sl
         }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        float s = 0.f;
-#pragma unroll
-        for (int v = 0; v < U; ++v) s += p[r][v];
-        part[r] += s;
-    }
+    for (int r = 0; r < R; ++r) part[r] += p[r][0] + p[r][1];
 }
 
 // the pairs of segment [i0, i1) that belong to warp w, for a lane holding R targets
@@ -226,34 +221,35 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
     }
 }
 
-// one pass over the targets tl[0, nt) (nt <= 64; tl[k] < 0 is padding);
-// nreal of them are real
+// One pass over the targets tl[0, nt) (nt <= 64; tl[k] < 0 is padding);
+// nreal of them are real.  A lane holds the two targets of slots 2j and
+// 2j+1 (one channel); with fewer than 33 targets the target pairs are padded
+// to a power of two P and 32/P lanes share a pair, each walking an
+// interleaved slice of the sources.
 template <int R>
 __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, int nt, int nreal,
                                            int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
                                            float cy, float cz, float4* stw,
                                            float (*red)[kNFMaxT], unsigned long long& evals) {
+    static_assert(R == 2, "two targets per lane");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int lg = 0, ntp = 32;
-    if (R == 1) {
-        while ((1 << lg) < nt) ++lg;
-        ntp = 1 << lg;
-    }
-    const int slices = R == 1 ? 32 >> lg : 1;
-    const int j = R == 1 ? (lane & (ntp - 1)) : lane;
-    const int ksl = R == 1 ? lane >> lg : 0;
-    // slot of target r of this lane: j (R = 1) or 2j + r (R = 2)
+    int lg = 0;
+    while ((1 << lg) < (nt + 1) / 2) ++lg;
+    const int npr = 1 << lg;                // lanes per slice (target pairs)
+    const int slices = 32 >> lg;
+    const int j = lane & (npr - 1);
+    const int ksl = lane >> lg;
     Tgts<R> tg;
     float acc[R];
     {
         // the channel of the lane's first slot (both slots share it)
-        const int s0 = R == 1 ? j : 2 * j;
+        const int s0 = 2 * j;
         const int32_t t0 = s0 < nt ? tl[s0] : -1;
         tg.ch = t0 >= 0 ? (pk_type(__float_as_uint(a.pts[t0].w)) ? 1 : 0) : 0;
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int slot = R == 1 ? j : 2 * j + r;
+        const int slot = 2 * j + r;
         const int32_t ts = slot < nt ? tl[slot] : -1;
         const bool valid = ts >= 0;
         const int32_t t = valid ? ts : tl[0];          // tl[0] is always a real target
@@ -269,19 +265,19 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         acc[r] = 0.f;
     }
     nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nreal);
-    // slices of a target (R == 1), then the 4 warps in a fixed order
+    // the slices of a target pair, then the 4 warps in a fixed order
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        for (int o = ntp; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        for (int o = npr; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     if (ksl == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) red[w][R == 1 ? j : 2 * j + r] = acc[r];
+        for (int r = 0; r < R; ++r) red[w][2 * j + r] = acc[r];
     }
     __syncthreads();
     if (w == 0 && ksl == 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int slot = R == 1 ? j : 2 * j + r;
+            const int slot = 2 * j + r;
             if (tg.t[r] >= 0) {
                 float s = red[0][slot];
 #pragma unroll
@@ -387,10 +383,7 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
                 const int m = min(kNFMaxT, ntl - c0);
                 int nreal = 0;
                 for (int k = 0; k < m; ++k) nreal += tl[c0 + k] >= 0;
-                if (m <= 32)
-                    nf_targets<1>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-                else
-                    nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             }
             if (pos >= tc) break;
         }
