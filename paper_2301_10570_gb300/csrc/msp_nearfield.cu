@@ -103,6 +103,30 @@ __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int sl
     if (MODE == 0) {
         const int step = 2 * slices;
         const float4* q = sc + 2 * e;
+        if (R == 2) {
+            // the two targets as packed pairs: the exponent chain and the sum
+            // run on the paired FP32 units, with the same rounding per target
+            // as the scalar fmaf / add
+            const float2 TX = make_float2(tg.x[0], tg.x[R - 1]);
+            const float2 TY = make_float2(tg.y[0], tg.y[R - 1]);
+            const float2 TZ = make_float2(tg.z[0], tg.z[R - 1]);
+            float2 P0 = make_float2(0.f, 0.f), P1 = make_float2(0.f, 0.f);
+            for (; e + (U - 1) * slices < m; e += U * slices, q += U * step) {
+#pragma unroll
+                for (int v = 0; v < U; ++v) {
+                    const float4 A = q[v * step];
+                    const float2 E2 = __ffma2_rn(
+                        TX, make_float2(A.x, A.x),
+                        __ffma2_rn(TY, make_float2(A.y, A.y),
+                                   __ffma2_rn(TZ, make_float2(A.z, A.z), make_float2(A.w, A.w))));
+                    const float2 X2 = make_float2(nf_ex2(E2.x), nf_ex2(E2.y));
+                    if (v & 1) P1 = __fadd2_rn(P1, X2);
+                    else       P0 = __fadd2_rn(P0, X2);
+                }
+            }
+            p[0][0] = P0.x; p[R - 1][0] = P0.y;
+            p[0][1] = P1.x; p[R - 1][1] = P1.y;
+        }
         for (; e + (U - 1) * slices < m; e += U * slices, q += U * step) {
 #pragma unroll
             for (int v = 0; v < U; ++v) {

@@ -2,10 +2,11 @@
 
     python -m paper_2301_10570_gb300.profile_cases near_field_131k
     python -m paper_2301_10570_gb300.profile_cases step_1m --steps 2
+    python -m paper_2301_10570_gb300.profile_cases graph_1m --steps 4
 
 Each case builds the library, runs a few plasticity steps (tree, attraction,
-selection) and prints the library's statistics; it exits non-zero on any
-error.  The cases are sized for the profiling rules of the pool: the full
+selection; graph_1m: the whole step captured as one CUDA graph and replayed)
+and prints the library's statistics; it exits non-zero on any error.  The cases are sized for the profiling rules of the pool: the full
 capture case holds well under 1 GB on the device.
 """
 from __future__ import annotations
@@ -30,7 +31,7 @@ def step_1m():
     return W.clustered_1m(**_plan())
 
 
-CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m}
+CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m, "graph_1m": step_1m}
 
 
 def main(argv=None):
@@ -45,10 +46,20 @@ def main(argv=None):
     w = CASES[args.case]()
     g = msp.MSP(w.params)
     dev = msp.to_device(w)
-    for k in range(args.steps):
-        g.build_tree(*dev)
+    if args.case.startswith("graph"):
+        # one eager step sizes the graph; then the whole step as graph
+        # replays (walk, build, attraction, selection, commit)
+        pos, typ, va, ve, vi = dev
+        va, ve, vi = va.clone(), ve.clone(), vi.clone()
+        g.build_tree(pos, typ, va, ve, vi)
         g.attraction()
-        g.select_partners(k)
+        g.step_graph_capture(pos, typ, va, ve, vi, first_step=0)
+        g.run_steps(0, args.steps)
+    else:
+        for k in range(args.steps):
+            g.build_tree(*dev)
+            g.attraction()
+            g.select_partners(k)
     torch.cuda.synchronize()
     print(args.case, g.stats())
     return 0
