@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="rerun the plan chooser on this workload and bench its plan")
+    ap.add_argument("--workload", default="clustered_1m", choices=["clustered_1m", "batched_256"],
+                    help="clustered_1m: the headline network; batched_256: 256 independent "
+                         "networks (about 11.7M neurons) in one batched step")
     return ap.parse_args()
 
 
@@ -71,6 +74,24 @@ def tuned_params():
 def workload():
     from paper_2301_10570_gb300 import workloads as W
     return W.clustered_1m(**tuned_params())
+
+
+BATCH_METRIC = "batched-step neurons/s, 256 independent networks (11.7M neurons) on GB300"
+BATCH_DESC = ("batched_256: 256 networks, n log-uniform in [1024, 262144] (11,718,582 neurons), "
+              "sigma uniform in [300, 1500] um, uniform or clustered, each scaled to sigma units "
+              "in its own octree cell (msp_batch_layout)")
+
+
+def batched_workload(dev):
+    """The 256-network batch placed as one problem of kernel width 1."""
+    import torch
+
+    from paper_2301_10570_gb300 import msp, workloads as W
+    b = W.batched_256()
+    plan = tuned_params()
+    placed, side, level = msp.batch_layout(torch.from_numpy(b.pos).to(dev), b.offsets, b.sigma,
+                                           plan["cutoff"], plan["leaf_capacity"])
+    return b.placed(placed.cpu().numpy(), side, **plan)
 
 
 def near_field_traffic():
@@ -163,7 +184,8 @@ def run_ours(args, rank, world):
     from paper_2301_10570_gb300 import msp, replicas
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = workload()
+    batched = args.workload == "batched_256"
+    w = batched_workload(dev) if batched else workload()
     n = w.n
     g = msp.MSP(w.params, device=dev.index)
     pos, typ, va0, ve0, vi0 = msp.to_device(w, dev)
@@ -272,7 +294,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     # direct all-pairs evaluation of the attraction on the same GPU
     direct = None
-    if not args.no_direct:
+    if not args.no_direct and not batched:
         ud = torch.empty(n, dtype=torch.float32, device=dev)
         g.direct(out=ud)
         torch.cuda.synchronize()
@@ -299,7 +321,7 @@ def run_ours(args, rank, world):
     roofline = {"kernel": "k_near_field", "bound": "alu", "achieved": round(achieved, 1),
                 "peak": round(peak_gex2, 1), "unit": "G interactions/s",
                 "frac": round(achieved / peak_gex2, 4),
-                "traffic": near_field_traffic(), "near_field_ms": round(nf, 3),
+                "traffic": None if batched else near_field_traffic(), "near_field_ms": round(nf, 3),
                 "near_field_share_of_step": round(nf / ms, 3),
                 "interactions_per_step": int(statistics.mean(inter)),
                 "peak_basis": f"issue bound: {SM_COUNT} SMs x {LANES_PER_SM_CLK} lanes/clk / "
@@ -307,12 +329,14 @@ def run_ours(args, rank, world):
                               f"{sm_max:.0f} MHz (EX2 pipe ~31/clk/SM and FP32 128/clk/SM "
                               f"not binding)"}
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    out = {"metric": BATCH_METRIC if batched else METRIC, "value": value, "unit": UNIT,
+           "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": "clustered_1m: 1,048,576 neurons, 64 Gaussian clusters (std 1500 um), "
-                                  "100,000 um cube, sigma 750 um, 80/20 E/I, vacancies U{0..3} + walk",
+           "config": {"workload": BATCH_DESC if batched else
+                      "clustered_1m: 1,048,576 neurons, 64 Gaussian clusters (std 1500 um), "
+                      "100,000 um cube, sigma 750 um, 80/20 E/I, vacancies U{0..3} + walk",
                       "plan": tuned_params(), "parallelism": f"replicas x{world}",
                       "l2": "flushed (256 MB write) between timed steps",
                       "timing": "CUDA events per step (one graph replay each), mean over steps",
@@ -351,7 +375,8 @@ def cpu_baseline(w, u_gpu=None, sample_clusters=16):
     o.select_partners(0)
     dt = time.perf_counter() - t0
     res = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"first {sample_clusters} clusters ({m} neurons) of the workload, one full step "
+           "sample": f"first {m} neurons of the workload ({sample_clusters} clusters of the 1M "
+                     f"network, or the first networks of the batch), one full step "
                      f"(tree, attraction, selection) in {dt:.1f} s"}
     if u_gpu is not None:
         rng = np.random.default_rng(0)
@@ -425,7 +450,8 @@ def main():
         _PLAN_OVERRIDE = best
     out, w, g, u = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy())
+        out["cpu_baseline"] = cpu_baseline(
+            w, None if args.workload == "batched_256" else u.cpu().numpy())
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

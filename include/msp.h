@@ -288,6 +288,34 @@ msp_status msp_export_expansions(msp_ctx *ctx, float *A, float *M, float *B,
 /* Message of the last error of the calling thread ("" if none). */
 const char *msp_last_error(void);
 
+/* ---- Many independent networks as one problem (batched step) ------------
+ * The attraction depends on positions only through |t - s| / sigma, so a
+ * network scaled by 1/sigma has kernel width 1.  msp_batch_layout scales each
+ * network k (neurons [offsets[k], offsets[k+1]) of the concatenated arrays,
+ * kernel width sigma[k]) by 1/sigma[k] and places it at the low corner of its
+ * own cell of a grid of octree boxes at level *level_out, on every other cell
+ * of each dimension, so any two networks are more than `cutoff` apart.  A
+ * context created with sigma = 1, origin = 0, side = *side_out and the same
+ * cutoff and leaf capacity then runs the whole batch through the ordinary
+ * calls (or the step graph) in one pass: box pairs between networks are
+ * pruned exactly, and every leaf and every shared axon-box choice of
+ * Algorithm 1 lies inside one network (each network has more neurons than
+ * the leaf capacity, so every box above its cell is split).  Neuron order is
+ * unchanged: u, partner and synapse indices refer to the concatenated arrays.
+ *   offsets            HOST, n_networks + 1 int64, offsets[0] = 0
+ *   x,y,z              DEVICE, offsets[n_networks] positions (any unit)
+ *   sigma              HOST, n_networks kernel widths (same unit)
+ *   x_out,y_out,z_out  DEVICE, the placed positions (sigma units)
+ *   side_out, level_out HOST: the domain side and the level of the cells
+ * Errors: MSP_ERR_INVALID_ARG (a network with <= leaf_capacity neurons,
+ * sigma <= 0, non-finite positions, bad offsets).  Needs no context;
+ * allocates a few bytes per network of device scratch.  Synchronous. */
+msp_status msp_batch_layout(int64_t n_networks, const int64_t *offsets, const float *x_dev,
+                            const float *y_dev, const float *z_dev, const double *sigma,
+                            double cutoff, int leaf_capacity, float *x_out_dev,
+                            float *y_out_dev, float *z_out_dev, float *side_out,
+                            int *level_out, void *stream);
+
 /* Largest n accepted by msp_direct_noalloc (the size of its fixed scratch). */
 #define MSP_NOALLOC_MAX_N 65536
 

@@ -73,7 +73,7 @@ __device__ inline int block_size(const NodeView& nv, int32_t X, int32_t Y) {
 __global__ void k_init_pairs(int64_t n, int32_t* pX, int32_t* pY, DevCounts* dc) {
     dc->depth_start[0] = 0;
     dc->depth_start[1] = n > 0 ? 1 : 0;
-    dc->overflow = 0;
+    dc->overflow &= ~1ll;       // the traversal's bit; the build's (16) stays for the step check
     dc->need_pairs = 0;
     dc->interactions = 0;
     if (n > 0) {

@@ -57,7 +57,7 @@ __global__ void k_graph_check(DevCounts* dc, int left_slot) {
     int64_t bad = 0;
     if (dc->overflow & 1) bad |= kHaltPairs;
     if (dc->overflow & 6) bad |= kHaltItems;
-    if (dc->more_levels > 0) bad |= kHaltLevels;
+    if (dc->more_levels > 0 || (dc->overflow & 16)) bad |= kHaltLevels;
     if (dc->items[left_slot] != 0) bad |= kHaltDescent;
     dc->halt |= bad;
 }

@@ -109,9 +109,10 @@ struct DevCounts {
     int64_t draws;
     int64_t n_req, n_syn;
     int64_t interactions;
-    int64_t overflow;                        // bit 0 pairs, 1 items, 2 leaf items, 3 steps
+    int64_t overflow;                        // bit 0 pairs, 1 items, 2 leaf items, 4 tree nodes
     int64_t need_pairs;                      // largest pair-table end asked for (before clamping)
     int64_t need_items;                      // largest descent item count asked for
+    int64_t need_nodes;                      // largest octree node end asked for
     int64_t scan_n;                          // element count of the next scan
     // whole-step graph: the step index its kernels draw with, the halt flag
     // (nonzero: a capacity was exceeded; the state-changing kernels stop) and
@@ -242,11 +243,11 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
 int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s);
 // Exclusive scan of in[0, *n_dev) (n_dev in device memory, at most n_cap)
 // into out; *total_dst = total (+ *base if base).  No host synchronisation.
-// With overflow given, an end above clamp_cap sets bit 0 of *overflow, raises
-// *need to it and stores *base instead.
+// With overflow given, an end above clamp_cap sets overflow_bit in *overflow,
+// raises *need to it and stores *base instead.
 void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev, int64_t n_cap,
               int64_t* total_dst, const int64_t* base, cudaStream_t s, int64_t clamp_cap = 0,
-              int64_t* overflow = nullptr, int64_t* need = nullptr);
+              int64_t* overflow = nullptr, int64_t* need = nullptr, int64_t overflow_bit = 1);
 // Stable radix sort of the first *n_dev (<= n_cap) pairs.  No host sync.
 void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                     int32_t* vals_tmp, const int64_t* n_dev, int64_t n_cap, int bits,

@@ -273,7 +273,7 @@ __global__ void k_sd_reduce(const int32_t* __restrict__ in, const int64_t* __res
 __global__ void k_sd_spine(long long* __restrict__ bsum, const int64_t* __restrict__ n_dev,
                            int64_t* __restrict__ dst, const int64_t* __restrict__ base,
                            int64_t clamp_cap, int64_t* __restrict__ overflow,
-                           int64_t* __restrict__ need) {
+                           int64_t* __restrict__ need, int64_t overflow_bit) {
     const int64_t n = *n_dev;
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     __shared__ long long chunk_total;
@@ -300,7 +300,8 @@ __global__ void k_sd_spine(long long* __restrict__ bsum, const int64_t* __restri
         const int64_t b = base ? *base : 0;
         int64_t end = carry + b;
         if (overflow && end > clamp_cap) {
-            atomicOr(reinterpret_cast<unsigned long long*>(overflow), 1ull);
+            atomicOr(reinterpret_cast<unsigned long long*>(overflow),
+                     (unsigned long long)overflow_bit);
             atomicMax(reinterpret_cast<unsigned long long*>(need), (unsigned long long)end);
             end = b;
         }
@@ -428,14 +429,14 @@ void pull_counts(msp_ctx& c, cudaStream_t s) {
 
 void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev, int64_t n_cap,
               int64_t* total_dst, const int64_t* base, cudaStream_t s, int64_t clamp_cap,
-              int64_t* overflow, int64_t* need) {
+              int64_t* overflow, int64_t* need, int64_t overflow_bit) {
     const int64_t tiles_cap = std::max<int64_t>((n_cap + kScanTile - 1) / kScanTile, 1);
     long long* bsum = c.sd_tmp.ensure<long long>((size_t)tiles_cap);
     const int G = (int)std::min<int64_t>(tiles_cap, (int64_t)c.sm_count * 8);
     k_sd_reduce<<<G, kScanThreads, 0, s>>>(in, n_dev, bsum);
     MSP_LAUNCH("scan_dev_reduce");
     k_sd_spine<<<1, kScanThreads, 0, s>>>(bsum, n_dev, total_dst, base, clamp_cap, overflow,
-                                          need);
+                                          need, overflow_bit);
     MSP_LAUNCH("scan_dev_spine");
     k_sd_apply<<<G, kScanThreads, 0, s>>>(in, out, n_dev, bsum);
     MSP_LAUNCH("scan_dev_apply");

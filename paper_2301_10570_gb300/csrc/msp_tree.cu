@@ -59,9 +59,10 @@ __global__ void k_u8_to_i32(const uint8_t* __restrict__ a, int64_t n, int32_t* _
 
 __global__ void k_init_root(int64_t n, uint8_t* level, uint64_t* prefix, int32_t* first,
                             int32_t* count, int32_t* parent, int32_t* child_first,
-                            uint8_t* nchild, int64_t* level_start) {
+                            uint8_t* nchild, int64_t* level_start, int64_t* overflow) {
     level_start[0] = 0;
     level_start[1] = 1;
+    *overflow &= ~16ll;
     level[0] = 0;
     prefix[0] = 0;
     first[0] = 0;
@@ -147,9 +148,13 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
                                 uint64_t* __restrict__ nd_prefix, int32_t* __restrict__ nd_first,
                                 int32_t* __restrict__ nd_count, int32_t* __restrict__ nd_parent,
                                 int32_t* __restrict__ nd_child_first,
-                                uint8_t* __restrict__ nd_nchild) {
+                                uint8_t* __restrict__ nd_nchild,
+                                const int64_t* __restrict__ overflow) {
     const int lane = threadIdx.x & 31, o = lane & 7;
     const int64_t l0 = lb[0], nl = lb[1] - lb[0], next0 = lb[1];
+    // the node arrays could not hold the next level (a bound that cannot be
+    // exceeded; guarded all the same): no children are written
+    if (*overflow & 16) return;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 4; base < nl; base += nw * 4) {
@@ -299,10 +304,17 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
     int32_t* cnt = c.cnt.ensure<int32_t>(nn + 8);
     int32_t* off = c.off.ensure<int32_t>(nn + 8);
+    // boxes at level l: at most min(8^l, n), and (l >= 1) at most 8 children
+    // of each box of level l-1 that splits, i.e. holds more than C neurons
+    const int64_t splitters = (int64_t)nn / ((int64_t)cfg.leaf_capacity + 1);
+    auto level_cap = [&](int l) -> int64_t {
+        int64_t c = l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
+        if (l >= 1) c = std::min<int64_t>(c, 8 * splitters);
+        return std::max<int64_t>(c, 1);
+    };
     for (;;) {
-        // node capacity: at most min(8^l, n) boxes per level
         int64_t cap = 0;
-        for (int l = 0; l <= L; ++l) cap += l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
+        for (int l = 0; l <= L; ++l) cap += level_cap(l);
         cap += 8;
         c.nd_level.ensure<uint8_t>((size_t)cap);
         c.nd_prefix.ensure<uint64_t>((size_t)cap);
@@ -317,21 +329,21 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
                                     c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
                                     c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
-                                    c.nd_nchild.get<uint8_t>(), dc->level_start);
+                                    c.nd_nchild.get<uint8_t>(), dc->level_start, &dc->overflow);
         MSP_LAUNCH("init_root");
         for (int l = 0; l < L; ++l) {
-            const int64_t lcap = l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
+            const int64_t lcap = level_cap(l);
             k_count_children<<<Gt, B, 0, s>>>(&dc->level_start[l], l, cfg.leaf_capacity,
                                               cfg.max_depth, k0, c.nd_first.get<int32_t>(),
                                               c.nd_count.get<int32_t>(), cnt, &dc->scan_n);
             MSP_LAUNCH("count_children");
             scan_dev(c, cnt, off, &dc->scan_n, lcap, &dc->level_start[l + 2],
-                     &dc->level_start[l + 1], s);
+                     &dc->level_start[l + 1], s, cap, &dc->overflow, &dc->need_nodes, 16);
             k_emit_children<<<Gt, B, 0, s>>>(
                 &dc->level_start[l], l, cfg.leaf_capacity, cfg.max_depth, k0, off,
                 c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
                 c.nd_count.get<int32_t>(), c.nd_parent.get<int32_t>(),
-                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>());
+                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), &dc->overflow);
             MSP_LAUNCH("emit_children");
         }
         // would a box of the last built level still split?
@@ -356,6 +368,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         // same levels; a deeper one sets more_levels, which halts the graph
         if (c.graph_mode) return;
         pull_counts(c, s);          // the one synchronisation of the build
+        if (c.hcount->overflow & 16) throw Error(MSP_ERR_CHECK, "octree node capacity exceeded");
         if (c.hcount->more_levels > 0 && L < cfg.max_depth) {
             L = cfg.max_depth;
             continue;

@@ -31,7 +31,7 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
             "msp_export_expansions", "msp_last_error", "msp_direct_noalloc",
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-            "msp_set_pair_capacity")
+            "msp_set_pair_capacity", "msp_batch_layout")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -90,8 +90,11 @@ def load(path: str = LIB_PATH):
         L.msp_step_graph_launch.argtypes = [vp, i64, vp]
         L.msp_step_graph_finish.argtypes = [vp, vp, C.POINTER(u64), C.POINTER(i64)]
         L.msp_set_pair_capacity.argtypes = [vp, i64]
+        L.msp_batch_layout.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, C.c_int, vp, vp, vp,
+                                       C.POINTER(C.c_float), C.POINTER(C.c_int), vp]
+        L.msp_batch_layout.restype = C.c_int
         for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-                     "msp_set_pair_capacity"):
+                     "msp_set_pair_capacity", "msp_batch_layout"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
@@ -357,6 +360,27 @@ def direct_noalloc(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, out=None
                                      _ptr(vac_dend_e), _ptr(vac_dend_i), float(sigma), _ptr(u),
                                      _stream(stream)))
     return u
+
+
+def batch_layout(pos, offsets, sigma, cutoff, leaf_capacity, stream=None):
+    """Places the networks of a batch (pos: (3, N) float32 CUDA tensor of the
+    concatenated networks; offsets: N_net + 1 int64; sigma: per network) in
+    one problem of kernel width 1.  Returns (placed (3, N) tensor, side,
+    cell level)."""
+    pos = pos.contiguous()
+    if not pos.is_cuda or pos.dtype != torch.float32:
+        raise TypeError("batch_layout expects CUDA float32 positions")
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    if len(off) != len(sig) + 1:
+        raise ValueError("offsets must have one entry more than sigma")
+    xs = [pos[d].contiguous() for d in range(3)]
+    out = torch.empty_like(pos)
+    side, level = C.c_float(0.0), C.c_int(0)
+    _check(load().msp_batch_layout(len(sig), _np(off), *[_ptr(t) for t in xs], _np(sig),
+                                   float(cutoff), int(leaf_capacity), _ptr(out[0]), _ptr(out[1]),
+                                   _ptr(out[2]), C.byref(side), C.byref(level), _stream(stream)))
+    return out, float(side.value), int(level.value)
 
 
 def to_device(w, device="cuda"):

@@ -110,3 +110,92 @@ def subset(w: Workload, idx: np.ndarray, name: str | None = None) -> Workload:
     return Workload(name or w.name + "_sub", np.ascontiguousarray(w.pos[:, idx]),
                     w.type[idx].copy(), w.vac_axon[idx].copy(), w.vac_dend_e[idx].copy(),
                     w.vac_dend_i[idx].copy(), dict(w.params))
+
+
+# -- many independent networks ------------------------------------------------
+@dataclass
+class Batch:
+    """Independent networks, concatenated: network k holds neurons
+    [offsets[k], offsets[k+1]) with kernel width sigma[k] (um)."""
+    name: str
+    pos: np.ndarray           # (3, N) float32, um, each network in its own frame
+    type: np.ndarray
+    vac_axon: np.ndarray
+    vac_dend_e: np.ndarray
+    vac_dend_i: np.ndarray
+    offsets: np.ndarray       # (K + 1,) int64
+    sigma: np.ndarray         # (K,) float64, um
+    kinds: list               # "uniform" or "clustered" per network
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[1])
+
+    def network_of(self) -> np.ndarray:
+        return np.repeat(np.arange(len(self.sigma)), np.diff(self.offsets))
+
+    def network(self, k: int, **kw) -> Workload:
+        """Network k alone, in its own frame, with its own kernel width."""
+        a, b = int(self.offsets[k]), int(self.offsets[k + 1])
+        pos = np.ascontiguousarray(self.pos[:, a:b])
+        lo = pos.min(axis=1, keepdims=True)
+        side = float((pos.max(axis=1) - lo[:, 0]).max()) * 1.001 + 1.0
+        params = default_params(side, sigma=float(self.sigma[k]),
+                                origin=tuple(float(v) for v in lo[:, 0]), **kw)
+        return Workload(f"{self.name}_{k}", pos, self.type[a:b].copy(),
+                        self.vac_axon[a:b].copy(), self.vac_dend_e[a:b].copy(),
+                        self.vac_dend_i[a:b].copy(), params)
+
+    def placed(self, pos_placed: np.ndarray, side: float, **kw) -> Workload:
+        """The whole batch as one problem of kernel width 1, from the placed
+        positions (sigma units) and the domain side."""
+        return Workload(self.name + "_placed", np.ascontiguousarray(pos_placed, np.float32),
+                        self.type, self.vac_axon, self.vac_dend_e, self.vac_dend_i,
+                        default_params(side, sigma=1.0, **kw))
+
+
+def batch(sizes, sigmas, kinds, seed: int, name: str = "batch") -> Batch:
+    """Networks of the given sizes: "uniform" ones fill a cube of side
+    625 n^(1/3) um (the density of uniform_4k); "clustered" ones hold
+    max(1, n / 16,384) Gaussian clusters (std 1,500 um) at the cluster spacing
+    of clustered_1m."""
+    rng = np.random.default_rng(seed)
+    pos, offs = [], [0]
+    for n, kind in zip(sizes, kinds):
+        n = int(n)
+        if kind == "uniform":
+            side = 625.0 * n ** (1.0 / 3.0)
+            p = rng.random((3, n)) * side
+        else:
+            nc = max(1, n // 16_384)
+            side = 100_000.0 * (nc / 64.0) ** (1.0 / 3.0)
+            margin = min(4500.0, side / 4)
+            centres = rng.uniform(margin, side - margin, (nc, 3))
+            which = rng.integers(0, nc, n)
+            p = (centres[which] + rng.normal(0.0, 1500.0, (n, 3))).T
+            p = np.clip(p, 0.0, side)
+        pos.append(p.astype(np.float32))
+        offs.append(offs[-1] + n)
+    n_all = offs[-1]
+    t, a, e, i = _counts(rng, n_all)
+    return Batch(name, np.ascontiguousarray(np.concatenate(pos, axis=1)), t, a, e, i,
+                 np.asarray(offs, np.int64), np.asarray(sigmas, np.float64), list(kinds))
+
+
+def batched_256(seed: int = 5) -> Batch:
+    """256 networks, n log-uniform in [1,024, 262,144] (about 12M neurons in
+    all), sigma uniform in [300, 1,500] um, each uniform or clustered."""
+    rng = np.random.default_rng(seed)
+    k = 256
+    sizes = np.exp(rng.uniform(np.log(1024), np.log(262_144), k)).astype(np.int64)
+    sigmas = rng.uniform(300.0, 1500.0, k)
+    kinds = ["clustered" if v else "uniform" for v in rng.random(k) < 0.5]
+    return batch(sizes, sigmas, kinds, seed=seed + 1, name="batched_256")
+
+
+def batched_small(seed: int = 8) -> Batch:
+    """Five small networks of both kinds and different widths (oracle-sized)."""
+    sizes = [700, 1500, 400, 2200, 900]
+    sigmas = [300.0, 750.0, 1500.0, 500.0, 1100.0]
+    kinds = ["uniform", "clustered", "uniform", "clustered", "uniform"]
+    return batch(sizes, sigmas, kinds, seed=seed, name="batched_small")
