@@ -14,6 +14,8 @@
  *   Algorithm 1   dual descent over (axon box, dendrite box) pairs
  *   Algorithm 2   candidate attractions, total, uniform draw, upper_bound
  *   Section 4     requests are resolved at the dendrite side
+ *   (derivatives) du/dsigma and the transposed transform sum_t g_t K(t,s) of
+ *                 Eq. 8, the adjoint of the attraction
  * and the readings of the paper listed in the design notes (kernel width,
  * sign of Eq. 6, truncation 0 <= alpha_d < p, centroids as expansion centres,
  * the Hermite-to-Taylor translation derived from Eq. 6 and Eq. 7, the
@@ -909,6 +911,79 @@ void orc_direct(int64_t n, const float *x, const float *y, const float *z, const
         }
         u[k] = s;
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* derivatives of the attraction (Eq. 8)                                      */
+/* ------------------------------------------------------------------------- */
+
+/* one (target t, source s) term of every output; t, s caller indices */
+static void grad_term(int64_t t, int64_t s, double d2, double sigma, const uint8_t *type,
+                      const uint8_t *va, const uint8_t *vde, const uint8_t *vdi,
+                      const double *g, double *u, double *dudsig, double *gE, double *gI)
+{
+    if (va[t] == 0) return;
+    double K = exp(-d2 / (sigma * sigma));
+    double w = type[t] ? vdi[s] : vde[s];
+    if (u) u[t] += w * K;
+    if (dudsig) dudsig[t] += w * K * 2.0 * d2 / (sigma * sigma * sigma);
+    if (g) {
+        double *gs = type[t] ? gI : gE;
+        if (gs) gs[s] += g[t] * K;
+    }
+}
+
+static void zero_outputs(int64_t n, double *u, double *dudsig, double *gE, double *gI)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (u) u[i] = 0.0;
+        if (dudsig) dudsig[i] = 0.0;
+        if (gE) gE[i] = 0.0;
+        if (gI) gI[i] = 0.0;
+    }
+}
+
+int orc_attraction_grad(const orc_ctx *c, const uint8_t *type, const uint8_t *vac_axon,
+                        const uint8_t *vac_dend_e, const uint8_t *vac_dend_i,
+                        const double *g, double *u, double *dudsig, double *gE, double *gI)
+{
+    if (!c->attraction_done) return -1;
+    for (int64_t q = 0; q < c->n_pairs; ++q)
+        if (c->pairs[q].kind == ORC_FAR) return -1;
+    zero_outputs(c->n, u, dudsig, gE, gI);
+    double sigma = c->cfg.sigma;
+    for (int64_t q = 0; q < c->n_pairs; ++q) {
+        const pair_t *pr = &c->pairs[q];
+        if (pr->kind != ORC_P2P) continue;
+        const node_t *X = &c->nodes[pr->X], *Y = &c->nodes[pr->Y];
+        for (int64_t t = X->first; t < (int64_t)X->first + X->count; ++t)
+            for (int64_t s = Y->first; s < (int64_t)Y->first + Y->count; ++s) {
+                if (s == t) continue;
+                double d2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double e = c->pos[3 * t + d] - c->pos[3 * s + d];
+                    d2 += e * e;
+                }
+                grad_term(c->perm[t], c->perm[s], d2, sigma, type, vac_axon, vac_dend_e,
+                          vac_dend_i, g, u, dudsig, gE, gI);
+            }
+    }
+    return 0;
+}
+
+void orc_direct_grad(int64_t n, const float *x, const float *y, const float *z,
+                     const uint8_t *type, const uint8_t *vac_axon, const uint8_t *vac_dend_e,
+                     const uint8_t *vac_dend_i, double sigma, const double *g, double *u,
+                     double *dudsig, double *gE, double *gI)
+{
+    zero_outputs(n, u, dudsig, gE, gI);
+    for (int64_t t = 0; t < n; ++t)
+        for (int64_t s = 0; s < n; ++s) {
+            if (s == t) continue;
+            double dx = (double)x[t] - x[s], dy = (double)y[t] - y[s], dz = (double)z[t] - z[s];
+            grad_term(t, s, dx * dx + dy * dy + dz * dz, sigma, type, vac_axon, vac_dend_e,
+                      vac_dend_i, g, u, dudsig, gE, gI);
+        }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -82,6 +82,25 @@ void orc_direct(int64_t n, const float *x, const float *y, const float *z,
                 double sigma, int64_t n_targets, const int64_t *targets,
                 double *u);
 
+/* Derivatives of the attraction (Eq. 8, K = exp(-r^2/sigma^2)), all arrays
+ * in caller order, evaluated at the counts given here:
+ *   u(t)         = sum_{s != t} w_s^{T(t)} K(t,s)             (a_t > 0, else 0)
+ *   dudsig(t)    = sum_{s != t} w_s^{T(t)} K(t,s) 2 r^2 / sigma^3   (a_t > 0)
+ *   gE(s), gI(s) = sum_{t != s, a_t > 0, T(t) = E resp. I} g_t K(t,s)
+ * so that gE, gI are the gradient of L = sum_t g_t u(t) with respect to the
+ * dendritic weights w^E, w^I.  orc_attraction_grad sums over the near-field
+ * leaf pairs of the last orc_attraction (whose tree may have been built with
+ * other counts: the counts only chose the pairs); it returns -1 when the
+ * attraction has not run or translated pairs are present.  orc_direct_grad
+ * sums over all pairs.  Any output may be NULL; g may be NULL (no gE, gI). */
+int orc_attraction_grad(const orc_ctx *c, const uint8_t *type, const uint8_t *vac_axon,
+                        const uint8_t *vac_dend_e, const uint8_t *vac_dend_i,
+                        const double *g, double *u, double *dudsig, double *gE, double *gI);
+void orc_direct_grad(int64_t n, const float *x, const float *y, const float *z,
+                     const uint8_t *type, const uint8_t *vac_axon, const uint8_t *vac_dend_e,
+                     const uint8_t *vac_dend_i, double sigma, const double *g, double *u,
+                     double *dudsig, double *gE, double *gI);
+
 /* Vacancy random walk: v <- clamp(v +- 1, 0, 5) per neuron and channel. */
 void orc_vacancy_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t *vac_axon,
                       uint8_t *vac_dend_e, uint8_t *vac_dend_i);

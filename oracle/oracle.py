@@ -67,6 +67,9 @@ def lib():
             L.orc_select_partners.restype = i64
             L.orc_select_partners.argtypes = [vp, u64] + [vp] * 6
             L.orc_direct.argtypes = [i64] + [vp] * 7 + [d, i64, vp, vp]
+            L.orc_attraction_grad.restype = C.c_int
+            L.orc_attraction_grad.argtypes = [vp] * 10
+            L.orc_direct_grad.argtypes = [i64] + [vp] * 7 + [d] + [vp] * 5
             L.orc_vacancy_walk.argtypes = [i64, u64, u64, vp, vp, vp]
             L.orc_commit_synapses.argtypes = [i64] + [vp] * 6
             for f in ("orc_num_nodes", "orc_num_pairs", "orc_num_elements"):
@@ -152,6 +155,22 @@ class Oracle:
         lib().orc_attraction(self._h, _p(u))
         return u[: self.n]
 
+    def attraction_grad(self, type_, vac_axon, vac_dend_e, vac_dend_i, g=None):
+        """u, du/dsigma and (with g) the gradient of sum_t g_t u(t) with respect
+        to w^E, w^I, over the near-field pairs of the last attraction, at the
+        given counts (caller order)."""
+        n = self.n
+        arrs = [_u8(type_), _u8(vac_axon), _u8(vac_dend_e), _u8(vac_dend_i)]
+        gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+        out = [np.zeros(max(n, 1)) for _ in range(4)]
+        rc = lib().orc_attraction_grad(self._h, *[_p(a) for a in arrs],
+                                       None if gg is None else _p(gg), *[_p(o) for o in out])
+        if rc != 0:
+            raise RuntimeError("attraction_grad needs a finished attraction without far pairs")
+        u, du, gE, gI = (o[:n] for o in out)
+        return dict(u=u, dudsigma=du, gE=gE if g is not None else None,
+                    gI=gI if g is not None else None)
+
     def select_partners(self, step: int):
         ne = int(lib().orc_num_elements(self._h))
         m = max(ne, 1)
@@ -235,6 +254,22 @@ def direct(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, targets=None):
     u = np.zeros(max(len(t), 1))
     lib().orc_direct(n, *[_p(a) for a in arrs], float(sigma), len(t), _p(t), _p(u))
     return u[: len(t)]
+
+
+def direct_grad(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, g=None):
+    """u, du/dsigma and (with g) dL/dw^E, dL/dw^I for L = sum_t g_t u(t), by
+    brute force over all pairs (FP64)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = pos.shape[1]
+    arrs = [np.ascontiguousarray(pos[d]) for d in range(3)] + [
+        _u8(type_), _u8(vac_axon), _u8(vac_dend_e), _u8(vac_dend_i)]
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    out = [np.zeros(max(n, 1)) for _ in range(4)]
+    lib().orc_direct_grad(n, *[_p(a) for a in arrs], float(sigma),
+                          None if gg is None else _p(gg), *[_p(o) for o in out])
+    u, du, gE, gI = (o[:n] for o in out)
+    return dict(u=u, dudsigma=du, gE=gE if g is not None else None,
+                gI=gI if g is not None else None)
 
 
 def hermite(nmax: int, x: float):

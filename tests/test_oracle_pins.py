@@ -614,3 +614,74 @@ def test_philox_statistics(oracle_mod):
     a = oracle_mod.philox([1, 2, 3, 4], [5, 6])
     b = oracle_mod.philox([1, 2, 3, 4], [5, 7])
     assert not np.array_equal(a, b)
+
+
+# -- derivatives of the attraction (the adjoint) ----------------------------
+def _grad_case(n=260, seed=4, **kw):
+    return W.uniform_cube(n, 3000.0, seed=seed, leaf_capacity=8, rho_max=0.0, cutoff=5.0, **kw)
+
+
+def test_dsigma_matches_central_difference_of_brute_force(oracle_mod):
+    # u by the independent brute-force routine at sigma (1 +- h)
+    w = _grad_case()
+    sig = w.params["sigma"]
+    r = oracle_mod.direct_grad(*w.arrays(), sig)
+    h = 1e-5
+    up = oracle_mod.direct(*w.arrays(), sig * (1 + h))
+    um = oracle_mod.direct(*w.arrays(), sig * (1 - h))
+    fd = (up - um) / (2 * sig * h)
+    m = np.abs(r["dudsigma"]) > 1e-9 * np.abs(r["dudsigma"]).max()
+    assert m.sum() > 100
+    assert np.max(np.abs(fd[m] - r["dudsigma"][m]) / np.abs(r["dudsigma"][m])) < 1e-6
+    assert np.allclose(r["u"], oracle_mod.direct(*w.arrays(), sig), rtol=1e-13, atol=0)
+
+
+def test_weight_gradient_is_the_transposed_transform(oracle_mod):
+    # u is linear in the dendritic weights: adding one element to w^T_s
+    # changes L = sum_t g_t u(t) (independent brute force) by exactly g^T_s
+    w = _grad_case()
+    sig = w.params["sigma"]
+    g = np.random.default_rng(2).normal(size=w.n)
+    r = oracle_mod.direct_grad(*w.arrays(), sig, g=g)
+    base = float(g @ oracle_mod.direct(*w.arrays(), sig))
+    # the whole identity: L = sum_s gE_s wE_s + gI_s wI_s
+    lin = float(r["gE"] @ w.vac_dend_e + r["gI"] @ w.vac_dend_i)
+    assert abs(lin - base) < 1e-12 * abs(base)
+    for s in (0, 17, 111, 259):
+        for ch, key in ((0, "gE"), (1, "gI")):
+            e, i = w.vac_dend_e.copy(), w.vac_dend_i.copy()
+            (e if ch == 0 else i)[s] += 1
+            up = float(g @ oracle_mod.direct(w.pos, w.type, w.vac_axon, e, i, sig))
+            assert abs((up - base) - r[key][s]) < 1e-10 * (abs(base) + 1.0)
+
+
+def test_gradient_over_the_leaf_pairs_equals_all_pairs(oracle_mod):
+    # pair lists from a tree built with every count 1 (no box is pruned for
+    # being empty), cutoff 5 sigma: the lists miss only terms below exp(-25)
+    w = _grad_case()
+    ones = np.ones(w.n, np.uint8)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(w.pos, w.type, ones, ones, ones)
+    o.attraction()
+    g = np.random.default_rng(3).normal(size=w.n)
+    r = o.attraction_grad(w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i, g=g)
+    ref = oracle_mod.direct_grad(*w.arrays(), w.params["sigma"], g=g)
+    for key in ("u", "dudsigma", "gE", "gI"):
+        scale = np.abs(ref[key]).max()
+        assert np.max(np.abs(r[key] - ref[key])) < 1e-9 * scale, key
+
+
+def test_gradient_u_equals_the_attraction_and_far_pairs_are_refused(oracle_mod):
+    w = _grad_case()
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    u = o.attraction()
+    r = o.attraction_grad(w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i)
+    assert np.allclose(r["u"], u, rtol=1e-12, atol=0)
+    wf = W.clustered_small(1, 1536, seed=9, leaf_capacity=8, rho_max=0.3, p=4)
+    of = oracle_mod.Oracle(wf.params)
+    of.build_tree(*wf.arrays())
+    of.attraction()
+    assert of.stats()["far_pairs"] > 0
+    with pytest.raises(RuntimeError):
+        of.attraction_grad(wf.type, wf.vac_axon, wf.vac_dend_e, wf.vac_dend_i)
