@@ -256,6 +256,28 @@ msp_status msp_step_graph_finish(msp_ctx *ctx, void *stream, uint64_t *next_step
  * allowed (the next eager attraction grows the table again). */
 msp_status msp_set_pair_capacity(msp_ctx *ctx, int64_t pairs);
 
+/* ---- Derivatives of the attraction (the adjoint of Eq. 8) -----------------
+ * With K(t,s) = exp(-|t - s|^2 / sigma^2), at the counts given here (DEVICE,
+ * caller order, n = the last build's neurons):
+ *   u(t)          = sum_{s != t} w_s^{T(t)} K(t,s)              (a_t > 0, else 0)
+ *   du_dsigma(t)  = sum_{s != t} w_s^{T(t)} K(t,s) 2 |t - s|^2 / sigma^3
+ *   grad_w_e(s), grad_w_i(s) = sum_{t != s, a_t > 0, T(t) = E resp. I} g_t K(t,s),
+ * i.e. the gradient of L = sum_t g_t u(t) with respect to the dendritic
+ * weights w^E, w^I (the transposed Gauss transform; dL/dsigma is
+ * sum_t g_t du_dsigma(t)).  The sums run over the near-field leaf pairs of
+ * the last msp_attraction, which must have no translated pairs
+ * (rho_max = 0).  Box pairs whose dendrite box had no vacant dendrites in the
+ * build are absent; to differentiate with respect to weights that are zero,
+ * build the tree with every count positive (e.g. all ones): the counts passed
+ * here are the ones the derivatives are taken at.  g may be NULL (then
+ * grad_w_* must be NULL); any output may be NULL.  Errors: MSP_ERR_NOT_BUILT,
+ * MSP_ERR_INVALID_ARG (translated pairs present).  Asynchronous. */
+msp_status msp_attraction_grad(msp_ctx *ctx, const uint8_t *type_dev,
+                               const uint8_t *vac_axon_dev, const uint8_t *vac_dend_e_dev,
+                               const uint8_t *vac_dend_i_dev, const float *g_dev, float *u_dev,
+                               float *du_dsigma_dev, float *grad_w_e_dev, float *grad_w_i_dev,
+                               void *stream);
+
 /* Sizes and counts of the last calls.  Synchronous. */
 msp_status msp_get_stats(msp_ctx *ctx, msp_stats *out);
 

@@ -20,6 +20,9 @@ void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vd
 void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const int32_t* pre,
                      const int32_t* post, const uint8_t* styp, uint8_t* va, uint8_t* vde,
                      uint8_t* vdi, cudaStream_t s);
+void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const uint8_t* vde,
+                     const uint8_t* vdi, const float* g, float* u, float* dud, float* gE,
+                     float* gI, cudaStream_t s);
 void graph_release(msp_ctx& c);
 void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s);
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s);
@@ -137,6 +140,8 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->pr_kind, &c->pr_cf, &c->pr_w, &c->far_q, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
                          &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1,
+                         &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
+                         &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
                          &c->leaf_items, &c->leaf_map, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
@@ -314,6 +319,16 @@ msp_status msp_step_graph_finish(msp_ctx* c, void* stream, uint64_t* next_step, 
     return guarded(c, [&] {
         require(next_step && halted, "null output");
         msp::graph_finish(*c, as_stream(stream), next_step, halted);
+    });
+}
+
+msp_status msp_attraction_grad(msp_ctx* c, const uint8_t* type, const uint8_t* va,
+                               const uint8_t* vde, const uint8_t* vdi, const float* g, float* u,
+                               float* du_dsigma, float* grad_we, float* grad_wi, void* stream) {
+    return guarded(c, [&] {
+        require(c->n == 0 || (type && va && vde && vdi), "null input pointer");
+        msp::attraction_grad(*c, type, va, vde, vdi, g, u, du_dsigma, grad_we, grad_wi,
+                             as_stream(stream));
     });
 }
 

@@ -31,7 +31,7 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
             "msp_export_expansions", "msp_last_error", "msp_direct_noalloc",
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-            "msp_set_pair_capacity", "msp_batch_layout")
+            "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -93,8 +93,10 @@ def load(path: str = LIB_PATH):
         L.msp_batch_layout.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, C.c_int, vp, vp, vp,
                                        C.POINTER(C.c_float), C.POINTER(C.c_int), vp]
         L.msp_batch_layout.restype = C.c_int
+        L.msp_attraction_grad.argtypes = [vp] * 11
+        L.msp_attraction_grad.restype = C.c_int
         for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-                     "msp_set_pair_capacity", "msp_batch_layout"):
+                     "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
@@ -251,6 +253,27 @@ class MSP:
                                           _ptr(sel["syn_pre"]), _ptr(sel["syn_post"]),
                                           _ptr(sel["syn_type"]), _ptr(vac_axon),
                                           _ptr(vac_dend_e), _ptr(vac_dend_i), _stream(stream)))
+
+    # -- derivatives ------------------------------------------------------------
+    def attraction_grad(self, type_, vac_axon, vac_dend_e, vac_dend_i, g=None, want_u=True,
+                        stream=None):
+        """u, du/dsigma and (with g) the gradient of sum_t g_t u(t) with respect to
+        w^E and w^I, over the near-field pairs of the last attraction, at the
+        given counts (CUDA uint8 tensors, caller order)."""
+        n = self.n
+        dev = type_.device
+        ins = [t.contiguous() for t in (type_, vac_axon, vac_dend_e, vac_dend_i)]
+        out = dict(u=torch.empty(n, dtype=torch.float32, device=dev) if want_u else None,
+                   du_dsigma=torch.empty(n, dtype=torch.float32, device=dev))
+        gg = None
+        if g is not None:
+            gg = g.to(torch.float32).contiguous()
+            out["grad_w_e"] = torch.empty(n, dtype=torch.float32, device=dev)
+            out["grad_w_i"] = torch.empty(n, dtype=torch.float32, device=dev)
+        _check(load().msp_attraction_grad(
+            self._h, *[_ptr(t) for t in ins], _ptr(gg), _ptr(out["u"]), _ptr(out["du_dsigma"]),
+            _ptr(out.get("grad_w_e")), _ptr(out.get("grad_w_i")), _stream(stream)))
+        return out
 
     # -- the whole step as a CUDA graph ---------------------------------------
     def step_graph_capture(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, first_step,
