@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="rerun the plan chooser on this workload and bench its plan")
-    ap.add_argument("--workload", default="clustered_1m", choices=["clustered_1m", "batched_256"],
+    ap.add_argument("--workload", default="clustered_1m",
+                    choices=["clustered_1m", "batched_256", "gradient_262k"],
                     help="clustered_1m: the headline network; batched_256: 256 independent "
-                         "networks (about 11.7M neurons) in one batched step")
+                         "networks (about 11.7M neurons) in one batched step; gradient_262k: "
+                         "the derivatives of the attraction at 262,144 clustered neurons")
     return ap.parse_args()
 
 
@@ -174,6 +176,90 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+# -- the derivative pass (config 4) ------------------------------------------------
+GRAD_METRIC = "gradient-pass neurons/s (u, du/dsigma, dL/dw) at 262k clustered neurons on GB300"
+
+
+def run_gradient(args, rank, world):
+    """u, du/dsigma and the weight gradient of L = sum g u over the leaf pairs
+    of a tree built with every count 1 (cutoff 5 sigma, no translations), at
+    the workload's counts; timed per pass with CUDA events, L2 flushed."""
+    import numpy as np
+    import torch
+
+    from paper_2301_10570_gb300 import msp, replicas, workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # leaf capacity 128: fastest of 64 / 128 / 192 for this pass (7.2 ms vs 11.1 / 7.9)
+    plan = dict(leaf_capacity=128, cutoff=5.0, rho_max=0.0, p=4, m2l_min_pairs=0)
+    w = W.clustered_small(16, 16_384, seed=15, **plan)
+    n = w.n
+    pos, t, a, e, i = msp.to_device(w, dev)
+    ones = torch.ones_like(a)
+    g = msp.MSP(w.params, device=dev.index)
+    g.build_tree(pos, t, ones, ones, ones)
+    g.attraction()
+    gv = torch.from_numpy(np.random.default_rng(6).normal(size=n)).float().to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        g.attraction_grad(t, a, e, i, g=gv)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    launches0 = g.stats()["kernel_launches"]
+    clocks = Clocks(dev.index)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        g.attraction_grad(t, a, e, i, g=gv)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    replicas.barrier()
+    clk = clocks.stop()
+    launches = g.stats()["kernel_launches"] - launches0
+    ms_list = [x.elapsed_time(y) for x, y in ev]
+    agg = replicas.aggregate_throughput(n, sum(ms_list) / len(ms_list), dev)
+    # exact interaction count: every target with a vacant axon against the
+    # sources of its leaf's partner leaves (self excluded), once forward and
+    # once transposed
+    tr, pr = g.export_tree(), g.export_pairs()
+    cnt = tr["count"].astype(np.int64)
+    p2p = pr["kind"] == 2
+    X, Y = pr["X"][p2p], pr["Y"][p2p]
+    act_sorted = (w.vac_axon[tr["perm"]] > 0).astype(np.int64)
+    first = tr["first"]
+    nact = np.array([act_sorted[first[k]:first[k] + cnt[k]].sum() for k in range(len(cnt))])
+    fwd = int((nact[X] * cnt[Y]).sum() - nact[X[X == Y]].sum())
+    inter = 2 * fwd
+    ms = agg["ms"]
+    achieved = inter / (ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * LANES_PER_SM_CLK / INSTR_PER_INTERACTION * sm_max * 1e6 / 1e9
+    g.close()
+    return {"metric": GRAD_METRIC, "value": agg["per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "gradient_262k: 16 Gaussian clusters x 16,384 neurons "
+                                   "(std 1500 um, cluster spacing of clustered_1m), sigma 750 um, "
+                                   "cutoff 5 sigma, pair lists from a tree with "
+                                   "every count 1; outputs u, du/dsigma, dL/dw^E, dL/dw^I",
+                       "plan": plan, "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MB write) between timed passes",
+                       "timing": "CUDA events per pass, mean over passes",
+                       "median_ms_per_step": round(statistics.median(ms_list), 3)},
+            "clocks": clk, "gpu_launches": int(launches),
+            "roofline": {"kernel": "k_grad_forward + k_grad_adjoint", "bound": "alu",
+                         "achieved": round(achieved, 1), "peak": round(peak, 1),
+                         "unit": "G interactions/s", "frac": round(achieved / peak, 4),
+                         "traffic": None, "interactions_per_step": inter,
+                         "peak_basis": "issue bound of the expanded-form evaluation (5 "
+                                       "instructions per interaction); these kernels use the "
+                                       "difference form (about 10)"}}
 
 
 # -- our arm -------------------------------------------------------------------
@@ -448,6 +534,14 @@ def main():
         for row in table:
             print(json.dumps(row), file=sys.stderr)
         _PLAN_OVERRIDE = best
+    if args.workload == "gradient_262k":
+        out = run_gradient(args, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
     out, w, g, u = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(
