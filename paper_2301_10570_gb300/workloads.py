@@ -146,6 +146,17 @@ class Batch:
                         self.vac_axon[a:b].copy(), self.vac_dend_e[a:b].copy(),
                         self.vac_dend_i[a:b].copy(), params)
 
+    def select(self, nets) -> "Batch":
+        """The networks `nets` of this batch, in that order."""
+        nets = [int(k) for k in nets]
+        idx = np.concatenate([np.arange(self.offsets[k], self.offsets[k + 1]) for k in nets])
+        sizes = np.diff(self.offsets)[nets]
+        return Batch(f"{self.name}_part", np.ascontiguousarray(self.pos[:, idx]),
+                     self.type[idx].copy(), self.vac_axon[idx].copy(),
+                     self.vac_dend_e[idx].copy(), self.vac_dend_i[idx].copy(),
+                     np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64),
+                     self.sigma[nets].copy(), [self.kinds[k] for k in nets])
+
     def placed(self, pos_placed: np.ndarray, side: float, **kw) -> Workload:
         """The whole batch as one problem of kernel width 1, from the placed
         positions (sigma units) and the domain side."""

@@ -113,3 +113,59 @@ def test_replicas_aggregate_over_two_gloo_ranks():
         assert wsize == 2 and r == rank
         assert agg["units"] == 3000 and agg["ms"] == 15.0
         assert agg["per_s"] == pytest.approx(3000 / 0.015)
+
+
+def _batch_worker(rank, world, port, q):
+    import os
+
+    import torch.distributed as dist
+
+    from paper_2301_10570_gb300 import replicas
+    from paper_2301_10570_gb300 import workloads as W
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = W.batched_small()
+    part = b.select(range(rank, len(b.sigma), world))
+    total = replicas.sum_over_ranks(part.n)
+    q.put((rank, part.n, int(total), part.sigma.tolist()))
+    dist.destroy_process_group()
+
+
+def test_batched_networks_split_over_two_gloo_ranks():
+    # every network on exactly one rank, no exchange; the ranks' neurons add up
+    import socket
+
+    import torch.multiprocessing as mp
+    from paper_2301_10570_gb300 import workloads as W
+    b = W.batched_small()
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][2] == res[1][2] == b.n == res[0][1] + res[1][1]
+    assert sorted(res[0][3] + res[1][3]) == sorted(b.sigma.tolist())
+
+
+def test_batch_select_keeps_networks_whole():
+    import numpy as np
+
+    from paper_2301_10570_gb300 import workloads as W
+    b = W.batched_small()
+    even, odd = b.select(range(0, 5, 2)), b.select(range(1, 5, 2))
+    assert even.n + odd.n == b.n
+    for part, nets in ((even, [0, 2, 4]), (odd, [1, 3])):
+        for j, k in enumerate(nets):
+            a0, a1 = part.offsets[j], part.offsets[j + 1]
+            b0, b1 = b.offsets[k], b.offsets[k + 1]
+            assert np.array_equal(part.pos[:, a0:a1], b.pos[:, b0:b1])
+            assert np.array_equal(part.vac_axon[a0:a1], b.vac_axon[b0:b1])
+            assert part.sigma[j] == b.sigma[k] and part.kinds[j] == b.kinds[k]
