@@ -65,12 +65,12 @@ _PLAN_OVERRIDE = None
 
 
 def tuned_params():
-    """Plan chosen by the autotuner for this workload (leaf capacity, cutoff,
+    """Plan chosen by the plan chooser for this workload (leaf capacity, cutoff,
     expansions; `python bench.py --autotune` reruns it, see
     paper_2301_10570_gb300/autotune.py and profiles/autotune_clustered_1m.md)."""
     if _PLAN_OVERRIDE is not None:
         return dict(_PLAN_OVERRIDE)
-    return dict(leaf_capacity=192, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+    return dict(leaf_capacity=256, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
 
 
 def workload():
@@ -111,12 +111,15 @@ def near_field_traffic():
         with open(path) as f:
             for line in f:
                 if ":" in line and line.split(":")[0].strip() in ("dram_bytes_per_launch",
-                                                                    "kernel_source_sha256"):
+                                                                    "kernel_source_sha256",
+                                                                    "plan_leaf_capacity"):
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip().strip("`")
         with open(src, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
         if fields.get("kernel_source_sha256") != sha:
+            return None
+        if fields.get("plan_leaf_capacity") != str(tuned_params()["leaf_capacity"]):
             return None
         return int(float(fields["dram_bytes_per_launch"]))
     except Exception:

@@ -17,7 +17,7 @@ import sys
 
 def _plan():
     # the benchmark's plan (leaf capacity, cutoff, no translations)
-    return dict(leaf_capacity=192, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+    return dict(leaf_capacity=256, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
 
 
 def near_field_131k():
