@@ -143,7 +143,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
-                         &c->leaf_items, &c->leaf_map, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
+                         &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
                          &c->small_dev, &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
                          &c->h_post, &c->h_type, &c->h_nsyn, &c->c_type, &c->c_va,

@@ -106,6 +106,7 @@ struct DevCounts {
     int64_t n_far, n_p2p, nseg;
     int64_t items[3];                        // descent items, rotating: in / out / reset
     int64_t n_leaf;                          // leaf pairs reached by the descent
+    int64_t leaf_next;                       // work counter of the leaf draw
     int64_t draws;
     int64_t n_req, n_syn;
     int64_t interactions;
@@ -173,8 +174,7 @@ struct msp_ctx {
     msp::DBuf expA, expM, expB;
     msp::DBuf u_sorted;
     // descent
-    msp::DBuf items0, items1, leaf_items, leaf_map, rq_key0, rq_key1, rq_val0, rq_val1, accepted,
-        acc_off;
+    msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
     // generic scratch
     msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist, sd_tmp;
     // device-resident sizes and their pinned host mirror

@@ -136,6 +136,7 @@ __global__ void k_init_items(const int4* __restrict__ sums, const double2* __res
     dc->items[0] = k;
     dc->items[1] = 0;
     dc->n_leaf = 0;
+    dc->leaf_next = 0;
     dc->draws = 0;
     dc->overflow &= ~6ll;       // the descent's bits; bit 0 (pair table) stays
 }
@@ -230,114 +231,171 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
     }
 }
 
-// The leaf pair reached by each (axon leaf, channel): the descent's items
-// partition the axon boxes of a channel, so every axon leaf has at most one.
-__global__ void k_leaf_map(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf,
-                           int64_t cap_leaf, int32_t* __restrict__ map) {
-    const int64_t n = min(*n_leaf, cap_leaf);
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const Item it = items[k];
-        map[2 * (int64_t)it.X + it.ch] = it.Y;
+// Per-element draw inside the chosen dendrite leaf, one warp per leaf pair
+// (X, Y, channel) taken from a device work counter: the warp stages Y's
+// points with their weights of the channel in shared memory, collects X's
+// neurons of that channel with vacant axons, and gives each lane one of them.
+// A lane forms the weights w_s K(t,s) of the sources s != t of Y, truncated at
+// the cutoff, their total and then the inclusive prefix sums in exact 64-bit
+// fixed point (scale 2^shift; a weight is at most 255: integer adds are exact
+// and full rate, where double precision adds are scarce on this GPU; weights
+// below 2^-shift, far below exp(-cutoff^2) for the cutoffs the library
+// accepts, count as zero).  The element draws r_e = floor(U_e tot) (U_e with
+// 53 bits) go in groups of up to 8 sorted thresholds; one prefix walk serves
+// a group: the first source whose inclusive prefix exceeds r_e.  Leaves of
+// more than kLdStage points (possible only where coincident points overfill a
+// leaf at the deepest level) read their points from global memory.
+constexpr int kLdWarps = 4;
+constexpr int kLdStage = 256;
+
+struct LdSrc {
+    const float4* sp;      // staged points {x, y, z, w} or null (global memory)
+    const float4* pts;
+    const float2* wts;
+    int32_t sf;
+    int ch;
+    __device__ float4 get(int j) const {
+        if (sp) return sp[j];
+        const float4 S = pts[sf + j];
+        return make_float4(S.x, S.y, S.z, ch ? wts[sf + j].y : wts[sf + j].x);
     }
+};
+
+__device__ __forceinline__ uint64_t ld_weight(const float4& T, const float4& S, float k2,
+                                              float rc2, int shift) {
+    const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ws = r2 < rc2 ? S.w * ex2_approx_sel(-r2 * k2) : 0.f;
+    return __float2ull_rz(ldexpf(ws, shift));
 }
 
-// Per-element draw inside the chosen dendrite leaf, one thread per axon
-// neuron t (sorted order): weights w_s K(t,s) of the sources s != t of the
-// leaf, truncated at the cutoff, and the inclusive prefix sums over the
-// leaf's order.
-__global__ void k_leaf_draw(int64_t n, const int32_t* __restrict__ leaf_of,
-                            const int32_t* __restrict__ map, const int32_t* __restrict__ nfirst,
-                            const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
-                            const float2* __restrict__ wts, const int32_t* __restrict__ perm,
-                            const int32_t* __restrict__ eoff, float k2, float rc2, uint64_t seed,
-                            StepRef stp, int32_t* __restrict__ partner,
-                            unsigned long long* __restrict__ draw_ctr,
-                            const int64_t* __restrict__ n_elem) {
+__global__ void __launch_bounds__(kLdWarps * 32)
+k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf, int64_t cap_leaf,
+              unsigned long long* __restrict__ next, const int32_t* __restrict__ nfirst,
+              const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
+              const float2* __restrict__ wts, const int32_t* __restrict__ perm,
+              const int32_t* __restrict__ eoff, float k2, float rc2, uint64_t seed, StepRef stp,
+              int32_t* __restrict__ partner, unsigned long long* __restrict__ draw_ctr,
+              const int64_t* __restrict__ n_elem) {
+    __shared__ float4 s_pts[kLdWarps][kLdStage];
+    __shared__ int32_t s_tl[kLdWarps][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t step = stp.get();
     const int64_t ne = *n_elem;
+    const int64_t n_items = min(*n_leaf, cap_leaf);
     unsigned long long draws = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const float4 T = pts[t];
-        const uint32_t tw = __float_as_uint(T.w);
-        const int ch = pk_type(tw) ? 1 : 0;
-        const int a = (int)pk_axon(tw);
-        if (a == 0) continue;
-        const int32_t Y = map[2 * (int64_t)leaf_of[t] + ch];
-        if (Y < 0) continue;
-        const int32_t sf = nfirst[Y], sc = ncount[Y];
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(next, 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if ((int64_t)k >= n_items) break;
+        const Item it = items[k];
+        const int ch = it.ch;
+        const int32_t tf = nfirst[it.X], tc = ncount[it.X];
+        const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
         // fixed-point scale: sc weights of at most 2^8 must stay below 2^63
         int lg = 0;
         while ((1 << lg) < sc + 1 && lg < 30) ++lg;
         const int shift = min(40, 55 - lg);
-        // Prefix sums of the weights in exact 64-bit fixed point (scale
-        // 2^shift; a weight is at most 255): integer adds are exact and full
-        // rate, where double precision adds are scarce on this GPU.  Weights
-        // below 2^-shift (far below exp(-cutoff^2) for the cutoffs the library
-        // accepts) count as zero.
-        uint64_t tot = 0;
-        for (int32_t s = sf; s < sf + sc; ++s) {
-            if (s == t) continue;
-            const float4 S = pts[s];
-            const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-            tot += __float2ull_rz(ldexpf(ws, shift));
+        LdSrc src{nullptr, pts, wts, sf, ch};
+        if (sc <= kLdStage) {
+            __syncwarp();
+            for (int j = lane; j < sc; j += 32) {
+                const float4 S = pts[sf + j];
+                s_pts[w][j] = make_float4(S.x, S.y, S.z, ch ? wts[sf + j].y : wts[sf + j].x);
+            }
+            __syncwarp();
+            src.sp = s_pts[w];
         }
-        const int32_t to = perm[t];
-        if (tot == 0 || (int64_t)eoff[to] + a > ne) continue;
-        // the element draws r_e = floor(U_e * tot) (U_e with 53 bits), in
-        // groups of up to 8 sorted thresholds; one prefix walk over the leaf
-        // serves a whole group: the first source whose inclusive prefix
-        // exceeds r_e
-        constexpr int kGroup = 8;
-        for (int e0 = 0; e0 < a; e0 += kGroup) {
-            const int ng = min(kGroup, a - e0);
-            uint64_t r[kGroup];
-            int ord[kGroup];
-            for (int e = 0; e < ng; ++e) {
-                uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
-                uint32_t o4[4];
-                philox_draw(seed, (uint32_t)to, c1, step, o4);
-                uint64_t u53 = (((uint64_t)o4[0] << 32) | o4[1]) >> 11;
-                uint64_t v = __umul64hi(u53 << 11, tot);     // floor(u53 * tot / 2^53)
-                int j = e;
-                while (j > 0 && r[j - 1] > v) {
-                    r[j] = r[j - 1];
-                    ord[j] = ord[j - 1];
-                    --j;
+        int32_t pos = 0;
+        while (pos < tc) {
+            // up to 32 of X's neurons of the channel with vacant axons, from pos on
+            int nt = 0;
+            while (pos < tc && nt < 32) {
+                const int32_t tt = tf + pos + lane;
+                uint32_t tw = 0;
+                if (pos + lane < tc) tw = __float_as_uint(pts[tt].w);
+                const bool mine =
+                    pos + lane < tc && pk_axon(tw) > 0 && (pk_type(tw) ? 1 : 0) == ch;
+                const unsigned mask = __ballot_sync(0xffffffffu, mine);
+                const int room = 32 - nt, cnt = __popc(mask);
+                const int take = min(cnt, room);
+                const int rank = __popc(mask & ((1u << lane) - 1u));
+                if (mine && rank < take) s_tl[w][nt + rank] = tt;
+                nt += take;
+                if (take < cnt) {
+                    // continue after the lane of the last target taken
+                    pos += (int32_t)__fns(mask, 0, take) + 1;
+                    break;
                 }
-                r[j] = v;
-                ord[j] = e;
+                pos += 32;
             }
-            int32_t pick[kGroup];
-            uint64_t pre = 0;
-            int next = 0;
-            uint64_t rn = r[0];          // the smallest threshold not yet crossed
-            for (int32_t s = sf; s < sf + sc && next < ng; ++s) {
-                if (s == t) continue;
-                const float4 S = pts[s];
-                const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ws = r2 < rc2 ? (ch ? wts[s].y : wts[s].x) * ex2_approx_sel(-r2 * k2) : 0.f;
-                pre += __float2ull_rz(ldexpf(ws, shift));
-                if (pre > rn) {
-                    do {
-                        pick[ord[next++]] = s;
-                        rn = next < ng ? r[next] : 0;
-                    } while (next < ng && pre > rn);
+            __syncwarp();
+            const bool act = lane < nt;
+            const int32_t t = act ? s_tl[w][lane] : tf;
+            __syncwarp();
+            const float4 T = pts[t];
+            const int a = act ? (int)pk_axon(__float_as_uint(T.w)) : 0;
+            // totals: all lanes walk the same points (shared-memory broadcast)
+            uint64_t tot = 0;
+            if (nt > 0) {
+                for (int j = 0; j < sc; ++j) {
+                    const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                    tot += sf + j == t ? 0ull : v;
                 }
             }
-            // r < tot = the final prefix, so every threshold was crossed
-            for (int e = 0; e < ng; ++e) {
-                partner[eoff[to] + e0 + e] = perm[pick[e]];
-                ++draws;
+            const int32_t to = perm[t];
+            const bool draw = act && tot != 0 && (int64_t)eoff[to] + a <= ne;
+            constexpr int kGroup = 8;
+            const int groups = draw ? (a + kGroup - 1) / kGroup : 0;
+            const int gmax = __reduce_max_sync(0xffffffffu, groups);
+            for (int gi = 0; gi < gmax; ++gi) {
+                const int e0 = gi * kGroup;
+                const int ng = gi < groups ? min(kGroup, a - e0) : 0;
+                uint64_t r[kGroup];
+                int ord[kGroup];
+                for (int e = 0; e < ng; ++e) {
+                    uint32_t c1 = (uint32_t)(e0 + e) | ((uint32_t)ch << 8) | (kTagLeaf << 16);
+                    uint32_t o4[4];
+                    philox_draw(seed, (uint32_t)to, c1, step, o4);
+                    uint64_t u53 = (((uint64_t)o4[0] << 32) | o4[1]) >> 11;
+                    uint64_t v = __umul64hi(u53 << 11, tot);     // floor(u53 * tot / 2^53)
+                    int jj = e;
+                    while (jj > 0 && r[jj - 1] > v) {
+                        r[jj] = r[jj - 1];
+                        ord[jj] = ord[jj - 1];
+                        --jj;
+                    }
+                    r[jj] = v;
+                    ord[jj] = e;
+                }
+                int32_t pick[kGroup];
+                uint64_t pre = 0;
+                int nx = 0;
+                uint64_t rn = ng > 0 ? r[0] : 0;       // the smallest threshold not yet crossed
+                for (int j = 0; j < sc; ++j) {
+                    if (!__any_sync(0xffffffffu, nx < ng)) break;
+                    if (nx < ng) {
+                        const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                        pre += sf + j == t ? 0ull : v;
+                        if (pre > rn) {
+                            do {
+                                pick[ord[nx++]] = sf + j;
+                                rn = nx < ng ? r[nx] : 0;
+                            } while (nx < ng && pre > rn);
+                        }
+                    }
+                }
+                // r < tot = the final prefix, so every threshold was crossed
+                for (int e = 0; e < ng; ++e) {
+                    partner[eoff[to] + e0 + e] = perm[pick[e]];
+                    ++draws;
+                }
             }
         }
     }
     for (int o = 16; o > 0; o >>= 1) draws += __shfl_xor_sync(0xffffffffu, draws, o);
-    if ((threadIdx.x & 31) == 0 && draws) atomicAdd(draw_ctr, draws);
+    if (lane == 0 && draws) atomicAdd(draw_ctr, draws);
 }
 
 // requests in element order: flag, then key = (dendrite*2 + channel) << 32 | priority
@@ -550,16 +608,12 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
                                                  cap_leaf, ct);
         MSP_LAUNCH("descend");
     }
-    // the leaf pair of each (axon leaf, channel), then one thread per neuron
-    int32_t* lmap = c.leaf_map.ensure<int32_t>((size_t)(2 * c.n_nodes));
-    MSP_CUDA(cudaMemsetAsync(lmap, 0xff, (size_t)(2 * c.n_nodes) * sizeof(int32_t), s));
-    k_leaf_map<<<grid_for(cap_leaf, B, (int64_t)c.sm_count * 4), B, 0, s>>>(lit, &dc->n_leaf,
-                                                                           cap_leaf, lmap);
-    MSP_LAUNCH("leaf_map");
-    k_leaf_draw<<<grid_for(n, 128, (int64_t)c.sm_count * 64), 128, 0, s>>>(
-        n, c.leaf_of.get<int32_t>(), lmap, c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-        c.pts.get<float4>(), c.wts.get<float2>(), c.perm.get<int32_t>(),
-        c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, stp, partner, ull(&dc->draws), &dc->n_elem);
+    // one warp per leaf pair, from a device work counter
+    k_leaf_draw_w<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 8), kLdWarps * 32, 0, s>>>(
+        lit, &dc->n_leaf, cap_leaf, ull(&dc->leaf_next), c.nd_first.get<int32_t>(),
+        c.nd_count.get<int32_t>(), c.pts.get<float4>(), c.wts.get<float2>(),
+        c.perm.get<int32_t>(), c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, stp, partner,
+        ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
 
     // a12: requests, sorted by (dendrite, channel, priority, element)
