@@ -398,7 +398,7 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
     if (lane == 0 && draws) atomicAdd(draw_ctr, draws);
 }
 
-// requests in element order: flag, then key = (dendrite*2 + channel) << 32 | priority
+// requests in element order: flag, then key = priority << 32 | (dendrite*2 + channel)
 __global__ void k_request_flags(const int32_t* __restrict__ partner,
                                 const int64_t* __restrict__ n_dev, int32_t* __restrict__ flag) {
     const int64_t n_elem = *n_dev;
@@ -426,26 +426,41 @@ __global__ void k_request_emit(int64_t n, const uint8_t* __restrict__ type,
             uint32_t o[4];
             philox_draw(seed, (uint32_t)t, (uint32_t)k | (kTagAccept << 16), step, o);
             int32_t r = roff[e0 + k];
-            key[r] = ((uint64_t)((uint32_t)s * 2u + ch) << 32) | o[0];
+            key[r] = ((uint64_t)o[0] << 32) | ((uint32_t)s * 2u + ch);
             val[r] = e0 + k;
         }
     }
 }
 
-// a dendrite neuron accepts, per channel, its first `capacity` requests in
-// (priority, element) order: request i is accepted unless request i - cap
-// belongs to the same (dendrite, channel) group
+// A dendrite neuron accepts, per channel, its first `capacity` requests in
+// (priority, element) order.  The requests are sorted stably by group
+// (dendrite, channel) only, so inside a group they are in element order; the
+// rank of request i is the number of requests of its group before it in
+// (priority, element) order: those with a smaller priority, and those earlier
+// in the group with an equal one.  Groups are small (the requests one neuron
+// receives), so each request counts over its group directly.
 __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
                          const int64_t* __restrict__ nr_dev, const uint8_t* __restrict__ vde,
                          const uint8_t* __restrict__ vdi, uint8_t* __restrict__ accepted) {
     const int64_t nr = *nr_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t g = (uint32_t)(key[i] >> 32);
-        uint32_t s = g >> 1;
-        int cap = (g & 1u) ? vdi[s] : vde[s];
-        bool ok = cap > 0 && (i < cap || (uint32_t)(key[i - cap] >> 32) != g);
-        accepted[val[i]] = ok ? 1 : 0;
+        const uint64_t ki = key[i];
+        const uint32_t g = (uint32_t)ki, pr = (uint32_t)(ki >> 32);
+        const uint32_t s = g >> 1;
+        const int cap = (g & 1u) ? vdi[s] : vde[s];
+        int rank = 0;
+        for (int64_t j = i - 1; j >= 0 && rank < cap; --j) {
+            const uint64_t kj = key[j];
+            if ((uint32_t)kj != g) break;
+            rank += (uint32_t)(kj >> 32) <= pr;
+        }
+        for (int64_t j = i + 1; j < nr && rank < cap; ++j) {
+            const uint64_t kj = key[j];
+            if ((uint32_t)kj != g) break;
+            rank += (uint32_t)(kj >> 32) < pr;
+        }
+        accepted[val[i]] = rank < cap ? 1 : 0;
     }
 }
 
@@ -616,7 +631,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
 
-    // a12: requests, sorted by (dendrite, channel, priority, element)
+    // a12: requests grouped by (dendrite, channel), ranked by (priority, element)
     int32_t* flag = c.cnt.ensure<int32_t>((size_t)ne);
     int32_t* roff = c.off.ensure<int32_t>((size_t)ne);
     const int gn = grid_for(n, B, (int64_t)c.sm_count * 16);
@@ -632,7 +647,8 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     k_request_emit<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff,
                                     cfg.seed, stp, k0, v0, &dc->n_elem);
     MSP_LAUNCH("request_emit");
-    radix_sort_dev(c, k0, v0, k1, v1, &dc->n_req, ne, 32 + bits_for_sel(2 * n), s);
+    // stable sort by (dendrite, channel): the low bits of the key
+    radix_sort_dev(c, k0, v0, k1, v1, &dc->n_req, ne, bits_for_sel(2 * n), s);
     k_accept<<<ge, B, 0, s>>>(k0, v0, &dc->n_req, vde_dev, vdi_dev, acc);
     MSP_LAUNCH("accept");
     k_acc_flags<<<ge, B, 0, s>>>(acc, &dc->n_elem, flag);
