@@ -243,7 +243,9 @@ msp_status msp_step_graph_capture(msp_ctx *ctx, int64_t n, const float *x_dev,
                                   int64_t syn_capacity, int64_t *n_syn_dev,
                                   int64_t *history_dev, int64_t history_len,
                                   uint64_t first_step, void *stream);
-/* Enqueues n_steps replays on `stream`.  Asynchronous. */
+/* Enqueues n_steps replays on `stream`.  Asynchronous.  Fails with
+ * MSP_ERR_NOT_BUILT if any workspace buffer of the library was reallocated
+ * since the capture (an eager call on larger inputs): capture again. */
 msp_status msp_step_graph_launch(msp_ctx *ctx, int64_t n_steps, void *stream);
 /* Waits for the replays (see above).  msp_get_stats then reports the last
  * replay's sizes and, in near_field_ms and p2p_interactions, the means over

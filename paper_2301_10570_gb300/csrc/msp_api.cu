@@ -35,6 +35,7 @@ thread_local std::string g_last_error;
 
 namespace msp {
 std::atomic<long long> g_kernel_launches{0};
+std::atomic<long long> g_alloc_epoch{0};
 void set_last_error(const char* msg) { g_last_error = msg; }
 }
 

@@ -194,11 +194,16 @@ void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s) {
     // the event-record nodes are addressed through the template graph, so
     // it lives as long as the executable graph
     c.g_template = graph;
+    c.g_epoch = g_alloc_epoch.load();
     cudaStreamDestroy(cs);
 }
 
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s) {
     if (!c.gexec) throw Error(MSP_ERR_NOT_BUILT, "no captured step graph");
+    // a workspace buffer reallocated since the capture (by an eager call)
+    // would leave the graph's kernels pointing at freed memory
+    if (g_alloc_epoch.load() != c.g_epoch)
+        throw Error(MSP_ERR_NOT_BUILT, "workspace changed since the capture: capture again");
     // replays accumulate until graph_finish; each has its own event pair
     const size_t need = (size_t)(2 * (c.g_replays + n_steps));
     while (c.g_events.size() < need) {

@@ -42,6 +42,11 @@ extern std::atomic<long long> g_kernel_launches;
     (::msp::g_kernel_launches.fetch_add(1, std::memory_order_relaxed), \
      ::msp::cuda_check(cudaGetLastError(), what))
 
+// Bumped whenever a workspace buffer is (re)allocated or freed: a captured
+// step graph records it and refuses to replay once it changed (its kernels
+// hold the old addresses).
+extern std::atomic<long long> g_alloc_epoch;
+
 // grow-only device buffer
 struct DBuf {
     void* p = nullptr;
@@ -53,6 +58,7 @@ struct DBuf {
         size_t need = count * sizeof(T);
         if (need == 0) need = sizeof(T);
         if (need > bytes) {
+            g_alloc_epoch.fetch_add(1, std::memory_order_relaxed);
             if (p) cudaFree(p);
             p = nullptr;
             bytes = 0;
@@ -62,25 +68,8 @@ struct DBuf {
         }
         return static_cast<T*>(p);
     }
-    // grow to `count` elements keeping the first `keep` (stream-ordered copy)
-    template <class T>
-    T* grow(size_t count, size_t keep, cudaStream_t s) {
-        size_t need = count * sizeof(T);
-        if (need == 0) need = sizeof(T);
-        if (need <= bytes) return static_cast<T*>(p);
-        size_t alloc = need + need / 2 + 256;
-        void* q = nullptr;
-        cuda_check(cudaMalloc(&q, alloc), "cudaMalloc");
-        if (p && keep)
-            cuda_check(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s),
-                       "cudaMemcpyAsync");
-        cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-        if (p) cudaFree(p);
-        p = q;
-        bytes = alloc;
-        return static_cast<T*>(p);
-    }
     void release() {
+        if (p) g_alloc_epoch.fetch_add(1, std::memory_order_relaxed);
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
@@ -200,6 +189,7 @@ struct msp_ctx {
     std::vector<cudaEvent_t> g_events;         // two per replay of the last launch
     int64_t g_replays = 0;                     // replays of the last launch
     int g_left_slot = 0;                       // descent counter slot that must end empty
+    long long g_epoch = -1;                    // allocation epoch at capture
     double g_nf_ms_mean = 0.0;                 // mean near-field time over them
     bool last_was_graph = false;               // statistics come from graph replays
     struct GraphArgs {

@@ -153,3 +153,25 @@ def test_full_size_graph_replays_equal_eager_steps():
         assert np.array_equal(x, y)
     for key in ("pre", "post", "typ"):
         assert np.array_equal(lg[key], le[key])
+
+
+def test_graph_refuses_to_replay_after_workspace_reallocation():
+    # any workspace (re)allocation after the capture, here the batch
+    # layout's scratch, invalidates the graph: launch fails, a new capture works
+    from paper_2301_10570_gb300 import workloads as W2
+    w = _workload()
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    g.step_graph_capture(pos, t, a, e, i, first_step=0)
+    g.run_steps(0, 1)
+    b = W2.batched_small()
+    msp.batch_layout(torch.from_numpy(b.pos).cuda(), b.offsets, b.sigma, 3.25, 16)
+    with pytest.raises(msp.MSPError):
+        g.step_graph_launch(1)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    g.step_graph_capture(pos, t, a, e, i, first_step=1)
+    assert g.run_steps(1, 2) == 3
+    g.close()
