@@ -5,18 +5,17 @@
 // leaves Y (a contiguous segment of the pair list sorted by X).  Blocks take
 // the segments longest first (the order comes from an estimate of each
 // segment's work), so the last wave of blocks is short.  The block collects
-// the targets of X with vacant axons, up to 128 at a time, excitatory ones
-// first (their count padded to even), and evaluates them in passes of up to
-// 64; the warps take the partner pairs round-robin.  Each warp stages the
-// sources of its current pair in its own shared memory and every lane
-// evaluates them against its targets:
-// every lane holds 2 targets of one channel (the E-first order with even
-// padding guarantees it), so one staged source serves both with one
-// shared-memory load; passes of up to 32 targets pad their target pairs to
-// P = 2^k and 32/P lanes share a pair, walking interleaved slices of the
-// sources (small leaves still fill the warp).
-// Capping a pass at 64 targets keeps the kernel at 64 registers (8 blocks of
-// 4 warps per SM).
+// the targets of X with vacant axons, up to 125 at a time, excitatory ones
+// first (their count padded with empty slots to a multiple of 4 when
+// inhibitory ones follow), and evaluates them in one pass; the warps take the
+// partner pairs round-robin.  Each warp stages the sources of its current
+// pair in its own shared memory and every lane evaluates them against its
+// targets: a lane holds 2 targets (passes of up to 64) or 4 (up to 128), all
+// of one channel, so one staged source (one shared-memory load) serves 2 or 4
+// evaluations; passes of up to 32 targets pad their target pairs to P = 2^k
+// and 32/P lanes share a pair, walking interleaved slices of the sources
+// (small leaves still fill the warp).  The kernel takes 72 registers (7
+// blocks of 4 warps per SM).
 // The per-target sums of the 4 warps are added in a fixed order, so u is
 // reproducible run to run.  Per pair, the warp reduces the box-pair
 // attraction W(X,Y) = sum_t a_t sum_s w_s K(t,s) of each channel in single
@@ -43,13 +42,13 @@ namespace {
 
 // the block's transposed per-pair W buffer (16 pairs x 32 lanes per warp, one
 // padding column), set by the kernel before use
-__shared__ float2* s_wt;
+__shared__ float* s_wt;
 __shared__ int32_t* s_wii;
 
 constexpr int kNFWarps = 4;
 constexpr int kNFStage = 64;
-constexpr int kNFMaxT = 32 * 2;    // targets per pass (at most 2 per lane: 64 registers)
-constexpr int kNFList = 128;       // targets collected per round
+constexpr int kNFMaxT = 32 * 4;    // targets per pass (2 or 4 per lane)
+constexpr int kNFList = 128;       // target slots per round (one pass)
 constexpr float kNFFastT2 = 20.f;  // largest |t^|^2 of the expanded form
 
 __device__ inline float nf_ex2(float x) {
@@ -77,15 +76,22 @@ struct NFArgs {
     unsigned long long* work;
 };
 
-// the targets of a lane (R of them, one channel)
+// the targets of a lane (R of them, one channel); their scale factors and
+// axon weights sit in shared memory by slot (s_scale, s_fa)
 template <int R>
 struct Tgts {
     float x[R], y[R], z[R];   // 2 t^ (expanded form) or t^ (difference form)
-    float scale[R];           // 2^(-|t^|^2) or 1
-    float fa[R];              // a_t * scale, 0 for padding
-    int32_t t[R];             // sorted index, -1 for padding
     int ch;                   // 0 excitatory, 1 inhibitory
+    int slot0;                // slot of target 0 (targets r at slot0 + r)
 };
+
+// per slot of the current pass: 2^(-|t^|^2) (or 1), a_t times it (0 for
+// padding) and the target list (sorted index, -1 for padding; slots past the
+// pass hold stale entries whose results are discarded), set by the kernel
+// before use
+__shared__ float* s_scale;
+__shared__ float* s_fa;
+__shared__ const int32_t* s_tl;
 
 // Evaluate the staged sources [0, m) (lane slice ksl of `slices`) against the
 // lane's R targets.  MODE 0: expanded exponent; 1: expanded, skipping the
@@ -93,8 +99,9 @@ struct Tgts {
 template <int R, int MODE>
 __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int slices,
                                         const Tgts<R>& tg, int32_t base, float (&part)[R]) {
-    // U sources per iteration, two partial sums per target
-    constexpr int U = 4;
+    // U sources per iteration (two with four targets: register budget), two
+    // partial sums per target
+    constexpr int U = R == 4 ? 2 : 4;
     float p[R][2];
 #pragma unroll
     for (int r = 0; r < R; ++r) p[r][0] = p[r][1] = 0.f;
@@ -154,7 +161,7 @@ __device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int sl
                     const float dx = tg.x[r] - A.x, dy = tg.y[r] - A.y, dz = tg.z[r] - A.z;
                     v = nf_ex2(A.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 }
-                if (MODE == 1 || MODE == 3) v = base + e == tg.t[r] ? 0.f : v;
+                if (MODE == 1 || MODE == 3) v = base + e == s_tl[tg.slot0 + r] ? 0.f : v;
                 p[r][0] += v;
             }
         }
@@ -170,8 +177,9 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                                          int slices, const Tgts<R>& tg, float (&acc)[R],
                                          float4* stw, unsigned long long& evals, int nreal) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 (*wt)[33] = reinterpret_cast<float2 (*)[33]>(s_wt + w * 16 * 33);
+    float (*wt)[33] = reinterpret_cast<float (*)[33]>(s_wt + w * 16 * 33);
     int32_t* wii = s_wii + w * 16;
+    const unsigned imask = __ballot_sync(0xffffffffu, tg.ch != 0);   // inhibitory lanes
     for (int32_t cb = i0 + w; cb < i1; cb += 32 * kNFWarps) {
         // metadata of the warp's next 32 pairs, one per lane
         int32_t mi = cb + kNFWarps * lane, msf = 0, msc = 0;
@@ -213,30 +221,30 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 acc[k] += part[k];
-                v = fmaf(tg.fa[k], part[k], v);
+                v = fmaf(s_fa[tg.slot0 + k], part[k], v);
             }
             // W(X,Y) of each channel: every lane's term goes into a transposed
             // buffer; every 16 pairs the warp sums the rows (half a row per
             // lane, then one shuffle) and adds them to the pairs' slots
             const int slot = r & 15;
-            wt[slot][lane] = tg.ch ? make_float2(0.f, v) : make_float2(v, 0.f);
+            wt[slot][lane] = v;
             if (lane == 0) wii[slot] = ii;
             if (slot == 15 || r == nb - 1) {
                 __syncwarp();
                 const int row = lane & 15, half = lane >> 4;
-                float2 s2 = make_float2(0.f, 0.f);
+                float sE = 0.f, sI = 0.f;
 #pragma unroll 4
                 for (int c = 0; c < 16; ++c) {
-                    float2 v2 = wt[row][half * 16 + c];
-                    s2.x += v2.x;
-                    s2.y += v2.y;
+                    const int col = half * 16 + c;
+                    const float v2 = wt[row][col];
+                    if ((imask >> col) & 1u) sI += v2; else sE += v2;
                 }
-                s2.x += __shfl_down_sync(0xffffffffu, s2.x, 16);
-                s2.y += __shfl_down_sync(0xffffffffu, s2.y, 16);
+                sE += __shfl_down_sync(0xffffffffu, sE, 16);
+                sI += __shfl_down_sync(0xffffffffu, sI, 16);
                 if (lane <= slot) {
                     const int32_t pi = wii[lane];
                     float2 cur = a.w32[pi];
-                    a.w32[pi] = make_float2(cur.x + s2.x, cur.y + s2.y);
+                    a.w32[pi] = make_float2(cur.x + sE, cur.y + sI);
                 }
                 __syncwarp();
             }
@@ -245,35 +253,35 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
     }
 }
 
-// One pass over the targets tl[0, nt) (nt <= 64; tl[k] < 0 is padding);
-// nreal of them are real.  A lane holds the two targets of slots 2j and
-// 2j+1 (one channel); with fewer than 33 targets the target pairs are padded
-// to a power of two P and 32/P lanes share a pair, each walking an
-// interleaved slice of the sources.
+// One pass over the targets tl[0, nt) (nt <= R * 32; tl[k] < 0 is padding);
+// nreal of them are real.  A lane holds the R targets of slots R j .. R j + R-1
+// (one channel); when they fit in fewer lanes the target groups are padded to
+// a power of two P and 32/P lanes share a group, each walking an interleaved
+// slice of the sources.
 template <int R>
 __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, int nt, int nreal,
                                            int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
                                            float cy, float cz, float4* stw,
                                            float (*red)[kNFMaxT], unsigned long long& evals) {
-    static_assert(R == 2, "two targets per lane");
+    static_assert(R == 2 || R == 4, "two or four targets per lane");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0;
-    while ((1 << lg) < (nt + 1) / 2) ++lg;
-    const int npr = 1 << lg;                // lanes per slice (target pairs)
+    while ((1 << lg) < (nt + R - 1) / R) ++lg;
+    const int npr = 1 << lg;                // lanes per slice (target groups)
     const int slices = 32 >> lg;
     const int j = lane & (npr - 1);
     const int ksl = lane >> lg;
     Tgts<R> tg;
+    tg.slot0 = R * j;
     float acc[R];
     {
-        // the channel of the lane's first slot (both slots share it)
-        const int s0 = 2 * j;
-        const int32_t t0 = s0 < nt ? tl[s0] : -1;
+        // the channel of the lane's first slot (all its slots share it)
+        const int32_t t0 = tg.slot0 < nt ? tl[tg.slot0] : -1;
         tg.ch = t0 >= 0 ? (pk_type(__float_as_uint(a.pts[t0].w)) ? 1 : 0) : 0;
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int slot = 2 * j + r;
+        const int slot = tg.slot0 + r;
         const int32_t ts = slot < nt ? tl[slot] : -1;
         const bool valid = ts >= 0;
         const int32_t t = valid ? ts : tl[0];          // tl[0] is always a real target
@@ -283,45 +291,53 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         tg.x[r] = fast ? 2.f * hx : hx;
         tg.y[r] = fast ? 2.f * hy : hy;
         tg.z[r] = fast ? 2.f * hz : hz;
-        tg.scale[r] = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
-        tg.fa[r] = valid ? (float)pk_axon(tw) * tg.scale[r] : 0.f;
-        tg.t[r] = valid ? t : -1;
         acc[r] = 0.f;
+        if (w == 0 && ksl == 0) {
+            const float sc = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
+            s_scale[slot] = sc;
+            s_fa[slot] = valid ? (float)pk_axon(tw) * sc : 0.f;
+        }
     }
+    __syncthreads();
     nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nreal);
-    // the slices of a target pair, then the 4 warps in a fixed order
+    // the slices of a target group, then the 4 warps in a fixed order
 #pragma unroll
     for (int r = 0; r < R; ++r)
         for (int o = npr; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     if (ksl == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) red[w][2 * j + r] = acc[r];
+        for (int r = 0; r < R; ++r) red[w][tg.slot0 + r] = acc[r];
     }
     __syncthreads();
     if (w == 0 && ksl == 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int slot = 2 * j + r;
-            if (tg.t[r] >= 0) {
-                float s = red[0][slot];
+            const int slot = tg.slot0 + r;
+            const int32_t t = slot < nt ? tl[slot] : -1;
+            if (t >= 0) {
+                float sacc = red[0][slot];
 #pragma unroll
-                for (int k = 1; k < kNFWarps; ++k) s += red[k][slot];
-                a.u[tg.t[r]] += s * tg.scale[r];
+                for (int k = 1; k < kNFWarps; ++k) sacc += red[k][slot];
+                a.u[t] += sacc * s_scale[slot];
             }
         }
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
+__global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
     __shared__ float4 st[kNFWarps][2 * kNFStage];
     __shared__ float red[kNFWarps][kNFMaxT];
     __shared__ int32_t tl[kNFList];
-    __shared__ int s_nt, s_nreal, s_pos;
-    __shared__ float2 wt_all[kNFWarps][16][33];
+    __shared__ int s_nt, s_pos;
+    __shared__ float wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
+    __shared__ float scale_all[kNFMaxT], fa_all[kNFMaxT];
     s_wt = &wt_all[0][0][0];
     s_wii = &wii_all[0][0];
+    s_scale = scale_all;
+    s_fa = fa_all;
+    s_tl = tl;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stw = st[w];
     const int64_t nseg = *a.nseg;
@@ -340,21 +356,21 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
         unsigned long long evals = 0;
         int32_t pos = 0;
         for (;;) {
-            // warp 0 collects up to kNFList - 1 targets with vacant axons from
+            // warp 0 collects up to kNFList - 3 targets with vacant axons from
             // pos on: first walk counts them per channel and finds where the
-            // round ends, second walk writes the excitatory ones, a padding
-            // entry if their count is odd and inhibitory ones follow, then the
-            // inhibitory ones
+            // round ends, second walk writes the excitatory ones, padding
+            // entries up to a multiple of 4 if inhibitory ones follow, then
+            // the inhibitory ones (a lane's 2 or 4 slots share a channel)
             if (w == 0) {
                 int nt = 0, nE = 0;
                 int32_t p = pos;
-                while (p < tc && nt < kNFList - 1) {
+                while (p < tc && nt < kNFList - 3) {
                     const int32_t t = tf + p + lane;
                     const uint32_t tw = p + lane < tc ? __float_as_uint(a.pts[t].w) : 0u;
                     const bool act = pk_axon(tw) > 0;
                     const unsigned mask = __ballot_sync(0xffffffffu, act);
                     const unsigned emask = __ballot_sync(0xffffffffu, act && !pk_type(tw));
-                    const int room = kNFList - 1 - nt;
+                    const int room = kNFList - 3 - nt;
                     if (__popc(mask) > room) {
                         // stop after the lane of the room-th target
                         int last = 0;
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
                 }
                 const int32_t pend = min(p, tc);
                 const int nI = nt - nE;
-                const int pad = (nE & 1) && nI > 0 ? 1 : 0;
+                const int pad = nI > 0 ? (4 - (nE & 3)) & 3 : 0;
                 int we = 0, wi = nE + pad;
                 for (int32_t q = pos; q < pend; q += 32) {
                     const int32_t t = tf + q + lane;
@@ -391,10 +407,9 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
                     we += __popc(me);
                     wi += __popc(mI);
                 }
-                if (pad && lane == 0) tl[nE] = -1;
+                if (lane < pad) tl[nE + lane] = -1;
                 if (lane == 0) {
                     s_nt = nt + pad;
-                    s_nreal = nt;
                     s_pos = pend;
                 }
             }
@@ -407,7 +422,10 @@ __global__ void __launch_bounds__(kNFWarps * 32, 8) k_near_field(NFArgs a) {
                 const int m = min(kNFMaxT, ntl - c0);
                 int nreal = 0;
                 for (int k = 0; k < m; ++k) nreal += tl[c0 + k] >= 0;
-                nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                if (m > 64)
+                    nf_targets<4>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                else
+                    nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             }
             if (pos >= tc) break;
         }
