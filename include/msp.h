@@ -131,7 +131,9 @@ msp_status msp_destroy(msp_ctx *ctx);
  * The inputs are read during the call's stream work only; the context keeps
  * its own sorted copy.  Synchronous (the per-level node counts are read
  * back).  n may be 0.  Errors: MSP_ERR_INVALID_ARG (n < 0, n > 2^31-2, null
- * pointer with n > 0), MSP_ERR_OOM. */
+ * pointer with n > 0, a position outside [origin, origin + side) or not
+ * finite: the boxes of the tree must contain their points), MSP_ERR_OOM
+ * (including the workspace limit of msp_set_workspace_limit). */
 msp_status msp_build_tree(msp_ctx *ctx, int64_t n, const float *x_dev, const float *y_dev,
                           const float *z_dev, const uint8_t *type_dev,
                           const uint8_t *vac_axon_dev, const uint8_t *vac_dend_e_dev,
@@ -279,6 +281,16 @@ msp_status msp_attraction_grad(msp_ctx *ctx, const uint8_t *type_dev,
                                const uint8_t *vac_dend_i_dev, const float *g_dev, float *u_dev,
                                float *du_dsigma_dev, float *grad_w_e_dev, float *grad_w_i_dev,
                                void *stream);
+
+/* Cap on the device memory that the workspaces of all contexts of this
+ * process may hold (bytes; 0, the default, means none).  A workspace
+ * allocation beyond it fails with MSP_ERR_OOM and leaves the context usable
+ * (for processes that share a GPU, and to exercise the out-of-memory path).
+ * Does not free memory already held: destroy contexts for that.  Applies to
+ * allocations after the call. */
+msp_status msp_set_workspace_limit(int64_t bytes);
+/* Device memory held by the workspaces of all contexts of this process. */
+int64_t msp_workspace_bytes(void);
 
 /* Sizes and counts of the last calls.  Synchronous. */
 msp_status msp_get_stats(msp_ctx *ctx, msp_stats *out);

@@ -36,6 +36,8 @@ thread_local std::string g_last_error;
 namespace msp {
 std::atomic<long long> g_kernel_launches{0};
 std::atomic<long long> g_alloc_epoch{0};
+std::atomic<long long> g_ws_bytes{0};
+std::atomic<long long> g_ws_limit{0};
 void set_last_error(const char* msg) { g_last_error = msg; }
 }
 
@@ -332,6 +334,15 @@ msp_status msp_attraction_grad(msp_ctx* c, const uint8_t* type, const uint8_t* v
                              as_stream(stream));
     });
 }
+
+msp_status msp_set_workspace_limit(int64_t bytes) {
+    if (bytes < 0) return fail(MSP_ERR_INVALID_ARG, "limit must not be negative");
+    msp::g_ws_limit.store(bytes);
+    g_last_error.clear();
+    return MSP_OK;
+}
+
+int64_t msp_workspace_bytes(void) { return msp::g_ws_bytes.load(); }
 
 msp_status msp_set_pair_capacity(msp_ctx* c, int64_t pairs) {
     return guarded(c, [&] {

@@ -88,6 +88,7 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
                   const float* z, const double* sigma, double cutoff, int leaf_capacity,
                   float* xo, float* yo, float* zo, float* side_out, int* level_out,
                   cudaStream_t s) {
+    NvtxRange nv_("msp batch_layout");
     for (int64_t k = 0; k < nnet; ++k) {
         if (off_host[k + 1] <= off_host[k] + leaf_capacity)
             throw Error(MSP_ERR_INVALID_ARG, "every network needs more neurons than the leaf capacity");

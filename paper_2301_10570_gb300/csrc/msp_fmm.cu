@@ -517,6 +517,7 @@ static int bits_for(int64_t v) {
 }
 
 void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
+    NvtxRange nv_("msp attraction");
     if (!c.tree_built) throw Error(MSP_ERR_NOT_BUILT, "msp_build_tree must run first");
     if (!c.graph_mode) {
         c.attraction_done = false;

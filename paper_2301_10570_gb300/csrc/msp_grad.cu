@@ -197,6 +197,7 @@ int bits_for_grad(int64_t v) {
 void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const uint8_t* vde,
                      const uint8_t* vdi, const float* g, float* u, float* dud, float* gE,
                      float* gI, cudaStream_t s) {
+    NvtxRange nv_("msp attraction_grad");
     if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
     if (c.n_far > 0)
         throw Error(MSP_ERR_INVALID_ARG,

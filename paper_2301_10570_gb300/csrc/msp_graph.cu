@@ -57,7 +57,7 @@ __global__ void k_graph_check(DevCounts* dc, int left_slot) {
     int64_t bad = 0;
     if (dc->overflow & 1) bad |= kHaltPairs;
     if (dc->overflow & 6) bad |= kHaltItems;
-    if (dc->more_levels > 0 || (dc->overflow & 16)) bad |= kHaltLevels;
+    if (dc->more_levels > 0 || (dc->overflow & 16) || dc->bad_pos) bad |= kHaltLevels;
     if (dc->items[left_slot] != 0) bad |= kHaltDescent;
     dc->halt |= bad;
 }
@@ -108,6 +108,7 @@ void graph_release(msp_ctx& c) {
 }
 
 void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s) {
+    NvtxRange nv_("msp step_graph_capture");
     if (!c.tree_built || !c.attraction_done || c.n != args.n)
         throw Error(MSP_ERR_NOT_BUILT,
                     "build the tree of these positions and run the attraction once first");
@@ -199,6 +200,7 @@ void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s) {
 }
 
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s) {
+    NvtxRange nv_("msp step_graph_launch");
     if (!c.gexec) throw Error(MSP_ERR_NOT_BUILT, "no captured step graph");
     // a workspace buffer reallocated since the capture (by an eager call)
     // would leave the graph's kernels pointing at freed memory
@@ -227,6 +229,7 @@ void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s) {
 // (growing what overflowed) and captures the graph again from the next step.
 // Returns the index of the next step to run and whether a halt was handled.
 void graph_finish(msp_ctx& c, cudaStream_t s, uint64_t* next_step, int64_t* halted) {
+    NvtxRange nv_("msp step_graph_finish");
     if (!c.gexec) throw Error(MSP_ERR_NOT_BUILT, "no captured step graph");
     pull_counts(c, s);
     const DevCounts hc = *c.hcount;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -46,6 +47,18 @@ extern std::atomic<long long> g_kernel_launches;
 // step graph records it and refuses to replay once it changed (its kernels
 // hold the old addresses).
 extern std::atomic<long long> g_alloc_epoch;
+// Device memory held by all workspace buffers, and an optional cap on it
+// (0: none); an allocation beyond the cap fails with MSP_ERR_OOM.
+extern std::atomic<long long> g_ws_bytes;
+extern std::atomic<long long> g_ws_limit;
+
+// a named range for profilers and tracers (NVTX; free when no tool listens)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // grow-only device buffer
 struct DBuf {
@@ -59,18 +72,23 @@ struct DBuf {
         if (need == 0) need = sizeof(T);
         if (need > bytes) {
             g_alloc_epoch.fetch_add(1, std::memory_order_relaxed);
-            if (p) cudaFree(p);
-            p = nullptr;
-            bytes = 0;
+            release();
             size_t alloc = need + need / 4 + 256;
+            const long long lim = g_ws_limit.load();
+            if (lim > 0 && g_ws_bytes.load() + (long long)alloc > lim)
+                throw Error(MSP_ERR_OOM, "workspace limit reached");
             cuda_check(cudaMalloc(&p, alloc), "cudaMalloc");
             bytes = alloc;
+            g_ws_bytes.fetch_add((long long)alloc);
         }
         return static_cast<T*>(p);
     }
     void release() {
-        if (p) g_alloc_epoch.fetch_add(1, std::memory_order_relaxed);
-        if (p) cudaFree(p);
+        if (p) {
+            g_alloc_epoch.fetch_add(1, std::memory_order_relaxed);
+            g_ws_bytes.fetch_sub((long long)bytes);
+            cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -103,6 +121,7 @@ struct DevCounts {
     int64_t need_pairs;                      // largest pair-table end asked for (before clamping)
     int64_t need_items;                      // largest descent item count asked for
     int64_t need_nodes;                      // largest octree node end asked for
+    int64_t bad_pos;                         // positions outside the domain (last build)
     int64_t scan_n;                          // element count of the next scan
     // whole-step graph: the step index its kernels draw with, the halt flag
     // (nonzero: a capacity was exceeded; the state-changing kernels stop) and

@@ -559,6 +559,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
                      const uint8_t* vde_dev, const uint8_t* vdi_dev, int32_t* partner,
                      int32_t* syn_pre, int32_t* syn_post, uint8_t* syn_type, int64_t* n_syn,
                      cudaStream_t s) {
+    NvtxRange nv_("msp select_partners");
     if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
     const msp_config& cfg = c.cfg;
     // the element count: exact from the build, or (whole-step graph) the

@@ -16,17 +16,30 @@ __device__ inline uint32_t quantise(float v, float o, float scale) {
     return (uint32_t)f;
 }
 
+__global__ void k_build_init(DevCounts* dc, int64_t n) {
+    dc->n = n;
+    dc->bad_pos = 0;
+}
+
+// keys; a position outside [origin, origin + side) or not finite is counted
+// (the build then fails: the tree's boxes must contain their points)
 __global__ void k_morton(const float* __restrict__ x, const float* __restrict__ y,
                          const float* __restrict__ z, int64_t n, float ox, float oy, float oz,
-                         float scale, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+                         float side, float scale, uint64_t* __restrict__ keys,
+                         int32_t* __restrict__ vals, int64_t* __restrict__ bad) {
+    bool any_bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        any_bad |= !(x[i] >= ox && x[i] < ox + side && y[i] >= oy && y[i] < oy + side &&
+                     z[i] >= oz && z[i] < oz + side);
         uint32_t qx = quantise(x[i], ox, scale);
         uint32_t qy = quantise(y[i], oy, scale);
         uint32_t qz = quantise(z[i], oz, scale);
         keys[i] = (spread_by3(qx) << 2) | (spread_by3(qy) << 1) | spread_by3(qz);
         vals[i] = (int32_t)i;
     }
+    if (__any_sync(0xffffffffu, any_bad) && (threadIdx.x & 31) == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(bad), 1ull);
 }
 
 __global__ void k_gather(const int32_t* __restrict__ order, int64_t n, const float* __restrict__ x,
@@ -248,6 +261,7 @@ __global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox,
 void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const float* z,
                 const uint8_t* type, const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
                 cudaStream_t s) {
+    NvtxRange nv_("msp build_tree");
     if (!c.graph_mode) {
         c.tree_built = false;
         c.attraction_done = false;
@@ -255,7 +269,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     c.n = n;
     const msp_config& cfg = c.cfg;
     DevCounts* dc = dcounts(c);
-    dev_set(&dc->n, n, s);
+    k_build_init<<<1, 1, 0, s>>>(dc, n);
+    MSP_LAUNCH("build_init");
     size_t nn = (size_t)(n > 0 ? n : 1);
     uint64_t* k0 = c.keys0.ensure<uint64_t>(nn);
     uint64_t* k1 = c.keys1.ensure<uint64_t>(nn);
@@ -274,7 +289,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     // a1 + a2: keys, stable sort, gather into Morton order
     if (n > 0) {
         k_morton<<<G, B, 0, s>>>(x, y, z, n, cfg.origin[0], cfg.origin[1], cfg.origin[2],
-                                 c.morton_scale, k0, v0);
+                                 cfg.side, c.morton_scale, k0, v0, &dc->bad_pos);
         MSP_LAUNCH("morton");
         radix_sort(c, k0, v0, k1, v1, n, 3 * kMortonBits, s);
         k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
@@ -368,6 +383,9 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         // same levels; a deeper one sets more_levels, which halts the graph
         if (c.graph_mode) return;
         pull_counts(c, s);          // the one synchronisation of the build
+        if (c.hcount->bad_pos)
+            throw Error(MSP_ERR_INVALID_ARG, "a position is outside [origin, origin + side) "
+                                             "or not finite");
         if (c.hcount->overflow & 16) throw Error(MSP_ERR_CHECK, "octree node capacity exceeded");
         if (c.hcount->more_levels > 0 && L < cfg.max_depth) {
             L = cfg.max_depth;

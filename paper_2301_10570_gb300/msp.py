@@ -31,7 +31,8 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_commit_synapses", "msp_get_stats", "msp_export_tree", "msp_export_pairs",
             "msp_export_expansions", "msp_last_error", "msp_direct_noalloc",
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-            "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad")
+            "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
+            "msp_set_workspace_limit", "msp_workspace_bytes")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -95,8 +96,13 @@ def load(path: str = LIB_PATH):
         L.msp_batch_layout.restype = C.c_int
         L.msp_attraction_grad.argtypes = [vp] * 11
         L.msp_attraction_grad.restype = C.c_int
+        L.msp_set_workspace_limit.argtypes = [i64]
+        L.msp_set_workspace_limit.restype = C.c_int
+        L.msp_workspace_bytes.argtypes = []
+        L.msp_workspace_bytes.restype = i64
         for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
-                     "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad"):
+                     "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
+            "msp_set_workspace_limit", "msp_workspace_bytes"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
@@ -404,6 +410,15 @@ def batch_layout(pos, offsets, sigma, cutoff, leaf_capacity, stream=None):
                                    float(cutoff), int(leaf_capacity), _ptr(out[0]), _ptr(out[1]),
                                    _ptr(out[2]), C.byref(side), C.byref(level), _stream(stream)))
     return out, float(side.value), int(level.value)
+
+
+def set_workspace_limit(nbytes: int):
+    """Cap the device memory all contexts' workspaces may hold (0: no cap)."""
+    _check(load().msp_set_workspace_limit(int(nbytes)))
+
+
+def workspace_bytes() -> int:
+    return int(load().msp_workspace_bytes())
 
 
 def to_device(w, device="cuda"):

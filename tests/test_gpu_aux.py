@@ -1,0 +1,105 @@
+"""Auxiliary behaviour of the library on the GPU: work linear in the number of
+neurons at fixed density (the complexity claim of Section 4.1), checkpoint
+and resume (a step is a function of positions, vacancies, types, parameters,
+seed and step index), the workspace memory cap and its out-of-memory path,
+and rejection of positions outside the domain.
+"""
+import numpy as np
+import pytest
+
+from paper_2301_10570_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_10570_gb300 import msp  # noqa: E402
+
+PLAN = dict(leaf_capacity=64, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+
+
+def test_work_grows_linearly_with_n_at_fixed_density():
+    # uniform cubes at the density of uniform_4k, n growing by 8 (so the
+    # octree of each is the one before, repeated: the leaves have the same
+    # size): interactions, box pairs and boxes per neuron approach a constant
+    # (boundary layers shrink as n grows)
+    per_n = []
+    for n in (32_768, 262_144, 2_097_152):
+        side = 10_000.0 * (n / 4096) ** (1 / 3)
+        w = W.uniform_cube(n, side, seed=21, **PLAN)
+        g = msp.MSP(w.params)
+        g.build_tree(*msp.to_device(w))
+        g.attraction()
+        st = g.stats()
+        g.close()
+        per_n.append((st["p2p_interactions"] / n, st["n_pairs"] / n, st["n_nodes"] / n))
+    per_n = np.array(per_n)
+    for col in range(3):
+        v = per_n[:, col]
+        assert v.max() / v.min() < 1.35, per_n
+    # and toward the interior value: the larger cubes have less boundary
+    assert per_n[2, 0] >= per_n[0, 0]
+
+
+def _steps(w, va, ve, vi, first, count):
+    pos, t = msp.to_device(w)[:2]
+    a, e, i = (torch.from_numpy(v.copy()).cuda() for v in (va, ve, vi))
+    g = msp.MSP(w.params)
+    syn = []
+    for k in range(first, first + count):
+        g.vacancy_walk(k, a, e, i)
+        g.build_tree(pos, t, a, e, i)
+        g.attraction()
+        sel = g.select_partners(k)
+        g.commit_synapses(sel, a, e, i)
+        ns = int(sel["n_syn"].item())
+        syn.append((sel["syn_pre"][:ns].cpu().numpy(), sel["syn_post"][:ns].cpu().numpy()))
+    state = [v.cpu().numpy() for v in (a, e, i)]
+    g.close()
+    return syn, state
+
+
+def test_checkpoint_and_resume_replay_bit_identically():
+    w = W.clustered_small(2, 2048, seed=22, **PLAN)
+    full, _ = _steps(w, w.vac_axon, w.vac_dend_e, w.vac_dend_i, 0, 6)
+    head, ckpt = _steps(w, w.vac_axon, w.vac_dend_e, w.vac_dend_i, 0, 3)
+    tail, _ = _steps(w, *ckpt, 3, 3)
+    for (p1, q1), (p2, q2) in zip(full, head + tail):
+        assert np.array_equal(p1, p2) and np.array_equal(q1, q2)
+
+
+def test_workspace_limit_fails_cleanly_and_recovers():
+    w = W.clustered_small(1, 16_384, seed=23, **PLAN)
+    dev = msp.to_device(w)
+    try:
+        msp.set_workspace_limit(msp.workspace_bytes() + (1 << 20))
+        g = msp.MSP(w.params)
+        with pytest.raises(msp.MSPError) as ei:
+            g.build_tree(*dev)
+        assert ei.value.code == 3                        # MSP_ERR_OOM
+    finally:
+        msp.set_workspace_limit(0)
+    g.build_tree(*dev)                                   # the same context works again
+    u = g.attraction()
+    assert torch.isfinite(u).all()
+    g.close()
+    with pytest.raises(msp.MSPError):
+        msp.set_workspace_limit(-1)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -1.0, "side"])
+def test_positions_outside_the_domain_are_rejected(bad):
+    w = W.uniform_4k()
+    pos = w.pos.copy()
+    pos[1, 123] = np.float32(w.params["side"]) if bad == "side" else np.float32(bad)
+    g = msp.MSP(w.params)
+    dev = list(msp.to_device(w))
+    dev[0] = torch.from_numpy(pos).cuda()
+    with pytest.raises(msp.MSPError) as ei:
+        g.build_tree(*dev)
+    assert ei.value.code == 1                            # MSP_ERR_INVALID_ARG
+    g.build_tree(*msp.to_device(w))                      # valid inputs still work
+    g.attraction()
+    g.close()
