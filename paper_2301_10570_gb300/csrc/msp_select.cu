@@ -199,6 +199,39 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
         const int ny = tr.nchild[Y];
         const int32_t cy = tr.child_first[Y];
         const int nsrc = lx ? 1 : tr.nchild[X];
+        if (split) {
+            // the candidates' attractions are in the pair table: lane i draws
+            // for axon child i
+            const uint32_t c1 =
+                (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
+            bool drew = false;
+            if (lane < nsrc) {
+                const int i = lane;
+                const int32_t xc = lx ? X : tr.child_first[X] + i;
+                const int4 sm = tr.sums[xc];
+                if (lx || (ch ? sm.y : sm.x) != 0) {
+                    double wk[8];
+                    for (int j = 0; j < ny; ++j) {
+                        const double2 v = pw[cf + (int64_t)i * ny + j];
+                        wk[j] = ch ? v.y : v.x;
+                    }
+                    const double U = philox_uniform(seed, (uint32_t)xc, c1, step);
+                    const int kk = draw_index(wk, ny, U);
+                    drew = true;
+                    if (kk >= 0) {
+                        const unsigned long long slot = atomicAdd(ct.n_out, 1ull);
+                        const Item nx_it = {xc, cy + kk, cf + i * ny + kk, ch};
+                        if ((int64_t)slot < cap_out) out[slot] = nx_it;
+                        else atomicOr(ct.overflow, 2ull);
+                    }
+                }
+            }
+            const unsigned dm = __ballot_sync(0xffffffffu, drew);
+            if (lane == 0 && dm) atomicAdd(ct.draws, (unsigned long long)__popc(dm));
+            continue;
+        }
+        // below a translated pair: each candidate's attraction is a
+        // translation the whole warp evaluates
         for (int i = 0; i < nsrc; ++i) {
             const int32_t xc = lx ? X : tr.child_first[X] + i;
             if (!lx) {

@@ -199,6 +199,10 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
 // Box aggregates, deepest level first.  A leaf sums its points; an inner box
 // combines its children.  Centroids are accumulated as weighted offsets from
 // the box's geometric centre so that single precision keeps them accurate.
+// One warp per box of the level: a leaf's lanes take its points, an inner
+// box's lanes its children (at most 8); warp sums, then lane 0 writes the
+// box's vacant-element sums and its axon / dendrite centroids (offsets from
+// the geometric centre summed, then divided by the weight).
 __global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox, float oy, float oz,
                             float side, const float4* __restrict__ pts,
                             const uint64_t* __restrict__ prefix, const int32_t* __restrict__ first,
@@ -208,51 +212,61 @@ __global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox,
                             float4* __restrict__ ca, float4* __restrict__ cd,
                             int32_t* __restrict__ leaf_of) {
     const int64_t l0 = lb[0], nl = lb[1] - lb[0];
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = l0 + k;
-        uint64_t pre = prefix[i];
-        float bs = ldexpf(side, -level);
-        float g[3] = {ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs,
-                      oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs,
-                      oz + ((float)compact_by3(pre) + 0.5f) * bs};
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nl; k += nw) {
+        const int64_t i = l0 + k;
+        const uint64_t pre = prefix[i];
+        const float bs = ldexpf(side, -level);
+        const float g[3] = {ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs,
+                            oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs,
+                            oz + ((float)compact_by3(pre) + 0.5f) * bs};
         int aE = 0, aI = 0, wE = 0, wI = 0;
         float sa[3] = {0.f, 0.f, 0.f}, sd[3] = {0.f, 0.f, 0.f};
-        int32_t cf = child_first[i];
+        const int32_t cf = child_first[i];
         if (cf < 0) {
-            int32_t f = first[i], c = count[i];
-            for (int32_t j = f; j < f + c; ++j) {
-                float4 p = pts[j];
-                uint32_t w = __float_as_uint(p.w);
-                int a = (int)pk_axon(w), de = (int)pk_de(w), di = (int)pk_di(w);
+            const int32_t f = first[i], c = count[i];
+            for (int32_t j = f + lane; j < f + c; j += 32) {
+                const float4 p = pts[j];
+                const uint32_t w = __float_as_uint(p.w);
+                const int a = (int)pk_axon(w), de = (int)pk_de(w), di = (int)pk_di(w);
                 if (pk_type(w)) aI += a; else aE += a;
                 wE += de;
                 wI += di;
-                float fa = (float)a, fd = (float)(de + di);
-                float dx = p.x - g[0], dy = p.y - g[1], dz = p.z - g[2];
+                const float fa = (float)a, fd = (float)(de + di);
+                const float dx = p.x - g[0], dy = p.y - g[1], dz = p.z - g[2];
                 sa[0] = fmaf(fa, dx, sa[0]); sa[1] = fmaf(fa, dy, sa[1]); sa[2] = fmaf(fa, dz, sa[2]);
                 sd[0] = fmaf(fd, dx, sd[0]); sd[1] = fmaf(fd, dy, sd[1]); sd[2] = fmaf(fd, dz, sd[2]);
                 leaf_of[j] = (int32_t)i;
             }
-        } else {
-            int nc = nchild[i];
-            for (int j = 0; j < nc; ++j) {
-                int4 s = sums[cf + j];
-                float4 a4 = ca[cf + j], d4 = cd[cf + j];
-                aE += s.x; aI += s.y; wE += s.z; wI += s.w;
-                float fa = (float)(s.x + s.y), fd = (float)(s.z + s.w);
-                sa[0] = fmaf(fa, a4.x - g[0], sa[0]); sa[1] = fmaf(fa, a4.y - g[1], sa[1]);
-                sa[2] = fmaf(fa, a4.z - g[2], sa[2]);
-                sd[0] = fmaf(fd, d4.x - g[0], sd[0]); sd[1] = fmaf(fd, d4.y - g[1], sd[1]);
-                sd[2] = fmaf(fd, d4.z - g[2], sd[2]);
+        } else if (lane < nchild[i]) {
+            const int4 sm = sums[cf + lane];
+            const float4 a4 = ca[cf + lane], d4 = cd[cf + lane];
+            aE = sm.x; aI = sm.y; wE = sm.z; wI = sm.w;
+            const float fa = (float)(sm.x + sm.y), fd = (float)(sm.z + sm.w);
+            sa[0] = fa * (a4.x - g[0]); sa[1] = fa * (a4.y - g[1]); sa[2] = fa * (a4.z - g[2]);
+            sd[0] = fd * (d4.x - g[0]); sd[1] = fd * (d4.y - g[1]); sd[2] = fd * (d4.z - g[2]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            aE += __shfl_xor_sync(0xffffffffu, aE, o);
+            aI += __shfl_xor_sync(0xffffffffu, aI, o);
+            wE += __shfl_xor_sync(0xffffffffu, wE, o);
+            wI += __shfl_xor_sync(0xffffffffu, wI, o);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sa[d] += __shfl_xor_sync(0xffffffffu, sa[d], o);
+                sd[d] += __shfl_xor_sync(0xffffffffu, sd[d], o);
             }
         }
-        sums[i] = make_int4(aE, aI, wE, wI);
-        float ta = (float)(aE + aI), td = (float)(wE + wI);
-        ca[i] = ta > 0.f ? make_float4(g[0] + sa[0] / ta, g[1] + sa[1] / ta, g[2] + sa[2] / ta, ta)
-                         : make_float4(g[0], g[1], g[2], 0.f);
-        cd[i] = td > 0.f ? make_float4(g[0] + sd[0] / td, g[1] + sd[1] / td, g[2] + sd[2] / td, td)
-                         : make_float4(g[0], g[1], g[2], 0.f);
+        if (lane == 0) {
+            sums[i] = make_int4(aE, aI, wE, wI);
+            const float ta = (float)(aE + aI), td = (float)(wE + wI);
+            ca[i] = ta > 0.f ? make_float4(g[0] + sa[0] / ta, g[1] + sa[1] / ta, g[2] + sa[2] / ta, ta)
+                             : make_float4(g[0], g[1], g[2], 0.f);
+            cd[i] = td > 0.f ? make_float4(g[0] + sd[0] / td, g[1] + sd[1] / td, g[2] + sd[2] / td, td)
+                             : make_float4(g[0], g[1], g[2], 0.f);
+        }
     }
 }
 
