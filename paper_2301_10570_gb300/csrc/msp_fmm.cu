@@ -107,7 +107,8 @@ __global__ void k_classify(const int64_t* __restrict__ db, NodeView nv, Geo geo,
 __global__ void k_emit_pairs(const int64_t* __restrict__ db, NodeView nv,
                              const uint8_t* __restrict__ kind, const int32_t* __restrict__ off,
                              int32_t* __restrict__ pX, int32_t* __restrict__ pY,
-                             int32_t* __restrict__ pcf, double2* __restrict__ pw, int64_t cap,
+                             int32_t* __restrict__ pcf, uint8_t* __restrict__ pnb,
+                             double2* __restrict__ pw, int64_t cap,
                              const int64_t* __restrict__ overflow) {
     const int64_t q0 = db[0], nq = db[1] - db[0], next0 = db[1];
     const bool full = (*overflow & 1) != 0;
@@ -121,11 +122,13 @@ __global__ void k_emit_pairs(const int64_t* __restrict__ db, NodeView nv,
         }
         int32_t X = pX[q], Y = pY[q];
         int64_t cf = next0 + off[k];
-        if (full || cf + block_size(nv, X, Y) > cap) {
+        const int nb = block_size(nv, X, Y);
+        if (full || cf + nb > cap) {
             pcf[q] = -1;
             continue;
         }
         pcf[q] = (int32_t)cf;
+        pnb[q] = (uint8_t)nb;
         int32_t cx = nv.child_first[X], cy = nv.child_first[Y];
         if (cx >= 0 && cy >= 0) {
             int nx = nv.nchild[X], ny = nv.nchild[Y];
@@ -404,9 +407,8 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
 }
 
 // a10: attraction of a split pair = sum over its child block (double)
-__global__ void k_reduce_pairs(const int64_t* __restrict__ db, NodeView nv,
-                               const uint8_t* __restrict__ kind, const int32_t* __restrict__ pX,
-                               const int32_t* __restrict__ pY, const int32_t* __restrict__ pcf,
+__global__ void k_reduce_pairs(const int64_t* __restrict__ db, const uint8_t* __restrict__ kind,
+                               const int32_t* __restrict__ pcf, const uint8_t* __restrict__ pnb,
                                double2* __restrict__ pw) {
     // four interleaved partial sums (children c = j mod 4), combined in a fixed
     // order: deterministic, and four independent add chains
@@ -416,7 +418,7 @@ __global__ void k_reduce_pairs(const int64_t* __restrict__ db, NodeView nv,
         const int64_t q = q0 + k;
         const int32_t cf = pcf[q];
         if (kind[q] != kSplit || cf < 0) continue;     // cf < 0: children not stored (overflow)
-        const int nb = block_size(nv, pX[q], pY[q]);
+        const int nb = pnb[q];
         double e[4] = {0.0, 0.0, 0.0, 0.0}, i[4] = {0.0, 0.0, 0.0, 0.0};
         int c = 0;
         for (; c + 3 < nb; c += 4) {
@@ -552,6 +554,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     c.pr_Y.ensure<int32_t>((size_t)cap);
     c.pr_kind.ensure<uint8_t>((size_t)cap);
     c.pr_cf.ensure<int32_t>((size_t)cap);
+    c.pr_nb.ensure<uint8_t>((size_t)cap);
     c.pr_w.ensure<double2>((size_t)cap);
     int32_t* cnt = c.cnt.ensure<int32_t>((size_t)cap);
     int32_t* off = c.off.ensure<int32_t>((size_t)cap);
@@ -568,7 +571,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
                  cap, &dc->overflow, &dc->need_pairs);
         k_emit_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[d], nv, kind, off, c.pr_X.get<int32_t>(),
                                       c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
-                                      c.pr_w.get<double2>(), cap, &dc->overflow);
+                                      c.pr_nb.get<uint8_t>(), c.pr_w.get<double2>(), cap,
+                                      &dc->overflow);
         MSP_LAUNCH("emit_pairs");
     }
     const int64_t* n_pairs_dev = &dc->depth_start[D];
@@ -639,9 +643,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     c.nf_timed = n > 0;
     // a10: pair table, deepest pairs first
     for (int dd = D - 1; dd >= 0; --dd) {
-        k_reduce_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[dd], nv, kind, c.pr_X.get<int32_t>(),
-                                        c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
-                                        c.pr_w.get<double2>());
+        k_reduce_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[dd], kind, c.pr_cf.get<int32_t>(),
+                                        c.pr_nb.get<uint8_t>(), c.pr_w.get<double2>());
         MSP_LAUNCH("reduce_pairs");
     }
     if (u_dev && n > 0) {

@@ -172,7 +172,7 @@ struct msp_ctx {
     msp::DBuf nd_level, nd_prefix, nd_first, nd_count, nd_parent, nd_child_first, nd_nchild;
     msp::DBuf nd_sums, nd_ca, nd_cd;
     // dual traversal
-    msp::DBuf pr_X, pr_Y, pr_kind, pr_cf, pr_w;
+    msp::DBuf pr_X, pr_Y, pr_kind, pr_cf, pr_nb, pr_w;
     // lists
     msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
     msp::DBuf nf_okey0, nf_okey1, nf_oval0, nf_oval1;   // near-field segment order
