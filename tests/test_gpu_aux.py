@@ -103,3 +103,28 @@ def test_positions_outside_the_domain_are_rejected(bad):
     g.build_tree(*msp.to_device(w))                      # valid inputs still work
     g.attraction()
     g.close()
+
+
+def test_uniform_256k_translations_converge_with_p():
+    # 262,144 uniform neurons at the paper's density (~625 um spacing), boxes
+    # up to 0.5 sigma half-width translated (at 0.25 sigma no box is populated
+    # enough to carry an expansion): the deviation from the all-pairs GPU
+    # evaluation falls with the expansion order (measured: 5e-2, 2e-2, 3e-3,
+    # 2e-4 at p = 3, 4, 6, 8)
+    w0 = W.uniform_256k(leaf_capacity=8, rho_max=0.5, cutoff=4.0, m2l_min_pairs=0)
+    dev = msp.to_device(w0)
+    ref_ctx = msp.MSP(w0.params)
+    ref_ctx.build_tree(*dev)
+    ud = ref_ctx.direct()
+    ref_ctx.close()
+    m = ud > 1e-6 * ud.max()
+    errs = {}
+    for p in (3, 4, 6, 8):
+        g = msp.MSP(dict(w0.params, p=p))
+        g.build_tree(*dev)
+        u = g.attraction()
+        assert g.stats()["n_far"] > 0
+        errs[p] = ((u[m] - ud[m]).abs() / ud[m]).max().item()
+        g.close()
+    assert errs[3] > errs[4] > errs[6] > errs[8], errs
+    assert errs[4] < 5e-2 and errs[8] < 1e-3, errs
