@@ -117,7 +117,6 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
     c->device = device;
     msp_status st = guarded(c, [&] {
         MSP_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
-        MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->small_host), 16 * sizeof(int64_t)));
         MSP_CUDA(cudaEventCreate(&c->ev_nf0));
         MSP_CUDA(cudaEventCreate(&c->ev_nf1));
         MSP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->hcount), sizeof(msp::DevCounts)));
@@ -148,12 +147,11 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
                          &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
-                         &c->small_dev, &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
+                         &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
                          &c->h_post, &c->h_type, &c->h_nsyn, &c->c_type, &c->c_va,
                          &c->c_vde, &c->c_vdi};
     for (msp::DBuf* b : bufs) b->release();
     for (auto& b : c->h_in) b.release();
-    if (c->small_host) cudaFreeHost(c->small_host);
     if (c->hcount) cudaFreeHost(c->hcount);
     c->dcount.release();
     c->sd_tmp.release();

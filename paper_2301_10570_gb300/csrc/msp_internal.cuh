@@ -184,13 +184,12 @@ struct msp_ctx {
     // descent
     msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
     // generic scratch
-    msp::DBuf cnt, off, scan_tmp, small_dev, rs_hist, sd_tmp;
+    msp::DBuf cnt, off, scan_tmp, rs_hist, sd_tmp;
     // device-resident sizes and their pinned host mirror
     msp::DBuf dcount;
     msp::DevCounts* hcount = nullptr;
     int depth_hint = -1;                 // tree depth of the last build (-1: none)
     int64_t pair_cap = 0;                // capacity of the pair table
-    int64_t* small_host = nullptr;     // pinned, for count readbacks
     cudaEvent_t ev_nf0 = nullptr, ev_nf1 = nullptr;   // around the near-field kernel
     bool nf_timed = false;
     // per-neuron inputs of the last build in caller order (context-owned
@@ -234,10 +233,6 @@ namespace msp {
 // ---------------------------------------------------------------------------
 // primitives (msp_prims.cu)
 // ---------------------------------------------------------------------------
-// Exclusive scan of n int32 values into out (may alias in); returns the total
-// (synchronous: reads it back).  Throws MSP_ERR_CAPACITY if the total does not
-// fit in int32.
-int64_t scan_exclusive(msp_ctx& c, const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
 // Stable LSD radix sort of (key, value) by the low `bits` bits of key.  The
 // result ends in (keys, vals); (keys_tmp, vals_tmp) are scratch of n entries.
 void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
@@ -250,8 +245,6 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
                        int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
                        int64_t nlist_cap, float* u_sorted, unsigned long long* work,
                        cudaStream_t s);
-// Read an int64 from device memory (synchronous).
-int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s);
 // Exclusive scan of in[0, *n_dev) (n_dev in device memory, at most n_cap)
 // into out; *total_dst = total (+ *base if base).  No host synchronisation.
 // With overflow given, an end above clamp_cap sets overflow_bit in *overflow,
@@ -265,7 +258,6 @@ void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tm
                     cudaStream_t s);
 // small device-side bookkeeping (msp_prims.cu)
 void dev_set(int64_t* dst, int64_t v, cudaStream_t s);
-void dev_sub(int64_t* dst, const int64_t* a, const int64_t* b, cudaStream_t s);   // *dst = *b - *a
 void dev_store_i32(int32_t* dst, const int64_t* src, cudaStream_t s);
 // device counts of a context and their host mirror (synchronous)
 inline DevCounts* dcounts(msp_ctx& c) { return c.dcount.get<DevCounts>(); }

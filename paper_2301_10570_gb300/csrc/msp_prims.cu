@@ -176,33 +176,6 @@ __global__ void k_copy_kv(const uint64_t* __restrict__ ks, const int32_t* __rest
 
 }  // namespace
 
-int64_t read_i64(msp_ctx& c, const int64_t* dev, cudaStream_t s) {
-    MSP_CUDA(cudaMemcpyAsync(c.small_host, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaStreamSynchronize(s));
-    return c.small_host[0];
-}
-
-int64_t scan_exclusive(msp_ctx& c, const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
-    if (n <= 0) return 0;
-    long long* total = c.small_dev.ensure<long long>(8);
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb == 1) {
-        k_scan_tile<int32_t, int32_t><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
-        MSP_LAUNCH("scan_tile");
-    } else {
-        long long* scratch = c.scan_tmp.ensure<long long>((size_t)(2 * nb + 64));
-        k_scan_reduce<int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch);
-        MSP_LAUNCH("scan_reduce");
-        scan_i64(c, scratch, nb, nullptr, scratch + nb, s);
-        k_scan_tile<int32_t, int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, scratch,
-                                                                          total);
-        MSP_LAUNCH("scan_tile");
-    }
-    int64_t t = read_i64(c, reinterpret_cast<int64_t*>(total), s);
-    if (t > 0x7fffffffll) throw Error(MSP_ERR_CAPACITY, "scan total exceeds int32 range");
-    return t;
-}
-
 void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp, int32_t* vals_tmp,
                 int64_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return;
@@ -406,17 +379,12 @@ __global__ void k_copy_kv_dev(const uint64_t* __restrict__ ks, const int32_t* __
 
 namespace {
 __global__ void k_dev_set(int64_t* dst, int64_t v) { *dst = v; }
-__global__ void k_dev_sub(int64_t* dst, const int64_t* a, const int64_t* b) { *dst = *b - *a; }
 __global__ void k_dev_store_i32(int32_t* dst, const int64_t* src) { *dst = (int32_t)*src; }
 }  // namespace
 
 void dev_set(int64_t* dst, int64_t v, cudaStream_t s) {
     k_dev_set<<<1, 1, 0, s>>>(dst, v);
     MSP_LAUNCH("dev_set");
-}
-void dev_sub(int64_t* dst, const int64_t* a, const int64_t* b, cudaStream_t s) {
-    k_dev_sub<<<1, 1, 0, s>>>(dst, a, b);
-    MSP_LAUNCH("dev_sub");
 }
 void dev_store_i32(int32_t* dst, const int64_t* src, cudaStream_t s) {
     k_dev_store_i32<<<1, 1, 0, s>>>(dst, src);
