@@ -175,3 +175,21 @@ def test_graph_refuses_to_replay_after_workspace_reallocation():
     g.step_graph_capture(pos, t, a, e, i, first_step=1)
     assert g.run_steps(1, 2) == 3
     g.close()
+
+
+def test_graph_replays_of_a_batch_equal_eager_steps():
+    # the batched problem (several networks placed in one domain) through the
+    # step graph, against the same steps as eager calls
+    from paper_2301_10570_gb300 import workloads as W2
+    b = W2.batched_small()
+    plan = dict(leaf_capacity=16, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+    placed, side, _ = msp.batch_layout(torch.from_numpy(b.pos).cuda(), b.offsets, b.sigma,
+                                       plan["cutoff"], plan["leaf_capacity"])
+    w = b.placed(placed.cpu().numpy(), side, **plan)
+    ce, se, le = _eager(w, 7, 4)
+    cg, sg, lg, _, _ = _graph(w, 7, 4)
+    assert cg == ce
+    for x, y in zip(sg, se):
+        assert np.array_equal(x, y)
+    for key in ("pre", "post", "typ"):
+        assert np.array_equal(lg[key], le[key])
