@@ -33,14 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "plasticity-step neurons/s at 1M neurons, FMM vs direct on GB300, rel.err<=1e-4"
 UNIT = "neurons/s"
 SM_COUNT = 152
-# The near-field evaluation needs five issued instructions per interaction
-# (three FFMA, one FADD, one EX2); an SM issues four warp-instructions (128
-# lanes) per clock, so it completes at most 128 / 5 = 25.6 interactions per
-# clock.  The pipes themselves are not binding: FP32 runs 128 lanes per clock
-# (32 interactions at four FP32 operations each) and EX2 about 31 per clock
-# (measured with paper_2301_10570_gb300/probes/sfu_rate.cu).
-LANES_PER_SM_CLK = 128
-INSTR_PER_INTERACTION = 5
+# One near-field interaction is one EX2 and four FP32 operations (three FMAs
+# for the exponent, one add).  The EX2 unit delivers 30.25 results per SM per
+# clock (measured with paper_2301_10570_gb300/probes/sfu_rate.cu, 16 blocks of
+# 128 threads per SM), the FP32 pipe 128 operations (32 interactions), and with
+# the FMAs and adds paired over two sources an interaction takes about 3.5
+# issue slots of 128 per clock (36 interactions): the EX2 unit binds.
+EX2_PER_SM_CLK = 30.25
 
 
 def parse():
@@ -245,7 +244,7 @@ def run_gradient(args, rank, world):
     achieved = inter / (ms / 1e3) / 1e9
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * LANES_PER_SM_CLK / INSTR_PER_INTERACTION * sm_max * 1e6 / 1e9
+    peak = SM_COUNT * EX2_PER_SM_CLK * sm_max * 1e6 / 1e9
     g.close()
     return {"metric": GRAD_METRIC, "value": agg["per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -264,9 +263,10 @@ def run_gradient(args, rank, world):
                          "achieved": round(achieved, 1), "peak": round(peak, 1),
                          "unit": "G interactions/s", "frac": round(achieved / peak, 4),
                          "traffic": None, "interactions_per_step": inter,
-                         "peak_basis": "issue bound of the expanded-form evaluation (5 "
-                                       "instructions per interaction); these kernels use the "
-                                       "difference form (about 10)"}}
+                         "peak_basis": f"EX2 rate: {SM_COUNT} SMs x {EX2_PER_SM_CLK} "
+                                       f"results/clk (measured) x {sm_max:.0f} MHz, one EX2 per "
+                                       f"interaction; these kernels use the difference form "
+                                       f"(about 10 instructions per interaction)"}}
 
 
 # -- our arm -------------------------------------------------------------------
@@ -451,7 +451,7 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel (near field: one EX2 per interaction)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gex2 = SM_COUNT * LANES_PER_SM_CLK / INSTR_PER_INTERACTION * sm_max * 1e6 / 1e9
+    peak_gex2 = SM_COUNT * EX2_PER_SM_CLK * sm_max * 1e6 / 1e9
     nf = statistics.mean(nf_ms)
     achieved = statistics.mean(inter) / (nf / 1e3) / 1e9 if nf > 0 else 0.0
     roofline = {"kernel": "k_near_field", "bound": "alu", "achieved": round(achieved, 1),
@@ -460,10 +460,10 @@ def run_ours(args, rank, world):
                 "traffic": None if batched else near_field_traffic(), "near_field_ms": round(nf, 3),
                 "near_field_share_of_step": round(nf / ms, 3),
                 "interactions_per_step": int(statistics.mean(inter)),
-                "peak_basis": f"issue bound: {SM_COUNT} SMs x {LANES_PER_SM_CLK} lanes/clk / "
-                              f"{INSTR_PER_INTERACTION} instructions per interaction x "
-                              f"{sm_max:.0f} MHz (EX2 pipe ~31/clk/SM and FP32 128/clk/SM "
-                              f"not binding)"}
+                "peak_basis": f"EX2 rate: {SM_COUNT} SMs x {EX2_PER_SM_CLK} results/clk "
+                              f"(measured) x {sm_max:.0f} MHz, one EX2 per interaction (FP32 "
+                              f"pipe 32/clk, issue ~36/clk with paired FP32 instructions: not "
+                              f"binding)"}
 
     out = {"metric": BATCH_METRIC if batched else METRIC, "value": value, "unit": UNIT,
            "n_gpus": world,

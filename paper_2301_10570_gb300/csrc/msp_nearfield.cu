@@ -5,17 +5,17 @@
 // leaves Y (a contiguous segment of the pair list sorted by X).  Blocks take
 // the segments longest first (the order comes from an estimate of each
 // segment's work), so the last wave of blocks is short.  The block collects
-// the targets of X with vacant axons, up to 125 at a time, excitatory ones
-// first (their count padded with empty slots to a multiple of 4 when
-// inhibitory ones follow), and evaluates them in one pass; the warps take the
-// partner pairs round-robin.  Each warp stages the sources of its current
-// pair in its own shared memory and every lane evaluates them against its
-// targets: a lane holds 2 targets (passes of up to 64) or 4 (up to 128), all
-// of one channel, so one staged source (one shared-memory load) serves 2 or 4
-// evaluations; passes of up to 32 targets pad their target pairs to P = 2^k
-// and 32/P lanes share a pair, walking interleaved slices of the sources
-// (small leaves still fill the warp).  The kernel takes 72 registers (7
-// blocks of 4 warps per SM).
+// the targets of X with vacant axons, up to 125 at a time, and evaluates them
+// in one pass; the warps take the partner pairs round-robin.  A lane holds R
+// targets of one channel, R = 2, 3 or 4, the smallest whose 32 R slots hold
+// the round (excitatory targets first, their count padded with empty slots to
+// a multiple of R when inhibitory ones follow).  Each warp stages the sources
+// of its current pair in its own shared memory, in pairs of sources, and
+// every lane evaluates them against its targets, so one staged source pair
+// (two shared-memory loads) serves 2R evaluations; passes of up to 32
+// targets pad their target pairs to P = 2^k and 32/P lanes share a pair,
+// walking interleaved slices of the sources (small leaves still fill the
+// warp).
 // The per-target sums of the 4 warps are added in a fixed order, so u is
 // reproducible run to run.  Per pair, the warp reduces the box-pair
 // attraction W(X,Y) = sum_t a_t sum_s w_s K(t,s) of each channel in single
@@ -26,7 +26,8 @@
 // for the geometric centre c of X,
 //   w_s K(t,s) = 2^( 2 t^.s^ - |s^|^2 + log2 w_s ) * 2^(-|t^|^2),
 // so a source is staged once per warp as (s^, -|s^|^2 + log2 w_s) for each
-// channel and one evaluation is three FMAs, one EX2 on the SFU and one add.
+// channel and one evaluation is three FMAs, one EX2 on the SFU and one add;
+// the FMAs and the add run as paired FP32 instructions over two sources.
 // The first factor is at most 2^(|t^|^2 + 8), so the expanded form is used
 // while |t^|^2 <= 20 for every target of X (leaves up to about 4.3 sigma
 // wide; the exponent's rounding then stays near 1e-6 relative); wider leaves
@@ -47,7 +48,7 @@ __shared__ int32_t* s_wii;
 
 constexpr int kNFWarps = 4;
 constexpr int kNFStage = 64;
-constexpr int kNFMaxT = 32 * 4;    // targets per pass (2 or 4 per lane)
+constexpr int kNFMaxT = 32 * 4;    // targets per pass (2, 3 or 4 per lane)
 constexpr int kNFList = 128;       // target slots per round (one pass)
 constexpr float kNFFastT2 = 20.f;  // largest |t^|^2 of the expanded form
 
@@ -76,11 +77,12 @@ struct NFArgs {
     unsigned long long* work;
 };
 
-// the targets of a lane (R of them, one channel); their scale factors and
-// axon weights sit in shared memory by slot (s_scale, s_fa)
+// the targets of a lane (R of them, one channel), each coordinate broadcast
+// into both halves of a register pair; their scale factors and axon weights
+// sit in shared memory by slot (s_scale, s_fa)
 template <int R>
 struct Tgts {
-    float x[R], y[R], z[R];   // 2 t^ (expanded form) or t^ (difference form)
+    float2 x[R], y[R], z[R];  // 2 t^ (expanded form) or t^ (difference form)
     int ch;                   // 0 excitatory, 1 inhibitory
     int slot0;                // slot of target 0 (targets r at slot0 + r)
 };
@@ -93,81 +95,89 @@ __shared__ float* s_scale;
 __shared__ float* s_fa;
 __shared__ const int32_t* s_tl;
 
-// Evaluate the staged sources [0, m) (lane slice ksl of `slices`) against the
-// lane's R targets.  MODE 0: expanded exponent; 1: expanded, skipping the
-// target itself; 2: difference form; 3: difference form, skipping the target.
-template <int R, int MODE>
-__device__ __forceinline__ void nf_eval(const float4* st, int m, int ksl, int slices,
-                                        const Tgts<R>& tg, int32_t base, float (&part)[R]) {
-    // U sources per iteration (two with four targets: register budget), two
-    // partial sums per target
-    constexpr int U = R == 4 ? 2 : 4;
-    float p[R][2];
+// A warp's staged sources, in pairs: pair j (sources 2j, 2j+1) is the float4
+// (x0, x1, y0, y1) at [j] and (z0, z1, c0, c1) at [32 + j] for the excitatory
+// and at [64 + j] for the inhibitory channel, c = -|s^|^2 + log2 w (expanded
+// form) or log2 w (difference form); an odd count is padded with c = -inf.
+constexpr int kNFStageFloats = 3 * 4 * (kNFStage / 2);
+
+__device__ __forceinline__ float4 nf_source(const float* f, int ch, int e) {
+    const int j = e >> 1, h = e & 1;
+    return make_float4(f[4 * j + h], f[4 * j + 2 + h], f[4 * (32 + j) + h],
+                       f[4 * (32 + 32 * ch + j) + 2 + h]);
+}
+
+// Evaluate the staged source pairs [0, mp) (lane slice ksl of `slices`)
+// against the lane's R targets in the expanded form.  One evaluation of two
+// sources is three paired FMAs, two EX2 and one paired add: the paired FP32
+// instructions take one issue slot for two results.
+template <int R>
+__device__ __forceinline__ void nf_eval_fast(const float4* st, int mp, int ksl, int slices,
+                                             const Tgts<R>& tg, float (&part)[R]) {
+    constexpr int NA = R == 2 ? 2 : 1;   // accumulator pairs per target
+    float2 P[R][NA];
 #pragma unroll
-    for (int r = 0; r < R; ++r) p[r][0] = p[r][1] = 0.f;
-    const float4* sc = st + tg.ch;
-    int e = ksl;
-    if (MODE == 0) {
-        const int step = 2 * slices;
-        const float4* q = sc + 2 * e;
-        if (R == 2) {
-            // the two targets as packed pairs: the exponent chain and the sum
-            // run on the paired FP32 units, with the same rounding per target
-            // as the scalar fmaf / add
-            const float2 TX = make_float2(tg.x[0], tg.x[R - 1]);
-            const float2 TY = make_float2(tg.y[0], tg.y[R - 1]);
-            const float2 TZ = make_float2(tg.z[0], tg.z[R - 1]);
-            float2 P0 = make_float2(0.f, 0.f), P1 = make_float2(0.f, 0.f);
-            for (; e + (U - 1) * slices < m; e += U * slices, q += U * step) {
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int v = 0; v < U; ++v) {
-                    const float4 A = q[v * step];
-                    const float2 E2 = __ffma2_rn(
-                        TX, make_float2(A.x, A.x),
-                        __ffma2_rn(TY, make_float2(A.y, A.y),
-                                   __ffma2_rn(TZ, make_float2(A.z, A.z), make_float2(A.w, A.w))));
-                    const float2 X2 = make_float2(nf_ex2(E2.x), nf_ex2(E2.y));
-                    if (v & 1) P1 = __fadd2_rn(P1, X2);
-                    else       P0 = __fadd2_rn(P0, X2);
-                }
-            }
-            p[0][0] = P0.x; p[R - 1][0] = P0.y;
-            p[0][1] = P1.x; p[R - 1][1] = P1.y;
-        }
-        for (; e + (U - 1) * slices < m; e += U * slices, q += U * step) {
+        for (int k = 0; k < NA; ++k) P[r][k] = make_float2(0.f, 0.f);
+    const float4* xy = st;
+    const float4* zc = st + 32 + 32 * tg.ch;
+    int j = ksl;
+    for (; j + slices < mp; j += 2 * slices) {
 #pragma unroll
-            for (int v = 0; v < U; ++v) {
-                const float4 A = q[v * step];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    p[r][v & 1] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
-            }
-        }
-        for (; e < m; e += slices) {
-            const float4 A = sc[2 * e];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                p[r][0] += nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
-        }
-    } else {
-        for (; e < m; e += slices) {
-            const float4 A = sc[2 * e];
+        for (int v = 0; v < 2; ++v) {
+            const float4 A = xy[j + v * slices], B = zc[j + v * slices];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float v;
-                if (MODE == 0 || MODE == 1) {
-                    v = nf_ex2(fmaf(tg.x[r], A.x, fmaf(tg.y[r], A.y, fmaf(tg.z[r], A.z, A.w))));
-                } else {
-                    const float dx = tg.x[r] - A.x, dy = tg.y[r] - A.y, dz = tg.z[r] - A.z;
-                    v = nf_ex2(A.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                }
-                if (MODE == 1 || MODE == 3) v = base + e == s_tl[tg.slot0 + r] ? 0.f : v;
-                p[r][0] += v;
+                const float2 E = __ffma2_rn(
+                    tg.x[r], make_float2(A.x, A.y),
+                    __ffma2_rn(tg.y[r], make_float2(A.z, A.w),
+                               __ffma2_rn(tg.z[r], make_float2(B.x, B.y), make_float2(B.z, B.w))));
+                P[r][v % NA] = __fadd2_rn(P[r][v % NA], make_float2(nf_ex2(E.x), nf_ex2(E.y)));
             }
         }
     }
+    if (j < mp) {
+        const float4 A = xy[j], B = zc[j];
 #pragma unroll
-    for (int r = 0; r < R; ++r) part[r] += p[r][0] + p[r][1];
+        for (int r = 0; r < R; ++r) {
+            const float2 E = __ffma2_rn(
+                tg.x[r], make_float2(A.x, A.y),
+                __ffma2_rn(tg.y[r], make_float2(A.z, A.w),
+                           __ffma2_rn(tg.z[r], make_float2(B.x, B.y), make_float2(B.z, B.w))));
+            P[r][0] = __fadd2_rn(P[r][0], make_float2(nf_ex2(E.x), nf_ex2(E.y)));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float t = P[r][0].x + P[r][0].y;
+        if (NA == 2) t += P[r][NA - 1].x + P[r][NA - 1].y;
+        part[r] += t;
+    }
+}
+
+// The other forms, one source at a time (sources [0, m), slice ksl of
+// `slices`): MODE 1 expanded, skipping the target itself; 2 difference form;
+// 3 difference form, skipping the target.
+template <int R, int MODE>
+__device__ __forceinline__ void nf_eval_slow(const float4* st, int m, int ksl, int slices,
+                                             const Tgts<R>& tg, int32_t base, float (&part)[R]) {
+    const float* f = reinterpret_cast<const float*>(st);
+    for (int e = ksl; e < m; e += slices) {
+        const float4 A = nf_source(f, tg.ch, e);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float v;
+            if (MODE == 1) {
+                v = nf_ex2(fmaf(tg.x[r].x, A.x, fmaf(tg.y[r].x, A.y, fmaf(tg.z[r].x, A.z, A.w))));
+            } else {
+                const float dx = tg.x[r].x - A.x, dy = tg.y[r].x - A.y, dz = tg.z[r].x - A.z;
+                v = nf_ex2(A.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            }
+            if (MODE == 1 || MODE == 3) v = base + e == s_tl[tg.slot0 + r] ? 0.f : v;
+            part[r] += v;
+        }
+    }
 }
 
 // the pairs of segment [i0, i1) that belong to warp w, for a lane holding R targets
@@ -199,22 +209,36 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
             for (int k = 0; k < R; ++k) part[k] = 0.f;
             for (int32_t sb = 0; sb < sc; sb += kNFStage) {
                 const int m = min(kNFStage, sc - sb);
+                const int mp = (m + 1) >> 1;
                 __syncwarp();
-                for (int e = lane; e < m; e += 32) {
-                    float4 S = a.pts[sf + sb + e];
-                    float2 L = a.lw[sf + sb + e];
-                    float sx = (S.x - cx) * a.sqk, sy = (S.y - cy) * a.sqk, sz = (S.z - cz) * a.sqk;
-                    float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
-                    stw[2 * e] = make_float4(sx, sy, sz, n2 + L.x);
-                    stw[2 * e + 1] = make_float4(sx, sy, sz, n2 + L.y);
+                float* f = reinterpret_cast<float*>(stw);
+                for (int e = lane; e < 2 * mp; e += 32) {
+                    float sx = 0.f, sy = 0.f, sz = 0.f, cE = -INFINITY, cI = -INFINITY;
+                    if (e < m) {
+                        const float4 S = a.pts[sf + sb + e];
+                        const float2 L = a.lw[sf + sb + e];
+                        sx = (S.x - cx) * a.sqk;
+                        sy = (S.y - cy) * a.sqk;
+                        sz = (S.z - cz) * a.sqk;
+                        const float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
+                        cE = n2 + L.x;
+                        cI = n2 + L.y;
+                    }
+                    const int j = e >> 1, h = e & 1;
+                    f[4 * j + h] = sx;
+                    f[4 * j + 2 + h] = sy;
+                    f[4 * (32 + j) + h] = sz;
+                    f[4 * (32 + j) + 2 + h] = cE;
+                    f[4 * (64 + j) + h] = sz;
+                    f[4 * (64 + j) + 2 + h] = cI;
                 }
                 __syncwarp();
                 if (fast) {
-                    if (self) nf_eval<R, 1>(stw, m, ksl, slices, tg, sf + sb, part);
-                    else      nf_eval<R, 0>(stw, m, ksl, slices, tg, sf + sb, part);
+                    if (self) nf_eval_slow<R, 1>(stw, m, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval_fast<R>(stw, mp, ksl, slices, tg, part);
                 } else {
-                    if (self) nf_eval<R, 3>(stw, m, ksl, slices, tg, sf + sb, part);
-                    else      nf_eval<R, 2>(stw, m, ksl, slices, tg, sf + sb, part);
+                    if (self) nf_eval_slow<R, 3>(stw, m, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval_slow<R, 2>(stw, m, ksl, slices, tg, sf + sb, part);
                 }
             }
             float v = 0.f;
@@ -263,7 +287,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
                                            int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
                                            float cy, float cz, float4* stw,
                                            float (*red)[kNFMaxT], unsigned long long& evals) {
-    static_assert(R == 2 || R == 4, "two or four targets per lane");
+    static_assert(R >= 2 && R <= 4, "two to four targets per lane");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0;
     while ((1 << lg) < (nt + R - 1) / R) ++lg;
@@ -288,9 +312,10 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         const float4 T = a.pts[t];
         const uint32_t tw = __float_as_uint(T.w);
         const float hx = (T.x - cx) * a.sqk, hy = (T.y - cy) * a.sqk, hz = (T.z - cz) * a.sqk;
-        tg.x[r] = fast ? 2.f * hx : hx;
-        tg.y[r] = fast ? 2.f * hy : hy;
-        tg.z[r] = fast ? 2.f * hz : hz;
+        const float f2 = fast ? 2.f : 1.f;
+        tg.x[r] = make_float2(f2 * hx, f2 * hx);
+        tg.y[r] = make_float2(f2 * hy, f2 * hy);
+        tg.z[r] = make_float2(f2 * hz, f2 * hz);
         acc[r] = 0.f;
         if (w == 0 && ksl == 0) {
             const float sc = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
@@ -326,10 +351,10 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
 }
 
 __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
-    __shared__ float4 st[kNFWarps][2 * kNFStage];
+    __shared__ float4 st[kNFWarps][kNFStageFloats / 4];
     __shared__ float red[kNFWarps][kNFMaxT];
     __shared__ int32_t tl[kNFList];
-    __shared__ int s_nt, s_pos;
+    __shared__ int s_nt, s_pos, s_R;
     __shared__ float wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
     __shared__ float scale_all[kNFMaxT], fa_all[kNFMaxT];
@@ -359,8 +384,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
             // warp 0 collects up to kNFList - 3 targets with vacant axons from
             // pos on: first walk counts them per channel and finds where the
             // round ends, second walk writes the excitatory ones, padding
-            // entries up to a multiple of 4 if inhibitory ones follow, then
-            // the inhibitory ones (a lane's 2 or 4 slots share a channel)
+            // entries up to a multiple of R if inhibitory ones follow, then
+            // the inhibitory ones (a lane's R slots share a channel)
             if (w == 0) {
                 int nt = 0, nE = 0;
                 int32_t p = pos;
@@ -391,7 +416,13 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
                 }
                 const int32_t pend = min(p, tc);
                 const int nI = nt - nE;
-                const int pad = nI > 0 ? (4 - (nE & 3)) & 3 : 0;
+                // R targets per lane: the fewest slots (2, 3 or 4 per lane
+                // over 32 lanes) that hold the round with its padding
+                auto pad_for = [&](int R) { return nI > 0 ? (R - nE % R) % R : 0; };
+                int R = 4;
+                if (nt + pad_for(2) <= 64) R = 2;
+                else if (nt + pad_for(3) <= 96) R = 3;
+                const int pad = pad_for(R);
                 int we = 0, wi = nE + pad;
                 for (int32_t q = pos; q < pend; q += 32) {
                     const int32_t t = tf + q + lane;
@@ -410,23 +441,23 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
                 if (lane < pad) tl[nE + lane] = -1;
                 if (lane == 0) {
                     s_nt = nt + pad;
+                    s_R = R;
                     s_pos = pend;
                 }
             }
             __syncthreads();
-            const int ntl = s_nt;
+            const int ntl = s_nt, R = s_R;
             pos = s_pos;
             __syncthreads();
             if (ntl == 0) break;
-            for (int c0 = 0; c0 < ntl; c0 += kNFMaxT) {
-                const int m = min(kNFMaxT, ntl - c0);
-                int nreal = 0;
-                for (int k = 0; k < m; ++k) nreal += tl[c0 + k] >= 0;
-                if (m > 64)
-                    nf_targets<4>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-                else
-                    nf_targets<2>(a, tl + c0, m, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-            }
+            int nreal = 0;
+            for (int k = 0; k < ntl; ++k) nreal += tl[k] >= 0;
+            if (R == 4)
+                nf_targets<4>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+            else if (R == 3)
+                nf_targets<3>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+            else
+                nf_targets<2>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             if (pos >= tc) break;
         }
         if (lane == 0 && evals) atomicAdd(a.work, evals);
