@@ -287,7 +287,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
                                            int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
                                            float cy, float cz, float4* stw,
                                            float (*red)[kNFMaxT], unsigned long long& evals) {
-    static_assert(R >= 2 && R <= 4, "two to four targets per lane");
+    static_assert(R >= 2 && R <= 6, "two to six targets per lane");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0;
     while ((1 << lg) < (nt + R - 1) / R) ++lg;
@@ -416,12 +416,21 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
                 }
                 const int32_t pend = min(p, tc);
                 const int nI = nt - nE;
-                // R targets per lane: the fewest slots (2, 3 or 4 per lane
-                // over 32 lanes) that hold the round with its padding
+                // R targets per lane (3 or 4), by the cost of a pass per
+                // staged source pair: the iterations of a lane (npr / 32 with
+                // npr lanes per slice, a power of two) times the cost of one
+                // iteration, the larger of the shared-memory delivery (two
+                // 16-byte loads per lane: 8 cycles) and the EX2 unit (2 R
+                // results per lane at ~30 per SM per clock)
                 auto pad_for = [&](int R) { return nI > 0 ? (R - nE % R) % R : 0; };
-                int R = 4;
-                if (nt + pad_for(2) <= 64) R = 2;
-                else if (nt + pad_for(3) <= 96) R = 3;
+                auto cost_for = [&](int R) {
+                    const int g = (nt + pad_for(R) + R - 1) / R;
+                    if (g > 32) return 1 << 30;
+                    int npr = 1;
+                    while (npr < g) npr <<= 1;
+                    return npr * max(53 * R, 200);
+                };
+                const int R = cost_for(3) <= cost_for(4) ? 3 : 4;
                 const int pad = pad_for(R);
                 int we = 0, wi = nE + pad;
                 for (int32_t q = pos; q < pend; q += 32) {
@@ -454,10 +463,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
             for (int k = 0; k < ntl; ++k) nreal += tl[k] >= 0;
             if (R == 4)
                 nf_targets<4>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
-            else if (R == 3)
-                nf_targets<3>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             else
-                nf_targets<2>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
+                nf_targets<3>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             if (pos >= tc) break;
         }
         if (lane == 0 && evals) atomicAdd(a.work, evals);
