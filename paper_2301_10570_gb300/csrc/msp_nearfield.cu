@@ -47,7 +47,7 @@ __shared__ float* s_wt;
 __shared__ int32_t* s_wii;
 
 constexpr int kNFWarps = 4;
-constexpr int kNFStage = 64;
+constexpr int kNFStage = 128;
 constexpr int kNFMaxT = 32 * 4;    // targets per pass (2, 3 or 4 per lane)
 constexpr int kNFList = 128;       // target slots per round (one pass)
 constexpr float kNFFastT2 = 20.f;  // largest |t^|^2 of the expanded form
@@ -96,24 +96,48 @@ __shared__ float* s_fa;
 __shared__ const int32_t* s_tl;
 
 // A warp's staged sources, in pairs: pair j (sources 2j, 2j+1) is the float4
-// (x0, x1, y0, y1) at [j] and (z0, z1, c0, c1) at [32 + j] for the excitatory
-// and at [64 + j] for the inhibitory channel, c = -|s^|^2 + log2 w (expanded
+// (x0, x1, y0, y1) at [j] and (z0, z1, c0, c1) at [kNFZE + j] for the
+// excitatory and at [kNFZI + j] for the inhibitory channel (one float4 apart
+// from a multiple of 128 bytes, so that the two channels' lanes read different
+// banks), c = -|s^|^2 + log2 w (expanded
 // form) or log2 w (difference form); an odd count is padded with c = -inf.
-constexpr int kNFStageFloats = 3 * 4 * (kNFStage / 2);
-
-__device__ __forceinline__ float4 nf_source(const float* f, int ch, int e) {
-    const int j = e >> 1, h = e & 1;
-    return make_float4(f[4 * j + h], f[4 * j + 2 + h], f[4 * (32 + j) + h],
-                       f[4 * (32 + 32 * ch + j) + 2 + h]);
-}
+constexpr int kNFZE = kNFStage / 2, kNFZI = kNFStage + 1;
+constexpr int kNFStageFloats = 4 * (kNFZI + kNFStage / 2);
 
 // Evaluate the staged source pairs [0, mp) (lane slice ksl of `slices`)
-// against the lane's R targets in the expanded form.  One evaluation of two
-// sources is three paired FMAs, two EX2 and one paired add: the paired FP32
-// instructions take one issue slot for two results.
-template <int R>
-__device__ __forceinline__ void nf_eval_fast(const float4* st, int mp, int ksl, int slices,
-                                             const Tgts<R>& tg, float (&part)[R]) {
+// against the lane's R targets.  MODE 0: expanded form; 1: expanded, skipping
+// the target itself; 2: difference form; 3: difference form, skipping the
+// target.  In the expanded form one evaluation of two sources is three paired
+// FMAs, two EX2 and one paired add (the paired FP32 instructions take one
+// issue slot for two results); the difference form stages -s^ and takes
+// t^ - s^ first.  In MODE 1 and 3 target r sits at position
+// s_tl[slot0 + r] - base among the staged sources (out of range when it is not
+// among them).
+template <int R, int MODE>
+__device__ __forceinline__ float2 nf_term(const Tgts<R>& tg, int r, const float4& A,
+                                          const float4& B) {
+    float2 E;
+    if (MODE <= 1) {
+        E = __ffma2_rn(tg.x[r], make_float2(A.x, A.y),
+                       __ffma2_rn(tg.y[r], make_float2(A.z, A.w),
+                                  __ffma2_rn(tg.z[r], make_float2(B.x, B.y),
+                                             make_float2(B.z, B.w))));
+    } else {
+        const float2 dx = __fadd2_rn(tg.x[r], make_float2(A.x, A.y));
+        const float2 dy = __fadd2_rn(tg.y[r], make_float2(A.z, A.w));
+        const float2 dz = __fadd2_rn(tg.z[r], make_float2(B.x, B.y));
+        E = __ffma2_rn(make_float2(-dx.x, -dx.y), dx,
+                       __ffma2_rn(make_float2(-dy.x, -dy.y), dy,
+                                  __ffma2_rn(make_float2(-dz.x, -dz.y), dz,
+                                             make_float2(B.z, B.w))));
+    }
+    return make_float2(nf_ex2(E.x), nf_ex2(E.y));
+}
+
+template <int R, int MODE>
+__device__ __forceinline__ void nf_eval(const float4* st, int mp, int ksl, int slices,
+                                        const Tgts<R>& tg, int32_t base, float (&part)[R]) {
+    constexpr bool kSkip = MODE == 1 || MODE == 3;
     constexpr int NA = R == 2 ? 2 : 1;   // accumulator pairs per target
     float2 P[R][NA];
 #pragma unroll
@@ -121,31 +145,35 @@ __device__ __forceinline__ void nf_eval_fast(const float4* st, int mp, int ksl, 
 #pragma unroll
         for (int k = 0; k < NA; ++k) P[r][k] = make_float2(0.f, 0.f);
     const float4* xy = st;
-    const float4* zc = st + 32 + 32 * tg.ch;
+    const float4* zc = st + (tg.ch ? kNFZI : kNFZE);
     int j = ksl;
-    for (; j + slices < mp; j += 2 * slices) {
+    // two source pairs per iteration (one when skipping: register budget)
+    for (; !kSkip && j + slices < mp; j += 2 * slices) {
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
-            const float4 A = xy[j + v * slices], B = zc[j + v * slices];
+            const int jj = j + v * slices;
+            const float4 A = xy[jj], B = zc[jj];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 E = __ffma2_rn(
-                    tg.x[r], make_float2(A.x, A.y),
-                    __ffma2_rn(tg.y[r], make_float2(A.z, A.w),
-                               __ffma2_rn(tg.z[r], make_float2(B.x, B.y), make_float2(B.z, B.w))));
-                P[r][v % NA] = __fadd2_rn(P[r][v % NA], make_float2(nf_ex2(E.x), nf_ex2(E.y)));
-            }
+            for (int r = 0; r < R; ++r)
+                P[r][v % NA] = __fadd2_rn(P[r][v % NA], nf_term<R, MODE>(tg, r, A, B));
         }
     }
-    if (j < mp) {
+    for (; kSkip && j < mp; j += slices) {
         const float4 A = xy[j], B = zc[j];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 E = __ffma2_rn(
-                tg.x[r], make_float2(A.x, A.y),
-                __ffma2_rn(tg.y[r], make_float2(A.z, A.w),
-                           __ffma2_rn(tg.z[r], make_float2(B.x, B.y), make_float2(B.z, B.w))));
-            P[r][0] = __fadd2_rn(P[r][0], make_float2(nf_ex2(E.x), nf_ex2(E.y)));
+            float2 X = nf_term<R, MODE>(tg, r, A, B);
+            const int d = s_tl[tg.slot0 + r] - base - 2 * j;
+            X.x = d == 0 ? 0.f : X.x;
+            X.y = d == 1 ? 0.f : X.y;
+            P[r][0] = __fadd2_rn(P[r][0], X);
+        }
+    }
+    if (!kSkip && j < mp) {
+        const float4 A = xy[j], B = zc[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            P[r][0] = __fadd2_rn(P[r][0], nf_term<R, MODE>(tg, r, A, B));
         }
     }
 #pragma unroll
@@ -153,30 +181,6 @@ __device__ __forceinline__ void nf_eval_fast(const float4* st, int mp, int ksl, 
         float t = P[r][0].x + P[r][0].y;
         if (NA == 2) t += P[r][NA - 1].x + P[r][NA - 1].y;
         part[r] += t;
-    }
-}
-
-// The other forms, one source at a time (sources [0, m), slice ksl of
-// `slices`): MODE 1 expanded, skipping the target itself; 2 difference form;
-// 3 difference form, skipping the target.
-template <int R, int MODE>
-__device__ __forceinline__ void nf_eval_slow(const float4* st, int m, int ksl, int slices,
-                                             const Tgts<R>& tg, int32_t base, float (&part)[R]) {
-    const float* f = reinterpret_cast<const float*>(st);
-    for (int e = ksl; e < m; e += slices) {
-        const float4 A = nf_source(f, tg.ch, e);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float v;
-            if (MODE == 1) {
-                v = nf_ex2(fmaf(tg.x[r].x, A.x, fmaf(tg.y[r].x, A.y, fmaf(tg.z[r].x, A.z, A.w))));
-            } else {
-                const float dx = tg.x[r].x - A.x, dy = tg.y[r].x - A.y, dz = tg.z[r].x - A.z;
-                v = nf_ex2(A.w - fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            }
-            if (MODE == 1 || MODE == 3) v = base + e == s_tl[tg.slot0 + r] ? 0.f : v;
-            part[r] += v;
-        }
     }
 }
 
@@ -223,22 +227,27 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                         const float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
                         cE = n2 + L.x;
                         cI = n2 + L.y;
+                        if (!fast) {
+                            sx = -sx;
+                            sy = -sy;
+                            sz = -sz;
+                        }
                     }
                     const int j = e >> 1, h = e & 1;
                     f[4 * j + h] = sx;
                     f[4 * j + 2 + h] = sy;
-                    f[4 * (32 + j) + h] = sz;
-                    f[4 * (32 + j) + 2 + h] = cE;
-                    f[4 * (64 + j) + h] = sz;
-                    f[4 * (64 + j) + 2 + h] = cI;
+                    f[4 * (kNFZE + j) + h] = sz;
+                    f[4 * (kNFZE + j) + 2 + h] = cE;
+                    f[4 * (kNFZI + j) + h] = sz;
+                    f[4 * (kNFZI + j) + 2 + h] = cI;
                 }
                 __syncwarp();
                 if (fast) {
-                    if (self) nf_eval_slow<R, 1>(stw, m, ksl, slices, tg, sf + sb, part);
-                    else      nf_eval_fast<R>(stw, mp, ksl, slices, tg, part);
+                    if (self) nf_eval<R, 1>(stw, mp, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval<R, 0>(stw, mp, ksl, slices, tg, sf + sb, part);
                 } else {
-                    if (self) nf_eval_slow<R, 3>(stw, m, ksl, slices, tg, sf + sb, part);
-                    else      nf_eval_slow<R, 2>(stw, m, ksl, slices, tg, sf + sb, part);
+                    if (self) nf_eval<R, 3>(stw, mp, ksl, slices, tg, sf + sb, part);
+                    else      nf_eval<R, 2>(stw, mp, ksl, slices, tg, sf + sb, part);
                 }
             }
             float v = 0.f;
