@@ -58,6 +58,10 @@ __device__ inline float nf_ex2(float x) {
     return y;
 }
 
+__device__ inline void nf_prefetch_l1(const void* p) {
+    asm volatile("prefetch.L1 [%0];" ::"l"(p));
+}
+
 struct NFArgs {
     const int32_t* seg_first;
     const int64_t* nseg;         // segment count (device memory)
@@ -208,6 +212,17 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
             const int32_t sf = __shfl_sync(0xffffffffu, msf, r);
             const int32_t sc = __shfl_sync(0xffffffffu, msc, r);
             const bool self = sf == tf;
+            {
+                // the next pair's sources into L1 while this one is evaluated
+                // (one 128-byte line of points and of weights per lane)
+                const int rn = min(r + 1, 31);
+                const int32_t sfn = __shfl_sync(0xffffffffu, msf, rn);
+                const int32_t scn = __shfl_sync(0xffffffffu, msc, rn);
+                if (r + 1 < nb) {
+                    if (8 * lane < scn) nf_prefetch_l1(a.pts + sfn + 8 * lane);
+                    if (16 * lane < scn) nf_prefetch_l1(a.lw + sfn + 16 * lane);
+                }
+            }
             float part[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) part[k] = 0.f;

@@ -294,12 +294,25 @@ struct LdSrc {
     }
 };
 
+// floor(v * 2^shift) for a finite 0 <= v < 2^24 (shift <= 40), exact, from the
+// bits of v on the integer pipe: a float to 64-bit integer conversion runs on
+// the FP64 unit, which is scarce on this GPU
+__device__ __forceinline__ uint64_t fixed_point(float v, int shift) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)(b >> 23);                  // biased exponent (v >= 0)
+    if (e == 0) return 0ull;                       // zero or subnormal: below 2^-126
+    const uint64_t m = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + shift;                // v * 2^shift = m * 2^sh
+    if (sh >= 0) return m << sh;
+    return sh > -24 ? m >> -sh : 0ull;
+}
+
 __device__ __forceinline__ uint64_t ld_weight(const float4& T, const float4& S, float k2,
                                               float rc2, int shift) {
     const float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float ws = r2 < rc2 ? S.w * ex2_approx_sel(-r2 * k2) : 0.f;
-    return __float2ull_rz(ldexpf(ws, shift));
+    return fixed_point(ws, shift);
 }
 
 __global__ void __launch_bounds__(kLdWarps * 32)
