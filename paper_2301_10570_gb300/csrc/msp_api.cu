@@ -141,7 +141,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
                          &c->pr_kind, &c->pr_cf, &c->pr_nb, &c->pr_w, &c->far_q, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
-                         &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1,
+                         &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1, &c->nf_src,
                          &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,

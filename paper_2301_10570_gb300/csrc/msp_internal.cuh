@@ -176,6 +176,7 @@ struct msp_ctx {
     // lists
     msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
     msp::DBuf nf_okey0, nf_okey1, nf_oval0, nf_oval1;   // near-field segment order
+    msp::DBuf nf_src;                                    // per near-field pair: (first, count) of Y
     // derivatives (msp_grad.cu)
     msp::DBuf gr_w, gr_tmp, gr_key0, gr_key1, gr_val0, gr_val1, gr_flag, gr_off, gr_seg;
     // expansions

@@ -68,7 +68,7 @@ struct NFArgs {
     const int32_t* order;        // segments, longest first
     const int32_t* list_q;
     const int32_t* pX;
-    const int32_t* pY;
+    const int2* src;             // per near-field pair (list order): Y's first point, count
     const uint8_t* nlevel;
     const uint64_t* nprefix;
     const int32_t* nfirst;
@@ -202,9 +202,9 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
         // metadata of the warp's next 32 pairs, one per lane
         int32_t mi = cb + kNFWarps * lane, msf = 0, msc = 0;
         if (mi < i1) {
-            int32_t Y = a.pY[a.list_q[mi]];
-            msf = a.nfirst[Y];
-            msc = a.ncount[Y];
+            const int2 m = a.src[mi];
+            msf = m.x;
+            msc = m.y;
         }
         const int nb = min(32, (i1 - cb + kNFWarps - 1) / kNFWarps);
         for (int r = 0; r < nb; ++r) {
@@ -289,11 +289,9 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 }
                 sE += __shfl_down_sync(0xffffffffu, sE, 16);
                 sI += __shfl_down_sync(0xffffffffu, sI, 16);
-                if (lane <= slot) {
-                    const int32_t pi = wii[lane];
-                    float2 cur = a.w32[pi];
-                    a.w32[pi] = make_float2(cur.x + sE, cur.y + sI);
-                }
+                // fire-and-forget adds (a pair's slot is only touched by
+                // this warp, once per round of targets, in round order)
+                if (lane <= slot) atomicAdd(&a.w32[wii[lane]], make_float2(sE, sI));
                 __syncwarp();
             }
             evals += (unsigned long long)sc * (unsigned long long)nreal;
@@ -497,13 +495,15 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
 
 // Segment order, longest first: key = 16-bit complement of 1024 log2(work),
 // work = targets of X times the sources of its partner leaves (an estimate:
-// every neuron of X counts as a target).
+// every neuron of X counts as a target).  Also the source range of every
+// pair in list order, so the near field reads one int2 per pair.
 __global__ void k_seg_order_keys(const int32_t* __restrict__ seg_first,
                                  const int64_t* __restrict__ nseg_dev,
                                  const int32_t* __restrict__ list_q,
                                  const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+                                 const int32_t* __restrict__ nfirst,
                                  const int32_t* __restrict__ ncount, uint64_t* __restrict__ key,
-                                 int32_t* __restrict__ val) {
+                                 int32_t* __restrict__ val, int2* __restrict__ src) {
     // one warp per segment, lanes over its pairs
     const int64_t nseg = *nseg_dev;
     const int lane = threadIdx.x & 31;
@@ -512,7 +512,12 @@ __global__ void k_seg_order_keys(const int32_t* __restrict__ seg_first,
          sg += nw) {
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
         float srcs = 0.f;
-        for (int32_t i = i0 + lane; i < i1; i += 32) srcs += (float)ncount[pY[list_q[i]]];
+        for (int32_t i = i0 + lane; i < i1; i += 32) {
+            const int32_t Y = pY[list_q[i]];
+            const int32_t cnt = ncount[Y];
+            src[i] = make_int2(nfirst[Y], cnt);
+            srcs += (float)cnt;
+        }
         for (int o = 16; o > 0; o >>= 1) srcs += __shfl_xor_sync(0xffffffffu, srcs, o);
         if (lane == 0) {
             const float work = srcs * (float)ncount[pX[list_q[i0]]];
@@ -559,9 +564,10 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     uint64_t* ok1 = c.nf_okey1.ensure<uint64_t>((size_t)nseg_cap);
     int32_t* ov0 = c.nf_oval0.ensure<int32_t>((size_t)nseg_cap);
     int32_t* ov1 = c.nf_oval1.ensure<int32_t>((size_t)nseg_cap);
+    int2* src = c.nf_src.ensure<int2>((size_t)nlist_cap);
     k_seg_order_keys<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 16), 128, 0, s>>>(
         seg_first, nseg_dev, list_q, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
-        c.nd_count.get<int32_t>(), ok0, ov0);
+        c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), ok0, ov0, src);
     MSP_LAUNCH("seg_order_keys");
     radix_sort_dev(c, ok0, ov0, ok1, ov1, nseg_dev, nseg_cap, 16, s);
     NFArgs a;
@@ -570,7 +576,7 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     a.order = ov0;
     a.list_q = list_q;
     a.pX = c.pr_X.get<int32_t>();
-    a.pY = c.pr_Y.get<int32_t>();
+    a.src = src;
     a.nlevel = c.nd_level.get<uint8_t>();
     a.nprefix = c.nd_prefix.get<uint64_t>();
     a.nfirst = c.nd_first.get<int32_t>();
