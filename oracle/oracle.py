@@ -21,6 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msp_oracle.c")
 _HDR = os.path.join(_HERE, "msp_oracle.h")
+_SRC_NEURON = os.path.join(_HERE, "msp_neuron.c")
+_HDR_NEURON = os.path.join(_HERE, "msp_neuron.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -32,12 +34,13 @@ SPLIT, FAR, P2P, PRUNED = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FP contraction)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    srcs = (_SRC, _HDR, _SRC_NEURON, _HDR_NEURON)
     stale = force or not os.path.exists(_LIB_PATH) or max(
-        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB_PATH)
+        os.path.getmtime(f) for f in srcs) > os.path.getmtime(_LIB_PATH)
     if stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_NEURON, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -71,6 +74,13 @@ def lib():
             L.orc_attraction_grad.argtypes = [vp] * 10
             L.orc_direct_grad.argtypes = [i64] + [vp] * 7 + [d] + [vp] * 5
             L.orc_vacancy_walk.argtypes = [i64, u64, u64, vp, vp, vp]
+            L.orc_expf.restype = C.c_float
+            L.orc_expf.argtypes = [C.c_float]
+            L.orc_growth.restype = C.c_float
+            L.orc_growth.argtypes = [C.c_float] * 4
+            L.orc_neuron_steps.argtypes = [i64, u64, u64, C.c_int, vp, i64] + [vp] * 9
+            L.orc_update_synapses.restype = i64
+            L.orc_update_synapses.argtypes = [i64, u64, u64, vp, vp, vp, i64] + [vp] * 6
             L.orc_commit_synapses.argtypes = [i64] + [vp] * 6
             for f in ("orc_num_nodes", "orc_num_pairs", "orc_num_elements"):
                 getattr(L, f).restype = i64
@@ -336,3 +346,58 @@ def commit_synapses(syn_pre, syn_post, syn_type, vac_axon, vac_dend_e, vac_dend_
     ty = np.ascontiguousarray(syn_type, np.uint8)
     lib().orc_commit_synapses(len(pre), _p(pre), _p(post), _p(ty), _p(a), _p(e), _p(i))
     return a, e, i
+
+
+# -- the neuron side of the model (Section 3.1, Table 1) ---------------------
+class NeuronParams(C.Structure):
+    """Table 1 values (beta = 5e-4 of the table; the text says 1e-3)."""
+    _fields_ = [("x0", C.c_float), ("tau_x", C.c_float), ("background", C.c_float),
+                ("input_per_spike", C.c_float), ("refractory", C.c_int),
+                ("beta_ca", C.c_float), ("decay_ca", C.c_float), ("eps", C.c_float),
+                ("eta_axon", C.c_float), ("eta_dend", C.c_float), ("mu", C.c_float)]
+
+
+TABLE1 = dict(x0=0.05, tau_x=5.0, background=0.003, input_per_spike=5e-4, refractory=4,
+              beta_ca=5e-4, decay_ca=1e-5, eps=0.7, eta_axon=0.4, eta_dend=0.1, mu=1e-4)
+
+
+def neuron_params(**kw):
+    return NeuronParams(**dict(TABLE1, **kw))
+
+
+def expf(x: float) -> float:
+    return float(lib().orc_expf(float(x)))
+
+
+def growth(ca: float, eta: float, eps: float, mu: float) -> float:
+    return float(lib().orc_growth(float(ca), float(eta), float(eps), float(mu)))
+
+
+NEURON_STATE = (("x", np.float32), ("refractory", np.uint8), ("calcium", np.float32),
+                ("z_axon", np.float32), ("z_dend_e", np.float32), ("z_dend_i", np.float32),
+                ("spiked", np.uint8))
+
+
+def neuron_steps(seed, first_step, n_steps, params, edge_pre, edge_post, state):
+    """n_steps steps of activity, spikes, calcium and elements; returns a new
+    state dict (keys of NEURON_STATE)."""
+    st = {k: np.array(state[k], dtype=t, copy=True) for k, t in NEURON_STATE}
+    n = len(st["x"])
+    pre = np.ascontiguousarray(edge_pre, np.int32)
+    post = np.ascontiguousarray(edge_post, np.int32)
+    lib().orc_neuron_steps(n, int(seed), int(first_step), int(n_steps), C.byref(params),
+                           len(pre), _p(pre), _p(post), *[_p(st[k]) for k, _ in NEURON_STATE])
+    return st
+
+
+def update_synapses(seed, step, z_axon, z_dend_e, z_dend_i, edge_pre, edge_post, edge_type):
+    """Deletion of excess synapses and the vacancies; returns (edges, vacancies)."""
+    za, ze, zi = (np.ascontiguousarray(v, np.float32) for v in (z_axon, z_dend_e, z_dend_i))
+    n = len(za)
+    pre = np.array(edge_pre, np.int32, copy=True)
+    post = np.array(edge_post, np.int32, copy=True)
+    ty = np.array(edge_type, np.uint8, copy=True)
+    va, ve, vi = (np.zeros(max(n, 1), np.uint8) for _ in range(3))
+    m = lib().orc_update_synapses(n, int(seed), int(step), _p(za), _p(ze), _p(zi), len(pre),
+                                  _p(pre), _p(post), _p(ty), _p(va), _p(ve), _p(vi))
+    return (pre[:m], post[:m], ty[:m]), (va[:n], ve[:n], vi[:n])
