@@ -202,6 +202,72 @@ msp_status msp_commit_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t c
                                uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev,
                                void *stream);
 
+/* ---- The neuron side of the model (Section 3.1, Table 1) -------------------
+ * The Model of Structural Plasticity's neurons produce the vacant elements
+ * that the synapse search consumes.  The network's synapses are an edge list
+ * (pre, post, type) in caller-owned device memory, in insertion order, with
+ * its length in device memory (*n_edges_dev) and a capacity; type = the
+ * channel (the pre neuron's type).  Every edge must name neurons in [0, n).
+ * The neuron state is caller-owned device memory, n entries each: activity x,
+ * refractory counter, calcium, the element counts z (continuous) of the axon
+ * and of the two dendrite types, and last step's spike flags.  Draws use the
+ * context's seed.  All three calls are bit-for-bit reproducible. */
+typedef struct {
+    float x0;              /* resting potential (Table 1: 0.05)             */
+    float tau_x;           /* membrane potential decay constant (5)         */
+    float background;      /* background activity per step (0.003)          */
+    float input_per_spike; /* per synapse from a neuron that spiked (5e-4)  */
+    int   refractory;      /* steps without a spike after one (4), <= 255   */
+    float beta_ca;         /* calcium increase per spike (5e-4)             */
+    float decay_ca;        /* calcium decay per step (1e-5)                 */
+    float eps;             /* growth curve right intersection (0.7)         */
+    float eta_axon;        /* growth curve left intersection, axons (0.4)   */
+    float eta_dend;        /* left intersection, dendrites (0.1)            */
+    float mu;              /* growth scaling, the maximum rate (1e-4)       */
+} msp_neuron_params;
+
+/* n_steps simulation steps first_step .. first_step + n_steps - 1 (Section
+ * 3.1).  Per step and neuron t: input = number of edges s -> t whose s
+ * spiked in the previous step (spiked_dev on entry); x <- x + (x0 - x)/tau_x
+ * + background + input_per_spike * input; unless refractory, a Philox draw
+ * U in [0,1) fires when U < x (then refractory = `refractory`); calcium
+ * decays by decay_ca and rises by beta_ca on a spike; each z grows by the
+ * Gaussian growth curve mu (2 exp(-((Ca - xi)/zeta)^2) - 1), xi = (eta +
+ * eps)/2, zeta = (eps - eta)/(2 sqrt(ln 2)) (eta_axon for the axon, eta_dend
+ * for both dendrites), and stays >= 0.  Single precision.  At most
+ * edge_capacity edges are read; an edge naming a neuron outside [0, n) is
+ * skipped.  Asynchronous. */
+msp_status msp_neuron_steps(msp_ctx *ctx, int64_t n, uint64_t first_step, int n_steps,
+                            const msp_neuron_params *params, const int64_t *n_edges_dev,
+                            int64_t edge_capacity, const int32_t *edge_pre_dev,
+                            const int32_t *edge_post_dev,
+                            float *x_dev, uint8_t *refractory_dev, float *calcium_dev,
+                            float *z_axon_dev, float *z_dend_e_dev, float *z_dend_i_dev,
+                            uint8_t *spiked_dev, void *stream);
+
+/* Update of synapses (Section 3.1): a neuron with more bound synapses on a
+ * side (outgoing; incoming of each type) than floor(z) deletes the excess,
+ * chosen uniformly at random with Philox step `step`; an edge chosen by
+ * either of its sides is removed and the list compacted in place, order
+ * kept.  Then vac = clamp(floor(z) - bound, 0, 255) for the axon and both
+ * dendrite types.  Synchronises once (it checks the edges: an endpoint
+ * outside [0, n) gives MSP_ERR_INVALID_ARG and changes nothing). */
+msp_status msp_update_synapses(msp_ctx *ctx, int64_t n, uint64_t step, const float *z_axon_dev,
+                               const float *z_dend_e_dev, const float *z_dend_i_dev,
+                               int64_t *n_edges_dev, int32_t *edge_pre_dev,
+                               int32_t *edge_post_dev, uint8_t *edge_type_dev,
+                               int64_t edge_capacity, uint8_t *vac_axon_dev,
+                               uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev, void *stream);
+
+/* Append the synapses formed by msp_select_partners (*n_syn_dev of them, at
+ * most syn_capacity, the length of the syn_* arrays) to the edge list.  Synchronises once; when the capacity is exceeded, the
+ * synapses that fit are appended and MSP_ERR_CAPACITY is returned. */
+msp_status msp_append_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t syn_capacity,
+                               const int32_t *syn_pre_dev, const int32_t *syn_post_dev,
+                               const uint8_t *syn_type_dev, int64_t *n_edges_dev, int32_t *edge_pre_dev,
+                               int32_t *edge_post_dev, uint8_t *edge_type_dev,
+                               int64_t edge_capacity, void *stream);
+
 /* ---- The whole plasticity step as one CUDA graph ---------------------------
  * A plasticity step of the 100-step run is: vacancy walk (step k), octree
  * build (Section 3.2), attraction (Section 3.3, Eq. 6-8), selection

@@ -17,6 +17,17 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
                      cudaStream_t s);
 void vacancy_walk(msp_ctx& c, int64_t n, uint64_t step, uint8_t* va, uint8_t* vde, uint8_t* vdi,
                   cudaStream_t s);
+void neuron_steps(msp_ctx& c, int64_t n, uint64_t first_step, int n_steps,
+                  const msp_neuron_params& mp, const int64_t* n_edges, int64_t cap,
+                  const int32_t* pre,
+                  const int32_t* post, float* x, uint8_t* refr, float* calcium, float* za,
+                  float* ze, float* zi, uint8_t* spiked, cudaStream_t s);
+void update_synapses(msp_ctx& c, int64_t n, uint64_t step, const float* za, const float* ze,
+                     const float* zi, int64_t* n_edges, int32_t* pre, int32_t* post, uint8_t* typ,
+                     int64_t cap, uint8_t* va, uint8_t* ve, uint8_t* vi, cudaStream_t s);
+void append_synapses(msp_ctx& c, const int64_t* n_syn, int64_t syn_cap, const int32_t* sp,
+                     const int32_t* sq, const uint8_t* st, int64_t* n_edges, int32_t* pre, int32_t* post,
+                     uint8_t* typ, int64_t cap, cudaStream_t s);
 void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const int32_t* pre,
                      const int32_t* post, const uint8_t* styp, uint8_t* va, uint8_t* vde,
                      uint8_t* vdi, cudaStream_t s);
@@ -142,6 +153,10 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->pr_kind, &c->pr_cf, &c->pr_nb, &c->pr_w, &c->far_q, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,
                          &c->nf_w32, &c->nf_okey0, &c->nf_okey1, &c->nf_oval0, &c->nf_oval1, &c->nf_src,
+                         &c->nr_inp, &c->nr_bout, &c->nr_bin, &c->nr_xout, &c->nr_xin,
+                         &c->nr_sout, &c->nr_sin, &c->nr_cnt, &c->nr_key0, &c->nr_key1,
+                         &c->nr_val0, &c->nr_val1, &c->nr_del, &c->nr_keep, &c->nr_pos,
+                         &c->nr_pre2, &c->nr_post2, &c->nr_typ2,
                          &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
@@ -279,6 +294,57 @@ msp_status msp_commit_synapses(msp_ctx* c, const int64_t* n_syn, int64_t capacit
         require(capacity == 0 || (n_syn && pre && post && styp && va && vde && vdi),
                 "null pointer");
         msp::commit_synapses(*c, n_syn, capacity, pre, post, styp, va, vde, vdi,
+                             as_stream(stream));
+    });
+}
+
+msp_status msp_neuron_steps(msp_ctx* c, int64_t n, uint64_t first_step, int n_steps,
+                            const msp_neuron_params* params, const int64_t* n_edges,
+                            int64_t capacity, const int32_t* pre, const int32_t* post, float* x,
+                            uint8_t* refr,
+                            float* calcium, float* za, float* ze, float* zi, uint8_t* spiked,
+                            void* stream) {
+    return guarded(c, [&] {
+        require(n >= 0 && n < 0x7fffffffll, "n out of range");
+        require(n_steps >= 0, "n_steps out of range");
+        require(capacity >= 0 && capacity < 0x7fffffffll, "capacity out of range");
+        require(params != nullptr, "null parameters");
+        require(params->refractory >= 0 && params->refractory <= 255, "refractory out of range");
+        require(params->tau_x != 0.f && params->eps != params->eta_axon &&
+                    params->eps != params->eta_dend, "degenerate parameters");
+        require(n == 0 || (n_edges && pre && post && x && refr && calcium && za && ze && zi &&
+                           spiked), "null pointer");
+        msp::neuron_steps(*c, n, first_step, n_steps, *params, n_edges, capacity, pre, post, x,
+                          refr,
+                          calcium, za, ze, zi, spiked, as_stream(stream));
+    });
+}
+
+msp_status msp_update_synapses(msp_ctx* c, int64_t n, uint64_t step, const float* za,
+                               const float* ze, const float* zi, int64_t* n_edges, int32_t* pre,
+                               int32_t* post, uint8_t* typ, int64_t capacity, uint8_t* va,
+                               uint8_t* ve, uint8_t* vi, void* stream) {
+    return guarded(c, [&] {
+        require(n >= 0 && n < 0x3fffffffll, "n out of range");
+        require(capacity >= 0 && capacity < 0x7fffffffll, "capacity out of range");
+        require(n == 0 || (za && ze && zi && n_edges && pre && post && typ && va && ve && vi),
+                "null pointer");
+        msp::update_synapses(*c, n, step, za, ze, zi, n_edges, pre, post, typ, capacity, va, ve,
+                             vi, as_stream(stream));
+    });
+}
+
+msp_status msp_append_synapses(msp_ctx* c, const int64_t* n_syn, int64_t syn_capacity,
+                               const int32_t* sp, const int32_t* sq, const uint8_t* st,
+                               int64_t* n_edges,
+                               int32_t* pre, int32_t* post, uint8_t* typ, int64_t capacity,
+                               void* stream) {
+    return guarded(c, [&] {
+        require(capacity >= 0 && capacity < 0x7fffffffll, "capacity out of range");
+        require(syn_capacity >= 0, "synapse capacity out of range");
+        require(n_syn && sp && sq && st && n_edges && pre && post && typ, "null pointer");
+        msp::append_synapses(*c, n_syn, syn_capacity, sp, sq, st, n_edges, pre, post, typ,
+                             capacity,
                              as_stream(stream));
     });
 }

@@ -177,6 +177,11 @@ struct msp_ctx {
     msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
     msp::DBuf nf_okey0, nf_okey1, nf_oval0, nf_oval1;   // near-field segment order
     msp::DBuf nf_src;                                    // per near-field pair: (first, count) of Y
+    // neuron side (msp_neuron.cu): input counts, bound synapses, excess, group
+    // starts, deletion sort keys, flags and the compacted edge copy
+    msp::DBuf nr_inp, nr_bout, nr_bin, nr_xout, nr_xin, nr_sout, nr_sin, nr_cnt;
+    msp::DBuf nr_key0, nr_key1, nr_val0, nr_val1, nr_del, nr_keep, nr_pos;
+    msp::DBuf nr_pre2, nr_post2, nr_typ2;
     // derivatives (msp_grad.cu)
     msp::DBuf gr_w, gr_tmp, gr_key0, gr_key1, gr_val0, gr_val1, gr_flag, gr_off, gr_seg;
     // expansions

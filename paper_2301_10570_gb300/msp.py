@@ -32,9 +32,51 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_export_expansions", "msp_last_error", "msp_direct_noalloc",
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
             "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
-            "msp_set_workspace_limit", "msp_workspace_bytes")
+            "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
+            "msp_update_synapses", "msp_append_synapses")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
+
+
+class NeuronParams(C.Structure):
+    """msp_neuron_params of include/msp.h."""
+    _fields_ = [("x0", C.c_float), ("tau_x", C.c_float), ("background", C.c_float),
+                ("input_per_spike", C.c_float), ("refractory", C.c_int),
+                ("beta_ca", C.c_float), ("decay_ca", C.c_float), ("eps", C.c_float),
+                ("eta_axon", C.c_float), ("eta_dend", C.c_float), ("mu", C.c_float)]
+
+
+# Table 1 (beta = 5e-4 of the table; the text says 1e-3), refractory period 4
+# and 5e-4 per spiking presynaptic partner (Section 3.1)
+TABLE1 = dict(x0=0.05, tau_x=5.0, background=0.003, input_per_spike=5e-4, refractory=4,
+              beta_ca=5e-4, decay_ca=1e-5, eps=0.7, eta_axon=0.4, eta_dend=0.1, mu=1e-4)
+
+
+def neuron_params(**kw) -> NeuronParams:
+    return NeuronParams(**dict(TABLE1, **kw))
+
+
+NEURON_STATE = (("x", torch.float32), ("refractory", torch.uint8), ("calcium", torch.float32),
+                ("z_axon", torch.float32), ("z_dend_e", torch.float32),
+                ("z_dend_i", torch.float32), ("spiked", torch.uint8))
+
+
+def edge_list(capacity: int, device="cuda", pre=None, post=None, type_=None) -> dict:
+    """An edge list (pre, post, type) of the given capacity, filled with the
+    given edges (any array-likes) and its length in device memory."""
+    e = dict(pre=torch.zeros(max(capacity, 1), dtype=torch.int32, device=device),
+             post=torch.zeros(max(capacity, 1), dtype=torch.int32, device=device),
+             type=torch.zeros(max(capacity, 1), dtype=torch.uint8, device=device),
+             n=torch.zeros(1, dtype=torch.int64, device=device), capacity=int(capacity))
+    if pre is not None:
+        m = len(pre)
+        if m > capacity:
+            raise ValueError("more edges than the capacity")
+        e["pre"][:m] = torch.as_tensor(pre, dtype=torch.int32)
+        e["post"][:m] = torch.as_tensor(post, dtype=torch.int32)
+        e["type"][:m] = torch.as_tensor(type_, dtype=torch.uint8)
+        e["n"].fill_(m)
+    return e
 
 
 class MSPError(RuntimeError):
@@ -100,9 +142,16 @@ def load(path: str = LIB_PATH):
         L.msp_set_workspace_limit.restype = C.c_int
         L.msp_workspace_bytes.argtypes = []
         L.msp_workspace_bytes.restype = i64
+        L.msp_neuron_steps.argtypes = [vp, i64, u64, C.c_int, C.POINTER(NeuronParams), vp,
+                                       i64] + [vp] * 9 + [vp]
+        L.msp_update_synapses.argtypes = [vp, i64, u64] + [vp] * 7 + [i64] + [vp] * 3 + [vp]
+        L.msp_append_synapses.argtypes = [vp, vp, i64] + [vp] * 7 + [i64, vp]
+        for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses"):
+            getattr(L, name).restype = C.c_int
         for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
                      "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
-            "msp_set_workspace_limit", "msp_workspace_bytes"):
+            "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
+            "msp_update_synapses", "msp_append_synapses"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
@@ -259,6 +308,35 @@ class MSP:
                                           _ptr(sel["syn_pre"]), _ptr(sel["syn_post"]),
                                           _ptr(sel["syn_type"]), _ptr(vac_axon),
                                           _ptr(vac_dend_e), _ptr(vac_dend_i), _stream(stream)))
+
+    # -- the neuron side of the model (Section 3.1) ------------------------------
+    def neuron_steps(self, first_step, n_steps, params, edges, state, stream=None):
+        """n_steps steps of activity, spikes, calcium and elements, in place on
+        `state` (CUDA tensors, keys of NEURON_STATE)."""
+        n = int(state["x"].numel())
+        _check(load().msp_neuron_steps(
+            self._h, n, int(first_step), int(n_steps), C.byref(params), _ptr(edges["n"]),
+            int(edges["capacity"]), _ptr(edges["pre"]), _ptr(edges["post"]),
+            *[_ptr(state[k]) for k, _ in NEURON_STATE], _stream(stream)))
+
+    def update_synapses(self, step, state, edges, vac_axon, vac_dend_e, vac_dend_i,
+                        stream=None):
+        """Deletion of the synapses beyond floor(elements) and the vacancies
+        (uint8 CUDA tensors, written)."""
+        n = int(state["x"].numel())
+        _check(load().msp_update_synapses(
+            self._h, n, int(step), _ptr(state["z_axon"]), _ptr(state["z_dend_e"]),
+            _ptr(state["z_dend_i"]), _ptr(edges["n"]), _ptr(edges["pre"]), _ptr(edges["post"]),
+            _ptr(edges["type"]), int(edges["capacity"]), _ptr(vac_axon), _ptr(vac_dend_e),
+            _ptr(vac_dend_i), _stream(stream)))
+
+    def append_synapses(self, sel, edges, stream=None):
+        """Append the synapses of a selection to the edge list."""
+        _check(load().msp_append_synapses(
+            self._h, _ptr(sel["n_syn"]), int(sel["syn_pre"].numel()), _ptr(sel["syn_pre"]),
+            _ptr(sel["syn_post"]),
+            _ptr(sel["syn_type"]), _ptr(edges["n"]), _ptr(edges["pre"]), _ptr(edges["post"]),
+            _ptr(edges["type"]), int(edges["capacity"]), _stream(stream)))
 
     # -- derivatives ------------------------------------------------------------
     def attraction_grad(self, type_, vac_axon, vac_dend_e, vac_dend_i, g=None, want_u=True,
