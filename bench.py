@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="rerun the plan chooser on this workload and bench its plan")
     ap.add_argument("--workload", default="clustered_1m",
-                    choices=["clustered_1m", "batched_256", "gradient_262k"],
+                    choices=["clustered_1m", "batched_256", "gradient_262k", "simulation_1m"],
                     help="clustered_1m: the headline network; batched_256: 256 independent "
                          "networks (about 11.7M neurons) in one batched step; gradient_262k: "
-                         "the derivatives of the attraction at 262,144 clustered neurons")
+                         "the derivatives of the attraction at 262,144 clustered neurons; "
+                         "simulation_1m: the model's simulation loop (100 neuron steps and one "
+                         "connectivity update per cycle) on the 1M clustered network")
     return ap.parse_args()
 
 
@@ -267,6 +269,120 @@ def run_gradient(args, rank, world):
                                        f"results/clk (measured) x {sm_max:.0f} MHz, one EX2 per "
                                        f"interaction; these kernels use the difference form "
                                        f"(about 10 instructions per interaction)"}}
+
+
+# -- the simulation loop of the model (neuron side + synapse search) ------------
+SIM_METRIC = ("MSP simulation neuron-steps/s at 1M neurons (100 activity steps and one "
+              "connectivity update per cycle) on GB300")
+
+
+def run_simulation(args, rank, world):
+    """Cycles of the model's simulation (Section 3.1): 100 steps of activity,
+    spikes, calcium and element growth, then the update of synapses
+    (deletion, vacancies) and the synapse search on those vacancies with the
+    formed synapses appended to the network.  Timed per cycle with CUDA
+    events, L2 flushed between cycles."""
+    import numpy as np
+    import torch
+
+    from paper_2301_10570_gb300 import msp, replicas, workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = tuned_params()
+    w = W.clustered_1m(**plan)
+    n = w.n
+    rng = np.random.default_rng(41)
+    pos, t, a, e, i = msp.to_device(w, dev)
+    # activity at rest, calcium spread over the growth curve, elements just
+    # above the workload's vacant counts (no synapse yet)
+    state = {
+        "x": torch.full((n,), 0.065, dtype=torch.float32, device=dev),
+        "refractory": torch.zeros(n, dtype=torch.uint8, device=dev),
+        "calcium": torch.from_numpy(rng.uniform(0.3, 0.8, n).astype(np.float32)).to(dev),
+        "z_axon": a.float() + 0.5, "z_dend_e": e.float() + 0.5, "z_dend_i": i.float() + 0.5,
+        "spiked": torch.zeros(n, dtype=torch.uint8, device=dev)}
+    params = msp.neuron_params()
+    edges = msp.edge_list(12 * n, device=dev)
+    vac = [torch.zeros(n, dtype=torch.uint8, device=dev) for _ in range(3)]
+    cap = 6 * n
+    sel = dict(partner=torch.empty(cap, dtype=torch.int32, device=dev),
+               syn_pre=torch.empty(cap, dtype=torch.int32, device=dev),
+               syn_post=torch.empty(cap, dtype=torch.int32, device=dev),
+               syn_type=torch.empty(cap, dtype=torch.uint8, device=dev),
+               n_syn=torch.zeros(1, dtype=torch.int64, device=dev))
+    g = msp.MSP(w.params, device=dev.index)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def cycle(k, ev=None):
+        if ev is not None:
+            ev[0].record()
+        g.neuron_steps(100 * k, 100, params, edges, state)
+        if ev is not None:
+            ev[1].record()
+        g.update_synapses(k, state, edges, *vac)
+        g.build_tree(pos, t, *vac)
+        if g.num_elements() > cap:
+            raise RuntimeError("more vacant axonal elements than the selection buffers hold")
+        g.attraction()
+        g.select_partners(k, out=sel)
+        g.append_synapses(sel, edges)
+        if ev is not None:
+            ev[2].record()
+
+    for k in range(args.warmup):
+        cycle(k)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    launches0 = g.stats()["kernel_launches"]
+    n_edges = []
+    clocks = Clocks(dev.index)
+    clocks.start()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        n_edges.append(edges["n"].clone())
+        cycle(args.warmup + k, evs[k])
+    torch.cuda.synchronize()
+    replicas.barrier()
+    clk = clocks.stop()
+    launches = g.stats()["kernel_launches"] - launches0
+    cyc = [x.elapsed_time(z) for x, _, z in evs]
+    neu = [x.elapsed_time(y) for x, y, _ in evs]
+    agg = replicas.aggregate_throughput(100 * n, sum(cyc) / len(cyc), dev)
+    # algorithmic bytes of a neuron step: per neuron the state read and
+    # written (activity 4+4, refractory 1+1, calcium 4+4, three element
+    # counts 12+12, spike flag 1, input count 4+4) = 51 B; per spiking neuron
+    # its edge range (8 B) and per outgoing edge the target (4 B) and the
+    # input count it adds to (4 B); spikes per step from the last step
+    m = float(torch.stack(n_edges).double().mean().item())
+    spikes = float(state["spiked"].sum().item())
+    bytes_step = 51.0 * n + spikes * (8.0 + 8.0 * m / n)
+    nm = statistics.mean(neu)
+    achieved = 100 * bytes_step / (nm / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    g.close()
+    return {"metric": SIM_METRIC, "value": agg["per_s"], "unit": "neuron-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(agg["ms"], 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "simulation_1m: clustered_1m positions and types; a step of "
+                                   "the cycle is 100 neuron steps (Table 1 parameters), the "
+                                   "update of synapses and one synapse search whose synapses "
+                                   "join the network",
+                       "plan": plan, "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MB write) between timed cycles",
+                       "timing": "CUDA events per cycle, mean over cycles",
+                       "median_ms_per_step": round(statistics.median(cyc), 3),
+                       "neuron_steps_ms_per_cycle": round(nm, 3),
+                       "edges_mean": round(m, 1)},
+            "clocks": clk, "gpu_launches": int(launches),
+            "roofline": {"kernel": "k_neuron_step", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "bytes_per_step": round(bytes_step, 1),
+                         "spikes_per_step": spikes,
+                         "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
 
 
 # -- our arm -------------------------------------------------------------------
@@ -612,8 +728,9 @@ def main():
         for row in table:
             print(json.dumps(row), file=sys.stderr)
         _PLAN_OVERRIDE = best
-    if args.workload == "gradient_262k":
-        out = run_gradient(args, rank, world)
+    if args.workload in ("gradient_262k", "simulation_1m"):
+        out = (run_gradient if args.workload == "gradient_262k" else run_simulation)(
+            args, rank, world)
         if rank == 0:
             print(json.dumps(out))
         if world > 1:

@@ -69,18 +69,46 @@ __device__ float nr_growth(float ca, float eta, float eps, float mu) {
     return __fmul_rn(mu, __fadd_rn(__fadd_rn(e, e), -1.0f));
 }
 
-// input: one count per edge s -> t whose s spiked in the previous step (an
-// edge naming a neuron outside [0, n) is skipped)
-__global__ void k_spike_input(const int64_t* __restrict__ n_edges, int64_t cap, int64_t n,
-                              const int32_t* __restrict__ pre, const int32_t* __restrict__ post,
-                              const uint8_t* __restrict__ spiked, int32_t* __restrict__ inp) {
+// The input of a step is event driven: the outgoing edges of each neuron, as
+// a compressed list by presynaptic neuron rebuilt at the start of every
+// call, and two input-count buffers; a neuron that spikes in step k adds one
+// to the next buffer for each of its outgoing edges, which step k + 1 reads
+// (and clears).  Edges naming a neuron outside [0, n) are skipped.
+__global__ void k_out_degree(const int64_t* __restrict__ n_edges, int64_t cap, int64_t n,
+                             const int32_t* __restrict__ pre, const int32_t* __restrict__ post,
+                             int32_t* __restrict__ deg) {
     const int64_t m = min(*n_edges, cap);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = pre[e], b = post[e];
         if (a < 0 || a >= n || b < 0 || b >= n) continue;
-        if (spiked[a]) atomicAdd(&inp[b], 1);
+        atomicAdd(&deg[a], 1);
     }
+}
+
+// targets of each neuron's outgoing edges at [off[s], off[s] + deg[s]) (the
+// order inside a neuron's range does not matter: only counts are formed)
+__global__ void k_out_fill(const int64_t* __restrict__ n_edges, int64_t cap, int64_t n,
+                           const int32_t* __restrict__ pre, const int32_t* __restrict__ post,
+                           const int32_t* __restrict__ off, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ targets) {
+    const int64_t m = min(*n_edges, cap);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = pre[e], b = post[e];
+        if (a < 0 || a >= n || b < 0 || b >= n) continue;
+        targets[off[a] + atomicAdd(&cursor[a], 1)] = b;
+    }
+}
+
+// the input of the first step of a call: last step's spikes
+__global__ void k_seed_input(int64_t n, const uint8_t* __restrict__ spiked,
+                             const int32_t* __restrict__ off, const int32_t* __restrict__ deg,
+                             const int32_t* __restrict__ targets, int32_t* __restrict__ inp) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        if (spiked[t])
+            for (int32_t j = off[t], j1 = off[t] + deg[t]; j < j1; ++j) atomicAdd(&inp[targets[j]], 1);
 }
 
 // edges naming a neuron outside [0, n), or a count above the capacity
@@ -97,16 +125,19 @@ __global__ void k_check_edges(const int64_t* __restrict__ n_edges, int64_t cap, 
     }
 }
 
-// one step of every neuron; consumes (and clears) the input counts
+// one step of every neuron: consumes (and clears) its input count in `cur`,
+// and a spike adds one to `next` for each outgoing edge
 __global__ void k_neuron_step(int64_t n, uint64_t seed, uint64_t step, msp_neuron_params mp,
-                              int32_t* __restrict__ inp, float* __restrict__ x,
+                              int32_t* __restrict__ cur, int32_t* __restrict__ next,
+                              const int32_t* __restrict__ off, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ targets, float* __restrict__ x,
                               uint8_t* __restrict__ refr, float* __restrict__ calcium,
                               float* __restrict__ za, float* __restrict__ ze,
                               float* __restrict__ zi, uint8_t* __restrict__ spiked) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t in = inp[t];
-        inp[t] = 0;
+        const int32_t in = cur[t];
+        cur[t] = 0;
         float xt = x[t];
         float d = __fadd_rn(mp.x0, -xt);
         d = __fdiv_rn(d, mp.tau_x);
@@ -136,6 +167,9 @@ __global__ void k_neuron_step(int64_t n, uint64_t seed, uint64_t step, msp_neuro
         ze[t] = e > 0.0f ? e : 0.0f;
         zi[t] = i > 0.0f ? i : 0.0f;
         spiked[t] = (uint8_t)s;
+        if (s)
+            for (int32_t j = off[t], j1 = off[t] + deg[t]; j < j1; ++j)
+                atomicAdd(&next[targets[j]], 1);
     }
 }
 
@@ -281,21 +315,37 @@ int bits_for_neuron(int64_t v) {
 
 void neuron_steps(msp_ctx& c, int64_t n, uint64_t first_step, int n_steps,
                   const msp_neuron_params& mp, const int64_t* n_edges, int64_t cap,
-                  const int32_t* pre,
-                  const int32_t* post, float* x, uint8_t* refr, float* calcium, float* za,
-                  float* ze, float* zi, uint8_t* spiked, cudaStream_t s) {
+                  const int32_t* pre, const int32_t* post, float* x, uint8_t* refr,
+                  float* calcium, float* za, float* ze, float* zi, uint8_t* spiked,
+                  cudaStream_t s) {
     NvtxRange nv_("msp neuron_steps");
     if (n <= 0 || n_steps <= 0) return;
-    const bool fresh = c.nr_inp.bytes < (size_t)n * sizeof(int32_t);
-    int32_t* inp = c.nr_inp.ensure<int32_t>((size_t)n);
-    if (fresh) MSP_CUDA(cudaMemsetAsync(inp, 0, (size_t)n * sizeof(int32_t), s));
+    int32_t* inp = c.nr_inp.ensure<int32_t>((size_t)2 * n);
+    int32_t* deg = c.nr_bout.ensure<int32_t>((size_t)n);
+    int32_t* off = c.nr_sout.ensure<int32_t>((size_t)n);
+    int32_t* cursor = c.nr_xout.ensure<int32_t>((size_t)n);
+    int32_t* targets = c.nr_pos.ensure<int32_t>((size_t)std::max<int64_t>(cap, 1));
+    int64_t* cnt = c.nr_cnt.ensure<int64_t>(4);
     const int ge = (int)c.sm_count * 8;
     const int gn = grid_for(n, 256, (int64_t)c.sm_count * 16);
+    // outgoing edges by presynaptic neuron
+    MSP_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int32_t), s));
+    MSP_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), s));
+    MSP_CUDA(cudaMemsetAsync(inp, 0, (size_t)2 * n * sizeof(int32_t), s));
+    k_out_degree<<<ge, 256, 0, s>>>(n_edges, cap, n, pre, post, deg);
+    MSP_LAUNCH("out_degree");
+    dev_set(cnt, n, s);
+    scan_dev(c, deg, off, cnt, n, cnt + 2, nullptr, s);
+    k_out_fill<<<ge, 256, 0, s>>>(n_edges, cap, n, pre, post, off, cursor, targets);
+    MSP_LAUNCH("out_fill");
+    k_seed_input<<<gn, 256, 0, s>>>(n, spiked, off, deg, targets, inp);
+    MSP_LAUNCH("seed_input");
     for (int k = 0; k < n_steps; ++k) {
-        k_spike_input<<<ge, 256, 0, s>>>(n_edges, cap, n, pre, post, spiked, inp);
-        MSP_LAUNCH("spike_input");
-        k_neuron_step<<<gn, 256, 0, s>>>(n, c.cfg.seed, first_step + (uint64_t)k, mp, inp, x, refr,
-                                          calcium, za, ze, zi, spiked);
+        int32_t* cur = inp + (size_t)(k & 1) * n;
+        int32_t* next = inp + (size_t)((k + 1) & 1) * n;
+        k_neuron_step<<<gn, 256, 0, s>>>(n, c.cfg.seed, first_step + (uint64_t)k, mp, cur, next,
+                                          off, deg, targets, x, refr, calcium, za, ze, zi,
+                                          spiked);
         MSP_LAUNCH("neuron_step");
     }
 }
