@@ -125,51 +125,111 @@ __global__ void k_check_edges(const int64_t* __restrict__ n_edges, int64_t cap, 
     }
 }
 
-// one step of every neuron: consumes (and clears) its input count in `cur`,
-// and a spike adds one to `next` for each outgoing edge
-__global__ void k_neuron_step(int64_t n, uint64_t seed, uint64_t step, msp_neuron_params mp,
-                              int32_t* __restrict__ cur, int32_t* __restrict__ next,
-                              const int32_t* __restrict__ off, const int32_t* __restrict__ deg,
-                              const int32_t* __restrict__ targets, float* __restrict__ x,
-                              uint8_t* __restrict__ refr, float* __restrict__ calcium,
-                              float* __restrict__ za, float* __restrict__ ze,
-                              float* __restrict__ zi, uint8_t* __restrict__ spiked) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t in = cur[t];
-        cur[t] = 0;
-        float xt = x[t];
-        float d = __fadd_rn(mp.x0, -xt);
-        d = __fdiv_rn(d, mp.tau_x);
-        xt = __fadd_rn(xt, d);
-        xt = __fadd_rn(xt, mp.background);
-        xt = __fadd_rn(xt, __fmul_rn(mp.input_per_spike, (float)in));
-        x[t] = xt;
-        int s = 0;
-        const uint8_t rf = refr[t];
-        if (rf > 0) {
-            refr[t] = (uint8_t)(rf - 1);
-        } else {
-            const uint32_t o = nr_draw(seed, (uint32_t)t, kTagSpike << 16, step);
-            const float u = __fmul_rn((float)(o >> 8), 1.0f / 16777216.0f);
-            s = u < xt;
-            if (s) refr[t] = (uint8_t)mp.refractory;
+// The state of one neuron through one step (Section 3.1): activity with
+// input `in`, the spike draw, calcium, the three element counts.  Returns the
+// spike.
+struct NrState {
+    float x, ca, za, ze, zi;
+    uint32_t rf;
+};
+
+__device__ __forceinline__ int nr_update(NrState& v, int32_t in, uint32_t t, uint64_t seed,
+                                         uint64_t step, const msp_neuron_params& mp) {
+    float d = __fadd_rn(mp.x0, -v.x);
+    d = __fdiv_rn(d, mp.tau_x);
+    float xt = __fadd_rn(v.x, d);
+    xt = __fadd_rn(xt, mp.background);
+    xt = __fadd_rn(xt, __fmul_rn(mp.input_per_spike, (float)in));
+    v.x = xt;
+    int s = 0;
+    if (v.rf > 0) {
+        v.rf -= 1;
+    } else {
+        const uint32_t o = nr_draw(seed, t, kTagSpike << 16, step);
+        const float u = __fmul_rn((float)(o >> 8), 1.0f / 16777216.0f);
+        s = u < xt;
+        if (s) v.rf = (uint32_t)mp.refractory;
+    }
+    float ca = __fadd_rn(v.ca, -__fmul_rn(v.ca, mp.decay_ca));
+    if (s) ca = __fadd_rn(ca, mp.beta_ca);
+    v.ca = ca;
+    const float a = __fadd_rn(v.za, nr_growth(ca, mp.eta_axon, mp.eps, mp.mu));
+    const float gd = nr_growth(ca, mp.eta_dend, mp.eps, mp.mu);
+    const float e = __fadd_rn(v.ze, gd);
+    const float i = __fadd_rn(v.zi, gd);
+    v.za = a > 0.0f ? a : 0.0f;
+    v.ze = e > 0.0f ? e : 0.0f;
+    v.zi = i > 0.0f ? i : 0.0f;
+    return s;
+}
+
+// One step of every neuron: consumes (and clears) its input count in `cur`;
+// a spike adds one to `next` for each outgoing edge.  With vec4 set (every
+// array 16-byte aligned, the byte arrays 4-byte aligned) a thread takes four
+// consecutive neurons with 16-byte loads and stores, so that more of the
+// state is in flight per thread; the last n mod 4 neurons (or all, without
+// vec4) go one per thread.
+__global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
+                              msp_neuron_params mp, int32_t* __restrict__ cur,
+                              int32_t* __restrict__ next, const int32_t* __restrict__ off,
+                              const int32_t* __restrict__ deg, const int32_t* __restrict__ targets,
+                              float* __restrict__ x, uint8_t* __restrict__ refr,
+                              float* __restrict__ calcium, float* __restrict__ za,
+                              float* __restrict__ ze, float* __restrict__ zi,
+                              uint8_t* __restrict__ spiked) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = vec4 ? n / 4 : 0;
+    for (int64_t q = tid; q < n4; q += stride) {
+        const int4 in4 = reinterpret_cast<const int4*>(cur)[q];
+        const int4 o4 = reinterpret_cast<const int4*>(off)[q];
+        const int4 d4 = reinterpret_cast<const int4*>(deg)[q];
+        const float4 x4 = reinterpret_cast<const float4*>(x)[q];
+        const float4 c4 = reinterpret_cast<const float4*>(calcium)[q];
+        const float4 a4 = reinterpret_cast<const float4*>(za)[q];
+        const float4 e4 = reinterpret_cast<const float4*>(ze)[q];
+        const float4 i4 = reinterpret_cast<const float4*>(zi)[q];
+        const uint32_t r4 = reinterpret_cast<const uint32_t*>(refr)[q];
+        reinterpret_cast<int4*>(cur)[q] = make_int4(0, 0, 0, 0);
+        const int32_t ins[4] = {in4.x, in4.y, in4.z, in4.w};
+        const int32_t j0s[4] = {o4.x, o4.y, o4.z, o4.w};
+        const int32_t njs[4] = {d4.x, d4.y, d4.z, d4.w};
+        NrState v[4] = {{x4.x, c4.x, a4.x, e4.x, i4.x, r4 & 0xffu},
+                        {x4.y, c4.y, a4.y, e4.y, i4.y, (r4 >> 8) & 0xffu},
+                        {x4.z, c4.z, a4.z, e4.z, i4.z, (r4 >> 16) & 0xffu},
+                        {x4.w, c4.w, a4.w, e4.w, i4.w, r4 >> 24}};
+        uint32_t sp = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = nr_update(v[k], ins[k], (uint32_t)(4 * q + k), seed, step, mp);
+            sp |= (uint32_t)s << (8 * k);
+            if (s)
+                for (int32_t j = j0s[k]; j < j0s[k] + njs[k]; ++j) atomicAdd(&next[targets[j]], 1);
         }
-        float ca = calcium[t];
-        ca = __fadd_rn(ca, -__fmul_rn(ca, mp.decay_ca));
-        if (s) ca = __fadd_rn(ca, mp.beta_ca);
-        calcium[t] = ca;
-        const float a = __fadd_rn(za[t], nr_growth(ca, mp.eta_axon, mp.eps, mp.mu));
-        const float gd = nr_growth(ca, mp.eta_dend, mp.eps, mp.mu);
-        const float e = __fadd_rn(ze[t], gd);
-        const float i = __fadd_rn(zi[t], gd);
-        za[t] = a > 0.0f ? a : 0.0f;
-        ze[t] = e > 0.0f ? e : 0.0f;
-        zi[t] = i > 0.0f ? i : 0.0f;
+        reinterpret_cast<float4*>(x)[q] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+        reinterpret_cast<float4*>(calcium)[q] = make_float4(v[0].ca, v[1].ca, v[2].ca, v[3].ca);
+        reinterpret_cast<float4*>(za)[q] = make_float4(v[0].za, v[1].za, v[2].za, v[3].za);
+        reinterpret_cast<float4*>(ze)[q] = make_float4(v[0].ze, v[1].ze, v[2].ze, v[3].ze);
+        reinterpret_cast<float4*>(zi)[q] = make_float4(v[0].zi, v[1].zi, v[2].zi, v[3].zi);
+        reinterpret_cast<uint32_t*>(refr)[q] = v[0].rf | (v[1].rf << 8) | (v[2].rf << 16) |
+                                               (v[3].rf << 24);
+        reinterpret_cast<uint32_t*>(spiked)[q] = sp;
+    }
+    for (int64_t t = 4 * n4 + tid; t < n; t += stride) {
+        const int32_t in = cur[t];
+        const int32_t j0 = off[t], nj = deg[t];
+        cur[t] = 0;
+        NrState v = {x[t], calcium[t], za[t], ze[t], zi[t], refr[t]};
+        const int s = nr_update(v, in, (uint32_t)t, seed, step, mp);
+        x[t] = v.x;
+        calcium[t] = v.ca;
+        za[t] = v.za;
+        ze[t] = v.ze;
+        zi[t] = v.zi;
+        refr[t] = (uint8_t)v.rf;
         spiked[t] = (uint8_t)s;
         if (s)
-            for (int32_t j = off[t], j1 = off[t] + deg[t]; j < j1; ++j)
-                atomicAdd(&next[targets[j]], 1);
+            for (int32_t j = j0; j < j0 + nj; ++j) atomicAdd(&next[targets[j]], 1);
     }
 }
 
@@ -320,7 +380,9 @@ void neuron_steps(msp_ctx& c, int64_t n, uint64_t first_step, int n_steps,
                   cudaStream_t s) {
     NvtxRange nv_("msp neuron_steps");
     if (n <= 0 || n_steps <= 0) return;
-    int32_t* inp = c.nr_inp.ensure<int32_t>((size_t)2 * n);
+    // two input-count buffers, the second at a 16-byte boundary
+    const int64_t n_pad = (n + 3) & ~(int64_t)3;
+    int32_t* inp = c.nr_inp.ensure<int32_t>((size_t)2 * n_pad);
     int32_t* deg = c.nr_bout.ensure<int32_t>((size_t)n);
     int32_t* off = c.nr_sout.ensure<int32_t>((size_t)n);
     int32_t* cursor = c.nr_xout.ensure<int32_t>((size_t)n);
@@ -331,7 +393,7 @@ void neuron_steps(msp_ctx& c, int64_t n, uint64_t first_step, int n_steps,
     // outgoing edges by presynaptic neuron
     MSP_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int32_t), s));
     MSP_CUDA(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), s));
-    MSP_CUDA(cudaMemsetAsync(inp, 0, (size_t)2 * n * sizeof(int32_t), s));
+    MSP_CUDA(cudaMemsetAsync(inp, 0, (size_t)2 * n_pad * sizeof(int32_t), s));
     k_out_degree<<<ge, 256, 0, s>>>(n_edges, cap, n, pre, post, deg);
     MSP_LAUNCH("out_degree");
     dev_set(cnt, n, s);
@@ -340,11 +402,18 @@ void neuron_steps(msp_ctx& c, int64_t n, uint64_t first_step, int n_steps,
     MSP_LAUNCH("out_fill");
     k_seed_input<<<gn, 256, 0, s>>>(n, spiked, off, deg, targets, inp);
     MSP_LAUNCH("seed_input");
+    // four neurons per thread where every array allows 16-byte (bytes: 4-byte) access
+    auto al = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; };
+    const int32_t* inp1 = inp + n_pad;
+    const int vec4 = al(inp, 16) && al(inp1, 16) && al(off, 16) && al(deg, 16) && al(x, 16) &&
+                     al(calcium, 16) && al(za, 16) && al(ze, 16) && al(zi, 16) && al(refr, 4) &&
+                     al(spiked, 4);
+    const int gv = grid_for(vec4 ? (n + 3) / 4 : n, 256, (int64_t)c.sm_count * 16);
     for (int k = 0; k < n_steps; ++k) {
-        int32_t* cur = inp + (size_t)(k & 1) * n;
-        int32_t* next = inp + (size_t)((k + 1) & 1) * n;
-        k_neuron_step<<<gn, 256, 0, s>>>(n, c.cfg.seed, first_step + (uint64_t)k, mp, cur, next,
-                                          off, deg, targets, x, refr, calcium, za, ze, zi,
+        int32_t* cur = inp + (size_t)(k & 1) * n_pad;
+        int32_t* next = inp + (size_t)((k + 1) & 1) * n_pad;
+        k_neuron_step<<<gv, 256, 0, s>>>(n, vec4, c.cfg.seed, first_step + (uint64_t)k, mp, cur,
+                                          next, off, deg, targets, x, refr, calcium, za, ze, zi,
                                           spiked);
         MSP_LAUNCH("neuron_step");
     }

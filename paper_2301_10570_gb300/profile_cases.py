@@ -3,9 +3,11 @@
     python -m paper_2301_10570_gb300.profile_cases near_field_131k
     python -m paper_2301_10570_gb300.profile_cases step_1m --steps 2
     python -m paper_2301_10570_gb300.profile_cases graph_1m --steps 4
+    python -m paper_2301_10570_gb300.profile_cases neuron_1m --steps 2
 
 Each case builds the library, runs a few plasticity steps (tree, attraction,
-selection; graph_1m: the whole step captured as one CUDA graph and replayed)
+selection; graph_1m: the whole step captured as one CUDA graph and replayed;
+neuron_1m: calls of 10 neuron steps of the model on the 1M network)
 and prints the library's statistics; it exits non-zero on any error.  The cases are sized for the profiling rules of the pool: the full
 capture case holds well under 1 GB on the device.
 """
@@ -31,7 +33,26 @@ def step_1m():
     return W.clustered_1m(**_plan())
 
 
-CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m, "graph_1m": step_1m}
+CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m, "graph_1m": step_1m,
+         "neuron_1m": step_1m}
+
+
+def _neuron_case(w, g, steps):
+    # neuron steps on the 1M network with 1.5 random synapses per neuron
+    import numpy as np
+    import torch
+
+    from . import msp
+    n = w.n
+    rng = np.random.default_rng(42)
+    m = 3 * n // 2
+    edges = msp.edge_list(m, pre=rng.integers(0, n, m), post=rng.integers(0, n, m),
+                          type_=np.zeros(m, np.uint8))
+    state = {k: torch.zeros(n, dtype=t, device="cuda") for k, t in msp.NEURON_STATE}
+    state["x"].fill_(0.065)
+    state["calcium"].uniform_(0.3, 0.8)
+    for k in range(steps):
+        g.neuron_steps(10 * k, 10, msp.neuron_params(), edges, state)
 
 
 def main(argv=None):
@@ -46,7 +67,9 @@ def main(argv=None):
     w = CASES[args.case]()
     g = msp.MSP(w.params)
     dev = msp.to_device(w)
-    if args.case.startswith("graph"):
+    if args.case == "neuron_1m":
+        _neuron_case(w, g, args.steps)
+    elif args.case.startswith("graph"):
         # one eager step sizes the graph; then the whole step as graph
         # replays (walk, build, attraction, selection, commit)
         pos, typ, va, ve, vi = dev

@@ -47,10 +47,23 @@ def _ctx(**kw):
     return msp.MSP(dict(w.params, **kw))
 
 
-@pytest.mark.parametrize("input_per_spike", [5e-4, 0.02])
-def test_neuron_steps_match_the_oracle_bit_for_bit(input_per_spike):
+def _to_dev_offset(st):
+    # views that start one element into a larger buffer (no 16-byte alignment)
+    out = {}
+    for k, v in st.items():
+        buf = torch.zeros(len(v) + 1, dtype=torch.from_numpy(v[:1]).dtype, device="cuda")
+        buf[1:] = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+        out[k] = buf[1:]
+    return out
+
+
+@pytest.mark.parametrize("input_per_spike,n,aligned", [(5e-4, 5000, True), (0.02, 5000, True),
+                                                       (0.02, 5003, True), (0.02, 5000, False)])
+def test_neuron_steps_match_the_oracle_bit_for_bit(input_per_spike, n, aligned):
+    # four neurons per thread with 16-byte accesses where the arrays allow it,
+    # one per thread for the remainder and for unaligned arrays
     rng = np.random.default_rng(31)
-    n, m = 5000, 25_000
+    m = 25_000
     pre = rng.integers(0, n, m).astype(np.int32)
     post = rng.integers(0, n, m).astype(np.int32)
     st = _random_state(rng, n)
@@ -58,7 +71,7 @@ def test_neuron_steps_match_the_oracle_bit_for_bit(input_per_spike):
     want = O.neuron_steps(17, 40, 300, O.neuron_params(**kw), pre, post, st)
     g = _ctx(seed=17)
     edges = msp.edge_list(m, pre=pre, post=post, type_=np.zeros(m, np.uint8))
-    dev = _to_dev(st)
+    dev = _to_dev(st) if aligned else _to_dev_offset(st)
     g.neuron_steps(40, 300, msp.neuron_params(**kw), edges, dev)
     torch.cuda.synchronize()
     g.close()
