@@ -16,8 +16,9 @@
  *   Section 4     requests are resolved at the dendrite side
  *   (derivatives) du/dsigma and the transposed transform sum_t g_t K(t,s) of
  *                 Eq. 8, the adjoint of the attraction
- * and the readings of the paper listed in the design notes (kernel width,
- * sign of Eq. 6, truncation 0 <= alpha_d < p, centroids as expansion centres,
+ * and these readings of the paper (kernel width,
+ * sign of Eq. 6, truncation 0 <= alpha_d < p, centroids as expansion centres
+ * (or, with centre_mode 1, the boxes' geometric centres),
  * the Hermite-to-Taylor translation derived from Eq. 6 and Eq. 7, the
  * separation/cutoff rule, the leaf rule of Algorithm 1, resolution order).
  *
@@ -229,6 +230,7 @@ typedef struct {
     uint8_t nchild;
     int64_t sa[2], sw[2];     /* vacant axons (E,I), vacant dendrites (E,I) */
     double ca[3], cd[3];      /* axon / dendrite centroids                 */
+    double gc[3];             /* geometric centre                          */
 } node_t;
 
 typedef struct {
@@ -430,6 +432,7 @@ int orc_build_tree(orc_ctx *c, int64_t n, const float *x, const float *y, const 
             double gc = cfg->origin[d] + (prefix_coord(nd->prefix, nd->level, d) + 0.5) * bs;
             nd->ca[d] = swa > 0 ? pa[d] / swa : gc;
             nd->cd[d] = swd > 0 ? pd[d] / swd : gc;
+            nd->gc[d] = gc;
         }
         if (nd->child_first < 0)
             for (int64_t s = nd->first; s < (int64_t)nd->first + nd->count; ++s)
@@ -490,6 +493,19 @@ static void push_pair(orc_ctx *c, int32_t X, int32_t Y)
     memset(&pr, 0, sizeof(pr));
     pr.X = X; pr.Y = Y; pr.child_first = -1;
     c->pairs[c->n_pairs++] = pr;
+}
+
+/* expansion centres of a box: the axon / dendrite centroids, or (centre_mode
+ * 1) the geometric centre for both, so that a translation depends only on
+ * the boxes' levels and integer offset */
+static const double *centre_a(const orc_ctx *c, const node_t *nd)
+{
+    return c->cfg.centre_mode ? nd->gc : nd->ca;
+}
+
+static const double *centre_d(const orc_ctx *c, const node_t *nd)
+{
+    return c->cfg.centre_mode ? nd->gc : nd->cd;
 }
 
 static int64_t expansion_off(const orc_ctx *c, int64_t node, int ch)
@@ -553,8 +569,8 @@ int orc_attraction(orc_ctx *c, double *u)
         for (int64_t s = nd->first; s < (int64_t)nd->first + nd->count; ++s) {
             double yd[3], xa[3];
             for (int d = 0; d < 3; ++d) {
-                yd[d] = (c->pos[3 * s + d] - nd->cd[d]) / sigma;
-                xa[d] = (c->pos[3 * s + d] - nd->ca[d]) / sigma;
+                yd[d] = (c->pos[3 * s + d] - centre_d(c, nd)[d]) / sigma;
+                xa[d] = (c->pos[3 * s + d] - centre_a(c, nd)[d]) / sigma;
             }
             int t = c->type[s] ? 1 : 0;
             for (int a0 = 0; a0 < p; ++a0)
@@ -582,7 +598,8 @@ int orc_attraction(orc_ctx *c, double *u)
         c->stats[1]++;
         const node_t *X = &c->nodes[pr->X], *Y = &c->nodes[pr->Y];
         for (int ch = 0; ch < 2; ++ch) {
-            orc_m2l(p, sigma, &c->A[expansion_off(c, pr->Y, ch)], X->ca, Y->cd, Bp);
+            orc_m2l(p, sigma, &c->A[expansion_off(c, pr->Y, ch)], centre_a(c, X),
+                    centre_d(c, Y), Bp);
             double w = 0.0;
             for (int b = 0; b < p3; ++b) {
                 c->B[expansion_off(c, pr->X, ch) + b] += Bp[b];
@@ -601,8 +618,8 @@ int orc_attraction(orc_ctx *c, double *u)
         int64_t nd = c->leaf_of[s];
         while (nd >= 0) {
             if (c->nodes[nd].level >= c->l_far)
-                uu[s] += orc_l2p(p, sigma, &c->B[expansion_off(c, nd, t)], c->nodes[nd].ca,
-                                 &c->pos[3 * s]);
+                uu[s] += orc_l2p(p, sigma, &c->B[expansion_off(c, nd, t)],
+                                 centre_a(c, &c->nodes[nd]), &c->pos[3 * s]);
             nd = c->nodes[nd].parent;
         }
     }
@@ -663,8 +680,8 @@ static double far_w(const orc_ctx *c, int32_t X, int32_t Y, int ch)
 {
     int p = c->cfg.p, p3 = p * p * p;
     double Bp[MAXP * MAXP * MAXP];
-    orc_m2l(p, c->cfg.sigma, &c->A[expansion_off(c, Y, ch)], c->nodes[X].ca,
-            c->nodes[Y].cd, Bp);
+    orc_m2l(p, c->cfg.sigma, &c->A[expansion_off(c, Y, ch)], centre_a(c, &c->nodes[X]),
+            centre_d(c, &c->nodes[Y]), Bp);
     double w = 0.0;
     for (int b = 0; b < p3; ++b) w += Bp[b] * c->M[expansion_off(c, X, ch) + b];
     return w;

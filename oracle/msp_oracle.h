@@ -46,6 +46,9 @@ typedef struct {
     long long m2l_min_pairs;
     double   boundary_tol;   /* draws within this relative distance of a CDF
                                 boundary are flagged (not an algorithm input) */
+    int      centre_mode;    /* expansion centres: 0 the weighted centroids
+                                (Section 3.2, Section 4), 1 the boxes'
+                                geometric centres */
 } orc_config;
 
 typedef struct orc_ctx orc_ctx;

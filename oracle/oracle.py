@@ -49,7 +49,8 @@ class _Cfg(C.Structure):
     _fields_ = [("sigma", C.c_double), ("p", C.c_int), ("leaf_capacity", C.c_int),
                 ("max_depth", C.c_int), ("origin", C.c_float * 3), ("side", C.c_float),
                 ("seed", C.c_uint64), ("rho_max", C.c_double), ("cutoff", C.c_double),
-                ("m2l_min_pairs", C.c_longlong), ("boundary_tol", C.c_double)]
+                ("m2l_min_pairs", C.c_longlong), ("boundary_tol", C.c_double),
+                ("centre_mode", C.c_int)]
 
 
 def _p(a):
@@ -123,6 +124,7 @@ def _cfg(params: dict) -> _Cfg:
     c.cutoff = float(params["cutoff"])
     c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
     c.boundary_tol = float(params.get("boundary_tol", 1e-5))
+    c.centre_mode = int(params.get("centre_mode", 0))
     return c
 
 

@@ -296,10 +296,13 @@ def test_pruned_and_far_pairs_respect_geometry(oracle_mod):
     assert n_far > 0
 
 
+@pytest.mark.parametrize("centre_mode", [0, 1])
 @pytest.mark.parametrize("p", [4, 6])
-def test_fmm_matches_brute_force_tiny(oracle_mod, p):
-    """N <= 64 with far pairs forced: FMM within its truncation, brute force exact."""
-    w = W.uniform_cube(64, 1500.0, seed=21, leaf_capacity=2, rho_max=0.3, cutoff=6.0, p=p)
+def test_fmm_matches_brute_force_tiny(oracle_mod, p, centre_mode):
+    """N <= 64 with far pairs forced: FMM within its truncation, brute force
+    exact; expansions about the centroids or about the geometric centres."""
+    w = W.uniform_cube(64, 1500.0, seed=21, leaf_capacity=2, rho_max=0.3, cutoff=6.0, p=p,
+                       centre_mode=centre_mode)
     o = oracle_mod.Oracle(w.params)
     o.build_tree(*w.arrays())
     u = o.attraction()
@@ -317,14 +320,15 @@ def test_fmm_matches_brute_force_tiny(oracle_mod, p):
     assert np.allclose(oracle_mod.direct(*w.arrays(), w.params["sigma"]), ref, rtol=1e-12, atol=1e-300)
 
 
-def test_paper_cutoff_meets_paper_accuracy(oracle_mod):
+@pytest.mark.parametrize("centre_mode", [0, 1])
+def test_paper_cutoff_meets_paper_accuracy(oracle_mod, centre_mode):
     """With the paper's cut-off alpha = beta = (3,3,3) (p = 4) the expansions
     stay within the paper's largest outlier, 0.125 %, of direct evaluation
     when boxes carrying an expansion are at most 0.2 sigma across half."""
     k = _paper()
     p = k["cutoff_multi_index"]["value"][0] + 1
     w = W.clustered_small(1, 2048, seed=2, leaf_capacity=4, rho_max=0.2, p=p,
-                          sigma=k["sigma_um"]["value"])
+                          sigma=k["sigma_um"]["value"], centre_mode=centre_mode)
     o = oracle_mod.Oracle(w.params)
     o.build_tree(*w.arrays())
     u = o.attraction()
@@ -334,9 +338,11 @@ def test_paper_cutoff_meets_paper_accuracy(oracle_mod):
     assert np.max(np.abs(u[m] - ref[m]) / ref[m]) < k["max_expansion_deviation"]["value"]
 
 
-def test_pair_table_total_equals_weighted_attraction(oracle_mod):
+@pytest.mark.parametrize("centre_mode", [0, 1])
+def test_pair_table_total_equals_weighted_attraction(oracle_mod, centre_mode):
     """W(root, root) of each channel = sum over that channel's targets of a_t u(t)."""
-    w = W.clustered_small(1, 1500, seed=12, leaf_capacity=4, rho_max=0.3, p=4)
+    w = W.clustered_small(1, 1500, seed=12, leaf_capacity=4, rho_max=0.3, p=4,
+                          centre_mode=centre_mode)
     o = oracle_mod.Oracle(w.params)
     o.build_tree(*w.arrays())
     u = o.attraction()
