@@ -75,7 +75,12 @@ typedef enum {
  *                  single precision relative resolution of any sum)
  *   m2l_min_pairs  a well-separated pair is translated only if
  *                  count(X)*count(Y) >= m2l_min_pairs; otherwise it is
- *                  refined down to the near field                          */
+ *                  refined down to the near field
+ *   centre_mode    expansion centres: 0 the weighted centroids (Section 3.2,
+ *                  Section 4); 1 the boxes' geometric centres, for which a
+ *                  translation depends only on the boxes' offset, so the
+ *                  translations of all pairs with one offset run as one
+ *                  matrix product (p <= 5)                                 */
 typedef struct {
     double    sigma;
     int       p;
@@ -87,6 +92,7 @@ typedef struct {
     double    rho_max;
     double    cutoff;
     long long m2l_min_pairs;
+    int       centre_mode;
 } msp_config;
 
 /* Sizes and operation counts of the last build / attraction / selection. */

@@ -114,7 +114,7 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
     if (!(cfg->sigma > 0.0) || cfg->p < 1 || cfg->p > msp::kMaxP || cfg->leaf_capacity < 1 ||
         cfg->max_depth < 0 || cfg->max_depth > msp::kMortonBits || !(cfg->side > 0.0f) ||
         !(cfg->rho_max >= 0.0) || !(cfg->cutoff > 0.0) || !(cfg->cutoff <= 5.0) ||
-        cfg->m2l_min_pairs < 0 ||
+        cfg->m2l_min_pairs < 0 || (cfg->centre_mode != 0 && cfg->centre_mode != 1) ||
         !std::isfinite(cfg->origin[0]) || !std::isfinite(cfg->origin[1]) ||
         !std::isfinite(cfg->origin[2]) || !std::isfinite(cfg->side))
         return fail(MSP_ERR_INVALID_ARG, "configuration value out of range");
@@ -156,7 +156,9 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nr_inp, &c->nr_bout, &c->nr_bin, &c->nr_xout, &c->nr_xin,
                          &c->nr_sout, &c->nr_sin, &c->nr_cnt, &c->nr_key0, &c->nr_key1,
                          &c->nr_val0, &c->nr_val1, &c->nr_del, &c->nr_keep, &c->nr_pos,
-                         &c->nr_pre2, &c->nr_post2, &c->nr_typ2,
+                         &c->nr_pre2, &c->nr_post2, &c->nr_typ2, &c->nd_gc, &c->gm_key0,
+                         &c->gm_key1, &c->gm_q, &c->gm_q1, &c->gm_flag, &c->gm_gid,
+                         &c->gm_gstart, &c->gm_ntile, &c->gm_toff, &c->gm_tiles, &c->gm_cnt,
                          &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,

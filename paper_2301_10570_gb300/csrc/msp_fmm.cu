@@ -329,7 +329,8 @@ __device__ float warp_m2l(int p, const float* __restrict__ Ag, const float* __re
 constexpr int kM2LWarps = 4;
 
 __global__ void __launch_bounds__(kM2LWarps * 32)
-k_m2l(const int32_t* __restrict__ far_q, const int64_t* __restrict__ nfar_dev, int64_t exp_first,
+k_m2l(const int32_t* __restrict__ far_q, const int64_t* __restrict__ nfar_dev,
+      const int64_t* __restrict__ first_dev, int64_t exp_first,
       int p, float inv_sigma, const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
       const float4* __restrict__ ca, const float4* __restrict__ cd, const float* __restrict__ A,
       const float* __restrict__ M, float* __restrict__ B, double2* __restrict__ pw) {
@@ -338,7 +339,8 @@ k_m2l(const int32_t* __restrict__ far_q, const int64_t* __restrict__ nfar_dev, i
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p3 = p * p * p;
     const int64_t nfar = *nfar_dev;
-    for (int64_t k = (int64_t)blockIdx.x * kM2LWarps + w; k < nfar;
+    const int64_t k0 = first_dev ? *first_dev : 0;   // pairs [k0, nfar)
+    for (int64_t k = k0 + (int64_t)blockIdx.x * kM2LWarps + w; k < nfar;
          k += (int64_t)gridDim.x * kM2LWarps) {
         int32_t q = far_q[k];
         int32_t X = pX[q], Y = pY[q];
@@ -613,19 +615,35 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     float* eA = c.expA.ensure<float>(ecount);
     float* eM = c.expM.ensure<float>(ecount);
     float* eB = c.expB.ensure<float>(ecount);
+    // expansion centres: the centroids, or the geometric centres (centre_mode 1)
+    const bool geo = c.cfg.centre_mode == 1;
+    const float4* eca = c.nd_ca.get<float4>();
+    const float4* ecd = c.nd_cd.get<float4>();
+    if (geo && c.exp_nodes > 0) {
+        geo_centres(c, s);
+        eca = ecd = c.nd_gc.get<float4>();
+    }
     if (c.exp_nodes > 0) {
         MSP_CUDA(cudaMemsetAsync(eB, 0, ecount * sizeof(float), s));
         k_p2m<<<(unsigned)c.exp_nodes, kP2MThreads, 0, s>>>(
             c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.nd_first.get<int32_t>(),
-            c.nd_count.get<int32_t>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM);
+            c.nd_count.get<int32_t>(), eca, ecd, eA, eM);
         MSP_LAUNCH("p2m");
     }
-    // a7: translations, accumulating B(X) and W(X,Y)
+    // a7: translations, accumulating B(X) and W(X,Y); with geometric centres
+    // the pairs that share an offset share one operator (matrix products),
+    // the rest one pair at a time
     if (c.exp_nodes > 0) {
+        const int32_t* mq = far_q;
+        const int64_t* first = nullptr;
+        if (geo && m2l_gemm_fits(p)) {
+            int64_t* fb = nullptr;
+            mq = m2l_gemm(c, far_q, &dc->n_far, cap, eA, eM, eB, c.pr_w.get<double2>(), &fb, s);
+            first = fb;
+        }
         k_m2l<<<(int)c.sm_count * 8, kM2LWarps * 32, 0, s>>>(
-            far_q, &dc->n_far, c.exp_first, p, inv_sigma, c.pr_X.get<int32_t>(),
-            c.pr_Y.get<int32_t>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), eA, eM, eB,
-            c.pr_w.get<double2>());
+            mq, &dc->n_far, first, c.exp_first, p, inv_sigma, c.pr_X.get<int32_t>(),
+            c.pr_Y.get<int32_t>(), eca, ecd, eA, eM, eB, c.pr_w.get<double2>());
         MSP_LAUNCH("m2l");
     }
     // a8: Taylor evaluation initialises u in sorted order; a9 adds the near field
@@ -634,7 +652,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     if (n > 0) {
         k_l2p<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(
             n, c.exp_first, p, inv_sigma, c.pts.get<float4>(), c.leaf_of.get<int32_t>(),
-            c.nd_parent.get<int32_t>(), c.nd_ca.get<float4>(), eB, us);
+            c.nd_parent.get<int32_t>(), eca, eB, us);
         MSP_LAUNCH("l2p");
         MSP_CUDA(cudaEventRecordWithFlags(c.ev_nf0, s, ev_flags));
         launch_near_field(c, seg_first, &dc->nseg, c.n_nodes, pv0, &dc->n_p2p, cap, us, work, s);

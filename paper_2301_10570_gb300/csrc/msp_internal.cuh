@@ -182,6 +182,10 @@ struct msp_ctx {
     msp::DBuf nr_inp, nr_bout, nr_bin, nr_xout, nr_xin, nr_sout, nr_sin, nr_cnt;
     msp::DBuf nr_key0, nr_key1, nr_val0, nr_val1, nr_del, nr_keep, nr_pos;
     msp::DBuf nr_pre2, nr_post2, nr_typ2;
+    // geometric expansion centres and the grouped translations (msp_m2l_gemm.cu)
+    int gm_smem_set = 0;   // dynamic shared memory opted in for the grouped translations
+    msp::DBuf nd_gc, gm_key0, gm_key1, gm_q, gm_q1, gm_flag, gm_gid, gm_gstart, gm_ntile,
+        gm_toff, gm_tiles, gm_cnt;
     // derivatives (msp_grad.cu)
     msp::DBuf gr_w, gr_tmp, gr_key0, gr_key1, gr_val0, gr_val1, gr_flag, gr_off, gr_seg;
     // expansions
@@ -247,6 +251,12 @@ void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
 // (msp_nearfield.cu); accumulates into u_sorted and the pair table.
 // Segment and list counts live in device memory (*nseg_dev <= nseg_cap,
 // *nlist_dev <= nlist_cap); no host synchronisation.
+// expansions about the geometric centres (msp_m2l_gemm.cu)
+void geo_centres(msp_ctx& c, cudaStream_t s);
+bool m2l_gemm_fits(int p);
+const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, int64_t cap,
+                        const float* A, const float* M, float* B, double2* pw,
+                        int64_t** first_fallback, cudaStream_t s);
 void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
                        int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
                        int64_t nlist_cap, float* u_sorted, unsigned long long* work,

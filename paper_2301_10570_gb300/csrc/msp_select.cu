@@ -635,8 +635,9 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     tr.child_first = c.nd_child_first.get<int32_t>();
     tr.nchild = c.nd_nchild.get<uint8_t>();
     tr.sums = c.nd_sums.get<int4>();
-    tr.ca = c.nd_ca.get<float4>();
-    tr.cd = c.nd_cd.get<float4>();
+    // expansion centres (the geometric ones with centre_mode 1)
+    tr.ca = c.cfg.centre_mode == 1 ? c.nd_gc.get<float4>() : c.nd_ca.get<float4>();
+    tr.cd = c.cfg.centre_mode == 1 ? c.nd_gc.get<float4>() : c.nd_cd.get<float4>();
     Exps ex;
     ex.A = c.expA.get<float>();
     ex.M = c.expM.get<float>();

@@ -89,7 +89,7 @@ class Config(C.Structure):
     _fields_ = [("sigma", C.c_double), ("p", C.c_int), ("leaf_capacity", C.c_int),
                 ("max_depth", C.c_int), ("origin", C.c_float * 3), ("side", C.c_float),
                 ("seed", C.c_uint64), ("rho_max", C.c_double), ("cutoff", C.c_double),
-                ("m2l_min_pairs", C.c_longlong)]
+                ("m2l_min_pairs", C.c_longlong), ("centre_mode", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -193,6 +193,7 @@ def make_config(params: dict) -> Config:
     c.rho_max = float(params["rho_max"])
     c.cutoff = float(params["cutoff"])
     c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
+    c.centre_mode = int(params.get("centre_mode", 0))
     return c
 
 

@@ -46,6 +46,14 @@ CASES = {
     "single_leaf": lambda: W.uniform_cube(40, 3000.0, seed=31, leaf_capacity=64),
     "one_neuron": lambda: W.uniform_cube(1, 1000.0, seed=1),
     "no_vacancies": lambda: _zero_axons(),
+    # expansions about the geometric centres: translations grouped by offset
+    # as matrix products (p <= 5), one pair at a time above
+    "geo_far_p4": lambda: W.clustered_small(1, 4096, leaf_capacity=8, rho_max=0.3, p=4,
+                                            centre_mode=1),
+    "geo_far_p5": lambda: W.clustered_small(2, 2048, seed=17, leaf_capacity=8, rho_max=0.3,
+                                            p=5, centre_mode=1),
+    "geo_far_p6": lambda: W.clustered_small(1, 1536, seed=9, leaf_capacity=8, rho_max=0.3,
+                                            p=6, centre_mode=1),
 }
 
 
@@ -170,7 +178,8 @@ def test_direct_path_matches_oracle_brute_force(name):
     assert np.max(np.abs(g["direct"][m] - ref[m]) / ref[m]) < 1e-5
 
 
-@pytest.mark.parametrize("name", ["clustered_far_p4", "clustered_far_p6", "ragged_37"])
+@pytest.mark.parametrize("name", ["clustered_far_p4", "clustered_far_p6", "ragged_37",
+                                  "geo_far_p4", "geo_far_p5", "geo_far_p6"])
 def test_expansions_match_oracle(name):
     w, g, o = run(name)
     A, M, B, first = g["exps"]
