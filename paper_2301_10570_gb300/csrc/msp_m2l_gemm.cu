@@ -144,15 +144,21 @@ struct GemmArgs {
     float half_box_over_sigma_l0;   // side / 2 / sigma (half a level-0 box)
 };
 
-// dynamic shared memory: T[p3][p3], As[p3][64], Cs[p3][64], H[3][16], pair ids
+// Dynamic shared memory: the operator transposed, Tt[alpha][beta] with beta
+// padded to PB = 16 RM rows (zero rows past p^3), the columns As[alpha][64],
+// the product Cs[beta][64], the Hermite rows H[3][16], pair ids and W.  The
+// product runs on a 16 x 16 grid of threads, each owning RM rows x 4 columns
+// in registers (two 16-byte shared-memory loads per 4 RM multiply-adds).
+template <int RM>
 __global__ void __launch_bounds__(kGemmThreads) k_m2l_gemm(GemmArgs a) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
+    constexpr int PB = 16 * RM;
     const int p = a.p, p2 = p * p, p3 = p2 * p;
     const int ncol = 2 * kGemmTile;
-    float* T = sm;
-    float* As = T + p3 * p3;
-    float* Cs = As + p3 * ncol;
-    float* H = Cs + p3 * ncol;                       // 3 x 16
+    float* T = sm;                                   // Tt: p3 x PB
+    float* As = T + p3 * PB;
+    float* Cs = As + p3 * ncol;                      // PB x ncol
+    float* H = Cs + PB * ncol;                       // 3 x 16
     int32_t* sq = reinterpret_cast<int32_t*>(H + 48);  // kGemmTile pair ids
     float* sw = reinterpret_cast<float*>(sq + kGemmTile);   // ncol W values
     const int64_t nt = *a.ntiles;
@@ -172,14 +178,18 @@ __global__ void __launch_bounds__(kGemmThreads) k_m2l_gemm(GemmArgs a) {
         }
         if (threadIdx.x < npair) sq[threadIdx.x] = a.q[tg.y + threadIdx.x];
         __syncthreads();
-        // operator T
-        for (int i = threadIdx.x; i < p3 * p3; i += blockDim.x) {
-            const int b = i / p3, al = i - b * p3;
-            const int b0 = b / p2, b1 = (b / p) % p, b2 = b % p;
-            const int a0 = al / p2, a1 = (al / p) % p, a2 = al % p;
-            float sc = c_inv_fact_g[b0] * c_inv_fact_g[b1] * c_inv_fact_g[b2];
-            if ((b0 + b1 + b2) & 1) sc = -sc;
-            T[i] = sc * H[a0 + b0] * H[16 + a1 + b1] * H[32 + a2 + b2];
+        // operator, transposed: T[al * PB + b]
+        for (int i = threadIdx.x; i < p3 * PB; i += blockDim.x) {
+            const int al = i / PB, b = i - al * PB;
+            float v = 0.f;
+            if (b < p3) {
+                const int b0 = b / p2, b1 = (b / p) % p, b2 = b % p;
+                const int a0 = al / p2, a1 = (al / p) % p, a2 = al % p;
+                float sc = c_inv_fact_g[b0] * c_inv_fact_g[b1] * c_inv_fact_g[b2];
+                if ((b0 + b1 + b2) & 1) sc = -sc;
+                v = sc * H[a0 + b0] * H[16 + a1 + b1] * H[32 + a2 + b2];
+            }
+            T[i] = v;
         }
         // coefficient columns: column 2 i + ch = A(Y_i, ch)
         for (int i = threadIdx.x; i < p3 * ncol; i += blockDim.x) {
@@ -193,13 +203,34 @@ __global__ void __launch_bounds__(kGemmThreads) k_m2l_gemm(GemmArgs a) {
             As[i] = v;
         }
         __syncthreads();
-        // C = T As
-        for (int i = threadIdx.x; i < p3 * ncol; i += blockDim.x) {
-            const int b = i / ncol, col = i - b * ncol;
-            const float* tr = T + b * p3;
-            float acc = 0.f;
-            for (int al = 0; al < p3; ++al) acc = fmaf(tr[al], As[al * ncol + col], acc);
-            Cs[i] = acc;
+        // C = T As, RM x 4 outputs per thread
+        {
+            const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+            const int r0 = ty * RM, c0 = tx * 4;
+            float acc[RM][4];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int al = 0; al < p3; ++al) {
+                const float4 av = *reinterpret_cast<const float4*>(As + al * ncol + c0);
+#pragma unroll
+                for (int i4 = 0; i4 < RM / 4; ++i4) {
+                    const float4 tv = *reinterpret_cast<const float4*>(T + al * PB + r0 + 4 * i4);
+                    const float t[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[4 * i4 + i][0] = fmaf(t[i], av.x, acc[4 * i4 + i][0]);
+                        acc[4 * i4 + i][1] = fmaf(t[i], av.y, acc[4 * i4 + i][1]);
+                        acc[4 * i4 + i][2] = fmaf(t[i], av.z, acc[4 * i4 + i][2]);
+                        acc[4 * i4 + i][3] = fmaf(t[i], av.w, acc[4 * i4 + i][3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+                *reinterpret_cast<float4*>(Cs + (r0 + i) * ncol + c0) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         }
         __syncthreads();
         // W per column, B(X) += column
@@ -277,10 +308,14 @@ const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, i
     k_tile_list<<<ge, 256, 0, s>>>(gstart, ntile, toff, cnt, tiles);
     MSP_LAUNCH("tile_list");
     const int p = c.cfg.p, p3 = p * p * p;
-    const size_t smem = sizeof(float) * ((size_t)p3 * p3 + 2 * (size_t)p3 * 2 * kGemmTile + 48) +
-                        sizeof(int32_t) * kGemmTile + sizeof(float) * 2 * kGemmTile;
+    const int RM = p3 <= 64 ? 4 : 8;
+    const size_t PB = 16 * (size_t)RM, ncol = 2 * kGemmTile;
+    const size_t smem = sizeof(float) * ((size_t)p3 * PB + (size_t)p3 * ncol + PB * ncol + 48) +
+                        sizeof(int32_t) * kGemmTile + sizeof(float) * ncol;
     if (smem > 48 * 1024 && (int)smem > c.gm_smem_set) {
-        MSP_CUDA(cudaFuncSetAttribute(k_m2l_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MSP_CUDA(cudaFuncSetAttribute(k_m2l_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        MSP_CUDA(cudaFuncSetAttribute(k_m2l_gemm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         c.gm_smem_set = (int)smem;
     }
@@ -301,7 +336,9 @@ const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, i
     a.exp_first = c.exp_first;
     a.p = p;
     a.half_box_over_sigma_l0 = (float)(0.5 * (double)c.cfg.side / c.cfg.sigma);
-    k_m2l_gemm<<<(int)c.sm_count * 2, kGemmThreads, smem, s>>>(a);
+    const int grid = (int)c.sm_count * (smem <= 64 * 1024 ? 3 : 1);
+    if (RM == 4) k_m2l_gemm<4><<<grid, kGemmThreads, smem, s>>>(a);
+    else         k_m2l_gemm<8><<<grid, kGemmThreads, smem, s>>>(a);
     MSP_LAUNCH("m2l_gemm");
     *first_fallback = cnt + 2;
     return v0;
