@@ -4,6 +4,7 @@
     python -m paper_2301_10570_gb300.profile_cases step_1m --steps 2
     python -m paper_2301_10570_gb300.profile_cases graph_1m --steps 4
     python -m paper_2301_10570_gb300.profile_cases neuron_1m --steps 2
+    python -m paper_2301_10570_gb300.profile_cases translations_256k --p 4 --centre-mode 1
 
 Each case builds the library, runs a few plasticity steps (tree, attraction,
 selection; graph_1m: the whole step captured as one CUDA graph and replayed;
@@ -33,8 +34,14 @@ def step_1m():
     return W.clustered_1m(**_plan())
 
 
+def translations_256k(p=4, centre_mode=0):
+    from . import workloads as W
+    return W.uniform_256k(leaf_capacity=8, rho_max=0.5, cutoff=4.0, m2l_min_pairs=0, p=p,
+                          centre_mode=centre_mode)
+
+
 CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m, "graph_1m": step_1m,
-         "neuron_1m": step_1m}
+         "neuron_1m": step_1m, "translations_256k": translations_256k}
 
 
 def _neuron_case(w, g, steps):
@@ -59,16 +66,35 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=sorted(CASES))
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--p", type=int, default=4, help="translations_256k: expansion order")
+    ap.add_argument("--centre-mode", type=int, default=0,
+                    help="translations_256k: 0 centroids, 1 geometric centres")
     args = ap.parse_args(argv)
     import torch
 
     from . import build, msp
     build.build()
-    w = CASES[args.case]()
+    if args.case == "translations_256k":
+        w = translations_256k(args.p, args.centre_mode)
+    else:
+        w = CASES[args.case]()
     g = msp.MSP(w.params)
     dev = msp.to_device(w)
     if args.case == "neuron_1m":
         _neuron_case(w, g, args.steps)
+    elif args.case == "translations_256k":
+        # attraction only, timed with CUDA events (median of the steps after the first)
+        import statistics
+        g.build_tree(*dev)
+        ts = []
+        for _ in range(max(args.steps, 2)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.attraction()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        print(f"attraction_ms {statistics.median(ts[1:]):.3f}")
     elif args.case.startswith("graph"):
         # one eager step sizes the graph; then the whole step as graph
         # replays (walk, build, attraction, selection, commit)
