@@ -132,6 +132,10 @@ struct DevCounts {
     int64_t interactions_run;                // near-field interactions over the replays
 };
 
+// DevCounts::overflow bit set when a bounded wait of the single-pass scan
+// gave up (its result is then wrong; the host reports MSP_ERR_TIMEOUT)
+constexpr int64_t kScanTimeoutBit = 1ll << 40;
+
 // the vacancy walk keeps every vacant count in [0, kMaxVacancy]
 constexpr int kMaxVacancy = 5;
 

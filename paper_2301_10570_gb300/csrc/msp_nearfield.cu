@@ -7,15 +7,14 @@
 // segment's work), so the last wave of blocks is short.  The block collects
 // the targets of X with vacant axons, up to 125 at a time, and evaluates them
 // in one pass; the warps take the partner pairs round-robin.  A lane holds R
-// targets of one channel, R = 2, 3 or 4, the smallest whose 32 R slots hold
-// the round (excitatory targets first, their count padded with empty slots to
-// a multiple of R when inhibitory ones follow).  Each warp stages the sources
-// of its current pair in its own shared memory, in pairs of sources, and
-// every lane evaluates them against its targets, so one staged source pair
-// (two shared-memory loads) serves 2R evaluations; passes of up to 32
-// targets pad their target pairs to P = 2^k and 32/P lanes share a pair,
-// walking interleaved slices of the sources (small leaves still fill the
-// warp).
+// targets of one channel, R = 3 or 4 chosen per round (below; excitatory
+// targets first, their count padded with empty slots to a multiple of R when
+// inhibitory ones follow).  Each warp stages the sources of its current pair
+// in its own shared memory, in pairs of sources, and every lane evaluates them
+// against its targets, so one staged source pair (two shared-memory loads)
+// serves 2R evaluations; when the round's target groups fit in fewer lanes
+// they are padded to P = 2^k lanes and 32/P lanes share a group, walking
+// interleaved slices of the sources (small leaves still fill the warp).
 // The per-target sums of the 4 warps are added in a fixed order, so u is
 // reproducible run to run.  Per pair, the warp reduces the box-pair
 // attraction W(X,Y) = sum_t a_t sum_s w_s K(t,s) of each channel in single
@@ -48,7 +47,7 @@ __shared__ int32_t* s_wii;
 
 constexpr int kNFWarps = 4;
 constexpr int kNFStage = 128;
-constexpr int kNFMaxT = 32 * 4;    // targets per pass (2, 3 or 4 per lane)
+constexpr int kNFMaxT = 32 * 4;    // targets per pass (3 or 4 per lane)
 constexpr int kNFList = 128;       // target slots per round (one pass)
 constexpr float kNFFastT2 = 20.f;  // largest |t^|^2 of the expanded form
 

@@ -27,8 +27,6 @@
 
 namespace msp {
 
-void set_last_error(const char* msg);
-
 namespace {
 
 constexpr uint32_t kTagSpike = 5u, kTagDelAxon = 6u, kTagDelDend = 7u;

@@ -221,86 +221,122 @@ void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp, i
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void k_sd_reduce(const int32_t* __restrict__ in, const int64_t* __restrict__ n_dev,
-                            long long* __restrict__ bsum) {
+// Single-pass exclusive scan of in[0, *n_dev) with a decoupled look-back.
+// Blocks take tiles in order from a counter (status[0]), so every tile's
+// predecessors have started; a tile publishes its sum (flag 1) before it
+// looks back, then its inclusive prefix (flag 2), in status[1 + tile] as one
+// 64-bit word (flag in the top two bits).  The look-back reads 32
+// predecessors per step with a warp, waiting on each for at most kSpinLimit
+// polls; a wait that gives up sets bit kScanTimeoutBit in *overflow and
+// counts the tile as 0 (the result is then wrong and the host reports it).
+// The last tile writes the total (+ *base) to *dst; with a clamp, an end
+// beyond clamp_cap is recorded (overflow_bit, need = the largest end asked
+// for) and *dst gets *base instead: the next range is empty.
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_1p(const int32_t* in, int32_t* out, const int64_t* __restrict__ n_dev,
+          unsigned long long* status, int64_t* __restrict__ dst,
+          const int64_t* __restrict__ base, int64_t clamp_cap, int64_t* __restrict__ overflow,
+          int64_t* __restrict__ need, int64_t overflow_bit, int64_t timeout_bit) {
+    __shared__ int32_t s_v[kScanTile + kScanTile / 32];
+    __shared__ long long s_tot, s_excl;
+    __shared__ int64_t s_tile;
     const int64_t n = *n_dev;
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    __shared__ long long tot;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        long long s = 0;
+    volatile unsigned long long* st = status;
+    if (ntiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && dst) *dst = base ? *base : 0;
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&status[0], 1ull);
+        __syncthreads();
+        const int64_t t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const int64_t t0 = t * kScanTile;
+        // coalesced load into shared memory (one padding word per 32)
         for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
-            int64_t i = t * kScanTile + j;
-            if (i < n) s += in[i];
+            const int64_t i = t0 + j;
+            s_v[j + (j >> 5)] = i < n ? in[i] : 0;
         }
-        long long d = block_excl_scan(s, &tot);
-        (void)d;
-        if (threadIdx.x == 0) bsum[t] = tot;
         __syncthreads();
-    }
-}
-
-// one block: exclusive scan of the tile sums in chunks, total (+ *base) to
-// *dst.  With a clamp, an end beyond clamp_cap is recorded (overflow bit 0,
-// need = the largest end asked for) and *dst gets *base instead: the next
-// range is empty.
-__global__ void k_sd_spine(long long* __restrict__ bsum, const int64_t* __restrict__ n_dev,
-                           int64_t* __restrict__ dst, const int64_t* __restrict__ base,
-                           int64_t clamp_cap, int64_t* __restrict__ overflow,
-                           int64_t* __restrict__ need, int64_t overflow_bit) {
-    const int64_t n = *n_dev;
-    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    __shared__ long long chunk_total;
-    long long carry = 0;
-    for (int64_t c0 = 0; c0 < ntiles; c0 += (int64_t)kScanThreads * kScanItems) {
+        // each thread: kScanItems consecutive values
         long long v[kScanItems];
-        long long s = 0;
-        const int64_t b = c0 + (int64_t)threadIdx.x * kScanItems;
+        long long sum = 0;
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            v[j] = b + j < ntiles ? bsum[b + j] : 0;
-            s += v[j];
+        for (int k = 0; k < kScanItems; ++k) {
+            const int j = threadIdx.x * kScanItems + k;
+            v[k] = s_v[j + (j >> 5)];
+            sum += v[k];
         }
-        long long pre = block_excl_scan(s, &chunk_total) + carry;
+        const long long pre = block_excl_scan(sum, &s_tot);
+        const long long agg = s_tot;
+        // publish the sum, then look back
+        if (threadIdx.x == 0)
+            st[1 + t] = (t == 0 ? kFlagPre : kFlagAgg) | ((unsigned long long)agg & kValMask);
+        if (threadIdx.x < 32) {
+            long long excl = 0;
+            int64_t j = t - 1;
+            const int lane = threadIdx.x;
+            while (j >= 0) {
+                const int64_t jj = j - lane;
+                unsigned long long w = kFlagPre;     // lanes past tile 0 count as a prefix of 0
+                if (jj >= 0) {
+                    int spin = 0;
+                    w = st[1 + jj];
+                    while ((w >> 62) == 0 && spin < kSpinLimit) {
+                        ++spin;
+                        w = st[1 + jj];
+                    }
+                    if ((w >> 62) == 0) {
+                        atomicOr(reinterpret_cast<unsigned long long*>(overflow),
+                                 (unsigned long long)timeout_bit);
+                        w = kFlagPre;
+                    }
+                }
+                const unsigned pmask = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+                const int stop = pmask ? __ffs(pmask) - 1 : 31;   // first prefix, else all 32
+                long long val = lane <= stop ? (long long)(w & kValMask) : 0;
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            if (b + j < ntiles) bsum[b + j] = pre;
-            pre += v[j];
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                excl += val;
+                if (pmask) break;
+                j -= 32;
+            }
+            if (lane == 0) {
+                s_excl = excl;
+                if (t > 0) st[1 + t] = kFlagPre | ((unsigned long long)(excl + agg) & kValMask);
+            }
         }
-        carry += chunk_total;
         __syncthreads();
-    }
-    if (threadIdx.x == 0 && dst) {
-        const int64_t b = base ? *base : 0;
-        int64_t end = carry + b;
-        if (overflow && end > clamp_cap) {
-            atomicOr(reinterpret_cast<unsigned long long*>(overflow),
-                     (unsigned long long)overflow_bit);
-            atomicMax(reinterpret_cast<unsigned long long*>(need), (unsigned long long)end);
-            end = b;
-        }
-        *dst = end;
-    }
-}
-
-__global__ void k_sd_apply(const int32_t* in, int32_t* out, const int64_t* __restrict__ n_dev,
-                           const long long* __restrict__ bsum) {
-    const int64_t n = *n_dev;
-    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    __shared__ long long tot;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t base = t * kScanTile + (int64_t)threadIdx.x * kScanItems;
-        long long v[kScanItems];
-        long long s = 0;
+        const long long excl = s_excl;
+        // offsets through shared memory, stored coalesced
+        long long run = excl + pre;
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            v[j] = base + j < n ? in[base + j] : 0;
-            s += v[j];
+        for (int k = 0; k < kScanItems; ++k) {
+            const int j = threadIdx.x * kScanItems + k;
+            s_v[j + (j >> 5)] = (int32_t)run;
+            run += v[k];
         }
-        long long pre = block_excl_scan(s, &tot) + bsum[t];
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            if (base + j < n) out[base + j] = (int32_t)pre;
-            pre += v[j];
+        __syncthreads();
+        for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+            const int64_t i = t0 + j;
+            if (i < n) out[i] = s_v[j + (j >> 5)];
+        }
+        if (t == ntiles - 1 && threadIdx.x == 0 && dst) {
+            const int64_t b = base ? *base : 0;
+            int64_t end = excl + agg + b;
+            if (overflow && end > clamp_cap && clamp_cap > 0) {
+                atomicOr(reinterpret_cast<unsigned long long*>(overflow),
+                         (unsigned long long)overflow_bit);
+                atomicMax(reinterpret_cast<unsigned long long*>(need), (unsigned long long)end);
+                end = b;
+            }
+            *dst = end;
         }
         __syncthreads();
     }
@@ -393,21 +429,26 @@ void dev_store_i32(int32_t* dst, const int64_t* src, cudaStream_t s) {
 void pull_counts(msp_ctx& c, cudaStream_t s) {
     MSP_CUDA(cudaMemcpyAsync(c.hcount, c.dcount.p, sizeof(DevCounts), cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaStreamSynchronize(s));
+    if (c.hcount->overflow & kScanTimeoutBit) {
+        c.hcount->overflow &= ~kScanTimeoutBit;
+        dev_set(&dcounts(c)->overflow, c.hcount->overflow, s);
+        throw Error(MSP_ERR_TIMEOUT, "a bounded wait of the device scan gave up");
+    }
 }
 
 void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev, int64_t n_cap,
               int64_t* total_dst, const int64_t* base, cudaStream_t s, int64_t clamp_cap,
               int64_t* overflow, int64_t* need, int64_t overflow_bit) {
     const int64_t tiles_cap = std::max<int64_t>((n_cap + kScanTile - 1) / kScanTile, 1);
-    long long* bsum = c.sd_tmp.ensure<long long>((size_t)tiles_cap);
-    const int G = (int)std::min<int64_t>(tiles_cap, (int64_t)c.sm_count * 8);
-    k_sd_reduce<<<G, kScanThreads, 0, s>>>(in, n_dev, bsum);
-    MSP_LAUNCH("scan_dev_reduce");
-    k_sd_spine<<<1, kScanThreads, 0, s>>>(bsum, n_dev, total_dst, base, clamp_cap, overflow,
-                                          need, overflow_bit);
-    MSP_LAUNCH("scan_dev_spine");
-    k_sd_apply<<<G, kScanThreads, 0, s>>>(in, out, n_dev, bsum);
-    MSP_LAUNCH("scan_dev_apply");
+    // single pass: a tile counter and one status word per tile, cleared first
+    unsigned long long* status = c.sd_tmp.ensure<unsigned long long>((size_t)tiles_cap + 1);
+    MSP_CUDA(cudaMemsetAsync(status, 0, ((size_t)tiles_cap + 1) * sizeof(unsigned long long), s));
+    const int G = (int)std::min<int64_t>(tiles_cap, (int64_t)c.sm_count * 4);
+    DevCounts* dc = dcounts(c);
+    k_scan_1p<<<G, kScanThreads, 0, s>>>(in, out, n_dev, status, total_dst, base,
+                                         overflow ? clamp_cap : 0, overflow ? overflow : &dc->overflow,
+                                         need, overflow_bit, kScanTimeoutBit);
+    MSP_LAUNCH("scan_dev");
 }
 
 void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
