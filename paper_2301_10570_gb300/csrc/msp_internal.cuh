@@ -130,6 +130,7 @@ struct DevCounts {
     int64_t halt;
     int64_t steps_run;
     int64_t interactions_run;                // near-field interactions over the replays
+    uint64_t pos_sum;                        // checksum of the positions of the last build
 };
 
 // DevCounts::overflow bit set when a bounded wait of the single-pass scan
@@ -203,6 +204,11 @@ struct msp_ctx {
     msp::DBuf dcount;
     msp::DevCounts* hcount = nullptr;
     int depth_hint = -1;                 // tree depth of the last build (-1: none)
+    // the octree depends on the positions only: graph steps reuse the one of
+    // the last eager build (levels built, checksum of its positions) and
+    // refresh the counts and aggregates
+    int tree_levels = 0;
+    uint64_t pos_sum_ref = 0;
     int64_t pair_cap = 0;                // capacity of the pair table
     cudaEvent_t ev_nf0 = nullptr, ev_nf1 = nullptr;   // around the near-field kernel
     bool nf_timed = false;

@@ -19,6 +19,33 @@ __device__ inline uint32_t quantise(float v, float o, float scale) {
 __global__ void k_build_init(DevCounts* dc, int64_t n) {
     dc->n = n;
     dc->bad_pos = 0;
+    dc->pos_sum = 0;
+}
+
+// order-independent checksum of the positions: the sum over i of a mix of
+// i and the three coordinates' bits (modulo 2^64)
+__global__ void k_pos_sum(const float* __restrict__ x, const float* __restrict__ y,
+                          const float* __restrict__ z, int64_t n,
+                          unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+        h ^= __float_as_uint(x[i]);
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= (unsigned long long)__float_as_uint(y[i]) << 21;
+        h *= 0x94D049BB133111EBull;
+        h ^= (unsigned long long)__float_as_uint(z[i]) << 42;
+        h ^= h >> 31;
+        acc += h;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// the positions of a graph step must be those its octree was built from
+__global__ void k_pos_check(DevCounts* dc, uint64_t ref) {
+    if (dc->pos_sum != ref) dc->bad_pos = 1;
 }
 
 // keys; a position outside [origin, origin + side) or not finite is counted
@@ -299,6 +326,40 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     int32_t* leaf_of = c.leaf_of.ensure<int32_t>(nn);
     const int B = 256;
     const int G = grid_for(n, B, (int64_t)c.sm_count * 16);
+    if (n > 0) {
+        k_pos_sum<<<G, B, 0, s>>>(x, y, z, n, reinterpret_cast<unsigned long long*>(&dc->pos_sum));
+        MSP_LAUNCH("pos_sum");
+    }
+
+    // Inside the whole-step graph the positions are those of the last eager
+    // build (checked: a different checksum halts the graph), so its sorted
+    // order and octree are reused; the counts are gathered again and the
+    // aggregates recomputed.
+    if (c.graph_mode && c.tree_built) {
+        k_pos_check<<<1, 1, 0, s>>>(dc, c.pos_sum_ref);
+        MSP_LAUNCH("pos_check");
+        if (n > 0) {
+            k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
+            MSP_LAUNCH("gather");
+            int32_t* tmp = c.cnt.ensure<int32_t>(nn);
+            k_u8_to_i32<<<G, B, 0, s>>>(va, n, tmp);
+            MSP_LAUNCH("u8_to_i32");
+            scan_dev(c, tmp, eoff, &dc->n, n, &dc->n_elem, nullptr, s);
+            dev_store_i32(eoff + n, &dc->n_elem, s);
+        } else {
+            dev_set(&dc->n_elem, 0, s);
+        }
+        const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
+        for (int l = c.tree_levels; l >= 0; --l) {
+            k_aggregate<<<Gt, 128, 0, s>>>(
+                &dc->level_start[l], l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
+                c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(),
+                c.nd_sums.get<int4>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), leaf_of);
+            MSP_LAUNCH("aggregate");
+        }
+        return;
+    }
 
     // a1 + a2: keys, stable sort, gather into Morton order
     if (n > 0) {
@@ -416,6 +477,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     c.tree_depth = depth;
     c.depth_hint = depth;
     c.n_elem = hc.n_elem;
+    c.tree_levels = L;
+    c.pos_sum_ref = hc.pos_sum;
     c.tree_built = true;
 }
 

@@ -112,6 +112,34 @@ def test_graph_halt_finishes_the_step_eagerly():
         assert np.array_equal(x, y)
 
 
+def test_graph_with_moved_positions_halts_and_rebuilds():
+    # graph steps reuse the octree of the eager build (neurons do not move);
+    # positions changed after the capture are detected by their checksum:
+    # the replay halts (the tree bit) and the step is finished eagerly on a
+    # new tree, so the run equals eager steps on the new positions
+    w = _workload()
+    moved = W.clustered_small(2, 2048, seed=11, leaf_capacity=32)
+    moved.pos[:, 10] = moved.pos[:, 500]         # one neuron onto another's place
+    k_steps = 3
+    ce, se, _ = _eager(moved, 0, k_steps)
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    out = g.step_graph_capture(pos, t, a, e, i, first_step=0, history_len=k_steps)
+    pos.copy_(torch.from_numpy(moved.pos).cuda())
+    step, halts = 0, []
+    while step < k_steps:
+        g.step_graph_launch(k_steps - step)
+        step, h = g.step_graph_finish()
+        halts.append(h)
+    assert halts[0] & 4, halts
+    assert out["history"].cpu().numpy().tolist() == ce
+    for x, y in zip([v.cpu().numpy() for v in (a, e, i)], se):
+        assert np.array_equal(x, y)
+    g.close()
+
+
 def test_graph_counts_its_kernel_launches():
     w = _workload()
     pos, t, a, e, i = _state(w)
