@@ -377,19 +377,33 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                 pos += 32;
             }
             __syncwarp();
-            const bool act = lane < nt;
-            const int32_t t = act ? s_tl[w][lane] : tf;
+            // S lanes per target when the round has few targets (S = 1, 2, 4):
+            // lane = q * TS + ti takes target ti and slice q of the sources
+            const int S = nt <= 8 ? 4 : (nt <= 16 ? 2 : 1);
+            const int TS = 32 / S;
+            const int ti = lane & (TS - 1), q = lane / TS;
+            const bool act = ti < nt;
+            const int32_t t = act ? s_tl[w][ti] : tf;
             __syncwarp();
             const float4 T = pts[t];
             const int a = act ? (int)pk_axon(__float_as_uint(T.w)) : 0;
-            // totals: all lanes walk the same points (shared-memory broadcast)
-            uint64_t tot = 0;
-            if (nt > 0) {
-                for (int j = 0; j < sc; ++j) {
+            const int L = (sc + S - 1) / S;
+            const int j0 = min(q * L, sc), j1 = min(j0 + L, sc);
+            // the slice's sum, the target's total and the slice's offset
+            // (integer sums: exact, the same as one walk over all sources)
+            uint64_t part = 0;
+            if (nt > 0)
+                for (int j = j0; j < j1; ++j) {
                     const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
-                    tot += sf + j == t ? 0ull : v;
+                    part += sf + j == t ? 0ull : v;
                 }
+            uint64_t tot = part, incl = part;
+            for (int o = TS; o < 32; o <<= 1) {
+                tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                const uint64_t up = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += up;
             }
+            const uint64_t off = incl - part;
             const int32_t to = perm[t];
             const bool draw = act && tot != 0 && (int64_t)eoff[to] + a <= ne;
             constexpr int kGroup = 8;
@@ -415,27 +429,27 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                     r[jj] = v;
                     ord[jj] = e;
                 }
-                int32_t pick[kGroup];
-                uint64_t pre = 0;
+                // this slice owns the thresholds in [off, off + part): the
+                // first source whose inclusive prefix exceeds a threshold
+                // lies in the slice whose prefix range contains it
                 int nx = 0;
-                uint64_t rn = ng > 0 ? r[0] : 0;       // the smallest threshold not yet crossed
-                for (int j = 0; j < sc; ++j) {
-                    if (!__any_sync(0xffffffffu, nx < ng)) break;
-                    if (nx < ng) {
+                while (nx < ng && r[nx] < off) ++nx;
+                int nend = nx;
+                while (nend < ng && r[nend] < off + part) ++nend;
+                uint64_t pre = off;
+                // every lane runs the same L iterations (the warp votes in each)
+                for (int jj = 0; jj < L; ++jj) {
+                    const int j = j0 + jj;
+                    if (!__any_sync(0xffffffffu, nx < nend && j < j1)) break;
+                    if (nx < nend && j < j1) {
                         const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
                         pre += sf + j == t ? 0ull : v;
-                        if (pre > rn) {
-                            do {
-                                pick[ord[nx++]] = sf + j;
-                                rn = nx < ng ? r[nx] : 0;
-                            } while (nx < ng && pre > rn);
+                        while (nx < nend && pre > r[nx]) {
+                            partner[eoff[to] + e0 + ord[nx]] = perm[sf + j];
+                            ++draws;
+                            ++nx;
                         }
                     }
-                }
-                // r < tot = the final prefix, so every threshold was crossed
-                for (int e = 0; e < ng; ++e) {
-                    partner[eoff[to] + e0 + e] = perm[pick[e]];
-                    ++draws;
                 }
             }
         }
