@@ -377,9 +377,9 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                 pos += 32;
             }
             __syncwarp();
-            // S lanes per target when the round has few targets (S = 1, 2, 4):
+            // S lanes per target when the round has few targets (S = 1, 2, 4, 8):
             // lane = q * TS + ti takes target ti and slice q of the sources
-            const int S = nt <= 8 ? 4 : (nt <= 16 ? 2 : 1);
+            const int S = nt <= 4 ? 8 : (nt <= 8 ? 4 : (nt <= 16 ? 2 : 1));
             const int TS = 32 / S;
             const int ti = lane & (TS - 1), q = lane / TS;
             const bool act = ti < nt;
