@@ -187,6 +187,42 @@ __device__ __forceinline__ void nf_eval(const float4* st, int mp, int ksl, int s
     }
 }
 
+// The expanded form when every lane walks all staged source pairs (one slice):
+// unit-stride pointers, two source pairs per iteration.
+template <int R>
+__device__ __forceinline__ void nf_eval_unit(const float4* st, int mp, const Tgts<R>& tg,
+                                             float (&part)[R]) {
+    constexpr int NA = R == 2 ? 2 : 1;
+    float2 P[R][NA];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < NA; ++k) P[r][k] = make_float2(0.f, 0.f);
+    const float4* xp = st;
+    const float4* zp = st + (tg.ch ? kNFZI : kNFZE);
+    const float4* const xe = st + (mp & ~1);
+    for (; xp < xe; xp += 2, zp += 2) {
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const float4 A = xp[v], B = zp[v];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                P[r][v % NA] = __fadd2_rn(P[r][v % NA], nf_term<R, 0>(tg, r, A, B));
+        }
+    }
+    if (mp & 1) {
+        const float4 A = xp[0], B = zp[0];
+#pragma unroll
+        for (int r = 0; r < R; ++r) P[r][0] = __fadd2_rn(P[r][0], nf_term<R, 0>(tg, r, A, B));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float t = P[r][0].x + P[r][0].y;
+        if (NA == 2) t += P[r][NA - 1].x + P[r][NA - 1].y;
+        part[r] += t;
+    }
+}
+
 // the pairs of segment [i0, i1) that belong to warp w, for a lane holding R targets
 template <int R>
 __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1, int32_t tf,
@@ -257,8 +293,9 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 }
                 __syncwarp();
                 if (fast) {
-                    if (self) nf_eval<R, 1>(stw, mp, ksl, slices, tg, sf + sb, part);
-                    else      nf_eval<R, 0>(stw, mp, ksl, slices, tg, sf + sb, part);
+                    if (self)             nf_eval<R, 1>(stw, mp, ksl, slices, tg, sf + sb, part);
+                    else if (slices == 1) nf_eval_unit<R>(stw, mp, tg, part);
+                    else                  nf_eval<R, 0>(stw, mp, ksl, slices, tg, sf + sb, part);
                 } else {
                     if (self) nf_eval<R, 3>(stw, mp, ksl, slices, tg, sf + sb, part);
                     else      nf_eval<R, 2>(stw, mp, ksl, slices, tg, sf + sb, part);
