@@ -280,6 +280,7 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
 // leaf at the deepest level) read their points from global memory.
 constexpr int kLdWarps = 4;
 constexpr int kLdStage = 256;
+constexpr int kLdBlocks = kLdStage / 32;   // blocks of 32 sources per lane slice
 
 struct LdSrc {
     const float4* sp;      // staged points {x, y, z, w} or null (global memory)
@@ -325,6 +326,7 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
               const int64_t* __restrict__ n_elem) {
     __shared__ float4 s_pts[kLdWarps][kLdStage];
     __shared__ int32_t s_tl[kLdWarps][32];
+    __shared__ uint64_t s_bsum[kLdWarps][kLdBlocks][32];   // per lane: sums of 32 sources
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t step = stp.get();
     const int64_t ne = *n_elem;
@@ -390,13 +392,29 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
             const int L = (sc + S - 1) / S;
             const int j0 = min(q * L, sc), j1 = min(j0 + L, sc);
             // the slice's sum, the target's total and the slice's offset
-            // (integer sums: exact, the same as one walk over all sources)
+            // (integer sums: exact, the same as one walk over all sources);
+            // with at most kLdBlocks blocks of 32 sources per slice the block
+            // sums are kept too, so that the walk can skip whole blocks
+            const bool use_blocks = L <= 32 * kLdBlocks;
             uint64_t part = 0;
-            if (nt > 0)
-                for (int j = j0; j < j1; ++j) {
-                    const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
-                    part += sf + j == t ? 0ull : v;
+            if (nt > 0) {
+                if (use_blocks) {
+                    for (int b = 0; j0 + 32 * b < j1; ++b) {
+                        uint64_t bsum = 0;
+                        for (int j = j0 + 32 * b; j < min(j1, j0 + 32 * b + 32); ++j) {
+                            const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                            bsum += sf + j == t ? 0ull : v;
+                        }
+                        s_bsum[w][b][lane] = bsum;
+                        part += bsum;
+                    }
+                } else {
+                    for (int j = j0; j < j1; ++j) {
+                        const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                        part += sf + j == t ? 0ull : v;
+                    }
                 }
+            }
             uint64_t tot = part, incl = part;
             for (int o = TS; o < 32; o <<= 1) {
                 tot += __shfl_xor_sync(0xffffffffu, tot, o);
@@ -437,17 +455,54 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                 int nend = nx;
                 while (nend < ng && r[nend] < off + part) ++nend;
                 uint64_t pre = off;
-                // every lane runs the same L iterations (the warp votes in each)
-                for (int jj = 0; jj < L; ++jj) {
-                    const int j = j0 + jj;
-                    if (!__any_sync(0xffffffffu, nx < nend && j < j1)) break;
-                    if (nx < nend && j < j1) {
-                        const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
-                        pre += sf + j == t ? 0ull : v;
-                        while (nx < nend && pre > r[nx]) {
-                            partner[eoff[to] + e0 + ord[nx]] = perm[sf + j];
-                            ++draws;
-                            ++nx;
+                if (use_blocks) {
+                    // from the block holding the next threshold (the blocks
+                    // before it are skipped by their sums), source by source;
+                    // at most L evaluations, the warp voting in each
+                    int b = 0, j = j0;
+                    uint64_t cb = off;          // prefix before block b
+                    bool placed = false;
+                    for (int it = 0; it < L; ++it) {
+                        if (!__any_sync(0xffffffffu, nx < nend)) break;
+                        if (nx < nend) {
+                            if (!placed) {
+                                while (cb + s_bsum[w][b][lane] <= r[nx]) {
+                                    cb += s_bsum[w][b][lane];
+                                    ++b;
+                                }
+                                j = j0 + 32 * b;
+                                pre = cb;
+                                placed = true;
+                            }
+                            const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                            pre += sf + j == t ? 0ull : v;
+                            while (nx < nend && pre > r[nx]) {
+                                partner[eoff[to] + e0 + ord[nx]] = perm[sf + j];
+                                ++draws;
+                                ++nx;
+                            }
+                            ++j;
+                            // the next threshold beyond this block: skip again
+                            if (nx < nend && r[nx] >= cb + s_bsum[w][b][lane]) {
+                                cb += s_bsum[w][b][lane];
+                                ++b;
+                                placed = false;
+                            }
+                        }
+                    }
+                } else {
+                    // every lane runs the same L iterations (the warp votes in each)
+                    for (int jj = 0; jj < L; ++jj) {
+                        const int j = j0 + jj;
+                        if (!__any_sync(0xffffffffu, nx < nend && j < j1)) break;
+                        if (nx < nend && j < j1) {
+                            const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                            pre += sf + j == t ? 0ull : v;
+                            while (nx < nend && pre > r[nx]) {
+                                partner[eoff[to] + e0 + ord[nx]] = perm[sf + j];
+                                ++draws;
+                                ++nx;
+                            }
                         }
                     }
                 }
