@@ -208,6 +208,13 @@ msp_status msp_commit_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t c
                                uint8_t *vac_dend_e_dev, uint8_t *vac_dend_i_dev,
                                void *stream);
 
+/* Self-test of the device's bounded waits: runs the single-pass scan with a
+ * predecessor tile that never publishes its sum, so the waiting tiles give
+ * up after a bounded number of polls.  Returns MSP_ERR_TIMEOUT when the wait
+ * gave up as designed (any other status is a failure); the context stays
+ * usable.  Synchronises. */
+msp_status msp_selftest_bounded_wait(msp_ctx *ctx, void *stream);
+
 /* ---- The neuron side of the model (Section 3.1, Table 1) -------------------
  * The Model of Structural Plasticity's neurons produce the vacant elements
  * that the synapse search consumes.  The network's synapses are an edge list

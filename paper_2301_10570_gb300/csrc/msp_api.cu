@@ -34,6 +34,7 @@ void commit_synapses(msp_ctx& c, const int64_t* n_syn, int64_t capacity, const i
 void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const uint8_t* vde,
                      const uint8_t* vdi, const float* g, float* u, float* dud, float* gE,
                      float* gI, cudaStream_t s);
+void scan_wait_selftest(msp_ctx& c, cudaStream_t s);
 void graph_release(msp_ctx& c);
 void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s);
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s);
@@ -298,6 +299,10 @@ msp_status msp_commit_synapses(msp_ctx* c, const int64_t* n_syn, int64_t capacit
         msp::commit_synapses(*c, n_syn, capacity, pre, post, styp, va, vde, vdi,
                              as_stream(stream));
     });
+}
+
+msp_status msp_selftest_bounded_wait(msp_ctx* c, void* stream) {
+    return guarded(c, [&] { msp::scan_wait_selftest(*c, as_stream(stream)); });
 }
 
 msp_status msp_neuron_steps(msp_ctx* c, int64_t n, uint64_t first_step, int n_steps,

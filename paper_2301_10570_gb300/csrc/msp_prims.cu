@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan_1p(const int32_t* in, int32_t* out, const int64_t* __restrict__ n_dev,
           unsigned long long* status, int64_t* __restrict__ dst,
           const int64_t* __restrict__ base, int64_t clamp_cap, int64_t* __restrict__ overflow,
-          int64_t* __restrict__ need, int64_t overflow_bit, int64_t timeout_bit) {
+          int64_t* __restrict__ need, int64_t overflow_bit, int64_t timeout_bit, int spin_limit) {
     __shared__ int32_t s_v[kScanTile + kScanTile / 32];
     __shared__ long long s_tot, s_excl;
     __shared__ int64_t s_tile;
@@ -288,7 +288,7 @@ k_scan_1p(const int32_t* in, int32_t* out, const int64_t* __restrict__ n_dev,
                 if (jj >= 0) {
                     int spin = 0;
                     w = st[1 + jj];
-                    while ((w >> 62) == 0 && spin < kSpinLimit) {
+                    while ((w >> 62) == 0 && spin < spin_limit) {
                         ++spin;
                         w = st[1 + jj];
                     }
@@ -447,8 +447,29 @@ void scan_dev(msp_ctx& c, const int32_t* in, int32_t* out, const int64_t* n_dev,
     DevCounts* dc = dcounts(c);
     k_scan_1p<<<G, kScanThreads, 0, s>>>(in, out, n_dev, status, total_dst, base,
                                          overflow ? clamp_cap : 0, overflow ? overflow : &dc->overflow,
-                                         need, overflow_bit, kScanTimeoutBit);
+                                         need, overflow_bit, kScanTimeoutBit, kSpinLimit);
     MSP_LAUNCH("scan_dev");
+}
+
+// The scan's bounded wait, exercised: the tile counter starts at 1, so tile
+// 0 is never taken and its status never published; the tiles after it wait
+// on it at most `spin_limit` polls, give up, record the timeout bit and
+// finish.  pull_counts then reports MSP_ERR_TIMEOUT.
+void scan_wait_selftest(msp_ctx& c, cudaStream_t s) {
+    const int64_t n = 3 * (int64_t)kScanTile;
+    int32_t* in = c.cnt.ensure<int32_t>((size_t)n);
+    int32_t* out = c.off.ensure<int32_t>((size_t)n);
+    int64_t* nd = c.gm_cnt.ensure<int64_t>(4);
+    unsigned long long* status = c.sd_tmp.ensure<unsigned long long>(4 + 1);
+    MSP_CUDA(cudaMemsetAsync(in, 0, (size_t)n * sizeof(int32_t), s));
+    MSP_CUDA(cudaMemsetAsync(status, 0, 5 * sizeof(unsigned long long), s));
+    dev_set(reinterpret_cast<int64_t*>(status), 1, s);       // tile 0 is skipped
+    dev_set(nd, n, s);
+    k_scan_1p<<<3, kScanThreads, 0, s>>>(in, out, nd, status, nd + 1, nullptr, 0,
+                                         &dcounts(c)->overflow, nullptr, 0, kScanTimeoutBit,
+                                         1 << 12);
+    MSP_LAUNCH("scan_wait_selftest");
+    pull_counts(c, s);
 }
 
 void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,

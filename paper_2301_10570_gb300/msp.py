@@ -33,7 +33,7 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
             "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
-            "msp_update_synapses", "msp_append_synapses")
+            "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -146,12 +146,14 @@ def load(path: str = LIB_PATH):
                                        i64] + [vp] * 9 + [vp]
         L.msp_update_synapses.argtypes = [vp, i64, u64] + [vp] * 7 + [i64] + [vp] * 3 + [vp]
         L.msp_append_synapses.argtypes = [vp, vp, i64] + [vp] * 7 + [i64, vp]
-        for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses"):
+        L.msp_selftest_bounded_wait.argtypes = [vp, vp]
+        for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
+                     "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
                      "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
-            "msp_update_synapses", "msp_append_synapses"):
+            "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
         for name in ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction",
                      "msp_direct", "msp_select_partners", "msp_plasticity_step_host",
@@ -309,6 +311,11 @@ class MSP:
                                           _ptr(sel["syn_pre"]), _ptr(sel["syn_post"]),
                                           _ptr(sel["syn_type"]), _ptr(vac_axon),
                                           _ptr(vac_dend_e), _ptr(vac_dend_i), _stream(stream)))
+
+    def selftest_bounded_wait(self, stream=None):
+        """Runs the device scan with a predecessor that never publishes; the
+        bounded wait gives up: raises MSPError with code 4 (MSP_ERR_TIMEOUT)."""
+        _check(load().msp_selftest_bounded_wait(self._h, _stream(stream)))
 
     # -- the neuron side of the model (Section 3.1) ------------------------------
     def neuron_steps(self, first_step, n_steps, params, edges, state, stream=None):

@@ -128,3 +128,18 @@ def test_uniform_256k_translations_converge_with_p():
         g.close()
     assert errs[3] > errs[4] > errs[6] > errs[8], errs
     assert errs[4] < 5e-2 and errs[8] < 1e-3, errs
+
+
+def test_bounded_wait_gives_up_and_reports_a_timeout():
+    # the device scan's look-back waits on a predecessor that never publishes
+    # (a flag nothing sets): the wait gives up after a bounded number of
+    # polls, the call reports MSP_ERR_TIMEOUT and the context keeps working
+    w = W.uniform_4k()
+    g = msp.MSP(w.params)
+    with pytest.raises(msp.MSPError) as ei:
+        g.selftest_bounded_wait()
+    assert ei.value.code == 4                            # MSP_ERR_TIMEOUT
+    g.build_tree(*msp.to_device(w))
+    u = g.attraction()
+    assert torch.isfinite(u).all() and float(u.max()) > 0
+    g.close()
