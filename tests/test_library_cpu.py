@@ -48,14 +48,18 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "msp.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(msp_config), sizeof(msp_stats),'
-        ' offsetof(msp_config, seed), offsetof(msp_stats, near_field_ms),'
-        ' offsetof(msp_config, m2l_min_pairs)); return 0;}\n')
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(msp_config),'
+        ' sizeof(msp_stats), offsetof(msp_config, seed), offsetof(msp_stats, near_field_ms),'
+        ' offsetof(msp_config, m2l_min_pairs), offsetof(msp_config, centre_mode),'
+        ' sizeof(msp_neuron_params), offsetof(msp_neuron_params, refractory),'
+        ' offsetof(msp_neuron_params, mu)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [ctypes.sizeof(msp.Config), ctypes.sizeof(msp.Stats), msp.Config.seed.offset,
-                   msp.Stats.near_field_ms.offset, msp.Config.m2l_min_pairs.offset]
+                   msp.Stats.near_field_ms.offset, msp.Config.m2l_min_pairs.offset,
+                   msp.Config.centre_mode.offset, ctypes.sizeof(msp.NeuronParams),
+                   msp.NeuronParams.refractory.offset, msp.NeuronParams.mu.offset]
 
 
 def test_last_error_is_a_string_and_create_validates(lib):
