@@ -207,3 +207,24 @@ def test_simulation_loop_matches_the_oracle():
         compared += 1
     g.close()
     assert compared >= 1
+
+
+def test_neuron_steps_full_size_bit_exact():
+    # the simulation benchmark's size: 1,048,576 neurons, 1.5 synapses each,
+    # 20 steps; every state array bit for bit against the oracle
+    rng = np.random.default_rng(36)
+    n = 1 << 20
+    m = 3 * n // 2
+    pre = rng.integers(0, n, m).astype(np.int32)
+    post = rng.integers(0, n, m).astype(np.int32)
+    st = _random_state(rng, n)
+    kw = dict(input_per_spike=0.02)
+    want = O.neuron_steps(19, 1000, 20, O.neuron_params(**kw), pre, post, st)
+    g = _ctx(seed=19)
+    edges = msp.edge_list(m, pre=pre, post=post, type_=np.zeros(m, np.uint8))
+    dev = _to_dev(st)
+    g.neuron_steps(1000, 20, msp.neuron_params(**kw), edges, dev)
+    torch.cuda.synchronize()
+    g.close()
+    for k, _ in msp.NEURON_STATE:
+        assert _same(dev[k].cpu().numpy(), want[k]), k
