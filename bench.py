@@ -147,17 +147,42 @@ class Clocks:
         self.dev = device_index
 
     def start(self):
+        """Start sampling every 50 ms; returns once the sampler has written its
+        first line (at most 3 s), so that it is live when the timed region
+        begins, and drops that line (taken before the region)."""
+        self.skip = 0
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and self._lines() == 0:
+            time.sleep(0.01)
+        self.mark()
+
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return f.read().count("\n")
+        except OSError:
+            return 0
+
+    def mark(self):
+        """The timed region begins: samples written before now are dropped."""
+        if self.proc is not None:
+            self.skip = self._lines()
 
     def stop(self):
         if self.proc is None:
             return None
+        # at least one sample from the timed region or right after it (at most 1 s)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.0 and self._lines() <= self.skip:
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -167,7 +192,7 @@ class Clocks:
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         with open(self.path) as f:
-            for line in f:
+            for line in f.read().splitlines()[self.skip:]:
                 p = [x.strip() for x in line.split(",")]
                 if len(p) < 9:
                     continue
