@@ -166,8 +166,10 @@ __device__ __forceinline__ int nr_update(NrState& v, int32_t in, uint32_t t, uin
 // array 16-byte aligned, the byte arrays 4-byte aligned) a thread takes four
 // consecutive neurons with 16-byte loads and stores, so that more of the
 // state is in flight per thread; the last n mod 4 neurons (or all, without
-// vec4) go one per thread.
-__global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
+// vec4) go one per thread.  The step is bound by the latency of its loads:
+// at most 48 registers (no spills) keep five blocks resident per SM.
+__global__ void __launch_bounds__(256, 5)
+k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
                               msp_neuron_params mp, int32_t* __restrict__ cur,
                               int32_t* __restrict__ next, const int32_t* __restrict__ off,
                               const int32_t* __restrict__ deg, const int32_t* __restrict__ targets,
@@ -180,8 +182,6 @@ __global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
     const int64_t n4 = vec4 ? n / 4 : 0;
     for (int64_t q = tid; q < n4; q += stride) {
         const int4 in4 = reinterpret_cast<const int4*>(cur)[q];
-        const int4 o4 = reinterpret_cast<const int4*>(off)[q];
-        const int4 d4 = reinterpret_cast<const int4*>(deg)[q];
         const float4 x4 = reinterpret_cast<const float4*>(x)[q];
         const float4 c4 = reinterpret_cast<const float4*>(calcium)[q];
         const float4 a4 = reinterpret_cast<const float4*>(za)[q];
@@ -190,8 +190,6 @@ __global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
         const uint32_t r4 = reinterpret_cast<const uint32_t*>(refr)[q];
         reinterpret_cast<int4*>(cur)[q] = make_int4(0, 0, 0, 0);
         const int32_t ins[4] = {in4.x, in4.y, in4.z, in4.w};
-        const int32_t j0s[4] = {o4.x, o4.y, o4.z, o4.w};
-        const int32_t njs[4] = {d4.x, d4.y, d4.z, d4.w};
         NrState v[4] = {{x4.x, c4.x, a4.x, e4.x, i4.x, r4 & 0xffu},
                         {x4.y, c4.y, a4.y, e4.y, i4.y, (r4 >> 8) & 0xffu},
                         {x4.z, c4.z, a4.z, e4.z, i4.z, (r4 >> 16) & 0xffu},
@@ -201,8 +199,11 @@ __global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
         for (int k = 0; k < 4; ++k) {
             const int s = nr_update(v[k], ins[k], (uint32_t)(4 * q + k), seed, step, mp);
             sp |= (uint32_t)s << (8 * k);
-            if (s)
-                for (int32_t j = j0s[k]; j < j0s[k] + njs[k]; ++j) atomicAdd(&next[targets[j]], 1);
+            if (s) {
+                // the outgoing edges are read only for the neurons that spiked
+                const int32_t j0 = off[4 * q + k], j1 = j0 + deg[4 * q + k];
+                for (int32_t j = j0; j < j1; ++j) atomicAdd(&next[targets[j]], 1);
+            }
         }
         reinterpret_cast<float4*>(x)[q] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
         reinterpret_cast<float4*>(calcium)[q] = make_float4(v[0].ca, v[1].ca, v[2].ca, v[3].ca);
@@ -215,7 +216,6 @@ __global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
     }
     for (int64_t t = 4 * n4 + tid; t < n; t += stride) {
         const int32_t in = cur[t];
-        const int32_t j0 = off[t], nj = deg[t];
         cur[t] = 0;
         NrState v = {x[t], calcium[t], za[t], ze[t], zi[t], refr[t]};
         const int s = nr_update(v, in, (uint32_t)t, seed, step, mp);
@@ -227,7 +227,8 @@ __global__ void k_neuron_step(int64_t n, int vec4, uint64_t seed, uint64_t step,
         refr[t] = (uint8_t)v.rf;
         spiked[t] = (uint8_t)s;
         if (s)
-            for (int32_t j = j0; j < j0 + nj; ++j) atomicAdd(&next[targets[j]], 1);
+            for (int32_t j = off[t], j1 = off[t] + deg[t]; j < j1; ++j)
+                atomicAdd(&next[targets[j]], 1);
     }
 }
 
