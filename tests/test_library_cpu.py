@@ -173,3 +173,35 @@ def test_batch_select_keeps_networks_whole():
             assert np.array_equal(part.pos[:, a0:a1], b.pos[:, b0:b1])
             assert np.array_equal(part.vac_axon[a0:a1], b.vac_axon[b0:b1])
             assert part.sigma[j] == b.sigma[k] and part.kinds[j] == b.kinds[k]
+
+
+def test_clock_sampler_drops_samples_before_the_timed_region(tmp_path, monkeypatch):
+    # a stand-in for nvidia-smi that prints one sample line every 20 ms: the
+    # first line it writes (before the timed region) is dropped, throttle
+    # reasons reported as Active are collected
+    import sys
+    import time
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/bash\n"
+                    "echo '0, 1500, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "sleep 0.2\n"
+                    "while true; do\n"
+                    "  echo '0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.02\n"
+                    "done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    c = bench.Clocks(0)
+    c.start()
+    time.sleep(0.4)
+    r = c.stop()
+    assert r is not None and r["samples"] >= 1
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
+    # without nvidia-smi there is no clock record, and no error
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop() is None
