@@ -142,7 +142,7 @@ class Clocks:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
-        self.path = tempfile.mktemp(prefix="msp_clocks_", suffix=".csv")
+        self.path = None
         self.proc = None
         self.dev = device_index
 
@@ -151,13 +151,16 @@ class Clocks:
         first line (at most 3 s), so that it is live when the timed region
         begins, and drops that line (taken before the region)."""
         self.skip = 0
+        fd, self.path = tempfile.mkstemp(prefix="msp_clocks_", suffix=".csv")
+        self.f = os.fdopen(fd, "w")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            self.f.close()
+            os.unlink(self.path)
             return
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < 3.0 and self._lines() == 0:
