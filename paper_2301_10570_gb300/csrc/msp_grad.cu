@@ -44,30 +44,69 @@ __global__ void k_grad_gather(int64_t n, const int32_t* __restrict__ perm,
 
 constexpr int kGrWarps = 4;
 constexpr int kGrStage = 64;
+constexpr int kGrList = 64;    // evaluation points per pass (two per lane)
+
+// A staged pair of sources against one evaluation point t, whose scaled
+// coordinates are broadcast into both halves of register pairs; every step is
+// a paired FP32 instruction (two results, one issue slot) with the
+// per-element rounding of the scalar form: dx = t - s (s is staged negated),
+// q = fma(dx, dx, fma(dy, dy, dz dz)), K = 2^-q.  Staged pair j (sources
+// 2j, 2j + 1): A = (-x0, -x1, -y0, -y1), B = (-z0, -z1, w0_0, w0_1),
+// C = (w1_0, w1_1, index0, index1); a padding source has zero weights and
+// index -1.  SELF: a source may be t itself (sorted index e); its term is zero.
+template <bool FORWARD, bool SELF>
+__device__ __forceinline__ void gr_term(const float4 A, const float4 B, const float4 C,
+                                        float2 tx, float2 ty, float2 tz, bool inh, int32_t e,
+                                        float2& a0, float2& a1) {
+    const float2 dx = __fadd2_rn(tx, make_float2(A.x, A.y));
+    const float2 dy = __fadd2_rn(ty, make_float2(A.z, A.w));
+    const float2 dz = __fadd2_rn(tz, make_float2(B.x, B.y));
+    const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 ex = make_float2(gr_ex2(-q.x), gr_ex2(-q.y));
+    if (SELF) {
+        ex.x = __float_as_int(C.z) == e ? 0.f : ex.x;
+        ex.y = __float_as_int(C.w) == e ? 0.f : ex.y;
+    }
+    if (FORWARD) {
+        const float2 wk = __fmul2_rn(inh ? make_float2(C.x, C.y) : make_float2(B.z, B.w), ex);
+        a0 = __fadd2_rn(a0, wk);
+        a1 = __ffma2_rn(wk, q, a1);
+    } else {
+        a0 = __ffma2_rn(make_float2(B.z, B.w), ex, a0);
+        a1 = __ffma2_rn(make_float2(C.x, C.y), ex, a1);
+    }
+}
 
 // One block per leaf L of a segment list (the evaluation leaf), its 4 warps
-// taking the segment's partner leaves P round-robin.  Each warp stages P's
-// points in shared memory, 64 at a time, as scaled positions
-// sqrt(k2) (x - o) relative to a point o of L, and two weights; each lane holds one evaluation point of
-// L (several passes for leaves over 32 points) and sums over the staged
-// points, q = |t^ - s^|^2 and 2^-q in single precision.  The 4 warps' sums
-// are added in a fixed order.
+// taking the segment's partner leaves P round-robin.  Warp 0 lists L's
+// evaluation points, up to 64 per pass (FORWARD: the targets, a_t > 0;
+// ADJOINT: every point); each lane holds two of them (lane, lane + 32).  Each
+// warp stages P's points in shared memory, 64 at a time in pairs, as scaled
+// positions sqrt(k2) (x - o) relative to a point o of L, and two weights, and
+// every lane sums over the staged pairs, q = |t^ - s^|^2 and 2^-q in single
+// precision, the even and the odd sources of a point in the two halves of a
+// register pair.  The 4 warps' sums are added in a fixed order, so a point's
+// sum does not depend on how the points are packed into passes.
 //   FORWARD: evaluation points = targets t (a_t > 0), partner weights
 //            (w^E, w^I): u += w^{T(t)} 2^-q, d += w^{T(t)} q 2^-q.
 //   ADJOINT: evaluation points = sources s, partner weights
 //            (g_t [T(t) = E], g_t [T(t) = I]) (0 unless a_t > 0):
 //            gE += w0 2^-q, gI += w1 2^-q.
+// Points that are not evaluated keep the zero the caller wrote.  Six blocks
+// per SM (at most 80 registers: the unrolled paired loop spills below that).
 template <bool FORWARD>
-__global__ void __launch_bounds__(kGrWarps * 32)
+__global__ void __launch_bounds__(kGrWarps * 32, 6)
 k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
              const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
              const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
              const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
              const float4* __restrict__ gw, const int32_t* __restrict__ perm, float sqk,
              float dscale, float* __restrict__ out0, float* __restrict__ out1) {
-    __shared__ float4 sp[kGrWarps][kGrStage];
-    __shared__ float2 sw[kGrWarps][kGrStage];
-    __shared__ float red[kGrWarps][2][32];
+    __shared__ float4 sA[kGrWarps][kGrStage / 2], sB[kGrWarps][kGrStage / 2],
+        sC[kGrWarps][kGrStage / 2];
+    __shared__ float red[kGrWarps][2][kGrList];
+    __shared__ int32_t plist[kGrList];
+    __shared__ int s_np, s_pos;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nseg = *nseg_dev;
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
@@ -77,79 +116,139 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
         // positions relative to a point of L before scaling: small operands,
         // so the differences keep their precision
         const float4 O = pts[lf];
-        for (int32_t p0 = 0; p0 < lc; p0 += 32) {
-            // this lane's evaluation point
-            const int32_t e = lf + p0 + lane;
-            const bool valid = p0 + lane < lc;
-            const float4 T = pts[valid ? e : lf];
-            const float4 G = gw[valid ? e : lf];
-            const uint32_t fl = __float_as_uint(G.w);
-            const bool act = valid && (!FORWARD || (fl & 2u));
-            const bool inh = fl & 1u;
-            const float tx = (T.x - O.x) * sqk, ty = (T.y - O.y) * sqk, tz = (T.z - O.z) * sqk;
-            float a0 = 0.f, a1 = 0.f;
+        int32_t pos = 0;
+        for (;;) {
+            if (w == 0) {
+                // the next (at most) kGrList evaluation points from pos on
+                int np = 0;
+                int32_t p = pos;
+                while (p < lc && np < kGrList) {
+                    const int32_t idx = p + lane;
+                    bool ok = idx < lc;
+                    if (FORWARD && ok) ok = (__float_as_uint(gw[lf + idx].w) & 2u) != 0;
+                    const unsigned mk = __ballot_sync(0xffffffffu, ok);
+                    const int room = kGrList - np;
+                    const int rank = __popc(mk & ((1u << lane) - 1u));
+                    if (ok && rank < room) plist[np + rank] = lf + idx;
+                    if (__popc(mk) > room) {
+                        // the room-th point ends the pass: resume after it
+                        unsigned keep = mk;
+                        for (int k = 0; k < room; ++k) keep &= keep - 1u;
+                        p += __ffs(keep) - 1;
+                        np = kGrList;
+                        break;
+                    }
+                    np += __popc(mk);
+                    p += 32;
+                }
+                if (lane == 0) {
+                    s_np = np;
+                    s_pos = min(p, lc);
+                }
+            }
+            __syncthreads();
+            const int np = s_np;
+            pos = s_pos;
+            __syncthreads();
+            if (np == 0) break;
+            const bool v0 = lane < np, v1 = lane + 32 < np;
+            const int32_t e0 = v0 ? plist[lane] : -1, e1 = v1 ? plist[lane + 32] : -1;
+            const float4 T0 = pts[v0 ? e0 : plist[0]], T1 = pts[v1 ? e1 : plist[0]];
+            const bool inh0 = __float_as_uint(gw[v0 ? e0 : plist[0]].w) & 1u;
+            const bool inh1 = __float_as_uint(gw[v1 ? e1 : plist[0]].w) & 1u;
+            const float x0 = (T0.x - O.x) * sqk, y0 = (T0.y - O.y) * sqk, z0 = (T0.z - O.z) * sqk;
+            const float x1 = (T1.x - O.x) * sqk, y1 = (T1.y - O.y) * sqk, z1 = (T1.z - O.z) * sqk;
+            const float2 tx0 = make_float2(x0, x0), ty0 = make_float2(y0, y0),
+                         tz0 = make_float2(z0, z0);
+            const float2 tx1 = make_float2(x1, x1), ty1 = make_float2(y1, y1),
+                         tz1 = make_float2(z1, z1);
+            float2 a00 = make_float2(0.f, 0.f), a10 = make_float2(0.f, 0.f);
+            float2 a01 = make_float2(0.f, 0.f), a11 = make_float2(0.f, 0.f);
             for (int32_t i = i0 + w; i < i1; i += kGrWarps) {
                 const int32_t P = pPart[pairs[i]];
                 const int32_t pf = nfirst[P], pc = ncount[P];
                 for (int32_t sb = 0; sb < pc; sb += kGrStage) {
                     const int m = min(kGrStage, pc - sb);
+                    const int mp = (m + 1) >> 1;
                     __syncwarp();
-                    for (int k = lane; k < m; k += 32) {
-                        const float4 S = pts[pf + sb + k];
-                        const float4 W = gw[pf + sb + k];
-                        sp[w][k] = make_float4((S.x - O.x) * sqk, (S.y - O.y) * sqk,
-                                               (S.z - O.z) * sqk, __int_as_float(pf + sb + k));
-                        if (FORWARD) {
-                            sw[w][k] = make_float2(W.x, W.y);
-                        } else {
-                            const uint32_t f2 = __float_as_uint(W.w);
-                            const float gv = (f2 & 2u) ? W.z : 0.f;
-                            sw[w][k] = (f2 & 1u) ? make_float2(0.f, gv) : make_float2(gv, 0.f);
+                    float* fA = reinterpret_cast<float*>(sA[w]);
+                    float* fB = reinterpret_cast<float*>(sB[w]);
+                    float* fC = reinterpret_cast<float*>(sC[w]);
+                    for (int k = lane; k < 2 * mp; k += 32) {
+                        float sx = 0.f, sy = 0.f, sz = 0.f, w0 = 0.f, w1 = 0.f;
+                        int32_t si = -1;
+                        if (k < m) {
+                            const float4 S = pts[pf + sb + k];
+                            const float4 W = gw[pf + sb + k];
+                            sx = (S.x - O.x) * sqk;
+                            sy = (S.y - O.y) * sqk;
+                            sz = (S.z - O.z) * sqk;
+                            if (FORWARD) {
+                                w0 = W.x;
+                                w1 = W.y;
+                            } else {
+                                const uint32_t f2 = __float_as_uint(W.w);
+                                const float gv = (f2 & 2u) ? W.z : 0.f;
+                                w0 = (f2 & 1u) ? 0.f : gv;
+                                w1 = (f2 & 1u) ? gv : 0.f;
+                            }
+                            si = pf + sb + k;
                         }
+                        const int j = k >> 1, h = k & 1;
+                        fA[4 * j + h] = -sx;
+                        fA[4 * j + 2 + h] = -sy;
+                        fB[4 * j + h] = -sz;
+                        fB[4 * j + 2 + h] = w0;
+                        fC[4 * j + h] = w1;
+                        fC[4 * j + 2 + h] = __int_as_float(si);
                     }
                     __syncwarp();
-                    if (act) {
-                        const bool self = P == L;
-#pragma unroll 4
-                        for (int k = 0; k < m; ++k) {
-                            const float4 S = sp[w][k];
-                            const float2 W = sw[w][k];
-                            const float dx = tx - S.x, dy = ty - S.y, dz = tz - S.z;
-                            const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float ex = gr_ex2(-q);
-                            if (self && __float_as_int(S.w) == e) ex = 0.f;
-                            if (FORWARD) {
-                                const float wk = (inh ? W.y : W.x) * ex;
-                                a0 += wk;
-                                a1 = fmaf(wk, q, a1);
-                            } else {
-                                a0 = fmaf(W.x, ex, a0);
-                                a1 = fmaf(W.y, ex, a1);
+                    if (v0) {
+                        if (P == L) {
+                            for (int j = 0; j < mp; ++j) {
+                                const float4 A = sA[w][j], B = sB[w][j], C = sC[w][j];
+                                gr_term<FORWARD, true>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
+                                gr_term<FORWARD, true>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
+                            }
+                        } else {
+#pragma unroll 2
+                            for (int j = 0; j < mp; ++j) {
+                                const float4 A = sA[w][j], B = sB[w][j], C = sC[w][j];
+                                gr_term<FORWARD, false>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
+                                gr_term<FORWARD, false>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
                             }
                         }
                     }
                 }
             }
-            red[w][0][lane] = a0;
-            red[w][1][lane] = a1;
+            red[w][0][lane] = a00.x + a00.y;
+            red[w][0][lane + 32] = a01.x + a01.y;
+            red[w][1][lane] = a10.x + a10.y;
+            red[w][1][lane + 32] = a11.x + a11.y;
             __syncthreads();
-            if (w == 0 && valid) {
-                float s0 = red[0][0][lane], s1 = red[0][1][lane];
+            if (w == 0) {
 #pragma unroll
-                for (int k = 1; k < kGrWarps; ++k) {
-                    s0 += red[k][0][lane];
-                    s1 += red[k][1][lane];
-                }
-                const int32_t c = perm[e];
-                if (FORWARD) {
-                    if (out0) out0[c] = act ? s0 : 0.f;
-                    if (out1) out1[c] = act ? s1 * dscale : 0.f;
-                } else {
-                    out0[c] = s0;
-                    out1[c] = s1;
+                for (int r = 0; r < 2; ++r) {
+                    const int j = lane + 32 * r;
+                    if (j >= np) continue;
+                    float s0 = red[0][0][j], s1 = red[0][1][j];
+#pragma unroll
+                    for (int k = 1; k < kGrWarps; ++k) {
+                        s0 += red[k][0][j];
+                        s1 += red[k][1][j];
+                    }
+                    const int32_t c = perm[plist[j]];
+                    if (FORWARD) {
+                        if (out0) out0[c] = s0;
+                        if (out1) out1[c] = s1 * dscale;
+                    } else {
+                        out0[c] = s0;
+                        out1[c] = s1;
+                    }
                 }
             }
             __syncthreads();
+            if (pos >= lc) break;
         }
     }
 }

@@ -5,10 +5,12 @@
     python -m paper_2301_10570_gb300.profile_cases graph_1m --steps 4
     python -m paper_2301_10570_gb300.profile_cases neuron_1m --steps 2
     python -m paper_2301_10570_gb300.profile_cases translations_256k --p 4 --centre-mode 1
+    python -m paper_2301_10570_gb300.profile_cases gradient_262k --steps 2
 
 Each case builds the library, runs a few plasticity steps (tree, attraction,
 selection; graph_1m: the whole step captured as one CUDA graph and replayed;
-neuron_1m: calls of 10 neuron steps of the model on the 1M network)
+neuron_1m: calls of 10 neuron steps of the model on the 1M network;
+gradient_262k: derivative passes of the attraction on 16 clusters of 16,384)
 and prints the library's statistics; it exits non-zero on any error.  The cases are sized for the profiling rules of the pool: the full
 capture case holds well under 1 GB on the device.
 """
@@ -40,8 +42,17 @@ def translations_256k(p=4, centre_mode=0):
                           centre_mode=centre_mode)
 
 
+def gradient_262k():
+    # the derivative benchmark's workload and plan (cutoff 5 sigma, leaf
+    # capacity 128, no translations)
+    from . import workloads as W
+    return W.clustered_small(16, 16_384, seed=15, leaf_capacity=128, cutoff=5.0, rho_max=0.0,
+                             p=4, m2l_min_pairs=0)
+
+
 CASES = {"near_field_131k": near_field_131k, "step_1m": step_1m, "graph_1m": step_1m,
-         "neuron_1m": step_1m, "translations_256k": translations_256k}
+         "neuron_1m": step_1m, "translations_256k": translations_256k,
+         "gradient_262k": gradient_262k}
 
 
 def _neuron_case(w, g, steps):
@@ -95,6 +106,16 @@ def main(argv=None):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         print(f"attraction_ms {statistics.median(ts[1:]):.3f}")
+    elif args.case == "gradient_262k":
+        # geometric lists (every count 1), derivatives at the real counts
+        import numpy as np
+        pos, typ, va, ve, vi = dev
+        ones = torch.ones_like(va)
+        g.build_tree(pos, typ, ones, ones, ones)
+        g.attraction()
+        gv = torch.from_numpy(np.random.default_rng(6).normal(size=w.n)).float().cuda()
+        for _ in range(args.steps):
+            g.attraction_grad(typ, va, ve, vi, g=gv)
     elif args.case.startswith("graph"):
         # one eager step sizes the graph; then the whole step as graph
         # replays (walk, build, attraction, selection, commit)
