@@ -77,6 +77,22 @@ __device__ __forceinline__ void gr_term(const float4 A, const float4 B, const fl
     }
 }
 
+// The staged pairs [0, mp) against the lane's first point, and its second
+// point too when NP = 2.
+template <bool FORWARD, bool SELF, int NP>
+__device__ __forceinline__ void gr_eval(const float4* sA, const float4* sB, const float4* sC,
+                                        int mp, float2 tx0, float2 ty0, float2 tz0, float2 tx1,
+                                        float2 ty1, float2 tz1, bool inh0, bool inh1, int32_t e0,
+                                        int32_t e1, float2& a00, float2& a10, float2& a01,
+                                        float2& a11) {
+#pragma unroll 2
+    for (int j = 0; j < mp; ++j) {
+        const float4 A = sA[j], B = sB[j], C = sC[j];
+        gr_term<FORWARD, SELF>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
+        if (NP == 2) gr_term<FORWARD, SELF>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
+    }
+}
+
 // One block per leaf L of a segment list (the evaluation leaf), its 4 warps
 // taking the segment's partner leaves P round-robin.  Warp 0 lists L's
 // evaluation points, up to 64 per pass (FORWARD: the targets, a_t > 0;
@@ -204,19 +220,26 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
                     }
                     __syncwarp();
                     if (v0) {
-                        if (P == L) {
-                            for (int j = 0; j < mp; ++j) {
-                                const float4 A = sA[w][j], B = sB[w][j], C = sC[w][j];
-                                gr_term<FORWARD, true>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
-                                gr_term<FORWARD, true>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
-                            }
+                        // the second point of the lanes only while the pass
+                        // has more than 32 points
+                        if (np > 32) {
+                            if (P == L)
+                                gr_eval<FORWARD, true, 2>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
+                                                          tx1, ty1, tz1, inh0, inh1, e0, e1, a00,
+                                                          a10, a01, a11);
+                            else
+                                gr_eval<FORWARD, false, 2>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
+                                                           tx1, ty1, tz1, inh0, inh1, e0, e1,
+                                                           a00, a10, a01, a11);
                         } else {
-#pragma unroll 2
-                            for (int j = 0; j < mp; ++j) {
-                                const float4 A = sA[w][j], B = sB[w][j], C = sC[w][j];
-                                gr_term<FORWARD, false>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
-                                gr_term<FORWARD, false>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
-                            }
+                            if (P == L)
+                                gr_eval<FORWARD, true, 1>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
+                                                          tx1, ty1, tz1, inh0, inh1, e0, e1, a00,
+                                                          a10, a01, a11);
+                            else
+                                gr_eval<FORWARD, false, 1>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
+                                                           tx1, ty1, tz1, inh0, inh1, e0, e1,
+                                                           a00, a10, a01, a11);
                         }
                     }
                 }
