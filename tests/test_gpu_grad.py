@@ -43,9 +43,12 @@ def _rel(a, b, floor=1e-6):
     return np.max(np.abs(a[m] - b[m]) / np.abs(b[m]))
 
 
-def test_gradients_match_the_oracle_on_the_same_pairs():
+@pytest.mark.parametrize("leaf_capacity", [32, 160])
+def test_gradients_match_the_oracle_on_the_same_pairs(leaf_capacity):
+    # leaves of up to 160 points: passes of more than 32 evaluation points
+    # (two per lane) and leaves that take several passes
     from oracle import oracle as O
-    w = W.clustered_small(2, 2048, seed=12, **PLAN)
+    w = W.clustered_small(2, 2048, seed=12, **dict(PLAN, leaf_capacity=leaf_capacity))
     g = np.random.default_rng(4).normal(size=w.n)
     r = _gpu_grad(w, g)
     ones = np.ones(w.n, np.uint8)
