@@ -296,7 +296,8 @@ def run_gradient(args, rank, world):
                          "peak_basis": f"EX2 rate: {SM_COUNT} SMs x {EX2_PER_SM_CLK} "
                                        f"results/clk (measured) x {sm_max:.0f} MHz, one EX2 per "
                                        f"interaction; these kernels use the difference form "
-                                       f"(about 10 instructions per interaction)"}}
+                                       f"(about 7 instructions per interaction, paired FP32 "
+                                       f"over two sources)"}}
 
 
 # -- the simulation loop of the model (neuron side + synapse search) ------------
