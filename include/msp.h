@@ -431,6 +431,21 @@ msp_status msp_batch_layout(int64_t n_networks, const int64_t *offsets, const fl
                             float *y_out_dev, float *z_out_dev, float *side_out,
                             int *level_out, void *stream);
 
+/* The counter-based generator behind every random draw of the library:
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11), ten rounds, run on the device for n caller-given
+ * counters and keys, so that a caller can check the stream the draws use
+ * against the published known-answer vectors.  The draws of the search use
+ * key = (seed_lo, seed_hi) and counter = (c0, c1, step_lo, step_hi) with
+ * U = top 53 bits of output words 0 and 1.
+ *   ctr   DEVICE, n x 4 uint32 counters
+ *   key   DEVICE, n x 2 uint32 keys
+ *   out   DEVICE, n x 4 uint32 output blocks
+ * Needs no context.  Errors: MSP_ERR_INVALID_ARG (n < 0, null pointer with
+ * n > 0).  Asynchronous on `stream`. */
+msp_status msp_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                      void *stream);
+
 /* Largest n accepted by msp_direct_noalloc (the size of its fixed scratch). */
 #define MSP_NOALLOC_MAX_N 65536
 
@@ -450,7 +465,11 @@ msp_status msp_batch_layout(int64_t n_networks, const int64_t *offsets, const fl
  * file-scope device array of MSP_NOALLOC_MAX_N * 24 bytes that every GPU
  * loading this library holds until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  The
+ * address is kept per device and CUDA context: after cudaDeviceReset (a new
+ * context) the next call looks it up again, so that call, too, belongs before
+ * any stream capture.  Every pointer must be device (or managed) memory of
+ * the current device; others give MSP_ERR_INVALID_ARG.  All calls
  * share the array and it keeps the last call's contents (each call rewrites
  * the part it reads before reading it), so calls whose work overlaps on the
  * same GPU (for example on two streams) race on it: the caller must

@@ -12,9 +12,8 @@
  * quantisation, which is done in single precision with round-to-nearest so
  * that the integer keys (and hence the tree) are the same on both sides.
  *
- * Parity unpinned: the Philox stream (no published known-answer vectors are
- * available to this project; it is checked statistically and for
- * bijectivity only).
+ * The Philox stream is pinned by the generator's published known-answer
+ * vectors (Salmon et al., SC'11).
  */
 #ifndef MSP_ORACLE_H
 #define MSP_ORACLE_H

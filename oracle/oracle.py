@@ -123,7 +123,11 @@ def _cfg(params: dict) -> _Cfg:
     c.rho_max = float(params["rho_max"])
     c.cutoff = float(params["cutoff"])
     c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
-    c.boundary_tol = float(params.get("boundary_tol", 1e-5))
+    # draws within this relative distance of a CDF boundary are flagged: 1e-6
+    # when no pair is translated (single precision sums of exact terms), 1e-5
+    # with translations (their single precision coefficients move W by ~1e-5)
+    c.boundary_tol = float(params.get("boundary_tol",
+                                      1e-6 if float(params["rho_max"]) == 0.0 else 1e-5))
     c.centre_mode = int(params.get("centre_mode", 0))
     return c
 

@@ -36,6 +36,8 @@ inline void cuda_check(cudaError_t e, const char* what) {
     msp_status c = (e == cudaErrorMemoryAllocation) ? MSP_ERR_OOM : MSP_ERR_CUDA;
     throw Error(c, std::string(what) + ": " + cudaGetErrorString(e));
 }
+// message of the calling thread's last error (msp_last_error)
+void set_last_error(const char* msg);
 // kernels launched by the library (process-wide), counted at each launch check
 extern std::atomic<long long> g_kernel_launches;
 #define MSP_CUDA(x) ::msp::cuda_check((x), #x)

@@ -228,7 +228,8 @@ template <int R>
 __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1, int32_t tf,
                                          bool fast, float cx, float cy, float cz, int ksl,
                                          int slices, const Tgts<R>& tg, float (&acc)[R],
-                                         float4* stw, unsigned long long& evals, int nreal) {
+                                         float (&cmp)[R], float4* stw,
+                                         unsigned long long& evals, int nreal) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float (*wt)[33] = reinterpret_cast<float (*)[33]>(s_wt + w * 16 * 33);
     int32_t* wii = s_wii + w * 16;
@@ -301,10 +302,15 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                     else      nf_eval<R, 2>(stw, mp, ksl, slices, tg, sf + sb, part);
                 }
             }
+            // the pair's sum joins the target's total by Kahan's compensated
+            // summation (cmp holds what the running total gained by rounding)
             float v = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                acc[k] += part[k];
+                const float y = __fsub_rn(part[k], cmp[k]);
+                const float t2 = __fadd_rn(acc[k], y);
+                cmp[k] = __fsub_rn(__fsub_rn(t2, acc[k]), y);
+                acc[k] = t2;
                 v = fmaf(s_fa[tg.slot0 + k], part[k], v);
             }
             // W(X,Y) of each channel: every lane's term goes into a transposed
@@ -355,7 +361,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
     const int ksl = lane >> lg;
     Tgts<R> tg;
     tg.slot0 = R * j;
-    float acc[R];
+    float acc[R], cmp[R];
     {
         // the channel of the lane's first slot (all its slots share it)
         const int32_t t0 = tg.slot0 < nt ? tl[tg.slot0] : -1;
@@ -375,6 +381,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         tg.y[r] = make_float2(f2 * hy, f2 * hy);
         tg.z[r] = make_float2(f2 * hz, f2 * hz);
         acc[r] = 0.f;
+        cmp[r] = 0.f;
         if (w == 0 && ksl == 0) {
             const float sc = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
             s_scale[slot] = sc;
@@ -382,11 +389,14 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         }
     }
     __syncthreads();
-    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nreal);
-    // the slices of a target group, then the 4 warps in a fixed order
+    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, cmp, stw, evals, nreal);
+    // the compensated totals, then the slices of a target group and the 4
+    // warps in a fixed order
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
+        acc[r] = __fsub_rn(acc[r], cmp[r]);
         for (int o = npr; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    }
     if (ksl == 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) red[w][tg.slot0 + r] = acc[r];

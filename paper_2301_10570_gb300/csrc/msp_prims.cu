@@ -510,3 +510,45 @@ void radix_sort_dev(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tm
 }
 
 }  // namespace msp
+
+// ---------------------------------------------------------------------------
+// The counter-based generator of every draw, on caller-given counters and
+// keys (msp_philox of include/msp.h)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_philox_blocks(int64_t n, const uint32_t* __restrict__ ctr,
+                                const uint32_t* __restrict__ key, uint32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+        msp::philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+        out[4 * i] = c[0];
+        out[4 * i + 1] = c[1];
+        out[4 * i + 2] = c[2];
+        out[4 * i + 3] = c[3];
+    }
+}
+}  // namespace
+
+extern "C" msp_status msp_philox(int64_t n, const uint32_t* ctr, const uint32_t* key,
+                                 uint32_t* out, void* stream) {
+    if (n < 0) {
+        msp::set_last_error("msp_philox: n must not be negative");
+        return MSP_ERR_INVALID_ARG;
+    }
+    if (n == 0) return MSP_OK;
+    if (!ctr || !key || !out) {
+        msp::set_last_error("msp_philox: null pointer");
+        return MSP_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    k_philox_blocks<<<msp::grid_for(n, 256), 256, 0, s>>>(n, ctr, key, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        msp::set_last_error(cudaGetErrorString(e));
+        return MSP_ERR_CUDA;
+    }
+    msp::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    msp::set_last_error("");
+    return MSP_OK;
+}

@@ -33,7 +33,8 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_step_graph_capture", "msp_step_graph_launch", "msp_step_graph_finish",
             "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
-            "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait")
+            "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait",
+            "msp_philox")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -147,6 +148,8 @@ def load(path: str = LIB_PATH):
         L.msp_update_synapses.argtypes = [vp, i64, u64] + [vp] * 7 + [i64] + [vp] * 3 + [vp]
         L.msp_append_synapses.argtypes = [vp, vp, i64] + [vp] * 7 + [i64, vp]
         L.msp_selftest_bounded_wait.argtypes = [vp, vp]
+        L.msp_philox.argtypes = [i64, vp, vp, vp, vp]
+        L.msp_philox.restype = C.c_int
         for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
                      "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
@@ -468,13 +471,49 @@ def direct_noalloc(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, out=None
     """msp_direct_noalloc: all-pairs attraction without any device allocation
     by the library, for callers that cannot allocate (n <= NOALLOC_MAX_N).
     `out` (n float32, CUDA) may be preallocated by the caller."""
+    if pos.dim() != 2 or pos.shape[0] != 3:
+        raise ValueError("pos must be a (3, n) tensor")
     n = int(pos.shape[1])
-    xs = [pos[d].contiguous() for d in range(3)]
-    u = out if out is not None else torch.empty(n, dtype=torch.float32, device=pos.device)
-    _check(load().msp_direct_noalloc(n, *[_ptr(t) for t in xs], _ptr(type_), _ptr(vac_axon),
-                                     _ptr(vac_dend_e), _ptr(vac_dend_i), float(sigma), _ptr(u),
-                                     _stream(stream)))
+    dev = pos.device
+    if dev.type != "cuda" or pos.dtype != torch.float32:
+        raise TypeError("pos must be a float32 CUDA tensor")
+    counts = [type_.contiguous(), vac_axon.contiguous(), vac_dend_e.contiguous(),
+              vac_dend_i.contiguous()]
+    for t in counts:
+        if t.device != dev or t.dtype != torch.uint8 or t.numel() != n:
+            raise TypeError(f"counts must be uint8 tensors of {n} entries on {dev}")
+    if out is not None and (out.device != dev or out.dtype != torch.float32
+                            or out.numel() != n or not out.is_contiguous()):
+        raise TypeError(f"out must be a contiguous float32 tensor of {n} entries on {dev}")
+    # the library launches on the current device: make it pos's device, and
+    # take that device's current stream unless one is given
+    with torch.cuda.device(dev):
+        xs = [pos[d].contiguous() for d in range(3)]
+        u = out if out is not None else torch.empty(n, dtype=torch.float32, device=dev)
+        _check(load().msp_direct_noalloc(n, *[_ptr(t) for t in xs], *[_ptr(t) for t in counts],
+                                         float(sigma), _ptr(u),
+                                         _stream(stream if stream is not None else
+                                                 torch.cuda.current_stream(dev))))
     return u
+
+
+def philox(ctr, key, stream=None):
+    """msp_philox: the library's device Philox4x32-10 on (n, 4) uint32 counters
+    and (n, 2) uint32 keys (CUDA int32 tensors holding the uint32 bits);
+    returns the (n, 4) output blocks (int32 tensor holding the bits)."""
+    ctr = ctr.contiguous()
+    key = key.contiguous()
+    if ctr.dim() != 2 or ctr.shape[1] != 4 or key.shape != (ctr.shape[0], 2):
+        raise ValueError("ctr must be (n, 4) and key (n, 2)")
+    for t in (ctr, key):
+        if not t.is_cuda or t.dtype != torch.int32 or t.device != ctr.device:
+            raise TypeError("ctr and key must be int32 CUDA tensors on one device")
+    out = torch.empty_like(ctr)
+    with torch.cuda.device(ctr.device):
+        _check(load().msp_philox(int(ctr.shape[0]), _ptr(ctr), _ptr(key), _ptr(out),
+                                 _stream(stream if stream is not None else
+                                         torch.cuda.current_stream(ctr.device))))
+    return out
 
 
 def batch_layout(pos, offsets, sigma, cutoff, leaf_capacity, stream=None):

@@ -26,3 +26,25 @@ def oracle_mod():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def boundary_report(request):
+    """Per parity case: partner draws, draws the oracle flags as within its
+    band of a CDF boundary, and partners that differ from the oracle's
+    (printed in the run's summary)."""
+    if not hasattr(request.config, "_msp_boundary"):
+        request.config._msp_boundary = {}
+    return request.config._msp_boundary
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    rep = getattr(config, "_msp_boundary", None)
+    if not rep:
+        return
+    terminalreporter.write_sep("-", "boundary draws per parity case (oracle band)")
+    for name, r in sorted(rep.items()):
+        terminalreporter.write_line(
+            f"{name}: band {r['band']:.0e}, draws {r['draws']}, flagged draws "
+            f"{r['boundary_draws']}, flagged elements {r['flagged']}/{r['elements']}, "
+            f"partners differing {r['differ']} (all flagged: {r['differ_flagged']})")

@@ -221,3 +221,48 @@ def test_graph_replays_of_a_batch_equal_eager_steps():
         assert np.array_equal(x, y)
     for key in ("pre", "post", "typ"):
         assert np.array_equal(lg[key], le[key])
+
+
+def _oracle_steps(w, first, k_steps):
+    """The oracle's plasticity steps first .. first+k_steps-1 (walk, tree,
+    attraction, selection, commit): per-step synapse counts, the vacancy state
+    after each step and whether any draw of the step was within the oracle's
+    band of a CDF boundary."""
+    from oracle import oracle as O
+    a, e, i = w.vac_axon.copy(), w.vac_dend_e.copy(), w.vac_dend_i.copy()
+    o = O.Oracle(w.params)
+    counts, states, flagged = [], [], []
+    for k in range(first, first + k_steps):
+        a, e, i = O.vacancy_walk(w.params["seed"], k, a, e, i)
+        o.build_tree(w.pos, w.type, a, e, i)
+        o.attraction()
+        r = o.select_partners(k)
+        a, e, i = O.commit_synapses(r["syn_pre"], r["syn_post"], r["syn_type"], a, e, i)
+        counts.append(r["n_syn"])
+        states.append((a.copy(), e.copy(), i.copy()))
+        flagged.append(bool(r["near_boundary"].any()))
+    return counts, states, flagged
+
+
+@pytest.mark.parametrize("case", ["clustered_4k_c32", "bench_plan_2x16k"])
+def test_graph_replays_equal_the_oracle_steps(case):
+    """K replays of the captured step (walk, tree, attraction, selection,
+    commit) against the oracle's K-step loop: the synapse count of every step
+    and the vacancy state after the run, bit for bit.  Runs can only part at a
+    draw the oracle flags as within its band of a CDF boundary; the comparison
+    covers the steps before the first such step (required to be most of them)."""
+    if case == "clustered_4k_c32":
+        w, k_steps = W.clustered_small(1, 4096, seed=21, leaf_capacity=32, cutoff=3.25,
+                                       rho_max=0.0), 8
+    else:
+        w, k_steps = W.clustered_small(2, 16_384, seed=22, leaf_capacity=256, cutoff=3.25,
+                                       rho_max=0.0, m2l_min_pairs=0), 4
+    first = 5
+    oc, ostates, oflag = _oracle_steps(w, first, k_steps)
+    upto = oflag.index(True) if True in oflag else k_steps
+    assert upto >= k_steps // 2, f"boundary draws from step {first + upto} on"
+    gc, gstate, _, _, _ = _graph(w, first, k_steps)
+    assert gc[:upto] == oc[:upto]
+    if upto == k_steps:
+        for got, ref in zip(gstate, ostates[-1]):
+            assert np.array_equal(got, ref)

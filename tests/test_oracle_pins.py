@@ -352,6 +352,160 @@ def test_pair_table_total_equals_weighted_attraction(oracle_mod, centre_mode):
         assert pr[name][0] == pytest.approx(ref, rel=1e-10)
 
 
+def _sorted_views(o, w):
+    _, perm = o.keys()
+    return (w.pos[:, perm].astype(np.float64), w.vac_axon[perm].astype(np.float64),
+            w.type[perm].astype(int),
+            (w.vac_dend_e[perm].astype(np.float64), w.vac_dend_i[perm].astype(np.float64)))
+
+
+@pytest.mark.parametrize("seed", [3, 19])
+def test_pair_table_every_pair_equals_point_set_sums(oracle_mod, seed):
+    """Near field only and no pair beyond the cutoff (the cube's diagonal is
+    4.6 sigma < 5 sigma): every pair of the table, split or leaf pair, holds
+    W(X, Y) = sum_{t in X} a_t sum_{s in Y, s != t} w_s K(t, s) of its two point
+    sets (Algorithm 1's box attraction; a split pair is the sum of its child
+    block, so a slip in the block indexing fails here)."""
+    w = W.uniform_cube(320, 2000.0, seed=seed, leaf_capacity=4, rho_max=0.0, cutoff=5.0)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    nd, pr = o.nodes(), o.pairs()
+    x, a, chs, wt = _sorted_views(o, w)
+    n_split = 0
+    for q in range(len(pr["X"])):
+        X, Y, kind = pr["X"][q], pr["Y"][q], pr["kind"][q]
+        rx = (nd["first"][X], nd["first"][X] + nd["count"][X])
+        ry = (nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+        n_split += kind == 0
+        for ch, key in ((0, "wE"), (1, "wI")):
+            ref = _point_set_w(x, a, wt[ch], chs, ch, rx, ry)
+            if kind == 3:        # pruned only for an empty side here
+                assert pr[key][q] == 0.0 and ref == 0.0
+            else:
+                assert pr[key][q] == pytest.approx(ref, rel=1e-12, abs=1e-300)
+    assert n_split > 20
+
+
+def test_pair_table_with_pruning_is_bracketed_by_point_set_sums(oracle_mod):
+    """With pruning at cutoff*sigma a pair's W lies between the point-set sum
+    over pairs closer than the cutoff and the full point-set sum: a pruned box
+    pair drops only point pairs at least the cutoff apart, and a kept leaf pair
+    keeps all of its point pairs."""
+    w = W.clustered_small(1, 900, seed=23, leaf_capacity=6, rho_max=0.0, cutoff=1.5)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    assert o.stats()["p2p_pairs"] > 0
+    nd, pr = o.nodes(), o.pairs()
+    x, a, chs, wt = _sorted_views(o, w)
+    rc2 = (1.5 * 750.0) ** 2
+    strict = 0
+    for q in np.nonzero(pr["kind"] != 3)[0][::3]:
+        X, Y = pr["X"][q], pr["Y"][q]
+        t = np.arange(nd["first"][X], nd["first"][X] + nd["count"][X])
+        s = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+        d2 = ((x[:, t, None] - x[:, None, s]) ** 2).sum(0)
+        for ch, key in ((0, "wE"), (1, "wI")):
+            k = np.exp(-d2 / 750.0 ** 2) * wt[ch][None, s] * (a[t] * (chs[t] == ch))[:, None]
+            k[t[:, None] == s[None, :]] = 0.0
+            lo, hi = k[d2 < rc2].sum(), k.sum()
+            assert lo * (1 - 1e-12) <= pr[key][q] <= hi * (1 + 1e-12) + 1e-300
+            strict += lo < hi
+    assert strict > 0
+
+
+def _cramer_f(rho, p=None, nmax=60):
+    return sum(rho ** n / math.sqrt(math.factorial(n)) for n in range(nmax if p is None else p))
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_far_pairs_within_the_truncation_bound(oracle_mod, p):
+    """Every translated pair's W(X, Y) is within the truncation bound of its
+    point-set sum.  Per point pair the Hermite (Eq. 7) and Taylor (Eq. 6)
+    truncations together err by at most a_t w_s kappa^3 (F(rho)^6 - F_p(rho)^6),
+    rho = 2 max |coordinate offset from the box centre| / sigma, F_p(rho) =
+    sum_{n<p} rho^n / sqrt(n!): Cramer's inequality |h_n(x)| <= kappa
+    2^{n/2} sqrt(n!) and (n+m)! <= 2^{n+m} n! m! bound each dropped term."""
+    w = W.uniform_cube(400, 1000.0, seed=29, leaf_capacity=2, rho_max=0.12, cutoff=3.0, p=p)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    nd, pr = o.nodes(), o.pairs()
+    x, a, chs, wt = _sorted_views(o, w)
+    cent = nd["centroids"]
+    kappa = 1.0865
+    far = np.nonzero(pr["kind"] == 1)[0]
+    assert len(far) > 100
+    worst = 0.0
+    for q in far[:: max(1, len(far) // 400)]:
+        X, Y = pr["X"][q], pr["Y"][q]
+        t = np.arange(nd["first"][X], nd["first"][X] + nd["count"][X])
+        s = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+        off = max(np.abs(x[:, t] - cent[X, :3, None]).max(), np.abs(x[:, s] - cent[Y, 3:, None]).max())
+        rho = 2.0 * off / 750.0
+        tail = kappa ** 3 * (_cramer_f(rho) ** 6 - _cramer_f(rho, p) ** 6)
+        d2 = ((x[:, t, None] - x[:, None, s]) ** 2).sum(0)
+        for ch, key in ((0, "wE"), (1, "wI")):
+            at = a[t] * (chs[t] == ch)
+            ref = float((at[:, None] * np.exp(-d2 / 750.0 ** 2) * wt[ch][None, s]).sum())
+            bound = at.sum() * wt[ch][s].sum() * tail
+            assert abs(pr[key][q] - ref) <= bound * (1 + 1e-9) + 1e-12 * ref
+            if bound > 0:
+                worst = max(worst, abs(pr[key][q] - ref) / bound)
+    assert worst > 0      # the expansions are in use and not exact
+
+
+def test_leaf_draw_truncation_moves_probabilities_within_bound(oracle_mod):
+    """Inside a chosen leaf the draw weights drop sources beyond cutoff*sigma
+    (the pruning radius), while u and W keep every source of a kept leaf pair.
+    Over the leaf pairs of a plan, the distributions with and without the
+    truncation differ per source by at most m * exp(-cutoff^2) * w_max / total
+    (m sources dropped) and in total variation by (dropped weight) / total;
+    and a dropped source has probability at most exp(-cutoff^2) w_max / total
+    untruncated.  The oracle's draws never pick a dropped source."""
+    cutoff = 1.25
+    w = W.clustered_small(1, 1500, seed=31, leaf_capacity=48, rho_max=0.0, cutoff=cutoff)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(*w.arrays())
+    o.attraction()
+    nd, pr = o.nodes(), o.pairs()
+    x, a, chs, wt = _sorted_views(o, w)
+    _, perm = o.keys()
+    inv = np.argsort(perm)
+    e_c2 = math.exp(-cutoff ** 2)
+    n_dropped = 0
+    for q in np.nonzero(pr["kind"] == 2)[0][::5]:
+        X, Y = pr["X"][q], pr["Y"][q]
+        s = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
+        for t in range(nd["first"][X], nd["first"][X] + nd["count"][X]):
+            if a[t] == 0:
+                continue
+            wv = wt[chs[t]][s]
+            d2 = ((x[:, s] - x[:, t:t + 1]) ** 2).sum(0)
+            full = wv * np.exp(-d2 / 750.0 ** 2)
+            full[s == t] = 0.0
+            trunc = np.where(d2 < (cutoff * 750.0) ** 2, full, 0.0)
+            if trunc.sum() <= 1e-30:
+                continue
+            drop = (full > 0) & (trunc == 0)
+            m = int(drop.sum())
+            n_dropped += m
+            pf, pt = full / full.sum(), trunc / trunc.sum()
+            wmax = wv.max()
+            assert np.all(np.abs(pf - pt) <= m * e_c2 * wmax / full.sum() + 1e-15)
+            assert np.all(pf[drop] <= e_c2 * wmax / full.sum() + 1e-15)
+            assert 0.5 * np.abs(pf - pt).sum() == pytest.approx(full[drop].sum() / full.sum(),
+                                                               rel=1e-9, abs=1e-15)
+    assert n_dropped > 0
+    r = o.select_partners(2)
+    owner = np.repeat(np.arange(w.n), w.vac_axon)
+    ok = r["partner"] >= 0
+    tt, ss = inv[owner[ok]], inv[r["partner"][ok]]
+    d2 = ((x[:, tt] - x[:, ss]) ** 2).sum(0)
+    assert np.all(d2 < (cutoff * 750.0) ** 2)
+
+
 def test_kernel_symmetry(oracle_mod):
     """sum_t a_t u_w(t) = sum_s w_s u_a(s): the Gaussian is symmetric."""
     w = W.uniform_cube(700, 8000.0, seed=13)
@@ -418,15 +572,32 @@ def _leaf_of(nd, point):
     return k
 
 
+def _point_set_w(x, a, wt, ch_of, ch, X_rng, Y_rng):
+    """W(X, Y) of channel ch written out from the point sets (Algorithm 1's box
+    attraction, Eq. 8 summed): sum over targets t in X of channel ch of
+    a_t sum_{s in Y, s != t} w_s K(t, s), sorted-order index ranges."""
+    t = np.arange(*X_rng)
+    t = t[(ch_of[t] == ch) & (a[t] > 0)]
+    if len(t) == 0 or Y_rng[1] <= Y_rng[0]:
+        return 0.0
+    s = np.arange(*Y_rng)
+    d2 = ((x[:, t, None] - x[:, None, s]) ** 2).sum(0)
+    k = np.exp(-d2 / 750.0 ** 2) * wt[None, s]
+    k[t[:, None] == s[None, :]] = 0.0
+    return float((a[t, None] * k).sum())
+
+
 def _exact_partner_distribution(o, w, t_orig):
     """Product of the per-level choice probabilities of Algorithm 2 along every
-    path of Algorithm 1, times the leaf probability, for one neuron."""
-    nd, pr = o.nodes(), o.pairs()
+    path of Algorithm 1, times the leaf probability, for one neuron.  The
+    candidate attractions are computed here from the boxes' point sets, not
+    read from the oracle's pair table, so an indexing slip in the table or in
+    the descent shows up as a wrong distribution."""
+    nd = o.nodes()
     keys, perm = o.keys()
     inv = np.argsort(perm)
     t = int(inv[t_orig])
     ch = int(w.type[t_orig])
-    wkey = "wI" if ch else "wE"
     leaf = _leaf_of(nd, t)
     anc = set()
     k = leaf
@@ -435,7 +606,15 @@ def _exact_partner_distribution(o, w, t_orig):
         k = nd["parent"][k]
     x = w.pos[:, perm].astype(np.float64)
     wt = (w.vac_dend_i if ch else w.vac_dend_e)[perm].astype(np.float64)
+    a_s = w.vac_axon[perm].astype(np.float64)
+    ch_s = w.type[perm].astype(int)
     out = np.zeros(w.n)
+
+    def rng(k):
+        return (nd["first"][k], nd["first"][k] + nd["count"][k])
+
+    def bw(X, Y):
+        return _point_set_w(x, a_s, wt, ch_s, ch, rng(X), rng(Y))
 
     def is_leaf(k):
         return nd["child_first"][k] < 0
@@ -443,7 +622,7 @@ def _exact_partner_distribution(o, w, t_orig):
     def kids(k):
         return list(range(nd["child_first"][k], nd["child_first"][k] + nd["nchild"][k]))
 
-    def visit(X, Y, q, prob):
+    def visit(X, Y, prob):
         if is_leaf(X) and is_leaf(Y):
             ys = np.arange(nd["first"][Y], nd["first"][Y] + nd["count"][Y])
             d2 = ((x[:, ys] - x[:, t:t + 1]) ** 2).sum(0)
@@ -452,26 +631,23 @@ def _exact_partner_distribution(o, w, t_orig):
             if ws.sum() > 1e-30:
                 out[ys] += prob * ws / ws.sum()
             return
-        cf = pr["child_first"][q]
         if is_leaf(X):
-            wk = np.maximum(pr[wkey][cf: cf + nd["nchild"][Y]], 0)
+            wk = np.array([bw(X, Yc) for Yc in kids(Y)])
             for kk, Yc in enumerate(kids(Y)):
                 if wk[kk] > 0:
-                    visit(X, Yc, cf + kk, prob * wk[kk] / wk.sum())
+                    visit(X, Yc, prob * wk[kk] / wk.sum())
             return
-        i = [j for j, Xc in enumerate(kids(X)) if Xc in anc][0]
-        Xc = kids(X)[i]
+        Xc = [c for c in kids(X) if c in anc][0]
         if is_leaf(Y):
-            if pr[wkey][cf + i] > 0:
-                visit(Xc, Y, cf + i, prob)
+            if bw(Xc, Y) > 0:
+                visit(Xc, Y, prob)
             return
-        ny = nd["nchild"][Y]
-        wk = np.maximum(pr[wkey][cf + i * ny: cf + (i + 1) * ny], 0)
+        wk = np.array([bw(Xc, Yc) for Yc in kids(Y)])
         for kk, Yc in enumerate(kids(Y)):
             if wk[kk] > 0:
-                visit(Xc, Yc, cf + i * ny + kk, prob * wk[kk] / wk.sum())
+                visit(Xc, Yc, prob * wk[kk] / wk.sum())
 
-    visit(0, 0, 0, 1.0)
+    visit(0, 0, 1.0)
     res = np.zeros(w.n)
     res[perm] = out
     return res
@@ -605,6 +781,21 @@ def test_vacancy_walk_and_commit(oracle_mod):
     a2, e2, i2 = (v.astype(int) for v in (a2, e2, i2))
     assert a3[0] == max(a2[0] - 2, 0) and a3[3] == max(a2[3] - 1, 0)
     assert e3[5] == max(e2[5] - 2, 0) and i3[6] == max(i2[6] - 1, 0)
+
+
+def test_philox_known_answer_vectors(oracle_mod):
+    """The oracle's Philox4x32-10 reproduces the generator's published
+    known-answer vectors (golden/philox4x32_10_kat.json, Salmon et al. SC'11)."""
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.json")) as f:
+        kat = json.load(f)
+    for v in kat["vectors"]:
+        ctr = [int(h, 16) for h in v["counter"]]
+        key = [int(h, 16) for h in v["key"]]
+        out = oracle_mod.philox(ctr, key)
+        assert [int(o) for o in out] == [int(h, 16) for h in v["output"]]
+    # the uniform of every draw: the top 53 bits of output words 0 and 1
+    o = [int(h, 16) for h in kat["vectors"][0]["output"]]
+    assert oracle_mod.uniform(0, 0, 0, 0) == ((o[0] << 32 | o[1]) >> 11) * 2.0 ** -53
 
 
 def test_philox_statistics(oracle_mod):
