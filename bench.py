@@ -13,6 +13,8 @@ counts uniform in {0..3} (synthetic, seeded).
 
   python bench.py [--gpus N --steps K --warmup W]          # this library
   python bench.py --impl reference [...]                    # the FP64 CPU oracle
+  python bench.py --workload batched_256|gradient_262k|simulation_1m
+  python bench.py --profile-case NAME [--steps K]           # small named cases for ncu
 Multi-GPU runs are independent replicas (one network per GPU, no exchange).
 Prints one JSON line.
 """
@@ -33,13 +35,27 @@ sys.path.insert(0, ROOT)
 METRIC = "plasticity-step neurons/s at 1M neurons, FMM vs direct on GB300, rel.err<=1e-4"
 UNIT = "neurons/s"
 SM_COUNT = 152
-# One near-field interaction is one EX2 and four FP32 operations (three FMAs
-# for the exponent, one add).  The EX2 unit delivers 30.25 results per SM per
-# clock (measured with paper_2301_10570_gb300/probes/sfu_rate.cu, 16 blocks of
-# 128 threads per SM), the FP32 pipe 128 operations (32 interactions), and with
-# the FMAs and adds paired over two sources an interaction takes about 3.5
-# issue slots of 128 per clock (36 interactions): the EX2 unit binds.
+# The near field's unit of work is one target-source interaction.  Its work
+# count in the design is 8 FP32 operations (3 differences, 3 products or FMAs
+# for r^2, the scale, the accumulate) and 1 EX2; the FP32 pipe takes 128
+# operations per SM per clock, the EX2 unit 30.25 results (measured with a
+# dedicated kernel, 16 blocks of 128 threads per SM; profiles/sfu_rate_gb300.md),
+# so at that count the FP32 pipe binds: 16 interactions per SM per clock.  The
+# kernel evaluates an interaction with 4 FP32 operations (the expanded
+# exponent), which leaves the EX2 unit as its own binding unit: 30.25 per SM
+# per clock.  Both bases are reported.
 EX2_PER_SM_CLK = 30.25
+FP32_PER_SM_CLK = 128
+FP32_PER_INTERACTION = 8
+# algorithmic DRAM bytes of one near-field launch: per neuron its packed point
+# (16 B) and log-weights (8 B) read once and u (4 B) written; per near-field
+# pair its source range (8 B), list entry (4 B) and W slot (8 B)
+NF_BYTES_PER_NEURON = 28
+NF_BYTES_PER_PAIR = 20
+# the fastest plan with translated pairs found for the 1M clustered network
+# (profiles/autotune_clustered_1m.md): timed beside the headline
+FMM_TRANSLATED_PLAN = dict(leaf_capacity=64, cutoff=3.25, rho_max=0.25, p=6, m2l_min_pairs=512)
+FP64_SAMPLE = 4096
 
 
 def parse():
@@ -50,6 +66,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the records beside the headline (batched, gradient, translated "
+                         "plan, full rebuild)")
     ap.add_argument("--autotune", action="store_true",
                     help="rerun the plan chooser on this workload and bench its plan")
     ap.add_argument("--workload", default="clustered_1m",
@@ -59,6 +78,12 @@ def parse():
                          "the derivatives of the attraction at 262,144 clustered neurons; "
                          "simulation_1m: the model's simulation loop (100 neuron steps and one "
                          "connectivity update per cycle) on the 1M clustered network")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run a small named case for a profiler and print the library's "
+                         "statistics (no timing)")
+    ap.add_argument("--case-p", type=int, default=4, help="translations_256k: expansion order")
+    ap.add_argument("--case-centre-mode", type=int, default=0,
+                    help="translations_256k: 0 centroids, 1 geometric centres")
     return ap.parse_args()
 
 
@@ -135,6 +160,43 @@ def measured_peaks():
         return {}
 
 
+def near_field_roofline(inter, nf_ms, n, n_p2p, traffic=None):
+    """Roofline of the near-field kernel for `inter` interactions in `nf_ms`:
+    the design's work count (8 FP32 + 1 EX2 per interaction, FP32 binds) as
+    the primary basis, the EX2 unit (the kernel's own ceiling) beside it, and
+    the algorithmic bytes over the measured copy bandwidth."""
+    peaks = measured_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    p_fp32 = SM_COUNT * FP32_PER_SM_CLK * clk           # FP32 operations / s
+    p_ex2 = SM_COUNT * EX2_PER_SM_CLK * clk              # EX2 results / s
+    nbytes = NF_BYTES_PER_NEURON * n + NF_BYTES_PER_PAIR * n_p2p
+    t = {"fp32": FP32_PER_INTERACTION * inter / p_fp32, "ex2": inter / p_ex2,
+         "hbm": nbytes / hbm}
+    bound_t = max(t.values())
+    sec = nf_ms / 1e3
+    achieved = inter / sec / 1e9 if sec > 0 else 0.0
+    peak = p_fp32 / FP32_PER_INTERACTION / 1e9
+    peak_ex2 = p_ex2 / 1e9
+    return {"kernel": "k_near_field", "bound": "alu", "achieved": round(achieved, 1),
+            "peak": round(peak, 1), "unit": "G interactions/s",
+            "frac": round(achieved / peak, 4) if peak else 0.0,
+            "traffic": traffic, "near_field_ms": round(nf_ms, 3),
+            "interactions_per_launch": int(inter),
+            "algorithmic_bytes_per_launch": int(nbytes),
+            "roofline_ms": {k: round(1e3 * v, 4) for k, v in t.items()},
+            "frac_of_roofline_time": round(bound_t / sec, 4) if sec > 0 else 0.0,
+            "peak_basis": (f"design work count 8 FP32 + 1 EX2 per interaction: FP32 pipe "
+                           f"{SM_COUNT} SMs x {FP32_PER_SM_CLK}/clk x {clk / 1e6:.0f} MHz / 8 "
+                           f"(binds: EX2 {EX2_PER_SM_CLK}/clk measured, bytes over the "
+                           f"measured copy bandwidth far below)"),
+            "ex2_basis": {"peak": round(peak_ex2, 1),
+                          "frac": round(achieved / peak_ex2, 4) if peak_ex2 else 0.0,
+                          "note": "the kernel's own ceiling: it evaluates an interaction with "
+                                  "4 FP32 operations (expanded exponent), so its EX2 unit "
+                                  "binds"}}
+
+
 # -- clocks ------------------------------------------------------------------
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -147,7 +209,7 @@ class Clocks:
         self.dev = device_index
 
     def start(self):
-        """Start sampling every 50 ms; returns once the sampler has written its
+        """Start sampling every 20 ms; returns once the sampler has written its
         first line (at most 3 s), so that it is live when the timed region
         begins, and drops that line (taken before the region)."""
         self.skip = 0
@@ -155,7 +217,7 @@ class Clocks:
         self.f = os.fdopen(fd, "w")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -216,20 +278,23 @@ class Clocks:
 
 # -- the derivative pass (config 4) ------------------------------------------------
 GRAD_METRIC = "gradient-pass neurons/s (u, du/dsigma, dL/dw) at 262k clustered neurons on GB300"
+GRAD_PLAN = dict(leaf_capacity=128, cutoff=5.0, rho_max=0.0, p=4, m2l_min_pairs=0)
+GRAD_DESC = ("gradient_262k: 16 Gaussian clusters x 16,384 neurons (std 1500 um, cluster spacing "
+             "of clustered_1m), sigma 750 um, cutoff 5 sigma, pair lists from a tree with every "
+             "count 1; outputs u, du/dsigma, dL/dw^E, dL/dw^I")
 
 
-def run_gradient(args, rank, world):
+def gradient_passes(steps, warmup, dev, timed_clocks=False):
     """u, du/dsigma and the weight gradient of L = sum g u over the leaf pairs
     of a tree built with every count 1 (cutoff 5 sigma, no translations), at
-    the workload's counts; timed per pass with CUDA events, L2 flushed."""
+    the workload's counts; timed per pass with CUDA events, L2 flushed.
+    Returns (neurons, per-pass ms list, launches, clocks, interactions)."""
     import numpy as np
     import torch
 
     from paper_2301_10570_gb300 import msp, replicas, workloads as W
-    dev = torch.device("cuda", torch.cuda.current_device())
     # leaf capacity 128: fastest of 64 / 128 / 192 for this pass (7.2 ms vs 11.1 / 7.9)
-    plan = dict(leaf_capacity=128, cutoff=5.0, rho_max=0.0, p=4, m2l_min_pairs=0)
-    w = W.clustered_small(16, 16_384, seed=15, **plan)
+    w = W.clustered_small(16, 16_384, seed=15, **GRAD_PLAN)
     n = w.n
     pos, t, a, e, i = msp.to_device(w, dev)
     ones = torch.ones_like(a)
@@ -238,26 +303,26 @@ def run_gradient(args, rank, world):
     g.attraction()
     gv = torch.from_numpy(np.random.default_rng(6).normal(size=n)).float().to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.attraction_grad(t, a, e, i, g=gv)
     torch.cuda.synchronize()
     replicas.barrier()
     launches0 = g.stats()["kernel_launches"]
-    clocks = Clocks(dev.index)
-    clocks.start()
+    clocks = Clocks(dev.index) if timed_clocks else None
+    if clocks:
+        clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for k in range(args.steps):
+          for _ in range(steps)]
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record()
         g.attraction_grad(t, a, e, i, g=gv)
         ev[k][1].record()
     torch.cuda.synchronize()
     replicas.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     launches = g.stats()["kernel_launches"] - launches0
     ms_list = [x.elapsed_time(y) for x, y in ev]
-    agg = replicas.aggregate_throughput(n, sum(ms_list) / len(ms_list), dev)
     # exact interaction count: every target with a vacant axon against the
     # sources of its leaf's partner leaves (self excluded), once forward and
     # once transposed
@@ -269,22 +334,27 @@ def run_gradient(args, rank, world):
     first = tr["first"]
     nact = np.array([act_sorted[first[k]:first[k] + cnt[k]].sum() for k in range(len(cnt))])
     fwd = int((nact[X] * cnt[Y]).sum() - nact[X[X == Y]].sum())
-    inter = 2 * fwd
+    g.close()
+    return n, ms_list, launches, clk, 2 * fwd
+
+
+def run_gradient(args, rank, world):
+    from paper_2301_10570_gb300 import replicas
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, ms_list, launches, clk, inter = gradient_passes(args.steps, args.warmup, dev, True)
+    agg = replicas.aggregate_throughput(n, sum(ms_list) / len(ms_list), dev)
     ms = agg["ms"]
     achieved = inter / (ms / 1e3) / 1e9
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * EX2_PER_SM_CLK * sm_max * 1e6 / 1e9
-    g.close()
     return {"metric": GRAD_METRIC, "value": agg["per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "gradient_262k: 16 Gaussian clusters x 16,384 neurons "
-                                   "(std 1500 um, cluster spacing of clustered_1m), sigma 750 um, "
-                                   "cutoff 5 sigma, pair lists from a tree with "
-                                   "every count 1; outputs u, du/dsigma, dL/dw^E, dL/dw^I",
-                       "plan": plan, "parallelism": f"replicas x{world}",
+            "config": {"workload": GRAD_DESC, "plan": GRAD_PLAN,
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MB write) between timed passes",
                        "timing": "CUDA events per pass, mean over passes",
                        "median_ms_per_step": round(statistics.median(ms_list), 3)},
@@ -415,6 +485,70 @@ def run_simulation(args, rank, world):
 
 
 # -- our arm -------------------------------------------------------------------
+def _timed_replays(g, steps, flush):
+    """`steps` graph replays, one per CUDA-event pair, L2 flushed between them
+    (untimed); a replay that halted is finished eagerly and the steps timed
+    again.  Returns (per-step ms, next step index, halt bits)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    halted = 0
+    for attempt in range(2):
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record()
+            g.step_graph_launch(1)
+            ev[i][1].record()
+        nxt, halted = g.step_graph_finish()
+        if not halted:
+            break
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], nxt, halted
+
+
+def _fp64_targets(job):
+    """One host core: the oracle's FP64 brute force (Eq. 8) for some targets."""
+    arrays, sigma, idx = job
+    from oracle import oracle as O
+    return O.direct(*arrays, sigma, targets=idx)
+
+
+def fp64_reference(w, idx, cores=None):
+    """FP64 brute force for the targets idx, split over the host cores (one
+    spawned process each)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from oracle import oracle as O
+    O.build()
+    cores = cores or max(1, min(os.cpu_count() or 1, 16))
+    parts = [p for p in np.array_split(np.asarray(idx), cores) if len(p)]
+    jobs = [(w.arrays(), w.params["sigma"], p) for p in parts]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_fp64_targets, jobs, chunksize=1)
+    return np.concatenate(res)
+
+
+def error_report(u, ref):
+    """Accuracy of u against ref (same targets): the bar's masked relative
+    error (targets with ref >= 1e-6 max ref), with the count of targets it
+    leaves out, the normwise errors, the largest relative error over every
+    target with ref > 0, and the targets whose u is 0 while ref > 0."""
+    import numpy as np
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    pos = ref > 0
+    m = ref >= 1e-6 * ref.max()
+    d = np.abs(u - ref)
+    return {"max_rel_err": float(np.max(d[m] / ref[m])) if m.any() else 0.0,
+            "targets": int(len(ref)), "targets_below_mask": int((pos & ~m).sum()),
+            "max_abs_err_over_max_ref": float(d.max() / ref.max()) if ref.max() > 0 else 0.0,
+            "l2_rel_err": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) if pos.any() else 0.0,
+            "max_rel_err_all_positive": float(np.max(d[pos] / ref[pos])) if pos.any() else 0.0,
+            "zero_where_positive": int(((u == 0) & pos).sum())}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -461,34 +595,41 @@ def run_ours(args, rank, world):
     clocks = Clocks(dev.index)
     clocks.start()
     launches0 = g.stats()["kernel_launches"]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     t_wall = time.perf_counter()
-    halted = 0
-    for attempt in range(2):
-        for i in range(args.steps):
-            flush.zero_()                  # L2 flushed between timed steps (untimed)
-            ev[i][0].record()
-            g.step_graph_launch(1)
-            ev[i][1].record()
-        nxt, halted = g.step_graph_finish()
-        if not halted:                     # a halted step was finished eagerly: time again
-            break
-    first_timed = nxt - args.steps
-    torch.cuda.synchronize()
+    step_ms, nxt, halted = _timed_replays(g, args.steps, flush)
     replicas.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     st = g.stats()
     launches = st["kernel_launches"] - launches0
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     agg = replicas.aggregate_throughput(n, sum(step_ms) / len(step_ms), dev)
     ms = agg["ms"]
     value = agg["per_s"]
+    first_timed = nxt - args.steps
     hist = gout["history"].cpu().numpy()
     synapses = [int(v) for v in hist[first_timed - args.warmup:nxt - args.warmup]]
-    nf_ms, inter = [st["near_field_ms"]], [st["p2p_interactions"]]
+    nf_ms, inter, n_p2p = st["near_field_ms"], st["p2p_interactions"], st["n_p2p"]
+
+    # the same step with the whole octree rebuilt in every replay (a1-a12 in
+    # full: Morton keys, radix sort, subdivision, aggregates)
+    full = None
+    if not args.no_extras:
+        g.build_tree(pos, typ, va, ve, vi)
+        g.attraction()
+        g.step_graph_set_full_build(True)
+        g.step_graph_capture(pos, typ, va, ve, vi, first_step=nxt)
+        kf = g.run_steps(nxt, args.warmup)
+        fms, nxt, fh = _timed_replays(g, args.steps, flush)
+        g.step_graph_set_full_build(False)
+        fst = g.stats()
+        full = {"ms_per_step": round(statistics.mean(fms), 3),
+                "median_ms_per_step": round(statistics.median(fms), 3),
+                "neurons_per_s": n / (statistics.mean(fms) / 1e3),
+                "near_field_ms": round(fst["near_field_ms"], 3), "graph_halted": int(fh),
+                "path": "whole step as one CUDA graph whose replays rebuild the octree "
+                        "(Morton keys, radix sort, subdivision, aggregates) from the positions "
+                        "every step"}
 
     # the same steps as separate calls, for comparison
     for k in range(nxt, nxt + 2):
@@ -504,77 +645,47 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         eager_ms.append(e0.elapsed_time(e1))
 
-    # End to end, the way a simulator that owns the vacancy dynamics drives the
-    # library: positions stay on the GPU (neurons do not move); every step
-    # uploads the vacancy state from pinned host memory, replays the step
-    # graph, and reads back the synapse count, the formed synapses and the
-    # updated vacancies.
-    g.build_tree(pos, typ, va, ve, vi)
-    g.attraction()
-    gout = g.step_graph_capture(pos, typ, va, ve, vi, first_step=10_000)
-    hv = [torch.empty(n, dtype=torch.uint8).pin_memory() for _ in range(3)]
-    for h, d in zip(hv, (va, ve, vi)):
-        h.copy_(d)
-    hsyn = [torch.empty(5 * n, dtype=torch.int32).pin_memory(),
-            torch.empty(5 * n, dtype=torch.int32).pin_memory(),
-            torch.empty(5 * n, dtype=torch.uint8).pin_memory()]
-    hns = torch.empty(1, dtype=torch.int64).pin_memory()
-
-    def host_step():
-        for h, d in zip(hv, (va, ve, vi)):
-            d.copy_(h, non_blocking=True)
-        g.step_graph_launch(1)
-        hns.copy_(gout["n_syn"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        k = int(hns[0])
-        for h, d in zip(hsyn, (gout["syn_pre"], gout["syn_post"], gout["syn_type"])):
-            h[:k].copy_(d[:k], non_blocking=True)
-        for h, d in zip(hv, (va, ve, vi)):
-            h.copy_(d, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return k
-
-    for _ in range(2):
-        host_step()
-    g.step_graph_finish()
+    # End to end through the C ABI's host-buffer call: every step copies the
+    # inputs (positions, types, vacant counts) up from pinned host memory, runs
+    # steps a1-a12 and copies u, the partners and the synapses back (the call
+    # replays its own graph of the step after the first call)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hp = pinned(w.pos)
+    ht, ha, he, hi = (pinned(a) for a in (w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i))
+    ne0 = int(ha.sum(dtype=np.int64))
+    hout = dict(u=pinned(np.zeros(n, np.float32)), partner=pinned(np.zeros(ne0, np.int32)),
+                syn_pre=pinned(np.zeros(ne0, np.int32)), syn_post=pinned(np.zeros(ne0, np.int32)),
+                syn_type=pinned(np.zeros(ne0, np.uint8)), n_syn=pinned(np.zeros(1, np.int64)))
+    for k in range(max(2, args.warmup)):
+        g.plasticity_step_host(k, hp, ht, ha, he, hi, out=hout)
+    torch.cuda.synchronize()
     e2e_t, d2h = [], []
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        k = host_step()
+        g.plasticity_step_host(100 + i, hp, ht, ha, he, hi, out=hout)
         e2e_t.append(time.perf_counter() - t0)
-        d2h.append(8 + 9 * k + 3 * n)
-    g.step_graph_finish()
+        d2h.append(8 + 4 * n + 4 * ne0 + 9 * int(hout["n_syn"][0]))
     e2e = replicas.aggregate_throughput(n, 1e3 * sum(e2e_t) / len(e2e_t), dev)
-    e2e_ms = e2e["ms"]
-
-    # the same through the host-buffer entry point (positions and counts
-    # uploaded, u, partners and synapses read back, every step)
-    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    hp = pinned(w.pos)
-    ht, ha, he, hi = (pinned(a) for a in (w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i))
-    ne = int(ha.sum(dtype=np.int64))
-    hout = dict(u=pinned(np.zeros(n, np.float32)), partner=pinned(np.zeros(ne, np.int32)),
-                syn_pre=pinned(np.zeros(ne, np.int32)), syn_post=pinned(np.zeros(ne, np.int32)),
-                syn_type=pinned(np.zeros(ne, np.uint8)), n_syn=np.zeros(1, np.int64))
-    g.plasticity_step_host(0, hp, ht, ha, he, hi, out=hout)
-    torch.cuda.synchronize()
-    hs_t = []
-    for i in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        g.plasticity_step_host(i, hp, ht, ha, he, hi, out=hout)
-        hs_t.append(time.perf_counter() - t0)
-    host_api_ms = 1e3 * sum(hs_t) / len(hs_t)
 
     # the attraction of the unwalked inputs (accuracy checks below)
     g.build_tree(pos, typ, va0, ve0, vi0)
     uf = g.attraction()
     torch.cuda.synchronize()
+    # the attraction alone, near field only (the plan's), for the translated
+    # plan's comparison
+    att_ms = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.attraction(out=u)
+        e1.record()
+        torch.cuda.synchronize()
+        att_ms.append(e0.elapsed_time(e1))
     # direct all-pairs evaluation of the attraction on the same GPU
-    direct = None
+    direct, ud = None, None
     if not args.no_direct and not batched:
         ud = torch.empty(n, dtype=torch.float32, device=dev)
         g.direct(out=ud)
@@ -586,29 +697,19 @@ def run_ours(args, rank, world):
         e1.record()
         torch.cuda.synchronize()
         d_ms = e0.elapsed_time(e1)
-        m = ud > 1e-6 * ud.max()
-        rel = ((uf[m] - ud[m]).abs() / ud[m]).max().item()
+        rep = error_report(uf.cpu().numpy(), ud.cpu().numpy())
         direct = {"direct_attraction_ms": round(d_ms, 3),
                   "direct_neurons_per_s": n / (d_ms / 1e3),
                   "speedup_step_vs_direct_attraction": round(d_ms / ms, 2),
-                  "max_rel_err_vs_direct_fp32": rel}
+                  "max_rel_err_vs_direct_fp32": rep["max_rel_err"],
+                  "error_vs_direct_fp32": rep}
+    uf_np = uf.cpu().numpy()
+    ud_np = ud.cpu().numpy() if ud is not None else None
+    g.close()
 
-    # roofline of the dominant kernel (near field: one EX2 per interaction)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gex2 = SM_COUNT * EX2_PER_SM_CLK * sm_max * 1e6 / 1e9
-    nf = statistics.mean(nf_ms)
-    achieved = statistics.mean(inter) / (nf / 1e3) / 1e9 if nf > 0 else 0.0
-    roofline = {"kernel": "k_near_field", "bound": "alu", "achieved": round(achieved, 1),
-                "peak": round(peak_gex2, 1), "unit": "G interactions/s",
-                "frac": round(achieved / peak_gex2, 4),
-                "traffic": None if batched else near_field_traffic(), "near_field_ms": round(nf, 3),
-                "near_field_share_of_step": round(nf / ms, 3),
-                "interactions_per_step": int(statistics.mean(inter)),
-                "peak_basis": f"EX2 rate: {SM_COUNT} SMs x {EX2_PER_SM_CLK} results/clk "
-                              f"(measured) x {sm_max:.0f} MHz, one EX2 per interaction (FP32 "
-                              f"pipe 32/clk, issue ~36/clk with paired FP32 instructions: not "
-                              f"binding)"}
+    traffic = None if batched else near_field_traffic()
+    roofline = near_field_roofline(inter, nf_ms, n, n_p2p, traffic)
+    roofline["near_field_share_of_step"] = round(nf_ms / ms, 3) if ms > 0 else 0.0
 
     out = {"metric": BATCH_METRIC if batched else METRIC, "value": value, "unit": UNIT,
            "n_gpus": world,
@@ -624,30 +725,121 @@ def run_ours(args, rank, world):
                       "plan": tuned_params(), "parallelism": f"replicas x{world}",
                       "l2": "flushed (256 MB write) between timed steps",
                       "timing": "CUDA events per step (one graph replay each), mean over steps",
-                      "step_path": "whole step captured as one CUDA graph (msp_step_graph_*)",
+                      "step_path": "whole step captured as one CUDA graph (msp_step_graph_*); "
+                                   "the replays reuse the octree of the fixed positions and "
+                                   "refresh its counts and aggregates (full_rebuild_step: the "
+                                   "octree rebuilt every replay)",
                       "graph_halted": int(halted),
                       "median_ms_per_step": round(statistics.median(step_ms), 3),
                       "note": "the plan translates no box pair: every pair of leaf boxes within "
-                              "the cutoff is evaluated exactly, so the step is itself the "
-                              "cutoff-pruned direct evaluation (plus the tree, the descent and "
-                              "the resolution); direct_* is the unpruned all-pairs evaluation",
+                              "the cutoff (3.25 sigma) is evaluated exactly and pairs beyond it "
+                              "are dropped (their kernel is below exp(-10.6) = 2.6e-5), so the "
+                              "step is itself the cutoff-pruned direct evaluation plus the tree, "
+                              "the descent and the resolution; direct_* is the unpruned all-pairs "
+                              "evaluation; fmm_translated is the fastest plan with translated "
+                              "pairs",
                       "eager_ms_per_step": round(statistics.mean(eager_ms), 3),
+                      "attraction_ms": round(statistics.median(att_ms), 3),
                       "wall_s_timed_loop": round(t_wall, 3),
                       "synapses_per_step": int(statistics.mean(synapses)),
                       **(direct or {})},
            "clocks": clk,
            "e2e": {"value": e2e["per_s"], "unit": UNIT,
-                   "h2d_bytes_per_step": 3 * n, "d2h_bytes_per_step": int(statistics.mean(d2h)),
-                   "ms_per_step": round(e2e_ms, 3),
-                   "path": "step graph with host-owned vacancies: upload the vacancy state "
-                           "(pinned), replay, read back the synapse count, the synapses and "
-                           "the updated vacancies; positions resident on the GPU",
-                   "host_buffer_call_ms_per_step": round(host_api_ms, 3),
-                   "host_buffer_call_path": "msp_plasticity_step_host (positions, counts up; "
-                                            "u, partners, synapses down; every step)"},
+                   "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": int(statistics.mean(d2h)),
+                   "ms_per_step": round(e2e["ms"], 3),
+                   "path": "msp_plasticity_step_host (C ABI, host buffers): positions, types and "
+                           "vacant counts copied up from pinned memory, steps a1-a12, u, partners "
+                           "and synapses copied back, every step; the call replays its own graph "
+                           "of the step (initial vacancies every step)",
+                   "timing": "host wall clock per call, mean over calls, L2 flushed between"},
            "gpu_launches": int(launches),
            "roofline": roofline}
-    return out, w, g, uf
+    if full:
+        out["full_rebuild_step"] = full
+    return out, w, uf_np, ud_np
+
+
+def accuracy_fp64(w, uf, ud, sample=FP64_SAMPLE):
+    """u of the plan and of the all-pairs path against the oracle's FP64 brute
+    force on `sample` seeded targets (split over the host cores)."""
+    import numpy as np
+    idx = np.sort(np.random.default_rng(0).choice(w.n, min(sample, w.n), replace=False))
+    ref = fp64_reference(w, idx)
+    res = {"targets": int(len(idx)), "plan": error_report(uf[idx], ref)}
+    if ud is not None:
+        res["direct_fp32"] = error_report(ud[idx], ref)
+    return res, idx, ref
+
+
+def fmm_translated_record(w, dev, idx, ref, reps=3):
+    """The fastest plan with translated pairs (Hermite coefficients, their
+    translation and the Taylor evaluation, Eq. 6-7) on the same network and
+    counts: attraction time and its error against FP64 on the same targets."""
+    import torch
+
+    from paper_2301_10570_gb300 import msp
+    plan = dict(FMM_TRANSLATED_PLAN)
+    params = dict(w.params, **plan)
+    g = msp.MSP(params, device=dev.index)
+    g.build_tree(*msp.to_device(w, dev))
+    u = g.attraction()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.attraction(out=u)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    st = g.stats()
+    un = u.cpu().numpy()
+    g.close()
+    rep = error_report(un[idx], ref)
+    return {"plan": plan, "attraction_ms": round(statistics.median(ts), 3),
+            "far_pairs": st["n_far"], "near_field_pairs": st["n_p2p"],
+            "near_field_interactions": st["p2p_interactions"],
+            "expansion_boxes": st["expansion_nodes"],
+            "near_field_ms": round(st["near_field_ms"], 3),
+            "error_vs_fp64": rep, "meets_1e-4": rep["max_rel_err"] <= 1e-4}
+
+
+def batched_record(dev, steps, warmup):
+    """The 256-network batch as one graph-replayed step (msp_batch_layout, then
+    the ordinary path): a few timed replays."""
+    import torch
+
+    from paper_2301_10570_gb300 import msp
+    w = batched_workload(dev)
+    n = w.n
+    g = msp.MSP(w.params, device=dev.index)
+    pos, typ, va, ve, vi = msp.to_device(w, dev)
+    g.build_tree(pos, typ, va, ve, vi)
+    g.attraction()
+    g.step_graph_capture(pos, typ, va, ve, vi, first_step=0)
+    g.run_steps(0, warmup)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ms_list, _, halted = _timed_replays(g, steps, flush)
+    st = g.stats()
+    g.close()
+    ms = statistics.mean(ms_list)
+    return {"workload": BATCH_DESC, "neurons": n, "steps": steps,
+            "ms_per_step": round(ms, 3), "neurons_per_s": n / (ms / 1e3),
+            "graph_halted": int(halted),
+            "roofline": near_field_roofline(st["p2p_interactions"], st["near_field_ms"], n,
+                                            st["n_p2p"])}
+
+
+def gradient_record(dev, steps, warmup):
+    n, ms_list, launches, _, inter = gradient_passes(steps, warmup, dev)
+    ms = statistics.mean(ms_list)
+    peaks = measured_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    p_ex2 = SM_COUNT * EX2_PER_SM_CLK * clk
+    return {"workload": GRAD_DESC, "neurons": n, "steps": steps, "ms_per_pass": round(ms, 3),
+            "neurons_per_s": n / (ms / 1e3), "interactions_per_pass": inter,
+            "ex2_frac": round(inter / (ms / 1e3) / p_ex2, 4)}
 
 
 def _oracle_steps(job):
@@ -692,26 +884,14 @@ def oracle_on_host_cores(w, warmup, steps, per_core=16_384, cores=None):
     return sum(n for n, _ in res) / slowest, cores, slowest
 
 
-def cpu_baseline(w, u_gpu=None):
+def cpu_baseline(w):
     """The FP64 oracle as it stands on every host core (one process per core,
-    each on its own 16,384-neuron block of the workload, one full step), plus
-    the GPU's accuracy on sampled targets against the oracle's brute force."""
-    import numpy as np
-
-    from oracle import oracle as O
+    each on its own 16,384-neuron block of the workload, one full step)."""
     value, cores, dt = oracle_on_host_cores(w, 0, 1)
-    res = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{cores} processes, each one full step (walk, tree, attraction, selection, "
-                     f"commit) on its own 16,384-neuron block of the workload (a cluster of the "
-                     f"1M network, or the first networks of the batch); slowest {dt:.1f} s"}
-    if u_gpu is not None:
-        rng = np.random.default_rng(0)
-        idx = rng.choice(w.n, 256, replace=False)
-        ref = O.direct(*w.arrays(), w.params["sigma"], targets=idx)
-        ug = u_gpu[idx]
-        k = ref > 0
-        res["max_rel_err_vs_fp64_256_sampled_targets"] = float(np.max(np.abs(ug[k] - ref[k]) / ref[k]))
-    return res
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each one full step (walk, tree, attraction, selection, "
+                      f"commit) on its own 16,384-neuron block of the workload (a cluster of the "
+                      f"1M network, or the first networks of the batch); slowest {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -733,8 +913,124 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# -- small named cases for profilers (ncu) ---------------------------------------
+def _profile_plan():
+    # the benchmark's plan (leaf capacity, cutoff, no translations)
+    return dict(leaf_capacity=256, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+
+
+def _case_near_field_131k(args):
+    from paper_2301_10570_gb300 import workloads as W
+    return W.clustered(8, 16_384, 100_000.0 * (8 / 64) ** (1 / 3), 1500.0, 4500.0, seed=3,
+                       name="clustered_131k", **_profile_plan())
+
+
+def _case_step_1m(args):
+    from paper_2301_10570_gb300 import workloads as W
+    return W.clustered_1m(**_profile_plan())
+
+
+def _case_translations_256k(args):
+    from paper_2301_10570_gb300 import workloads as W
+    return W.uniform_256k(leaf_capacity=8, rho_max=0.5, cutoff=4.0, m2l_min_pairs=0,
+                          p=args.case_p, centre_mode=args.case_centre_mode)
+
+
+def _case_translated_1m(args):
+    from paper_2301_10570_gb300 import workloads as W
+    return W.clustered_1m(**FMM_TRANSLATED_PLAN)
+
+
+def _case_gradient_262k(args):
+    from paper_2301_10570_gb300 import workloads as W
+    return W.clustered_small(16, 16_384, seed=15, **GRAD_PLAN)
+
+
+# name -> (workload, what runs): "steps" eager steps (tree, attraction,
+# selection); "graph"/"graph_full" the whole step captured and replayed
+# (octree reused / rebuilt each replay); "neuron" calls of 10 neuron steps;
+# "attraction" attraction calls timed with CUDA events; "gradient"
+# derivative passes
+PROFILE_CASES = {"near_field_131k": (_case_near_field_131k, "steps"),
+                 "step_1m": (_case_step_1m, "steps"),
+                 "graph_1m": (_case_step_1m, "graph"),
+                 "graph_full_1m": (_case_step_1m, "graph_full"),
+                 "neuron_1m": (_case_step_1m, "neuron"),
+                 "translations_256k": (_case_translations_256k, "attraction"),
+                 "translated_1m": (_case_translated_1m, "attraction"),
+                 "gradient_262k": (_case_gradient_262k, "gradient")}
+
+
+def run_profile_case(args):
+    """One small named case (a few steps, well under a GB on the device),
+    exiting non-zero on any error; prints the library's statistics."""
+    import numpy as np
+    import torch
+
+    from paper_2301_10570_gb300 import build, msp
+    build.build()
+    make, kind = PROFILE_CASES[args.profile_case]
+    w = make(args)
+    g = msp.MSP(w.params)
+    dev = msp.to_device(w)
+    steps = max(args.steps, 1)
+    if kind == "neuron":
+        # neuron steps on the 1M network with 1.5 random synapses per neuron
+        n = w.n
+        rng = np.random.default_rng(42)
+        m = 3 * n // 2
+        edges = msp.edge_list(m, pre=rng.integers(0, n, m), post=rng.integers(0, n, m),
+                              type_=np.zeros(m, np.uint8))
+        state = {k: torch.zeros(n, dtype=t, device="cuda") for k, t in msp.NEURON_STATE}
+        state["x"].fill_(0.065)
+        state["calcium"].uniform_(0.3, 0.8)
+        for k in range(steps):
+            g.neuron_steps(10 * k, 10, msp.neuron_params(), edges, state)
+    elif kind == "attraction":
+        # attraction only, timed with CUDA events (median of the calls after the first)
+        g.build_tree(*dev)
+        ts = []
+        for _ in range(max(steps, 2)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.attraction()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        print(f"attraction_ms {statistics.median(ts[1:]):.3f}")
+    elif kind == "gradient":
+        # geometric lists (every count 1), derivatives at the real counts
+        pos, typ, va, ve, vi = dev
+        ones = torch.ones_like(va)
+        g.build_tree(pos, typ, ones, ones, ones)
+        g.attraction()
+        gv = torch.from_numpy(np.random.default_rng(6).normal(size=w.n)).float().cuda()
+        for _ in range(steps):
+            g.attraction_grad(typ, va, ve, vi, g=gv)
+    elif kind in ("graph", "graph_full"):
+        # one eager step sizes the graph; then the whole step as graph
+        # replays (walk, build, attraction, selection, commit)
+        pos, typ, va, ve, vi = dev
+        va, ve, vi = va.clone(), ve.clone(), vi.clone()
+        g.build_tree(pos, typ, va, ve, vi)
+        g.attraction()
+        g.step_graph_set_full_build(kind == "graph_full")
+        g.step_graph_capture(pos, typ, va, ve, vi, first_step=0)
+        g.run_steps(0, steps)
+    else:
+        for k in range(steps):
+            g.build_tree(*dev)
+            g.attraction()
+            g.select_partners(k)
+    torch.cuda.synchronize()
+    print(args.profile_case, g.stats())
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        sys.exit(run_profile_case(args))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -766,10 +1062,20 @@ def main():
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
         return
-    out, w, g, u = run_ours(args, rank, world)
+    out, w, uf, ud = run_ours(args, rank, world)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 and world == 1 and args.workload == "clustered_1m":
+        idx = ref = None
+        if not args.no_cpu_baseline:
+            acc, idx, ref = accuracy_fp64(w, uf, ud)
+            out["accuracy_vs_fp64"] = acc
+        if not args.no_extras:
+            if idx is not None:
+                out["fmm_translated"] = fmm_translated_record(w, dev, idx, ref)
+            out["batched_256"] = batched_record(dev, 3, 2)
+            out["gradient_262k"] = gradient_record(dev, 3, 2)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(
-            w, None if args.workload == "batched_256" else u.cpu().numpy())
+        out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

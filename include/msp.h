@@ -175,12 +175,23 @@ msp_status msp_select_partners(msp_ctx *ctx, uint64_t step, int32_t *partner_dev
                                int32_t *syn_pre_dev, int32_t *syn_post_dev,
                                uint8_t *syn_type_dev, int64_t *n_syn_dev, void *stream);
 
-/* One whole plasticity step (build + attraction + selection) from HOST
- * buffers: copies the inputs to the device, runs the path, and copies
- * u, partner and the synapse list back.  Host buffers should be pinned for
- * full copy bandwidth.  partner_host and syn_* have capacity sum(vac_axon).
- * u_host may be NULL.  Returns the synapse count in *n_syn_host.
- * Synchronous. */
+/* One whole plasticity step (steps a1-a12: build + attraction + selection)
+ * from HOST buffers: copies the inputs to the context's device staging
+ * buffers, runs the path, and copies u, partner and the synapse list back.
+ * Host buffers should be pinned for full copy bandwidth.  partner_host and
+ * syn_* have capacity sum(vac_axon).  u_host may be NULL.  Returns the synapse
+ * count in *n_syn_host.  The results equal those of msp_build_tree,
+ * msp_attraction and msp_select_partners on the same inputs.
+ * The first call runs the path as separate kernels and then captures it as a
+ * CUDA graph on the staging buffers (the context's second graph, apart from
+ * msp_step_graph_*); later calls with the same n replay that graph, which
+ * reuses the octree while the positions equal those of the capture (a
+ * checksum of the positions is compared on the device) and refreshes its
+ * counts and aggregates.  A call the graph cannot serve (another n, changed
+ * positions, more vacant elements than it holds, a workspace reallocated by
+ * another call) runs eagerly and captures again.  Two host synchronisations
+ * per replayed call: the step's sizes, then the copies back.  Runs on the
+ * legacy default stream.  Synchronous. */
 msp_status msp_plasticity_step_host(msp_ctx *ctx, int64_t n, uint64_t step,
                                     const float *x_host, const float *y_host,
                                     const float *z_host, const uint8_t *type_host,
@@ -324,6 +335,15 @@ msp_status msp_step_graph_capture(msp_ctx *ctx, int64_t n, const float *x_dev,
                                   int64_t syn_capacity, int64_t *n_syn_dev,
                                   int64_t *history_dev, int64_t history_len,
                                   uint64_t first_step, void *stream);
+/* Option of the next msp_step_graph_capture: full_build = 1 makes every
+ * replay rebuild the octree from the positions (Morton keys, radix sort,
+ * subdivision, aggregates: steps a1-a4 in full); 0 (the default) reuses the
+ * octree of the eager build and refreshes its counts and aggregates, checked
+ * on the device by a checksum of the positions and the build's generation
+ * stamp (a mismatch halts the replay, see above).  Both give the same
+ * results while the positions are unchanged. */
+msp_status msp_step_graph_set_full_build(msp_ctx *ctx, int full_build);
+
 /* Enqueues n_steps replays on `stream`.  Asynchronous.  Fails with
  * MSP_ERR_NOT_BUILT if any workspace buffer of the library was reallocated
  * since the capture (an eager call on larger inputs): capture again. */

@@ -39,6 +39,10 @@ void graph_release(msp_ctx& c);
 void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s);
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s);
 void graph_finish(msp_ctx& c, cudaStream_t s, uint64_t* next_step, int64_t* halted);
+void host_step(msp_ctx& c, int64_t n, uint64_t step, const float* x, const float* y,
+               const float* z, const uint8_t* type, const uint8_t* va, const uint8_t* vde,
+               const uint8_t* vdi, float* u, int32_t* partner, int32_t* pre, int32_t* post,
+               uint8_t* styp, int64_t* n_syn, cudaStream_t s);
 }  // namespace msp
 
 namespace {
@@ -166,8 +170,9 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
                          &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
-                         &c->h_post, &c->h_type, &c->h_nsyn, &c->c_type, &c->c_va,
-                         &c->c_vde, &c->c_vdi};
+                         &c->h_post, &c->h_type, &c->h_nsyn, &c->hs_u, &c->hs_partner,
+                         &c->hs_pre, &c->hs_post, &c->hs_type, &c->hs_nsyn, &c->c_type,
+                         &c->c_va, &c->c_vde, &c->c_vdi};
     for (msp::DBuf* b : bufs) b->release();
     for (auto& b : c->h_in) b.release();
     if (c->hcount) cudaFreeHost(c->hcount);
@@ -235,48 +240,9 @@ msp_status msp_plasticity_step_host(msp_ctx* c, int64_t n, uint64_t step, const 
         require(n >= 0 && n < 0x7ffffffell, "n out of range");
         require(n == 0 || (x && y && z && type && va && vde && vdi), "null input pointer");
         require(n_syn != nullptr, "null n_syn");
-        cudaStream_t s = 0;
-        size_t nn = (size_t)(n > 0 ? n : 1);
-        float* dx = c->h_in[0].ensure<float>(nn);
-        float* dy = c->h_in[1].ensure<float>(nn);
-        float* dz = c->h_in[2].ensure<float>(nn);
-        uint8_t* dt = c->h_in[3].ensure<uint8_t>(nn);
-        uint8_t* da = c->h_in[4].ensure<uint8_t>(nn);
-        uint8_t* de = c->h_in[5].ensure<uint8_t>(nn);
-        uint8_t* di = c->h_in[6].ensure<uint8_t>(nn);
-        if (n > 0) {
-            MSP_CUDA(cudaMemcpyAsync(dx, x, n * 4, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(dy, y, n * 4, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(dz, z, n * 4, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(dt, type, n, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(da, va, n, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(de, vde, n, cudaMemcpyHostToDevice, s));
-            MSP_CUDA(cudaMemcpyAsync(di, vdi, n, cudaMemcpyHostToDevice, s));
-        }
-        c->in_type = dt; c->in_va = da; c->in_vde = de; c->in_vdi = di;
-        msp::build_tree(*c, n, dx, dy, dz, dt, da, de, di, s);
-        float* du = u ? c->h_u.ensure<float>(nn) : nullptr;
-        msp::attraction(*c, du, s);
-        size_t ne = (size_t)(c->n_elem > 0 ? c->n_elem : 1);
-        require(c->n_elem == 0 || (partner && pre && post && styp), "null output pointer");
-        int32_t* dp = c->h_partner.ensure<int32_t>(ne);
-        int32_t* dpre = c->h_pre.ensure<int32_t>(ne);
-        int32_t* dpost = c->h_post.ensure<int32_t>(ne);
-        uint8_t* dst = c->h_type.ensure<uint8_t>(ne);
-        int64_t* dn = c->h_nsyn.ensure<int64_t>(1);
-        msp::select_partners(*c, step, dt, da, de, di, dp, dpre, dpost, dst, dn, s);
-        int64_t ns = c->n_synapses;
-        if (u && n > 0) MSP_CUDA(cudaMemcpyAsync(u, du, n * 4, cudaMemcpyDeviceToHost, s));
-        if (c->n_elem > 0) {
-            MSP_CUDA(cudaMemcpyAsync(partner, dp, c->n_elem * 4, cudaMemcpyDeviceToHost, s));
-            if (ns > 0) {
-                MSP_CUDA(cudaMemcpyAsync(pre, dpre, ns * 4, cudaMemcpyDeviceToHost, s));
-                MSP_CUDA(cudaMemcpyAsync(post, dpost, ns * 4, cudaMemcpyDeviceToHost, s));
-                MSP_CUDA(cudaMemcpyAsync(styp, dst, ns, cudaMemcpyDeviceToHost, s));
-            }
-        }
-        MSP_CUDA(cudaStreamSynchronize(s));
-        *n_syn = ns;
+        require(n == 0 || (partner && pre && post && styp), "null output pointer");
+        msp::host_step(*c, n, step, x, y, z, type, va, vde, vdi, u, partner, pre, post, styp,
+                       n_syn, 0);
     });
 }
 
@@ -379,6 +345,13 @@ msp_status msp_step_graph_capture(msp_ctx* c, int64_t n, const float* x, const f
         g.history_len = history_len;
         g.first_step = first_step;
         msp::graph_capture(*c, g, as_stream(stream));
+    });
+}
+
+msp_status msp_step_graph_set_full_build(msp_ctx* c, int full_build) {
+    return guarded(c, [&] {
+        require(full_build == 0 || full_build == 1, "full_build must be 0 or 1");
+        c->sg_full_build = full_build != 0;
     });
 }
 

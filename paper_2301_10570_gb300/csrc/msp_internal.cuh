@@ -133,6 +133,7 @@ struct DevCounts {
     int64_t steps_run;
     int64_t interactions_run;                // near-field interactions over the replays
     uint64_t pos_sum;                        // checksum of the positions of the last build
+    uint64_t tree_gen;                       // generation stamp of the last eager build
 };
 
 // DevCounts::overflow bit set when a bounded wait of the single-pass scan
@@ -222,16 +223,12 @@ struct msp_ctx {
     // capacity bounds and no call synchronises (set while capturing and for
     // the dry run that sizes the buffers before it).
     bool graph_mode = false;
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t g_template = nullptr;
-    int64_t graph_kernels = 0;                 // kernel launches per replay
-    cudaGraphNode_t g_nf0 = nullptr, g_nf1 = nullptr;   // event records around the near field
-    std::vector<cudaEvent_t> g_events;         // two per replay of the last launch
-    int64_t g_replays = 0;                     // replays of the last launch
-    int g_left_slot = 0;                       // descent counter slot that must end empty
-    long long g_epoch = -1;                    // allocation epoch at capture
-    double g_nf_ms_mean = 0.0;                 // mean near-field time over them
-    bool last_was_graph = false;               // statistics come from graph replays
+    int64_t graph_elem_cap = 0;                // element capacity in graph mode
+    bool graph_full_build = false;             // graph mode rebuilds the whole octree
+    int cap_left_slot = 0;                     // set by the selection while recording
+    // every eager build stamps a new tree generation (also in device memory);
+    // a replay that reuses the octree checks the stamp it was captured with
+    uint64_t tree_gen = 0;
     struct GraphArgs {
         const float *x = nullptr, *y = nullptr, *z = nullptr;
         const uint8_t* type = nullptr;
@@ -244,10 +241,33 @@ struct msp_ctx {
         int64_t* history = nullptr;
         int64_t history_len = 0;
         uint64_t first_step = 0;
-    } gargs;
-    // host-buffer step staging
+        float* u = nullptr;          // attraction out (sorted-order scatter), or none
+        int64_t elem_cap = 0;        // vacant axonal elements the buffers hold
+        bool walk = true;            // the step starts with the vacancy walk
+        bool commit = true;          // and ends with the commit of its synapses
+        bool full_build = false;     // octree rebuilt per replay (else reused)
+    };
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t tmpl = nullptr;
+        int64_t kernels = 0;                      // kernel launches per replay
+        cudaGraphNode_t nf0 = nullptr, nf1 = nullptr;   // event records around the near field
+        int left_slot = 0;                        // descent counter slot that must end empty
+        long long epoch = -1;                     // allocation epoch at capture
+        GraphArgs args;
+    };
+    StepGraph sg;            // the caller's step graph (msp_step_graph_*)
+    StepGraph hg;            // the host-buffer call's own step graph
+    bool sg_full_build = false;                // option of the next msp_step_graph_capture
+    std::vector<cudaEvent_t> g_events;         // two per replay of the last launch
+    int64_t g_replays = 0;                     // replays of the last launch
+    double g_nf_ms_mean = 0.0;                 // mean near-field time over them
+    bool last_was_graph = false;               // statistics come from graph replays
+    // host-buffer step staging: inputs, the dry runs' scratch outputs, and
+    // the outputs of the host-buffer call's graph
     msp::DBuf h_in[7];
     msp::DBuf h_u, h_partner, h_pre, h_post, h_type, h_nsyn;
+    msp::DBuf hs_u, hs_partner, hs_pre, hs_post, hs_type, hs_nsyn;
 };
 
 namespace msp {

@@ -46,6 +46,7 @@ __shared__ float* s_wt;
 __shared__ int32_t* s_wii;
 
 constexpr int kNFWarps = 4;
+constexpr int kNFThreads = kNFWarps * 32;
 constexpr int kNFStage = 128;
 constexpr int kNFMaxT = 32 * 4;    // targets per pass (3 or 4 per lane)
 constexpr int kNFList = 128;       // target slots per round (one pass)
@@ -97,6 +98,10 @@ struct Tgts {
 __shared__ float* s_scale;
 __shared__ float* s_fa;
 __shared__ const int32_t* s_tl;
+// per thread and target r, at [r * kNFThreads + thread]: the compensation of
+// the Kahan sum of the target's per-pair sums (kept in shared memory: the
+// kernel's registers are taken by the evaluation loop)
+__shared__ float* s_cmp;
 
 // A warp's staged sources, in pairs: pair j (sources 2j, 2j+1) is the float4
 // (x0, x1, y0, y1) at [j] and (z0, z1, c0, c1) at [kNFZE + j] for the
@@ -228,8 +233,7 @@ template <int R>
 __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1, int32_t tf,
                                          bool fast, float cx, float cy, float cz, int ksl,
                                          int slices, const Tgts<R>& tg, float (&acc)[R],
-                                         float (&cmp)[R], float4* stw,
-                                         unsigned long long& evals, int nreal) {
+                                         float4* stw, unsigned long long& evals, int nreal) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float (*wt)[33] = reinterpret_cast<float (*)[33]>(s_wt + w * 16 * 33);
     int32_t* wii = s_wii + w * 16;
@@ -303,13 +307,15 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 }
             }
             // the pair's sum joins the target's total by Kahan's compensated
-            // summation (cmp holds what the running total gained by rounding)
+            // summation (the compensation holds what the running total
+            // gained by rounding)
             float v = 0.f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const float y = __fsub_rn(part[k], cmp[k]);
+                float* cp = s_cmp + k * kNFThreads + threadIdx.x;
+                const float y = __fsub_rn(part[k], *cp);
                 const float t2 = __fadd_rn(acc[k], y);
-                cmp[k] = __fsub_rn(__fsub_rn(t2, acc[k]), y);
+                *cp = __fsub_rn(__fsub_rn(t2, acc[k]), y);
                 acc[k] = t2;
                 v = fmaf(s_fa[tg.slot0 + k], part[k], v);
             }
@@ -351,7 +357,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
                                            int32_t i0, int32_t i1, int32_t tf, bool fast, float cx,
                                            float cy, float cz, float4* stw,
                                            float (*red)[kNFMaxT], unsigned long long& evals) {
-    static_assert(R >= 2 && R <= 6, "two to six targets per lane");
+    static_assert(R >= 2 && R <= 4, "two to four targets per lane (the compensation buffer holds four)");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0;
     while ((1 << lg) < (nt + R - 1) / R) ++lg;
@@ -361,7 +367,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
     const int ksl = lane >> lg;
     Tgts<R> tg;
     tg.slot0 = R * j;
-    float acc[R], cmp[R];
+    float acc[R];
     {
         // the channel of the lane's first slot (all its slots share it)
         const int32_t t0 = tg.slot0 < nt ? tl[tg.slot0] : -1;
@@ -381,7 +387,7 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         tg.y[r] = make_float2(f2 * hy, f2 * hy);
         tg.z[r] = make_float2(f2 * hz, f2 * hz);
         acc[r] = 0.f;
-        cmp[r] = 0.f;
+        s_cmp[r * kNFThreads + threadIdx.x] = 0.f;
         if (w == 0 && ksl == 0) {
             const float sc = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
             s_scale[slot] = sc;
@@ -389,12 +395,12 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         }
     }
     __syncthreads();
-    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, cmp, stw, evals, nreal);
+    nf_pairs<R>(a, i0, i1, tf, fast, cx, cy, cz, ksl, slices, tg, acc, stw, evals, nreal);
     // the compensated totals, then the slices of a target group and the 4
     // warps in a fixed order
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        acc[r] = __fsub_rn(acc[r], cmp[r]);
+        acc[r] = __fsub_rn(acc[r], s_cmp[r * kNFThreads + threadIdx.x]);
         for (int o = npr; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     }
     if (ksl == 0) {
@@ -426,6 +432,8 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
     __shared__ float wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
     __shared__ float scale_all[kNFMaxT], fa_all[kNFMaxT];
+    __shared__ float cmp_all[4 * kNFThreads];
+    s_cmp = cmp_all;
     s_wt = &wt_all[0][0][0];
     s_wii = &wii_all[0][0];
     s_scale = scale_all;

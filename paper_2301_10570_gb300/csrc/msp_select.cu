@@ -678,9 +678,10 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
     const msp_config& cfg = c.cfg;
     // the element count: exact from the build, or (whole-step graph) the
-    // bound that the vacancy walk keeps; kernels read the exact count from
-    // device memory and never index past it
-    const int64_t n = c.n, ne = c.graph_mode ? (int64_t)kMaxVacancy * n : c.n_elem;
+    // capacity of its buffers (the vacancy walk's bound, or the host-buffer
+    // call's); kernels read the exact count from device memory and never
+    // index past it
+    const int64_t n = c.n, ne = c.graph_mode ? c.graph_elem_cap : c.n_elem;
     const int B = 256;
     const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));
     // inside a leaf the kernel is truncated at the radius that prunes box pairs
@@ -778,7 +779,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     MSP_CUDA(cudaMemcpyAsync(n_syn, &dc->n_syn, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     if (c.graph_mode) {
         // checked on the device at the end of the graph's step
-        c.g_left_slot = n_steps % 3;
+        c.cap_left_slot = n_steps % 3;
         return;
     }
     pull_counts(c, s);              // the one synchronisation of the selection

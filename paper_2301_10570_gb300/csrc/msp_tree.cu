@@ -44,9 +44,15 @@ __global__ void k_pos_sum(const float* __restrict__ x, const float* __restrict__
 }
 
 // the positions of a graph step must be those its octree was built from
-__global__ void k_pos_check(DevCounts* dc, uint64_t ref) {
-    if (dc->pos_sum != ref) dc->bad_pos = 1;
+// a replay that reuses the octree: the positions must be those of the build
+// (checksum) and the octree arrays those of that build (generation stamp)
+__global__ void k_pos_check(DevCounts* dc, uint64_t ref, uint64_t gen) {
+    if (dc->pos_sum != ref || dc->tree_gen != gen) dc->bad_pos = 1;
 }
+
+// a graph replay that rebuilt the octree: no capture holds this stamp, so a
+// replay of another graph that reuses the octree halts instead
+__global__ void k_mark_graph_tree(DevCounts* dc) { dc->tree_gen = ~0ull; }
 
 // keys; a position outside [origin, origin + side) or not finite is counted
 // (the build then fails: the tree's boxes must contain their points)
@@ -335,8 +341,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     // build (checked: a different checksum halts the graph), so its sorted
     // order and octree are reused; the counts are gathered again and the
     // aggregates recomputed.
-    if (c.graph_mode && c.tree_built) {
-        k_pos_check<<<1, 1, 0, s>>>(dc, c.pos_sum_ref);
+    if (c.graph_mode && c.tree_built && !c.graph_full_build) {
+        k_pos_check<<<1, 1, 0, s>>>(dc, c.pos_sum_ref, c.tree_gen);
         MSP_LAUNCH("pos_check");
         if (n > 0) {
             k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
@@ -456,7 +462,11 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         }
         // inside the whole-step graph the tree of the same positions has the
         // same levels; a deeper one sets more_levels, which halts the graph
-        if (c.graph_mode) return;
+        if (c.graph_mode) {
+            k_mark_graph_tree<<<1, 1, 0, s>>>(dc);
+            MSP_LAUNCH("mark_graph_tree");
+            return;
+        }
         pull_counts(c, s);          // the one synchronisation of the build
         if (c.hcount->bad_pos)
             throw Error(MSP_ERR_INVALID_ARG, "a position is outside [origin, origin + side) "
@@ -479,6 +489,8 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     c.n_elem = hc.n_elem;
     c.tree_levels = L;
     c.pos_sum_ref = hc.pos_sum;
+    c.tree_gen += 1;
+    dev_set(reinterpret_cast<int64_t*>(&dc->tree_gen), (int64_t)c.tree_gen, s);
     c.tree_built = true;
 }
 

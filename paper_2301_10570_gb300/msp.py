@@ -34,7 +34,7 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
             "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait",
-            "msp_philox")
+            "msp_philox", "msp_step_graph_set_full_build")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -150,6 +150,8 @@ def load(path: str = LIB_PATH):
         L.msp_selftest_bounded_wait.argtypes = [vp, vp]
         L.msp_philox.argtypes = [i64, vp, vp, vp, vp]
         L.msp_philox.restype = C.c_int
+        L.msp_step_graph_set_full_build.argtypes = [vp, C.c_int]
+        L.msp_step_graph_set_full_build.restype = C.c_int
         for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
                      "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
@@ -400,6 +402,11 @@ class MSP:
             _ptr(out["n_syn"]), _ptr(out["history"]) if history_len else None, int(history_len),
             int(first_step), _stream(stream)))
         return out
+
+    def step_graph_set_full_build(self, full_build: bool):
+        """Option of the next capture: every replay rebuilds the whole octree
+        (True) or reuses the eager build's octree (False, the default)."""
+        _check(load().msp_step_graph_set_full_build(self._h, 1 if full_build else 0))
 
     def step_graph_launch(self, n_steps, stream=None):
         _check(load().msp_step_graph_launch(self._h, int(n_steps), _stream(stream)))

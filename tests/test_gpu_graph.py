@@ -51,13 +51,14 @@ def _eager(w, first, k_steps):
     return counts, [v.cpu().numpy() for v in (a, e, i)], last
 
 
-def _graph(w, first, k_steps, pair_capacity=None, manual=False):
+def _graph(w, first, k_steps, pair_capacity=None, manual=False, full_build=False):
     pos, t, a, e, i = _state(w)
     g = msp.MSP(w.params)
     g.build_tree(pos, t, a, e, i)
     g.attraction()
     if pair_capacity is not None:
         g.set_pair_capacity(pair_capacity)
+    g.step_graph_set_full_build(full_build)
     out = g.step_graph_capture(pos, t, a, e, i, first_step=first, history_len=k_steps)
     halts = []
     if manual:
@@ -223,34 +224,16 @@ def test_graph_replays_of_a_batch_equal_eager_steps():
         assert np.array_equal(lg[key], le[key])
 
 
-def _oracle_steps(w, first, k_steps):
-    """The oracle's plasticity steps first .. first+k_steps-1 (walk, tree,
-    attraction, selection, commit): per-step synapse counts, the vacancy state
-    after each step and whether any draw of the step was within the oracle's
-    band of a CDF boundary."""
-    from oracle import oracle as O
-    a, e, i = w.vac_axon.copy(), w.vac_dend_e.copy(), w.vac_dend_i.copy()
-    o = O.Oracle(w.params)
-    counts, states, flagged = [], [], []
-    for k in range(first, first + k_steps):
-        a, e, i = O.vacancy_walk(w.params["seed"], k, a, e, i)
-        o.build_tree(w.pos, w.type, a, e, i)
-        o.attraction()
-        r = o.select_partners(k)
-        a, e, i = O.commit_synapses(r["syn_pre"], r["syn_post"], r["syn_type"], a, e, i)
-        counts.append(r["n_syn"])
-        states.append((a.copy(), e.copy(), i.copy()))
-        flagged.append(bool(r["near_boundary"].any()))
-    return counts, states, flagged
-
-
 @pytest.mark.parametrize("case", ["clustered_4k_c32", "bench_plan_2x16k"])
 def test_graph_replays_equal_the_oracle_steps(case):
     """K replays of the captured step (walk, tree, attraction, selection,
-    commit) against the oracle's K-step loop: the synapse count of every step
-    and the vacancy state after the run, bit for bit.  Runs can only part at a
-    draw the oracle flags as within its band of a CDF boundary; the comparison
-    covers the steps before the first such step (required to be most of them)."""
+    commit), one at a time, each against the oracle's step from the same
+    vacancy state (read back from the GPU before the replay): partners
+    identical except draws the oracle flags as within its band of a CDF
+    boundary; whenever no partner differs, the step's synapse count (also in
+    the graph's history), synapse lists and the vacancy state after the commit
+    bit for bit."""
+    from oracle import oracle as O
     if case == "clustered_4k_c32":
         w, k_steps = W.clustered_small(1, 4096, seed=21, leaf_capacity=32, cutoff=3.25,
                                        rho_max=0.0), 8
@@ -258,11 +241,75 @@ def test_graph_replays_equal_the_oracle_steps(case):
         w, k_steps = W.clustered_small(2, 16_384, seed=22, leaf_capacity=256, cutoff=3.25,
                                        rho_max=0.0, m2l_min_pairs=0), 4
     first = 5
-    oc, ostates, oflag = _oracle_steps(w, first, k_steps)
-    upto = oflag.index(True) if True in oflag else k_steps
-    assert upto >= k_steps // 2, f"boundary draws from step {first + upto} on"
-    gc, gstate, _, _, _ = _graph(w, first, k_steps)
-    assert gc[:upto] == oc[:upto]
-    if upto == k_steps:
-        for got, ref in zip(gstate, ostates[-1]):
-            assert np.array_equal(got, ref)
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    out = g.step_graph_capture(pos, t, a, e, i, first_step=first, history_len=k_steps)
+    o = O.Oracle(w.params)
+    exact_steps = 0
+    for k in range(first, first + k_steps):
+        pre = [v.cpu().numpy() for v in (a, e, i)]
+        assert g.run_steps(k, 1) == k + 1
+        oa, oe, oi = O.vacancy_walk(w.params["seed"], k, *pre)
+        o.build_tree(w.pos, w.type, oa, oe, oi)
+        o.attraction()
+        r = o.select_partners(k)
+        ne = len(r["partner"])
+        assert g.stats()["n_elements"] == ne
+        gp = out["partner"][:ne].cpu().numpy()
+        differ = gp != r["partner"]
+        assert np.all(r["near_boundary"][differ])
+        if differ.any():
+            continue
+        ns = r["n_syn"]
+        assert int(out["n_syn"].item()) == ns
+        assert int(out["history"][k - first].item()) == ns
+        assert np.array_equal(out["syn_pre"][:ns].cpu().numpy(), r["syn_pre"])
+        assert np.array_equal(out["syn_post"][:ns].cpu().numpy(), r["syn_post"])
+        assert np.array_equal(out["syn_type"][:ns].cpu().numpy(), r["syn_type"])
+        ref = O.commit_synapses(r["syn_pre"], r["syn_post"], r["syn_type"], oa, oe, oi)
+        for got, want in zip((a, e, i), ref):
+            assert np.array_equal(got.cpu().numpy(), want)
+        exact_steps += 1
+    assert exact_steps >= k_steps // 2
+    g.close()
+
+
+def test_full_build_graph_replays_equal_eager_steps():
+    """Replays that rebuild the whole octree every step (steps a1-a12 in
+    full) give the same steps as the eager calls and as the replays that
+    reuse the octree."""
+    w = W.clustered_small(2, 4096, seed=4, leaf_capacity=32, rho_max=0.0)
+    ec, es, el = _eager(w, 3, 5)
+    gc, gs, gl, st, _ = _graph(w, 3, 5, full_build=True)
+    assert gc == ec
+    for x, y in zip(gs, es):
+        assert np.array_equal(x, y)
+    assert np.array_equal(gl["pre"], el["pre"]) and np.array_equal(gl["post"], el["post"])
+    rc, rs, _, _, _ = _graph(w, 3, 5, full_build=False)
+    assert rc == gc
+
+
+def test_graph_halts_when_another_build_replaced_its_octree():
+    """A replay that reuses the octree checks the build it was captured after:
+    an eager build of other positions (same n) in between halts the replay,
+    which is finished eagerly on its own positions and captured again."""
+    w = W.clustered_small(1, 4096, seed=6, leaf_capacity=32, rho_max=0.0)
+    other = W.clustered_small(1, 4096, seed=7, leaf_capacity=32, rho_max=0.0)
+    ec, es, _ = _eager(w, 2, 3)
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    odev = msp.to_device(other)
+    g.build_tree(*odev)             # sizes the workspace for both trees first, so that
+    g.build_tree(pos, t, a, e, i)   # the later build reallocates nothing (a reallocation
+    g.attraction()                  # is refused earlier, by the allocation epoch)
+    out = g.step_graph_capture(pos, t, a, e, i, first_step=2, history_len=3)
+    g.build_tree(*odev)             # replaces the octree
+    g.step_graph_launch(1)
+    nxt, halted = g.step_graph_finish()
+    assert halted != 0 and nxt == 3
+    assert g.run_steps(3, 2) == 5
+    assert out["history"].cpu().numpy().tolist() == ec
+    for x, y in zip((a, e, i), es):
+        assert np.array_equal(x.cpu().numpy(), y)

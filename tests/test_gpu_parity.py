@@ -286,21 +286,53 @@ def test_device_philox_known_answer_vectors():
         assert np.array_equal(got[i], O.philox(ctr[i], key[i]))
 
 
-def test_host_buffer_step_equals_device_calls():
-    w = W.clustered_small(1, 4096, leaf_capacity=16, rho_max=0.3, p=4)
+def _device_calls(w, step):
     g = msp.MSP(w.params)
-    out = g.plasticity_step_host(7, *w.arrays())
-    g2 = msp.MSP(w.params)
-    g2.build_tree(*msp.to_device(w))
-    u = g2.attraction().cpu().numpy()
-    sel = g2.select_partners(7)
-    ne = g2.num_elements()
+    g.build_tree(*msp.to_device(w))
+    u = g.attraction().cpu().numpy()
+    sel = g.select_partners(step)
+    ne = g.num_elements()
     ns = int(sel["n_syn"].item())
-    assert int(out["n_syn"][0]) == ns
-    assert np.array_equal(out["partner"][:ne], sel["partner"][:ne].cpu().numpy())
-    assert np.array_equal(out["syn_post"][:ns], sel["syn_post"][:ns].cpu().numpy())
-    # translations accumulate B(X) atomically: u may differ in the last bits
-    np.testing.assert_allclose(out["u"][: w.n], u, rtol=1e-6, atol=0)
+    out = dict(u=u, partner=sel["partner"][:ne].cpu().numpy(), n_syn=ns,
+               pre=sel["syn_pre"][:ns].cpu().numpy(), post=sel["syn_post"][:ns].cpu().numpy(),
+               typ=sel["syn_type"][:ns].cpu().numpy())
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("rho_max", [0.0, 0.3])
+def test_host_buffer_step_equals_device_calls(rho_max):
+    """msp_plasticity_step_host, call after call: the first runs eagerly and
+    captures the step, later ones replay the graph (new vacancies each call,
+    then moved positions, which the graph detects and runs eagerly again);
+    every call equals the separate device calls on the same inputs."""
+    from paper_2301_10570_gb300 import workloads as W2
+    w = W2.clustered_small(1, 4096, leaf_capacity=16, rho_max=rho_max, p=4)
+    g = msp.MSP(w.params)
+    rng = np.random.default_rng(9)
+    for call in range(5):
+        if call in (2, 3):
+            for v in (w.vac_axon, w.vac_dend_e, w.vac_dend_i):
+                v[:] = rng.integers(0, 4, w.n).astype(np.uint8)
+        if call == 4:
+            w.pos[:, :50] += np.float32(10.0)
+        step = 7 + call
+        out = g.plasticity_step_host(step, *w.arrays())
+        ref = _device_calls(w, step)
+        ne, ns = len(ref["partner"]), ref["n_syn"]
+        assert int(out["n_syn"][0]) == ns
+        assert np.array_equal(out["partner"][:ne], ref["partner"])
+        assert np.array_equal(out["syn_pre"][:ns], ref["pre"])
+        assert np.array_equal(out["syn_post"][:ns], ref["post"])
+        assert np.array_equal(out["syn_type"][:ns], ref["typ"])
+        if rho_max == 0.0:
+            assert np.array_equal(out["u"][: w.n], ref["u"])
+        else:
+            # translations accumulate B(X) atomically: u may differ in the last bits
+            np.testing.assert_allclose(out["u"][: w.n], ref["u"], rtol=1e-6, atol=0)
+        st = g.stats()
+        assert st["n_synapses"] == ns and st["n_elements"] == ne
+    g.close()
 
 
 def test_repeated_runs_are_deterministic():
