@@ -648,10 +648,12 @@ def run_ours(args, rank, world):
     # End to end through the C ABI's host-buffer call: every step copies the
     # inputs (positions, types, vacant counts) up from pinned host memory, runs
     # steps a1-a12 and copies u, the partners and the synapses back (the call
-    # replays its own graph of the step after the first call)
+    # replays its own graph of the step after the first call).  The vacant
+    # counts are the walked state the timed graph replays reached.
     pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hp = pinned(w.pos)
-    ht, ha, he, hi = (pinned(a) for a in (w.type, w.vac_axon, w.vac_dend_e, w.vac_dend_i))
+    ht = pinned(w.type)
+    ha, he, hi = (pinned(v.cpu().numpy()) for v in (va, ve, vi))
     ne0 = int(ha.sum(dtype=np.int64))
     hout = dict(u=pinned(np.zeros(n, np.float32)), partner=pinned(np.zeros(ne0, np.int32)),
                 syn_pre=pinned(np.zeros(ne0, np.int32)), syn_post=pinned(np.zeros(ne0, np.int32)),
@@ -750,7 +752,7 @@ def run_ours(args, rank, world):
                    "path": "msp_plasticity_step_host (C ABI, host buffers): positions, types and "
                            "vacant counts copied up from pinned memory, steps a1-a12, u, partners "
                            "and synapses copied back, every step; the call replays its own graph "
-                           "of the step (initial vacancies every step)",
+                           "of the step (the walked vacancy state of the timed replays)",
                    "timing": "host wall clock per call, mean over calls, L2 flushed between"},
            "gpu_launches": int(launches),
            "roofline": roofline}

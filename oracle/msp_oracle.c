@@ -1004,6 +1004,146 @@ void orc_direct_grad(int64_t n, const float *x, const float *y, const float *z,
 }
 
 /* ------------------------------------------------------------------------- */
+/* expected mean synapse length (Eq. 1 / Eq. 8 probabilities) and its         */
+/* derivatives: the loss of the differentiation workload                      */
+/* ------------------------------------------------------------------------- */
+
+/* forward terms of one (target t, source s) pair, caller indices: the sums
+ * u(t) = sum w K, v(t) = sum w K r and their sigma derivatives */
+static void len_fwd_term(int64_t t, int64_t s, double d2, double sigma, const uint8_t *type,
+                         const uint8_t *va, const double *we, const double *wi, double *U,
+                         double *V, double *dU, double *dV)
+{
+    if (va[t] == 0) return;
+    double K = exp(-d2 / (sigma * sigma));
+    double r = sqrt(d2);
+    double w = type[t] ? wi[s] : we[s];
+    double dK = K * 2.0 * d2 / (sigma * sigma * sigma);    /* dK/dsigma */
+    U[t] += w * K;
+    V[t] += w * K * r;
+    dU[t] += w * dK;
+    dV[t] += w * dK * r;
+}
+
+/* adjoint terms: dm/dw^T(t)_s += alpha_t K r - beta_t K */
+static void len_adj_term(int64_t t, int64_t s, double d2, double sigma, const uint8_t *type,
+                         const double *alpha, const double *beta, double *gE, double *gI)
+{
+    if (alpha[t] == 0.0 && beta[t] == 0.0) return;
+    double K = exp(-d2 / (sigma * sigma));
+    double *gs = type[t] ? gI : gE;
+    gs[s] += alpha[t] * K * sqrt(d2) - beta[t] * K;
+}
+
+/* The mean over the targets from their sums, the loss and the sigma
+ * derivative; alpha, beta receive the adjoint's per-target coefficients of
+ * dloss/dw (already times 2 (m - target)). */
+static void len_finish(int64_t n, const uint8_t *va, const double *U, const double *V,
+                       const double *dU, const double *dV, double target, double *out4,
+                       double *alpha, double *beta)
+{
+    double A = 0.0, S = 0.0, dS = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        if (va[t] == 0 || !(U[t] > 0.0)) continue;
+        A += va[t];
+        S += va[t] * V[t] / U[t];
+        dS += va[t] * (dV[t] * U[t] - V[t] * dU[t]) / (U[t] * U[t]);
+    }
+    double m = A > 0.0 ? S / A : 0.0;
+    double dm = A > 0.0 ? dS / A : 0.0;
+    double f = 2.0 * (m - target);
+    out4[0] = (m - target) * (m - target);
+    out4[1] = m;
+    out4[2] = f * dm;
+    out4[3] = dm;
+    for (int64_t t = 0; t < n; ++t) {
+        alpha[t] = beta[t] = 0.0;
+        if (va[t] == 0 || !(U[t] > 0.0) || !(A > 0.0)) continue;
+        alpha[t] = f * va[t] / (A * U[t]);
+        beta[t] = f * va[t] * V[t] / (A * U[t] * U[t]);
+    }
+}
+
+/* d2 of a sorted-order point pair of the context */
+static double ctx_d2(const orc_ctx *c, int64_t t, int64_t s)
+{
+    double d2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double e = c->pos[3 * t + d] - c->pos[3 * s + d];
+        d2 += e * e;
+    }
+    return d2;
+}
+
+int orc_length_loss(const orc_ctx *c, const uint8_t *type, const uint8_t *vac_axon,
+                    const double *we, const double *wi, double target, double *out4,
+                    double *gE, double *gI)
+{
+    if (!c->attraction_done) return -1;
+    for (int64_t q = 0; q < c->n_pairs; ++q)
+        if (c->pairs[q].kind == ORC_FAR) return -1;
+    int64_t n = c->n;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *U = (double *)calloc(nn, sizeof(double)), *V = (double *)calloc(nn, sizeof(double));
+    double *dU = (double *)calloc(nn, sizeof(double)), *dV = (double *)calloc(nn, sizeof(double));
+    double *al = (double *)calloc(nn, sizeof(double)), *be = (double *)calloc(nn, sizeof(double));
+    double sigma = c->cfg.sigma;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            len_finish(n, vac_axon, U, V, dU, dV, target, out4, al, be);
+            if (!gE || !gI) break;
+            for (int64_t i = 0; i < n; ++i) gE[i] = gI[i] = 0.0;
+        }
+        for (int64_t q = 0; q < c->n_pairs; ++q) {
+            const pair_t *pr = &c->pairs[q];
+            if (pr->kind != ORC_P2P) continue;
+            const node_t *X = &c->nodes[pr->X], *Y = &c->nodes[pr->Y];
+            for (int64_t t = X->first; t < (int64_t)X->first + X->count; ++t)
+                for (int64_t s = Y->first; s < (int64_t)Y->first + Y->count; ++s) {
+                    if (s == t) continue;
+                    double d2 = ctx_d2(c, t, s);
+                    if (pass == 0)
+                        len_fwd_term(c->perm[t], c->perm[s], d2, sigma, type, vac_axon, we, wi,
+                                     U, V, dU, dV);
+                    else
+                        len_adj_term(c->perm[t], c->perm[s], d2, sigma, type, al, be, gE, gI);
+                }
+        }
+    }
+    free(U); free(V); free(dU); free(dV); free(al); free(be);
+    return 0;
+}
+
+void orc_direct_length_loss(int64_t n, const float *x, const float *y, const float *z,
+                            const uint8_t *type, const uint8_t *vac_axon, const double *we,
+                            const double *wi, double sigma, double target, double *out4,
+                            double *gE, double *gI)
+{
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *U = (double *)calloc(nn, sizeof(double)), *V = (double *)calloc(nn, sizeof(double));
+    double *dU = (double *)calloc(nn, sizeof(double)), *dV = (double *)calloc(nn, sizeof(double));
+    double *al = (double *)calloc(nn, sizeof(double)), *be = (double *)calloc(nn, sizeof(double));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            len_finish(n, vac_axon, U, V, dU, dV, target, out4, al, be);
+            if (!gE || !gI) break;
+            for (int64_t i = 0; i < n; ++i) gE[i] = gI[i] = 0.0;
+        }
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                if (s == t) continue;
+                double dx = (double)x[t] - x[s], dy = (double)y[t] - y[s], dz = (double)z[t] - z[s];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                if (pass == 0)
+                    len_fwd_term(t, s, d2, sigma, type, vac_axon, we, wi, U, V, dU, dV);
+                else
+                    len_adj_term(t, s, d2, sigma, type, al, be, gE, gI);
+            }
+    }
+    free(U); free(V); free(dU); free(dV); free(al); free(be);
+}
+
+/* ------------------------------------------------------------------------- */
 /* vacancy updates                                                            */
 /* ------------------------------------------------------------------------- */
 void orc_vacancy_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t *vac_axon,

@@ -103,6 +103,25 @@ void orc_direct_grad(int64_t n, const float *x, const float *y, const float *z,
                      const uint8_t *vac_dend_i, double sigma, const double *g, double *u,
                      double *dudsig, double *gE, double *gI);
 
+/* Expected mean synapse length and its gradient (the loss of the
+ * differentiation workload).  An axonal element of t draws dendrite s with
+ * probability w_s K(t,s) / u(t) (Eq. 1, Eq. 8; w = the continuous dendritic
+ * weights of t's channel, K = exp(-r^2/sigma^2)), so its synapse is
+ * l(t) = v(t) / u(t) long on average, with u = sum_s w_s K, v = sum_s w_s K r.
+ *   m    = sum_t a_t l(t) / sum_t a_t     (t with a_t > 0 and u(t) > 0)
+ *   loss = (m - target)^2
+ * out4 = {loss, m, dloss/dsigma, dm/dsigma}; gE, gI (may be NULL: no weight
+ * gradient) = dloss/dw^E, dloss/dw^I.  orc_length_loss sums over the
+ * near-field leaf pairs of the last orc_attraction (returns -1 without one or
+ * with translated pairs); orc_direct_length_loss over all pairs. */
+int orc_length_loss(const orc_ctx *c, const uint8_t *type, const uint8_t *vac_axon,
+                    const double *we, const double *wi, double target, double *out4,
+                    double *gE, double *gI);
+void orc_direct_length_loss(int64_t n, const float *x, const float *y, const float *z,
+                            const uint8_t *type, const uint8_t *vac_axon, const double *we,
+                            const double *wi, double sigma, double target, double *out4,
+                            double *gE, double *gI);
+
 /* Vacancy random walk: v <- clamp(v +- 1, 0, 5) per neuron and channel. */
 void orc_vacancy_walk(int64_t n, uint64_t seed, uint64_t step, uint8_t *vac_axon,
                       uint8_t *vac_dend_e, uint8_t *vac_dend_i);

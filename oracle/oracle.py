@@ -74,6 +74,9 @@ def lib():
             L.orc_attraction_grad.restype = C.c_int
             L.orc_attraction_grad.argtypes = [vp] * 10
             L.orc_direct_grad.argtypes = [i64] + [vp] * 7 + [d] + [vp] * 5
+            L.orc_length_loss.restype = C.c_int
+            L.orc_length_loss.argtypes = [vp] * 5 + [d] + [vp] * 3
+            L.orc_direct_length_loss.argtypes = [i64] + [vp] * 7 + [d, d] + [vp] * 3
             L.orc_vacancy_walk.argtypes = [i64, u64, u64, vp, vp, vp]
             L.orc_expf.restype = C.c_float
             L.orc_expf.argtypes = [C.c_float]
@@ -187,6 +190,24 @@ class Oracle:
         return dict(u=u, dudsigma=du, gE=gE if g is not None else None,
                     gI=gI if g is not None else None)
 
+    def length_loss(self, type_, vac_axon, w_e, w_i, target, grad=True):
+        """Expected mean synapse length m, loss (m - target)^2 and its
+        gradient over the near-field pairs of the last attraction (w_e, w_i:
+        continuous dendritic weights, caller order)."""
+        n = self.n
+        we = np.ascontiguousarray(w_e, dtype=np.float64)
+        wi = np.ascontiguousarray(w_i, dtype=np.float64)
+        ty, va = _u8(type_), _u8(vac_axon)
+        out = np.zeros(4)
+        gE, gI = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+        rc = lib().orc_length_loss(self._h, _p(ty), _p(va), _p(we), _p(wi),
+                                   float(target), _p(out), _p(gE) if grad else None,
+                                   _p(gI) if grad else None)
+        if rc != 0:
+            raise RuntimeError("length_loss needs a finished attraction without far pairs")
+        return dict(loss=out[0], mean=out[1], dloss_dsigma=out[2], dmean_dsigma=out[3],
+                    gE=gE[:n] if grad else None, gI=gI[:n] if grad else None)
+
     def select_partners(self, step: int):
         ne = int(lib().orc_num_elements(self._h))
         m = max(ne, 1)
@@ -286,6 +307,25 @@ def direct_grad(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, g=None):
     u, du, gE, gI = (o[:n] for o in out)
     return dict(u=u, dudsigma=du, gE=gE if g is not None else None,
                 gI=gI if g is not None else None)
+
+
+def direct_length_loss(pos, type_, vac_axon, w_e, w_i, sigma, target, grad=True):
+    """The expected mean synapse length, its loss and gradient by brute force
+    over all pairs (FP64)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = pos.shape[1]
+    we = np.ascontiguousarray(w_e, dtype=np.float64)
+    wi = np.ascontiguousarray(w_i, dtype=np.float64)
+    xs = [np.ascontiguousarray(pos[d]) for d in range(3)]
+    ty, va = _u8(type_), _u8(vac_axon)
+    out = np.zeros(4)
+    gE, gI = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    lib().orc_direct_length_loss(n, *[_p(x) for x in xs],
+                                 _p(ty), _p(va), _p(we), _p(wi), float(sigma),
+                                 float(target), _p(out), _p(gE) if grad else None,
+                                 _p(gI) if grad else None)
+    return dict(loss=out[0], mean=out[1], dloss_dsigma=out[2], dmean_dsigma=out[3],
+                gE=gE[:n] if grad else None, gI=gI[:n] if grad else None)
 
 
 def hermite(nmax: int, x: float):

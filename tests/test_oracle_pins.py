@@ -882,3 +882,112 @@ def test_gradient_u_equals_the_attraction_and_far_pairs_are_refused(oracle_mod):
     assert of.stats()["far_pairs"] > 0
     with pytest.raises(RuntimeError):
         of.attraction_grad(wf.type, wf.vac_axon, wf.vac_dend_e, wf.vac_dend_i)
+
+
+# -- expected mean synapse length (the loss of the differentiation workload) --
+def _len_case(n=220, seed=5, side=3000.0):
+    w = W.uniform_cube(n, side, seed=seed, leaf_capacity=8, rho_max=0.0, cutoff=5.0)
+    rng = np.random.default_rng(seed)
+    we = rng.uniform(0.2, 3.0, w.n)
+    wi = rng.uniform(0.2, 3.0, w.n)
+    return w, we, wi
+
+
+def test_length_loss_of_two_neurons_is_their_distance(oracle_mod):
+    """One axon, one dendrite: every synapse has the same length, the distance
+    (Eq. 1: the only candidate has probability 1), whatever sigma or weight."""
+    pos = np.array([[100.0, 700.0], [200.0, -300.0], [50.0, 1250.0]], np.float32)
+    d = float(np.linalg.norm(pos[:, 0].astype(np.float64) - pos[:, 1]))
+    for sigma in (300.0, 750.0, 2000.0):
+        r = oracle_mod.direct_length_loss(pos, np.zeros(2, np.uint8), np.array([2, 0], np.uint8),
+                                          np.array([0.0, 1.7]), np.zeros(2), sigma, 1000.0)
+        assert r["mean"] == pytest.approx(d, rel=1e-13)
+        assert r["loss"] == pytest.approx((d - 1000.0) ** 2, rel=1e-12)
+        assert abs(r["dmean_dsigma"]) < 1e-12 * d
+        assert np.all(np.abs(r["gE"]) < 1e-9) and np.all(r["gI"] == 0)
+
+
+def test_length_loss_is_homogeneous_in_the_weights(oracle_mod):
+    """Scaling every dendritic weight leaves each partner distribution and so
+    the mean unchanged (degree 0): Euler's identity sum_s w_s dm/dw_s = 0 for
+    the gradient, and the mean itself is invariant."""
+    w, we, wi = _len_case()
+    a = oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, we, wi, 750.0, 1000.0)
+    b = oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, 3.7 * we, 3.7 * wi, 750.0, 1000.0)
+    assert a["mean"] == pytest.approx(b["mean"], rel=1e-13)
+    scale = np.abs(we * a["gE"]).sum() + np.abs(wi * a["gI"]).sum()
+    assert abs(float(we @ a["gE"] + wi @ a["gI"])) < 1e-12 * scale
+
+
+def test_length_loss_limits_in_sigma(oracle_mod):
+    """sigma far below the spacing: each axon reaches its nearest dendrite
+    (the mean tends to the weighted mean nearest-neighbour distance); sigma
+    far above every distance: K -> 1 and the mean is the plain weighted mean
+    distance.  Both written here from the point set."""
+    # 30 pairs 100-200 um apart on a lattice of 2,000 um: at sigma = 150 um every
+    # other neuron is >= 1,800 um away (its terms are below exp(-144))
+    rng = np.random.default_rng(8)
+    centres = np.stack(np.meshgrid(np.arange(5), np.arange(3), np.arange(2)), -1).reshape(-1, 3)
+    centres = centres * 2000.0 + 500.0
+    dirs = rng.normal(size=(30, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    half = rng.uniform(50.0, 100.0, 30)[:, None]
+    pts = np.concatenate([centres - half * dirs, centres + half * dirs]).T.astype(np.float32)
+    n = pts.shape[1]
+    ty = (rng.random(n) < 0.2).astype(np.uint8)
+    va = rng.integers(1, 4, n).astype(np.uint8)
+    we, wi = rng.uniform(0.2, 3.0, n), rng.uniform(0.2, 3.0, n)
+    xp = pts.astype(np.float64)
+    pair_d = np.linalg.norm(xp[:, :30] - xp[:, 30:], axis=0)
+    near = np.concatenate([pair_d, pair_d])
+    ref_small = float((va * near).sum() / va.sum())
+    r = oracle_mod.direct_length_loss(pts, ty, va, we, wi, 150.0, 1000.0)
+    assert r["mean"] == pytest.approx(ref_small, rel=1e-12)
+    w, we, wi = _len_case(n=60, seed=8, side=5000.0)
+    x = w.pos.astype(np.float64)
+    d = np.sqrt(((x[:, :, None] - x[:, None, :]) ** 2).sum(0))
+    act = w.vac_axon > 0
+    np.fill_diagonal(d, 0.0)
+    wt = np.where(w.type[:, None] == 0, we[None, :], wi[None, :])
+    np.fill_diagonal(wt, 0.0)
+    ell = (wt * d).sum(1) / wt.sum(1)
+    ref_big = float((w.vac_axon[act] * ell[act]).sum() / w.vac_axon[act].sum())
+    r = oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, we, wi, 1e8, 1000.0)
+    assert r["mean"] == pytest.approx(ref_big, rel=1e-6)
+
+
+def test_length_loss_gradient_matches_central_differences(oracle_mod):
+    """dloss/dsigma and dloss/dw against central differences of the loss
+    (h = 1e-3 relative for sigma, 1e-4 absolute for a weight)."""
+    w, we, wi = _len_case()
+    sig, tgt = 750.0, 1000.0
+    r = oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, we, wi, sig, tgt)
+    f = lambda s, e, i: oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, e, i, s, tgt,
+                                                      grad=False)["loss"]
+    h = 1e-3 * sig
+    fd = (f(sig + h, we, wi) - f(sig - h, we, wi)) / (2 * h)
+    assert fd == pytest.approx(r["dloss_dsigma"], rel=1e-5)
+    for s in (0, 31, 77, 219):
+        for key, arr in (("gE", we), ("gI", wi)):
+            e, i = we.copy(), wi.copy()
+            (e if key == "gE" else i)[s] += 1e-4
+            up = f(sig, e, i)
+            (e if key == "gE" else i)[s] -= 2e-4
+            dn = f(sig, e, i)
+            assert (up - dn) / 2e-4 == pytest.approx(r[key][s], rel=1e-5, abs=1e-9)
+
+
+def test_length_loss_over_leaf_pairs_equals_all_pairs(oracle_mod):
+    """Pair lists from a tree built with every count 1 at cutoff 5 sigma miss
+    only terms below exp(-25): the list sums equal the all-pairs sums."""
+    w, we, wi = _len_case()
+    ones = np.ones(w.n, np.uint8)
+    o = oracle_mod.Oracle(w.params)
+    o.build_tree(w.pos, w.type, ones, ones, ones)
+    o.attraction()
+    r = o.length_loss(w.type, w.vac_axon, we, wi, 1000.0)
+    ref = oracle_mod.direct_length_loss(w.pos, w.type, w.vac_axon, we, wi, 750.0, 1000.0)
+    for key in ("loss", "mean", "dloss_dsigma", "dmean_dsigma"):
+        assert r[key] == pytest.approx(ref[key], rel=1e-9), key
+    for key in ("gE", "gI"):
+        assert np.max(np.abs(r[key] - ref[key])) < 1e-9 * np.abs(ref[key]).max()
