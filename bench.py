@@ -833,15 +833,56 @@ def batched_record(dev, steps, warmup):
                                             st["n_p2p"])}
 
 
+def length_loss_passes(steps, warmup, dev, target=1000.0):
+    """The loss of the differentiation workload: the expected mean synapse
+    length m, (m - target)^2 and its gradient with respect to sigma and the
+    dendritic weights (msp_length_loss), timed per pass with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2301_10570_gb300 import msp, workloads as W
+    w = W.clustered_small(16, 16_384, seed=15, **GRAD_PLAN)
+    pos, t, a, e, i = msp.to_device(w, dev)
+    ones = torch.ones_like(a)
+    g = msp.MSP(w.params, device=dev.index)
+    g.build_tree(pos, t, ones, ones, ones)
+    g.attraction()
+    rng = np.random.default_rng(7)
+    wE = torch.from_numpy(rng.uniform(0.2, 3.0, w.n)).float().to(dev)
+    wI = torch.from_numpy(rng.uniform(0.2, 3.0, w.n)).float().to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        r = g.length_loss(t, a, wE, wI, target)
+    ms_list = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = g.length_loss(t, a, wE, wI, target)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_list.append(e0.elapsed_time(e1))
+    g.close()
+    return w.n, ms_list, r
+
+
 def gradient_record(dev, steps, warmup):
     n, ms_list, launches, _, inter = gradient_passes(steps, warmup, dev)
     ms = statistics.mean(ms_list)
     peaks = measured_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     p_ex2 = SM_COUNT * EX2_PER_SM_CLK * clk
+    _, lms, r = length_loss_passes(steps, warmup, dev)
     return {"workload": GRAD_DESC, "neurons": n, "steps": steps, "ms_per_pass": round(ms, 3),
             "neurons_per_s": n / (ms / 1e3), "interactions_per_pass": inter,
-            "ex2_frac": round(inter / (ms / 1e3) / p_ex2, 4)}
+            "ex2_frac": round(inter / (ms / 1e3) / p_ex2, 4),
+            "length_loss": {"ms_per_pass": round(statistics.mean(lms), 3),
+                            "neurons_per_s": n / (statistics.mean(lms) / 1e3),
+                            "mean_synapse_length_um": round(r["mean"], 3),
+                            "loss": r["loss"], "dloss_dsigma": r["dloss_dsigma"],
+                            "what": "expected mean synapse length m, (m - 1000 um)^2 and its "
+                                    "gradient in sigma and the dendritic weights, uniform "
+                                    "weights in [0.2, 3]"}}
 
 
 def _oracle_steps(job):

@@ -381,6 +381,39 @@ msp_status msp_attraction_grad(msp_ctx *ctx, const uint8_t *type_dev,
                                float *du_dsigma_dev, float *grad_w_e_dev, float *grad_w_i_dev,
                                void *stream);
 
+/* ---- Expected mean synapse length and its gradient ------------------------
+ * The calibration target of the differentiation workload.  An axonal element
+ * of t draws dendrite s with probability w_s K(t,s) / u(t) (Eq. 1 with the
+ * kernel of Eq. 8, K = exp(-|t - s|^2 / sigma^2); w the continuous dendritic
+ * weights of t's channel), so its synapse is on average
+ *   l(t) = v(t) / u(t) long,  u(t) = sum_s w_s K,  v(t) = sum_s w_s K |t - s|.
+ * Over the vacant axonal elements (a_t > 0, u(t) > 0):
+ *   m = sum_t a_t l(t) / sum_t a_t,   loss = (m - target)^2.
+ *   type_dev, vac_axon_dev   n bytes (caller order): channels and a_t
+ *   w_e_dev, w_i_dev         n floats: dendritic weights per channel
+ *   out4_host                4 doubles out: loss, m, dloss/dsigma, dm/dsigma
+ *   grad_w_e_dev/_i_dev      n floats out (either may be NULL): dloss/dw^E,
+ *                            dloss/dw^I (the transposed sums; K is symmetric)
+ * The sums run over the near-field leaf pairs of the last msp_attraction,
+ * which must have no translated pairs (|t - s| has no Hermite expansion);
+ * build the tree with every count 1 so that no box pair is dropped for empty
+ * counts, and a cutoff of 5 (the sums then miss terms below exp(-25)).
+ * Single precision sums with Kahan-compensated chunks; the scalar reductions
+ * in double, in a fixed order (reproducible).  Errors: MSP_ERR_NOT_BUILT,
+ * MSP_ERR_INVALID_ARG (translated pairs present).  Synchronous. */
+msp_status msp_length_loss(msp_ctx *ctx, const uint8_t *type_dev, const uint8_t *vac_axon_dev,
+                           const float *w_e_dev, const float *w_i_dev, double target,
+                           double *out4_host, float *grad_w_e_dev, float *grad_w_i_dev,
+                           void *stream);
+
+/* Sets the kernel width sigma of the context (the rest of the configuration
+ * stays).  The octree stays (it depends on the positions only); the pair
+ * lists and the pair table depend on sigma (cutoff radius, expansion
+ * boxes), so msp_attraction must run again before the calls that need it,
+ * and captured step graphs are released.  For the calibration of sigma
+ * against a target mean synapse length.  Errors: MSP_ERR_INVALID_ARG. */
+msp_status msp_set_sigma(msp_ctx *ctx, double sigma);
+
 /* Cap on the device memory that the workspaces of all contexts of this
  * process may hold (bytes; 0, the default, means none).  A workspace
  * allocation beyond it fails with MSP_ERR_OOM and leaves the context usable

@@ -35,6 +35,9 @@ void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const u
                      const uint8_t* vdi, const float* g, float* u, float* dud, float* gE,
                      float* gI, cudaStream_t s);
 void scan_wait_selftest(msp_ctx& c, cudaStream_t s);
+void length_loss(msp_ctx& c, const uint8_t* type, const uint8_t* va, const float* we,
+                 const float* wi, double target, double* out4, float* gE, float* gI,
+                 cudaStream_t s);
 void graph_release(msp_ctx& c);
 void graph_capture(msp_ctx& c, const msp_ctx::GraphArgs& args, cudaStream_t s);
 void graph_launch(msp_ctx& c, int64_t n_steps, cudaStream_t s);
@@ -165,7 +168,8 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->gm_key1, &c->gm_q, &c->gm_q1, &c->gm_flag, &c->gm_gid,
                          &c->gm_gstart, &c->gm_ntile, &c->gm_toff, &c->gm_tiles, &c->gm_cnt,
                          &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
-                         &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg,
+                         &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg, &c->ln_sums,
+                         &c->ln_part, &c->ln_coef,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
                          &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
                          &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
@@ -376,6 +380,28 @@ msp_status msp_attraction_grad(msp_ctx* c, const uint8_t* type, const uint8_t* v
         require(c->n == 0 || (type && va && vde && vdi), "null input pointer");
         msp::attraction_grad(*c, type, va, vde, vdi, g, u, du_dsigma, grad_we, grad_wi,
                              as_stream(stream));
+    });
+}
+
+msp_status msp_length_loss(msp_ctx* c, const uint8_t* type, const uint8_t* va, const float* we,
+                           const float* wi, double target, double* out4, float* gE, float* gI,
+                           void* stream) {
+    return guarded(c, [&] {
+        require(out4 != nullptr, "null result pointer");
+        require(c->n == 0 || (type && va && we && wi), "null input pointer");
+        require(std::isfinite(target), "target must be finite");
+        msp::length_loss(*c, type, va, we, wi, target, out4, gE, gI, as_stream(stream));
+    });
+}
+
+msp_status msp_set_sigma(msp_ctx* c, double sigma) {
+    return guarded(c, [&] {
+        require(sigma > 0.0 && std::isfinite(sigma), "sigma must be positive and finite");
+        c->cfg.sigma = sigma;
+        derive(*c);
+        // the pair lists and every captured graph hold the old width
+        c->attraction_done = false;
+        msp::graph_release(*c);
     });
 }
 

@@ -316,6 +316,36 @@ int bits_for_grad(int64_t v) {
 
 }  // namespace
 
+// The near-field pair list regrouped by source leaf (device radix sort of the
+// pair indices by Y): *list receives the pair indices, *segf the first list
+// entry of every source leaf's segment (segment count in dcounts(c)->scan_n).
+void pairs_by_source(msp_ctx& c, cudaStream_t s, const int32_t** segf_out,
+                     const int32_t** list_out) {
+    DevCounts* dc = dcounts(c);
+    const int B = 256;
+    const int64_t nseg_cap = std::max<int64_t>(c.n_nodes, 1);
+    const int64_t cap = std::max<int64_t>(c.n_p2p, 1);
+    uint64_t* k0 = c.gr_key0.ensure<uint64_t>((size_t)cap);
+    uint64_t* k1 = c.gr_key1.ensure<uint64_t>((size_t)cap);
+    int32_t* v0 = c.gr_val0.ensure<int32_t>((size_t)cap);
+    int32_t* v1 = c.gr_val1.ensure<int32_t>((size_t)cap);
+    int32_t* flag = c.gr_flag.ensure<int32_t>((size_t)cap);
+    int32_t* off = c.gr_off.ensure<int32_t>((size_t)cap);
+    int32_t* segf = c.gr_seg.ensure<int32_t>((size_t)nseg_cap + 2);
+    const int Gp = grid_for(cap, B, (int64_t)c.sm_count * 16);
+    k_grad_keys<<<Gp, B, 0, s>>>(c.p2p_val0.get<int32_t>(), &dc->n_p2p, c.pr_Y.get<int32_t>(),
+                                 k0, v0);
+    MSP_LAUNCH("grad_keys");
+    radix_sort_dev(c, k0, v0, k1, v1, &dc->n_p2p, cap, bits_for_grad(c.n_nodes), s);
+    k_grad_seg_flags<<<Gp, B, 0, s>>>(k0, &dc->n_p2p, flag);
+    MSP_LAUNCH("grad_seg_flags");
+    scan_dev(c, flag, off, &dc->n_p2p, cap, &dc->scan_n, nullptr, s);
+    k_grad_seg_first<<<Gp, B, 0, s>>>(flag, off, &dc->n_p2p, &dc->scan_n, segf);
+    MSP_LAUNCH("grad_seg_first");
+    *segf_out = segf;
+    *list_out = v0;
+}
+
 void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const uint8_t* vde,
                      const uint8_t* vdi, const float* g, float* u, float* dud, float* gE,
                      float* gI, cudaStream_t s) {
@@ -353,23 +383,8 @@ void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const u
         float* oI = gI ? gI : c.gr_tmp.ensure<float>((size_t)n);
         MSP_CUDA(cudaMemsetAsync(oE, 0, (size_t)n * sizeof(float), s));
         MSP_CUDA(cudaMemsetAsync(oI, 0, (size_t)n * sizeof(float), s));
-        const int64_t cap = std::max<int64_t>(c.n_p2p, 1);
-        uint64_t* k0 = c.gr_key0.ensure<uint64_t>((size_t)cap);
-        uint64_t* k1 = c.gr_key1.ensure<uint64_t>((size_t)cap);
-        int32_t* v0 = c.gr_val0.ensure<int32_t>((size_t)cap);
-        int32_t* v1 = c.gr_val1.ensure<int32_t>((size_t)cap);
-        int32_t* flag = c.gr_flag.ensure<int32_t>((size_t)cap);
-        int32_t* off = c.gr_off.ensure<int32_t>((size_t)cap);
-        int32_t* segf = c.gr_seg.ensure<int32_t>((size_t)nseg_cap + 2);
-        const int Gp = grid_for(cap, B, (int64_t)c.sm_count * 16);
-        k_grad_keys<<<Gp, B, 0, s>>>(list_q, &dc->n_p2p, c.pr_Y.get<int32_t>(), k0, v0);
-        MSP_LAUNCH("grad_keys");
-        radix_sort_dev(c, k0, v0, k1, v1, &dc->n_p2p, cap, bits_for_grad(c.n_nodes), s);
-        k_grad_seg_flags<<<Gp, B, 0, s>>>(k0, &dc->n_p2p, flag);
-        MSP_LAUNCH("grad_seg_flags");
-        scan_dev(c, flag, off, &dc->n_p2p, cap, &dc->scan_n, nullptr, s);
-        k_grad_seg_first<<<Gp, B, 0, s>>>(flag, off, &dc->n_p2p, &dc->scan_n, segf);
-        MSP_LAUNCH("grad_seg_first");
+        const int32_t *segf = nullptr, *v0 = nullptr;
+        pairs_by_source(c, s, &segf, &v0);
         k_grad_pairs<false><<<nb, kGrWarps * 32, 0, s>>>(
             segf, &dc->scan_n, v0, c.pr_Y.get<int32_t>(), c.pr_X.get<int32_t>(),
             c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), c.pts.get<float4>(), gw,

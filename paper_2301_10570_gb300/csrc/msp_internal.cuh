@@ -196,6 +196,9 @@ struct msp_ctx {
         gm_toff, gm_tiles, gm_cnt;
     // derivatives (msp_grad.cu)
     msp::DBuf gr_w, gr_tmp, gr_key0, gr_key1, gr_val0, gr_val1, gr_flag, gr_off, gr_seg;
+    // expected synapse length (msp_length.cu): per-target sums, block
+    // partials and results, per-target coefficients of the transposed sums
+    msp::DBuf ln_sums, ln_part, ln_coef;
     // expansions
     msp::DBuf expA, expM, expB;
     msp::DBuf u_sorted;

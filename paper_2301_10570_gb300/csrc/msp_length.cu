@@ -1,0 +1,300 @@
+// msp_length.cu -- the expected mean synapse length and its gradient, the
+// loss of the differentiation workload.
+//
+// An axonal element of t draws dendrite s with probability w_s K(t,s) / u(t)
+// (Eq. 1 with the kernel of Eq. 8, K = exp(-r^2/sigma^2); w = the continuous
+// dendritic weights of t's channel), so its synapse is l(t) = v(t)/u(t) long
+// on average, with
+//   u(t) = sum_s w_s K,   v(t) = sum_s w_s K r.
+// Over the vacant axonal elements (a_t > 0, u(t) > 0; A = sum of their a_t):
+//   m = sum_t a_t l(t) / A,   loss = (m - target)^2,
+//   dm/dsigma = sum_t a_t (v' u - v u') / (A u^2),  with ' = d/dsigma:
+//               u' = sum w K 2 r^2 / sigma^3,  v' = sum w K r 2 r^2 / sigma^3,
+//   dm/dw^T_s = sum_{t: T(t) = T} K(t,s) (alpha_t r - beta_t),
+//               alpha_t = a_t / (A u), beta_t = a_t v / (A u^2),
+// and every loss derivative is 2 (m - target) times m's.  The sums run over
+// the near-field leaf pairs of the last attraction (a plan without
+// translations: K r has no Hermite expansion), first grouped by target leaf
+// (u, v and their sigma derivatives), then by source leaf (the transposed
+// sums).  One block per leaf, one evaluation point per thread; the partner
+// leaves' points are staged in shared memory, and each staged chunk's sum is
+// added with Kahan's compensated summation.  Every sum has a fixed order, so
+// the results are reproducible; the scalar reductions run in double.
+#include <algorithm>
+#include <cmath>
+
+#include "msp_internal.cuh"
+
+namespace msp {
+
+void pairs_by_source(msp_ctx& c, cudaStream_t s, const int32_t** segf_out,
+                     const int32_t** list_out);
+
+namespace {
+
+constexpr int kLenThreads = 128;
+constexpr double kLog2e = 1.4426950408889634;
+
+__device__ inline float len_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ inline float len_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ inline void kahan_add(float& acc, float& cmp, float v) {
+    const float y = __fsub_rn(v, cmp);
+    const float t = __fadd_rn(acc, y);
+    cmp = __fsub_rn(__fsub_rn(t, acc), y);
+    acc = t;
+}
+
+// sorted-order inputs: {w^E, w^I, a, type}
+__global__ void k_len_gather(int64_t n, const int32_t* __restrict__ perm,
+                             const uint8_t* __restrict__ type, const uint8_t* __restrict__ va,
+                             const float* __restrict__ we, const float* __restrict__ wi,
+                             float4* __restrict__ gw) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = perm[s];
+        gw[s] = make_float4(we[c], wi[c], (float)va[c], type[c] ? 1.f : 0.f);
+    }
+}
+
+// One block per leaf L of a segment list; its threads take L's points, one
+// each (in rounds of kLenThreads), and every partner leaf P of the segment is
+// staged in shared memory, kLenThreads points at a time.  Coordinates are
+// scaled by sqk = sqrt(log2 e)/sigma relative to L's first point, so that
+// q = |t^ - s^|^2 gives K = 2^-q and r = rs sqrt(q), rs = sigma/sqrt(log2 e).
+//   FORWARD (L = the target leaf): per target t with a_t > 0, the sums
+//     U = sum w K, V = sum w K r, QU = sum w K q, QV = sum w K q r
+//     (w: the staged source's weight of t's channel), written in sorted order.
+//   ADJOINT (L = the source leaf): per point s, for each channel T,
+//     G_T = sum_{t: T(t) = T} K (alpha_t r - beta_t)
+//     over the staged targets t (coefficients in cf), written in caller order.
+template <bool FORWARD>
+__global__ void __launch_bounds__(kLenThreads)
+k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
+            const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
+            const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
+            const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
+            const float4* __restrict__ gw, const float2* __restrict__ cf,
+            const int32_t* __restrict__ perm, float sqk, float rs, float4* __restrict__ sums,
+            float* __restrict__ gE, float* __restrict__ gI) {
+    __shared__ float4 sp[kLenThreads];   // staged point: x^, y^, z^, index (bits)
+    __shared__ float4 sw[kLenThreads];   // FORWARD: w^E, w^I; ADJOINT: alpha, beta, channel
+    const int64_t nseg = *nseg_dev;
+    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+        const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
+        const int32_t L = pEval[pairs[i0]];
+        const int32_t lf = nfirst[L], lc = ncount[L];
+        const float4 O = pts[lf];
+        for (int32_t rb = 0; rb < lc; rb += kLenThreads) {
+            const int32_t e = rb + (int32_t)threadIdx.x;
+            const bool have = e < lc;
+            const int32_t t = lf + (have ? e : 0);
+            const float4 T = pts[t];
+            const float4 TW = gw[t];
+            const bool act = have && (FORWARD ? TW.z > 0.f : true);
+            const bool inh = TW.w != 0.f;
+            const float tx = (T.x - O.x) * sqk, ty = (T.y - O.y) * sqk, tz = (T.z - O.z) * sqk;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;     // running sums
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;     // their compensations
+            for (int32_t i = i0; i < i1; ++i) {
+                const int32_t P = pPart[pairs[i]];
+                const int32_t pf = nfirst[P], pc = ncount[P];
+                for (int32_t sb = 0; sb < pc; sb += kLenThreads) {
+                    const int m = min(kLenThreads, pc - sb);
+                    __syncthreads();
+                    if ((int)threadIdx.x < m) {
+                        const int32_t j = pf + sb + (int32_t)threadIdx.x;
+                        const float4 S = pts[j];
+                        const float4 SW = gw[j];
+                        sp[threadIdx.x] = make_float4((S.x - O.x) * sqk, (S.y - O.y) * sqk,
+                                                      (S.z - O.z) * sqk, __int_as_float(j));
+                        if (FORWARD) {
+                            sw[threadIdx.x] = make_float4(SW.x, SW.y, 0.f, 0.f);
+                        } else {
+                            const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
+                            sw[threadIdx.x] = make_float4(ab.x, ab.y, SW.w, 0.f);
+                        }
+                    }
+                    __syncthreads();
+                    if (!act) continue;
+                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+                    for (int k = 0; k < m; ++k) {
+                        const float4 S = sp[k];
+                        const float4 SW = sw[k];
+                        const float dx = tx - S.x, dy = ty - S.y, dz = tz - S.z;
+                        const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float K = __float_as_int(S.w) == t ? 0.f : len_ex2(-q);
+                        const float r = rs * len_sqrt(q);
+                        if (FORWARD) {
+                            const float wk = (inh ? SW.y : SW.x) * K;
+                            p0 += wk;
+                            p1 = fmaf(wk, r, p1);
+                            p2 = fmaf(wk, q, p2);
+                            p3 = fmaf(wk * q, r, p3);
+                        } else {
+                            const float v = K * fmaf(SW.x, r, -SW.y);
+                            if (SW.z != 0.f) p1 += v; else p0 += v;
+                        }
+                    }
+                    kahan_add(a0, c0, p0);
+                    kahan_add(a1, c1, p1);
+                    if (FORWARD) {
+                        kahan_add(a2, c2, p2);
+                        kahan_add(a3, c3, p3);
+                    }
+                }
+            }
+            if (act) {
+                if (FORWARD) {
+                    sums[t] = make_float4(__fsub_rn(a0, c0), __fsub_rn(a1, c1),
+                                          __fsub_rn(a2, c2), __fsub_rn(a3, c3));
+                } else {
+                    const int32_t o = perm[t];
+                    if (gE) gE[o] = __fsub_rn(a0, c0);
+                    if (gI) gI[o] = __fsub_rn(a1, c1);
+                }
+            }
+        }
+    }
+}
+
+constexpr int kLenRedThreads = 256;
+
+// per block: the partial sums A = sum a, S = sum a V/U, D = sum a (V'U - VU')/U^2
+// over the targets it takes (a > 0, U > 0), in double, reduced in a fixed
+// order; V' / U' are QV / QU times dscale = 2 / (sigma log2 e)
+__global__ void __launch_bounds__(kLenRedThreads)
+k_len_reduce(int64_t n, const float4* __restrict__ gw, const float4* __restrict__ sums,
+             double dscale, double* __restrict__ part) {
+    __shared__ double red[3][kLenRedThreads];
+    double A = 0.0, S = 0.0, D = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float a = gw[t].z;
+        if (!(a > 0.f)) continue;
+        const float4 s4 = sums[t];
+        const double U = s4.x, V = s4.y;
+        if (!(U > 0.0)) continue;
+        const double dU = dscale * s4.z, dV = dscale * s4.w;
+        A += a;
+        S += a * V / U;
+        D += a * (dV * U - V * dU) / (U * U);
+    }
+    red[0][threadIdx.x] = A;
+    red[1][threadIdx.x] = S;
+    red[2][threadIdx.x] = D;
+    __syncthreads();
+    for (int o = kLenRedThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[3 * blockIdx.x + k] = red[k][0];
+}
+
+// the blocks' partials in order; res = {loss, m, dloss/dsigma, dm/dsigma, A, f}
+__global__ void k_len_final(const double* __restrict__ part, int nblocks, double target,
+                            double* __restrict__ res) {
+    double A = 0.0, S = 0.0, D = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        A += part[3 * b];
+        S += part[3 * b + 1];
+        D += part[3 * b + 2];
+    }
+    const double m = A > 0.0 ? S / A : 0.0;
+    const double dm = A > 0.0 ? D / A : 0.0;
+    const double f = 2.0 * (m - target);
+    res[0] = (m - target) * (m - target);
+    res[1] = m;
+    res[2] = f * dm;
+    res[3] = dm;
+    res[4] = A;
+    res[5] = f;
+}
+
+// per target: (f alpha_t, f beta_t), f = 2 (m - target), sorted order
+__global__ void k_len_coef(int64_t n, const float4* __restrict__ gw,
+                           const float4* __restrict__ sums, const double* __restrict__ res,
+                           float2* __restrict__ cf) {
+    const double A = res[4], f = res[5];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float a = gw[t].z;
+        const float4 s4 = sums[t];
+        const double U = s4.x, V = s4.y;
+        float2 c = make_float2(0.f, 0.f);
+        if (a > 0.f && U > 0.0 && A > 0.0)
+            c = make_float2((float)(f * a / (A * U)), (float)(f * a * V / (A * U * U)));
+        cf[t] = c;
+    }
+}
+
+}  // namespace
+
+void length_loss(msp_ctx& c, const uint8_t* type, const uint8_t* va, const float* we,
+                 const float* wi, double target, double* out4, float* gE, float* gI,
+                 cudaStream_t s) {
+    NvtxRange nv_("msp length_loss");
+    if (!c.attraction_done) throw Error(MSP_ERR_NOT_BUILT, "msp_attraction must run first");
+    if (c.n_far > 0)
+        throw Error(MSP_ERR_INVALID_ARG,
+                    "the synapse length needs a plan without translated pairs (rho_max = 0)");
+    const int64_t n = c.n;
+    for (int k = 0; k < 4; ++k) out4[k] = 0.0;
+    if (n == 0) return;
+    const msp_config& cfg = c.cfg;
+    const int B = 256;
+    const int G = grid_for(n, B, (int64_t)c.sm_count * 16);
+    DevCounts* dc = dcounts(c);
+    float4* gw = c.gr_w.ensure<float4>((size_t)n);
+    k_len_gather<<<G, B, 0, s>>>(n, c.perm.get<int32_t>(), type, va, we, wi, gw);
+    MSP_LAUNCH("len_gather");
+    const float sqk = (float)std::sqrt(kLog2e / (cfg.sigma * cfg.sigma));
+    const float rs = (float)(cfg.sigma / std::sqrt(kLog2e));
+    const double dscale = 2.0 / (cfg.sigma * kLog2e);
+    const int64_t nseg_cap = std::max<int64_t>(c.n_nodes, 1);
+    const int nb = (int)std::min<int64_t>(nseg_cap, 1 << 30);
+    float4* sums = c.ln_sums.ensure<float4>((size_t)n);
+    MSP_CUDA(cudaMemsetAsync(sums, 0, (size_t)n * sizeof(float4), s));
+    k_len_pairs<true><<<nb, kLenThreads, 0, s>>>(
+        c.seg_first.get<int32_t>(), &dc->nseg, c.p2p_val0.get<int32_t>(), c.pr_X.get<int32_t>(),
+        c.pr_Y.get<int32_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
+        c.pts.get<float4>(), gw, nullptr, c.perm.get<int32_t>(), sqk, rs, sums, nullptr,
+        nullptr);
+    MSP_LAUNCH("len_forward");
+    const int Gr = (int)std::min<int64_t>(grid_for(n, kLenRedThreads), (int64_t)c.sm_count * 4);
+    double* part = c.ln_part.ensure<double>((size_t)3 * Gr + 8);
+    k_len_reduce<<<Gr, kLenRedThreads, 0, s>>>(n, gw, sums, dscale, part);
+    MSP_LAUNCH("len_reduce");
+    double* res = part + 3 * Gr;
+    k_len_final<<<1, 1, 0, s>>>(part, Gr, target, res);
+    MSP_LAUNCH("len_final");
+    if (gE || gI) {
+        float2* cf = c.ln_coef.ensure<float2>((size_t)n);
+        k_len_coef<<<G, B, 0, s>>>(n, gw, sums, res, cf);
+        MSP_LAUNCH("len_coef");
+        if (gE) MSP_CUDA(cudaMemsetAsync(gE, 0, (size_t)n * sizeof(float), s));
+        if (gI) MSP_CUDA(cudaMemsetAsync(gI, 0, (size_t)n * sizeof(float), s));
+        const int32_t *segf = nullptr, *list = nullptr;
+        pairs_by_source(c, s, &segf, &list);
+        k_len_pairs<false><<<nb, kLenThreads, 0, s>>>(
+            segf, &dc->scan_n, list, c.pr_Y.get<int32_t>(), c.pr_X.get<int32_t>(),
+            c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), c.pts.get<float4>(), gw, cf,
+            c.perm.get<int32_t>(), sqk, rs, nullptr, gE, gI);
+        MSP_LAUNCH("len_adjoint");
+    }
+    MSP_CUDA(cudaMemcpyAsync(out4, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace msp

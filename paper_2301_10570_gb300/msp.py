@@ -34,7 +34,8 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_set_pair_capacity", "msp_batch_layout", "msp_attraction_grad",
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
             "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait",
-            "msp_philox", "msp_step_graph_set_full_build")
+            "msp_philox", "msp_step_graph_set_full_build", "msp_length_loss",
+            "msp_set_sigma")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -152,6 +153,10 @@ def load(path: str = LIB_PATH):
         L.msp_philox.restype = C.c_int
         L.msp_step_graph_set_full_build.argtypes = [vp, C.c_int]
         L.msp_step_graph_set_full_build.restype = C.c_int
+        L.msp_length_loss.argtypes = [vp] * 5 + [C.c_double] + [vp] * 4
+        L.msp_length_loss.restype = C.c_int
+        L.msp_set_sigma.argtypes = [vp, C.c_double]
+        L.msp_set_sigma.restype = C.c_int
         for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
                      "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
@@ -372,6 +377,31 @@ class MSP:
             _ptr(out.get("grad_w_e")), _ptr(out.get("grad_w_i")), _stream(stream)))
         return out
 
+    def length_loss(self, type_, vac_axon, w_e, w_i, target, grad=True, stream=None):
+        """The expected mean synapse length m, the loss (m - target)^2, its
+        sigma derivatives and (grad) dloss/dw^E, dloss/dw^I over the
+        near-field pairs of the last attraction (msp_length_loss)."""
+        n = self.n
+        dev = type_.device
+        ins = [type_.contiguous(), vac_axon.contiguous()]
+        ws = [w_e.to(torch.float32).contiguous(), w_i.to(torch.float32).contiguous()]
+        for t, dt in zip(ins + ws, [torch.uint8] * 2 + [torch.float32] * 2):
+            if t.device != dev or t.dtype != dt or t.numel() != n:
+                raise TypeError(f"length_loss expects {n} entries on {dev} per array")
+        out = np.zeros(4, np.float64)
+        gE = torch.empty(n, dtype=torch.float32, device=dev) if grad else None
+        gI = torch.empty(n, dtype=torch.float32, device=dev) if grad else None
+        _check(load().msp_length_loss(self._h, *[_ptr(t) for t in ins + ws], float(target),
+                                      _np(out), _ptr(gE), _ptr(gI), _stream(stream)))
+        return dict(loss=float(out[0]), mean=float(out[1]), dloss_dsigma=float(out[2]),
+                    dmean_dsigma=float(out[3]), gE=gE, gI=gI)
+
+    def set_sigma(self, sigma: float):
+        """New kernel width; the next attraction rebuilds the pair lists."""
+        _check(load().msp_set_sigma(self._h, float(sigma)))
+        self.params["sigma"] = float(sigma)
+        self._cfg.sigma = float(sigma)
+
     # -- the whole step as a CUDA graph ---------------------------------------
     def step_graph_capture(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, first_step,
                            history_len=0, stream=None):
@@ -472,6 +502,34 @@ class MSP:
         first = np.zeros(1, np.int64)
         _check(load().msp_export_expansions(self._h, _np(A), _np(M), _np(B), _np(first)))
         return A[:m], M[:m], B[:m], int(first[0])
+
+
+class SynapseLengthLoss(torch.autograd.Function):
+    """loss = (m(sigma, w^E, w^I) - target)^2 for the expected mean synapse
+    length m (msp_length_loss) as a differentiable function of sigma (a 0-d
+    tensor) and the dendritic weights (n-vectors): forward sets sigma, redoes
+    the attraction's pair lists and computes the loss and its gradient in
+    the library; backward scales that gradient by the incoming one.
+
+        loss = SynapseLengthLoss.apply(sigma, w_e, w_i, ctx, type_, vac_axon, target)
+    """
+
+    @staticmethod
+    def forward(fctx, sigma, w_e, w_i, ctx, type_, vac_axon, target):
+        ctx.set_sigma(float(sigma))
+        ctx.attraction()
+        r = ctx.length_loss(type_, vac_axon, w_e.detach(), w_i.detach(), float(target), grad=True)
+        fctx.save_for_backward(r["gE"], r["gI"])
+        fctx.dsigma = r["dloss_dsigma"]
+        fctx.mean = r["mean"]
+        return torch.tensor(r["loss"], dtype=torch.float64, device=w_e.device)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        gE, gI = fctx.saved_tensors
+        go = grad_out.to(torch.float64)
+        return (go * fctx.dsigma, (go * gE.double()).to(gE.dtype), (go * gI.double()).to(gI.dtype),
+                None, None, None, None)
 
 
 def direct_noalloc(pos, type_, vac_axon, vac_dend_e, vac_dend_i, sigma, out=None, stream=None):
