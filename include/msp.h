@@ -80,7 +80,22 @@ typedef enum {
  *                  Section 4); 1 the boxes' geometric centres, for which a
  *                  translation depends only on the boxes' offset, so the
  *                  translations of all pairs with one offset run as one
- *                  matrix product (p <= 5)                                 */
+ *                  matrix product (p <= 5)
+ *   mac_mode       which box pairs are expanded: 0 (default) the accuracy
+ *                  rule above (rho_max, separation, m2l_min_pairs); 1 the
+ *                  paper's count rule of Algorithm 2: a pair of inner boxes
+ *                  whose dendrite box holds more than c1 vacant dendritic
+ *                  elements is expanded (Hermite when the axon box also holds
+ *                  more than c2 vacant axonal elements, Taylor otherwise;
+ *                  both run here as the one translation, Eq. 7 re-expanded by
+ *                  Eq. 6), every other pair is refined to exact leaf pairs;
+ *                  no size or distance criterion (every level may carry
+ *                  expansions), the cutoff still prunes, a box is never
+ *                  expanded against itself.  For comparison with the paper
+ *                  (its expansions of boxes much wider than sigma are far
+ *                  from the exact attraction); rho_max and m2l_min_pairs are
+ *                  ignored in this mode
+ *   c1, c2         Algorithm 2's thresholds (the paper: 70 and 70)           */
 typedef struct {
     double    sigma;
     int       p;
@@ -93,6 +108,8 @@ typedef struct {
     double    cutoff;
     long long m2l_min_pairs;
     int       centre_mode;
+    int       mac_mode;
+    int       c1, c2;
 } msp_config;
 
 /* Sizes and operation counts of the last build / attraction / selection. */

@@ -443,6 +443,7 @@ int orc_build_tree(orc_ctx *c, int64_t n, const float *x, const float *y, const 
     c->l_far = cfg->max_depth + 1;
     for (int l = 0; l <= cfg->max_depth; ++l)
         if (side / ldexp(1.0, l + 1) <= cfg->rho_max * cfg->sigma) { c->l_far = l; break; }
+    if (cfg->mac_mode == 1) c->l_far = 0;   /* Algorithm 2 has no size criterion */
     c->g2 = (long long *)malloc((MORTON_BITS + 1) * sizeof(long long));
     for (int l = 0; l <= MORTON_BITS; ++l) {
         double bl = side / ldexp(1.0, l);
@@ -475,6 +476,19 @@ static uint8_t classify(const orc_ctx *c, int32_t xi, int32_t yi)
         if (g > gmax) gmax = g;
     }
     if (gsum >= c->g2[lf]) return ORC_PRUNED;
+    if (c->cfg.mac_mode == 1) {
+        /* Algorithm 2 (choose_target): a leaf on either side is evaluated
+         * directly; an inner dendrite box holding more than c1 vacant
+         * dendritic elements is evaluated by an expansion (Hermite when the
+         * axon box holds more than c2 vacant axonal elements, else Taylor:
+         * here both are the one translation of Eq. 7 by Eq. 6); any other
+         * inner pair directly, i.e. refined down to its leaf pairs.  No box
+         * is expanded against itself (self pairs stay excluded). */
+        if (is_leaf(X) && is_leaf(Y)) return ORC_P2P;
+        if (!is_leaf(X) && !is_leaf(Y) && xi != yi && Y->sw[0] + Y->sw[1] > c->cfg.c1)
+            return ORC_FAR;
+        return ORC_SPLIT;
+    }
     int lmin = X->level < Y->level ? X->level : Y->level;
     if (lmin >= c->l_far && gmax >= 1 &&
         (long long)X->count * (long long)Y->count >= c->cfg.m2l_min_pairs)

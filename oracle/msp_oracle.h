@@ -48,6 +48,10 @@ typedef struct {
     int      centre_mode;    /* expansion centres: 0 the weighted centroids
                                 (Section 3.2, Section 4), 1 the boxes'
                                 geometric centres */
+    int      mac_mode;       /* 1: Algorithm 2's count rule chooses the
+                                expanded pairs (c1 dendrites; c2 would pick
+                                Hermite over Taylor, one translation here) */
+    int      c1, c2;
 } orc_config;
 
 typedef struct orc_ctx orc_ctx;

@@ -50,7 +50,8 @@ class _Cfg(C.Structure):
                 ("max_depth", C.c_int), ("origin", C.c_float * 3), ("side", C.c_float),
                 ("seed", C.c_uint64), ("rho_max", C.c_double), ("cutoff", C.c_double),
                 ("m2l_min_pairs", C.c_longlong), ("boundary_tol", C.c_double),
-                ("centre_mode", C.c_int)]
+                ("centre_mode", C.c_int), ("mac_mode", C.c_int), ("c1", C.c_int),
+                ("c2", C.c_int)]
 
 
 def _p(a):
@@ -128,10 +129,14 @@ def _cfg(params: dict) -> _Cfg:
     c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
     # draws within this relative distance of a CDF boundary are flagged: 1e-6
     # when no pair is translated (single precision sums of exact terms), 1e-5
-    # with translations (their single precision coefficients move W by ~1e-5)
-    c.boundary_tol = float(params.get("boundary_tol",
-                                      1e-6 if float(params["rho_max"]) == 0.0 else 1e-5))
+    # with translations (their single precision coefficients move W by ~1e-5;
+    # the count rule of Algorithm 2 translates whatever rho_max is)
+    translates = float(params["rho_max"]) > 0.0 or int(params.get("mac_mode", 0)) == 1
+    c.boundary_tol = float(params.get("boundary_tol", 1e-5 if translates else 1e-6))
     c.centre_mode = int(params.get("centre_mode", 0))
+    c.mac_mode = int(params.get("mac_mode", 0))
+    c.c1 = int(params.get("c1", 70))
+    c.c2 = int(params.get("c2", 70))
     return c
 
 

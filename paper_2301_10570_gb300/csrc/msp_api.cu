@@ -95,12 +95,14 @@ void derive(msp_ctx& c) {
     const msp_config& cfg = c.cfg;
     c.morton_scale = (float)((double)(1u << msp::kMortonBits) / (double)cfg.side);
     // boxes whose half-width is at most rho_max * sigma may carry expansions
+    // (the count rule of Algorithm 2: boxes of every level)
     c.l_far = cfg.max_depth + 1;
     for (int l = 0; l <= cfg.max_depth; ++l)
         if ((double)cfg.side / std::ldexp(1.0, l + 1) <= cfg.rho_max * cfg.sigma) {
             c.l_far = l;
             break;
         }
+    if (cfg.mac_mode == 1) c.l_far = 0;
     // prune a pair when (sum of squared gaps in boxes of level l) * side_l^2
     // >= (cutoff * sigma)^2
     for (int l = 0; l <= msp::kMortonBits; ++l) {
@@ -123,6 +125,7 @@ msp_status msp_create(msp_ctx** out, const msp_config* cfg, int device) {
         cfg->max_depth < 0 || cfg->max_depth > msp::kMortonBits || !(cfg->side > 0.0f) ||
         !(cfg->rho_max >= 0.0) || !(cfg->cutoff > 0.0) || !(cfg->cutoff <= 5.0) ||
         cfg->m2l_min_pairs < 0 || (cfg->centre_mode != 0 && cfg->centre_mode != 1) ||
+        (cfg->mac_mode != 0 && cfg->mac_mode != 1) || cfg->c1 < 0 || cfg->c2 < 0 ||
         !std::isfinite(cfg->origin[0]) || !std::isfinite(cfg->origin[1]) ||
         !std::isfinite(cfg->origin[2]) || !std::isfinite(cfg->side))
         return fail(MSP_ERR_INVALID_ARG, "configuration value out of range");

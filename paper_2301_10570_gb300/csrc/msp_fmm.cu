@@ -13,6 +13,8 @@ struct Geo {
     long long g2[kMortonBits + 1];   // prune when sum of squared box gaps >= g2[level]
     int l_far;                       // boxes at level >= l_far may carry expansions
     long long m2l_min_pairs;
+    int mac_mode;                    // 1: Algorithm 2's count rule
+    int c1;                          // its dendrite threshold
 };
 
 __device__ inline float ex2_approx(float x) {
@@ -56,11 +58,19 @@ __device__ inline uint8_t classify(const NodeView& nv, const Geo& geo, int32_t X
         if (g > gmax) gmax = g;
     }
     if (gsum >= geo.g2[lf]) return kPruned;
+    const bool leafx = nv.child_first[X] < 0, leafy = nv.child_first[Y] < 0;
+    if (geo.mac_mode == 1) {
+        // Algorithm 2: a leaf side is evaluated directly; an inner dendrite
+        // box with more than c1 vacant dendrites is expanded; else direct
+        if (leafx && leafy) return kP2P;
+        if (!leafx && !leafy && X != Y && sy.z + sy.w > geo.c1) return kFar;
+        return kSplit;
+    }
     int lmin = lx < ly ? lx : ly;
     if (lmin >= geo.l_far && gmax >= 1 &&
         (long long)nv.count[X] * (long long)nv.count[Y] >= geo.m2l_min_pairs)
         return kFar;
-    if (nv.child_first[X] < 0 && nv.child_first[Y] < 0) return kP2P;
+    if (leafx && leafy) return kP2P;
     return kSplit;
 }
 
@@ -547,6 +557,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     for (int l = 0; l <= kMortonBits; ++l) geo.g2[l] = c.g2[l];
     geo.l_far = c.l_far;
     geo.m2l_min_pairs = cfg.m2l_min_pairs;
+    geo.mac_mode = cfg.mac_mode;
+    geo.c1 = cfg.c1;
     const int p = cfg.p, p3 = p * p * p;
     const float inv_sigma = (float)(1.0 / cfg.sigma);
     const float k2 = (float)(1.4426950408889634 / (cfg.sigma * cfg.sigma));

@@ -91,7 +91,8 @@ class Config(C.Structure):
     _fields_ = [("sigma", C.c_double), ("p", C.c_int), ("leaf_capacity", C.c_int),
                 ("max_depth", C.c_int), ("origin", C.c_float * 3), ("side", C.c_float),
                 ("seed", C.c_uint64), ("rho_max", C.c_double), ("cutoff", C.c_double),
-                ("m2l_min_pairs", C.c_longlong), ("centre_mode", C.c_int)]
+                ("m2l_min_pairs", C.c_longlong), ("centre_mode", C.c_int),
+                ("mac_mode", C.c_int), ("c1", C.c_int), ("c2", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -206,6 +207,9 @@ def make_config(params: dict) -> Config:
     c.cutoff = float(params["cutoff"])
     c.m2l_min_pairs = int(params.get("m2l_min_pairs", 0))
     c.centre_mode = int(params.get("centre_mode", 0))
+    c.mac_mode = int(params.get("mac_mode", 0))
+    c.c1 = int(params.get("c1", 70))
+    c.c2 = int(params.get("c2", 70))
     return c
 
 

@@ -69,6 +69,10 @@ CASES = {
     "leaf_capacity_512": lambda: W.clustered_small(1, 16_384, seed=5, leaf_capacity=512,
                                                    cutoff=3.25, rho_max=0.0, p=4,
                                                    m2l_min_pairs=0),
+    # Algorithm 2's count rule (c1 = c2 = 70): inner pairs expanded by their
+    # dendrite counts at every level, boxes of at most ~2 sigma
+    "paper_count_rule_p6": lambda: W.uniform_cube(1500, 3000.0, seed=3, leaf_capacity=8, p=6,
+                                                  mac_mode=1, cutoff=5.0),
 }
 
 # cases whose FP64 brute force runs on sampled targets (all-targets would
@@ -205,7 +209,8 @@ def test_direct_path_matches_oracle_brute_force(name):
 
 
 @pytest.mark.parametrize("name", ["clustered_far_p4", "clustered_far_p6", "ragged_37",
-                                  "geo_far_p4", "geo_far_p5", "geo_far_p6"])
+                                  "geo_far_p4", "geo_far_p5", "geo_far_p6",
+                                  "paper_count_rule_p6"])
 def test_expansions_match_oracle(name):
     w, g, o = run(name)
     A, M, B, first = g["exps"]
@@ -234,7 +239,8 @@ def test_boundary_draws_are_counted_and_few(name, boundary_report):
     w, g, o = run(name)
     ro, st = o["sel"], o["stats"]
     differ = g["partner"] != ro["partner"]
-    band = 1e-6 if float(w.params["rho_max"]) == 0.0 else 1e-5
+    translates = float(w.params["rho_max"]) > 0.0 or int(w.params.get("mac_mode", 0)) == 1
+    band = 1e-5 if translates else 1e-6
     boundary_report[name] = dict(band=band, draws=st["draws"],
                                  boundary_draws=st["boundary_draws"],
                                  flagged=int(ro["near_boundary"].sum()),
