@@ -54,7 +54,7 @@ NF_BYTES_PER_NEURON = 28
 NF_BYTES_PER_PAIR = 20
 # the fastest plan with translated pairs found for the 1M clustered network
 # (profiles/autotune_clustered_1m.md): timed beside the headline
-FMM_TRANSLATED_PLAN = dict(leaf_capacity=64, cutoff=3.25, rho_max=0.25, p=6, m2l_min_pairs=512)
+FMM_TRANSLATED_PLAN = dict(leaf_capacity=64, cutoff=3.5, rho_max=0.35, p=6, m2l_min_pairs=256)
 FP64_SAMPLE = 4096
 
 
@@ -979,6 +979,14 @@ def _case_translations_256k(args):
                           p=args.case_p, centre_mode=args.case_centre_mode)
 
 
+def _case_translations_65k(args):
+    # the uniform density of translations_256k on a quarter of the neurons
+    from paper_2301_10570_gb300 import workloads as W
+    return W.uniform_cube(65_536, 40_000.0 * 0.25 ** (1 / 3), seed=2, name="uniform_65k",
+                          leaf_capacity=8, rho_max=0.55, cutoff=4.0, m2l_min_pairs=0,
+                          p=args.case_p, centre_mode=args.case_centre_mode)
+
+
 def _case_translated_1m(args):
     from paper_2301_10570_gb300 import workloads as W
     return W.clustered_1m(**FMM_TRANSLATED_PLAN)
@@ -1000,6 +1008,7 @@ PROFILE_CASES = {"near_field_131k": (_case_near_field_131k, "steps"),
                  "graph_full_1m": (_case_step_1m, "graph_full"),
                  "neuron_1m": (_case_step_1m, "neuron"),
                  "translations_256k": (_case_translations_256k, "attraction"),
+                 "translations_65k": (_case_translations_65k, "attraction"),
                  "translated_1m": (_case_translated_1m, "attraction"),
                  "gradient_262k": (_case_gradient_262k, "gradient")}
 
@@ -1095,6 +1104,8 @@ def main():
         best, table = autotune.tune(workload(), device=torch.cuda.current_device())
         for row in table:
             print(json.dumps(row), file=sys.stderr)
+        if best is None:
+            raise RuntimeError("no candidate plan meets the accuracy target")
         _PLAN_OVERRIDE = best
     if args.workload in ("gradient_262k", "simulation_1m"):
         out = (run_gradient if args.workload == "gradient_262k" else run_simulation)(

@@ -31,9 +31,10 @@
  *     for the calling thread.  No call throws or aborts.
  *   - Channels: 0 = excitatory, 1 = inhibitory.  An axon of a type-T neuron
  *     connects only to vacant dendritic elements of channel T.
- *   - Results are deterministic for fixed inputs, configuration and step,
- *     except that the near-field and L2P sums of u may differ in the last
- *     bits between runs when far pairs are present.
+ *   - Results are deterministic for fixed inputs, configuration and step
+ *     (every sum has a fixed order), except with centre_mode 1, whose grouped
+ *     translations add into the Taylor coefficients atomically: there u may
+ *     differ in the last bits between runs.
  */
 #ifndef MSP_H
 #define MSP_H

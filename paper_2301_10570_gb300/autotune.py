@@ -41,7 +41,8 @@ def _step_ms(g, dev, reps):
 
 
 def tune(workload, tol=1e-4, ref_err=1e-6, candidates=None, reps=4, device=0, verbose=False):
-    """Return (best plan dict, list of per-candidate results)."""
+    """Return (best plan dict, list of per-candidate results); the plan is
+    None when no candidate meets the accuracy target."""
     import torch
 
     from . import msp
@@ -77,6 +78,6 @@ def tune(workload, tol=1e-4, ref_err=1e-6, candidates=None, reps=4, device=0, ve
             print(results[-1], flush=True)
     accepted = [r for r in results if r.get("accepted")]
     if not accepted:
-        raise RuntimeError("no candidate plan meets the accuracy target")
+        return None, results
     best = min(accepted, key=lambda r: r["step_ms"])
     return best["plan"], results

@@ -286,90 +286,199 @@ k_p2m(int64_t first_node, int p, float inv_sigma, const float4* __restrict__ pts
 }
 
 // ---------------------------------------------------------------------------
-// a7: translation of one channel, cooperatively by a warp.  With
-// Delta = (c_A - c_D)/sigma and H_d[n] = h_n(Delta_d):
-//   B_beta = (-1)^|beta| / beta!  sum_alpha A_alpha H0[a0+b0] H1[a1+b1] H2[a2+b2]
-// done as three passes over one dimension each (p^4 multiply-adds per pass).
-// On return Bout (shared) holds B; the return value is sum_beta B_beta M_beta.
+// a7: translations.  With Delta = (c_A - c_D)/sigma and H_d[n] = h_n(Delta_d),
+//   B_beta(X <- Y) = (-1)^|beta| / beta!  sum_alpha A_alpha(Y) H0[a0+b0] H1[a1+b1] H2[a2+b2]
+// done as three passes over one dimension each (p^4 multiply-adds per pass
+// and channel), and W(X,Y) = sum_beta B_beta(X <- Y) M_beta(X).  The far pairs
+// are grouped by target box X (stable sort of the list by X); one warp takes
+// all pairs of one X in list order, so B(X) = sum_Y B(X <- Y) is summed in
+// registers in a fixed order (reproducible, no atomics) and added to B once.
+// A pass is one column per lane (channel and the two indices it does not
+// sum over), staged through the warp's shared memory between passes; the
+// last pass's columns are the lane's own for every pair of X.
 // ---------------------------------------------------------------------------
-__device__ inline void hermite_table(float x, int nmax, float* h) {
-    float h0 = __expf(-x * x);
+__device__ inline void hermite_row(float x, float* h, int nmax) {
+    const float h0 = __expf(-x * x);
     h[0] = h0;
     if (nmax >= 1) h[1] = 2.f * x * h0;
     for (int k = 1; k < nmax; ++k) h[k + 1] = 2.f * x * h[k] - 2.f * (float)k * h[k - 1];
 }
 
-__device__ float warp_m2l(int p, const float* __restrict__ Ag, const float* __restrict__ Mg,
-                          const float* H /*smem 3 x 16*/, float* src, float* t1, float* Bout) {
-    const int lane = threadIdx.x & 31;
-    const int p2 = p * p, p3 = p2 * p;
-    for (int i = lane; i < p3; i += 32) src[i] = Ag[i];
-    __syncwarp();
-    for (int o = lane; o < p3; o += 32) {        // (b0, a1, a2)
-        int b0 = o / p2, r = o - b0 * p2;
-        float s = 0.f;
-        for (int a0 = 0; a0 < p; ++a0) s = fmaf(H[a0 + b0], src[a0 * p2 + r], s);
-        t1[o] = s;
-    }
-    __syncwarp();
-    for (int o = lane; o < p3; o += 32) {        // (b0, b1, a2)
-        int b0 = o / p2, b1 = (o / p) % p, a2 = o % p;
-        float s = 0.f;
-        for (int a1 = 0; a1 < p; ++a1) s = fmaf(H[16 + a1 + b1], t1[b0 * p2 + a1 * p + a2], s);
-        src[o] = s;
-    }
-    __syncwarp();
-    float w = 0.f;
-    for (int o = lane; o < p3; o += 32) {        // (b0, b1, b2)
-        int b0 = o / p2, b1 = (o / p) % p, b2 = o % p;
-        float s = 0.f;
-        for (int a2 = 0; a2 < p; ++a2) s = fmaf(H[32 + a2 + b2], src[b0 * p2 + b1 * p + a2], s);
-        float sc = c_inv_fact[b0] * c_inv_fact[b1] * c_inv_fact[b2];
-        if ((b0 + b1 + b2) & 1) sc = -sc;
-        s *= sc;
-        Bout[o] = s;
-        w = fmaf(s, Mg[o], w);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    __syncwarp();
-    return w;
-}
-
 constexpr int kM2LWarps = 4;
 
+template <int P>
 __global__ void __launch_bounds__(kM2LWarps * 32)
-k_m2l(const int32_t* __restrict__ far_q, const int64_t* __restrict__ nfar_dev,
-      const int64_t* __restrict__ first_dev, int64_t exp_first,
-      int p, float inv_sigma, const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
-      const float4* __restrict__ ca, const float4* __restrict__ cd, const float* __restrict__ A,
-      const float* __restrict__ M, float* __restrict__ B, double2* __restrict__ pw) {
-    __shared__ float sH[kM2LWarps][48];
-    __shared__ float sbuf[kM2LWarps][3][kMaxP * kMaxP * kMaxP];
+k_m2l_seg(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
+          const int32_t* __restrict__ list, int64_t exp_first, float inv_sigma,
+          const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
+          const float4* __restrict__ ca, const float4* __restrict__ cd,
+          const float* __restrict__ A, const float* __restrict__ M, float* __restrict__ B,
+          double2* __restrict__ pw) {
+    constexpr int P2 = P * P, P3 = P2 * P;
+    constexpr int NC = 2 * P2;                 // columns of a pass (two channels)
+    constexpr int NL = (NC + 31) / 32;         // columns per lane
+    constexpr int NH = 2 * P - 1;              // Hermite functions h_0 .. h_{2p-2}
+    __shared__ float sbuf[kM2LWarps][2][2 * P3];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p3 = p * p * p;
-    const int64_t nfar = *nfar_dev;
-    const int64_t k0 = first_dev ? *first_dev : 0;   // pairs [k0, nfar)
-    for (int64_t k = k0 + (int64_t)blockIdx.x * kM2LWarps + w; k < nfar;
-         k += (int64_t)gridDim.x * kM2LWarps) {
-        int32_t q = far_q[k];
-        int32_t X = pX[q], Y = pY[q];
-        float4 a = ca[X], d = cd[Y];
-        if (lane < 3) {
-            float dl = (lane == 0 ? a.x - d.x : (lane == 1 ? a.y - d.y : a.z - d.z)) * inv_sigma;
-            hermite_table(dl, 2 * p - 2, &sH[w][16 * lane]);
+    float* s0 = sbuf[w][0];
+    float* s1 = sbuf[w][1];
+    // (-1)^|beta| / beta! of the lane's last-pass columns (c, b0, b1)
+    float scale[NL][P];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        const int col = lane + 32 * j;
+        const int b0 = (col / P) % P, b1 = col % P;
+#pragma unroll
+        for (int b2 = 0; b2 < P; ++b2) {
+            const float f = c_inv_fact[b0] * c_inv_fact[b1] * c_inv_fact[b2];
+            scale[j][b2] = ((b0 + b1 + b2) & 1) ? -f : f;
         }
-        __syncwarp();
-        int64_t ex = X - exp_first, ey = Y - exp_first;
-        float wch[2];
-        for (int ch = 0; ch < 2; ++ch) {
-            wch[ch] = warp_m2l(p, A + (ey * 2 + ch) * p3, M + (ex * 2 + ch) * p3, sH[w],
-                               sbuf[w][0], sbuf[w][1], sbuf[w][2]);
-            for (int i = lane; i < p3; i += 32) atomicAdd(&B[(ex * 2 + ch) * p3 + i], sbuf[w][2][i]);
+    }
+    const int64_t nseg = *nseg_dev;
+    for (int64_t sg = (int64_t)blockIdx.x * kM2LWarps + w; sg < nseg;
+         sg += (int64_t)gridDim.x * kM2LWarps) {
+        const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
+        const int32_t X = pX[list[i0]];
+        const int64_t ex = X - exp_first;
+        const float4 a = ca[X];
+        float acc[NL][P], mm[NL][P];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+            const int col = lane + 32 * j;
+            const int c = col / P2, b0 = (col / P) % P, b1 = col % P;
+#pragma unroll
+            for (int b2 = 0; b2 < P; ++b2) {
+                acc[j][b2] = 0.f;
+                mm[j][b2] = col < NC ? M[(ex * 2 + c) * P3 + b0 * P2 + b1 * P + b2] : 0.f;
+            }
+        }
+        // the next pair's list entry, centre and coefficients are loaded
+        // while the current pair is translated (a chain of dependent loads)
+        constexpr int NA = (2 * P3 + 31) / 32;     // coefficients per lane
+        int32_t qn = list[i0];
+        int32_t yn = pY[qn];
+        float4 dn = cd[yn];
+        float an[NA];
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const int e = lane + 32 * k;
+            an[k] = e < 2 * P3 ? A[(yn - exp_first) * 2 * P3 + e] : 0.f;
+        }
+        for (int32_t i = i0; i < i1; ++i) {
+            const int32_t q = qn;
+            const float4 d = dn;
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                const int e = lane + 32 * k;
+                if (e < 2 * P3) s0[e] = an[k];
+            }
+            if (i + 1 < i1) {
+                qn = list[i + 1];
+                yn = pY[qn];
+                dn = cd[yn];
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    const int e = lane + 32 * k;
+                    an[k] = e < 2 * P3 ? A[(yn - exp_first) * 2 * P3 + e] : 0.f;
+                }
+            }
+            float H[NH];
+            hermite_row((a.x - d.x) * inv_sigma, H, NH - 1);
             __syncwarp();
+            // pass 0 (over a0): column (c, a1, a2) -> s1[c][b0][a1][a2]
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                const int col = lane + 32 * j;
+                if (col >= NC) break;
+                const int c = col / P2, r = col % P2;
+                float v[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) v[k] = s0[c * P3 + k * P2 + r];
+#pragma unroll
+                for (int o = 0; o < P; ++o) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int k = 0; k < P; ++k) t = fmaf(H[k + o], v[k], t);
+                    s1[c * P3 + o * P2 + r] = t;
+                }
+            }
+            hermite_row((a.y - d.y) * inv_sigma, H, NH - 1);
+            __syncwarp();
+            // pass 1 (over a1): column (c, b0, a2) -> s0[c][b0][b1][a2]
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                const int col = lane + 32 * j;
+                if (col >= NC) break;
+                const int c = col / P2, b0 = (col / P) % P, a2 = col % P;
+                const int base = c * P3 + b0 * P2 + a2;
+                float v[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) v[k] = s1[base + k * P];
+#pragma unroll
+                for (int o = 0; o < P; ++o) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int k = 0; k < P; ++k) t = fmaf(H[k + o], v[k], t);
+                    s0[base + o * P] = t;
+                }
+            }
+            hermite_row((a.z - d.z) * inv_sigma, H, NH - 1);
+            __syncwarp();
+            // pass 2 (over a2): the lane's own columns (c, b0, b1)
+            float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                const int col = lane + 32 * j;
+                if (col >= NC) break;
+                const int base = (col / P2) * P3 + (col % P2) * P;
+                float v[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) v[k] = s0[base + k];
+                float wc = 0.f;
+#pragma unroll
+                for (int o = 0; o < P; ++o) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int k = 0; k < P; ++k) t = fmaf(H[k + o], v[k], t);
+                    t *= scale[j][o];
+                    acc[j][o] += t;
+                    wc = fmaf(t, mm[j][o], wc);
+                }
+                if (col < P2) w0 += wc; else w1 += wc;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+            }
+            if (lane == 0) pw[q] = make_double2((double)w0, (double)w1);
+            __syncwarp();      // s0 is the next pair's staging
         }
-        if (lane == 0) pw[q] = make_double2((double)wch[0], (double)wch[1]);
-        __syncwarp();
+        // B(X) += the sum over X's far pairs (no other warp adds to B(X) here)
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+            const int col = lane + 32 * j;
+            if (col >= NC) break;
+            const int c = col / P2, b0 = (col / P) % P, b1 = col % P;
+            float* Bx = B + (ex * 2 + c) * P3 + b0 * P2 + b1 * P;
+#pragma unroll
+            for (int b2 = 0; b2 < P; ++b2) Bx[b2] += acc[j][b2];
+        }
+    }
+}
+
+// keys of the far pairs [first, nfar) of `list` for the grouping by target box
+__global__ void k_m2l_keys(const int32_t* __restrict__ list, const int64_t* __restrict__ nfar,
+                           const int64_t* __restrict__ first, const int32_t* __restrict__ pX,
+                           uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                           int64_t* __restrict__ count) {
+    const int64_t k0 = first ? *first : 0, n = *nfar - k0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = n > 0 ? n : 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = list[k0 + i];
+        key[i] = (uint64_t)pX[q];
+        val[i] = q;
     }
 }
 
@@ -661,9 +770,37 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
             mq = m2l_gemm(c, far_q, &dc->n_far, cap, eA, eM, eB, c.pr_w.get<double2>(), &fb, s);
             first = fb;
         }
-        k_m2l<<<(int)c.sm_count * 8, kM2LWarps * 32, 0, s>>>(
-            mq, &dc->n_far, first, c.exp_first, p, inv_sigma, c.pr_X.get<int32_t>(),
-            c.pr_Y.get<int32_t>(), eca, ecd, eA, eM, eB, c.pr_w.get<double2>());
+        // the pairs [first, n_far) of mq grouped by target box
+        uint64_t* mk0 = c.m2_key0.ensure<uint64_t>((size_t)cap);
+        uint64_t* mk1 = c.m2_key1.ensure<uint64_t>((size_t)cap);
+        int32_t* mv0 = c.m2_val0.ensure<int32_t>((size_t)cap);
+        int32_t* mv1 = c.m2_val1.ensure<int32_t>((size_t)cap);
+        int32_t* mflag = c.m2_flag.ensure<int32_t>((size_t)cap);
+        int32_t* moff = c.m2_off.ensure<int32_t>((size_t)cap);
+        int32_t* mseg = c.m2_seg.ensure<int32_t>((size_t)c.n_nodes + 2);
+        k_m2l_keys<<<Gt, B, 0, s>>>(mq, &dc->n_far, first, c.pr_X.get<int32_t>(), mk0, mv0,
+                                    &dc->m2l_n);
+        MSP_LAUNCH("m2l_keys");
+        radix_sort_dev(c, mk0, mv0, mk1, mv1, &dc->m2l_n, cap, bits_for(c.n_nodes), s);
+        k_seg_flags<<<Gt, B, 0, s>>>(mk0, &dc->m2l_n, mflag);
+        MSP_LAUNCH("m2l_seg_flags");
+        scan_dev(c, mflag, moff, &dc->m2l_n, cap, &dc->m2l_nseg, nullptr, s);
+        k_seg_first<<<Gt, B, 0, s>>>(mflag, moff, &dc->m2l_n, &dc->m2l_nseg, mseg);
+        MSP_LAUNCH("m2l_seg_first");
+        const int gm = (int)c.sm_count * 8;
+#define MSP_M2L_CASE(PP)                                                                       \
+    case PP:                                                                                   \
+        k_m2l_seg<PP><<<gm, kM2LWarps * 32, 0, s>>>(mseg, &dc->m2l_nseg, mv0, c.exp_first,    \
+                                                    inv_sigma, c.pr_X.get<int32_t>(),         \
+                                                    c.pr_Y.get<int32_t>(), eca, ecd, eA, eM,  \
+                                                    eB, c.pr_w.get<double2>());               \
+        break;
+        switch (p) {
+            MSP_M2L_CASE(1) MSP_M2L_CASE(2) MSP_M2L_CASE(3) MSP_M2L_CASE(4)
+            MSP_M2L_CASE(5) MSP_M2L_CASE(6) MSP_M2L_CASE(7) MSP_M2L_CASE(8)
+            default: throw Error(MSP_ERR_INVALID_ARG, "expansion order out of range");
+        }
+#undef MSP_M2L_CASE
         MSP_LAUNCH("m2l");
     }
     // a8: Taylor evaluation initialises u in sorted order; a9 adds the near field
