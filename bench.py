@@ -866,6 +866,19 @@ def length_loss_passes(steps, warmup, dev, target=1000.0):
     return w.n, ms_list, r
 
 
+def simulation_record(steps, warmup):
+    """The model's simulation cycle on the 1M clustered network (100 neuron
+    steps, the update of synapses and one synapse search whose synapses join
+    the network): a few timed cycles."""
+    sargs = argparse.Namespace(steps=steps, warmup=warmup)
+    r = run_simulation(sargs, 0, 1)
+    return {"workload": r["config"]["workload"], "cycles": steps,
+            "ms_per_cycle": r["ms_per_step"], "neuron_steps_per_s": r["value"],
+            "neuron_steps_ms_per_cycle": r["config"]["neuron_steps_ms_per_cycle"],
+            "edges_mean": r["config"]["edges_mean"],
+            "neuron_step_hbm_frac": r["roofline"]["frac"]}
+
+
 def gradient_record(dev, steps, warmup):
     n, ms_list, launches, _, inter = gradient_passes(steps, warmup, dev)
     ms = statistics.mean(ms_list)
@@ -1128,6 +1141,7 @@ def main():
                 out["fmm_translated"] = fmm_translated_record(w, dev, idx, ref)
             out["batched_256"] = batched_record(dev, 3, 2)
             out["gradient_262k"] = gradient_record(dev, 3, 2)
+            out["simulation_1m"] = simulation_record(3, 2)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

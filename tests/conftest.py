@@ -38,7 +38,21 @@ def boundary_report(request):
     return request.config._msp_boundary
 
 
+@pytest.fixture(scope="session")
+def precision_report(request):
+    """Observed errors of the GPU results against the FP64 oracle, per
+    quantity and case (printed in the run's summary)."""
+    if not hasattr(request.config, "_msp_precision"):
+        request.config._msp_precision = {}
+    return request.config._msp_precision
+
+
 def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    prec = getattr(config, "_msp_precision", None)
+    if prec:
+        terminalreporter.write_sep("-", "observed errors against the FP64 oracle")
+        for key in sorted(prec):
+            terminalreporter.write_line(f"{key}: {prec[key]:.3e}")
     rep = getattr(config, "_msp_boundary", None)
     if not rep:
         return
