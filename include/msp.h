@@ -321,7 +321,10 @@ msp_status msp_append_synapses(msp_ctx *ctx, const int64_t *n_syn_dev, int64_t s
  *
  * Capture requirements: msp_build_tree and msp_attraction have run on the
  * same positions x/y/z (their tree depth and pair-table size give the
- * graph's capacities).  The positions and types must not change while the
+ * graph's capacities).  Unless the full-build option is set, the replays
+ * keep that build's octree and that attraction's traversal and pair lists
+ * (they depend on the positions only, for mac_mode 0) and redo the counts,
+ * aggregates, expansions, near field, pair table and everything after.  The positions and types must not change while the
  * graph is in use (neurons do not move in the model); the vacant counts are
  * the run's state, changed only by the graph (walk and commit).
  *   x/y/z/type_dev     n neurons, read every replay
@@ -387,10 +390,10 @@ msp_status msp_set_pair_capacity(msp_ctx *ctx, int64_t pairs);
  * weights w^E, w^I (the transposed Gauss transform; dL/dsigma is
  * sum_t g_t du_dsigma(t)).  The sums run over the near-field leaf pairs of
  * the last msp_attraction, which must have no translated pairs
- * (rho_max = 0).  Box pairs whose dendrite box had no vacant dendrites in the
- * build are absent; to differentiate with respect to weights that are zero,
- * build the tree with every count positive (e.g. all ones): the counts passed
- * here are the ones the derivatives are taken at.  g may be NULL (then
+ * (rho_max = 0).  The lists depend on the positions only (no box pair is
+ * dropped for empty counts), so the derivatives with respect to weights that
+ * are zero are complete; the counts passed here are the ones the derivatives
+ * are taken at.  g may be NULL (then
  * grad_w_* must be NULL); any output may be NULL.  Errors: MSP_ERR_NOT_BUILT,
  * MSP_ERR_INVALID_ARG (translated pairs present).  Asynchronous. */
 msp_status msp_attraction_grad(msp_ctx *ctx, const uint8_t *type_dev,
@@ -414,8 +417,7 @@ msp_status msp_attraction_grad(msp_ctx *ctx, const uint8_t *type_dev,
  *                            dloss/dw^I (the transposed sums; K is symmetric)
  * The sums run over the near-field leaf pairs of the last msp_attraction,
  * which must have no translated pairs (|t - s| has no Hermite expansion);
- * build the tree with every count 1 so that no box pair is dropped for empty
- * counts, and a cutoff of 5 (the sums then miss terms below exp(-25)).
+ * use a cutoff of 5 (the sums then miss terms below exp(-25)).
  * Single precision sums with Kahan-compensated chunks; the scalar reductions
  * in double, in a fixed order (reproducible).  Errors: MSP_ERR_NOT_BUILT,
  * MSP_ERR_INVALID_ARG (translated pairs present).  Synchronous. */

@@ -460,8 +460,11 @@ static int is_leaf(const node_t *nd) { return nd->child_first < 0; }
 
 static uint8_t classify(const orc_ctx *c, int32_t xi, int32_t yi)
 {
+    /* Pairs are pruned by the cutoff only.  A pair without vacant axonal or
+     * dendritic elements attracts with exactly zero and is never chosen by
+     * the descent, so keeping it changes no result; the lists then depend on
+     * the positions alone. */
     const node_t *X = &c->nodes[xi], *Y = &c->nodes[yi];
-    if (X->sa[0] + X->sa[1] == 0 || Y->sw[0] + Y->sw[1] == 0) return ORC_PRUNED;
     int lf = X->level > Y->level ? X->level : Y->level;
     long long gsum = 0, gmax = 0;
     for (int d = 0; d < 3; ++d) {

@@ -38,9 +38,12 @@ struct NodeView {
     const int4* sums;
 };
 
+// A pair is pruned by the cutoff only: a box pair without vacant axonal or
+// dendritic elements contributes exactly zero (log2 0 = -inf in every term,
+// or no target), so the lists depend on the positions alone and the step
+// graph can keep them across steps.
 __device__ inline uint8_t classify(const NodeView& nv, const Geo& geo, int32_t X, int32_t Y) {
-    int4 sx = nv.sums[X], sy = nv.sums[Y];
-    if (sx.x + sx.y == 0 || sy.z + sy.w == 0) return kPruned;
+    const int4 sy = nv.sums[Y];
     int lx = nv.level[X], ly = nv.level[Y];
     int lf = lx > ly ? lx : ly;
     uint64_t px = nv.prefix[X], py = nv.prefix[Y];
@@ -90,6 +93,12 @@ __global__ void k_init_pairs(int64_t n, int32_t* pX, int32_t* pY, DevCounts* dc)
         pX[0] = 0;
         pY[0] = 0;
     }
+}
+
+// a replay that keeps the lists: only the near field's work counter restarts
+__global__ void k_reuse_init(DevCounts* dc) {
+    dc->overflow &= ~1ll;
+    dc->interactions = 0;
 }
 
 // pairs of one depth: [db[0], db[1]); their count goes to *scan_n
@@ -676,6 +685,10 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     // traversal depth d holds the pairs whose finer box is at level d, so the
     // tree depth bounds the number of depths
     const int D = c.tree_depth + 1;
+    // replays of the step graph that reuse the octree keep the traversal and
+    // its lists too: the cutoff rule depends on the positions only (the count
+    // rule of Algorithm 2 depends on the vacant counts and is redone)
+    const bool reuse_lists = c.graph_mode && !c.graph_full_build && cfg.mac_mode == 0;
     if (c.pair_cap <= 0) c.pair_cap = std::max<int64_t>(64 * c.n_nodes, 1 << 16);
     const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
     for (int attempt = 0;; ++attempt) {
@@ -691,6 +704,17 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     int32_t* off = c.off.ensure<int32_t>((size_t)cap);
     uint8_t* kind = c.pr_kind.get<uint8_t>();
 
+    int32_t* far_q = c.far_q.ensure<int32_t>((size_t)cap);
+    int32_t* pv0 = c.p2p_val0.ensure<int32_t>((size_t)cap);
+    int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)c.n_nodes + 2);
+    const int64_t* n_pairs_dev = &dc->depth_start[D];
+    if (reuse_lists) {
+        // the step graph's replays keep the traversal and the lists of the
+        // eager attraction of the same positions (guarded by the build's
+        // checksum and generation stamp)
+        k_reuse_init<<<1, 1, 0, s>>>(dc);
+        MSP_LAUNCH("reuse_init");
+    } else {
     // a5: breadth-first dual traversal from (root, root)
     k_init_pairs<<<1, 1, 0, s>>>(n, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(), dc);
     MSP_LAUNCH("init_pairs");
@@ -706,14 +730,12 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
                                       &dc->overflow);
         MSP_LAUNCH("emit_pairs");
     }
-    const int64_t* n_pairs_dev = &dc->depth_start[D];
 
     // far and near-field lists
     int32_t* flag = cnt;
     k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kFar, flag);
     MSP_LAUNCH("flag_far");
     scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_far, nullptr, s);
-    int32_t* far_q = c.far_q.ensure<int32_t>((size_t)cap);
     k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kFar, off, c.pr_X.get<int32_t>(), far_q,
                                     nullptr);
     MSP_LAUNCH("compact_far");
@@ -722,7 +744,6 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_p2p, nullptr, s);
     uint64_t* pk0 = c.p2p_key0.ensure<uint64_t>((size_t)cap);
     uint64_t* pk1 = c.p2p_key1.ensure<uint64_t>((size_t)cap);
-    int32_t* pv0 = c.p2p_val0.ensure<int32_t>((size_t)cap);
     int32_t* pv1 = c.p2p_val1.ensure<int32_t>((size_t)cap);
     k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kP2P, off, c.pr_X.get<int32_t>(), pv0, pk0);
     MSP_LAUNCH("compact_p2p");
@@ -733,9 +754,9 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     MSP_LAUNCH("seg_flags");
     scan_dev(c, sflag, soff, &dc->n_p2p, cap, &dc->nseg, nullptr, s);
     // at most one segment per box
-    int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)c.n_nodes + 2);
     k_seg_first<<<Gt, B, 0, s>>>(sflag, soff, &dc->n_p2p, &dc->nseg, seg_first);
     MSP_LAUNCH("seg_first");
+    }
 
     // a6: expansions of every box at level >= l_far
     c.exp_first = c.l_far <= c.tree_depth ? c.level_start[c.l_far] : c.n_nodes;
@@ -778,15 +799,17 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
         int32_t* mflag = c.m2_flag.ensure<int32_t>((size_t)cap);
         int32_t* moff = c.m2_off.ensure<int32_t>((size_t)cap);
         int32_t* mseg = c.m2_seg.ensure<int32_t>((size_t)c.n_nodes + 2);
-        k_m2l_keys<<<Gt, B, 0, s>>>(mq, &dc->n_far, first, c.pr_X.get<int32_t>(), mk0, mv0,
-                                    &dc->m2l_n);
-        MSP_LAUNCH("m2l_keys");
-        radix_sort_dev(c, mk0, mv0, mk1, mv1, &dc->m2l_n, cap, bits_for(c.n_nodes), s);
-        k_seg_flags<<<Gt, B, 0, s>>>(mk0, &dc->m2l_n, mflag);
-        MSP_LAUNCH("m2l_seg_flags");
-        scan_dev(c, mflag, moff, &dc->m2l_n, cap, &dc->m2l_nseg, nullptr, s);
-        k_seg_first<<<Gt, B, 0, s>>>(mflag, moff, &dc->m2l_n, &dc->m2l_nseg, mseg);
-        MSP_LAUNCH("m2l_seg_first");
+        if (!reuse_lists || geo) {
+            k_m2l_keys<<<Gt, B, 0, s>>>(mq, &dc->n_far, first, c.pr_X.get<int32_t>(), mk0, mv0,
+                                        &dc->m2l_n);
+            MSP_LAUNCH("m2l_keys");
+            radix_sort_dev(c, mk0, mv0, mk1, mv1, &dc->m2l_n, cap, bits_for(c.n_nodes), s);
+            k_seg_flags<<<Gt, B, 0, s>>>(mk0, &dc->m2l_n, mflag);
+            MSP_LAUNCH("m2l_seg_flags");
+            scan_dev(c, mflag, moff, &dc->m2l_n, cap, &dc->m2l_nseg, nullptr, s);
+            k_seg_first<<<Gt, B, 0, s>>>(mflag, moff, &dc->m2l_n, &dc->m2l_nseg, mseg);
+            MSP_LAUNCH("m2l_seg_first");
+        }
         const int gm = (int)c.sm_count * 8;
 #define MSP_M2L_CASE(PP)                                                                       \
     case PP:                                                                                   \
@@ -812,7 +835,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
             c.nd_parent.get<int32_t>(), eca, eB, us);
         MSP_LAUNCH("l2p");
         MSP_CUDA(cudaEventRecordWithFlags(c.ev_nf0, s, ev_flags));
-        launch_near_field(c, seg_first, &dc->nseg, c.n_nodes, pv0, &dc->n_p2p, cap, us, work, s);
+        launch_near_field(c, seg_first, &dc->nseg, c.n_nodes, pv0, &dc->n_p2p, cap, us, work,
+                          reuse_lists, s);
         MSP_CUDA(cudaEventRecordWithFlags(c.ev_nf1, s, ev_flags));
     }
     c.nf_timed = n > 0;

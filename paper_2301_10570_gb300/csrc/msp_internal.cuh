@@ -297,7 +297,7 @@ const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, i
 void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
                        int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
                        int64_t nlist_cap, float* u_sorted, unsigned long long* work,
-                       cudaStream_t s);
+                       bool keep_order, cudaStream_t s);
 // Exclusive scan of in[0, *n_dev) (n_dev in device memory, at most n_cap)
 // into out; *total_dst = total (+ *base if base).  No host synchronisation.
 // With overflow given, an end above clamp_cap sets overflow_bit in *overflow,

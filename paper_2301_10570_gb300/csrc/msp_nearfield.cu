@@ -606,7 +606,7 @@ __global__ void k_widen_w(const int32_t* __restrict__ list_q, const float2* __re
 void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
                        int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
                        int64_t nlist_cap, float* u_sorted, unsigned long long* work,
-                       cudaStream_t s) {
+                       bool keep_order, cudaStream_t s) {
     if (nseg_cap <= 0 || nlist_cap <= 0) return;
     const msp_config& cfg = c.cfg;
     float2* w32 = c.nf_w32.ensure<float2>((size_t)nlist_cap);
@@ -619,11 +619,15 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     int32_t* ov0 = c.nf_oval0.ensure<int32_t>((size_t)nseg_cap);
     int32_t* ov1 = c.nf_oval1.ensure<int32_t>((size_t)nseg_cap);
     int2* src = c.nf_src.ensure<int2>((size_t)nlist_cap);
-    k_seg_order_keys<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 16), 128, 0, s>>>(
-        seg_first, nseg_dev, list_q, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
-        c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), ok0, ov0, src);
-    MSP_LAUNCH("seg_order_keys");
-    radix_sort_dev(c, ok0, ov0, ok1, ov1, nseg_dev, nseg_cap, 16, s);
+    // the order and the source ranges depend on the lists only: kept when
+    // the lists are (keep_order)
+    if (!keep_order) {
+        k_seg_order_keys<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 16), 128, 0, s>>>(
+            seg_first, nseg_dev, list_q, c.pr_X.get<int32_t>(), c.pr_Y.get<int32_t>(),
+            c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), ok0, ov0, src);
+        MSP_LAUNCH("seg_order_keys");
+        radix_sort_dev(c, ok0, ov0, ok1, ov1, nseg_dev, nseg_cap, 16, s);
+    }
     NFArgs a;
     a.seg_first = seg_first;
     a.nseg = nseg_dev;
