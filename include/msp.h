@@ -480,20 +480,26 @@ const char *msp_last_error(void);
  * The attraction depends on positions only through |t - s| / sigma, so a
  * network scaled by 1/sigma has kernel width 1.  msp_batch_layout scales each
  * network k (neurons [offsets[k], offsets[k+1]) of the concatenated arrays,
- * kernel width sigma[k]) by 1/sigma[k] and places it at the low corner of its
- * own cell of a grid of octree boxes at level *level_out, on every other cell
- * of each dimension, so any two networks are more than `cutoff` apart.  A
- * context created with sigma = 1, origin = 0, side = *side_out and the same
- * cutoff and leaf capacity then runs the whole batch through the ordinary
- * calls (or the step graph) in one pass: box pairs between networks are
- * pruned exactly, and every leaf and every shared axon-box choice of
- * Algorithm 1 lies inside one network (each network has more neurons than
- * the leaf capacity, so every box above its cell is split).  Neuron order is
- * unchanged: u, partner and synapse indices refer to the concatenated arrays.
+ * kernel width sigma[k]) by 1/sigma[k] and gives it its own cell of a grid of
+ * octree boxes at level *level_out, on every other cell of each dimension
+ * (cell k at grid coordinates 2 (k mod G, (k / G) mod G, k / G^2),
+ * G = 2^(level-1)), so any two networks are more than `cutoff` apart.  The
+ * positions it writes are each network's own, relative to the low corner of
+ * its cell: a context created with sigma = 1, origin = 0, side = *side_out
+ * and the same cutoff and leaf capacity, and told of the frames by
+ * msp_set_frames(ctx, n_networks, offsets, *level_out), then runs the whole
+ * batch through the ordinary calls (or the step graph) in one pass.  Box
+ * pairs between networks are pruned exactly, and every leaf and every shared
+ * axon-box choice of Algorithm 1 lies inside one network (each network has
+ * more neurons than the leaf capacity, so every box above its cell is split).
+ * Neuron order is unchanged: u, partner and synapse indices refer to the
+ * concatenated arrays.  The cell side is a power of two (the widest scaled
+ * network plus cutoff + 1, rounded up).
  *   offsets            HOST, n_networks + 1 int64, offsets[0] = 0
  *   x,y,z              DEVICE, offsets[n_networks] positions (any unit)
  *   sigma              HOST, n_networks kernel widths (same unit)
- *   x_out,y_out,z_out  DEVICE, the placed positions (sigma units)
+ *   x_out,y_out,z_out  DEVICE, the scaled positions (sigma units) relative to
+ *                      the network's cell, in [0, side_out / 2^level_out)
  *   side_out, level_out HOST: the domain side and the level of the cells
  * Errors: MSP_ERR_INVALID_ARG (a network with <= leaf_capacity neurons,
  * sigma <= 0, non-finite positions, bad offsets).  Needs no context;
@@ -503,6 +509,30 @@ msp_status msp_batch_layout(int64_t n_networks, const int64_t *offsets, const fl
                             double cutoff, int leaf_capacity, float *x_out_dev,
                             float *y_out_dev, float *z_out_dev, float *side_out,
                             int *level_out, void *stream);
+
+/* Independent networks in their own frames (the batched step of
+ * msp_batch_layout).  Network k holds the caller-order neurons
+ * [offsets[k], offsets[k+1]); its positions are given relative to the low
+ * corner of its cell of the octree grid at `level` (side / 2^level wide), the
+ * cell at grid coordinates 2 (k mod G, (k / G) mod G, k / G^2), G =
+ * 2^(level-1), and lie in [0, side / 2^level).  The Morton key of a point
+ * holds its cell in the top `level` bits of each axis and its local position
+ * below them, so the octree, the pair lists and every draw are those of the
+ * networks side by side in one domain; but positions, box centres and
+ * centroids stay in each network's own frame, so single precision keeps a
+ * network's own resolution however wide the batch's domain.  Boxes above the
+ * cell level span several networks: they carry no expansion and are never
+ * translated (mac_mode 1 included).  msp_direct takes, for each target, the
+ * sources of its own network only.  n_networks = 0 removes the frames.
+ *   offsets  HOST, n_networks + 1 int64: offsets[0] = 0, every network with
+ *            more neurons than the leaf capacity; the next msp_build_tree
+ *            must be given offsets[n_networks] neurons
+ *   level    1..min(10, max_depth - 1); n_networks <= G^3; side / 2^level
+ *            must exceed cutoff * sigma
+ * The context's octree, pair lists and captured step graphs are dropped.
+ * Errors: MSP_ERR_INVALID_ARG; a position outside its cell makes the next
+ * msp_build_tree fail with MSP_ERR_INVALID_ARG.  Synchronous. */
+msp_status msp_set_frames(msp_ctx *ctx, int64_t n_networks, const int64_t *offsets, int level);
 
 /* The counter-based generator behind every random draw of the library:
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy

@@ -103,6 +103,9 @@ void derive(msp_ctx& c) {
             break;
         }
     if (cfg.mac_mode == 1) c.l_far = 0;
+    // with frames, a box above the frame level spans several networks: it
+    // carries no expansion and is never translated
+    if (c.frame_level > 0) c.l_far = std::max(c.l_far, c.frame_level);
     // prune a pair when (sum of squared gaps in boxes of level l) * side_l^2
     // >= (cutoff * sigma)^2
     for (int l = 0; l <= msp::kMortonBits; ++l) {
@@ -172,7 +175,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nr_pre2, &c->nr_post2, &c->nr_typ2, &c->nd_gc, &c->gm_key0,
                          &c->gm_key1, &c->gm_q, &c->gm_q1, &c->gm_flag, &c->gm_gid,
                          &c->gm_gstart, &c->gm_ntile, &c->gm_toff, &c->gm_tiles, &c->gm_cnt,
-                         &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
+                         &c->frame_off, &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg, &c->ln_sums,
                          &c->ln_part, &c->ln_coef,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
@@ -405,6 +408,42 @@ msp_status msp_set_sigma(msp_ctx* c, double sigma) {
         c->cfg.sigma = sigma;
         derive(*c);
         // the pair lists and every captured graph hold the old width
+        c->attraction_done = false;
+        msp::graph_release(*c);
+    });
+}
+
+msp_status msp_set_frames(msp_ctx* c, int64_t n_networks, const int64_t* offsets, int level) {
+    return guarded(c, [&] {
+        const msp_config& cfg = c->cfg;
+        if (n_networks == 0) {
+            c->frame_level = 0;
+            c->frame_off_host.clear();
+        } else {
+            require(n_networks > 0 && offsets != nullptr, "networks and offsets required");
+            require(level >= 1 && level <= 10 && level < cfg.max_depth,
+                    "the frame level must lie in [1, min(10, max_depth - 1)]");
+            const int64_t G = (int64_t)1 << (level - 1);
+            require(n_networks <= G * G * G, "more networks than cells at that level");
+            require(offsets[0] == 0, "offsets[0] must be 0");
+            for (int64_t k = 0; k < n_networks; ++k)
+                require(offsets[k + 1] > offsets[k] + cfg.leaf_capacity,
+                        "every network needs more neurons than the leaf capacity");
+            require(offsets[n_networks] < 0x7fffffffll, "too many neurons");
+            // networks one cell apart must be beyond the cutoff
+            require((double)cfg.side / std::ldexp(1.0, level) > cfg.cutoff * cfg.sigma,
+                    "a cell must be wider than the cutoff radius");
+            c->frame_off_host.assign(offsets, offsets + n_networks + 1);
+            // work in flight may still read the old offsets
+            MSP_CUDA(cudaDeviceSynchronize());
+            int64_t* d = c->frame_off.ensure<int64_t>((size_t)n_networks + 1);
+            MSP_CUDA(cudaMemcpy(d, offsets, (size_t)(n_networks + 1) * sizeof(int64_t),
+                                cudaMemcpyHostToDevice));
+            c->frame_level = level;
+        }
+        derive(*c);
+        // the octree, the pair lists and every captured graph hold the old frames
+        c->tree_built = false;
         c->attraction_done = false;
         msp::graph_release(*c);
     });

@@ -3,9 +3,13 @@
 // The attraction depends on positions only through |t - s| / sigma, so a
 // network scaled by 1/sigma has kernel width 1.  Network k (neurons
 // [off_k, off_k+1) of the concatenated arrays) is scaled by 1/sigma_k and
-// placed at the low corner of its own cell of a grid of octree boxes at level
-// L0, using every other cell in each dimension: any two networks are at least
-// one empty cell (wider than the cutoff) apart.  Then
+// given its own cell of a grid of octree boxes at level L0, using every other
+// cell in each dimension: any two networks are at least one empty cell (wider
+// than the cutoff) apart.  Its positions are written relative to its cell's
+// low corner (its own frame), and a context told of the frames
+// (msp_set_frames) puts the cell in the top bits of every Morton key and
+// forms each box centre in the box's network's frame, so no position is ever
+// rounded to the resolution of the whole batch's domain.  Then
 //   - every box pair between networks is pruned by the box-distance test at
 //     the first level where the boxes are separated, so no attraction, pair
 //     weight or draw ever crosses networks;
@@ -13,7 +17,9 @@
 //     split and every leaf, and every axon box whose choice its neurons share
 //     (Algorithm 1), lies inside one network's cell;
 // and the single-network path (tree, traversal, near field, descent,
-// resolution) runs on the whole batch in one pass, unchanged.
+// resolution) runs on the whole batch in one pass, unchanged.  The cell side
+// is a power of two, so a network's key is exactly the key its points would
+// have in one common frame.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -64,21 +70,21 @@ __global__ void k_batch_bounds(const int64_t* __restrict__ off, const float* __r
     }
 }
 
-// place: one block per network; p' = origin_k + (p - lo_k) * inv_sigma_k
+// place: one block per network; p' = (p - lo_k) * inv_sigma_k, relative to
+// the network's own cell
 __global__ void k_batch_place(const int64_t* __restrict__ off, const float* __restrict__ x,
                               const float* __restrict__ y, const float* __restrict__ z,
-                              const float* __restrict__ bounds, const float* __restrict__ place,
+                              const float* __restrict__ bounds, const float* __restrict__ inv_sigma,
                               float* __restrict__ xo, float* __restrict__ yo,
                               float* __restrict__ zo) {
     const int64_t k = blockIdx.x;
     const int64_t i0 = off[k], i1 = off[k + 1];
     const float lx = bounds[6 * k], ly = bounds[6 * k + 1], lz = bounds[6 * k + 2];
-    const float ox = place[4 * k], oy = place[4 * k + 1], oz = place[4 * k + 2];
-    const float is = place[4 * k + 3];
+    const float is = inv_sigma[k];
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        xo[i] = fmaf(x[i] - lx, is, ox);
-        yo[i] = fmaf(y[i] - ly, is, oy);
-        zo[i] = fmaf(z[i] - lz, is, oz);
+        xo[i] = __fmul_rn(__fsub_rn(x[i], lx), is);
+        yo[i] = __fmul_rn(__fsub_rn(y[i], ly), is);
+        zo[i] = __fmul_rn(__fsub_rn(z[i], lz), is);
     }
 }
 
@@ -98,7 +104,7 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
     try {
         int64_t* off = d_off.ensure<int64_t>((size_t)nnet + 1);
         float* bounds = d_bounds.ensure<float>((size_t)6 * nnet);
-        float* place = d_place.ensure<float>((size_t)4 * nnet);
+        float* place = d_place.ensure<float>((size_t)nnet);
         MSP_CUDA(cudaMemcpyAsync(off, off_host, (nnet + 1) * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, s));
         k_batch_bounds<<<(unsigned)nnet, 256, 0, s>>>(off, x, y, z, bounds);
@@ -107,7 +113,8 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
         MSP_CUDA(cudaMemcpyAsync(hb.data(), bounds, hb.size() * sizeof(float),
                                  cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
-        // cell side: the widest scaled network plus a margin
+        // cell side: the widest scaled network plus a margin, rounded up to a
+        // power of two
         double ext = 0.0;
         for (int64_t k = 0; k < nnet; ++k)
             for (int d = 0; d < 3; ++d) {
@@ -115,19 +122,16 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
                 if (!std::isfinite(e)) throw Error(MSP_ERR_INVALID_ARG, "non-finite position");
                 ext = std::max(ext, e);
             }
-        const double cell = ext * (1.0 + 1e-3) + cutoff + 1.0;
+        const double cell = std::exp2(std::ceil(std::log2(ext * (1.0 + 1e-3) + cutoff + 1.0)));
+        if (!(cell < 1e30)) throw Error(MSP_ERR_INVALID_ARG, "networks too wide");
         // networks on the even cells of a 2G x 2G x 2G grid, G a power of two
         int lg = 0;
         while ((int64_t)1 << (3 * lg) < nnet) ++lg;
         const int64_t G = (int64_t)1 << lg;
         const int L0 = lg + 1;
         if (L0 > kMortonBits - 8) throw Error(MSP_ERR_INVALID_ARG, "too many networks");
-        std::vector<float> hp((size_t)4 * nnet);
-        for (int64_t k = 0; k < nnet; ++k) {
-            const int64_t c[3] = {k % G, (k / G) % G, k / (G * G)};
-            for (int d = 0; d < 3; ++d) hp[4 * k + d] = (float)(2.0 * (double)c[d] * cell);
-            hp[4 * k + 3] = (float)(1.0 / sigma[k]);
-        }
+        std::vector<float> hp((size_t)nnet);
+        for (int64_t k = 0; k < nnet; ++k) hp[k] = (float)(1.0 / sigma[k]);
         MSP_CUDA(cudaMemcpyAsync(place, hp.data(), hp.size() * sizeof(float),
                                  cudaMemcpyHostToDevice, s));
         k_batch_place<<<(unsigned)nnet, 256, 0, s>>>(off, x, y, z, bounds, place, xo, yo, zo);

@@ -62,14 +62,17 @@ __device__ inline uint8_t classify(const NodeView& nv, const Geo& geo, int32_t X
     }
     if (gsum >= geo.g2[lf]) return kPruned;
     const bool leafx = nv.child_first[X] < 0, leafy = nv.child_first[Y] < 0;
+    const int lmin = lx < ly ? lx : ly;
     if (geo.mac_mode == 1) {
         // Algorithm 2: a leaf side is evaluated directly; an inner dendrite
         // box with more than c1 vacant dendrites is expanded; else direct
+        // (boxes above l_far, which is 0 unless the points sit in frames,
+        // are split)
         if (leafx && leafy) return kP2P;
-        if (!leafx && !leafy && X != Y && sy.z + sy.w > geo.c1) return kFar;
+        if (!leafx && !leafy && X != Y && lmin >= geo.l_far && sy.z + sy.w > geo.c1)
+            return kFar;
         return kSplit;
     }
-    int lmin = lx < ly ? lx : ly;
     if (lmin >= geo.l_far && gmax >= 1 &&
         (long long)nv.count[X] * (long long)nv.count[Y] >= geo.m2l_min_pairs)
         return kFar;
@@ -584,11 +587,28 @@ __global__ void k_scatter_u(const float* __restrict__ us, const int32_t* __restr
 // ---------------------------------------------------------------------------
 constexpr int kDirThreads = 256;
 
+// first index of the sorted keys at or above v
+__device__ inline int64_t lower_bound_key(const uint64_t* __restrict__ keys, int64_t n, uint64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// FR: the points sit in frames (independent networks): a target takes only
+// the sources of its own network, which are contiguous in Morton order (the
+// key's top 3 L0 bits are the network's cell, fsh = 3 (21 - L0) bits below);
+// a block walks the tiles from its first target's network to its last one's
+template <bool FR>
 __global__ void __launch_bounds__(kDirThreads)
 k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ wts, float k2,
-         float* __restrict__ u) {
+         const uint64_t* __restrict__ keys, int fsh, float* __restrict__ u) {
     __shared__ float4 sp[kDirThreads];
     __shared__ float2 sw[kDirThreads];
+    __shared__ uint32_t sc[FR ? kDirThreads : 1];
+    __shared__ int64_t s_range[2];
     for (int64_t tb = (int64_t)blockIdx.x * kDirThreads; tb < n;
          tb += (int64_t)gridDim.x * kDirThreads) {
         int64_t t = tb + threadIdx.x;
@@ -596,12 +616,28 @@ k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ w
         float4 T = active ? pts[t] : make_float4(0.f, 0.f, 0.f, 0.f);
         uint32_t tw = __float_as_uint(T.w);
         bool inh = pk_type(tw) != 0;
+        uint32_t tcell = 0;
+        int64_t s0 = 0, s1 = n;
+        if (FR) {
+            tcell = active ? (uint32_t)(keys[t] >> fsh) : 0xffffffffu;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int64_t tl = tb + kDirThreads <= n ? tb + kDirThreads - 1 : n - 1;
+                const uint64_t c0 = keys[tb] >> fsh, c1 = keys[tl] >> fsh;
+                s_range[0] = lower_bound_key(keys, n, c0 << fsh) / kDirThreads * kDirThreads;
+                s_range[1] = lower_bound_key(keys, n, (c1 + 1) << fsh);
+            }
+            __syncthreads();
+            s0 = s_range[0];
+            s1 = s_range[1];
+        }
         float acc = 0.f, comp = 0.f;   // Kahan sum of the tile sums
-        for (int64_t sb = 0; sb < n; sb += kDirThreads) {
+        for (int64_t sb = s0; sb < s1; sb += kDirThreads) {
             __syncthreads();
             int64_t s = sb + threadIdx.x;
             sp[threadIdx.x] = s < n ? pts[s] : make_float4(3e30f, 3e30f, 3e30f, 0.f);
             sw[threadIdx.x] = s < n ? wts[s] : make_float2(0.f, 0.f);
+            if (FR) sc[threadIdx.x] = s < n ? (uint32_t)(keys[s] >> fsh) : 0xfffffffeu;
             __syncthreads();
             float part = 0.f;
             if (sb != tb) {
@@ -611,7 +647,9 @@ k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ w
                     float dx = T.x - S.x, dy = T.y - S.y, dz = T.z - S.z;
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     float e = ex2_approx(-r2 * k2);
-                    part = fmaf(inh ? sw[j].y : sw[j].x, e, part);
+                    float wj = inh ? sw[j].y : sw[j].x;
+                    if (FR && sc[j] != tcell) wj = 0.f;
+                    part = fmaf(wj, e, part);
                 }
             } else {
                 // the tile holding the targets themselves: skip j == t
@@ -621,6 +659,7 @@ k_direct(int64_t n, const float4* __restrict__ pts, const float2* __restrict__ w
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     float e = ex2_approx(-r2 * k2);
                     float wj = j == (int)threadIdx.x ? 0.f : (inh ? sw[j].y : sw[j].x);
+                    if (FR && sc[j] != tcell) wj = 0.f;
                     part = fmaf(wj, e, part);
                 }
             }
@@ -885,8 +924,15 @@ void direct(msp_ctx& c, float* u_dev, cudaStream_t s) {
     if (n == 0) return;
     const float k2 = (float)(1.4426950408889634 / (c.cfg.sigma * c.cfg.sigma));
     float* us = c.u_sorted.ensure<float>((size_t)n);
-    k_direct<<<grid_for(n, kDirThreads), kDirThreads, 0, s>>>(n, c.pts.get<float4>(),
-                                                              c.wts.get<float2>(), k2, us);
+    if (c.frame_level > 0) {
+        // the sorted keys of the build are still in keys0
+        k_direct<true><<<grid_for(n, kDirThreads), kDirThreads, 0, s>>>(
+            n, c.pts.get<float4>(), c.wts.get<float2>(), k2, c.keys0.get<uint64_t>(),
+            3 * (kMortonBits - c.frame_level), us);
+    } else {
+        k_direct<false><<<grid_for(n, kDirThreads), kDirThreads, 0, s>>>(
+            n, c.pts.get<float4>(), c.wts.get<float2>(), k2, nullptr, 0, us);
+    }
     MSP_LAUNCH("direct");
     k_scatter_u<<<grid_for(n, 256, (int64_t)c.sm_count * 16), 256, 0, s>>>(
         us, c.perm.get<int32_t>(), n, u_dev);

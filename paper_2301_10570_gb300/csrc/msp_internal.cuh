@@ -174,6 +174,12 @@ struct msp_ctx {
     int64_t exp_first = 0, exp_nodes = 0;
     int64_t n_p2p_targets = 0;
     bool tree_built = false, attraction_done = false;
+    // independent networks in local frames (msp_set_frames): network k holds
+    // the caller's neurons [frame_off[k], frame_off[k+1]) with positions
+    // relative to its own cell of the grid at level frame_level (0: one frame)
+    int frame_level = 0;
+    std::vector<int64_t> frame_off_host;
+    msp::DBuf frame_off;
     // sorted points
     msp::DBuf keys0, keys1, vals0, vals1;
     msp::DBuf perm, inv, pts, wts, lw, elem_off, leaf_of;
@@ -383,6 +389,19 @@ __host__ __device__ inline uint64_t spread_by3(uint32_t v) {
     x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
     x = (x | (x << 2)) & 0x1249249249249249ull;
     return x;
+}
+
+// A box's integer coordinate along axis d (0 = x) in units of its own side,
+// counted in the frame its points are given in.  With frames (frame_level
+// > 0) a box at or below the frame level is counted from the low corner of
+// its frame's cell (its coordinate modulo the cell's), so its centre is
+// formed in that network's own frame; a box above it spans several networks,
+// is never evaluated or translated and counts from 0.
+__host__ __device__ inline uint32_t box_axis(uint64_t prefix, int d, int level,
+                                             int frame_level) {
+    const uint32_t c = compact_by3(prefix >> (2 - d));
+    if (frame_level <= 0) return c;
+    return level >= frame_level ? c & ((1u << (level - frame_level)) - 1u) : 0u;
 }
 
 // packed per-point bytes: type | vac_axon << 8 | vac_dend_e << 16 | vac_dend_i << 24

@@ -33,17 +33,18 @@ __device__ __forceinline__ int64_t box_coord(uint64_t prefix, int d) {
     return (int64_t)compact_by3(prefix >> (2 - d));
 }
 
-// geometric centre of every box
+// geometric centre of every box (with frames, in its network's own frame)
 __global__ void k_geo_centres(int64_t n_nodes, const uint8_t* __restrict__ level,
-                              const uint64_t* __restrict__ prefix, float ox, float oy, float oz,
-                              float side, float4* __restrict__ gc) {
+                              const uint64_t* __restrict__ prefix, int frame_level, float ox,
+                              float oy, float oz, float side, float4* __restrict__ gc) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_nodes;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float bs = ldexpf(side, -(int)level[i]);
+        const int l = (int)level[i];
+        const float bs = ldexpf(side, -l);
         const uint64_t pre = prefix[i];
-        gc[i] = make_float4(ox + ((float)box_coord(pre, 0) + 0.5f) * bs,
-                            oy + ((float)box_coord(pre, 1) + 0.5f) * bs,
-                            oz + ((float)box_coord(pre, 2) + 0.5f) * bs, 0.f);
+        gc[i] = make_float4(ox + ((float)box_axis(pre, 0, l, frame_level) + 0.5f) * bs,
+                            oy + ((float)box_axis(pre, 1, l, frame_level) + 0.5f) * bs,
+                            oz + ((float)box_axis(pre, 2, l, frame_level) + 0.5f) * bs, 0.f);
     }
 }
 
@@ -265,8 +266,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_m2l_gemm(GemmArgs a) {
 void geo_centres(msp_ctx& c, cudaStream_t s) {
     float4* gc = c.nd_gc.ensure<float4>((size_t)std::max<int64_t>(c.n_nodes, 1));
     k_geo_centres<<<grid_for(c.n_nodes, 256, (int64_t)c.sm_count * 8), 256, 0, s>>>(
-        c.n_nodes, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.cfg.origin[0],
-        c.cfg.origin[1], c.cfg.origin[2], c.cfg.side, gc);
+        c.n_nodes, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.frame_level,
+        c.frame_level > 0 ? 0.f : c.cfg.origin[0], c.frame_level > 0 ? 0.f : c.cfg.origin[1],
+        c.frame_level > 0 ? 0.f : c.cfg.origin[2], c.cfg.side, gc);
     MSP_LAUNCH("geo_centres");
 }
 

@@ -76,6 +76,7 @@ struct NFArgs {
     const float4* pts;
     const float2* lw;
     float sqk, ox, oy, oz, side;
+    int frame_level;             // > 0: box centres in each network's own frame
     float* u;
     float2* w32;                 // per near-field pair (list order): W of E and I
     unsigned long long* work;
@@ -449,9 +450,10 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
         const int32_t tf = a.nfirst[X], tc = a.ncount[X];
         const uint64_t pre = a.nprefix[X];
         const float bs = ldexpf(a.side, -(int)a.nlevel[X]);
-        const float cx = a.ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs;
-        const float cy = a.oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs;
-        const float cz = a.oz + ((float)compact_by3(pre) + 0.5f) * bs;
+        const int lX = (int)a.nlevel[X];
+        const float cx = a.ox + ((float)box_axis(pre, 0, lX, a.frame_level) + 0.5f) * bs;
+        const float cy = a.oy + ((float)box_axis(pre, 1, lX, a.frame_level) + 0.5f) * bs;
+        const float cz = a.oz + ((float)box_axis(pre, 2, lX, a.frame_level) + 0.5f) * bs;
         // the expanded exponent needs |t^|^2 <= kNFFastT2 for every target of X
         const bool fast = 0.75f * a.sqk * a.sqk * bs * bs <= kNFFastT2;
         unsigned long long evals = 0;
@@ -642,10 +644,12 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     a.pts = c.pts.get<float4>();
     a.lw = c.lw.get<float2>();
     a.sqk = (float)std::sqrt(1.4426950408889634 / (cfg.sigma * cfg.sigma));
-    a.ox = cfg.origin[0];
-    a.oy = cfg.origin[1];
-    a.oz = cfg.origin[2];
+    const bool framed = c.frame_level > 0;
+    a.ox = framed ? 0.f : cfg.origin[0];
+    a.oy = framed ? 0.f : cfg.origin[1];
+    a.oz = framed ? 0.f : cfg.origin[2];
     a.side = cfg.side;
+    a.frame_level = c.frame_level;
     a.u = u_sorted;
     a.w32 = w32;
     a.work = work;

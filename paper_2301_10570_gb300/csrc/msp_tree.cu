@@ -75,6 +75,44 @@ __global__ void k_morton(const float* __restrict__ x, const float* __restrict__ 
         atomicAdd(reinterpret_cast<unsigned long long*>(bad), 1ull);
 }
 
+// Keys of independent networks in local frames.  Neuron i belongs to the
+// network k with off[k] <= i < off[k+1]; that network's cell at level L0 has
+// the grid coordinates 2 (k mod G, (k / G) mod G, k / G^2), G = 2^(L0-1), and
+// the neuron's position is relative to the cell's low corner, inside
+// [0, cs).  Each axis of the key holds the cell's coordinate in its top L0
+// bits and the local position, quantised on the same grid, below them: the
+// key the point would have in one common frame, without ever forming its
+// position in that frame in single precision.
+__global__ void k_morton_frames(const float* __restrict__ x, const float* __restrict__ y,
+                                const float* __restrict__ z, int64_t n,
+                                const int64_t* __restrict__ off, int64_t nf, int L0, float cs,
+                                float scale, uint64_t* __restrict__ keys,
+                                int32_t* __restrict__ vals, int64_t* __restrict__ bad) {
+    const int sh = kMortonBits - L0;
+    const uint32_t qmax = (1u << sh) - 1u;
+    const int64_t G = 1ll << (L0 - 1);
+    bool any_bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nf;   // off[lo] <= i < off[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid;
+        }
+        const uint32_t cx = (uint32_t)(2 * (lo % G)), cy = (uint32_t)(2 * ((lo / G) % G)),
+                       cz = (uint32_t)(2 * (lo / (G * G)));
+        any_bad |= !(x[i] >= 0.f && x[i] < cs && y[i] >= 0.f && y[i] < cs && z[i] >= 0.f &&
+                     z[i] < cs);
+        const uint32_t qx = (cx << sh) | min(quantise(x[i], 0.f, scale), qmax);
+        const uint32_t qy = (cy << sh) | min(quantise(y[i], 0.f, scale), qmax);
+        const uint32_t qz = (cz << sh) | min(quantise(z[i], 0.f, scale), qmax);
+        keys[i] = (spread_by3(qx) << 2) | (spread_by3(qy) << 1) | spread_by3(qz);
+        vals[i] = (int32_t)i;
+    }
+    if (__any_sync(0xffffffffu, any_bad) && (threadIdx.x & 31) == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(bad), 1ull);
+}
+
 __global__ void k_gather(const int32_t* __restrict__ order, int64_t n, const float* __restrict__ x,
                          const float* __restrict__ y, const float* __restrict__ z,
                          const uint8_t* __restrict__ type, const uint8_t* __restrict__ va,
@@ -231,13 +269,14 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
 
 // Box aggregates, deepest level first.  A leaf sums its points; an inner box
 // combines its children.  Centroids are accumulated as weighted offsets from
-// the box's geometric centre so that single precision keeps them accurate.
+// the box's geometric centre so that single precision keeps them accurate
+// (with frames, the centre in the box's network's own frame: box_axis).
 // One warp per box of the level: a leaf's lanes take its points, an inner
 // box's lanes its children (at most 8); warp sums, then lane 0 writes the
 // box's vacant-element sums and its axon / dendrite centroids (offsets from
 // the geometric centre summed, then divided by the weight).
-__global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox, float oy, float oz,
-                            float side, const float4* __restrict__ pts,
+__global__ void k_aggregate(const int64_t* __restrict__ lb, int level, int frame_level, float ox,
+                            float oy, float oz, float side, const float4* __restrict__ pts,
                             const uint64_t* __restrict__ prefix, const int32_t* __restrict__ first,
                             const int32_t* __restrict__ count,
                             const int32_t* __restrict__ child_first,
@@ -251,9 +290,9 @@ __global__ void k_aggregate(const int64_t* __restrict__ lb, int level, float ox,
         const int64_t i = l0 + k;
         const uint64_t pre = prefix[i];
         const float bs = ldexpf(side, -level);
-        const float g[3] = {ox + ((float)compact_by3(pre >> 2) + 0.5f) * bs,
-                            oy + ((float)compact_by3(pre >> 1) + 0.5f) * bs,
-                            oz + ((float)compact_by3(pre) + 0.5f) * bs};
+        const float g[3] = {ox + ((float)box_axis(pre, 0, level, frame_level) + 0.5f) * bs,
+                            oy + ((float)box_axis(pre, 1, level, frame_level) + 0.5f) * bs,
+                            oz + ((float)box_axis(pre, 2, level, frame_level) + 0.5f) * bs};
         int aE = 0, aI = 0, wE = 0, wI = 0;
         float sa[3] = {0.f, 0.f, 0.f}, sd[3] = {0.f, 0.f, 0.f};
         const int32_t cf = child_first[i];
@@ -332,6 +371,13 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     int32_t* leaf_of = c.leaf_of.ensure<int32_t>(nn);
     const int B = 256;
     const int G = grid_for(n, B, (int64_t)c.sm_count * 16);
+    // box centres: in the domain's frame, or (frames) in each network's own
+    const bool framed = c.frame_level > 0;
+    const float o3[3] = {framed ? 0.f : cfg.origin[0], framed ? 0.f : cfg.origin[1],
+                         framed ? 0.f : cfg.origin[2]};
+    if (framed && n != c.frame_off_host.back())
+        throw Error(MSP_ERR_INVALID_ARG, "the frames (msp_set_frames) hold a different number "
+                                         "of neurons");
     if (n > 0) {
         k_pos_sum<<<G, B, 0, s>>>(x, y, z, n, reinterpret_cast<unsigned long long*>(&dc->pos_sum));
         MSP_LAUNCH("pos_sum");
@@ -358,7 +404,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
         for (int l = c.tree_levels; l >= 0; --l) {
             k_aggregate<<<Gt, 128, 0, s>>>(
-                &dc->level_start[l], l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
+                &dc->level_start[l], l, c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
                 c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
                 c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(),
                 c.nd_sums.get<int4>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), leaf_of);
@@ -369,9 +415,17 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
 
     // a1 + a2: keys, stable sort, gather into Morton order
     if (n > 0) {
-        k_morton<<<G, B, 0, s>>>(x, y, z, n, cfg.origin[0], cfg.origin[1], cfg.origin[2],
-                                 cfg.side, c.morton_scale, k0, v0, &dc->bad_pos);
-        MSP_LAUNCH("morton");
+        if (framed) {
+            k_morton_frames<<<G, B, 0, s>>>(x, y, z, n, c.frame_off.get<int64_t>(),
+                                            (int64_t)c.frame_off_host.size() - 1, c.frame_level,
+                                            ldexpf(cfg.side, -c.frame_level), c.morton_scale, k0,
+                                            v0, &dc->bad_pos);
+            MSP_LAUNCH("morton_frames");
+        } else {
+            k_morton<<<G, B, 0, s>>>(x, y, z, n, cfg.origin[0], cfg.origin[1], cfg.origin[2],
+                                     cfg.side, c.morton_scale, k0, v0, &dc->bad_pos);
+            MSP_LAUNCH("morton");
+        }
         radix_sort(c, k0, v0, k1, v1, n, 3 * kMortonBits, s);
         k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
         MSP_LAUNCH("gather");
@@ -455,7 +509,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         // a4: aggregates, deepest level first (empty levels are no-ops)
         for (int l = L; l >= 0; --l) {
             k_aggregate<<<Gt, 128, 0, s>>>(
-                &dc->level_start[l], l, cfg.origin[0], cfg.origin[1], cfg.origin[2], cfg.side, pts,
+                &dc->level_start[l], l, c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
                 c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
                 c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
             MSP_LAUNCH("aggregate");
@@ -469,8 +523,10 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         }
         pull_counts(c, s);          // the one synchronisation of the build
         if (c.hcount->bad_pos)
-            throw Error(MSP_ERR_INVALID_ARG, "a position is outside [origin, origin + side) "
-                                             "or not finite");
+            throw Error(MSP_ERR_INVALID_ARG,
+                        framed ? "a position is outside its frame's cell [0, side / 2^level) "
+                                 "or not finite"
+                               : "a position is outside [origin, origin + side) or not finite");
         if (c.hcount->overflow & 16) throw Error(MSP_ERR_CHECK, "octree node capacity exceeded");
         if (c.hcount->more_levels > 0 && L < cfg.max_depth) {
             L = cfg.max_depth;

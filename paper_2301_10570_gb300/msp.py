@@ -35,7 +35,7 @@ EXPORTED = ("msp_create", "msp_destroy", "msp_build_tree", "msp_attraction", "ms
             "msp_set_workspace_limit", "msp_workspace_bytes", "msp_neuron_steps",
             "msp_update_synapses", "msp_append_synapses", "msp_selftest_bounded_wait",
             "msp_philox", "msp_step_graph_set_full_build", "msp_length_loss",
-            "msp_set_sigma")
+            "msp_set_sigma", "msp_set_frames")
 MAX_VACANCY = 5         # the vacancy walk's bound on every vacant count
 NOALLOC_MAX_N = 65536   # MSP_NOALLOC_MAX_N of include/msp.h
 
@@ -158,6 +158,8 @@ def load(path: str = LIB_PATH):
         L.msp_length_loss.restype = C.c_int
         L.msp_set_sigma.argtypes = [vp, C.c_double]
         L.msp_set_sigma.restype = C.c_int
+        L.msp_set_frames.argtypes = [vp, i64, vp, C.c_int]
+        L.msp_set_frames.restype = C.c_int
         for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
                      "msp_selftest_bounded_wait"):
             getattr(L, name).restype = C.c_int
@@ -231,7 +233,9 @@ def _close_all():
 class MSP:
     """One libmsp context on a CUDA device."""
 
-    def __init__(self, params: dict, device: int = 0):
+    def __init__(self, params: dict, device: int = 0, frames=None):
+        """frames: None, or (offsets, level) of independent networks in their
+        own frames (msp_set_frames; the output of batch_layout)."""
         L = load()
         self.params = dict(params)
         self.device = device
@@ -242,6 +246,8 @@ class MSP:
         self.n = 0
         self._inputs = None
         _live.add(self)
+        if frames is not None:
+            self.set_frames(*frames)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -405,6 +411,18 @@ class MSP:
         _check(load().msp_set_sigma(self._h, float(sigma)))
         self.params["sigma"] = float(sigma)
         self._cfg.sigma = float(sigma)
+
+    def set_frames(self, offsets, level: int):
+        """Independent networks in their own frames: network k holds neurons
+        [offsets[k], offsets[k+1]) with positions relative to its own cell at
+        `level` (msp_set_frames); offsets=None removes them."""
+        if offsets is None:
+            _check(load().msp_set_frames(self._h, 0, None, 0))
+            return
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if off.ndim != 1 or len(off) < 2:
+            raise ValueError("offsets must hold at least two entries")
+        _check(load().msp_set_frames(self._h, len(off) - 1, _np(off), int(level)))
 
     # -- the whole step as a CUDA graph ---------------------------------------
     def step_graph_capture(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, first_step,
@@ -586,10 +604,11 @@ def philox(ctr, key, stream=None):
 
 
 def batch_layout(pos, offsets, sigma, cutoff, leaf_capacity, stream=None):
-    """Places the networks of a batch (pos: (3, N) float32 CUDA tensor of the
-    concatenated networks; offsets: N_net + 1 int64; sigma: per network) in
-    one problem of kernel width 1.  Returns (placed (3, N) tensor, side,
-    cell level)."""
+    """Lays the networks of a batch (pos: (3, N) float32 CUDA tensor of the
+    concatenated networks; offsets: N_net + 1 int64; sigma: per network) out
+    as one problem of kernel width 1, each network in its own cell.  Returns
+    (local (3, N) tensor: sigma units relative to the network's cell, side,
+    cell level); a context then takes frames=(offsets, level)."""
     pos = pos.contiguous()
     if not pos.is_cuda or pos.dtype != torch.float32:
         raise TypeError("batch_layout expects CUDA float32 positions")

@@ -36,6 +36,7 @@ class Workload:
     vac_dend_e: np.ndarray   # (n,) uint8 vacant excitatory dendritic elements
     vac_dend_i: np.ndarray   # (n,) uint8 vacant inhibitory dendritic elements
     params: dict = field(default_factory=dict)
+    frames: tuple | None = None   # (offsets, level): networks in their own frames
 
     @property
     def n(self) -> int:
@@ -157,10 +158,29 @@ class Batch:
                      np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64),
                      self.sigma[nets].copy(), [self.kinds[k] for k in nets])
 
-    def placed(self, pos_placed: np.ndarray, side: float, **kw) -> Workload:
-        """The whole batch as one problem of kernel width 1, from the placed
-        positions (sigma units) and the domain side."""
-        return Workload(self.name + "_placed", np.ascontiguousarray(pos_placed, np.float32),
+    def cell_corners(self, side: float, level: int) -> np.ndarray:
+        """(3, N) low corner of every neuron's cell (sigma units): network k
+        in the cell at grid coordinates 2 (k mod G, (k / G) mod G, k / G^2),
+        G = 2^(level - 1)."""
+        G = 2 ** (level - 1)
+        k = self.network_of()
+        c = np.stack([k % G, (k // G) % G, k // (G * G)]).astype(np.float64)
+        return 2.0 * c * (side / 2.0 ** level)
+
+    def framed(self, pos_local: np.ndarray, side: float, level: int, **kw) -> Workload:
+        """The whole batch as one problem of kernel width 1, each network in
+        its own frame (positions relative to its cell, sigma units)."""
+        return Workload(self.name + "_framed", np.ascontiguousarray(pos_local, np.float32),
+                        self.type, self.vac_axon, self.vac_dend_e, self.vac_dend_i,
+                        default_params(side, sigma=1.0, **kw),
+                        frames=(self.offsets.copy(), int(level)))
+
+    def placed(self, pos_local: np.ndarray, side: float, level: int, **kw) -> Workload:
+        """The same problem in one common frame: every network moved to its
+        cell (single precision; exact when the local positions and the cell
+        corners share a fine enough dyadic grid)."""
+        g = pos_local.astype(np.float64) + self.cell_corners(side, level)
+        return Workload(self.name + "_placed", np.ascontiguousarray(g, np.float32),
                         self.type, self.vac_axon, self.vac_dend_e, self.vac_dend_i,
                         default_params(side, sigma=1.0, **kw))
 

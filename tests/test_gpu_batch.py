@@ -1,11 +1,15 @@
 """Many independent networks as one problem (the batched step).
 
-The layout scales each network by 1/sigma and places it in its own octree
-cell with an empty cell between networks.  Checks: the placement itself; the
-whole batch through the CUDA path against the oracle run on the same placed
-problem (the usual parity bars); and independence: every network's
-attraction equals its own all-pairs evaluation at its own kernel width, and
-no partner or synapse crosses networks.
+The layout scales each network by 1/sigma and gives it its own octree cell,
+with an empty cell between networks; each network keeps its own frame
+(positions relative to its cell) and the context is told of the frames
+(msp_set_frames).  Checks: the layout itself; the whole batch through the
+CUDA path against the oracle run on the same problem in one common frame, on
+networks whose scaled positions lie on a dyadic grid so that the common frame
+holds them exactly (keys bit for bit, the usual bars for u, partners and
+synapses); independence and precision: every network's attraction against
+the FP64 brute force of that network alone, at its own width, on its own
+unscaled positions; the argument checks of the frames.
 """
 import numpy as np
 import pytest
@@ -21,63 +25,78 @@ if not torch.cuda.is_available():
 from paper_2301_10570_gb300 import msp  # noqa: E402
 
 PLAN = dict(leaf_capacity=16, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
+PLANS = {"exact": dict(PLAN), "translations": dict(PLAN, rho_max=0.3, leaf_capacity=8),
+         "wide": dict(PLAN, cutoff=5.0)}
 
 
-def _placed(b, **plan):
+def _layout(b, **plan):
     pos = torch.from_numpy(b.pos).cuda()
-    placed, side, level = msp.batch_layout(pos, b.offsets, b.sigma, plan["cutoff"],
-                                           plan["leaf_capacity"])
-    return b.placed(placed.cpu().numpy(), side, **plan), side, level
+    local, side, level = msp.batch_layout(pos, b.offsets, b.sigma, plan["cutoff"],
+                                          plan["leaf_capacity"])
+    return local.cpu().numpy(), side, level
+
+
+def _dyadic(b, grid=256.0):
+    """The batch scaled to sigma units by the test, positions rounded to
+    multiples of 1/grid, every width 1: the layout then only translates, and
+    the common frame of the whole batch holds every position exactly."""
+    k = b.network_of()
+    pos = np.round(b.pos.astype(np.float64) / b.sigma[k] * grid) / grid
+    return W.Batch(b.name + "_dyadic", np.ascontiguousarray(pos, np.float32), b.type,
+                   b.vac_axon, b.vac_dend_e, b.vac_dend_i, b.offsets.copy(),
+                   np.ones_like(b.sigma), list(b.kinds))
+
+
+def _gpu(w, step=4):
+    g = msp.MSP(w.params, frames=w.frames)
+    g.build_tree(*msp.to_device(w))
+    u = g.attraction().cpu().numpy()
+    ud = g.direct().cpu().numpy()
+    sel = g.select_partners(step)
+    torch.cuda.synchronize()
+    ne = g.num_elements()
+    ns = int(sel["n_syn"].item())
+    res = dict(u=u, ud=ud, partner=sel["partner"][:ne].cpu().numpy(), n_syn=ns,
+               pre=sel["syn_pre"][:ns].cpu().numpy(), post=sel["syn_post"][:ns].cpu().numpy(),
+               keys=g.export_tree()["keys"], stats=g.stats())
+    g.close()
+    return res
 
 
 _cache = {}
 
 
-def _run(plan_key="exact"):
-    if plan_key in _cache:
-        return _cache[plan_key]
-    plan = {"exact": dict(PLAN), "translations": dict(PLAN, rho_max=0.3, leaf_capacity=8),
-            "wide": dict(PLAN, cutoff=5.0)}[plan_key]
-    b = W.batched_small()
-    w, side, level = _placed(b, **plan)
-    g = msp.MSP(w.params)
-    g.build_tree(*msp.to_device(w))
-    u = g.attraction().cpu().numpy()
-    sel = g.select_partners(4)
-    torch.cuda.synchronize()
-    ne = g.num_elements()
-    ns = int(sel["n_syn"].item())
-    res = dict(u=u, partner=sel["partner"][:ne].cpu().numpy(), n_syn=ns,
-               pre=sel["syn_pre"][:ns].cpu().numpy(), post=sel["syn_post"][:ns].cpu().numpy(),
-               typ=sel["syn_type"][:ns].cpu().numpy(), keys=g.export_tree()["keys"],
-               stats=g.stats())
-    g.close()
-    _cache[plan_key] = (b, w, side, level, res)
-    return _cache[plan_key]
+def _run(plan_key, dyadic):
+    key = (plan_key, dyadic)
+    if key not in _cache:
+        plan = PLANS[plan_key]
+        b = W.batched_small()
+        if dyadic:
+            b = _dyadic(b)
+        local, side, level = _layout(b, **plan)
+        w = b.framed(local, side, level, **plan)
+        _cache[key] = (b, w, local, side, level, _gpu(w))
+    return _cache[key]
 
 
-def test_layout_scales_and_separates_networks():
+def test_layout_scales_each_network_into_its_own_cell():
     b = W.batched_small()
-    w, side, level = _placed(b, **PLAN)
+    local, side, level = _layout(b, **PLAN)
     cell = side / 2.0 ** level
     G = 2 ** (level - 1)
+    assert G ** 3 >= len(b.sigma)
+    assert cell == 2.0 ** np.round(np.log2(cell))      # a power of two
+    assert side == 2 * G * cell
     for k in range(len(b.sigma)):
         a, e = b.offsets[k], b.offsets[k + 1]
         src = b.pos[:, a:e].astype(np.float64)
         lo = src.min(axis=1, keepdims=True)
-        c = np.array([k % G, (k // G) % G, k // (G * G)], np.float64)[:, None]
-        want = 2 * c * cell + (src - lo) / b.sigma[k]
-        got = w.pos[:, a:e].astype(np.float64)
-        assert np.max(np.abs(got - want)) < 1e-5 * side
-        # inside its own (even) cell
-        assert np.all(got >= 2 * c * cell - 1e-6 * side)
-        assert np.all(got < (2 * c + 1) * cell)
-    # any two networks are more than the cutoff apart (sigma units)
-    net = b.network_of()
-    cells = np.floor(w.pos / cell).astype(np.int64)
-    for k in range(len(b.sigma)):
-        assert len(np.unique(cells[:, net == k], axis=1).T) >= 1
-        assert np.all(cells[:, net == k] % 2 == 0)
+        want = (src - lo) / b.sigma[k]
+        got = local[:, a:e].astype(np.float64)
+        assert np.max(np.abs(got - want)) <= 4e-7 * max(1.0, want.max())
+        assert np.all(got >= 0) and np.all(got < cell)
+        # networks one cell apart: the gap exceeds the cutoff
+        assert cell - want.max() > PLAN["cutoff"]
 
 
 def test_layout_rejects_small_networks_and_bad_widths():
@@ -92,47 +111,110 @@ def test_layout_rejects_small_networks_and_bad_widths():
 
 
 @pytest.mark.parametrize("plan_key", ["exact", "translations"])
-def test_batch_matches_oracle_on_the_placed_problem(plan_key):
+def test_batch_matches_oracle_on_the_common_frame(plan_key, boundary_report):
+    """Frames against the oracle on the networks moved into one frame: on a
+    dyadic batch that frame is exact, so the problem is the same one."""
     from oracle import oracle as O
-    b, w, side, level, res = _run(plan_key)
-    o = O.Oracle(w.params)
-    o.build_tree(*w.arrays())
+    b, w, local, side, level, res = _run(plan_key, dyadic=True)
+    wp = b.placed(local, side, level, **PLANS[plan_key])
+    exact = local.astype(np.float64) + b.cell_corners(side, level)
+    assert np.array_equal(wp.pos.astype(np.float64), exact)   # the premise: no rounding
+    o = O.Oracle(wp.params)
+    o.build_tree(*wp.arrays())
     uo = o.attraction()
     ro = o.select_partners(4)
     keys, _ = o.keys()
     assert np.array_equal(res["keys"], keys)
     m = (w.vac_axon > 0) & (uo >= 1e-6 * uo.max())
     assert np.max(np.abs(res["u"][m] - uo[m]) / uo[m]) < 1e-5
-    ok = ~ro["near_boundary"]
-    assert np.array_equal(res["partner"][ok], ro["partner"][ok])
-    if not ro["near_boundary"].any():
+    if plan_key == "translations":
+        assert res["stats"]["n_far"] > 0
+    nb = ro["near_boundary"]
+    differ = res["partner"] != ro["partner"]
+    st = o.stats()
+    boundary_report[f"batch_frames_{plan_key}"] = dict(
+        band=1e-5 if PLANS[plan_key]["rho_max"] > 0 else 1e-6, draws=st["draws"],
+        boundary_draws=st["boundary_draws"], flagged=int(nb.sum()), elements=len(nb),
+        differ=int(differ.sum()), differ_flagged=bool(np.all(nb[differ])))
+    assert np.all(nb[differ])
+    o.close()
+    if not nb.any():
         assert res["n_syn"] == ro["n_syn"]
         assert np.array_equal(res["pre"], ro["syn_pre"])
         assert np.array_equal(res["post"], ro["syn_post"])
 
 
-def test_networks_are_independent():
-    # cutoff 5 sigma: the dropped attraction (below exp(-25) of a neighbour's)
-    # is far below single precision, so each network's u must equal its own
-    # all-pairs evaluation within the library's bar against brute force (both
-    # are single-precision sums in different orders: ~3e-5 observed on dense
-    # clusters)
-    b, w, side, level, res = _run("wide")
+def test_each_network_matches_its_own_fp64_evaluation(precision_report):
+    """Every network of the batch (its own width, its own unscaled positions)
+    against the FP64 all-pairs sum of that network alone: the frames keep
+    each network at its own single-precision resolution, however wide the
+    batch's domain.  Both the search (cutoff 5 sigma: the dropped attraction
+    is below exp(-25) of a neighbour's) and the all-pairs path of the batch."""
+    from oracle import oracle as O
+    b, w, local, side, level, res = _run("wide", dyadic=False)
+    worst_u = worst_d = 0.0
+    for k in range(len(b.sigma)):
+        a, e = b.offsets[k], b.offsets[k + 1]
+        wk = b.network(k)
+        exact = O.direct(*wk.arrays(), wk.params["sigma"])
+        m = (wk.vac_axon > 0) & (exact >= 1e-6 * exact.max())
+        worst_u = max(worst_u, np.max(np.abs(res["u"][a:e][m] - exact[m]) / exact[m]))
+        worst_d = max(worst_d, np.max(np.abs(res["ud"][a:e][m] - exact[m]) / exact[m]))
+        assert np.all(res["ud"][a:e][wk.vac_axon == 0] == 0)
+    precision_report["batch_frames_u_vs_fp64_each_network"] = worst_u
+    precision_report["batch_frames_direct_vs_fp64_each_network"] = worst_d
+    assert worst_u < 1e-5
+    assert worst_d < 1e-5
+
+
+def test_no_partner_or_synapse_crosses_networks():
+    b, w, local, side, level, res = _run("wide", dyadic=False)
     net = b.network_of()
     owner = np.repeat(np.arange(b.n), w.vac_axon)
     part = res["partner"]
     ok = part >= 0
     assert ok.mean() > 0.8
     assert np.all(net[part[ok]] == net[owner[ok]])
+    assert res["n_syn"] > 0
     assert np.all(net[res["pre"]] == net[res["post"]])
-    # each network's attraction is its own all-pairs evaluation at its own width
-    for k in range(len(b.sigma)):
-        a, e = b.offsets[k], b.offsets[k + 1]
-        wk = b.network(k)
-        gk = msp.MSP(wk.params)
-        gk.build_tree(*msp.to_device(wk))
-        ud = gk.direct().cpu().numpy()
-        gk.close()
-        ub = res["u"][a:e]
-        m = (wk.vac_axon > 0) & (ud >= 1e-6 * ud.max())
-        assert np.max(np.abs(ub[m] - ud[m]) / ud[m]) < 1e-4, k
+
+
+def test_frames_check_their_arguments():
+    b = W.batched_small()
+    local, side, level = _layout(b, **PLAN)
+    w = b.framed(local, side, level, **PLAN)
+    g = msp.MSP(w.params)
+    off = b.offsets
+    for args in [(off, 0), (off, 11), (off, w.params["max_depth"]),
+                 (np.array([0, 10, b.n]), level),                  # a network of <= 16
+                 (np.array([1, b.n]), level),                      # offsets[0] != 0
+                 (np.linspace(0, 9 * 100, 10).astype(np.int64), 2)]:   # 9 networks, 8 cells
+        with pytest.raises(msp.MSPError) as ei:
+            g.set_frames(*args)
+        assert ei.value.code == 1
+    g.close()
+    # a cell no wider than the cutoff radius
+    g = msp.MSP(dict(w.params, side=2 ** level * 3.0))
+    with pytest.raises(msp.MSPError):
+        g.set_frames(off, level)
+    g.close()
+    # the next build must be given offsets[-1] neurons, inside their cells
+    g = msp.MSP(w.params, frames=w.frames)
+    dev = msp.to_device(w)
+    with pytest.raises(msp.MSPError) as ei:
+        g.build_tree(dev[0][:, :-1].contiguous(), *[t[:-1].contiguous() for t in dev[1:]])
+    assert ei.value.code == 1
+    bad = dev[0].clone()
+    bad[0, 3] = side / 2 ** level
+    with pytest.raises(msp.MSPError) as ei:
+        g.build_tree(bad, *dev[1:])
+    assert ei.value.code == 1 and "frame" in str(ei.value)
+    g.build_tree(*dev)
+    u = g.attraction().cpu().numpy()
+    assert np.isfinite(u).all() and u.max() > 0
+    # without frames the same context takes one common frame again
+    g.set_frames(None, 0)
+    wp = b.placed(local, side, level, **PLAN)
+    g.build_tree(*msp.to_device(wp))
+    g.attraction()
+    g.close()

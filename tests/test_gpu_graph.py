@@ -32,7 +32,7 @@ def _eager(w, first, k_steps):
     """Steps first .. first+k_steps-1 as separate calls; returns per-step
     synapse counts, the final state and the last step's selection."""
     pos, t, a, e, i = _state(w)
-    g = msp.MSP(w.params)
+    g = msp.MSP(w.params, frames=w.frames)
     counts = []
     sel = None
     for k in range(first, first + k_steps):
@@ -53,7 +53,7 @@ def _eager(w, first, k_steps):
 
 def _graph(w, first, k_steps, pair_capacity=None, manual=False, full_build=False):
     pos, t, a, e, i = _state(w)
-    g = msp.MSP(w.params)
+    g = msp.MSP(w.params, frames=w.frames)
     g.build_tree(pos, t, a, e, i)
     g.attraction()
     if pair_capacity is not None:
@@ -209,14 +209,14 @@ def test_graph_refuses_to_replay_after_workspace_reallocation():
 
 
 def test_graph_replays_of_a_batch_equal_eager_steps():
-    # the batched problem (several networks placed in one domain) through the
-    # step graph, against the same steps as eager calls
+    # the batched problem (several networks, each in its own frame, as one
+    # problem) through the step graph, against the same steps as eager calls
     from paper_2301_10570_gb300 import workloads as W2
     b = W2.batched_small()
     plan = dict(leaf_capacity=16, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
-    placed, side, _ = msp.batch_layout(torch.from_numpy(b.pos).cuda(), b.offsets, b.sigma,
-                                       plan["cutoff"], plan["leaf_capacity"])
-    w = b.placed(placed.cpu().numpy(), side, **plan)
+    local, side, level = msp.batch_layout(torch.from_numpy(b.pos).cuda(), b.offsets, b.sigma,
+                                          plan["cutoff"], plan["leaf_capacity"])
+    w = b.framed(local.cpu().numpy(), side, level, **plan)
     ce, se, le = _eager(w, 7, 4)
     cg, sg, lg, _, _ = _graph(w, 7, 4)
     assert cg == ce
