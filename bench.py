@@ -107,28 +107,50 @@ def workload():
 BATCH_METRIC = "batched-step neurons/s, 256 independent networks (11.7M neurons) on GB300"
 BATCH_DESC = ("batched_256: 256 networks, n log-uniform in [1024, 262144] (11,718,582 neurons), "
               "sigma uniform in [300, 1500] um, uniform or clustered, each scaled to sigma units "
-              "in its own octree cell and frame (msp_batch_layout, msp_set_frames)")
+              "in its own octree cell and frame (msp_batch_layout, msp_set_frames), leaf "
+              "capacity 256 for all, a cutoff per network from the batch plan chooser")
+
+
+_BATCH_TUNING = {}
 
 
 def batched_workload(dev, rank=0, world=1, common_frame=False):
     """The 256-network batch as one problem of kernel width 1, each network in
-    its own cell and frame (the workload carries the frames); with several
-    ranks, rank r takes networks r, r + N, r + 2N, ... (the networks are
-    independent: no exchange).  common_frame: the same networks moved into
-    one frame instead (for the host-core oracle, which has no frames)."""
+    its own cell and frame, with the shared plan's leaf capacity and a cutoff
+    per network from the batch plan chooser (autotune.tune_batch_cutoffs; the
+    workload carries the frames and the cutoffs); with several ranks, rank r
+    takes networks r, r + N, r + 2N, ... (the networks are independent: no
+    exchange).  common_frame: the same networks moved into one frame instead,
+    with the shared plan (for the host-core oracle, which has no frames)."""
     import torch
 
-    from paper_2301_10570_gb300 import msp, workloads as W
+    from paper_2301_10570_gb300 import autotune, msp, workloads as W
     b = W.batched_256()
     if world > 1:
         b = b.select(range(rank, len(b.sigma), world))
     plan = tuned_params()
+    # cells wide enough for the largest candidate cutoff
     local, side, level = msp.batch_layout(torch.from_numpy(b.pos).to(dev), b.offsets, b.sigma,
-                                          plan["cutoff"], plan["leaf_capacity"])
+                                          max(autotune.BATCH_CUTOFFS), plan["leaf_capacity"])
     local = local.cpu().numpy()
     if common_frame:
         return b.placed(local, side, level, **plan)
-    return b.framed(local, side, level, **plan)
+    w = b.framed(local, side, level, **plan)
+    cuts, rep = autotune.tune_batch_cutoffs(w, device=dev.index)
+    _BATCH_TUNING.update(cutoffs=cuts, **rep)
+    return b.framed(local, side, level, plans=(None, cuts), **plan)
+
+
+def batch_tuning_summary():
+    """The batch plan chooser's result for the benchmark line."""
+    import collections
+    if not _BATCH_TUNING:
+        return None
+    hist = collections.Counter(_BATCH_TUNING["cutoffs"])
+    return {"cutoffs": {str(k): v for k, v in sorted(hist.items())},
+            "networks_raised": _BATCH_TUNING["raised"],
+            "rounds": _BATCH_TUNING["rounds"],
+            "max_rel_dev_vs_own_all_pairs": max(_BATCH_TUNING["per_network_max_err"])}
 
 
 def near_field_traffic():
@@ -730,6 +752,7 @@ def run_ours(args, rank, world):
                       "clustered_1m: 1,048,576 neurons, 64 Gaussian clusters (std 1500 um), "
                       "100,000 um cube, sigma 750 um, 80/20 E/I, vacancies U{0..3} + walk",
                       "plan": tuned_params(), "parallelism": f"replicas x{world}",
+                      **({"batch_plan_chooser": batch_tuning_summary()} if batched else {}),
                       "l2": "flushed (256 MB write) between timed steps",
                       "timing": "CUDA events per step (one graph replay each), mean over steps",
                       "step_path": "whole step captured as one CUDA graph (msp_step_graph_*); "
@@ -848,6 +871,7 @@ def batched_record(dev, steps, warmup):
             "ms_per_step": round(ms, 3), "neurons_per_s": n / (ms / 1e3),
             "graph_halted": int(halted),
             "max_rel_err_sampled_networks_vs_own_fp64": max(errs),
+            "plan_chooser": batch_tuning_summary(),
             "accuracy_note": "8 sampled networks x 512 sampled targets, each network against "
                              "the FP64 brute force of that network alone at its own width on "
                              "its own unscaled positions (every network keeps its own frame)",

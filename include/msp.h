@@ -524,15 +524,24 @@ msp_status msp_batch_layout(int64_t n_networks, const int64_t *offsets, const fl
  * cell level span several networks: they carry no expansion and are never
  * translated (mac_mode 1 included).  msp_direct takes, for each target, the
  * sources of its own network only.  n_networks = 0 removes the frames.
+ * Per-network plans: leaf_capacity[k] and cutoff[k] (either may be NULL: the
+ * configuration's value for every network) replace the configuration's leaf
+ * capacity and cutoff inside network k: its boxes split above its own
+ * capacity, its box pairs are pruned at its own cutoff, and its leaf draws
+ * are truncated at its own radius (boxes above the cell level always split
+ * and are pruned at the largest cutoff).
  *   offsets  HOST, n_networks + 1 int64: offsets[0] = 0, every network with
  *            more neurons than the leaf capacity; the next msp_build_tree
  *            must be given offsets[n_networks] neurons
  *   level    1..min(10, max_depth - 1); n_networks <= G^3; side / 2^level
- *            must exceed cutoff * sigma
+ *            must exceed every cutoff * sigma
+ *   leaf_capacity  HOST, n_networks int32 >= 1 (each network larger), or NULL
+ *   cutoff         HOST, n_networks doubles in (0, 5], or NULL
  * The context's octree, pair lists and captured step graphs are dropped.
  * Errors: MSP_ERR_INVALID_ARG; a position outside its cell makes the next
  * msp_build_tree fail with MSP_ERR_INVALID_ARG.  Synchronous. */
-msp_status msp_set_frames(msp_ctx *ctx, int64_t n_networks, const int64_t *offsets, int level);
+msp_status msp_set_frames(msp_ctx *ctx, int64_t n_networks, const int64_t *offsets, int level,
+                          const int32_t *leaf_capacity, const double *cutoff);
 
 /* The counter-based generator behind every random draw of the library:
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy

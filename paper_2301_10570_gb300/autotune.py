@@ -81,3 +81,59 @@ def tune(workload, tol=1e-4, ref_err=1e-6, candidates=None, reps=4, device=0, ve
         return None, results
     best = min(accepted, key=lambda r: r["step_ms"])
     return best["plan"], results
+
+
+BATCH_CUTOFFS = (3.25, 3.5, 4.0, 4.5, 5.0)
+
+
+def tune_batch_cutoffs(workload, tol=1e-4, ref_err=3e-5, cutoffs=BATCH_CUTOFFS, device=0,
+                       verbose=False):
+    """Per-network cutoffs for a batch of networks in their own frames (a
+    workload from Batch.framed with a shared plan; its layout must leave every
+    cell wider than the largest candidate).  Every network starts at the
+    smallest candidate; a network whose attraction deviates from its own
+    all-pairs evaluation (msp_direct of the batch: each target against its own
+    network's sources) by more than tol - ref_err moves to the next candidate,
+    and the batch is evaluated again, until every network passes or has the
+    largest candidate.  ref_err covers the all-pairs path's own deviation
+    from the exact sum of the unscaled network (its positions are rounded to
+    single precision in sigma units, up to ~133 sigma from the cell's
+    corner: a few 1e-5 observed).  Returns (cutoffs per network, report)."""
+    import numpy as np
+    import torch
+
+    from . import msp
+    offsets, level = workload.frames[0], workload.frames[1]
+    K = len(offsets) - 1
+    dev = msp.to_device(workload, f"cuda:{device}")
+    g = msp.MSP(workload.params, device=device, frames=(offsets, level))
+    try:
+        g.build_tree(*dev)
+        ref = g.direct().cpu().numpy().astype(np.float64)
+        va = workload.vac_axon
+        net = np.repeat(np.arange(K), np.diff(offsets))
+        # per-network mask: vacant axons and u >= 1e-6 of the network's largest
+        big = np.maximum.reduceat(ref, offsets[:-1])
+        mask = (va > 0) & (ref >= 1e-6 * big[net])
+        cur = np.zeros(K, np.int64)
+        rounds = []
+        while True:
+            cuts = [float(cutoffs[i]) for i in cur]
+            g.set_frames(offsets, level, None, cuts)
+            g.build_tree(*dev)
+            u = g.attraction().cpu().numpy().astype(np.float64)
+            torch.cuda.synchronize()
+            rel = np.where(mask, np.abs(u - ref) / np.maximum(ref, 1e-300), 0.0)
+            err = np.maximum.reduceat(rel, offsets[:-1])
+            fail = (err > tol - ref_err) & (cur < len(cutoffs) - 1)
+            rounds.append(dict(max_err=float(err.max()), failing=int((err > tol - ref_err).sum()),
+                               interactions=g.stats()["p2p_interactions"]))
+            if verbose:
+                print(rounds[-1], flush=True)
+            if not fail.any():
+                break
+            cur[fail] += 1
+    finally:
+        g.close()
+    return cuts, dict(rounds=rounds, per_network_max_err=err.tolist(),
+                      raised=int((cur > 0).sum()))

@@ -107,11 +107,30 @@ void derive(msp_ctx& c) {
     // carries no expansion and is never translated
     if (c.frame_level > 0) c.l_far = std::max(c.l_far, c.frame_level);
     // prune a pair when (sum of squared gaps in boxes of level l) * side_l^2
-    // >= (cutoff * sigma)^2
-    for (int l = 0; l <= msp::kMortonBits; ++l) {
-        double bl = (double)cfg.side / std::ldexp(1.0, l);
-        double r = cfg.cutoff * cfg.sigma / bl;
-        c.g2[l] = (long long)std::ceil(r * r);
+    // >= (cutoff * sigma)^2; with per-network cutoffs, the largest of them for
+    // pairs above the networks' cells, and each network's own below
+    auto g2_of = [&](double cutoff, int l) {
+        const double bl = (double)cfg.side / std::ldexp(1.0, l);
+        const double r = cutoff * cfg.sigma / bl;
+        return (long long)std::ceil(r * r);
+    };
+    double cmax = cfg.cutoff;
+    for (double v : c.frame_cut_host) cmax = std::max(cmax, v);
+    for (int l = 0; l <= msp::kMortonBits; ++l) c.g2[l] = g2_of(cmax, l);
+    if (c.frame_plans) {
+        const size_t nf = c.frame_cut_host.size();
+        std::vector<long long> g2((size_t)nf * (msp::kMortonBits + 1));
+        std::vector<float> rc2(nf);
+        for (size_t k = 0; k < nf; ++k) {
+            for (int l = 0; l <= msp::kMortonBits; ++l)
+                g2[k * (msp::kMortonBits + 1) + l] = g2_of(c.frame_cut_host[k], l);
+            const double rc = c.frame_cut_host[k] * cfg.sigma;
+            rc2[k] = (float)(rc * rc);
+        }
+        MSP_CUDA(cudaMemcpy(c.frame_g2.ensure<long long>(g2.size()), g2.data(),
+                            g2.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        MSP_CUDA(cudaMemcpy(c.frame_rc2.ensure<float>(nf), rc2.data(), nf * sizeof(float),
+                            cudaMemcpyHostToDevice));
     }
 }
 
@@ -175,7 +194,8 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->nr_pre2, &c->nr_post2, &c->nr_typ2, &c->nd_gc, &c->gm_key0,
                          &c->gm_key1, &c->gm_q, &c->gm_q1, &c->gm_flag, &c->gm_gid,
                          &c->gm_gstart, &c->gm_ntile, &c->gm_toff, &c->gm_tiles, &c->gm_cnt,
-                         &c->frame_off, &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
+                         &c->frame_off, &c->frame_cap, &c->frame_g2, &c->frame_rc2,
+                         &c->gr_w, &c->gr_tmp, &c->gr_key0, &c->gr_key1, &c->gr_val0,
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg, &c->ln_sums,
                          &c->ln_part, &c->ln_coef,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
@@ -413,9 +433,15 @@ msp_status msp_set_sigma(msp_ctx* c, double sigma) {
     });
 }
 
-msp_status msp_set_frames(msp_ctx* c, int64_t n_networks, const int64_t* offsets, int level) {
+msp_status msp_set_frames(msp_ctx* c, int64_t n_networks, const int64_t* offsets, int level,
+                          const int32_t* leaf_capacity, const double* cutoff) {
     return guarded(c, [&] {
         const msp_config& cfg = c->cfg;
+        // work in flight may still read the old tables
+        MSP_CUDA(cudaDeviceSynchronize());
+        c->frame_plans = false;
+        c->frame_cap_host.clear();
+        c->frame_cut_host.clear();
         if (n_networks == 0) {
             c->frame_level = 0;
             c->frame_off_host.clear();
@@ -426,16 +452,31 @@ msp_status msp_set_frames(msp_ctx* c, int64_t n_networks, const int64_t* offsets
             const int64_t G = (int64_t)1 << (level - 1);
             require(n_networks <= G * G * G, "more networks than cells at that level");
             require(offsets[0] == 0, "offsets[0] must be 0");
-            for (int64_t k = 0; k < n_networks; ++k)
-                require(offsets[k + 1] > offsets[k] + cfg.leaf_capacity,
-                        "every network needs more neurons than the leaf capacity");
+            const double cell = (double)cfg.side / std::ldexp(1.0, level);
+            for (int64_t k = 0; k < n_networks; ++k) {
+                const int cap = leaf_capacity ? leaf_capacity[k] : cfg.leaf_capacity;
+                const double cut = cutoff ? cutoff[k] : cfg.cutoff;
+                require(cap >= 1, "leaf capacities must be positive");
+                require(offsets[k + 1] > offsets[k] + cap,
+                        "every network needs more neurons than its leaf capacity");
+                require(cut > 0.0 && cut <= 5.0, "cutoffs must lie in (0, 5]");
+                // networks one cell apart must be beyond the cutoff
+                require(cell > cut * cfg.sigma, "a cell must be wider than the cutoff radius");
+            }
             require(offsets[n_networks] < 0x7fffffffll, "too many neurons");
-            // networks one cell apart must be beyond the cutoff
-            require((double)cfg.side / std::ldexp(1.0, level) > cfg.cutoff * cfg.sigma,
-                    "a cell must be wider than the cutoff radius");
             c->frame_off_host.assign(offsets, offsets + n_networks + 1);
-            // work in flight may still read the old offsets
-            MSP_CUDA(cudaDeviceSynchronize());
+            if (leaf_capacity || cutoff) {
+                c->frame_plans = true;
+                c->frame_cap_host.resize((size_t)n_networks);
+                c->frame_cut_host.resize((size_t)n_networks);
+                for (int64_t k = 0; k < n_networks; ++k) {
+                    c->frame_cap_host[k] = leaf_capacity ? leaf_capacity[k] : cfg.leaf_capacity;
+                    c->frame_cut_host[k] = cutoff ? cutoff[k] : cfg.cutoff;
+                }
+                MSP_CUDA(cudaMemcpy(c->frame_cap.ensure<int32_t>((size_t)n_networks),
+                                    c->frame_cap_host.data(), (size_t)n_networks * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice));
+            }
             int64_t* d = c->frame_off.ensure<int64_t>((size_t)n_networks + 1);
             MSP_CUDA(cudaMemcpy(d, offsets, (size_t)(n_networks + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice));

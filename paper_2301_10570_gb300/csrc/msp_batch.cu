@@ -70,21 +70,21 @@ __global__ void k_batch_bounds(const int64_t* __restrict__ off, const float* __r
     }
 }
 
-// place: one block per network; p' = (p - lo_k) * inv_sigma_k, relative to
-// the network's own cell
+// place: one block per network; p' = (p - lo_k) / sigma_k, relative to the
+// network's own cell, formed in double precision and rounded once
 __global__ void k_batch_place(const int64_t* __restrict__ off, const float* __restrict__ x,
                               const float* __restrict__ y, const float* __restrict__ z,
-                              const float* __restrict__ bounds, const float* __restrict__ inv_sigma,
+                              const float* __restrict__ bounds, const double* __restrict__ sigma,
                               float* __restrict__ xo, float* __restrict__ yo,
                               float* __restrict__ zo) {
     const int64_t k = blockIdx.x;
     const int64_t i0 = off[k], i1 = off[k + 1];
-    const float lx = bounds[6 * k], ly = bounds[6 * k + 1], lz = bounds[6 * k + 2];
-    const float is = inv_sigma[k];
+    const double lx = bounds[6 * k], ly = bounds[6 * k + 1], lz = bounds[6 * k + 2];
+    const double sg = sigma[k];
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        xo[i] = __fmul_rn(__fsub_rn(x[i], lx), is);
-        yo[i] = __fmul_rn(__fsub_rn(y[i], ly), is);
-        zo[i] = __fmul_rn(__fsub_rn(z[i], lz), is);
+        xo[i] = (float)(((double)x[i] - lx) / sg);
+        yo[i] = (float)(((double)y[i] - ly) / sg);
+        zo[i] = (float)(((double)z[i] - lz) / sg);
     }
 }
 
@@ -104,7 +104,7 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
     try {
         int64_t* off = d_off.ensure<int64_t>((size_t)nnet + 1);
         float* bounds = d_bounds.ensure<float>((size_t)6 * nnet);
-        float* place = d_place.ensure<float>((size_t)nnet);
+        double* place = d_place.ensure<double>((size_t)nnet);
         MSP_CUDA(cudaMemcpyAsync(off, off_host, (nnet + 1) * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, s));
         k_batch_bounds<<<(unsigned)nnet, 256, 0, s>>>(off, x, y, z, bounds);
@@ -130,9 +130,7 @@ void batch_layout(int64_t nnet, const int64_t* off_host, const float* x, const f
         const int64_t G = (int64_t)1 << lg;
         const int L0 = lg + 1;
         if (L0 > kMortonBits - 8) throw Error(MSP_ERR_INVALID_ARG, "too many networks");
-        std::vector<float> hp((size_t)nnet);
-        for (int64_t k = 0; k < nnet; ++k) hp[k] = (float)(1.0 / sigma[k]);
-        MSP_CUDA(cudaMemcpyAsync(place, hp.data(), hp.size() * sizeof(float),
+        MSP_CUDA(cudaMemcpyAsync(place, sigma, (size_t)nnet * sizeof(double),
                                  cudaMemcpyHostToDevice, s));
         k_batch_place<<<(unsigned)nnet, 256, 0, s>>>(off, x, y, z, bounds, place, xo, yo, zo);
         MSP_LAUNCH("batch_place");

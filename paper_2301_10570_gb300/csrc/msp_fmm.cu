@@ -15,6 +15,11 @@ struct Geo {
     long long m2l_min_pairs;
     int mac_mode;                    // 1: Algorithm 2's count rule
     int c1;                          // its dendrite threshold
+    // per-network cutoffs (points in frames): the thresholds of the finer
+    // box's network, [network][level], for levels at or below frame_level
+    const long long* fg2;
+    int frame_level;
+    int64_t nf;
 };
 
 __device__ inline float ex2_approx(float x) {
@@ -60,7 +65,14 @@ __device__ inline uint8_t classify(const NodeView& nv, const Geo& geo, int32_t X
         gsum += g * g;
         if (g > gmax) gmax = g;
     }
-    if (gsum >= geo.g2[lf]) return kPruned;
+    long long thr = geo.g2[lf];
+    if (geo.fg2 && lf >= geo.frame_level) {
+        // both boxes in one network: its cutoff; in two networks: at least a
+        // cell apart, beyond every network's cutoff
+        const int64_t k = box_frame(lx == lf ? px : py, lf, geo.frame_level, geo.nf);
+        thr = geo.fg2[k * (kMortonBits + 1) + lf];
+    }
+    if (gsum >= thr) return kPruned;
     const bool leafx = nv.child_first[X] < 0, leafy = nv.child_first[Y] < 0;
     const int lmin = lx < ly ? lx : ly;
     if (geo.mac_mode == 1) {
@@ -712,6 +724,9 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     NodeView nv = node_view(c);
     Geo geo;
     for (int l = 0; l <= kMortonBits; ++l) geo.g2[l] = c.g2[l];
+    geo.fg2 = c.frame_level > 0 && c.frame_plans ? c.frame_g2.get<long long>() : nullptr;
+    geo.frame_level = c.frame_level;
+    geo.nf = (int64_t)c.frame_off_host.size() - 1;
     geo.l_far = c.l_far;
     geo.m2l_min_pairs = cfg.m2l_min_pairs;
     geo.mac_mode = cfg.mac_mode;

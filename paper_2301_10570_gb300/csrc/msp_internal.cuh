@@ -180,6 +180,12 @@ struct msp_ctx {
     int frame_level = 0;
     std::vector<int64_t> frame_off_host;
     msp::DBuf frame_off;
+    // per-network plans (optional): leaf capacity, the pruning thresholds of
+    // every level (as g2 below) and the leaf draw's squared truncation radius
+    bool frame_plans = false;
+    std::vector<int32_t> frame_cap_host;
+    std::vector<double> frame_cut_host;
+    msp::DBuf frame_cap, frame_g2, frame_rc2;
     // sorted points
     msp::DBuf keys0, keys1, vals0, vals1;
     msp::DBuf perm, inv, pts, wts, lw, elem_off, leaf_of;
@@ -402,6 +408,20 @@ __host__ __device__ inline uint32_t box_axis(uint64_t prefix, int d, int level,
     const uint32_t c = compact_by3(prefix >> (2 - d));
     if (frame_level <= 0) return c;
     return level >= frame_level ? c & ((1u << (level - frame_level)) - 1u) : 0u;
+}
+
+// The network (frame) of a box at or below the frame level: its cell's
+// coordinates are the top frame_level bits of each axis of its prefix, and
+// network k sits in the cell 2 (k mod G, (k / G) mod G, k / G^2), G =
+// 2^(frame_level - 1).  Clamped to [0, nf).
+__host__ __device__ inline int64_t box_frame(uint64_t prefix, int level, int frame_level,
+                                             int64_t nf) {
+    const uint64_t cell = prefix >> (3 * (level - frame_level));
+    const int64_t G = 1ll << (frame_level - 1);
+    const int64_t k = (int64_t)(compact_by3(cell >> 2) >> 1) +
+                      G * ((int64_t)(compact_by3(cell >> 1) >> 1) +
+                           G * (int64_t)(compact_by3(cell) >> 1));
+    return k < 0 ? 0 : (k < nf ? k : nf - 1);
 }
 
 // packed per-point bytes: type | vac_axon << 8 | vac_dend_e << 16 | vac_dend_i << 24

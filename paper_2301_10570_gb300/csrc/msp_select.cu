@@ -316,12 +316,23 @@ __device__ __forceinline__ uint64_t ld_weight(const float4& T, const float4& S, 
     return fixed_point(ws, shift);
 }
 
+// per-network truncation radii (points in frames with per-network plans):
+// the squared radius of the axon leaf's network
+struct FrameRc2 {
+    const float* rc2;          // per network, or null: the kernel's rc2 everywhere
+    const uint64_t* prefix;
+    const uint8_t* level;
+    int frame_level;
+    int64_t nf;
+};
+
 __global__ void __launch_bounds__(kLdWarps * 32)
 k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf, int64_t cap_leaf,
               unsigned long long* __restrict__ next, const int32_t* __restrict__ nfirst,
               const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
               const float2* __restrict__ wts, const int32_t* __restrict__ perm,
-              const int32_t* __restrict__ eoff, float k2, float rc2, uint64_t seed, StepRef stp,
+              const int32_t* __restrict__ eoff, float k2, float rc2_all, FrameRc2 fr,
+              uint64_t seed, StepRef stp,
               int32_t* __restrict__ partner, unsigned long long* __restrict__ draw_ctr,
               const int64_t* __restrict__ n_elem) {
     __shared__ float4 s_pts[kLdWarps][kLdStage];
@@ -339,6 +350,9 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
         if ((int64_t)k >= n_items) break;
         const Item it = items[k];
         const int ch = it.ch;
+        const float rc2 =
+            fr.rc2 ? fr.rc2[box_frame(fr.prefix[it.X], fr.level[it.X], fr.frame_level, fr.nf)]
+                   : rc2_all;
         const int32_t tf = nfirst[it.X], tc = ncount[it.X];
         const int32_t sf = nfirst[it.Y], sc = ncount[it.Y];
         // fixed-point scale: sc weights of at most 2^8 must stay below 2^63
@@ -742,10 +756,13 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         MSP_LAUNCH("descend");
     }
     // one warp per leaf pair, from a device work counter
+    FrameRc2 frc{nullptr, c.nd_prefix.get<uint64_t>(), c.nd_level.get<uint8_t>(), c.frame_level,
+                 (int64_t)c.frame_off_host.size() - 1};
+    if (c.frame_level > 0 && c.frame_plans) frc.rc2 = c.frame_rc2.get<float>();
     k_leaf_draw_w<<<(int)std::max<int64_t>(1, (int64_t)c.sm_count * 8), kLdWarps * 32, 0, s>>>(
         lit, &dc->n_leaf, cap_leaf, ull(&dc->leaf_next), c.nd_first.get<int32_t>(),
         c.nd_count.get<int32_t>(), c.pts.get<float4>(), c.wts.get<float2>(),
-        c.perm.get<int32_t>(), c.elem_off.get<int32_t>(), k2, rc2, cfg.seed, stp, partner,
+        c.perm.get<int32_t>(), c.elem_off.get<int32_t>(), k2, rc2, frc, cfg.seed, stp, partner,
         ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
 

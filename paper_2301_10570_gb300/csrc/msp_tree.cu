@@ -180,8 +180,18 @@ struct OctantSplit {
     int32_t lo, end, start;
 };
 
+// Per-network leaf capacities (Caps.cap non-null, points in frames): a box at
+// or below the frame level splits above its network's capacity, a box above
+// it (several networks' cells) always splits.
+struct Caps {
+    const int32_t* cap;        // per network, or null: leaf_capacity for every box
+    const uint64_t* prefix;    // box prefixes (with cap)
+    int frame_level;
+    int64_t nf;
+};
+
 __device__ inline OctantSplit octant_split(int64_t base, int64_t l0, int64_t nl, int level,
-                                           int leaf_capacity, int max_depth,
+                                           int leaf_capacity, int max_depth, Caps cp,
                                            const uint64_t* __restrict__ keys,
                                            const int32_t* __restrict__ first,
                                            const int32_t* __restrict__ count) {
@@ -196,7 +206,12 @@ __device__ inline OctantSplit octant_split(int64_t base, int64_t l0, int64_t nl,
         const int64_t i = l0 + r.k;
         const int32_t c = count[i];
         r.lo = first[i];
-        r.split = c > leaf_capacity && level < max_depth;
+        int cap = leaf_capacity;
+        if (cp.cap)
+            cap = level >= cp.frame_level
+                      ? cp.cap[box_frame(cp.prefix[i], level, cp.frame_level, cp.nf)]
+                      : -1;
+        r.split = c > cap && level < max_depth;
         if (r.split)
             e = octant_lower_bound(keys, r.lo, r.lo + c, 3 * (kMortonBits - (level + 1)),
                                    (uint32_t)o + 1);
@@ -210,7 +225,7 @@ __device__ inline OctantSplit octant_split(int64_t base, int64_t l0, int64_t nl,
 // number of non-empty octants of every box at this level that is split; the
 // level's boxes are [lb[0], lb[1]), their count goes to *scan_n for the scan
 __global__ void k_count_children(const int64_t* __restrict__ lb, int level, int leaf_capacity,
-                                 int max_depth, const uint64_t* __restrict__ keys,
+                                 int max_depth, Caps cp, const uint64_t* __restrict__ keys,
                                  const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                                  int32_t* __restrict__ cnt, int64_t* __restrict__ scan_n) {
     const int lane = threadIdx.x & 31;
@@ -219,7 +234,8 @@ __global__ void k_count_children(const int64_t* __restrict__ lb, int level, int 
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 4; base < nl; base += nw * 4) {
-        OctantSplit r = octant_split(base, l0, nl, level, leaf_capacity, max_depth, keys, first, count);
+        OctantSplit r =
+            octant_split(base, l0, nl, level, leaf_capacity, max_depth, cp, keys, first, count);
         const unsigned m = __ballot_sync(0xffffffffu, r.split && r.end > r.start);
         if (r.valid && (lane & 7) == 0) cnt[r.k] = __popc((m >> (lane & ~7)) & 0xffu);
     }
@@ -227,7 +243,7 @@ __global__ void k_count_children(const int64_t* __restrict__ lb, int level, int 
 
 // children of the level's boxes [lb[0], lb[1]); the next level starts at lb[1]
 __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int leaf_capacity,
-                                int max_depth, const uint64_t* __restrict__ keys,
+                                int max_depth, Caps cp, const uint64_t* __restrict__ keys,
                                 const int32_t* __restrict__ off, uint8_t* __restrict__ nd_level,
                                 uint64_t* __restrict__ nd_prefix, int32_t* __restrict__ nd_first,
                                 int32_t* __restrict__ nd_count, int32_t* __restrict__ nd_parent,
@@ -242,8 +258,8 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 4; base < nl; base += nw * 4) {
-        OctantSplit r = octant_split(base, l0, nl, level, leaf_capacity, max_depth, keys, nd_first,
-                                     nd_count);
+        OctantSplit r = octant_split(base, l0, nl, level, leaf_capacity, max_depth, cp, keys,
+                                     nd_first, nd_count);
         const bool ne = r.split && r.end > r.start;
         const unsigned m = __ballot_sync(0xffffffffu, ne);
         const unsigned grp = (m >> (lane & ~7)) & 0xffu;
@@ -452,11 +468,15 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
     }
     L = std::min(std::max(L, 0), cfg.max_depth);
     const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
+    Caps cp{nullptr, nullptr, c.frame_level, (int64_t)c.frame_off_host.size() - 1};
+    int min_cap = cfg.leaf_capacity;
+    if (framed && c.frame_plans)
+        for (int32_t v : c.frame_cap_host) min_cap = std::min(min_cap, (int)v);
     int32_t* cnt = c.cnt.ensure<int32_t>(nn + 8);
     int32_t* off = c.off.ensure<int32_t>(nn + 8);
     // boxes at level l: at most min(8^l, n), and (l >= 1) at most 8 children
     // of each box of level l-1 that splits, i.e. holds more than C neurons
-    const int64_t splitters = (int64_t)nn / ((int64_t)cfg.leaf_capacity + 1);
+    const int64_t splitters = (int64_t)nn / ((int64_t)min_cap + 1);
     auto level_cap = [&](int l) -> int64_t {
         int64_t c = l < 8 ? std::min<int64_t>((int64_t)1 << (3 * l), (int64_t)nn) : (int64_t)nn;
         if (l >= 1) c = std::min<int64_t>(c, 8 * splitters);
@@ -474,6 +494,10 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         c.nd_child_first.ensure<int32_t>((size_t)cap);
         c.nd_nchild.ensure<uint8_t>((size_t)cap);
         int4* sums = c.nd_sums.ensure<int4>((size_t)cap);
+        if (framed && c.frame_plans) {
+            cp.cap = c.frame_cap.get<int32_t>();
+            cp.prefix = c.nd_prefix.get<uint64_t>();
+        }
         float4* ca = c.nd_ca.ensure<float4>((size_t)cap);
         float4* cd = c.nd_cd.ensure<float4>((size_t)cap);
         k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
@@ -484,13 +508,13 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         for (int l = 0; l < L; ++l) {
             const int64_t lcap = level_cap(l);
             k_count_children<<<Gt, B, 0, s>>>(&dc->level_start[l], l, cfg.leaf_capacity,
-                                              cfg.max_depth, k0, c.nd_first.get<int32_t>(),
+                                              cfg.max_depth, cp, k0, c.nd_first.get<int32_t>(),
                                               c.nd_count.get<int32_t>(), cnt, &dc->scan_n);
             MSP_LAUNCH("count_children");
             scan_dev(c, cnt, off, &dc->scan_n, lcap, &dc->level_start[l + 2],
                      &dc->level_start[l + 1], s, cap, &dc->overflow, &dc->need_nodes, 16);
             k_emit_children<<<Gt, B, 0, s>>>(
-                &dc->level_start[l], l, cfg.leaf_capacity, cfg.max_depth, k0, off,
+                &dc->level_start[l], l, cfg.leaf_capacity, cfg.max_depth, cp, k0, off,
                 c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
                 c.nd_count.get<int32_t>(), c.nd_parent.get<int32_t>(),
                 c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), &dc->overflow);
@@ -499,7 +523,7 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         // would a box of the last built level still split?
         if (L < cfg.max_depth) {
             k_count_children<<<Gt, B, 0, s>>>(&dc->level_start[L], L, cfg.leaf_capacity,
-                                              cfg.max_depth, k0, c.nd_first.get<int32_t>(),
+                                              cfg.max_depth, cp, k0, c.nd_first.get<int32_t>(),
                                               c.nd_count.get<int32_t>(), cnt, &dc->scan_n);
             MSP_LAUNCH("count_children");
             scan_dev(c, cnt, off, &dc->scan_n, (int64_t)nn, &dc->more_levels, nullptr, s);

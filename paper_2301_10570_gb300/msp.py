@@ -158,7 +158,7 @@ def load(path: str = LIB_PATH):
         L.msp_length_loss.restype = C.c_int
         L.msp_set_sigma.argtypes = [vp, C.c_double]
         L.msp_set_sigma.restype = C.c_int
-        L.msp_set_frames.argtypes = [vp, i64, vp, C.c_int]
+        L.msp_set_frames.argtypes = [vp, i64, vp, C.c_int, vp, vp]
         L.msp_set_frames.restype = C.c_int
         for name in ("msp_neuron_steps", "msp_update_synapses", "msp_append_synapses",
                      "msp_selftest_bounded_wait"):
@@ -412,17 +412,30 @@ class MSP:
         self.params["sigma"] = float(sigma)
         self._cfg.sigma = float(sigma)
 
-    def set_frames(self, offsets, level: int):
+    def set_frames(self, offsets, level: int, leaf_capacity=None, cutoff=None):
         """Independent networks in their own frames: network k holds neurons
         [offsets[k], offsets[k+1]) with positions relative to its own cell at
-        `level` (msp_set_frames); offsets=None removes them."""
+        `level` (msp_set_frames), optionally with its own leaf capacity and
+        cutoff; offsets=None removes them."""
         if offsets is None:
-            _check(load().msp_set_frames(self._h, 0, None, 0))
+            _check(load().msp_set_frames(self._h, 0, None, 0, None, None))
             return
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         if off.ndim != 1 or len(off) < 2:
             raise ValueError("offsets must hold at least two entries")
-        _check(load().msp_set_frames(self._h, len(off) - 1, _np(off), int(level)))
+        nn = len(off) - 1
+        cap = cut = None
+        if leaf_capacity is not None:
+            cap = np.ascontiguousarray(leaf_capacity, dtype=np.int32)
+            if cap.shape != (nn,):
+                raise ValueError("one leaf capacity per network")
+        if cutoff is not None:
+            cut = np.ascontiguousarray(cutoff, dtype=np.float64)
+            if cut.shape != (nn,):
+                raise ValueError("one cutoff per network")
+        _check(load().msp_set_frames(self._h, nn, _np(off), int(level),
+                                     None if cap is None else _np(cap),
+                                     None if cut is None else _np(cut)))
 
     # -- the whole step as a CUDA graph ---------------------------------------
     def step_graph_capture(self, pos, type_, vac_axon, vac_dend_e, vac_dend_i, first_step,

@@ -167,13 +167,17 @@ class Batch:
         c = np.stack([k % G, (k // G) % G, k // (G * G)]).astype(np.float64)
         return 2.0 * c * (side / 2.0 ** level)
 
-    def framed(self, pos_local: np.ndarray, side: float, level: int, **kw) -> Workload:
+    def framed(self, pos_local: np.ndarray, side: float, level: int, plans=None,
+               **kw) -> Workload:
         """The whole batch as one problem of kernel width 1, each network in
-        its own frame (positions relative to its cell, sigma units)."""
+        its own frame (positions relative to its cell, sigma units); plans:
+        None, or (leaf capacities, cutoffs) per network (either may be None)."""
+        frames = (self.offsets.copy(), int(level))
+        if plans is not None:
+            frames = frames + tuple(plans)
         return Workload(self.name + "_framed", np.ascontiguousarray(pos_local, np.float32),
                         self.type, self.vac_axon, self.vac_dend_e, self.vac_dend_i,
-                        default_params(side, sigma=1.0, **kw),
-                        frames=(self.offsets.copy(), int(level)))
+                        default_params(side, sigma=1.0, **kw), frames=frames)
 
     def placed(self, pos_local: np.ndarray, side: float, level: int, **kw) -> Workload:
         """The same problem in one common frame: every network moved to its

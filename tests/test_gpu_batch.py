@@ -179,6 +179,80 @@ def test_no_partner_or_synapse_crosses_networks():
     assert np.all(net[res["pre"]] == net[res["post"]])
 
 
+PER_NET = dict(leaf_capacity=[8, 32, 16, 64, 24], cutoff=[2.5, 3.5, 3.0, 4.0, 3.25])
+
+
+def _ranges(first, count, sel, base):
+    return {(int(f) - base, int(c)) for f, c in zip(first[sel], count[sel])}
+
+
+def test_per_network_plans_match_each_network_alone(precision_report):
+    """Every network with its own leaf capacity and cutoff inside the batch:
+    its leaves and its near-field box pairs (as point ranges of its sorted
+    points) equal those of the oracle run on that network alone, in its
+    frame, with its plan, bit for bit; its u agrees within 1e-5; every
+    partner lies within its own network's cutoff."""
+    from oracle import oracle as O
+    b = W.batched_small()
+    caps, cuts = PER_NET["leaf_capacity"], PER_NET["cutoff"]
+    plan = dict(PLAN, cutoff=max(cuts), leaf_capacity=max(caps))
+    local, side, level = _layout(b, **plan)
+    w = b.framed(local, side, level, plans=(caps, cuts), **plan)
+    g = msp.MSP(w.params, frames=w.frames)
+    g.build_tree(*msp.to_device(w))
+    u = g.attraction().cpu().numpy()
+    sel = g.select_partners(4)
+    torch.cuda.synchronize()
+    partner = sel["partner"][:g.num_elements()].cpu().numpy()
+    tree, pairs = g.export_tree(), g.export_pairs()
+    g.close()
+    net = b.network_of()
+    net_sorted = net[tree["perm"]]
+    cell = side / 2.0 ** level
+    leaf = tree["child_first"] < 0
+    near = pairs["kind"] == 2
+    worst = 0.0
+    for k in range(len(b.sigma)):
+        a, e = int(b.offsets[k]), int(b.offsets[k + 1])
+        base = int(np.argmax(net_sorted == k))
+        assert np.all(net_sorted[base:base + e - a] == k)      # contiguous in Morton order
+        params = W.default_params(cell, sigma=1.0, leaf_capacity=caps[k], cutoff=cuts[k],
+                                  rho_max=0.0, p=4, m2l_min_pairs=0, max_depth=21 - level)
+        o = O.Oracle(params)
+        o.build_tree(np.ascontiguousarray(local[:, a:e]), b.type[a:e], b.vac_axon[a:e],
+                     b.vac_dend_e[a:e], b.vac_dend_i[a:e])
+        uo = o.attraction()
+        on, op = o.nodes(), o.pairs()
+        o.close()
+        mine = (tree["first"] >= base) & (tree["first"] < base + e - a) & \
+            (tree["level"] >= level)
+        assert _ranges(tree["first"], tree["count"], leaf & mine, base) == \
+            _ranges(on["first"], on["count"], on["child_first"] < 0, 0), k
+        X, Y = pairs["X"][near], pairs["Y"][near]
+        inX = (tree["first"][X] >= base) & (tree["first"][X] < base + e - a)
+        got = {(int(tree["first"][x]) - base, int(tree["count"][x]), int(tree["first"][y]) - base,
+                int(tree["count"][y])) for x, y in zip(X[inX], Y[inX])}
+        oX, oY = op["X"][op["kind"] == 2], op["Y"][op["kind"] == 2]
+        want = {(int(on["first"][x]), int(on["count"][x]), int(on["first"][y]),
+                 int(on["count"][y])) for x, y in zip(oX, oY)}
+        assert got == want, k
+        m = (b.vac_axon[a:e] > 0) & (uo >= 1e-6 * uo.max())
+        worst = max(worst, float(np.max(np.abs(u[a:e][m] - uo[m]) / uo[m])))
+    precision_report["batch_per_network_plans_u_vs_oracle_alone"] = worst
+    assert worst < 1e-5
+    owner = np.repeat(np.arange(b.n), b.vac_axon)
+    ok = partner >= 0
+    assert ok.mean() > 0.5
+    assert np.all(net[partner[ok]] == net[owner[ok]])
+    d = np.linalg.norm(local[:, owner[ok]].astype(np.float64) -
+                       local[:, partner[ok]].astype(np.float64), axis=0)
+    lim = np.asarray(cuts)[net[owner[ok]]]
+    assert np.all(d < lim * (1 + 1e-5))
+    # the radius is each network's own: the wider networks reach past the
+    # narrowest network's radius
+    assert np.any(d > min(cuts))
+
+
 def test_frames_check_their_arguments():
     b = W.batched_small()
     local, side, level = _layout(b, **PLAN)
@@ -192,6 +266,14 @@ def test_frames_check_their_arguments():
         with pytest.raises(msp.MSPError) as ei:
             g.set_frames(*args)
         assert ei.value.code == 1
+    nn = len(b.sigma)
+    for caps, cuts in [([0] * nn, None), ([400] * nn, None),       # a network of 400
+                       (None, [0.0] * nn), (None, [5.5] * nn)]:
+        with pytest.raises(msp.MSPError) as ei:
+            g.set_frames(off, level, caps, cuts)
+        assert ei.value.code == 1
+    with pytest.raises(ValueError):
+        g.set_frames(off, level, [16] * (nn - 1))
     g.close()
     # a cell no wider than the cutoff radius
     g = msp.MSP(dict(w.params, side=2 ** level * 3.0))
@@ -218,3 +300,38 @@ def test_frames_check_their_arguments():
     g.build_tree(*msp.to_device(wp))
     g.attraction()
     g.close()
+
+
+def test_batch_plan_chooser_raises_the_cutoff_only_where_needed():
+    """The batch plan chooser against each network's own all-pairs
+    evaluation: with a tight bar it raises the cutoff of some networks, never
+    lowers one, and every network it leaves below the largest candidate
+    meets the bar (checked again here from the chosen cutoffs)."""
+    from paper_2301_10570_gb300 import autotune
+    b = W.batched_small()
+    local, side, level = _layout(b, **dict(PLAN, cutoff=max(autotune.BATCH_CUTOFFS)))
+    w = b.framed(local, side, level, **PLAN)
+    # a bar between the networks' errors at the smallest cutoff: some meet
+    # it there, the others need a larger cutoff
+    first, rep0 = autotune.tune_batch_cutoffs(w, tol=1.0, ref_err=0.0)
+    assert first == [autotune.BATCH_CUTOFFS[0]] * len(b.sigma)
+    errs0 = np.asarray(rep0["per_network_max_err"])
+    tol = float(np.median(errs0))
+    assert tol > 0
+    cuts, rep = autotune.tune_batch_cutoffs(w, tol=tol, ref_err=0.0)
+    assert len(cuts) == len(b.sigma)
+    assert all(c in autotune.BATCH_CUTOFFS for c in cuts)
+    assert rep["raised"] >= 1
+    assert rep["rounds"][-1]["max_err"] <= rep["rounds"][0]["max_err"]
+    wt = b.framed(local, side, level, plans=(None, cuts), **PLAN)
+    g = msp.MSP(wt.params, frames=wt.frames)
+    g.build_tree(*msp.to_device(wt))
+    u = g.attraction().cpu().numpy()
+    ud = g.direct().cpu().numpy()
+    g.close()
+    for k in range(len(b.sigma)):
+        if cuts[k] == max(autotune.BATCH_CUTOFFS):
+            continue
+        a, e = b.offsets[k], b.offsets[k + 1]
+        m = (b.vac_axon[a:e] > 0) & (ud[a:e] >= 1e-6 * ud[a:e].max())
+        assert np.max(np.abs(u[a:e][m] - ud[a:e][m]) / ud[a:e][m]) <= tol, k
