@@ -1259,7 +1259,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         # the oracle has no frames: the batch's networks in one common frame
         out["cpu_baseline"] = cpu_baseline(batched_workload(dev, common_frame=True)
-                                           if batched else w)
+                                           if args.workload == "batched_256" else w)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
