@@ -929,18 +929,25 @@ def _timed_attraction(g, flush, reps):
 
 def uniform_records(dev, reps=3):
     """The two uniform workloads: 4,096 neurons in a 10,000 um cube (p = 4,
-    leaf capacity 32: a whole eager step, launch-bound) and 262,144 neurons at
-    the same density in a 40,000 um cube, attraction with translated pairs at
-    p = 3, 4, 6 (leaf capacity 8, rho_max 0.5, cutoff 4 sigma) and with the
-    near field only, each against the all-pairs evaluation of the same GPU."""
+    leaf capacity 32: a whole eager step, launch-bound; u against the oracle's
+    FP64 brute force on every target) and 262,144 neurons at the same density
+    in a 40,000 um cube, attraction with translated pairs at p = 3, 4, 6 (leaf
+    capacity 8, rho_max 0.5, cutoff 4 sigma), with the near field only, and
+    with the plan chooser's plan, each against the all-pairs evaluation of the
+    same GPU on every target and the FP64 brute force on 4,096 sampled
+    targets."""
+    import numpy as np
     import torch
 
-    from paper_2301_10570_gb300 import msp, workloads as W
+    from paper_2301_10570_gb300 import autotune, msp, workloads as W
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out = {}
     w = W.uniform_4k()
     g = msp.MSP(w.params, device=dev.index)
     d = msp.to_device(w, dev)
+    g.build_tree(*d)
+    u4 = g.attraction().cpu().numpy()
+    ref4 = fp64_reference(w, np.arange(w.n))
     ts = []
     for k in range(reps + 2):
         flush.zero_()
@@ -955,13 +962,23 @@ def uniform_records(dev, reps=3):
     g.close()
     out["uniform_4k"] = {"what": "eager step (tree, attraction, selection), p = 4, leaf capacity 32",
                          "ms_per_step": round(statistics.median(ts[2:]), 3),
-                         "neurons_per_s": w.n / (statistics.median(ts[2:]) / 1e3)}
+                         "neurons_per_s": w.n / (statistics.median(ts[2:]) / 1e3),
+                         "error_vs_fp64_all_targets": error_report(u4, ref4)}
     rows = []
     ref = None
-    for plan in (dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=3, m2l_min_pairs=0),
-                 dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=4, m2l_min_pairs=0),
-                 dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=6, m2l_min_pairs=0),
-                 dict(leaf_capacity=64, rho_max=0.0, cutoff=3.5, p=4, m2l_min_pairs=0)):
+    w0 = W.uniform_256k()
+    idx = np.sort(np.random.default_rng(0).choice(w0.n, FP64_SAMPLE, replace=False))
+    ref64 = fp64_reference(w0, idx)
+    chosen, _ = autotune.tune(w0, device=dev.index, candidates=dict(
+        leaf_capacity=(16, 32, 64, 128), cutoff=(3.25, 3.5, 4.0),
+        expansions=((0.0, 4, 0), (0.5, 4, 0), (0.5, 6, 0))), reps=3)
+    plans = [dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=3, m2l_min_pairs=0),
+             dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=4, m2l_min_pairs=0),
+             dict(leaf_capacity=8, rho_max=0.5, cutoff=4.0, p=6, m2l_min_pairs=0),
+             dict(leaf_capacity=64, rho_max=0.0, cutoff=3.5, p=4, m2l_min_pairs=0)]
+    if chosen is not None:
+        plans.append(dict(chosen))
+    for i, plan in enumerate(plans):
         w = W.uniform_256k(**plan)
         g = msp.MSP(w.params, device=dev.index)
         g.build_tree(*msp.to_device(w, dev))
@@ -970,11 +987,14 @@ def uniform_records(dev, reps=3):
         ms, u = _timed_attraction(g, flush, reps)
         st = g.stats()
         g.close()
-        rep = error_report(u.cpu().numpy(), ref)
-        rows.append({"plan": plan, "attraction_ms": round(ms, 3), "far_pairs": st["n_far"],
+        un = u.cpu().numpy()
+        rep = error_report(un, ref)
+        rows.append({"plan": plan, "chosen_by_plan_chooser": chosen is not None and
+                     i == len(plans) - 1, "attraction_ms": round(ms, 3), "far_pairs": st["n_far"],
                      "near_field_pairs": st["n_p2p"],
                      "max_rel_err_vs_direct_fp32": rep["max_rel_err"],
-                     "l2_rel_err": rep["l2_rel_err"]})
+                     "l2_rel_err": rep["l2_rel_err"],
+                     "max_rel_err_vs_fp64_sampled": error_report(un[idx], ref64)["max_rel_err"]})
     out["uniform_256k"] = rows
     return out
 
