@@ -208,17 +208,21 @@ def test_graph_refuses_to_replay_after_workspace_reallocation():
     g.close()
 
 
-def test_graph_replays_of_a_batch_equal_eager_steps():
+@pytest.mark.parametrize("full_build", [False, True])
+def test_graph_replays_of_a_batch_equal_eager_steps(full_build):
     # the batched problem (several networks, each in its own frame, as one
-    # problem) through the step graph, against the same steps as eager calls
+    # problem, with a cutoff per network) through the step graph, against the
+    # same steps as eager calls; with full_build the replays recompute the
+    # frames' Morton keys and the octree every step
     from paper_2301_10570_gb300 import workloads as W2
     b = W2.batched_small()
     plan = dict(leaf_capacity=16, cutoff=3.25, rho_max=0.0, p=4, m2l_min_pairs=0)
     local, side, level = msp.batch_layout(torch.from_numpy(b.pos).cuda(), b.offsets, b.sigma,
-                                          plan["cutoff"], plan["leaf_capacity"])
-    w = b.framed(local.cpu().numpy(), side, level, **plan)
+                                          4.0, plan["leaf_capacity"])
+    w = b.framed(local.cpu().numpy(), side, level, plans=(None, [3.25, 4.0, 3.5, 3.25, 3.5]),
+                 **plan)
     ce, se, le = _eager(w, 7, 4)
-    cg, sg, lg, _, _ = _graph(w, 7, 4)
+    cg, sg, lg, _, _ = _graph(w, 7, 4, full_build=full_build)
     assert cg == ce
     for x, y in zip(sg, se):
         assert np.array_equal(x, y)
