@@ -44,7 +44,8 @@ __global__ void k_grad_gather(int64_t n, const int32_t* __restrict__ perm,
 
 constexpr int kGrWarps = 4;
 constexpr int kGrStage = 64;
-constexpr int kGrList = 64;    // evaluation points per pass (two per lane)
+constexpr int kGrMaxR = 3;                // evaluation points per lane
+constexpr int kGrList = 32 * kGrMaxR;     // evaluation points per pass
 
 // A staged pair of sources against one evaluation point t, whose scaled
 // coordinates are broadcast into both halves of register pairs; every step is
@@ -77,47 +78,189 @@ __device__ __forceinline__ void gr_term(const float4 A, const float4 B, const fl
     }
 }
 
-// The staged pairs [0, mp) against the lane's first point, and its second
-// point too when NP = 2.
-template <bool FORWARD, bool SELF, int NP>
+// The staged pairs j = ksl, ksl + slices, ... < mp against the lane's R points.
+template <bool FORWARD, bool SELF, int R>
 __device__ __forceinline__ void gr_eval(const float4* sA, const float4* sB, const float4* sC,
-                                        int mp, float2 tx0, float2 ty0, float2 tz0, float2 tx1,
-                                        float2 ty1, float2 tz1, bool inh0, bool inh1, int32_t e0,
-                                        int32_t e1, float2& a00, float2& a10, float2& a01,
-                                        float2& a11) {
+                                        int mp, int ksl, int slices, const float2 (&tx)[R],
+                                        const float2 (&ty)[R], const float2 (&tz)[R],
+                                        const bool (&inh)[R], const int32_t (&e)[R],
+                                        float2 (&a0)[R], float2 (&a1)[R]) {
 #pragma unroll 2
-    for (int j = 0; j < mp; ++j) {
+    for (int j = ksl; j < mp; j += slices) {
         const float4 A = sA[j], B = sB[j], C = sC[j];
-        gr_term<FORWARD, SELF>(A, B, C, tx0, ty0, tz0, inh0, e0, a00, a10);
-        if (NP == 2) gr_term<FORWARD, SELF>(A, B, C, tx1, ty1, tz1, inh1, e1, a01, a11);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            gr_term<FORWARD, SELF>(A, B, C, tx[r], ty[r], tz[r], inh[r], e[r], a0[r], a1[r]);
     }
 }
 
-// One block per leaf L of a segment list (the evaluation leaf), its 4 warps
-// taking the segment's partner leaves P round-robin.  Warp 0 lists L's
-// evaluation points, up to 64 per pass (FORWARD: the targets, a_t > 0;
-// ADJOINT: every point); each lane holds two of them (lane, lane + 32).  Each
-// warp stages P's points in shared memory, 64 at a time in pairs, as scaled
-// positions sqrt(k2) (x - o) relative to a point o of L, and two weights, and
-// every lane sums over the staged pairs, q = |t^ - s^|^2 and 2^-q in single
-// precision, the even and the odd sources of a point in the two halves of a
-// register pair.  The 4 warps' sums are added in a fixed order, so a point's
-// sum does not depend on how the points are packed into passes.
+// One pass over the evaluation points plist[0, np) of leaf L against the
+// partner leaves of pairs [i0, i1).  A lane holds R points (slots R j .. R j
+// + R - 1 of its group j); when the groups fit in fewer lanes they take
+// npr = 2^k lanes and 32 / npr lanes share a group, each walking an
+// interleaved slice of the staged sources.  The 4 warps take the partner
+// leaves round-robin; each packs its partners' points into chunks of 64 in
+// shared memory, in pairs, as scaled positions sqrt(k2) (x - o) relative to a
+// point o of L, and two weights (L's own points last, in chunks of their own,
+// where a point skips itself).  The slices' sums are combined by a fixed butterfly
+// and the 4 warps' in a fixed order, so a point's sum does not depend on the
+// timing of the warps.
+template <bool FORWARD, int R>
+__device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0, int32_t i1,
+                                        int32_t L, const float4& O,
+                                        const int32_t* __restrict__ pairs,
+                                        const int32_t* __restrict__ pPart,
+                                        const int32_t* __restrict__ nfirst,
+                                        const int32_t* __restrict__ ncount,
+                                        const float4* __restrict__ pts,
+                                        const float4* __restrict__ gw, float sqk, float4* sAw,
+                                        float4* sBw, float4* sCw, float (*red)[2][kGrList]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int lg = 0;
+    while ((1 << lg) < (np + R - 1) / R) ++lg;
+    const int npr = 1 << lg, slices = 32 >> lg;
+    const int j = lane & (npr - 1), ksl = lane >> lg;
+    const bool active = R * j < np;
+    float2 tx[R], ty[R], tz[R], a0[R], a1[R];
+    bool inh[R];
+    int32_t e[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int slot = R * j + r;
+        const bool v = slot < np;
+        e[r] = v ? plist[slot] : -1;
+        const int32_t pi = v ? e[r] : plist[0];
+        const float4 T = pts[pi];
+        inh[r] = (__float_as_uint(gw[pi].w) & 1u) != 0;
+        const float x = (T.x - O.x) * sqk, y = (T.y - O.y) * sqk, z = (T.z - O.z) * sqk;
+        tx[r] = make_float2(x, x);
+        ty[r] = make_float2(y, y);
+        tz[r] = make_float2(z, z);
+        a0[r] = make_float2(0.f, 0.f);
+        a1[r] = make_float2(0.f, 0.f);
+    }
+    float* fA = reinterpret_cast<float*>(sAw);
+    float* fB = reinterpret_cast<float*>(sBw);
+    float* fC = reinterpret_cast<float*>(sCw);
+    // stage sources [pf + sb, pf + sb + take) at chunk positions fill.. (two
+    // per staged pair); position m of an odd chunk is padded before use
+    auto stage = [&](int32_t pf, int32_t sb, int take, int fill) {
+        for (int k = lane; k < take; k += 32) {
+            const float4 S = pts[pf + sb + k];
+            const float4 W = gw[pf + sb + k];
+            float w0, w1;
+            if (FORWARD) {
+                w0 = W.x;
+                w1 = W.y;
+            } else {
+                const uint32_t f2 = __float_as_uint(W.w);
+                const float gv = (f2 & 2u) ? W.z : 0.f;
+                w0 = (f2 & 1u) ? 0.f : gv;
+                w1 = (f2 & 1u) ? gv : 0.f;
+            }
+            const int pos = fill + k, jj = pos >> 1, h = pos & 1;
+            fA[4 * jj + h] = -(S.x - O.x) * sqk;
+            fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
+            fB[4 * jj + h] = -(S.z - O.z) * sqk;
+            fB[4 * jj + 2 + h] = w0;
+            fC[4 * jj + h] = w1;
+            fC[4 * jj + 2 + h] = __int_as_float(pf + sb + k);
+        }
+    };
+    auto pad = [&](int m) {
+        if ((m & 1) && lane == 0) {
+            const int jj = m >> 1;
+            fA[4 * jj + 1] = 0.f;
+            fA[4 * jj + 3] = 0.f;
+            fB[4 * jj + 1] = 0.f;
+            fB[4 * jj + 3] = 0.f;
+            fC[4 * jj + 1] = 0.f;
+            fC[4 * jj + 3] = __int_as_float(-1);
+        }
+    };
+    // the partner leaves other than L, packed into full chunks (the sums
+    // need no per-pair result); then L itself, whose terms skip t = s
+    int fill = 0;
+    bool self = false;
+    for (int32_t i = i0 + w; i < i1; i += kGrWarps) {
+        const int32_t P = pPart[pairs[i]];
+        if (P == L) {
+            self = true;
+            continue;
+        }
+        const int32_t pf = nfirst[P], pc = ncount[P];
+        for (int32_t sb = 0; sb < pc;) {
+            const int take = min(kGrStage - fill, pc - sb);
+            stage(pf, sb, take, fill);
+            fill += take;
+            sb += take;
+            if (fill == kGrStage) {
+                __syncwarp();
+                if (active)
+                    gr_eval<FORWARD, false, R>(sAw, sBw, sCw, kGrStage / 2, ksl, slices, tx, ty,
+                                               tz, inh, e, a0, a1);
+                __syncwarp();
+                fill = 0;
+            }
+        }
+    }
+    if (fill > 0) {
+        pad(fill);
+        __syncwarp();
+        if (active)
+            gr_eval<FORWARD, false, R>(sAw, sBw, sCw, (fill + 1) >> 1, ksl, slices, tx, ty, tz,
+                                       inh, e, a0, a1);
+        __syncwarp();
+    }
+    if (self) {
+        const int32_t pf = nfirst[L], pc = ncount[L];
+        for (int32_t sb = 0; sb < pc; sb += kGrStage) {
+            const int m = min(kGrStage, pc - sb);
+            stage(pf, sb, m, 0);
+            pad(m);
+            __syncwarp();
+            if (active)
+                gr_eval<FORWARD, true, R>(sAw, sBw, sCw, (m + 1) >> 1, ksl, slices, tx, ty, tz,
+                                          inh, e, a0, a1);
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float s0 = a0[r].x + a0[r].y, s1 = a1[r].x + a1[r].y;
+        for (int o = npr; o < 32; o <<= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        const int slot = R * j + r;
+        if (ksl == 0 && slot < np) {
+            red[w][0][slot] = s0;
+            red[w][1][slot] = s1;
+        }
+    }
+}
+
+// One block per leaf L of a segment list (the evaluation leaf; with `order`,
+// the segments longest first), its 4 warps taking the segment's partner
+// leaves P.  Warp 0 lists L's evaluation points, up to kGrList per pass
+// (FORWARD: the targets, a_t > 0; ADJOINT: every point), and the pass holds R
+// = 1..3 of them per lane, R the fewest evaluated slots per source (ties to
+// the larger R: fewer shared-memory loads per evaluation).
 //   FORWARD: evaluation points = targets t (a_t > 0), partner weights
 //            (w^E, w^I): u += w^{T(t)} 2^-q, d += w^{T(t)} q 2^-q.
 //   ADJOINT: evaluation points = sources s, partner weights
 //            (g_t [T(t) = E], g_t [T(t) = I]) (0 unless a_t > 0):
 //            gE += w0 2^-q, gI += w1 2^-q.
-// Points that are not evaluated keep the zero the caller wrote.  Six blocks
-// per SM (at most 80 registers: the unrolled paired loop spills below that).
+// Points that are not evaluated keep the zero the caller wrote.
 template <bool FORWARD>
 __global__ void __launch_bounds__(kGrWarps * 32, 6)
 k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
-             const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
-             const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
-             const int32_t* __restrict__ ncount, const float4* __restrict__ pts,
-             const float4* __restrict__ gw, const int32_t* __restrict__ perm, float sqk,
-             float dscale, float* __restrict__ out0, float* __restrict__ out1) {
+             const int32_t* __restrict__ order, const int32_t* __restrict__ pairs,
+             const int32_t* __restrict__ pEval, const int32_t* __restrict__ pPart,
+             const int32_t* __restrict__ nfirst, const int32_t* __restrict__ ncount,
+             const float4* __restrict__ pts, const float4* __restrict__ gw,
+             const int32_t* __restrict__ perm, float sqk, float dscale, float* __restrict__ out0,
+             float* __restrict__ out1) {
     __shared__ float4 sA[kGrWarps][kGrStage / 2], sB[kGrWarps][kGrStage / 2],
         sC[kGrWarps][kGrStage / 2];
     __shared__ float red[kGrWarps][2][kGrList];
@@ -125,7 +268,8 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
     __shared__ int s_np, s_pos;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nseg = *nseg_dev;
-    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    for (int64_t b = blockIdx.x; b < nseg; b += gridDim.x) {
+        const int64_t sg = order ? order[b] : b;
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
         const int32_t L = pEval[pairs[i0]];
         const int32_t lf = nfirst[L], lc = ncount[L];
@@ -167,91 +311,30 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
             pos = s_pos;
             __syncthreads();
             if (np == 0) break;
-            const bool v0 = lane < np, v1 = lane + 32 < np;
-            const int32_t e0 = v0 ? plist[lane] : -1, e1 = v1 ? plist[lane + 32] : -1;
-            const float4 T0 = pts[v0 ? e0 : plist[0]], T1 = pts[v1 ? e1 : plist[0]];
-            const bool inh0 = __float_as_uint(gw[v0 ? e0 : plist[0]].w) & 1u;
-            const bool inh1 = __float_as_uint(gw[v1 ? e1 : plist[0]].w) & 1u;
-            const float x0 = (T0.x - O.x) * sqk, y0 = (T0.y - O.y) * sqk, z0 = (T0.z - O.z) * sqk;
-            const float x1 = (T1.x - O.x) * sqk, y1 = (T1.y - O.y) * sqk, z1 = (T1.z - O.z) * sqk;
-            const float2 tx0 = make_float2(x0, x0), ty0 = make_float2(y0, y0),
-                         tz0 = make_float2(z0, z0);
-            const float2 tx1 = make_float2(x1, x1), ty1 = make_float2(y1, y1),
-                         tz1 = make_float2(z1, z1);
-            float2 a00 = make_float2(0.f, 0.f), a10 = make_float2(0.f, 0.f);
-            float2 a01 = make_float2(0.f, 0.f), a11 = make_float2(0.f, 0.f);
-            for (int32_t i = i0 + w; i < i1; i += kGrWarps) {
-                const int32_t P = pPart[pairs[i]];
-                const int32_t pf = nfirst[P], pc = ncount[P];
-                for (int32_t sb = 0; sb < pc; sb += kGrStage) {
-                    const int m = min(kGrStage, pc - sb);
-                    const int mp = (m + 1) >> 1;
-                    __syncwarp();
-                    float* fA = reinterpret_cast<float*>(sA[w]);
-                    float* fB = reinterpret_cast<float*>(sB[w]);
-                    float* fC = reinterpret_cast<float*>(sC[w]);
-                    for (int k = lane; k < 2 * mp; k += 32) {
-                        float sx = 0.f, sy = 0.f, sz = 0.f, w0 = 0.f, w1 = 0.f;
-                        int32_t si = -1;
-                        if (k < m) {
-                            const float4 S = pts[pf + sb + k];
-                            const float4 W = gw[pf + sb + k];
-                            sx = (S.x - O.x) * sqk;
-                            sy = (S.y - O.y) * sqk;
-                            sz = (S.z - O.z) * sqk;
-                            if (FORWARD) {
-                                w0 = W.x;
-                                w1 = W.y;
-                            } else {
-                                const uint32_t f2 = __float_as_uint(W.w);
-                                const float gv = (f2 & 2u) ? W.z : 0.f;
-                                w0 = (f2 & 1u) ? 0.f : gv;
-                                w1 = (f2 & 1u) ? gv : 0.f;
-                            }
-                            si = pf + sb + k;
-                        }
-                        const int j = k >> 1, h = k & 1;
-                        fA[4 * j + h] = -sx;
-                        fA[4 * j + 2 + h] = -sy;
-                        fB[4 * j + h] = -sz;
-                        fB[4 * j + 2 + h] = w0;
-                        fC[4 * j + h] = w1;
-                        fC[4 * j + 2 + h] = __int_as_float(si);
-                    }
-                    __syncwarp();
-                    if (v0) {
-                        // the second point of the lanes only while the pass
-                        // has more than 32 points
-                        if (np > 32) {
-                            if (P == L)
-                                gr_eval<FORWARD, true, 2>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
-                                                          tx1, ty1, tz1, inh0, inh1, e0, e1, a00,
-                                                          a10, a01, a11);
-                            else
-                                gr_eval<FORWARD, false, 2>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
-                                                           tx1, ty1, tz1, inh0, inh1, e0, e1,
-                                                           a00, a10, a01, a11);
-                        } else {
-                            if (P == L)
-                                gr_eval<FORWARD, true, 1>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
-                                                          tx1, ty1, tz1, inh0, inh1, e0, e1, a00,
-                                                          a10, a01, a11);
-                            else
-                                gr_eval<FORWARD, false, 1>(sA[w], sB[w], sC[w], mp, tx0, ty0, tz0,
-                                                           tx1, ty1, tz1, inh0, inh1, e0, e1,
-                                                           a00, a10, a01, a11);
-                        }
-                    }
+            int R = 1, best = 1 << 30;
+            for (int rr = 1; rr <= kGrMaxR; ++rr) {
+                const int g = (np + rr - 1) / rr;
+                if (g > 32) continue;
+                int npr = 1;
+                while (npr < g) npr <<= 1;
+                if (npr * rr <= best) {
+                    best = npr * rr;
+                    R = rr;
                 }
             }
-            red[w][0][lane] = a00.x + a00.y;
-            red[w][0][lane + 32] = a01.x + a01.y;
-            red[w][1][lane] = a10.x + a10.y;
-            red[w][1][lane + 32] = a11.x + a11.y;
+            if (R == 1)
+                gr_pass<FORWARD, 1>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
+                                    gw, sqk, sA[w], sB[w], sC[w], red);
+            else if (R == 2)
+                gr_pass<FORWARD, 2>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
+                                    gw, sqk, sA[w], sB[w], sC[w], red);
+            else
+                gr_pass<FORWARD, 3>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
+                                    gw, sqk, sA[w], sB[w], sC[w], red);
             __syncthreads();
             if (w == 0) {
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
+                for (int r = 0; r < kGrMaxR; ++r) {
                     const int j = lane + 32 * r;
                     if (j >= np) continue;
                     float s0 = red[0][0][j], s1 = red[0][1][j];
@@ -372,8 +455,10 @@ void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const u
     if (u || dud) {
         if (u) MSP_CUDA(cudaMemsetAsync(u, 0, (size_t)n * sizeof(float), s));
         if (dud) MSP_CUDA(cudaMemsetAsync(dud, 0, (size_t)n * sizeof(float), s));
+        // the segments in the near field's order (longest first), kept with the lists
         k_grad_pairs<true><<<nb, kGrWarps * 32, 0, s>>>(
-            c.seg_first.get<int32_t>(), &dc->nseg, list_q, c.pr_X.get<int32_t>(),
+            c.seg_first.get<int32_t>(), &dc->nseg, c.nf_oval0.get<int32_t>(), list_q,
+            c.pr_X.get<int32_t>(),
             c.pr_Y.get<int32_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
             c.pts.get<float4>(), gw, c.perm.get<int32_t>(), sqk, dscale, u, dud);
         MSP_LAUNCH("grad_forward");
@@ -386,7 +471,7 @@ void attraction_grad(msp_ctx& c, const uint8_t* type, const uint8_t* va, const u
         const int32_t *segf = nullptr, *v0 = nullptr;
         pairs_by_source(c, s, &segf, &v0);
         k_grad_pairs<false><<<nb, kGrWarps * 32, 0, s>>>(
-            segf, &dc->scan_n, v0, c.pr_Y.get<int32_t>(), c.pr_X.get<int32_t>(),
+            segf, &dc->scan_n, nullptr, v0, c.pr_Y.get<int32_t>(), c.pr_X.get<int32_t>(),
             c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), c.pts.get<float4>(), gw,
             c.perm.get<int32_t>(), sqk, dscale, oE, oI);
         MSP_LAUNCH("grad_adjoint");
