@@ -94,6 +94,45 @@ __device__ __forceinline__ void gr_eval(const float4* sA, const float4* sB, cons
     }
 }
 
+// The transposed sums in the expanded form: with the point s^ held as 2 s^ and
+// a staged partner t as (t^, -|t^|^2), E = 2 s^.t^ - |t^|^2 and
+// K(t,s) = 2^E 2^-|s^|^2 (the last factor applied once per point; E <= |s^|^2,
+// which the pass keeps at most kGrFastT2).  Staged pair j: A = (x0, x1, y0, y1),
+// B = (z0, z1, c0, c1), C = (gE0, gE1, gI0, gI1), D = (index0, index1).
+constexpr float kGrFastT2 = 20.f;
+
+template <bool SELF>
+__device__ __forceinline__ void gr_term_fast(const float4 A, const float4 B, const float4 C,
+                                             const int2 D, float2 tx, float2 ty, float2 tz,
+                                             int32_t e, float2& a0, float2& a1) {
+    const float2 E = __ffma2_rn(tx, make_float2(A.x, A.y),
+                                __ffma2_rn(ty, make_float2(A.z, A.w),
+                                           __ffma2_rn(tz, make_float2(B.x, B.y),
+                                                      make_float2(B.z, B.w))));
+    float2 k = make_float2(gr_ex2(E.x), gr_ex2(E.y));
+    if (SELF) {
+        k.x = D.x == e ? 0.f : k.x;
+        k.y = D.y == e ? 0.f : k.y;
+    }
+    a0 = __ffma2_rn(make_float2(C.x, C.y), k, a0);
+    a1 = __ffma2_rn(make_float2(C.z, C.w), k, a1);
+}
+
+template <bool SELF, int R>
+__device__ __forceinline__ void gr_eval_fast(const float4* sA, const float4* sB, const float4* sC,
+                                             const int2* sD, int mp, int ksl, int slices,
+                                             const float2 (&tx)[R], const float2 (&ty)[R],
+                                             const float2 (&tz)[R], const int32_t (&e)[R],
+                                             float2 (&a0)[R], float2 (&a1)[R]) {
+#pragma unroll 2
+    for (int j = ksl; j < mp; j += slices) {
+        const float4 A = sA[j], B = sB[j], C = sC[j];
+        const int2 D = SELF ? sD[j] : make_int2(0, 0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) gr_term_fast<SELF>(A, B, C, D, tx[r], ty[r], tz[r], e[r], a0[r], a1[r]);
+    }
+}
+
 // One pass over the evaluation points plist[0, np) of leaf L against the
 // partner leaves of pairs [i0, i1).  A lane holds R points (slots R j .. R j
 // + R - 1 of its group j); when the groups fit in fewer lanes they take
@@ -105,7 +144,7 @@ __device__ __forceinline__ void gr_eval(const float4* sA, const float4* sB, cons
 // where a point skips itself).  The slices' sums are combined by a fixed butterfly
 // and the 4 warps' in a fixed order, so a point's sum does not depend on the
 // timing of the warps.
-template <bool FORWARD, int R>
+template <bool FORWARD, int R, bool FAST>
 __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0, int32_t i1,
                                         int32_t L, const float4& O,
                                         const int32_t* __restrict__ pairs,
@@ -114,7 +153,9 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
                                         const int32_t* __restrict__ ncount,
                                         const float4* __restrict__ pts,
                                         const float4* __restrict__ gw, float sqk, float4* sAw,
-                                        float4* sBw, float4* sCw, float (*red)[2][kGrList]) {
+                                        float4* sBw, float4* sCw, int2* sDw,
+                                        float (*red)[2][kGrList]) {
+    static_assert(!(FAST && FORWARD), "the expanded form serves the transposed sums only");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lg = 0;
     while ((1 << lg) < (np + R - 1) / R) ++lg;
@@ -124,6 +165,7 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
     float2 tx[R], ty[R], tz[R], a0[R], a1[R];
     bool inh[R];
     int32_t e[R];
+    float sc[R];   // FAST: 2^-|s^|^2 of the point
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int slot = R * j + r;
@@ -133,12 +175,15 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
         const float4 T = pts[pi];
         inh[r] = (__float_as_uint(gw[pi].w) & 1u) != 0;
         const float x = (T.x - O.x) * sqk, y = (T.y - O.y) * sqk, z = (T.z - O.z) * sqk;
-        tx[r] = make_float2(x, x);
-        ty[r] = make_float2(y, y);
-        tz[r] = make_float2(z, z);
+        const float f = FAST ? 2.f : 1.f;
+        tx[r] = make_float2(f * x, f * x);
+        ty[r] = make_float2(f * y, f * y);
+        tz[r] = make_float2(f * z, f * z);
+        sc[r] = FAST ? gr_ex2(-fmaf(x, x, fmaf(y, y, z * z))) : 1.f;
         a0[r] = make_float2(0.f, 0.f);
         a1[r] = make_float2(0.f, 0.f);
     }
+    int* fD = reinterpret_cast<int*>(sDw);
     float* fA = reinterpret_cast<float*>(sAw);
     float* fB = reinterpret_cast<float*>(sBw);
     float* fC = reinterpret_cast<float*>(sCw);
@@ -159,12 +204,24 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
                 w1 = (f2 & 1u) ? gv : 0.f;
             }
             const int pos = fill + k, jj = pos >> 1, h = pos & 1;
-            fA[4 * jj + h] = -(S.x - O.x) * sqk;
-            fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
-            fB[4 * jj + h] = -(S.z - O.z) * sqk;
-            fB[4 * jj + 2 + h] = w0;
-            fC[4 * jj + h] = w1;
-            fC[4 * jj + 2 + h] = __int_as_float(pf + sb + k);
+            if (FAST) {
+                const float sx = (S.x - O.x) * sqk, sy = (S.y - O.y) * sqk,
+                            sz = (S.z - O.z) * sqk;
+                fA[4 * jj + h] = sx;
+                fA[4 * jj + 2 + h] = sy;
+                fB[4 * jj + h] = sz;
+                fB[4 * jj + 2 + h] = -fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+                fC[4 * jj + h] = w0;
+                fC[4 * jj + 2 + h] = w1;
+                fD[2 * jj + h] = pf + sb + k;
+            } else {
+                fA[4 * jj + h] = -(S.x - O.x) * sqk;
+                fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
+                fB[4 * jj + h] = -(S.z - O.z) * sqk;
+                fB[4 * jj + 2 + h] = w0;
+                fC[4 * jj + h] = w1;
+                fC[4 * jj + 2 + h] = __int_as_float(pf + sb + k);
+            }
         }
     };
     auto pad = [&](int m) {
@@ -175,7 +232,26 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
             fB[4 * jj + 1] = 0.f;
             fB[4 * jj + 3] = 0.f;
             fC[4 * jj + 1] = 0.f;
-            fC[4 * jj + 3] = __int_as_float(-1);
+            fC[4 * jj + 3] = FAST ? 0.f : __int_as_float(-1);
+            if (FAST) fD[2 * jj + 1] = -1;
+        }
+    };
+    // the staged pairs [0, mp) against the lane's points
+    auto eval = [&](int mp, bool selfc) {
+        if (!active) return;
+        if (FAST) {
+            if (selfc)
+                gr_eval_fast<true, R>(sAw, sBw, sCw, sDw, mp, ksl, slices, tx, ty, tz, e, a0, a1);
+            else
+                gr_eval_fast<false, R>(sAw, sBw, sCw, sDw, mp, ksl, slices, tx, ty, tz, e, a0,
+                                       a1);
+        } else {
+            if (selfc)
+                gr_eval<FORWARD, true, R>(sAw, sBw, sCw, mp, ksl, slices, tx, ty, tz, inh, e, a0,
+                                          a1);
+            else
+                gr_eval<FORWARD, false, R>(sAw, sBw, sCw, mp, ksl, slices, tx, ty, tz, inh, e,
+                                           a0, a1);
         }
     };
     // the partner leaves other than L, packed into full chunks (the sums
@@ -196,9 +272,7 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
             sb += take;
             if (fill == kGrStage) {
                 __syncwarp();
-                if (active)
-                    gr_eval<FORWARD, false, R>(sAw, sBw, sCw, kGrStage / 2, ksl, slices, tx, ty,
-                                               tz, inh, e, a0, a1);
+                eval(kGrStage / 2, false);
                 __syncwarp();
                 fill = 0;
             }
@@ -207,9 +281,7 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
     if (fill > 0) {
         pad(fill);
         __syncwarp();
-        if (active)
-            gr_eval<FORWARD, false, R>(sAw, sBw, sCw, (fill + 1) >> 1, ksl, slices, tx, ty, tz,
-                                       inh, e, a0, a1);
+        eval((fill + 1) >> 1, false);
         __syncwarp();
     }
     if (self) {
@@ -219,9 +291,7 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
             stage(pf, sb, m, 0);
             pad(m);
             __syncwarp();
-            if (active)
-                gr_eval<FORWARD, true, R>(sAw, sBw, sCw, (m + 1) >> 1, ksl, slices, tx, ty, tz,
-                                          inh, e, a0, a1);
+            eval((m + 1) >> 1, true);
             __syncwarp();
         }
     }
@@ -231,6 +301,10 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
         for (int o = npr; o < 32; o <<= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (FAST) {
+            s0 *= sc[r];
+            s1 *= sc[r];
         }
         const int slot = R * j + r;
         if (ksl == 0 && slot < np) {
@@ -263,6 +337,7 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
              float* __restrict__ out1) {
     __shared__ float4 sA[kGrWarps][kGrStage / 2], sB[kGrWarps][kGrStage / 2],
         sC[kGrWarps][kGrStage / 2];
+    __shared__ int2 sD[kGrWarps][kGrStage / 2];
     __shared__ float red[kGrWarps][2][kGrList];
     __shared__ int32_t plist[kGrList];
     __shared__ int s_np, s_pos;
@@ -322,15 +397,33 @@ k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ 
                     R = rr;
                 }
             }
-            if (R == 1)
-                gr_pass<FORWARD, 1>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
-                                    gw, sqk, sA[w], sB[w], sC[w], red);
-            else if (R == 2)
-                gr_pass<FORWARD, 2>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
-                                    gw, sqk, sA[w], sB[w], sC[w], red);
-            else
-                gr_pass<FORWARD, 3>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts,
-                                    gw, sqk, sA[w], sB[w], sC[w], red);
+            // the transposed sums take the expanded form while every point of
+            // the pass has |s^|^2 <= kGrFastT2 (the same value in every warp)
+            bool fast = false;
+            if (!FORWARD) {
+                float m2 = 0.f;
+                for (int k = lane; k < np; k += 32) {
+                    const float4 T = pts[plist[k]];
+                    const float x = (T.x - O.x) * sqk, y = (T.y - O.y) * sqk,
+                                z = (T.z - O.z) * sqk;
+                    m2 = fmaxf(m2, fmaf(x, x, fmaf(y, y, z * z)));
+                }
+                for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                fast = m2 <= kGrFastT2;
+            }
+#define MSP_GR_PASS(RR, FF)                                                                   \
+    gr_pass<FORWARD, RR, FF>(plist, np, i0, i1, L, O, pairs, pPart, nfirst, ncount, pts, gw, sqk, \
+                             sA[w], sB[w], sC[w], sD[w], red)
+            if (!FORWARD && fast) {
+                if (R == 1) MSP_GR_PASS(1, !FORWARD);
+                else if (R == 2) MSP_GR_PASS(2, !FORWARD);
+                else MSP_GR_PASS(3, !FORWARD);
+            } else {
+                if (R == 1) MSP_GR_PASS(1, false);
+                else if (R == 2) MSP_GR_PASS(2, false);
+                else MSP_GR_PASS(3, false);
+            }
+#undef MSP_GR_PASS
             __syncthreads();
             if (w == 0) {
 #pragma unroll
