@@ -16,9 +16,10 @@
 // the near-field leaf pairs of the last attraction (a plan without
 // translations: K r has no Hermite expansion), first grouped by target leaf
 // (u, v and their sigma derivatives), then by source leaf (the transposed
-// sums).  One block per leaf, one evaluation point per thread; the partner
-// leaves' points are staged in shared memory, and each staged chunk's sum is
-// added with Kahan's compensated summation.  Every sum has a fixed order, so
+// sums).  One block of 4 warps per leaf, one evaluation point per lane, the
+// warps taking the partner leaves; the partners' points are staged in shared
+// memory, and each staged chunk's sum is added with Kahan's compensated
+// summation.  Every sum has a fixed order, so
 // the results are reproducible; the scalar reductions run in double.
 #include <algorithm>
 #include <cmath>
@@ -32,7 +33,6 @@ void pairs_by_source(msp_ctx& c, cudaStream_t s, const int32_t** segf_out,
 
 namespace {
 
-constexpr int kLenThreads = 128;
 constexpr double kLog2e = 1.4426950408889634;
 
 __device__ inline float len_ex2(float x) {
@@ -66,19 +66,60 @@ __global__ void k_len_gather(int64_t n, const int32_t* __restrict__ perm,
     }
 }
 
-// One block per leaf L of a segment list; its threads take L's points, one
-// each (in rounds of kLenThreads), and every partner leaf P of the segment is
-// staged in shared memory, kLenThreads points at a time.  Coordinates are
+constexpr int kLenWarps = 4;
+constexpr int kLenStage = 32;    // staged sources per warp and chunk
+
+// One block of 4 warps per leaf L of a segment list.  The leaf's points are
+// taken 32 at a time, one per lane, and every warp holds the same points; the
+// warps take the segment's partner leaves P round-robin, each packing its
+// partners' points into chunks of 32 in its own shared memory, and every
+// chunk's sum joins the lane's running sums by Kahan's compensated summation.
+// The 4 warps' compensated sums are added in a fixed order.  Coordinates are
 // scaled by sqk = sqrt(log2 e)/sigma relative to L's first point, so that
-// q = |t^ - s^|^2 gives K = 2^-q and r = rs sqrt(q), rs = sigma/sqrt(log2 e).
+// q = |t^ - s^|^2 gives K = 2^-q and r = rs sqrt(q), rs = sigma/sqrt(log2 e);
+// a point skips itself (by index).
 //   FORWARD (L = the target leaf): per target t with a_t > 0, the sums
 //     U = sum w K, V = sum w K r, QU = sum w K q, QV = sum w K q r
 //     (w: the staged source's weight of t's channel), written in sorted order.
 //   ADJOINT (L = the source leaf): per point s, for each channel T,
 //     G_T = sum_{t: T(t) = T} K (alpha_t r - beta_t)
 //     over the staged targets t (coefficients in cf), written in caller order.
+// the staged chunk [0, m) against the lane's point t, into the lane's
+// compensated running sums
 template <bool FORWARD>
-__global__ void __launch_bounds__(kLenThreads)
+__device__ __forceinline__ void len_eval(const float4* sp, const float4* sw, int m, int32_t t,
+                                         bool inh, float tx, float ty, float tz, float rs,
+                                         float& a0, float& a1, float& a2, float& a3, float& c0,
+                                         float& c1, float& c2, float& c3) {
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    for (int k = 0; k < m; ++k) {
+        const float4 S = sp[k];
+        const float4 SW = sw[k];
+        const float dx = tx - S.x, dy = ty - S.y, dz = tz - S.z;
+        const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float K = __float_as_int(S.w) == t ? 0.f : len_ex2(-q);
+        const float r = rs * len_sqrt(q);
+        if (FORWARD) {
+            const float wk = (inh ? SW.y : SW.x) * K;
+            p0 += wk;
+            p1 = fmaf(wk, r, p1);
+            p2 = fmaf(wk, q, p2);
+            p3 = fmaf(wk * q, r, p3);
+        } else {
+            const float v = K * fmaf(SW.x, r, -SW.y);
+            if (SW.z != 0.f) p1 += v; else p0 += v;
+        }
+    }
+    kahan_add(a0, c0, p0);
+    kahan_add(a1, c1, p1);
+    if (FORWARD) {
+        kahan_add(a2, c2, p2);
+        kahan_add(a3, c3, p3);
+    }
+}
+
+template <bool FORWARD>
+__global__ void __launch_bounds__(kLenWarps * 32)
 k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
             const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
             const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
@@ -86,16 +127,20 @@ k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ n
             const float4* __restrict__ gw, const float2* __restrict__ cf,
             const int32_t* __restrict__ perm, float sqk, float rs, float4* __restrict__ sums,
             float* __restrict__ gE, float* __restrict__ gI) {
-    __shared__ float4 sp[kLenThreads];   // staged point: x^, y^, z^, index (bits)
-    __shared__ float4 sw[kLenThreads];   // FORWARD: w^E, w^I; ADJOINT: alpha, beta, channel
+    __shared__ float4 sp_all[kLenWarps][kLenStage];   // staged point: x^, y^, z^, index (bits)
+    __shared__ float4 sw_all[kLenWarps][kLenStage];   // FORWARD: w^E, w^I; ADJOINT: alpha, beta, channel
+    __shared__ float4 red[kLenWarps][32];              // the warps' compensated sums
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* sp = sp_all[w];
+    float4* sw = sw_all[w];
     const int64_t nseg = *nseg_dev;
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
         const int32_t L = pEval[pairs[i0]];
         const int32_t lf = nfirst[L], lc = ncount[L];
         const float4 O = pts[lf];
-        for (int32_t rb = 0; rb < lc; rb += kLenThreads) {
-            const int32_t e = rb + (int32_t)threadIdx.x;
+        for (int32_t rb = 0; rb < lc; rb += 32) {
+            const int32_t e = rb + lane;
             const bool have = e < lc;
             const int32_t t = lf + (have ? e : 0);
             const float4 T = pts[t];
@@ -105,64 +150,66 @@ k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ n
             const float tx = (T.x - O.x) * sqk, ty = (T.y - O.y) * sqk, tz = (T.z - O.z) * sqk;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;     // running sums
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;     // their compensations
-            for (int32_t i = i0; i < i1; ++i) {
+            int fill = 0;
+            for (int32_t i = i0 + w; i < i1; i += kLenWarps) {
                 const int32_t P = pPart[pairs[i]];
                 const int32_t pf = nfirst[P], pc = ncount[P];
-                for (int32_t sb = 0; sb < pc; sb += kLenThreads) {
-                    const int m = min(kLenThreads, pc - sb);
-                    __syncthreads();
-                    if ((int)threadIdx.x < m) {
-                        const int32_t j = pf + sb + (int32_t)threadIdx.x;
+                for (int32_t sb = 0; sb < pc;) {
+                    const int take = min(kLenStage - fill, pc - sb);
+                    if (lane < take) {
+                        const int32_t j = pf + sb + lane;
                         const float4 S = pts[j];
                         const float4 SW = gw[j];
-                        sp[threadIdx.x] = make_float4((S.x - O.x) * sqk, (S.y - O.y) * sqk,
+                        sp[fill + lane] = make_float4((S.x - O.x) * sqk, (S.y - O.y) * sqk,
                                                       (S.z - O.z) * sqk, __int_as_float(j));
                         if (FORWARD) {
-                            sw[threadIdx.x] = make_float4(SW.x, SW.y, 0.f, 0.f);
+                            sw[fill + lane] = make_float4(SW.x, SW.y, 0.f, 0.f);
                         } else {
                             const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
-                            sw[threadIdx.x] = make_float4(ab.x, ab.y, SW.w, 0.f);
+                            sw[fill + lane] = make_float4(ab.x, ab.y, SW.w, 0.f);
                         }
                     }
-                    __syncthreads();
-                    if (!act) continue;
-                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-                    for (int k = 0; k < m; ++k) {
-                        const float4 S = sp[k];
-                        const float4 SW = sw[k];
-                        const float dx = tx - S.x, dy = ty - S.y, dz = tz - S.z;
-                        const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float K = __float_as_int(S.w) == t ? 0.f : len_ex2(-q);
-                        const float r = rs * len_sqrt(q);
-                        if (FORWARD) {
-                            const float wk = (inh ? SW.y : SW.x) * K;
-                            p0 += wk;
-                            p1 = fmaf(wk, r, p1);
-                            p2 = fmaf(wk, q, p2);
-                            p3 = fmaf(wk * q, r, p3);
-                        } else {
-                            const float v = K * fmaf(SW.x, r, -SW.y);
-                            if (SW.z != 0.f) p1 += v; else p0 += v;
-                        }
-                    }
-                    kahan_add(a0, c0, p0);
-                    kahan_add(a1, c1, p1);
-                    if (FORWARD) {
-                        kahan_add(a2, c2, p2);
-                        kahan_add(a3, c3, p3);
+                    fill += take;
+                    sb += take;
+                    if (fill == kLenStage) {
+                        __syncwarp();
+                        if (act)
+                            len_eval<FORWARD>(sp, sw, kLenStage, t, inh, tx, ty, tz, rs, a0, a1,
+                                              a2, a3, c0, c1, c2, c3);
+                        __syncwarp();
+                        fill = 0;
                     }
                 }
             }
-            if (act) {
+            if (fill > 0) {
+                __syncwarp();
+                if (act)
+                    len_eval<FORWARD>(sp, sw, fill, t, inh, tx, ty, tz, rs, a0, a1, a2, a3, c0,
+                                      c1, c2, c3);
+                __syncwarp();
+            }
+            red[w][lane] = make_float4(__fsub_rn(a0, c0), __fsub_rn(a1, c1), __fsub_rn(a2, c2),
+                                       __fsub_rn(a3, c3));
+            __syncthreads();
+            if (w == 0 && act) {
+                float4 v = red[0][lane];
+#pragma unroll
+                for (int k = 1; k < kLenWarps; ++k) {
+                    const float4 x = red[k][lane];
+                    v.x += x.x;
+                    v.y += x.y;
+                    v.z += x.z;
+                    v.w += x.w;
+                }
                 if (FORWARD) {
-                    sums[t] = make_float4(__fsub_rn(a0, c0), __fsub_rn(a1, c1),
-                                          __fsub_rn(a2, c2), __fsub_rn(a3, c3));
+                    sums[t] = v;
                 } else {
                     const int32_t o = perm[t];
-                    if (gE) gE[o] = __fsub_rn(a0, c0);
-                    if (gI) gI[o] = __fsub_rn(a1, c1);
+                    if (gE) gE[o] = v.x;
+                    if (gI) gI[o] = v.y;
                 }
             }
+            __syncthreads();
         }
     }
 }
@@ -266,7 +313,7 @@ void length_loss(msp_ctx& c, const uint8_t* type, const uint8_t* va, const float
     const int nb = (int)std::min<int64_t>(nseg_cap, 1 << 30);
     float4* sums = c.ln_sums.ensure<float4>((size_t)n);
     MSP_CUDA(cudaMemsetAsync(sums, 0, (size_t)n * sizeof(float4), s));
-    k_len_pairs<true><<<nb, kLenThreads, 0, s>>>(
+    k_len_pairs<true><<<nb, kLenWarps * 32, 0, s>>>(
         c.seg_first.get<int32_t>(), &dc->nseg, c.p2p_val0.get<int32_t>(), c.pr_X.get<int32_t>(),
         c.pr_Y.get<int32_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
         c.pts.get<float4>(), gw, nullptr, c.perm.get<int32_t>(), sqk, rs, sums, nullptr,
@@ -287,7 +334,7 @@ void length_loss(msp_ctx& c, const uint8_t* type, const uint8_t* va, const float
         if (gI) MSP_CUDA(cudaMemsetAsync(gI, 0, (size_t)n * sizeof(float), s));
         const int32_t *segf = nullptr, *list = nullptr;
         pairs_by_source(c, s, &segf, &list);
-        k_len_pairs<false><<<nb, kLenThreads, 0, s>>>(
+        k_len_pairs<false><<<nb, kLenWarps * 32, 0, s>>>(
             segf, &dc->scan_n, list, c.pr_Y.get<int32_t>(), c.pr_X.get<int32_t>(),
             c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(), c.pts.get<float4>(), gw, cf,
             c.perm.get<int32_t>(), sqk, rs, nullptr, gE, gI);
