@@ -1147,7 +1147,7 @@ def _case_gradient_262k(args):
 # selection); "graph"/"graph_full" the whole step captured and replayed
 # (octree reused / rebuilt each replay); "neuron" calls of 10 neuron steps;
 # "attraction" attraction calls timed with CUDA events; "gradient"
-# derivative passes
+# derivative passes, then synapse-length losses
 PROFILE_CASES = {"near_field_131k": (_case_near_field_131k, "steps"),
                  "step_1m": (_case_step_1m, "steps"),
                  "graph_1m": (_case_step_1m, "graph"),
@@ -1205,6 +1205,9 @@ def run_profile_case(args):
         gv = torch.from_numpy(np.random.default_rng(6).normal(size=w.n)).float().cuda()
         for _ in range(steps):
             g.attraction_grad(typ, va, ve, vi, g=gv)
+        # then the synapse-length loss with its gradient (k_len_pairs)
+        for _ in range(steps):
+            g.length_loss(typ, va, ve.float(), vi.float(), 1000.0)
     elif kind in ("graph", "graph_full"):
         # one eager step sizes the graph; then the whole step as graph
         # replays (walk, build, attraction, selection, commit)

@@ -119,7 +119,7 @@ __device__ __forceinline__ void len_eval(const float4* sp, const float4* sw, int
 }
 
 template <bool FORWARD>
-__global__ void __launch_bounds__(kLenWarps * 32)
+__global__ void __launch_bounds__(kLenWarps * 32, 8)
 k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
             const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
             const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
