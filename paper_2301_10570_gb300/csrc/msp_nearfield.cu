@@ -58,9 +58,6 @@ __device__ inline float nf_ex2(float x) {
     return y;
 }
 
-__device__ inline void nf_prefetch_l1(const void* p) {
-    asm volatile("prefetch.L1 [%0];" ::"l"(p));
-}
 
 struct NFArgs {
     const int32_t* seg_first;
@@ -253,17 +250,6 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
             const int32_t sf = __shfl_sync(0xffffffffu, msf, r);
             const int32_t sc = __shfl_sync(0xffffffffu, msc, r);
             const bool self = sf == tf;
-            {
-                // the next pair's sources into L1 while this one is evaluated
-                // (one 128-byte line of points and of weights per lane)
-                const int rn = min(r + 1, 31);
-                const int32_t sfn = __shfl_sync(0xffffffffu, msf, rn);
-                const int32_t scn = __shfl_sync(0xffffffffu, msc, rn);
-                if (r + 1 < nb) {
-                    if (8 * lane < scn) nf_prefetch_l1(a.pts + sfn + 8 * lane);
-                    if (16 * lane < scn) nf_prefetch_l1(a.lw + sfn + 16 * lane);
-                }
-            }
             float part[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) part[k] = 0.f;
@@ -429,7 +415,7 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
     __shared__ float4 st[kNFWarps][kNFStageFloats / 4];
     __shared__ float red[kNFWarps][kNFMaxT];
     __shared__ int32_t tl[kNFList];
-    __shared__ int s_nt, s_pos, s_R;
+    __shared__ int s_nt, s_nreal, s_pos, s_R;
     __shared__ float wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
     __shared__ float scale_all[kNFMaxT], fa_all[kNFMaxT];
@@ -528,17 +514,16 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
                 if (lane < pad) tl[nE + lane] = -1;
                 if (lane == 0) {
                     s_nt = nt + pad;
+                    s_nreal = nt;
                     s_R = R;
                     s_pos = pend;
                 }
             }
             __syncthreads();
-            const int ntl = s_nt, R = s_R;
+            const int ntl = s_nt, R = s_R, nreal = s_nreal;
             pos = s_pos;
             __syncthreads();
             if (ntl == 0) break;
-            int nreal = 0;
-            for (int k = 0; k < ntl; ++k) nreal += tl[k] >= 0;
             if (R == 4)
                 nf_targets<4>(a, tl, ntl, nreal, i0, i1, tf, fast, cx, cy, cz, stw, red, evals);
             else
