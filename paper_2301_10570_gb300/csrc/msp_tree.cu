@@ -22,21 +22,29 @@ __global__ void k_build_init(DevCounts* dc, int64_t n) {
     dc->pos_sum = 0;
 }
 
-// order-independent checksum of the positions: the sum over i of a mix of
-// i and the three coordinates' bits (modulo 2^64)
+// order-independent checksum of the positions: the sum over i (modulo 2^64)
+// of a mix of i and every bit of the three coordinates (the finaliser of
+// SplitMix64, Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014, applied twice)
+__device__ inline unsigned long long pos_mix(unsigned long long h) {
+    h ^= h >> 30;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 27;
+    h *= 0x94D049BB133111EBull;
+    h ^= h >> 31;
+    return h;
+}
+
 __global__ void k_pos_sum(const float* __restrict__ x, const float* __restrict__ y,
                           const float* __restrict__ z, int64_t n,
                           unsigned long long* __restrict__ out) {
     unsigned long long acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
-        h ^= __float_as_uint(x[i]);
-        h *= 0xBF58476D1CE4E5B9ull;
-        h ^= (unsigned long long)__float_as_uint(y[i]) << 21;
-        h *= 0x94D049BB133111EBull;
-        h ^= (unsigned long long)__float_as_uint(z[i]) << 42;
-        h ^= h >> 31;
+        const unsigned long long xy = ((unsigned long long)__float_as_uint(x[i]) << 32) |
+                                      __float_as_uint(y[i]);
+        unsigned long long h = pos_mix(xy ^ ((unsigned long long)i * 0x9E3779B97F4A7C15ull));
+        h = pos_mix(h ^ ((unsigned long long)__float_as_uint(z[i]) * 0xD6E8FEB86659FD93ull));
         acc += h;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -143,6 +143,33 @@ def test_graph_with_moved_positions_halts_and_rebuilds():
     g.close()
 
 
+def test_graph_detects_a_move_in_the_leading_bits_of_z():
+    # a neuron moved by doubling its z coordinate (same mantissa, next
+    # exponent): the positions' checksum covers every bit of every coordinate,
+    # so the replay halts and the step is finished on a new tree
+    w = _workload()
+    moved = W.clustered_small(2, 2048, seed=11, leaf_capacity=32)
+    side = moved.params["side"]
+    j = int(np.argmax((moved.pos[2] > 0.05 * side) & (moved.pos[2] < 0.45 * side)))
+    moved.pos[2, j] = moved.pos[2, j] * np.float32(2.0)
+    assert 0 < moved.pos[2, j] < side
+    ce, se, _ = _eager(moved, 0, 2)
+    pos, t, a, e, i = _state(w)
+    g = msp.MSP(w.params)
+    g.build_tree(pos, t, a, e, i)
+    g.attraction()
+    out = g.step_graph_capture(pos, t, a, e, i, first_step=0, history_len=2)
+    pos.copy_(torch.from_numpy(moved.pos).cuda())
+    step, halts = 0, []
+    while step < 2:
+        g.step_graph_launch(2 - step)
+        step, h = g.step_graph_finish()
+        halts.append(h)
+    assert halts[0] & 4, halts
+    assert out["history"].cpu().numpy().tolist() == ce
+    g.close()
+
+
 def test_graph_counts_its_kernel_launches():
     w = _workload()
     pos, t, a, e, i = _state(w)
