@@ -393,12 +393,13 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                 pos += 32;
             }
             __syncwarp();
-            // S lanes per target when the round has few targets (S = 1, 2, 4, 8):
+            // S lanes per target when the round has few targets (S = 32 / nt,
+            // at most 8; TS = nt lanes per slice, the last 32 - S TS lanes idle):
             // lane = q * TS + ti takes target ti and slice q of the sources
-            const int S = nt <= 4 ? 8 : (nt <= 8 ? 4 : (nt <= 16 ? 2 : 1));
-            const int TS = 32 / S;
-            const int ti = lane & (TS - 1), q = lane / TS;
-            const bool act = ti < nt;
+            const int TS = nt <= 16 ? max(nt, 1) : 32;
+            const int S = nt <= 16 ? min(8, 32 / TS) : 1;
+            const int ti = lane % TS, q = lane / TS;
+            const bool act = ti < nt && q < S;
             const int32_t t = act ? s_tl[w][ti] : tf;
             __syncwarp();
             const float4 T = pts[t];
@@ -429,12 +430,15 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
                     }
                 }
             }
-            uint64_t tot = part, incl = part;
-            for (int o = TS; o < 32; o <<= 1) {
-                tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            // inclusive scan of the slices' sums over q (offsets TS, 2 TS, ...;
+            // a lane reads only from lanes of the same target below it), the
+            // target's total from its last slice
+            uint64_t incl = part;
+            for (int o = TS; o < S * TS; o <<= 1) {
                 const uint64_t up = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += up;
             }
+            const uint64_t tot = __shfl_sync(0xffffffffu, incl, (S - 1) * TS + ti);
             const uint64_t off = incl - part;
             const int32_t to = perm[t];
             const bool draw = act && tot != 0 && (int64_t)eoff[to] + a <= ne;
