@@ -84,37 +84,57 @@ constexpr int kLenStage = 32;    // staged sources per warp and chunk
 //   ADJOINT (L = the source leaf): per point s, for each channel T,
 //     G_T = sum_{t: T(t) = T} K (alpha_t r - beta_t)
 //     over the staged targets t (coefficients in cf), written in caller order.
-// the staged chunk [0, m) against the lane's point t, into the lane's
-// compensated running sums
-template <bool FORWARD>
-__device__ __forceinline__ void len_eval(const float4* sp, const float4* sw, int m, int32_t t,
-                                         bool inh, float tx, float ty, float tz, float rs,
-                                         float& a0, float& a1, float& a2, float& a3, float& c0,
-                                         float& c1, float& c2, float& c3) {
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-    for (int k = 0; k < m; ++k) {
-        const float4 S = sp[k];
-        const float4 SW = sw[k];
-        const float dx = tx - S.x, dy = ty - S.y, dz = tz - S.z;
-        const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float K = __float_as_int(S.w) == t ? 0.f : len_ex2(-q);
-        const float r = rs * len_sqrt(q);
+// The staged pairs [0, mp) of a chunk against the lane's point t, into the
+// lane's compensated running sums.  Staged pair j (sources 2j, 2j + 1):
+//   A = (-x0, -x1, -y0, -y1), B = (-z0, -z1, index0, index1),
+//   C = FORWARD: (w^E_0, w^E_1, w^I_0, w^I_1); ADJOINT: (alpha0, alpha1,
+//       beta0, beta1),
+//   D = ADJOINT: (I0, I1, E0, E1), the sources' channels as 0/1,
+// a padding source with zero weights; every step is a paired FP32
+// instruction over the two sources (two results, one issue slot) with the
+// per-element rounding of the scalar form.  SELF: a source may be t itself;
+// its term is zero.
+template <bool FORWARD, bool SELF>
+__device__ __forceinline__ void len_eval(const float4* sA, const float4* sB, const float4* sC,
+                                         const float4* sD, int mp, int32_t t, bool inh,
+                                         float tx, float ty, float tz, float rs, float& a0,
+                                         float& a1, float& a2, float& a3, float& c0, float& c1,
+                                         float& c2, float& c3) {
+    const float2 tx2 = make_float2(tx, tx), ty2 = make_float2(ty, ty), tz2 = make_float2(tz, tz);
+    const float2 rs2 = make_float2(rs, rs);
+    float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;
+#pragma unroll 2
+    for (int j = 0; j < mp; ++j) {
+        const float4 A = sA[j], B = sB[j], C = sC[j];
+        const float2 dx = __fadd2_rn(tx2, make_float2(A.x, A.y));
+        const float2 dy = __fadd2_rn(ty2, make_float2(A.z, A.w));
+        const float2 dz = __fadd2_rn(tz2, make_float2(B.x, B.y));
+        const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        float2 K = make_float2(len_ex2(-q.x), len_ex2(-q.y));
+        if (SELF) {
+            K.x = __float_as_int(B.z) == t ? 0.f : K.x;
+            K.y = __float_as_int(B.w) == t ? 0.f : K.y;
+        }
+        const float2 r = __fmul2_rn(rs2, make_float2(len_sqrt(q.x), len_sqrt(q.y)));
         if (FORWARD) {
-            const float wk = (inh ? SW.y : SW.x) * K;
-            p0 += wk;
-            p1 = fmaf(wk, r, p1);
-            p2 = fmaf(wk, q, p2);
-            p3 = fmaf(wk * q, r, p3);
+            const float2 wk = __fmul2_rn(inh ? make_float2(C.z, C.w) : make_float2(C.x, C.y), K);
+            p0 = __fadd2_rn(p0, wk);
+            p1 = __ffma2_rn(wk, r, p1);
+            p2 = __ffma2_rn(wk, q, p2);
+            p3 = __ffma2_rn(__fmul2_rn(wk, q), r, p3);
         } else {
-            const float v = K * fmaf(SW.x, r, -SW.y);
-            if (SW.z != 0.f) p1 += v; else p0 += v;
+            const float4 D = sD[j];
+            const float2 v = __fmul2_rn(K, __ffma2_rn(make_float2(C.x, C.y), r,
+                                                      make_float2(-C.z, -C.w)));
+            p1 = __ffma2_rn(make_float2(D.x, D.y), v, p1);
+            p0 = __ffma2_rn(make_float2(D.z, D.w), v, p0);
         }
     }
-    kahan_add(a0, c0, p0);
-    kahan_add(a1, c1, p1);
+    kahan_add(a0, c0, p0.x + p0.y);
+    kahan_add(a1, c1, p1.x + p1.y);
     if (FORWARD) {
-        kahan_add(a2, c2, p2);
-        kahan_add(a3, c3, p3);
+        kahan_add(a2, c2, p2.x + p2.y);
+        kahan_add(a3, c3, p3.x + p3.y);
     }
 }
 
@@ -127,18 +147,63 @@ k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ n
             const float4* __restrict__ gw, const float2* __restrict__ cf,
             const int32_t* __restrict__ perm, float sqk, float rs, float4* __restrict__ sums,
             float* __restrict__ gE, float* __restrict__ gI) {
-    __shared__ float4 sp_all[kLenWarps][kLenStage];   // staged point: x^, y^, z^, index (bits)
-    __shared__ float4 sw_all[kLenWarps][kLenStage];   // FORWARD: w^E, w^I; ADJOINT: alpha, beta, channel
+    __shared__ float4 sA_all[kLenWarps][kLenStage / 2], sB_all[kLenWarps][kLenStage / 2],
+        sC_all[kLenWarps][kLenStage / 2], sD_all[kLenWarps][FORWARD ? 1 : kLenStage / 2];
     __shared__ float4 red[kLenWarps][32];              // the warps' compensated sums
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* sp = sp_all[w];
-    float4* sw = sw_all[w];
+    float4* sA = sA_all[w];
+    float4* sB = sB_all[w];
+    float4* sC = sC_all[w];
+    float4* sD = sD_all[w];
+    float* fA = reinterpret_cast<float*>(sA);
+    float* fB = reinterpret_cast<float*>(sB);
+    float* fC = reinterpret_cast<float*>(sC);
+    float* fD = reinterpret_cast<float*>(sD);
     const int64_t nseg = *nseg_dev;
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
         const int32_t L = pEval[pairs[i0]];
         const int32_t lf = nfirst[L], lc = ncount[L];
         const float4 O = pts[lf];
+        // stage sources [pf + sb, pf + sb + take) at chunk positions fill..;
+        // position m of an odd chunk is padded before use
+        auto stage = [&](int32_t pf, int32_t sb, int take, int fill) {
+            if (lane < take) {
+                const int32_t j = pf + sb + lane;
+                const float4 S = pts[j];
+                const float4 SW = gw[j];
+                const int pos = fill + lane, jj = pos >> 1, h = pos & 1;
+                fA[4 * jj + h] = -(S.x - O.x) * sqk;
+                fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
+                fB[4 * jj + h] = -(S.z - O.z) * sqk;
+                fB[4 * jj + 2 + h] = __int_as_float(j);
+                if (FORWARD) {
+                    fC[4 * jj + h] = SW.x;
+                    fC[4 * jj + 2 + h] = SW.y;
+                } else {
+                    const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
+                    fC[4 * jj + h] = ab.x;
+                    fC[4 * jj + 2 + h] = ab.y;
+                    fD[4 * jj + h] = SW.w != 0.f ? 1.f : 0.f;
+                    fD[4 * jj + 2 + h] = SW.w != 0.f ? 0.f : 1.f;
+                }
+            }
+        };
+        auto pad = [&](int m) {
+            if ((m & 1) && lane == 0) {
+                const int jj = m >> 1;
+                fA[4 * jj + 1] = 0.f;
+                fA[4 * jj + 3] = 0.f;
+                fB[4 * jj + 1] = 0.f;
+                fB[4 * jj + 3] = __int_as_float(-1);
+                fC[4 * jj + 1] = 0.f;
+                fC[4 * jj + 3] = 0.f;
+                if (!FORWARD) {
+                    fD[4 * jj + 1] = 0.f;
+                    fD[4 * jj + 3] = 0.f;
+                }
+            }
+        };
         for (int32_t rb = 0; rb < lc; rb += 32) {
             const int32_t e = rb + lane;
             const bool have = e < lc;
@@ -150,43 +215,51 @@ k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ n
             const float tx = (T.x - O.x) * sqk, ty = (T.y - O.y) * sqk, tz = (T.z - O.z) * sqk;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;     // running sums
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;     // their compensations
+            // the partner leaves other than L packed into full chunks, then L
+            // itself in chunks of its own (a point skips itself)
             int fill = 0;
+            bool self = false;
             for (int32_t i = i0 + w; i < i1; i += kLenWarps) {
                 const int32_t P = pPart[pairs[i]];
+                if (P == L) {
+                    self = true;
+                    continue;
+                }
                 const int32_t pf = nfirst[P], pc = ncount[P];
                 for (int32_t sb = 0; sb < pc;) {
                     const int take = min(kLenStage - fill, pc - sb);
-                    if (lane < take) {
-                        const int32_t j = pf + sb + lane;
-                        const float4 S = pts[j];
-                        const float4 SW = gw[j];
-                        sp[fill + lane] = make_float4((S.x - O.x) * sqk, (S.y - O.y) * sqk,
-                                                      (S.z - O.z) * sqk, __int_as_float(j));
-                        if (FORWARD) {
-                            sw[fill + lane] = make_float4(SW.x, SW.y, 0.f, 0.f);
-                        } else {
-                            const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
-                            sw[fill + lane] = make_float4(ab.x, ab.y, SW.w, 0.f);
-                        }
-                    }
+                    stage(pf, sb, take, fill);
                     fill += take;
                     sb += take;
                     if (fill == kLenStage) {
                         __syncwarp();
                         if (act)
-                            len_eval<FORWARD>(sp, sw, kLenStage, t, inh, tx, ty, tz, rs, a0, a1,
-                                              a2, a3, c0, c1, c2, c3);
+                            len_eval<FORWARD, false>(sA, sB, sC, sD, kLenStage / 2, t, inh, tx,
+                                                     ty, tz, rs, a0, a1, a2, a3, c0, c1, c2, c3);
                         __syncwarp();
                         fill = 0;
                     }
                 }
             }
             if (fill > 0) {
+                pad(fill);
                 __syncwarp();
                 if (act)
-                    len_eval<FORWARD>(sp, sw, fill, t, inh, tx, ty, tz, rs, a0, a1, a2, a3, c0,
-                                      c1, c2, c3);
+                    len_eval<FORWARD, false>(sA, sB, sC, sD, (fill + 1) >> 1, t, inh, tx, ty, tz,
+                                             rs, a0, a1, a2, a3, c0, c1, c2, c3);
                 __syncwarp();
+            }
+            if (self) {
+                for (int32_t sb = 0; sb < lc; sb += kLenStage) {
+                    const int m = min(kLenStage, lc - sb);
+                    stage(lf, sb, m, 0);
+                    pad(m);
+                    __syncwarp();
+                    if (act)
+                        len_eval<FORWARD, true>(sA, sB, sC, sD, (m + 1) >> 1, t, inh, tx, ty, tz,
+                                                rs, a0, a1, a2, a3, c0, c1, c2, c3);
+                    __syncwarp();
+                }
             }
             red[w][lane] = make_float4(__fsub_rn(a0, c0), __fsub_rn(a1, c1), __fsub_rn(a2, c2),
                                        __fsub_rn(a3, c3));

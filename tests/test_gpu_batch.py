@@ -254,6 +254,57 @@ def test_per_network_plans_match_each_network_alone(precision_report):
     assert np.any(d > min(cuts))
 
 
+def test_count_rule_on_frames_matches_each_network_alone(precision_report):
+    """Algorithm 2's count rule (mac_mode 1) on networks in their frames: the
+    boxes above the cell level, which span several networks, are never
+    translated, so every network gets the pairs of its own count-rule
+    evaluation alone (its cell as the root box): the translated-pair count
+    equals the oracle's over the networks run alone, and each network's u
+    equals the same library's evaluation of that network alone.  (Against
+    the oracle the count rule's translations of adjacent boxes, far from
+    convergence at 1.3e-1 of the exact sum, amplify single- against
+    double-precision rounding to a few 1e-4; that figure is recorded.)"""
+    from oracle import oracle as O
+    b = _dyadic(W.batched_small())
+    plan = dict(PLAN, mac_mode=1, c1=70, c2=70, p=6, leaf_capacity=8)
+    local, side, level = _layout(b, **plan)
+    w = b.framed(local, side, level, **plan)
+    g = msp.MSP(w.params, frames=w.frames)
+    g.build_tree(*msp.to_device(w))
+    u = g.attraction().cpu().numpy()
+    st = g.stats()
+    g.close()
+    assert st["n_far"] > 0
+    cell = side / 2.0 ** level
+    worst_gpu = worst_orc = 0.0
+    far_orc = far_gpu = 0
+    for k in range(len(b.sigma)):
+        a, e = int(b.offsets[k]), int(b.offsets[k + 1])
+        params = W.default_params(cell, sigma=1.0, max_depth=21 - level,
+                                  **{kk: v for kk, v in plan.items()})
+        arrays = (np.ascontiguousarray(local[:, a:e]), b.type[a:e], b.vac_axon[a:e],
+                  b.vac_dend_e[a:e], b.vac_dend_i[a:e])
+        o = O.Oracle(params)
+        o.build_tree(*arrays)
+        uo = o.attraction()
+        far_orc += o.stats()["far_pairs"]
+        o.close()
+        gk = msp.MSP(params)
+        gk.build_tree(*msp.to_device(W.Workload("alone", *arrays, params)))
+        ug = gk.attraction().cpu().numpy()
+        far_gpu += gk.stats()["n_far"]
+        gk.close()
+        m = (b.vac_axon[a:e] > 0) & (ug >= 1e-6 * ug.max())
+        worst_gpu = max(worst_gpu, float(np.max(np.abs(u[a:e][m] - ug[m]) / ug[m])))
+        m = (b.vac_axon[a:e] > 0) & (uo >= 1e-6 * uo.max())
+        worst_orc = max(worst_orc, float(np.max(np.abs(u[a:e][m] - uo[m]) / uo[m])))
+    precision_report["batch_frames_count_rule_u_vs_same_path_alone"] = worst_gpu
+    precision_report["batch_frames_count_rule_u_vs_oracle_alone"] = worst_orc
+    assert far_orc == st["n_far"] and far_gpu == st["n_far"]
+    assert worst_gpu < 1e-5
+    assert worst_orc < 1e-3
+
+
 def test_frames_check_their_arguments():
     b = W.batched_small()
     local, side, level = _layout(b, **PLAN)
