@@ -551,13 +551,47 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
     }
 }
 
-// a10: attraction of a split pair = sum over its child block (double)
+// a10: attraction of a split pair = sum over its child block (double).  A
+// depth with few pairs (the shallow ones, whose pairs have the largest child
+// blocks) gives each pair a warp: lane c and c + 32 load two children and a
+// fixed butterfly adds the lanes; a depth with many pairs gives each pair a
+// thread.  Both orders are fixed, so the table is reproducible.
+constexpr int64_t kReduceWarpPairs = 8192;
+
 __global__ void k_reduce_pairs(const int64_t* __restrict__ db, const uint8_t* __restrict__ kind,
                                const int32_t* __restrict__ pcf, const uint8_t* __restrict__ pnb,
                                double2* __restrict__ pw) {
+    const int64_t q0 = db[0], nq = db[1] - db[0];
+    if (nq <= kReduceWarpPairs) {
+        const int lane = threadIdx.x & 31;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nw) {
+            const int64_t q = q0 + k;
+            const int32_t cf = pcf[q];
+            if (kind[q] != kSplit || cf < 0) continue;     // uniform across the warp
+            const int nb = pnb[q];
+            double e = 0.0, i = 0.0;
+            if (lane < nb) {
+                const double2 v = pw[cf + lane];
+                e = v.x;
+                i = v.y;
+            }
+            if (lane + 32 < nb) {
+                const double2 v = pw[cf + lane + 32];
+                e += v.x;
+                i += v.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                e += __shfl_xor_sync(0xffffffffu, e, o);
+                i += __shfl_xor_sync(0xffffffffu, i, o);
+            }
+            if (lane == 0) pw[q] = make_double2(e, i);
+        }
+        return;
+    }
     // four interleaved partial sums (children c = j mod 4), combined in a fixed
     // order: deterministic, and four independent add chains
-    const int64_t q0 = db[0], nq = db[1] - db[0];
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = q0 + k;
