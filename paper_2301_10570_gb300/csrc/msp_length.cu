@@ -16,10 +16,10 @@
 // the near-field leaf pairs of the last attraction (a plan without
 // translations: K r has no Hermite expansion), first grouped by target leaf
 // (u, v and their sigma derivatives), then by source leaf (the transposed
-// sums).  One block of 4 warps per leaf, one evaluation point per lane, the
-// warps taking the partner leaves; the partners' points are staged in shared
-// memory, and each staged chunk's sum is added with Kahan's compensated
-// summation.  Every sum has a fixed order, so
+// sums).  One block of 4 warps per leaf, 1-2 evaluation points per lane,
+// the warps taking the partner leaves; the partners' points are staged in
+// shared memory, and each staged chunk's sum is added with Kahan's
+// compensated summation.  Every sum has a fixed order, so
 // the results are reproducible; the scalar reductions run in double.
 #include <algorithm>
 #include <cmath>
@@ -84,8 +84,12 @@ constexpr int kLenStage = 32;    // staged sources per warp and chunk
 //   ADJOINT (L = the source leaf): per point s, for each channel T,
 //     G_T = sum_{t: T(t) = T} K (alpha_t r - beta_t)
 //     over the staged targets t (coefficients in cf), written in caller order.
-// The staged pairs [0, mp) of a chunk against the lane's point t, into the
-// lane's compensated running sums.  Staged pair j (sources 2j, 2j + 1):
+constexpr int kLenMaxR = 2;                 // evaluation points per lane
+constexpr int kLenList = 32 * kLenMaxR;     // evaluation points per pass
+
+// The staged pairs j = ksl, ksl + slices, ... < mp of a chunk against the
+// lane's R points t[r], into their compensated running sums acc/cmp (4 each).
+// Staged pair j (sources 2j, 2j + 1):
 //   A = (-x0, -x1, -y0, -y1), B = (-z0, -z1, index0, index1),
 //   C = FORWARD: (w^E_0, w^E_1, w^I_0, w^I_1); ADJOINT: (alpha0, alpha1,
 //       beta0, beta1),
@@ -94,52 +98,217 @@ constexpr int kLenStage = 32;    // staged sources per warp and chunk
 // instruction over the two sources (two results, one issue slot) with the
 // per-element rounding of the scalar form.  SELF: a source may be t itself;
 // its term is zero.
-template <bool FORWARD, bool SELF>
+template <bool FORWARD, bool SELF, int R>
 __device__ __forceinline__ void len_eval(const float4* sA, const float4* sB, const float4* sC,
-                                         const float4* sD, int mp, int32_t t, bool inh,
-                                         float tx, float ty, float tz, float rs, float& a0,
-                                         float& a1, float& a2, float& a3, float& c0, float& c1,
-                                         float& c2, float& c3) {
-    const float2 tx2 = make_float2(tx, tx), ty2 = make_float2(ty, ty), tz2 = make_float2(tz, tz);
+                                         const float4* sD, int mp, int ksl, int slices,
+                                         const int32_t (&t)[R], const bool (&inh)[R],
+                                         const float2 (&tx)[R], const float2 (&ty)[R],
+                                         const float2 (&tz)[R], float rs, float (&acc)[R][4],
+                                         float (&cmp)[R][4]) {
     const float2 rs2 = make_float2(rs, rs);
-    float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;
-#pragma unroll 2
-    for (int j = 0; j < mp; ++j) {
+    float2 p[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[r][c] = make_float2(0.f, 0.f);
+    for (int j = ksl; j < mp; j += slices) {
         const float4 A = sA[j], B = sB[j], C = sC[j];
-        const float2 dx = __fadd2_rn(tx2, make_float2(A.x, A.y));
-        const float2 dy = __fadd2_rn(ty2, make_float2(A.z, A.w));
-        const float2 dz = __fadd2_rn(tz2, make_float2(B.x, B.y));
-        const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-        float2 K = make_float2(len_ex2(-q.x), len_ex2(-q.y));
-        if (SELF) {
-            K.x = __float_as_int(B.z) == t ? 0.f : K.x;
-            K.y = __float_as_int(B.w) == t ? 0.f : K.y;
-        }
-        const float2 r = __fmul2_rn(rs2, make_float2(len_sqrt(q.x), len_sqrt(q.y)));
-        if (FORWARD) {
-            const float2 wk = __fmul2_rn(inh ? make_float2(C.z, C.w) : make_float2(C.x, C.y), K);
-            p0 = __fadd2_rn(p0, wk);
-            p1 = __ffma2_rn(wk, r, p1);
-            p2 = __ffma2_rn(wk, q, p2);
-            p3 = __ffma2_rn(__fmul2_rn(wk, q), r, p3);
-        } else {
-            const float4 D = sD[j];
-            const float2 v = __fmul2_rn(K, __ffma2_rn(make_float2(C.x, C.y), r,
-                                                      make_float2(-C.z, -C.w)));
-            p1 = __ffma2_rn(make_float2(D.x, D.y), v, p1);
-            p0 = __ffma2_rn(make_float2(D.z, D.w), v, p0);
+        float4 D = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!FORWARD) D = sD[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 dx = __fadd2_rn(tx[r], make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(ty[r], make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(tz[r], make_float2(B.x, B.y));
+            const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            float2 K = make_float2(len_ex2(-q.x), len_ex2(-q.y));
+            if (SELF) {
+                K.x = __float_as_int(B.z) == t[r] ? 0.f : K.x;
+                K.y = __float_as_int(B.w) == t[r] ? 0.f : K.y;
+            }
+            const float2 rr = __fmul2_rn(rs2, make_float2(len_sqrt(q.x), len_sqrt(q.y)));
+            if (FORWARD) {
+                const float2 wk =
+                    __fmul2_rn(inh[r] ? make_float2(C.z, C.w) : make_float2(C.x, C.y), K);
+                p[r][0] = __fadd2_rn(p[r][0], wk);
+                p[r][1] = __ffma2_rn(wk, rr, p[r][1]);
+                p[r][2] = __ffma2_rn(wk, q, p[r][2]);
+                p[r][3] = __ffma2_rn(__fmul2_rn(wk, q), rr, p[r][3]);
+            } else {
+                const float2 v = __fmul2_rn(K, __ffma2_rn(make_float2(C.x, C.y), rr,
+                                                          make_float2(-C.z, -C.w)));
+                p[r][1] = __ffma2_rn(make_float2(D.x, D.y), v, p[r][1]);
+                p[r][0] = __ffma2_rn(make_float2(D.z, D.w), v, p[r][0]);
+            }
         }
     }
-    kahan_add(a0, c0, p0.x + p0.y);
-    kahan_add(a1, c1, p1.x + p1.y);
-    if (FORWARD) {
-        kahan_add(a2, c2, p2.x + p2.y);
-        kahan_add(a3, c3, p3.x + p3.y);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < (FORWARD ? 4 : 2); ++c)
+            kahan_add(acc[r][c], cmp[r][c], p[r][c].x + p[r][c].y);
+}
+
+// One pass over the evaluation points plist[0, np) of leaf L (first point
+// lf, O its position) against the partner leaves of pairs [i0, i1).  A lane
+// holds R points (slots R j .. R j + R - 1 of its group j); when the groups
+// fit in fewer lanes they take npr = 2^k lanes and 32 / npr lanes share a
+// group, each walking an interleaved slice of the staged sources.  The 4
+// warps take the partner leaves round-robin, packing their points into
+// chunks of kLenStage in shared memory (L's own points last, in chunks of
+// their own); every chunk's sums join the lane's compensated running sums.
+// The slices' compensated sums are added by a fixed butterfly; the warps'
+// go to red for a fixed-order sum.
+template <bool FORWARD, int R>
+__device__ __forceinline__ void len_pass(const int32_t* plist, int np, int32_t i0, int32_t i1,
+                                         int32_t L, int32_t lf, int32_t lc, const float4& O,
+                                         const int32_t* __restrict__ pairs,
+                                         const int32_t* __restrict__ pPart,
+                                         const int32_t* __restrict__ nfirst,
+                                         const int32_t* __restrict__ ncount,
+                                         const float4* __restrict__ pts,
+                                         const float4* __restrict__ gw,
+                                         const float2* __restrict__ cf, float sqk, float rs,
+                                         float4* sA, float4* sB, float4* sC, float4* sD,
+                                         float4 (*red)[kLenList]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int lg = 0;
+    while ((1 << lg) < (np + R - 1) / R) ++lg;
+    const int npr = 1 << lg, slices = 32 >> lg;
+    const int jg = lane & (npr - 1), ksl = lane >> lg;
+    const bool active = R * jg < np;
+    int32_t t[R];
+    bool inh[R];
+    float2 tx[R], ty[R], tz[R];
+    float acc[R][4], cmp[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int slot = R * jg + r;
+        t[r] = slot < np ? plist[slot] : -1;
+        const int32_t pi = slot < np ? t[r] : plist[0];
+        const float4 T = pts[pi];
+        inh[r] = gw[pi].w != 0.f;
+        const float x = (T.x - O.x) * sqk, y = (T.y - O.y) * sqk, z = (T.z - O.z) * sqk;
+        tx[r] = make_float2(x, x);
+        ty[r] = make_float2(y, y);
+        tz[r] = make_float2(z, z);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cmp[r][c] = 0.f;
+    }
+    float* fA = reinterpret_cast<float*>(sA);
+    float* fB = reinterpret_cast<float*>(sB);
+    float* fC = reinterpret_cast<float*>(sC);
+    float* fD = reinterpret_cast<float*>(sD);
+    // stage sources [pf + sb, pf + sb + take) at chunk positions fill..;
+    // position m of an odd chunk is padded before use
+    auto stage = [&](int32_t pf, int32_t sb, int take, int fill) {
+        if (lane < take) {
+            const int32_t j = pf + sb + lane;
+            const float4 S = pts[j];
+            const float4 SW = gw[j];
+            const int pos = fill + lane, jj = pos >> 1, h = pos & 1;
+            fA[4 * jj + h] = -(S.x - O.x) * sqk;
+            fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
+            fB[4 * jj + h] = -(S.z - O.z) * sqk;
+            fB[4 * jj + 2 + h] = __int_as_float(j);
+            if (FORWARD) {
+                fC[4 * jj + h] = SW.x;
+                fC[4 * jj + 2 + h] = SW.y;
+            } else {
+                const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
+                fC[4 * jj + h] = ab.x;
+                fC[4 * jj + 2 + h] = ab.y;
+                fD[4 * jj + h] = SW.w != 0.f ? 1.f : 0.f;
+                fD[4 * jj + 2 + h] = SW.w != 0.f ? 0.f : 1.f;
+            }
+        }
+    };
+    auto pad = [&](int m) {
+        if ((m & 1) && lane == 0) {
+            const int jj = m >> 1;
+            fA[4 * jj + 1] = 0.f;
+            fA[4 * jj + 3] = 0.f;
+            fB[4 * jj + 1] = 0.f;
+            fB[4 * jj + 3] = __int_as_float(-1);
+            fC[4 * jj + 1] = 0.f;
+            fC[4 * jj + 3] = 0.f;
+            if (!FORWARD) {
+                fD[4 * jj + 1] = 0.f;
+                fD[4 * jj + 3] = 0.f;
+            }
+        }
+    };
+    int fill = 0;
+    bool self = false;
+    for (int32_t i = i0 + w; i < i1; i += kLenWarps) {
+        const int32_t P = pPart[pairs[i]];
+        if (P == L) {
+            self = true;
+            continue;
+        }
+        const int32_t pf = nfirst[P], pc = ncount[P];
+        for (int32_t sb = 0; sb < pc;) {
+            const int take = min(kLenStage - fill, pc - sb);
+            stage(pf, sb, take, fill);
+            fill += take;
+            sb += take;
+            if (fill == kLenStage) {
+                __syncwarp();
+                if (active)
+                    len_eval<FORWARD, false, R>(sA, sB, sC, sD, kLenStage / 2, ksl, slices, t,
+                                                inh, tx, ty, tz, rs, acc, cmp);
+                __syncwarp();
+                fill = 0;
+            }
+        }
+    }
+    if (fill > 0) {
+        pad(fill);
+        __syncwarp();
+        if (active)
+            len_eval<FORWARD, false, R>(sA, sB, sC, sD, (fill + 1) >> 1, ksl, slices, t, inh, tx,
+                                        ty, tz, rs, acc, cmp);
+        __syncwarp();
+    }
+    if (self) {
+        for (int32_t sb = 0; sb < lc; sb += kLenStage) {
+            const int m = min(kLenStage, lc - sb);
+            stage(lf, sb, m, 0);
+            pad(m);
+            __syncwarp();
+            if (active)
+                len_eval<FORWARD, true, R>(sA, sB, sC, sD, (m + 1) >> 1, ksl, slices, t, inh, tx,
+                                           ty, tz, rs, acc, cmp);
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            v[c] = __fsub_rn(acc[r][c], cmp[r][c]);
+            for (int o = npr; o < 32; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+        }
+        const int slot = R * jg + r;
+        if (ksl == 0 && slot < np) red[w][slot] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
+// One block of 4 warps per leaf L of a segment list.  Warp 0 lists L's
+// evaluation points (FORWARD: the targets, a_t > 0; ADJOINT: every point), up
+// to kLenList per pass, and the pass holds R = 1 or 2 of them per lane, R the
+// fewest evaluated slots per source (ties to the larger R).  Coordinates are
+// scaled by sqk = sqrt(log2 e)/sigma relative to L's first point, so that
+// q = |t^ - s^|^2 gives K = 2^-q and r = rs sqrt(q), rs = sigma/sqrt(log2 e).
+//   FORWARD (L = the target leaf): per target t with a_t > 0, the sums
+//     U = sum w K, V = sum w K r, QU = sum w K q, QV = sum w K q r
+//     (w: the staged source's weight of t's channel), written in sorted order.
+//   ADJOINT (L = the source leaf): per point s, for each channel T,
+//     G_T = sum_{t: T(t) = T} K (alpha_t r - beta_t)
+//     over the staged targets t (coefficients in cf), written in caller order.
 template <bool FORWARD>
-__global__ void __launch_bounds__(kLenWarps * 32, 8)
+__global__ void __launch_bounds__(kLenWarps * 32, 6)
 k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
             const int32_t* __restrict__ pairs, const int32_t* __restrict__ pEval,
             const int32_t* __restrict__ pPart, const int32_t* __restrict__ nfirst,
@@ -149,140 +318,97 @@ k_len_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ n
             float* __restrict__ gE, float* __restrict__ gI) {
     __shared__ float4 sA_all[kLenWarps][kLenStage / 2], sB_all[kLenWarps][kLenStage / 2],
         sC_all[kLenWarps][kLenStage / 2], sD_all[kLenWarps][FORWARD ? 1 : kLenStage / 2];
-    __shared__ float4 red[kLenWarps][32];              // the warps' compensated sums
+    __shared__ float4 red[kLenWarps][kLenList];   // the warps' compensated sums per slot
+    __shared__ int32_t plist[kLenList];
+    __shared__ int s_np, s_pos;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* sA = sA_all[w];
-    float4* sB = sB_all[w];
-    float4* sC = sC_all[w];
-    float4* sD = sD_all[w];
-    float* fA = reinterpret_cast<float*>(sA);
-    float* fB = reinterpret_cast<float*>(sB);
-    float* fC = reinterpret_cast<float*>(sC);
-    float* fD = reinterpret_cast<float*>(sD);
     const int64_t nseg = *nseg_dev;
     for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const int32_t i0 = seg_first[sg], i1 = seg_first[sg + 1];
         const int32_t L = pEval[pairs[i0]];
         const int32_t lf = nfirst[L], lc = ncount[L];
         const float4 O = pts[lf];
-        // stage sources [pf + sb, pf + sb + take) at chunk positions fill..;
-        // position m of an odd chunk is padded before use
-        auto stage = [&](int32_t pf, int32_t sb, int take, int fill) {
-            if (lane < take) {
-                const int32_t j = pf + sb + lane;
-                const float4 S = pts[j];
-                const float4 SW = gw[j];
-                const int pos = fill + lane, jj = pos >> 1, h = pos & 1;
-                fA[4 * jj + h] = -(S.x - O.x) * sqk;
-                fA[4 * jj + 2 + h] = -(S.y - O.y) * sqk;
-                fB[4 * jj + h] = -(S.z - O.z) * sqk;
-                fB[4 * jj + 2 + h] = __int_as_float(j);
-                if (FORWARD) {
-                    fC[4 * jj + h] = SW.x;
-                    fC[4 * jj + 2 + h] = SW.y;
-                } else {
-                    const float2 ab = SW.z > 0.f ? cf[j] : make_float2(0.f, 0.f);
-                    fC[4 * jj + h] = ab.x;
-                    fC[4 * jj + 2 + h] = ab.y;
-                    fD[4 * jj + h] = SW.w != 0.f ? 1.f : 0.f;
-                    fD[4 * jj + 2 + h] = SW.w != 0.f ? 0.f : 1.f;
+        int32_t pos = 0;
+        for (;;) {
+            if (w == 0) {
+                // the next (at most) kLenList evaluation points from pos on
+                int np = 0;
+                int32_t p = pos;
+                while (p < lc && np < kLenList) {
+                    const int32_t idx = p + lane;
+                    bool ok = idx < lc;
+                    if (FORWARD && ok) ok = gw[lf + idx].z > 0.f;
+                    const unsigned mk = __ballot_sync(0xffffffffu, ok);
+                    const int room = kLenList - np;
+                    const int rank = __popc(mk & ((1u << lane) - 1u));
+                    if (ok && rank < room) plist[np + rank] = lf + idx;
+                    if (__popc(mk) > room) {
+                        // the room-th point ends the pass: resume after it
+                        unsigned keep = mk;
+                        for (int k = 0; k < room; ++k) keep &= keep - 1u;
+                        p += __ffs(keep) - 1;
+                        np = kLenList;
+                        break;
+                    }
+                    np += __popc(mk);
+                    p += 32;
+                }
+                if (lane == 0) {
+                    s_np = np;
+                    s_pos = min(p, lc);
                 }
             }
-        };
-        auto pad = [&](int m) {
-            if ((m & 1) && lane == 0) {
-                const int jj = m >> 1;
-                fA[4 * jj + 1] = 0.f;
-                fA[4 * jj + 3] = 0.f;
-                fB[4 * jj + 1] = 0.f;
-                fB[4 * jj + 3] = __int_as_float(-1);
-                fC[4 * jj + 1] = 0.f;
-                fC[4 * jj + 3] = 0.f;
-                if (!FORWARD) {
-                    fD[4 * jj + 1] = 0.f;
-                    fD[4 * jj + 3] = 0.f;
+            __syncthreads();
+            const int np = s_np;
+            pos = s_pos;
+            __syncthreads();
+            if (np == 0) break;
+            int R = 1, best = 1 << 30;
+            for (int rr = 1; rr <= kLenMaxR; ++rr) {
+                const int g = (np + rr - 1) / rr;
+                if (g > 32) continue;
+                int npr = 1;
+                while (npr < g) npr <<= 1;
+                if (npr * rr <= best) {
+                    best = npr * rr;
+                    R = rr;
                 }
             }
-        };
-        for (int32_t rb = 0; rb < lc; rb += 32) {
-            const int32_t e = rb + lane;
-            const bool have = e < lc;
-            const int32_t t = lf + (have ? e : 0);
-            const float4 T = pts[t];
-            const float4 TW = gw[t];
-            const bool act = have && (FORWARD ? TW.z > 0.f : true);
-            const bool inh = TW.w != 0.f;
-            const float tx = (T.x - O.x) * sqk, ty = (T.y - O.y) * sqk, tz = (T.z - O.z) * sqk;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;     // running sums
-            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;     // their compensations
-            // the partner leaves other than L packed into full chunks, then L
-            // itself in chunks of its own (a point skips itself)
-            int fill = 0;
-            bool self = false;
-            for (int32_t i = i0 + w; i < i1; i += kLenWarps) {
-                const int32_t P = pPart[pairs[i]];
-                if (P == L) {
-                    self = true;
-                    continue;
-                }
-                const int32_t pf = nfirst[P], pc = ncount[P];
-                for (int32_t sb = 0; sb < pc;) {
-                    const int take = min(kLenStage - fill, pc - sb);
-                    stage(pf, sb, take, fill);
-                    fill += take;
-                    sb += take;
-                    if (fill == kLenStage) {
-                        __syncwarp();
-                        if (act)
-                            len_eval<FORWARD, false>(sA, sB, sC, sD, kLenStage / 2, t, inh, tx,
-                                                     ty, tz, rs, a0, a1, a2, a3, c0, c1, c2, c3);
-                        __syncwarp();
-                        fill = 0;
+            if (R == 1)
+                len_pass<FORWARD, 1>(plist, np, i0, i1, L, lf, lc, O, pairs, pPart, nfirst,
+                                     ncount, pts, gw, cf, sqk, rs, sA_all[w], sB_all[w],
+                                     sC_all[w], sD_all[w], red);
+            else
+                len_pass<FORWARD, 2>(plist, np, i0, i1, L, lf, lc, O, pairs, pPart, nfirst,
+                                     ncount, pts, gw, cf, sqk, rs, sA_all[w], sB_all[w],
+                                     sC_all[w], sD_all[w], red);
+            __syncthreads();
+            if (w == 0) {
+#pragma unroll
+                for (int rr = 0; rr < kLenMaxR; ++rr) {
+                    const int j = lane + 32 * rr;
+                    if (j >= np) continue;
+                    float4 v = red[0][j];
+#pragma unroll
+                    for (int k = 1; k < kLenWarps; ++k) {
+                        const float4 x = red[k][j];
+                        v.x += x.x;
+                        v.y += x.y;
+                        v.z += x.z;
+                        v.w += x.w;
+                    }
+                    const int32_t t = plist[j];
+                    if (FORWARD) {
+                        sums[t] = v;
+                    } else {
+                        const int32_t o = perm[t];
+                        if (gE) gE[o] = v.x;
+                        if (gI) gI[o] = v.y;
                     }
                 }
             }
-            if (fill > 0) {
-                pad(fill);
-                __syncwarp();
-                if (act)
-                    len_eval<FORWARD, false>(sA, sB, sC, sD, (fill + 1) >> 1, t, inh, tx, ty, tz,
-                                             rs, a0, a1, a2, a3, c0, c1, c2, c3);
-                __syncwarp();
-            }
-            if (self) {
-                for (int32_t sb = 0; sb < lc; sb += kLenStage) {
-                    const int m = min(kLenStage, lc - sb);
-                    stage(lf, sb, m, 0);
-                    pad(m);
-                    __syncwarp();
-                    if (act)
-                        len_eval<FORWARD, true>(sA, sB, sC, sD, (m + 1) >> 1, t, inh, tx, ty, tz,
-                                                rs, a0, a1, a2, a3, c0, c1, c2, c3);
-                    __syncwarp();
-                }
-            }
-            red[w][lane] = make_float4(__fsub_rn(a0, c0), __fsub_rn(a1, c1), __fsub_rn(a2, c2),
-                                       __fsub_rn(a3, c3));
             __syncthreads();
-            if (w == 0 && act) {
-                float4 v = red[0][lane];
-#pragma unroll
-                for (int k = 1; k < kLenWarps; ++k) {
-                    const float4 x = red[k][lane];
-                    v.x += x.x;
-                    v.y += x.y;
-                    v.z += x.z;
-                    v.w += x.w;
-                }
-                if (FORWARD) {
-                    sums[t] = v;
-                } else {
-                    const int32_t o = perm[t];
-                    if (gE) gE[o] = v.x;
-                    if (gI) gI[o] = v.y;
-                }
-            }
-            __syncthreads();
+            if (pos >= lc) break;
         }
     }
 }
