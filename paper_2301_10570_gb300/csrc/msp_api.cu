@@ -429,6 +429,7 @@ msp_status msp_set_sigma(msp_ctx* c, double sigma) {
         derive(*c);
         // the pair lists and every captured graph hold the old width
         c->attraction_done = false;
+        c->lists_valid = false;
         msp::graph_release(*c);
     });
 }
@@ -486,6 +487,7 @@ msp_status msp_set_frames(msp_ctx* c, int64_t n_networks, const int64_t* offsets
         // the octree, the pair lists and every captured graph hold the old frames
         c->tree_built = false;
         c->attraction_done = false;
+        c->lists_valid = false;
         msp::graph_release(*c);
     });
 }

@@ -776,8 +776,21 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     // replays of the step graph that reuse the octree keep the traversal and
     // its lists too: the cutoff rule depends on the positions only (the count
     // rule of Algorithm 2 depends on the vacant counts and is redone)
-    const bool reuse_lists = c.graph_mode && !c.graph_full_build && cfg.mac_mode == 0;
     if (c.pair_cap <= 0) c.pair_cap = std::max<int64_t>(64 * c.n_nodes, 1 << 16);
+    // an eager attraction on a reused octree keeps the lists of the last one,
+    // provided no buffer that holds them is about to grow (which would lose
+    // them)
+    auto holds = [&](const DBuf& b, size_t elem) {
+        return b.bytes >= (size_t)c.pair_cap * elem;
+    };
+    const bool lists_fit = holds(c.pr_X, 4) && holds(c.pr_Y, 4) && holds(c.pr_kind, 1) &&
+                           holds(c.pr_cf, 4) && holds(c.pr_nb, 1) && holds(c.pr_w, 16) &&
+                           holds(c.p2p_val0, 4) && holds(c.far_q, 4) && holds(c.nf_src, 8) &&
+                           holds(c.nf_w32, 8) &&
+                           (c.exp_nodes == 0 || (holds(c.m2_key0, 8) && holds(c.m2_val0, 4)));
+    const bool reuse_lists =
+        cfg.mac_mode == 0 && ((c.graph_mode && !c.graph_full_build) ||
+                              (!c.graph_mode && c.tree_reused && c.lists_valid && lists_fit));
     const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
     for (int attempt = 0;; ++attempt) {
     const int64_t cap = c.pair_cap;
@@ -965,6 +978,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     break;
     }
     c.attraction_done = true;
+    c.lists_valid = cfg.mac_mode == 0;
 }
 
 void direct(msp_ctx& c, float* u_dev, cudaStream_t s) {

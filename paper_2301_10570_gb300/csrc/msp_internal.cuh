@@ -174,6 +174,11 @@ struct msp_ctx {
     int64_t exp_first = 0, exp_nodes = 0;
     int64_t n_p2p_targets = 0;
     bool tree_built = false, attraction_done = false;
+    // eager calls on fixed positions: the last build reused the octree of the
+    // one before (same positions), and the interaction lists of the last
+    // attraction belong to that octree (distance rule: they depend on the
+    // positions and the kernel width only)
+    bool tree_reused = false, lists_valid = false;
     // independent networks in local frames (msp_set_frames): network k holds
     // the caller's neurons [frame_off[k], frame_off[k+1]) with positions
     // relative to its own cell of the grid at level frame_level (0: one frame)

@@ -372,9 +372,12 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
                 const uint8_t* type, const uint8_t* va, const uint8_t* vde, const uint8_t* vdi,
                 cudaStream_t s) {
     NvtxRange nv_("msp build_tree");
+    const bool was_built = c.tree_built;
+    const int64_t prev_n = c.n;
     if (!c.graph_mode) {
         c.tree_built = false;
         c.attraction_done = false;
+        c.tree_reused = false;
     }
     c.n = n;
     const msp_config& cfg = c.cfg;
@@ -407,13 +410,31 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         MSP_LAUNCH("pos_sum");
     }
 
+    // An eager build on the positions of the last build (their checksum,
+    // read back: one more synchronisation) keeps its sorted order and octree,
+    // which depend on the positions only.
+    bool eager_reuse = false;
+    if (!c.graph_mode && was_built && n == prev_n && n > 0) {
+        unsigned long long ps = 0;
+        MSP_CUDA(cudaMemcpyAsync(&ps, &dc->pos_sum, sizeof(ps), cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        eager_reuse = ps == c.pos_sum_ref;
+    }
+    if (!eager_reuse && !c.graph_mode) c.lists_valid = false;
+
     // Inside the whole-step graph the positions are those of the last eager
     // build (checked: a different checksum halts the graph), so its sorted
     // order and octree are reused; the counts are gathered again and the
-    // aggregates recomputed.
-    if (c.graph_mode && c.tree_built && !c.graph_full_build) {
-        k_pos_check<<<1, 1, 0, s>>>(dc, c.pos_sum_ref, c.tree_gen);
-        MSP_LAUNCH("pos_check");
+    // aggregates recomputed.  The same for an eager build on those positions.
+    if ((c.graph_mode && c.tree_built && !c.graph_full_build) || eager_reuse) {
+        if (c.graph_mode) {
+            k_pos_check<<<1, 1, 0, s>>>(dc, c.pos_sum_ref, c.tree_gen);
+            MSP_LAUNCH("pos_check");
+        } else {
+            // the octree arrays are those of generation tree_gen (a graph
+            // replay that rebuilt them for the same positions left its mark)
+            dev_set(reinterpret_cast<int64_t*>(&dc->tree_gen), (int64_t)c.tree_gen, s);
+        }
         if (n > 0) {
             k_gather<<<G, B, 0, s>>>(v0, n, x, y, z, type, va, vde, vdi, perm, inv, pts, wts, lw);
             MSP_LAUNCH("gather");
@@ -433,6 +454,12 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
                 c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(),
                 c.nd_sums.get<int4>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), leaf_of);
             MSP_LAUNCH("aggregate");
+        }
+        if (eager_reuse) {
+            pull_counts(c, s);          // the one synchronisation of the build
+            c.n_elem = c.hcount->n_elem;
+            c.tree_built = true;
+            c.tree_reused = true;
         }
         return;
     }
