@@ -153,8 +153,11 @@ msp_status msp_destroy(msp_ctx *ctx);
  *   vac_axon_dev         n bytes, vacant axonal elements of the neuron's type
  *   vac_dend_e_dev/_i    n bytes, vacant dendritic elements per channel
  * The inputs are read during the call's stream work only; the context keeps
- * its own sorted copy.  Synchronous (the per-level node counts are read
- * back).  n may be 0.  Errors: MSP_ERR_INVALID_ARG (n < 0, n > 2^31-2, null
+ * its own sorted copy.  The octree depends on the positions only: when n and
+ * the positions equal those of the context's last build (a checksum of every
+ * coordinate's bits, read back: one more synchronisation), the sorted order
+ * and the octree are kept and only the counts and aggregates are refreshed.
+ * Synchronous (the per-level node counts are read back).  n may be 0.  Errors: MSP_ERR_INVALID_ARG (n < 0, n > 2^31-2, null
  * pointer with n > 0, a position outside [origin, origin + side) or not
  * finite: the boxes of the tree must contain their points), MSP_ERR_OOM
  * (including the workspace limit of msp_set_workspace_limit). */
@@ -170,6 +173,10 @@ msp_status msp_build_tree(msp_ctx *ctx, int64_t n, const float *x_dev, const flo
  * exact near field (Eq. 8), and the box-pair attraction table.
  *   u_dev   n floats out: u(t) of the neuron's own channel if vac_axon > 0,
  *           else 0.  May be NULL (only the pair table is produced).
+ * The traversal prunes by the cutoff only (mac_mode 0), so its interaction
+ * lists depend on the positions and the kernel width alone: after a build
+ * that kept the octree, the lists of the last attraction are kept as well
+ * (the counts, expansions, near field and pair table are recomputed).
  * Requires msp_build_tree.  Synchronous (per-depth pair counts are read
  * back).  Errors: MSP_ERR_NOT_BUILT, MSP_ERR_OOM, MSP_ERR_CAPACITY. */
 msp_status msp_attraction(msp_ctx *ctx, float *u_dev, void *stream);
