@@ -835,7 +835,7 @@ def fmm_translated_record(w, dev, idx, ref, reps=3):
             "error_vs_fp64": rep, "meets_1e-4": rep["max_rel_err"] <= 1e-4}
 
 
-def batched_record(dev, steps, warmup):
+def batched_record(dev, steps, warmup, fp64=True):
     """The 256-network batch as one graph-replayed step (msp_batch_layout and
     msp_set_frames, then the ordinary path): a few timed replays; and the
     attraction of 8 sampled networks, 512 sampled targets each, against the
@@ -854,7 +854,8 @@ def batched_record(dev, steps, warmup):
     b = W.batched_256()
     errs = []
     rng = np.random.default_rng(1)
-    for k in sorted(rng.choice(len(b.sigma), 8, replace=False).tolist()):
+    # the FP64 checks run the oracle on the host cores: part of the CPU leg
+    for k in (sorted(rng.choice(len(b.sigma), 8, replace=False).tolist()) if fp64 else []):
         wk = b.network(k, **tuned_params())
         idx = np.sort(rng.choice(wk.n, min(512, wk.n), replace=False))
         ref = fp64_reference(wk, idx)
@@ -870,7 +871,7 @@ def batched_record(dev, steps, warmup):
     return {"workload": BATCH_DESC, "neurons": n, "steps": steps,
             "ms_per_step": round(ms, 3), "neurons_per_s": n / (ms / 1e3),
             "graph_halted": int(halted),
-            "max_rel_err_sampled_networks_vs_own_fp64": max(errs),
+            "max_rel_err_sampled_networks_vs_own_fp64": max(errs) if errs else None,
             "plan_chooser": batch_tuning_summary(),
             "accuracy_note": "8 sampled networks x 512 sampled targets, each network against "
                              "the FP64 brute force of that network alone at its own width on "
@@ -927,7 +928,7 @@ def _timed_attraction(g, flush, reps):
     return statistics.median(ts), u
 
 
-def uniform_records(dev, reps=3):
+def uniform_records(dev, reps=3, fp64=True):
     """The two uniform workloads: 4,096 neurons in a 10,000 um cube (p = 4,
     leaf capacity 32: a whole eager step, launch-bound; u against the oracle's
     FP64 brute force on every target) and 262,144 neurons at the same density
@@ -947,7 +948,8 @@ def uniform_records(dev, reps=3):
     d = msp.to_device(w, dev)
     g.build_tree(*d)
     u4 = g.attraction().cpu().numpy()
-    ref4 = fp64_reference(w, np.arange(w.n))
+    # the FP64 checks run the oracle on the host cores: part of the CPU leg
+    ref4 = fp64_reference(w, np.arange(w.n)) if fp64 else None
     ts = []
     for k in range(reps + 2):
         flush.zero_()
@@ -963,12 +965,12 @@ def uniform_records(dev, reps=3):
     out["uniform_4k"] = {"what": "eager step (tree, attraction, selection), p = 4, leaf capacity 32",
                          "ms_per_step": round(statistics.median(ts[2:]), 3),
                          "neurons_per_s": w.n / (statistics.median(ts[2:]) / 1e3),
-                         "error_vs_fp64_all_targets": error_report(u4, ref4)}
+                         "error_vs_fp64_all_targets": error_report(u4, ref4) if fp64 else None}
     rows = []
     ref = None
     w0 = W.uniform_256k()
     idx = np.sort(np.random.default_rng(0).choice(w0.n, FP64_SAMPLE, replace=False))
-    ref64 = fp64_reference(w0, idx)
+    ref64 = fp64_reference(w0, idx) if fp64 else None
     chosen, _ = autotune.tune(w0, device=dev.index, candidates=dict(
         leaf_capacity=(16, 32, 64, 128), cutoff=(3.25, 3.5, 4.0),
         expansions=((0.0, 4, 0), (0.5, 4, 0), (0.5, 6, 0))), reps=3)
@@ -994,7 +996,8 @@ def uniform_records(dev, reps=3):
                      "near_field_pairs": st["n_p2p"],
                      "max_rel_err_vs_direct_fp32": rep["max_rel_err"],
                      "l2_rel_err": rep["l2_rel_err"],
-                     "max_rel_err_vs_fp64_sampled": error_report(un[idx], ref64)["max_rel_err"]})
+                     "max_rel_err_vs_fp64_sampled":
+                         error_report(un[idx], ref64)["max_rel_err"] if fp64 else None})
     out["uniform_256k"] = rows
     return out
 
@@ -1275,10 +1278,10 @@ def main():
         if not args.no_extras:
             if idx is not None:
                 out["fmm_translated"] = fmm_translated_record(w, dev, idx, ref)
-            out["batched_256"] = batched_record(dev, 3, 2)
+            out["batched_256"] = batched_record(dev, 3, 2, fp64=not args.no_cpu_baseline)
             out["gradient_262k"] = gradient_record(dev, 3, 2)
             out["simulation_1m"] = simulation_record(3, 2)
-            out.update(uniform_records(dev))
+            out.update(uniform_records(dev, fp64=not args.no_cpu_baseline))
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         # the oracle has no frames: the batch's networks in one common frame
         out["cpu_baseline"] = cpu_baseline(batched_workload(dev, common_frame=True)
