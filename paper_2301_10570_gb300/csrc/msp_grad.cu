@@ -327,7 +327,7 @@ __device__ __forceinline__ void gr_pass(const int32_t* plist, int np, int32_t i0
 //            gE += w0 2^-q, gI += w1 2^-q.
 // Points that are not evaluated keep the zero the caller wrote.
 template <bool FORWARD>
-__global__ void __launch_bounds__(kGrWarps * 32, 6)
+__global__ void __launch_bounds__(kGrWarps * 32, 7)
 k_grad_pairs(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nseg_dev,
              const int32_t* __restrict__ order, const int32_t* __restrict__ pairs,
              const int32_t* __restrict__ pEval, const int32_t* __restrict__ pPart,
