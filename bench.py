@@ -698,7 +698,13 @@ def run_ours(args, rank, world):
         d2h.append(8 + 4 * n + 4 * ne0 + 9 * int(hout["n_syn"][0]))
     e2e = replicas.aggregate_throughput(n, 1e3 * sum(e2e_t) / len(e2e_t), dev)
 
-    # the attraction of the unwalked inputs (accuracy checks below)
+    # the attraction at the vacancy state the timed replays walked to, and of
+    # the unwalked inputs (accuracy checks below)
+    from paper_2301_10570_gb300 import workloads as W
+    g.build_tree(pos, typ, va, ve, vi)
+    uw = g.attraction().cpu().numpy()
+    walked = (W.Workload(w.name + "_walked", w.pos, w.type, va.cpu().numpy(), ve.cpu().numpy(),
+                         vi.cpu().numpy(), dict(w.params)), uw)
     g.build_tree(pos, typ, va0, ve0, vi0)
     uf = g.attraction()
     torch.cuda.synchronize()
@@ -786,7 +792,7 @@ def run_ours(args, rank, world):
            "roofline": roofline}
     if full:
         out["full_rebuild_step"] = full
-    return out, w, uf_np, ud_np
+    return out, w, uf_np, ud_np, walked
 
 
 def accuracy_fp64(w, uf, ud, sample=FP64_SAMPLE):
@@ -1268,12 +1274,18 @@ def main():
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
         return
-    out, w, uf, ud = run_ours(args, rank, world)
+    out, w, uf, ud, walked = run_ours(args, rank, world)
     dev = torch.device("cuda", torch.cuda.current_device())
     if rank == 0 and world == 1 and args.workload == "clustered_1m":
         idx = ref = None
         if not args.no_cpu_baseline:
             acc, idx, ref = accuracy_fp64(w, uf, ud)
+            # the same targets at the vacancy state of the walked replays
+            ww, uw = walked
+            acc["walked_state"] = {
+                "after": "the warm-up, the timed graph replays and the eager steps, every "
+                         "step with the vacancy walk and the commit of its synapses",
+                "plan": error_report(uw[idx], fp64_reference(ww, idx))}
             out["accuracy_vs_fp64"] = acc
         if not args.no_extras:
             if idx is not None:
