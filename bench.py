@@ -968,7 +968,9 @@ def uniform_records(dev, reps=3, fp64=True):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     g.close()
-    out["uniform_4k"] = {"what": "eager step (tree, attraction, selection), p = 4, leaf capacity 32",
+    out["uniform_4k"] = {"what": "eager step (tree, attraction, selection), p = 4, leaf capacity 32; "
+                                 "the positions are fixed, so each build keeps the octree and each "
+                                 "attraction the lists (counts, aggregates and sums refreshed)",
                          "ms_per_step": round(statistics.median(ts[2:]), 3),
                          "neurons_per_s": w.n / (statistics.median(ts[2:]) / 1e3),
                          "error_vs_fp64_all_targets": error_report(u4, ref4) if fp64 else None}
