@@ -183,7 +183,7 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->wts, &c->lw, &c->elem_off, &c->leaf_of, &c->nd_level, &c->nd_prefix,
                          &c->nd_first, &c->nd_count, &c->nd_parent, &c->nd_child_first,
                          &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
-                         &c->pr_kind, &c->pr_cf, &c->pr_nb, &c->pr_w, &c->far_q, &c->m2_key0,
+                         &c->pr_kind, &c->pr_cf, &c->pr_nb, &c->pr_w, &c->far_q, &c->split_q, &c->m2_key0,
                          &c->m2_key1, &c->m2_val0, &c->m2_val1, &c->m2_flag, &c->m2_off,
                          &c->m2_seg, &c->p2p_key0,
                          &c->p2p_key1, &c->p2p_val0, &c->p2p_val1, &c->seg_first, &c->seg_flag,

@@ -551,70 +551,51 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
     }
 }
 
-// a10: attraction of a split pair = sum over its child block (double).  A
-// depth with few pairs (the shallow ones, whose pairs have the largest child
-// blocks) gives each pair a warp: lane c and c + 32 load two children and a
-// fixed butterfly adds the lanes; a depth with many pairs gives each pair a
-// thread.  Both orders are fixed, so the table is reproducible.
-constexpr int64_t kReduceWarpPairs = 8192;
-
-__global__ void k_reduce_pairs(const int64_t* __restrict__ db, const uint8_t* __restrict__ kind,
+// a10: attraction of a split pair = sum over its child block (double).  The
+// split pairs of each depth are listed once per traversal (the list keeps
+// pair order); 8 lanes take one split pair, lane c summing children c, c + 8,
+// ... (coalesced: 8 consecutive 16-byte entries per step), then a fixed
+// butterfly over the 8 lanes.  Both orders are fixed, so the table is
+// reproducible.  sb = [first, end) of the depth's entries in split_q.
+__global__ void k_reduce_split(const int64_t* __restrict__ sb, const int32_t* __restrict__ split_q,
                                const int32_t* __restrict__ pcf, const uint8_t* __restrict__ pnb,
                                double2* __restrict__ pw) {
-    const int64_t q0 = db[0], nq = db[1] - db[0];
-    if (nq <= kReduceWarpPairs) {
-        const int lane = threadIdx.x & 31;
-        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nw) {
-            const int64_t q = q0 + k;
-            const int32_t cf = pcf[q];
-            if (kind[q] != kSplit || cf < 0) continue;     // uniform across the warp
-            const int nb = pnb[q];
-            double e = 0.0, i = 0.0;
-            if (lane < nb) {
-                const double2 v = pw[cf + lane];
-                e = v.x;
-                i = v.y;
-            }
-            if (lane + 32 < nb) {
-                const double2 v = pw[cf + lane + 32];
-                e += v.x;
-                i += v.y;
-            }
+    const int64_t s0 = sb[0], ns = sb[1] - sb[0];
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the loop bound is uniform across the warp (its 4 groups shuffle together)
+    for (int64_t k0 = 4 * warp; k0 < ns; k0 += 4 * nwarp) {
+        const int64_t k = k0 + (lane >> 3);
+        int32_t q = -1, cf = -1;
+        int nb = 0;
+        if (k < ns) {
+            q = split_q[s0 + k];
+            cf = pcf[q];
+            nb = cf >= 0 ? (int)pnb[q] : 0;     // cf < 0: children not stored (overflow)
+        }
+        double e = 0.0, i = 0.0;
+        for (int c = sub; c < nb; c += 8) {
+            const double2 v = pw[cf + c];
+            e += v.x;
+            i += v.y;
+        }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                e += __shfl_xor_sync(0xffffffffu, e, o);
-                i += __shfl_xor_sync(0xffffffffu, i, o);
-            }
-            if (lane == 0) pw[q] = make_double2(e, i);
+        for (int o = 4; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            i += __shfl_xor_sync(0xffffffffu, i, o);
         }
-        return;
+        if (sub == 0 && cf >= 0) pw[q] = make_double2(e, i);
     }
-    // four interleaved partial sums (children c = j mod 4), combined in a fixed
-    // order: deterministic, and four independent add chains
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = q0 + k;
-        const int32_t cf = pcf[q];
-        if (kind[q] != kSplit || cf < 0) continue;     // cf < 0: children not stored (overflow)
-        const int nb = pnb[q];
-        double e[4] = {0.0, 0.0, 0.0, 0.0}, i[4] = {0.0, 0.0, 0.0, 0.0};
-        int c = 0;
-        for (; c + 3 < nb; c += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                double2 v = pw[cf + c + u];
-                e[u] += v.x;
-                i[u] += v.y;
-            }
-        }
-        for (; c < nb; ++c) {
-            double2 v = pw[cf + c];
-            e[c & 3] += v.x;
-            i[c & 3] += v.y;
-        }
-        pw[q] = make_double2((e[0] + e[1]) + (e[2] + e[3]), (i[0] + i[1]) + (i[2] + i[3]));
-    }
+}
+
+// the split pairs' range of every depth d <= D in split_q: the exclusive scan
+// of the split flags at the depth's first pair
+__global__ void k_split_starts(DevCounts* dc, const int32_t* __restrict__ off, int D) {
+    const int d = threadIdx.x;
+    if (d > D) return;
+    const int64_t q = dc->depth_start[d], n = dc->depth_start[D];
+    dc->split_start[d] = q < n ? (int64_t)off[q] : dc->n_split;
 }
 
 __global__ void k_scatter_u(const float* __restrict__ us, const int32_t* __restrict__ perm,
@@ -785,7 +766,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     };
     const bool lists_fit = holds(c.pr_X, 4) && holds(c.pr_Y, 4) && holds(c.pr_kind, 1) &&
                            holds(c.pr_cf, 4) && holds(c.pr_nb, 1) && holds(c.pr_w, 16) &&
-                           holds(c.p2p_val0, 4) && holds(c.far_q, 4) && holds(c.nf_src, 8) &&
+                           holds(c.p2p_val0, 4) && holds(c.far_q, 4) && holds(c.split_q, 4) &&
+                           holds(c.nf_src, 8) &&
                            holds(c.nf_w32, 8) &&
                            (c.exp_nodes == 0 || (holds(c.m2_key0, 8) && holds(c.m2_val0, 4)));
     const bool reuse_lists =
@@ -806,6 +788,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     uint8_t* kind = c.pr_kind.get<uint8_t>();
 
     int32_t* far_q = c.far_q.ensure<int32_t>((size_t)cap);
+    int32_t* split_q = c.split_q.ensure<int32_t>((size_t)cap);
     int32_t* pv0 = c.p2p_val0.ensure<int32_t>((size_t)cap);
     int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)c.n_nodes + 2);
     const int64_t* n_pairs_dev = &dc->depth_start[D];
@@ -834,6 +817,14 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
 
     // far and near-field lists
     int32_t* flag = cnt;
+    k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kSplit, flag);
+    MSP_LAUNCH("flag_split");
+    scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_split, nullptr, s);
+    k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kSplit, off, c.pr_X.get<int32_t>(),
+                                    split_q, nullptr);
+    MSP_LAUNCH("compact_split");
+    k_split_starts<<<1, 32, 0, s>>>(dc, off, D);
+    MSP_LAUNCH("split_starts");
     k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kFar, flag);
     MSP_LAUNCH("flag_far");
     scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_far, nullptr, s);
@@ -943,9 +934,9 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     c.nf_timed = n > 0;
     // a10: pair table, deepest pairs first
     for (int dd = D - 1; dd >= 0; --dd) {
-        k_reduce_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[dd], kind, c.pr_cf.get<int32_t>(),
+        k_reduce_split<<<Gt, B, 0, s>>>(&dc->split_start[dd], split_q, c.pr_cf.get<int32_t>(),
                                         c.pr_nb.get<uint8_t>(), c.pr_w.get<double2>());
-        MSP_LAUNCH("reduce_pairs");
+        MSP_LAUNCH("reduce_split");
     }
     if (u_dev && n > 0) {
         k_scatter_u<<<grid_for(n, B, (int64_t)c.sm_count * 16), B, 0, s>>>(

@@ -135,6 +135,8 @@ struct DevCounts {
     uint64_t pos_sum;                        // checksum of the positions of the last build
     uint64_t tree_gen;                       // generation stamp of the last eager build
     int64_t m2l_n, m2l_nseg;                 // far pairs translated pair by pair, their targets
+    int64_t n_split;                         // split pairs of the last traversal
+    int64_t split_start[kMaxLevels + 3];     // depth d split pairs: split_q[split_start[d], [d+1])
 };
 
 // DevCounts::overflow bit set when a bounded wait of the single-pass scan
@@ -202,6 +204,7 @@ struct msp_ctx {
     // lists
     msp::DBuf m2_key0, m2_key1, m2_val0, m2_val1, m2_flag, m2_off, m2_seg;   // far pairs by X
     msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
+    msp::DBuf split_q;                                   // split pairs, by depth
     msp::DBuf nf_okey0, nf_okey1, nf_oval0, nf_oval1;   // near-field segment order
     msp::DBuf nf_src;                                    // per near-field pair: (first, count) of Y
     // neuron side (msp_neuron.cu): input counts, bound synapses, excess, group
