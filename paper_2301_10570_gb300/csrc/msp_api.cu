@@ -182,7 +182,7 @@ msp_status msp_destroy(msp_ctx* c) {
     msp::DBuf* bufs[] = {&c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->perm, &c->inv, &c->pts,
                          &c->wts, &c->lw, &c->elem_off, &c->leaf_of, &c->nd_level, &c->nd_prefix,
                          &c->nd_first, &c->nd_count, &c->nd_parent, &c->nd_child_first,
-                         &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->pr_X, &c->pr_Y,
+                         &c->nd_nchild, &c->nd_sums, &c->nd_ca, &c->nd_cd, &c->nd_arrive, &c->pr_X, &c->pr_Y,
                          &c->pr_kind, &c->pr_cf, &c->pr_nb, &c->pr_w, &c->far_q, &c->split_q, &c->m2_key0,
                          &c->m2_key1, &c->m2_val0, &c->m2_val1, &c->m2_flag, &c->m2_off,
                          &c->m2_seg, &c->p2p_key0,
@@ -595,11 +595,12 @@ msp_status msp_export_pairs(msp_ctx* c, int32_t* X, int32_t* Y, uint8_t* kind,
         cp(kind, c->pr_kind.p, m);
         cp(child_first, c->pr_cf.p, m * 4);
         if ((w_e || w_i) && m) {
-            std::vector<double> w(2 * m);
+            // the table's double-FP32 values (hi, lo per channel), summed in double
+            std::vector<float> w(4 * m);
             cp(w.data(), c->pr_w.p, m * 16);
             for (size_t i = 0; i < m; ++i) {
-                if (w_e) w_e[i] = w[2 * i];
-                if (w_i) w_i[i] = w[2 * i + 1];
+                if (w_e) w_e[i] = (double)w[4 * i] + (double)w[4 * i + 1];
+                if (w_i) w_i[i] = (double)w[4 * i + 2] + (double)w[4 * i + 3];
             }
         }
         if (depth_start)

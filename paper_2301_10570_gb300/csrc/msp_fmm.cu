@@ -142,14 +142,14 @@ __global__ void k_emit_pairs(const int64_t* __restrict__ db, NodeView nv,
                              const uint8_t* __restrict__ kind, const int32_t* __restrict__ off,
                              int32_t* __restrict__ pX, int32_t* __restrict__ pY,
                              int32_t* __restrict__ pcf, uint8_t* __restrict__ pnb,
-                             double2* __restrict__ pw, int64_t cap,
+                             float4* __restrict__ pw, int64_t cap,
                              const int64_t* __restrict__ overflow) {
     const int64_t q0 = db[0], nq = db[1] - db[0], next0 = db[1];
     const bool full = (*overflow & 1) != 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = q0 + k;
-        pw[q] = make_double2(0.0, 0.0);
+        pw[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (kind[q] != kSplit) {
             pcf[q] = -1;
             continue;
@@ -337,7 +337,7 @@ k_m2l_seg(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nse
           const int32_t* __restrict__ pX, const int32_t* __restrict__ pY,
           const float4* __restrict__ ca, const float4* __restrict__ cd,
           const float* __restrict__ A, const float* __restrict__ M, float* __restrict__ B,
-          double2* __restrict__ pw) {
+          float4* __restrict__ pw) {
     constexpr int P2 = P * P, P3 = P2 * P;
     constexpr int NC = 2 * P2;                 // columns of a pass (two channels)
     constexpr int NL = (NC + 31) / 32;         // columns per lane
@@ -475,7 +475,7 @@ k_m2l_seg(const int32_t* __restrict__ seg_first, const int64_t* __restrict__ nse
                 w0 += __shfl_xor_sync(0xffffffffu, w0, o);
                 w1 += __shfl_xor_sync(0xffffffffu, w1, o);
             }
-            if (lane == 0) pw[q] = make_double2((double)w0, (double)w1);
+            if (lane == 0) pw[q] = make_float4(w0, 0.f, w1, 0.f);
             __syncwarp();      // s0 is the next pair's staging
         }
         // B(X) += the sum over X's far pairs (no other warp adds to B(X) here)
@@ -551,15 +551,18 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
     }
 }
 
-// a10: attraction of a split pair = sum over its child block (double).  The
+// a10: attraction of a split pair = sum over its child block (double-FP32
+// sums: no double precision instruction, which this GPU runs at 1/64 of the
+// single precision rate).  The
 // split pairs of each depth are listed once per traversal (the list keeps
-// pair order); 8 lanes take one split pair, lane c summing children c, c + 8,
-// ... (coalesced: 8 consecutive 16-byte entries per step), then a fixed
-// butterfly over the 8 lanes.  Both orders are fixed, so the table is
-// reproducible.  sb = [first, end) of the depth's entries in split_q.
-__global__ void k_reduce_split(const int64_t* __restrict__ sb, const int32_t* __restrict__ split_q,
-                               const int32_t* __restrict__ pcf, const uint8_t* __restrict__ pnb,
-                               double2* __restrict__ pw) {
+// pair order, each entry with its child block); 8 lanes take one split pair,
+// lane c summing children c, c + 8, ... (coalesced: 8 consecutive 16-byte
+// entries per step, all loaded before the sum), then a fixed butterfly over
+// the 8 lanes.  Both orders are fixed, so the table is
+// reproducible.  sb = [first, end) of the depth's entries in split; an entry
+// is (pair, first child, child count, 0).
+__global__ void k_reduce_split(const int64_t* __restrict__ sb, const int4* __restrict__ split,
+                               float4* __restrict__ pw) {
     const int64_t s0 = sb[0], ns = sb[1] - sb[0];
     const int lane = threadIdx.x & 31, sub = lane & 7;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -567,29 +570,49 @@ __global__ void k_reduce_split(const int64_t* __restrict__ sb, const int32_t* __
     // the loop bound is uniform across the warp (its 4 groups shuffle together)
     for (int64_t k0 = 4 * warp; k0 < ns; k0 += 4 * nwarp) {
         const int64_t k = k0 + (lane >> 3);
-        int32_t q = -1, cf = -1;
-        int nb = 0;
-        if (k < ns) {
-            q = split_q[s0 + k];
-            cf = pcf[q];
-            nb = cf >= 0 ? (int)pnb[q] : 0;     // cf < 0: children not stored (overflow)
-        }
-        double e = 0.0, i = 0.0;
-        for (int c = sub; c < nb; c += 8) {
-            const double2 v = pw[cf + c];
-            e += v.x;
-            i += v.y;
-        }
+        int4 ent = make_int4(-1, -1, 0, 0);
+        if (k < ns) ent = split[s0 + k];
+        const int32_t q = ent.x, cf = ent.y;
+        const int nb = cf >= 0 ? ent.z : 0;     // cf < 0: children not stored (overflow)
+        // a lane's children (at most 8 of a block of 64) loaded before they
+        // are summed, in compensated running sums of both channels
+        float4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (sub + 8 * t < nb) v[t] = pw[cf + sub + 8 * t];
+        float eh = 0.f, ec = 0.f, ih = 0.f, ic = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (sub + 8 * t < nb) {
+                ff_acc(eh, ec, v[t].x, v[t].y);
+                ff_acc(ih, ic, v[t].z, v[t].w);
+            }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
-            e += __shfl_xor_sync(0xffffffffu, e, o);
-            i += __shfl_xor_sync(0xffffffffu, i, o);
+            const float oeh = __shfl_xor_sync(0xffffffffu, eh, o);
+            const float oec = __shfl_xor_sync(0xffffffffu, ec, o);
+            const float oih = __shfl_xor_sync(0xffffffffu, ih, o);
+            const float oic = __shfl_xor_sync(0xffffffffu, ic, o);
+            ff_acc(eh, ec, oeh, oec);
+            ff_acc(ih, ic, oih, oic);
         }
-        if (sub == 0 && cf >= 0) pw[q] = make_double2(e, i);
+        if (sub == 0 && cf >= 0) {
+            const float2 e = ff_two_sum(eh, ec), i = ff_two_sum(ih, ic);
+            pw[q] = make_float4(e.x, e.y, i.x, i.y);
+        }
     }
 }
 
-// the split pairs' range of every depth d <= D in split_q: the exclusive scan
+__global__ void k_compact_split(const uint8_t* __restrict__ kind, const int64_t* __restrict__ n_dev,
+                                const int32_t* __restrict__ off, const int32_t* __restrict__ pcf,
+                                const uint8_t* __restrict__ pnb, int4* __restrict__ split) {
+    const int64_t n = *n_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (kind[i] == kSplit) split[off[i]] = make_int4((int32_t)i, pcf[i], (int)pnb[i], 0);
+}
+
+// the split pairs' range of every depth d <= D in split: the exclusive scan
 // of the split flags at the depth's first pair
 __global__ void k_split_starts(DevCounts* dc, const int32_t* __restrict__ off, int D) {
     const int d = threadIdx.x;
@@ -766,7 +789,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     };
     const bool lists_fit = holds(c.pr_X, 4) && holds(c.pr_Y, 4) && holds(c.pr_kind, 1) &&
                            holds(c.pr_cf, 4) && holds(c.pr_nb, 1) && holds(c.pr_w, 16) &&
-                           holds(c.p2p_val0, 4) && holds(c.far_q, 4) && holds(c.split_q, 4) &&
+                           holds(c.p2p_val0, 4) && holds(c.far_q, 4) && holds(c.split_q, 16) &&
                            holds(c.nf_src, 8) &&
                            holds(c.nf_w32, 8) &&
                            (c.exp_nodes == 0 || (holds(c.m2_key0, 8) && holds(c.m2_val0, 4)));
@@ -782,13 +805,13 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     c.pr_kind.ensure<uint8_t>((size_t)cap);
     c.pr_cf.ensure<int32_t>((size_t)cap);
     c.pr_nb.ensure<uint8_t>((size_t)cap);
-    c.pr_w.ensure<double2>((size_t)cap);
+    c.pr_w.ensure<float4>((size_t)cap);
     int32_t* cnt = c.cnt.ensure<int32_t>((size_t)cap);
     int32_t* off = c.off.ensure<int32_t>((size_t)cap);
     uint8_t* kind = c.pr_kind.get<uint8_t>();
 
     int32_t* far_q = c.far_q.ensure<int32_t>((size_t)cap);
-    int32_t* split_q = c.split_q.ensure<int32_t>((size_t)cap);
+    int4* split = c.split_q.ensure<int4>((size_t)cap);
     int32_t* pv0 = c.p2p_val0.ensure<int32_t>((size_t)cap);
     int32_t* seg_first = c.seg_first.ensure<int32_t>((size_t)c.n_nodes + 2);
     const int64_t* n_pairs_dev = &dc->depth_start[D];
@@ -810,7 +833,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
                  cap, &dc->overflow, &dc->need_pairs);
         k_emit_pairs<<<Gt, B, 0, s>>>(&dc->depth_start[d], nv, kind, off, c.pr_X.get<int32_t>(),
                                       c.pr_Y.get<int32_t>(), c.pr_cf.get<int32_t>(),
-                                      c.pr_nb.get<uint8_t>(), c.pr_w.get<double2>(), cap,
+                                      c.pr_nb.get<uint8_t>(), c.pr_w.get<float4>(), cap,
                                       &dc->overflow);
         MSP_LAUNCH("emit_pairs");
     }
@@ -820,8 +843,8 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     k_flag_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kSplit, flag);
     MSP_LAUNCH("flag_split");
     scan_dev(c, flag, off, n_pairs_dev, cap, &dc->n_split, nullptr, s);
-    k_compact_kind<<<Gt, B, 0, s>>>(kind, n_pairs_dev, kSplit, off, c.pr_X.get<int32_t>(),
-                                    split_q, nullptr);
+    k_compact_split<<<Gt, B, 0, s>>>(kind, n_pairs_dev, off, c.pr_cf.get<int32_t>(),
+                                     c.pr_nb.get<uint8_t>(), split);
     MSP_LAUNCH("compact_split");
     k_split_starts<<<1, 32, 0, s>>>(dc, off, D);
     MSP_LAUNCH("split_starts");
@@ -880,7 +903,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
         const int64_t* first = nullptr;
         if (geo && m2l_gemm_fits(p)) {
             int64_t* fb = nullptr;
-            mq = m2l_gemm(c, far_q, &dc->n_far, cap, eA, eM, eB, c.pr_w.get<double2>(), &fb, s);
+            mq = m2l_gemm(c, far_q, &dc->n_far, cap, eA, eM, eB, c.pr_w.get<float4>(), &fb, s);
             first = fb;
         }
         // the pairs [first, n_far) of mq grouped by target box
@@ -908,7 +931,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
         k_m2l_seg<PP><<<gm, kM2LWarps * 32, 0, s>>>(mseg, &dc->m2l_nseg, mv0, c.exp_first,    \
                                                     inv_sigma, c.pr_X.get<int32_t>(),         \
                                                     c.pr_Y.get<int32_t>(), eca, ecd, eA, eM,  \
-                                                    eB, c.pr_w.get<double2>());               \
+                                                    eB, c.pr_w.get<float4>());                \
         break;
         switch (p) {
             MSP_M2L_CASE(1) MSP_M2L_CASE(2) MSP_M2L_CASE(3) MSP_M2L_CASE(4)
@@ -934,8 +957,7 @@ void attraction(msp_ctx& c, float* u_dev, cudaStream_t s) {
     c.nf_timed = n > 0;
     // a10: pair table, deepest pairs first
     for (int dd = D - 1; dd >= 0; --dd) {
-        k_reduce_split<<<Gt, B, 0, s>>>(&dc->split_start[dd], split_q, c.pr_cf.get<int32_t>(),
-                                        c.pr_nb.get<uint8_t>(), c.pr_w.get<double2>());
+        k_reduce_split<<<Gt, B, 0, s>>>(&dc->split_start[dd], split, c.pr_w.get<float4>());
         MSP_LAUNCH("reduce_split");
     }
     if (u_dev && n > 0) {

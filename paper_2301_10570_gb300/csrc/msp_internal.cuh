@@ -22,6 +22,7 @@ enum PairKind : uint8_t { kSplit = 0, kFar = 1, kP2P = 2, kPruned = 3 };
 // A draw whose total attraction is at or below this has no candidate; every
 // attraction inside the cutoff radius is many orders of magnitude larger.
 constexpr double kMinAttraction = 1e-30;
+constexpr float kMinAttractionF = 1e-30f;
 
 // ---------------------------------------------------------------------------
 // errors: internal code throws; every C entry point converts to msp_status
@@ -199,12 +200,13 @@ struct msp_ctx {
     // octree (SoA)
     msp::DBuf nd_level, nd_prefix, nd_first, nd_count, nd_parent, nd_child_first, nd_nchild;
     msp::DBuf nd_sums, nd_ca, nd_cd;
+    msp::DBuf nd_arrive;                                 // aggregation arrival counters
     // dual traversal
     msp::DBuf pr_X, pr_Y, pr_kind, pr_cf, pr_nb, pr_w;
     // lists
     msp::DBuf m2_key0, m2_key1, m2_val0, m2_val1, m2_flag, m2_off, m2_seg;   // far pairs by X
     msp::DBuf far_q, p2p_key0, p2p_key1, p2p_val0, p2p_val1, seg_first, seg_flag, nf_w32;
-    msp::DBuf split_q;                                   // split pairs, by depth
+    msp::DBuf split_q;                                   // split pairs, by depth (int4 entries)
     msp::DBuf nf_okey0, nf_okey1, nf_oval0, nf_oval1;   // near-field segment order
     msp::DBuf nf_src;                                    // per near-field pair: (first, count) of Y
     // neuron side (msp_neuron.cu): input counts, bound synapses, excess, group
@@ -312,7 +314,7 @@ void radix_sort(msp_ctx& c, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
 void geo_centres(msp_ctx& c, cudaStream_t s);
 bool m2l_gemm_fits(int p);
 const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, int64_t cap,
-                        const float* A, const float* M, float* B, double2* pw,
+                        const float* A, const float* M, float* B, float4* pw,
                         int64_t** first_fallback, cudaStream_t s);
 void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg_dev,
                        int64_t nseg_cap, const int32_t* list_q, const int64_t* nlist_dev,
@@ -375,12 +377,61 @@ __host__ __device__ inline void philox_draw(uint64_t seed, uint32_t c0, uint32_t
 }
 
 // U in [0,1) from the top 53 bits of the first two output words
-__host__ __device__ inline double philox_uniform(uint64_t seed, uint32_t c0, uint32_t c1,
-                                                 uint64_t step) {
+// the 53 bits of a uniform draw U = bits 2^-53 in [0, 1)
+__host__ __device__ inline uint64_t philox_bits53(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                  uint64_t step) {
     uint32_t o[4];
     philox_draw(seed, c0, c1, step, o);
-    uint64_t bits = (((uint64_t)o[0] << 32) | o[1]) >> 11;
-    return (double)bits * (1.0 / 9007199254740992.0);
+    return (((uint64_t)o[0] << 32) | o[1]) >> 11;
+}
+
+__host__ __device__ inline double philox_uniform(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                 uint64_t step) {
+    return (double)philox_bits53(seed, c0, c1, step) * (1.0 / 9007199254740992.0);
+}
+
+// Double-FP32 ("float-float") values hi + lo, |lo| <= ulp(hi) / 2: about 48
+// significant bits on the FP32 pipe (double precision arithmetic is scarce on
+// this GPU).  The pair table holds W(X,Y) of both channels as one float4
+// (E hi, E lo, I hi, I lo).  Sums use Knuth's two-sum on both parts and two
+// renormalisations (relative error a few units of 2^-48); the product uses
+// the FMA's exact residual.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 ff_quick_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float2 s = ff_two_sum(a.x, b.x);
+    const float2 t = ff_two_sum(a.y, b.y);
+    s = ff_quick_two_sum(s.x, __fadd_rn(s.y, t.x));
+    return ff_quick_two_sum(s.x, __fadd_rn(s.y, t.y));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float e = __fmaf_rn(a.x, b.x, -p);
+    return ff_quick_two_sum(p, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e)));
+}
+// a compensated running sum (Neumaier): h += x.hi, the rounding error and
+// x.lo go into c; the pair (h, c) is turned into hi + lo at the end (two-sum).
+// Adding one such pair to another is the same step (commutative bit for bit).
+__device__ __forceinline__ void ff_acc(float& h, float& c, float xh, float xl) {
+    const float2 t = ff_two_sum(h, xh);
+    h = t.x;
+    c = __fadd_rn(__fadd_rn(c, xl), t.y);
+}
+__device__ __forceinline__ bool ff_gt(float2 a, float2 b) {
+    return a.x > b.x || (a.x == b.x && a.y > b.y);
+}
+// U = bits 2^-53 as hi + lo: the top 24 bits exactly, the other 29 rounded
+__device__ __forceinline__ float2 ff_uniform(uint64_t bits53) {
+    const float hi = (float)(uint32_t)(bits53 >> 29) * 0x1p-24f;
+    const float lo = (float)(uint32_t)(bits53 & 0x1FFFFFFFull) * 0x1p-53f;
+    return ff_quick_two_sum(hi, lo);
 }
 
 // every third bit of v (bits 0,3,6,...) packed into the low bits

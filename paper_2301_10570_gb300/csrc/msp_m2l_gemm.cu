@@ -139,7 +139,7 @@ struct GemmArgs {
     const float* A;
     const float* M;
     float* B;
-    double2* pw;
+    float4* pw;                // the pair table (double-FP32 W of both channels)
     int64_t exp_first;
     int p;
     float half_box_over_sigma_l0;   // side / 2 / sigma (half a level-0 box)
@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_m2l_gemm(GemmArgs a) {
         }
         __syncthreads();
         if (threadIdx.x < npair)
-            a.pw[sq[threadIdx.x]] = make_double2((double)sw[2 * threadIdx.x],
-                                                 (double)sw[2 * threadIdx.x + 1]);
+            a.pw[sq[threadIdx.x]] = make_float4(sw[2 * threadIdx.x], 0.f,
+                                               sw[2 * threadIdx.x + 1], 0.f);
         __syncthreads();
     }
 }
@@ -278,7 +278,7 @@ bool m2l_gemm_fits(int p) { return p <= kGemmMaxP; }
 // the far pairs are in key order in c.gm_q and *first_fallback (device)
 // holds the position from which the caller translates pair by pair.
 const int32_t* m2l_gemm(msp_ctx& c, const int32_t* far_q, const int64_t* nfar, int64_t cap,
-                        const float* A, const float* M, float* B, double2* pw,
+                        const float* A, const float* M, float* B, float4* pw,
                         int64_t** first_fallback, cudaStream_t s) {
     const size_t ncap = (size_t)std::max<int64_t>(cap, 1);
     uint64_t* k0 = c.gm_key0.ensure<uint64_t>(ncap);

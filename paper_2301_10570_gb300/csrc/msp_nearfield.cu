@@ -577,14 +577,14 @@ __global__ void k_zero_w(float2* __restrict__ w32, const int64_t* __restrict__ n
         w32[i] = make_float2(0.f, 0.f);
 }
 
-// the single precision per-pair attractions into the double precision table
+// the single precision per-pair attractions into the pair table (double-FP32)
 __global__ void k_widen_w(const int32_t* __restrict__ list_q, const float2* __restrict__ w32,
-                          const int64_t* __restrict__ n_dev, double2* __restrict__ pw) {
+                          const int64_t* __restrict__ n_dev, float4* __restrict__ pw) {
     const int64_t n = *n_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float2 v = w32[i];
-        pw[list_q[i]] = make_double2((double)v.x, (double)v.y);
+        pw[list_q[i]] = make_float4(v.x, 0.f, v.y, 0.f);
     }
 }
 
@@ -642,7 +642,7 @@ void launch_near_field(msp_ctx& c, const int32_t* seg_first, const int64_t* nseg
     int grid = (int)std::min<int64_t>(nseg_cap, 1 << 30);
     k_near_field<<<grid, kNFWarps * 32, 0, s>>>(a);
     MSP_LAUNCH("near_field");
-    k_widen_w<<<gl, 256, 0, s>>>(list_q, w32, nlist_dev, c.pr_w.get<double2>());
+    k_widen_w<<<gl, 256, 0, s>>>(list_q, w32, nlist_dev, c.pr_w.get<float4>());
     MSP_LAUNCH("widen_w");
 }
 

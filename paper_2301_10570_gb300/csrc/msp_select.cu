@@ -92,21 +92,22 @@ __device__ float warp_far_w(const Tree& tr, const Exps& ex, int32_t X, int32_t Y
 
 // Algorithm 2's last steps: negative candidates (truncation) count as zero;
 // -1 when the total is at most kMinAttraction; upper_bound over the inclusive
-// prefix sums, and
-// the last positive candidate when rounding puts r at the total.
-__device__ inline int draw_index(const double* w, int k, double U) {
-    double pre[8];
-    double tot = 0.0;
+// prefix sums, and the last positive candidate when rounding puts r at the
+// total.  The candidates, their prefix sums and r = U * total are double-FP32
+// values (hi + lo; the sign of a value is that of hi).
+__device__ inline int draw_index(const float2* w, int k, uint64_t bits53) {
+    float2 pre[8];
+    float2 tot = make_float2(0.f, 0.f);
     for (int i = 0; i < k; ++i) {
-        tot += w[i] > 0.0 ? w[i] : 0.0;
+        tot = ff_add(tot, w[i].x > 0.f ? w[i] : make_float2(0.f, 0.f));
         pre[i] = tot;
     }
-    if (!(tot > kMinAttraction)) return -1;
-    double r = U * tot;
+    if (!(tot.x > kMinAttractionF)) return -1;
+    const float2 r = ff_mul(ff_uniform(bits53), tot);
     for (int i = 0; i < k; ++i)
-        if (pre[i] > r) return i;
+        if (ff_gt(pre[i], r)) return i;
     for (int i = k - 1; i >= 0; --i)
-        if (w[i] > 0.0) return i;
+        if (w[i].x > 0.f) return i;
     return -1;
 }
 
@@ -126,13 +127,13 @@ struct DescCtr {
 
 // the items of both channels start at (root, root) where the root has
 // vacancies and attraction in that channel
-__global__ void k_init_items(const int4* __restrict__ sums, const double2* __restrict__ pw,
+__global__ void k_init_items(const int4* __restrict__ sums, const float4* __restrict__ pw,
                              Item* __restrict__ items, DevCounts* dc) {
     const int4 rs = sums[0];
-    const double2 rw = pw[0];
+    const float4 rw = pw[0];
     int64_t k = 0;
-    if (rs.x > 0 && rw.x > kMinAttraction) items[k++] = Item{0, 0, 0, 0};
-    if (rs.y > 0 && rw.y > kMinAttraction) items[k++] = Item{0, 0, 0, 1};
+    if (rs.x > 0 && rw.x > kMinAttractionF) items[k++] = Item{0, 0, 0, 0};
+    if (rs.y > 0 && rw.z > kMinAttractionF) items[k++] = Item{0, 0, 0, 1};
     dc->items[0] = k;
     dc->items[1] = 0;
     dc->n_leaf = 0;
@@ -144,7 +145,7 @@ __global__ void k_init_items(const int4* __restrict__ sums, const double2* __res
 __global__ void __launch_bounds__(kDescWarps * 32)
 k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
           const uint8_t* __restrict__ kind, const int32_t* __restrict__ pcf,
-          const double2* __restrict__ pw, uint64_t seed, StepRef stp, Item* __restrict__ out,
+          const float4* __restrict__ pw, uint64_t seed, StepRef stp, Item* __restrict__ out,
           int64_t cap_out, Item* __restrict__ leaf_out, int64_t cap_leaf, DescCtr ct) {
     const uint64_t step = stp.get();
     __shared__ float sH[kDescWarps][48];
@@ -184,7 +185,7 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
                 int4 sm = tr.sums[xc];
                 int sa = ch ? sm.y : sm.x;
                 bool keep = sa > 0;
-                if (keep && split) keep = (ch ? pw[cf + lane].y : pw[cf + lane].x) > kMinAttraction;
+                if (keep && split) keep = (ch ? pw[cf + lane].z : pw[cf + lane].x) > kMinAttractionF;
                 if (keep) {
                     unsigned long long slot = atomicAdd(ct.n_out, 1ull);
                     Item nx_it = {xc, Y, split ? cf + lane : -1, ch};
@@ -210,13 +211,12 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
                 const int32_t xc = lx ? X : tr.child_first[X] + i;
                 const int4 sm = tr.sums[xc];
                 if (lx || (ch ? sm.y : sm.x) != 0) {
-                    double wk[8];
+                    float2 wk[8];
                     for (int j = 0; j < ny; ++j) {
-                        const double2 v = pw[cf + (int64_t)i * ny + j];
-                        wk[j] = ch ? v.y : v.x;
+                        const float4 v = pw[cf + (int64_t)i * ny + j];
+                        wk[j] = ch ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
                     }
-                    const double U = philox_uniform(seed, (uint32_t)xc, c1, step);
-                    const int kk = draw_index(wk, ny, U);
+                    const int kk = draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
                     drew = true;
                     if (kk >= 0) {
                         const unsigned long long slot = atomicAdd(ct.n_out, 1ull);
@@ -238,19 +238,19 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
                 int4 sm = tr.sums[xc];
                 if ((ch ? sm.y : sm.x) == 0) continue;
             }
-            double wk[8];
+            float2 wk[8];
             for (int j = 0; j < ny; ++j) {
                 if (split) {
-                    double2 v = pw[cf + (int64_t)i * ny + j];
-                    wk[j] = ch ? v.y : v.x;
+                    const float4 v = pw[cf + (int64_t)i * ny + j];
+                    wk[j] = ch ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
                 } else {
-                    wk[j] = (double)warp_far_w(tr, ex, xc, cy + j, ch, sH[w], sb[w][0], sb[w][1]);
+                    wk[j] = make_float2(warp_far_w(tr, ex, xc, cy + j, ch, sH[w], sb[w][0], sb[w][1]),
+                                        0.f);
                 }
             }
             if (lane == 0) {
                 uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
-                double U = philox_uniform(seed, (uint32_t)xc, c1, step);
-                int kk = draw_index(wk, ny, U);
+                int kk = draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
                 atomicAdd(ct.draws, 1ull);
                 if (kk >= 0) {
                     unsigned long long slot = atomicAdd(ct.n_out, 1ull);
@@ -740,7 +740,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     const int64_t cap_items = 2 * c.n_nodes + 64, cap_leaf = 2 * c.n_nodes + 64;
     Item* ib[2] = {c.items0.ensure<Item>((size_t)cap_items), c.items1.ensure<Item>((size_t)cap_items)};
     Item* lit = c.leaf_items.ensure<Item>((size_t)cap_leaf);
-    k_init_items<<<1, 1, 0, s>>>(c.nd_sums.get<int4>(), c.pr_w.get<double2>(), ib[0], dc);
+    k_init_items<<<1, 1, 0, s>>>(c.nd_sums.get<int4>(), c.pr_w.get<float4>(), ib[0], dc);
     MSP_LAUNCH("init_items");
     auto ull = [](int64_t* p) { return reinterpret_cast<unsigned long long*>(p); };
     const int n_steps = c.tree_depth + 1;
@@ -754,7 +754,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         ct.draws = ull(&dc->draws);
         ct.overflow = ull(&dc->overflow);
         k_descend<<<gd, kDescWarps * 32, 0, s>>>(ib[k & 1], tr, ex, c.pr_kind.get<uint8_t>(),
-                                                 c.pr_cf.get<int32_t>(), c.pr_w.get<double2>(),
+                                                 c.pr_cf.get<int32_t>(), c.pr_w.get<float4>(),
                                                  cfg.seed, stp, ib[(k + 1) & 1], cap_items, lit,
                                                  cap_leaf, ct);
         MSP_LAUNCH("descend");

@@ -291,79 +291,135 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
     }
 }
 
-// Box aggregates, deepest level first.  A leaf sums its points; an inner box
-// combines its children.  Centroids are accumulated as weighted offsets from
-// the box's geometric centre so that single precision keeps them accurate
-// (with frames, the centre in the box's network's own frame: box_axis).
-// One warp per box of the level: a leaf's lanes take its points, an inner
-// box's lanes its children (at most 8); warp sums, then lane 0 writes the
-// box's vacant-element sums and its axon / dendrite centroids (offsets from
-// the geometric centre summed, then divided by the weight).
-__global__ void k_aggregate(const int64_t* __restrict__ lb, int level, int frame_level, float ox,
-                            float oy, float oz, float side, const float4* __restrict__ pts,
-                            const uint64_t* __restrict__ prefix, const int32_t* __restrict__ first,
-                            const int32_t* __restrict__ count,
-                            const int32_t* __restrict__ child_first,
-                            const uint8_t* __restrict__ nchild, int4* __restrict__ sums,
-                            float4* __restrict__ ca, float4* __restrict__ cd,
-                            int32_t* __restrict__ leaf_of) {
-    const int64_t l0 = lb[0], nl = lb[1] - lb[0];
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nl; k += nw) {
-        const int64_t i = l0 + k;
-        const uint64_t pre = prefix[i];
-        const float bs = ldexpf(side, -level);
-        const float g[3] = {ox + ((float)box_axis(pre, 0, level, frame_level) + 0.5f) * bs,
-                            oy + ((float)box_axis(pre, 1, level, frame_level) + 0.5f) * bs,
-                            oz + ((float)box_axis(pre, 2, level, frame_level) + 0.5f) * bs};
-        int aE = 0, aI = 0, wE = 0, wI = 0;
-        float sa[3] = {0.f, 0.f, 0.f}, sd[3] = {0.f, 0.f, 0.f};
-        const int32_t cf = child_first[i];
-        if (cf < 0) {
-            const int32_t f = first[i], c = count[i];
-            for (int32_t j = f + lane; j < f + c; j += 32) {
-                const float4 p = pts[j];
-                const uint32_t w = __float_as_uint(p.w);
-                const int a = (int)pk_axon(w), de = (int)pk_de(w), di = (int)pk_di(w);
-                if (pk_type(w)) aI += a; else aE += a;
-                wE += de;
-                wI += di;
-                const float fa = (float)a, fd = (float)(de + di);
-                const float dx = p.x - g[0], dy = p.y - g[1], dz = p.z - g[2];
-                sa[0] = fmaf(fa, dx, sa[0]); sa[1] = fmaf(fa, dy, sa[1]); sa[2] = fmaf(fa, dz, sa[2]);
-                sd[0] = fmaf(fd, dx, sd[0]); sd[1] = fmaf(fd, dy, sd[1]); sd[2] = fmaf(fd, dz, sd[2]);
-                leaf_of[j] = (int32_t)i;
-            }
-        } else if (lane < nchild[i]) {
-            const int4 sm = sums[cf + lane];
-            const float4 a4 = ca[cf + lane], d4 = cd[cf + lane];
-            aE = sm.x; aI = sm.y; wE = sm.z; wI = sm.w;
-            const float fa = (float)(sm.x + sm.y), fd = (float)(sm.z + sm.w);
-            sa[0] = fa * (a4.x - g[0]); sa[1] = fa * (a4.y - g[1]); sa[2] = fa * (a4.z - g[2]);
-            sd[0] = fd * (d4.x - g[0]); sd[1] = fd * (d4.y - g[1]); sd[2] = fd * (d4.z - g[2]);
+// Box aggregates, one launch for the whole octree.  A leaf sums its points;
+// an inner box combines its children, and it is computed by the warp of its
+// last child to finish: every box, once written, adds one to its parent's
+// arrival counter (after a fence), and the warp that brings the counter to the
+// parent's child count resets it and goes on with the parent, up to the root.
+// Centroids are accumulated as weighted offsets from the box's geometric
+// centre so that single precision keeps them accurate (with frames, the
+// centre in the box's network's own frame: box_axis).  A leaf's lanes take its
+// points, an inner box's lanes its children (at most 8); a fixed butterfly
+// sums the lanes, then lane 0 writes the box's vacant-element sums and its
+// axon / dendrite centroids (offsets summed, then divided by the weight).  The
+// order of every sum is fixed whichever warp computes a box, so the results
+// are those of a level-by-level pass.  The counters are zero on entry (cleared
+// by the host before an eager build; every complete launch leaves them zero).
+__device__ __forceinline__ void aggregate_box(int64_t i, int lane, int frame_level, float ox,
+                                              float oy, float oz, float side,
+                                              const float4* __restrict__ pts,
+                                              const uint8_t* __restrict__ level,
+                                              const uint64_t* __restrict__ prefix,
+                                              const int32_t* __restrict__ first,
+                                              const int32_t* __restrict__ count,
+                                              const int32_t* __restrict__ child_first,
+                                              const uint8_t* __restrict__ nchild,
+                                              int4* __restrict__ sums, float4* __restrict__ ca,
+                                              float4* __restrict__ cd,
+                                              int32_t* __restrict__ leaf_of) {
+    const uint64_t pre = prefix[i];
+    const int lv = (int)level[i];
+    const float bs = ldexpf(side, -lv);
+    const float g[3] = {ox + ((float)box_axis(pre, 0, lv, frame_level) + 0.5f) * bs,
+                        oy + ((float)box_axis(pre, 1, lv, frame_level) + 0.5f) * bs,
+                        oz + ((float)box_axis(pre, 2, lv, frame_level) + 0.5f) * bs};
+    int aE = 0, aI = 0, wE = 0, wI = 0;
+    float sa[3] = {0.f, 0.f, 0.f}, sd[3] = {0.f, 0.f, 0.f};
+    const int32_t cf = child_first[i];
+    if (cf < 0) {
+        const int32_t f = first[i], c = count[i];
+        for (int32_t j = f + lane; j < f + c; j += 32) {
+            const float4 p = pts[j];
+            const uint32_t w = __float_as_uint(p.w);
+            const int a = (int)pk_axon(w), de = (int)pk_de(w), di = (int)pk_di(w);
+            if (pk_type(w)) aI += a; else aE += a;
+            wE += de;
+            wI += di;
+            const float fa = (float)a, fd = (float)(de + di);
+            const float dx = p.x - g[0], dy = p.y - g[1], dz = p.z - g[2];
+            sa[0] = fmaf(fa, dx, sa[0]); sa[1] = fmaf(fa, dy, sa[1]); sa[2] = fmaf(fa, dz, sa[2]);
+            sd[0] = fmaf(fd, dx, sd[0]); sd[1] = fmaf(fd, dy, sd[1]); sd[2] = fmaf(fd, dz, sd[2]);
+            leaf_of[j] = (int32_t)i;
         }
+    } else if (lane < nchild[i]) {
+        // the children were written by other warps: read them from L2
+        const int4 sm = __ldcg(&sums[cf + lane]);
+        const float4 a4 = __ldcg(&ca[cf + lane]), d4 = __ldcg(&cd[cf + lane]);
+        aE = sm.x; aI = sm.y; wE = sm.z; wI = sm.w;
+        const float fa = (float)(sm.x + sm.y), fd = (float)(sm.z + sm.w);
+        sa[0] = fa * (a4.x - g[0]); sa[1] = fa * (a4.y - g[1]); sa[2] = fa * (a4.z - g[2]);
+        sd[0] = fd * (d4.x - g[0]); sd[1] = fd * (d4.y - g[1]); sd[2] = fd * (d4.z - g[2]);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            aE += __shfl_xor_sync(0xffffffffu, aE, o);
-            aI += __shfl_xor_sync(0xffffffffu, aI, o);
-            wE += __shfl_xor_sync(0xffffffffu, wE, o);
-            wI += __shfl_xor_sync(0xffffffffu, wI, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        aE += __shfl_xor_sync(0xffffffffu, aE, o);
+        aI += __shfl_xor_sync(0xffffffffu, aI, o);
+        wE += __shfl_xor_sync(0xffffffffu, wE, o);
+        wI += __shfl_xor_sync(0xffffffffu, wI, o);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                sa[d] += __shfl_xor_sync(0xffffffffu, sa[d], o);
-                sd[d] += __shfl_xor_sync(0xffffffffu, sd[d], o);
-            }
-        }
-        if (lane == 0) {
-            sums[i] = make_int4(aE, aI, wE, wI);
-            const float ta = (float)(aE + aI), td = (float)(wE + wI);
-            ca[i] = ta > 0.f ? make_float4(g[0] + sa[0] / ta, g[1] + sa[1] / ta, g[2] + sa[2] / ta, ta)
-                             : make_float4(g[0], g[1], g[2], 0.f);
-            cd[i] = td > 0.f ? make_float4(g[0] + sd[0] / td, g[1] + sd[1] / td, g[2] + sd[2] / td, td)
-                             : make_float4(g[0], g[1], g[2], 0.f);
+        for (int d = 0; d < 3; ++d) {
+            sa[d] += __shfl_xor_sync(0xffffffffu, sa[d], o);
+            sd[d] += __shfl_xor_sync(0xffffffffu, sd[d], o);
         }
     }
+    if (lane == 0) {
+        sums[i] = make_int4(aE, aI, wE, wI);
+        const float ta = (float)(aE + aI), td = (float)(wE + wI);
+        ca[i] = ta > 0.f ? make_float4(g[0] + sa[0] / ta, g[1] + sa[1] / ta, g[2] + sa[2] / ta, ta)
+                         : make_float4(g[0], g[1], g[2], 0.f);
+        cd[i] = td > 0.f ? make_float4(g[0] + sd[0] / td, g[1] + sd[1] / td, g[2] + sd[2] / td, td)
+                         : make_float4(g[0], g[1], g[2], 0.f);
+    }
+}
+
+// arrival at a parent: release for the box's own results, acquire for its
+// siblings' (the last arrival reads them)
+__device__ __forceinline__ int arrive_acq_rel(int32_t* p) {
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
+// nodes_end: the node count (device memory); one warp per leaf
+__global__ void k_aggregate_tree(const int64_t* __restrict__ nodes_end, int frame_level, float ox,
+                                 float oy, float oz, float side, const float4* __restrict__ pts,
+                                 const uint8_t* __restrict__ level,
+                                 const uint64_t* __restrict__ prefix,
+                                 const int32_t* __restrict__ first,
+                                 const int32_t* __restrict__ count,
+                                 const int32_t* __restrict__ parent,
+                                 const int32_t* __restrict__ child_first,
+                                 const uint8_t* __restrict__ nchild, int4* __restrict__ sums,
+                                 float4* __restrict__ ca, float4* __restrict__ cd,
+                                 int32_t* __restrict__ leaf_of, int32_t* __restrict__ arrive) {
+    const int64_t nn = *nodes_end;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nn; k += nw) {
+        if (child_first[k] >= 0) continue;        // inner boxes: done by their last child's warp
+        int64_t i = k;
+        for (;;) {
+            aggregate_box(i, lane, frame_level, ox, oy, oz, side, pts, level, prefix, first, count,
+                          child_first, nchild, sums, ca, cd, leaf_of);
+            const int32_t p = parent[i];
+            if (p < 0) break;
+            int last = 0;
+            if (lane == 0) {
+                // lane 0 wrote the box's results
+                last = arrive_acq_rel(&arrive[p]) == (int)nchild[p] - 1;
+                if (last) arrive[p] = 0;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) break;
+            __syncwarp();                         // the lanes' reads after lane 0's acquire
+            i = p;
+        }
+    }
+}
+
+// a warp per node (the leaves all start at once), at most 16 blocks per SM
+int agg_grid(int64_t nodes, int64_t sm_count) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((nodes + 3) / 4, sm_count * 16));
 }
 
 }  // namespace
@@ -447,14 +503,14 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
             dev_set(&dc->n_elem, 0, s);
         }
         const int Gt = (int)std::max<int64_t>(1, (int64_t)c.sm_count * 8);
-        for (int l = c.tree_levels; l >= 0; --l) {
-            k_aggregate<<<Gt, 128, 0, s>>>(
-                &dc->level_start[l], l, c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
-                c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(),
-                c.nd_sums.get<int4>(), c.nd_ca.get<float4>(), c.nd_cd.get<float4>(), leaf_of);
-            MSP_LAUNCH("aggregate");
-        }
+        if (!c.graph_mode) MSP_CUDA(cudaMemsetAsync(c.nd_arrive.p, 0, c.nd_arrive.bytes, s));
+        k_aggregate_tree<<<agg_grid(c.n_nodes, c.sm_count), 128, 0, s>>>(
+            &dc->level_start[c.tree_levels + 1], c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
+            c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
+            c.nd_count.get<int32_t>(), c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
+            c.nd_nchild.get<uint8_t>(), c.nd_sums.get<int4>(), c.nd_ca.get<float4>(),
+            c.nd_cd.get<float4>(), leaf_of, c.nd_arrive.get<int32_t>());
+        MSP_LAUNCH("aggregate");
         if (eager_reuse) {
             pull_counts(c, s);          // the one synchronisation of the build
             c.n_elem = c.hcount->n_elem;
@@ -535,6 +591,14 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         }
         float4* ca = c.nd_ca.ensure<float4>((size_t)cap);
         float4* cd = c.nd_cd.ensure<float4>((size_t)cap);
+        // the arrival counters: cleared before an eager build and whenever
+        // the buffer is new (a graph's dry run may build one level deeper than
+        // the eager build and grow it); a replay finds them as the last
+        // complete launch left them, zero
+        const size_t arrive_bytes = c.nd_arrive.bytes;
+        int32_t* arrive = c.nd_arrive.ensure<int32_t>((size_t)cap);
+        if (!c.graph_mode || c.nd_arrive.bytes != arrive_bytes)
+            MSP_CUDA(cudaMemsetAsync(arrive, 0, c.nd_arrive.bytes, s));
         k_init_root<<<1, 1, 0, s>>>(n, c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(),
                                     c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
                                     c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
@@ -565,14 +629,13 @@ void build_tree(msp_ctx& c, int64_t n, const float* x, const float* y, const flo
         } else {
             dev_set(&dc->more_levels, 0, s);
         }
-        // a4: aggregates, deepest level first (empty levels are no-ops)
-        for (int l = L; l >= 0; --l) {
-            k_aggregate<<<Gt, 128, 0, s>>>(
-                &dc->level_start[l], l, c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
-                c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(), c.nd_count.get<int32_t>(),
-                c.nd_child_first.get<int32_t>(), c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of);
-            MSP_LAUNCH("aggregate");
-        }
+        // a4: aggregates, leaves up to the root in one launch
+        k_aggregate_tree<<<agg_grid(cap, c.sm_count), 128, 0, s>>>(
+            &dc->level_start[L + 1], c.frame_level, o3[0], o3[1], o3[2], cfg.side, pts,
+            c.nd_level.get<uint8_t>(), c.nd_prefix.get<uint64_t>(), c.nd_first.get<int32_t>(),
+            c.nd_count.get<int32_t>(), c.nd_parent.get<int32_t>(), c.nd_child_first.get<int32_t>(),
+            c.nd_nchild.get<uint8_t>(), sums, ca, cd, leaf_of, arrive);
+        MSP_LAUNCH("aggregate");
         // inside the whole-step graph the tree of the same positions has the
         // same levels; a deeper one sets more_levels, which halts the graph
         if (c.graph_mode) {

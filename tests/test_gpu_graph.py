@@ -182,7 +182,9 @@ def test_graph_counts_its_kernel_launches():
     nxt, halted = g.step_graph_finish()
     assert (nxt, halted) == (3, 0)
     per = (g.stats()["kernel_launches"] - k0) / 3
-    assert per > 50 and per == int(per)
+    # a whole number of launches per replayed step, at least one per kind of
+    # work (the walk, the near field, the descent, the draw, the resolution)
+    assert per >= 20 and per == int(per)
     g.close()
 
 
