@@ -199,8 +199,8 @@ msp_status msp_destroy(msp_ctx* c) {
                          &c->gr_val1, &c->gr_flag, &c->gr_off, &c->gr_seg, &c->ln_sums,
                          &c->ln_part, &c->ln_coef,
                          &c->expA, &c->expM, &c->expB, &c->u_sorted, &c->items0, &c->items1,
-                         &c->leaf_items, &c->rq_key0, &c->rq_key1, &c->rq_val0, &c->rq_val1,
-                         &c->accepted, &c->acc_off, &c->cnt, &c->off, &c->scan_tmp,
+                         &c->leaf_items, &c->rq_key0, &c->rq_val0,
+                         &c->accepted, &c->acc_off, &c->rq_gcnt, &c->rq_goff, &c->cnt, &c->off, &c->scan_tmp,
                          &c->rs_hist, &c->h_u, &c->h_partner, &c->h_pre,
                          &c->h_post, &c->h_type, &c->h_nsyn, &c->hs_u, &c->hs_partner,
                          &c->hs_pre, &c->hs_post, &c->hs_type, &c->hs_nsyn, &c->c_type,

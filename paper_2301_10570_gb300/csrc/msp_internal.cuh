@@ -137,6 +137,7 @@ struct DevCounts {
     uint64_t tree_gen;                       // generation stamp of the last eager build
     int64_t m2l_n, m2l_nseg;                 // far pairs translated pair by pair, their targets
     int64_t n_split;                         // split pairs of the last traversal
+    int64_t n_groups;                        // request groups (channel, dendrite): 2 n
     int64_t split_start[kMaxLevels + 3];     // depth d split pairs: split_q[split_start[d], [d+1])
 };
 
@@ -227,7 +228,8 @@ struct msp_ctx {
     msp::DBuf expA, expM, expB;
     msp::DBuf u_sorted;
     // descent
-    msp::DBuf items0, items1, leaf_items, rq_key0, rq_key1, rq_val0, rq_val1, accepted, acc_off;
+    msp::DBuf items0, items1, leaf_items, rq_key0, rq_val0, accepted, acc_off;
+    msp::DBuf rq_gcnt, rq_goff;                          // requests per (channel, dendrite)
     // generic scratch
     msp::DBuf cnt, off, scan_tmp, rs_hist, sd_tmp;
     // device-resident sizes and their pinned host mirror

@@ -531,69 +531,85 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
     if (lane == 0 && draws) atomicAdd(draw_ctr, draws);
 }
 
-// requests in element order: flag, then key = priority << 32 | (dendrite*2 + channel)
-__global__ void k_request_flags(const int32_t* __restrict__ partner,
-                                const int64_t* __restrict__ n_dev, int32_t* __restrict__ flag) {
-    const int64_t n_elem = *n_dev;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
-         e += (int64_t)gridDim.x * blockDim.x)
-        flag[e] = partner[e] >= 0;
+// a12: the requests grouped by (channel, dendrite), group g = channel * n +
+// dendrite, by a counting sort: counts per group, their exclusive scan, and a
+// scatter that takes each request's slot from its group's count (counting it
+// back down to zero).  The order inside a group is left to the atomics; the
+// ranking below does not depend on it.
+__global__ void k_req_count(int64_t n, const uint8_t* __restrict__ type,
+                            const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
+                            const int32_t* __restrict__ partner, int32_t* __restrict__ gcnt,
+                            const int64_t* __restrict__ n_elem, int64_t* __restrict__ n_groups) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_groups = 2 * n;
+    const int64_t ne = *n_elem;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = va[t];
+        const int32_t e0 = eoff[t];
+        if ((int64_t)e0 + a > ne) continue;
+        const int64_t base = type[t] ? n : 0;
+        for (int k = 0; k < a; ++k) {
+            const int32_t s = partner[e0 + k];
+            if (s >= 0) atomicAdd(&gcnt[base + s], 1);
+        }
+    }
 }
 
-__global__ void k_request_emit(int64_t n, const uint8_t* __restrict__ type,
-                               const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
-                               const int32_t* __restrict__ partner, const int32_t* __restrict__ roff,
-                               uint64_t seed, StepRef stp, uint64_t* __restrict__ key,
-                               int32_t* __restrict__ val, const int64_t* __restrict__ n_elem) {
+// key = priority << 32 | group, val = element; cap bounds the slots (the
+// buffers' length) should the counts not match
+__global__ void k_req_scatter(int64_t n, const uint8_t* __restrict__ type,
+                              const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
+                              const int32_t* __restrict__ partner, const int32_t* __restrict__ goff,
+                              int32_t* __restrict__ gcnt, uint64_t seed, StepRef stp,
+                              uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                              const int64_t* __restrict__ n_elem, int64_t cap) {
     const uint64_t step = stp.get();
     const int64_t ne = *n_elem;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int a = va[t];
-        int32_t e0 = eoff[t];
+        const int a = va[t];
+        const int32_t e0 = eoff[t];
         if ((int64_t)e0 + a > ne) continue;
-        uint32_t ch = type[t] ? 1u : 0u;
+        const int64_t base = type[t] ? n : 0;
         for (int k = 0; k < a; ++k) {
-            int32_t s = partner[e0 + k];
+            const int32_t s = partner[e0 + k];
             if (s < 0) continue;
             uint32_t o[4];
             philox_draw(seed, (uint32_t)t, (uint32_t)k | (kTagAccept << 16), step, o);
-            int32_t r = roff[e0 + k];
-            key[r] = ((uint64_t)o[0] << 32) | ((uint32_t)s * 2u + ch);
+            const int64_t g = base + s;
+            const int64_t r = (int64_t)goff[g] + atomicSub(&gcnt[g], 1) - 1;
+            if (r < 0 || r >= cap) continue;
+            key[r] = ((uint64_t)o[0] << 32) | (uint32_t)g;
             val[r] = e0 + k;
         }
     }
 }
 
 // A dendrite neuron accepts, per channel, its first `capacity` requests in
-// (priority, element) order.  The requests are sorted stably by group
-// (dendrite, channel) only, so inside a group they are in element order; the
-// rank of request i is the number of requests of its group before it in
-// (priority, element) order: those with a smaller priority, and those earlier
-// in the group with an equal one.  Groups are small (the requests one neuron
-// receives), so each request counts over its group directly.
+// (priority, element) order: the rank of request i is the number of requests
+// of its group before it in that order.  Groups are small (the requests one
+// neuron receives), so each request counts over its group directly.
 __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
-                         const int64_t* __restrict__ nr_dev, const uint8_t* __restrict__ vde,
+                         const int32_t* __restrict__ goff, const int64_t* __restrict__ nr_dev,
+                         int64_t n, const uint8_t* __restrict__ vde,
                          const uint8_t* __restrict__ vdi, uint8_t* __restrict__ accepted) {
     const int64_t nr = *nr_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t ki = key[i];
-        const uint32_t g = (uint32_t)ki, pr = (uint32_t)(ki >> 32);
-        const uint32_t s = g >> 1;
-        const int cap = (g & 1u) ? vdi[s] : vde[s];
+        const int64_t g = (int64_t)(uint32_t)ki;
+        const uint32_t pr = (uint32_t)(ki >> 32);
+        const int32_t ei = val[i];
+        const bool inh = g >= n;
+        const int64_t s = inh ? g - n : g;
+        const int cap = inh ? vdi[s] : vde[s];
+        const int64_t j0 = goff[g], j1 = g + 1 < 2 * n ? (int64_t)goff[g + 1] : nr;
         int rank = 0;
-        for (int64_t j = i - 1; j >= 0 && rank < cap; --j) {
-            const uint64_t kj = key[j];
-            if ((uint32_t)kj != g) break;
-            rank += (uint32_t)(kj >> 32) <= pr;
+        for (int64_t j = j0; j < j1 && rank < cap; ++j) {
+            const uint32_t pj = (uint32_t)(key[j] >> 32);
+            rank += pj < pr || (pj == pr && val[j] < ei);
         }
-        for (int64_t j = i + 1; j < nr && rank < cap; ++j) {
-            const uint64_t kj = key[j];
-            if ((uint32_t)kj != g) break;
-            rank += (uint32_t)(kj >> 32) < pr;
-        }
-        accepted[val[i]] = rank < cap ? 1 : 0;
+        accepted[ei] = rank < cap ? 1 : 0;
     }
 }
 
@@ -682,12 +698,6 @@ __global__ void k_fill_i32(int32_t* __restrict__ p, const int64_t* __restrict__ 
 
 }  // namespace
 
-static int bits_for_sel(int64_t v) {
-    int b = 1;
-    while (b < 63 && (1ll << b) <= v) ++b;
-    return b;
-}
-
 void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const uint8_t* va_dev,
                      const uint8_t* vde_dev, const uint8_t* vdi_dev, int32_t* partner,
                      int32_t* syn_pre, int32_t* syn_post, uint8_t* syn_type, int64_t* n_syn,
@@ -770,25 +780,29 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
         ull(&dc->draws), &dc->n_elem);
     MSP_LAUNCH("leaf_draw");
 
-    // a12: requests grouped by (dendrite, channel), ranked by (priority, element)
+    // a12: requests grouped by (channel, dendrite), ranked by (priority, element)
     int32_t* flag = c.cnt.ensure<int32_t>((size_t)ne);
-    int32_t* roff = c.off.ensure<int32_t>((size_t)ne);
     const int gn = grid_for(n, B, (int64_t)c.sm_count * 16);
-    k_request_flags<<<ge, B, 0, s>>>(partner, &dc->n_elem, flag);
-    MSP_LAUNCH("request_flags");
-    scan_dev(c, flag, roff, &dc->n_elem, ne, &dc->n_req, nullptr, s);
+    const size_t ng = (size_t)std::max<int64_t>(2 * n, 1);
+    // the group counts: cleared before an eager selection and whenever the
+    // buffer is new; every complete scatter counts them back down to zero
+    const size_t gcnt_bytes = c.rq_gcnt.bytes;
+    int32_t* gcnt = c.rq_gcnt.ensure<int32_t>(ng);
+    if (!c.graph_mode || c.rq_gcnt.bytes != gcnt_bytes)
+        MSP_CUDA(cudaMemsetAsync(gcnt, 0, c.rq_gcnt.bytes, s));
+    int32_t* goff = c.rq_goff.ensure<int32_t>(ng);
     uint8_t* acc = c.accepted.ensure<uint8_t>((size_t)ne);
     MSP_CUDA(cudaMemsetAsync(acc, 0, (size_t)ne, s));
     uint64_t* k0 = c.rq_key0.ensure<uint64_t>((size_t)ne);
-    uint64_t* k1 = c.rq_key1.ensure<uint64_t>((size_t)ne);
     int32_t* v0 = c.rq_val0.ensure<int32_t>((size_t)ne);
-    int32_t* v1 = c.rq_val1.ensure<int32_t>((size_t)ne);
-    k_request_emit<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, roff,
-                                    cfg.seed, stp, k0, v0, &dc->n_elem);
-    MSP_LAUNCH("request_emit");
-    // stable sort by (dendrite, channel): the low bits of the key
-    radix_sort_dev(c, k0, v0, k1, v1, &dc->n_req, ne, bits_for_sel(2 * n), s);
-    k_accept<<<ge, B, 0, s>>>(k0, v0, &dc->n_req, vde_dev, vdi_dev, acc);
+    k_req_count<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, gcnt,
+                                 &dc->n_elem, &dc->n_groups);
+    MSP_LAUNCH("req_count");
+    scan_dev(c, gcnt, goff, &dc->n_groups, (int64_t)ng, &dc->n_req, nullptr, s);
+    k_req_scatter<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, goff,
+                                   gcnt, cfg.seed, stp, k0, v0, &dc->n_elem, (int64_t)ne);
+    MSP_LAUNCH("req_scatter");
+    k_accept<<<ge, B, 0, s>>>(k0, v0, goff, &dc->n_req, n, vde_dev, vdi_dev, acc);
     MSP_LAUNCH("accept");
     k_acc_flags<<<ge, B, 0, s>>>(acc, &dc->n_elem, flag);
     MSP_LAUNCH("acc_flags");
