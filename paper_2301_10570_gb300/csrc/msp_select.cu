@@ -142,6 +142,12 @@ __global__ void k_init_items(const int4* __restrict__ sums, const float4* __rest
     dc->overflow &= ~6ll;       // the descent's bits; bit 0 (pair table) stays
 }
 
+// One level step of the descent.  A warp takes four items, 8 lanes each
+// (lane i of a group for the item's axon child i): a leaf pair goes to the
+// per-element draw; a dendrite leaf is kept by every axon child with
+// vacancies; otherwise each axon child draws among the children of Y from
+// the pair table.  Items below a translated pair (candidates' attractions
+// evaluated as translations by the whole warp) follow, one at a time.
 __global__ void __launch_bounds__(kDescWarps * 32)
 k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
           const uint8_t* __restrict__ kind, const int32_t* __restrict__ pcf,
@@ -151,115 +157,122 @@ k_descend(const Item* __restrict__ in, Tree tr, Exps ex,
     __shared__ float sH[kDescWarps][48];
     __shared__ float sb[kDescWarps][2][kMaxP * kMaxP * kMaxP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane & 7;
     // the count may exceed the buffer (items past it were not stored and the
     // overflow bit is set)
     const int64_t n_in = min(*ct.n_in, cap_out);
     if (blockIdx.x == 0 && threadIdx.x == 0) *ct.n_reset = 0;
-    for (int64_t k = (int64_t)blockIdx.x * kDescWarps + w; k < n_in;
-         k += (int64_t)gridDim.x * kDescWarps) {
-        Item it = in[k];
-        const int32_t X = it.X, Y = it.Y;
-        const int ch = it.ch;
-        const bool lx = tr.child_first[X] < 0, ly = tr.child_first[Y] < 0;
-        const bool split = it.q >= 0 && kind[it.q] == kSplit;
-        const int32_t cf = split ? pcf[it.q] : -1;
-        // a split pair whose children did not fit in the pair table (the step
-        // is halted and redone with a larger table): nothing to read
-        if (split && cf < 0) continue;
-        if (lx && ly) {
-            // form_synapse: the leaf pair goes to the per-element draw
-            if (lane == 0) {
-                unsigned long long slot = atomicAdd(ct.n_leaf, 1ull);
-                if ((int64_t)slot < cap_leaf) leaf_out[slot] = it;
-                else atomicOr(ct.overflow, 4ull);
-            }
-            continue;
-        }
-        if (!lx && ly) {
-            // the dendrite side is a leaf: every axon child with vacancies of
-            // this channel keeps it, without a draw
-            int nx = tr.nchild[X];
-            int32_t cx = tr.child_first[X];
-            if (lane < nx) {
-                int32_t xc = cx + lane;
-                int4 sm = tr.sums[xc];
-                int sa = ch ? sm.y : sm.x;
-                bool keep = sa > 0;
-                if (keep && split) keep = (ch ? pw[cf + lane].z : pw[cf + lane].x) > kMinAttractionF;
-                if (keep) {
-                    unsigned long long slot = atomicAdd(ct.n_out, 1ull);
-                    Item nx_it = {xc, Y, split ? cf + lane : -1, ch};
-                    if ((int64_t)slot < cap_out) out[slot] = nx_it;
-                    else atomicOr(ct.overflow, 2ull);
+    const int64_t warp = (int64_t)blockIdx.x * kDescWarps + w;
+    const int64_t nwarp = (int64_t)gridDim.x * kDescWarps;
+    for (int64_t k0 = 4 * warp; k0 < n_in; k0 += 4 * nwarp) {
+        const int64_t k = k0 + (lane >> 3);
+        Item it = {0, 0, -1, 0};
+        bool far_item = false, drew = false;
+        if (k < n_in) {
+            it = in[k];
+            const int32_t X = it.X, Y = it.Y;
+            const int ch = it.ch;
+            const bool lx = tr.child_first[X] < 0, ly = tr.child_first[Y] < 0;
+            const bool split = it.q >= 0 && kind[it.q] == kSplit;
+            const int32_t cf = split ? pcf[it.q] : -1;
+            // a split pair whose children did not fit in the pair table (the
+            // step is halted and redone with a larger table): nothing to read
+            if (split && cf < 0) {
+            } else if (lx && ly) {
+                // form_synapse: the leaf pair goes to the per-element draw
+                if (sub == 0) {
+                    const unsigned long long slot = atomicAdd(ct.n_leaf, 1ull);
+                    if ((int64_t)slot < cap_leaf) leaf_out[slot] = it;
+                    else atomicOr(ct.overflow, 4ull);
                 }
-            }
-            continue;
-        }
-        // a draw among the children of Y, for X itself (X a leaf) or for each
-        // axon child of X (both inner)
-        const int ny = tr.nchild[Y];
-        const int32_t cy = tr.child_first[Y];
-        const int nsrc = lx ? 1 : tr.nchild[X];
-        if (split) {
-            // the candidates' attractions are in the pair table: lane i draws
-            // for axon child i
-            const uint32_t c1 =
-                (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
-            bool drew = false;
-            if (lane < nsrc) {
-                const int i = lane;
-                const int32_t xc = lx ? X : tr.child_first[X] + i;
-                const int4 sm = tr.sums[xc];
-                if (lx || (ch ? sm.y : sm.x) != 0) {
-                    float2 wk[8];
-                    for (int j = 0; j < ny; ++j) {
-                        const float4 v = pw[cf + (int64_t)i * ny + j];
-                        wk[j] = ch ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-                    }
-                    const int kk = draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
-                    drew = true;
-                    if (kk >= 0) {
+            } else if (!lx && ly) {
+                // the dendrite side is a leaf: every axon child with vacancies
+                // of this channel keeps it, without a draw
+                if (sub < tr.nchild[X]) {
+                    const int32_t xc = tr.child_first[X] + sub;
+                    const int4 sm = tr.sums[xc];
+                    bool keep = (ch ? sm.y : sm.x) > 0;
+                    if (keep && split)
+                        keep = (ch ? pw[cf + sub].z : pw[cf + sub].x) > kMinAttractionF;
+                    if (keep) {
                         const unsigned long long slot = atomicAdd(ct.n_out, 1ull);
-                        const Item nx_it = {xc, cy + kk, cf + i * ny + kk, ch};
+                        const Item nx_it = {xc, Y, split ? cf + sub : -1, ch};
                         if ((int64_t)slot < cap_out) out[slot] = nx_it;
                         else atomicOr(ct.overflow, 2ull);
                     }
                 }
+            } else if (split) {
+                // a draw among the children of Y, for X itself (X a leaf) or
+                // for each axon child of X (both inner); the candidates'
+                // attractions are in the pair table
+                const int ny = tr.nchild[Y];
+                const int32_t cy = tr.child_first[Y];
+                const int nsrc = lx ? 1 : tr.nchild[X];
+                if (sub < nsrc) {
+                    const int32_t xc = lx ? X : tr.child_first[X] + sub;
+                    const int4 sm = tr.sums[xc];
+                    if (lx || (ch ? sm.y : sm.x) != 0) {
+                        float2 wk[8];
+                        for (int j = 0; j < ny; ++j) {
+                            const float4 v = pw[cf + (int64_t)sub * ny + j];
+                            wk[j] = ch ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+                        }
+                        const uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) |
+                                            (kTagDescend << 16);
+                        const int kk =
+                            draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
+                        drew = true;
+                        if (kk >= 0) {
+                            const unsigned long long slot = atomicAdd(ct.n_out, 1ull);
+                            const Item nx_it = {xc, cy + kk, cf + sub * ny + kk, ch};
+                            if ((int64_t)slot < cap_out) out[slot] = nx_it;
+                            else atomicOr(ct.overflow, 2ull);
+                        }
+                    }
+                }
+            } else {
+                far_item = true;
             }
-            const unsigned dm = __ballot_sync(0xffffffffu, drew);
-            if (lane == 0 && dm) atomicAdd(ct.draws, (unsigned long long)__popc(dm));
-            continue;
         }
+        const unsigned dm = __ballot_sync(0xffffffffu, drew);
+        if (lane == 0 && dm) atomicAdd(ct.draws, (unsigned long long)__popc(dm));
         // below a translated pair: each candidate's attraction is a
         // translation the whole warp evaluates
-        for (int i = 0; i < nsrc; ++i) {
-            const int32_t xc = lx ? X : tr.child_first[X] + i;
-            if (!lx) {
-                int4 sm = tr.sums[xc];
-                if ((ch ? sm.y : sm.x) == 0) continue;
-            }
-            float2 wk[8];
-            for (int j = 0; j < ny; ++j) {
-                if (split) {
-                    const float4 v = pw[cf + (int64_t)i * ny + j];
-                    wk[j] = ch ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-                } else {
-                    wk[j] = make_float2(warp_far_w(tr, ex, xc, cy + j, ch, sH[w], sb[w][0], sb[w][1]),
-                                        0.f);
+        unsigned fm = __ballot_sync(0xffffffffu, far_item && sub == 0);
+        while (fm) {
+            const int src = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int32_t X = __shfl_sync(0xffffffffu, it.X, src);
+            const int32_t Y = __shfl_sync(0xffffffffu, it.Y, src);
+            const int ch = __shfl_sync(0xffffffffu, it.ch, src);
+            const bool lx = tr.child_first[X] < 0;
+            const int ny = tr.nchild[Y];
+            const int32_t cy = tr.child_first[Y];
+            const int nsrc = lx ? 1 : tr.nchild[X];
+            for (int i = 0; i < nsrc; ++i) {
+                const int32_t xc = lx ? X : tr.child_first[X] + i;
+                if (!lx) {
+                    const int4 sm = tr.sums[xc];
+                    if ((ch ? sm.y : sm.x) == 0) continue;
                 }
-            }
-            if (lane == 0) {
-                uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) | (kTagDescend << 16);
-                int kk = draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
-                atomicAdd(ct.draws, 1ull);
-                if (kk >= 0) {
-                    unsigned long long slot = atomicAdd(ct.n_out, 1ull);
-                    Item nx_it = {xc, cy + kk, split ? cf + i * ny + kk : -1, ch};
-                    if ((int64_t)slot < cap_out) out[slot] = nx_it;
-                    else atomicOr(ct.overflow, 2ull);
+                float2 wk[8];
+                for (int j = 0; j < ny; ++j)
+                    wk[j] = make_float2(
+                        warp_far_w(tr, ex, xc, cy + j, ch, sH[w], sb[w][0], sb[w][1]), 0.f);
+                if (lane == 0) {
+                    const uint32_t c1 = (uint32_t)(tr.level[Y] + 1) | ((uint32_t)ch << 8) |
+                                        (kTagDescend << 16);
+                    const int kk = draw_index(wk, ny, philox_bits53(seed, (uint32_t)xc, c1, step));
+                    atomicAdd(ct.draws, 1ull);
+                    if (kk >= 0) {
+                        const unsigned long long slot = atomicAdd(ct.n_out, 1ull);
+                        const Item nx_it = {xc, cy + kk, -1, ch};
+                        if ((int64_t)slot < cap_out) out[slot] = nx_it;
+                        else atomicOr(ct.overflow, 2ull);
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }
