@@ -49,6 +49,10 @@ CASES = {
     "single_leaf": lambda: W.uniform_cube(40, 3000.0, seed=31, leaf_capacity=64),
     "one_neuron": lambda: W.uniform_cube(1, 1000.0, seed=1),
     "no_vacancies": lambda: _zero_axons(),
+    # every neuron sends 3 axonal elements, 3 neurons have vacant dendrites:
+    # groups of thousands of requests at one dendrite, most boxes without
+    # attraction (translated pairs included)
+    "few_dendrites": lambda: _few_dendrites(),
     # expansions about the geometric centres: translations grouped by offset
     # as matrix products (p <= 5), one pair at a time above
     "geo_far_p4": lambda: W.clustered_small(1, 4096, leaf_capacity=8, rho_max=0.3, p=4,
@@ -78,6 +82,17 @@ CASES = {
 # cases whose FP64 brute force runs on sampled targets (all-targets would
 # take the oracle tens of seconds)
 SAMPLED_DIRECT = {"bench_plan_3x16k": 4096, "leaf_capacity_512": 2048}
+
+
+def _few_dendrites():
+    w = W.uniform_cube(3000, 8000.0, seed=12, leaf_capacity=16)
+    w.vac_axon[:] = 3
+    w.vac_dend_e[:] = 0
+    w.vac_dend_i[:] = 0
+    idx = np.array([5, 1200, 2900])
+    w.vac_dend_e[idx] = 5
+    w.vac_dend_i[idx] = 5
+    return w
 
 
 def _zero_axons():
