@@ -305,13 +305,16 @@ class MSP:
 
     def plasticity_step_host(self, step, pos, type_, vac_axon, vac_dend_e, vac_dend_i,
                              out=None, want_u=True):
-        """Whole step from host (numpy, ideally pinned) buffers; returns host results."""
+        """Whole step from host (numpy, ideally pinned) buffers; returns host results.
+        Caller-given `out` buffers must hold sum(vac_axon) elements (partner,
+        syn_*) and n floats (u), as msp_plasticity_step_host requires."""
         n = int(pos.shape[1])
         x, y, z = (np.ascontiguousarray(pos[d], dtype=np.float32) for d in range(3))
         t, a, e, i = (np.ascontiguousarray(v, dtype=np.uint8) for v in
                       (type_, vac_axon, vac_dend_e, vac_dend_i))
-        ne = max(int(a.sum(dtype=np.int64)), 1)
         if out is None:
+            # sized by the vacant axonal elements (only when the caller gives no buffers)
+            ne = max(int(a.sum(dtype=np.int64)), 1)
             out = dict(u=np.zeros(max(n, 1), np.float32), partner=np.zeros(ne, np.int32),
                        syn_pre=np.zeros(ne, np.int32), syn_post=np.zeros(ne, np.int32),
                        syn_type=np.zeros(ne, np.uint8), n_syn=np.zeros(1, np.int64))
