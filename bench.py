@@ -627,6 +627,12 @@ def run_ours(args, rank, world):
     replicas.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    # the vacancy state a replay's build sees (the timed replays' last state
+    # walked once more, as the next step's walk would): the end-to-end leg
+    # below runs on it (the host-buffer call runs steps a1-a12, without the
+    # walk and the commit; the runs in between walk and commit further)
+    timed_state = [v.clone() for v in (va, ve, vi)]
+    g.vacancy_walk(nxt, *timed_state)
     st = g.stats()
     launches = st["kernel_launches"] - launches0
     clk = clocks.stop()
@@ -676,11 +682,11 @@ def run_ours(args, rank, world):
     # inputs (positions, types, vacant counts) up from pinned host memory, runs
     # steps a1-a12 and copies u, the partners and the synapses back (the call
     # replays its own graph of the step after the first call).  The vacant
-    # counts are the walked state the timed graph replays reached.
+    # counts are those a timed replay's build sees (snapshot above).
     pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hp = pinned(w.pos)
     ht = pinned(w.type)
-    ha, he, hi = (pinned(v.cpu().numpy()) for v in (va, ve, vi))
+    ha, he, hi = (pinned(v.cpu().numpy()) for v in timed_state)
     ne0 = int(ha.sum(dtype=np.int64))
     hout = dict(u=pinned(np.zeros(n, np.float32)), partner=pinned(np.zeros(ne0, np.int32)),
                 syn_pre=pinned(np.zeros(ne0, np.int32)), syn_post=pinned(np.zeros(ne0, np.int32)),
@@ -786,7 +792,9 @@ def run_ours(args, rank, world):
                    "path": "msp_plasticity_step_host (C ABI, host buffers): positions, types and "
                            "vacant counts copied up from pinned memory, steps a1-a12, u, partners "
                            "and synapses copied back, every step; the call replays its own graph "
-                           "of the step (the walked vacancy state of the timed replays)",
+                           "of the step (the vacancy state a timed replay's build sees: its last "
+                           "state walked once more; the walk and the commit, about 40 us of the "
+                           "replayed step under ncu, are not part of this call)",
                    "timing": "host wall clock per call, mean over calls, L2 flushed between"},
            "gpu_launches": int(launches),
            "roofline": roofline}
