@@ -257,31 +257,41 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
                 const int m = min(kNFStage, sc - sb);
                 const int mp = (m + 1) >> 1;
                 __syncwarp();
-                float* f = reinterpret_cast<float*>(stw);
-                for (int e = lane; e < 2 * mp; e += 32) {
-                    float sx = 0.f, sy = 0.f, sz = 0.f, cE = -INFINITY, cI = -INFINITY;
-                    if (e < m) {
-                        const float4 S = a.pts[sf + sb + e];
-                        const float2 L = a.lw[sf + sb + e];
-                        sx = (S.x - cx) * a.sqk;
-                        sy = (S.y - cy) * a.sqk;
-                        sz = (S.z - cz) * a.sqk;
-                        const float n2 = fast ? -fmaf(sx, sx, fmaf(sy, sy, sz * sz)) : 0.f;
-                        cE = n2 + L.x;
-                        cI = n2 + L.y;
-                        if (!fast) {
-                            sx = -sx;
-                            sy = -sy;
-                            sz = -sz;
-                        }
+                // a lane stages source pairs (2j, 2j+1) with paired FP32 (the
+                // same rounding per source as the scalar form) and three
+                // 16-byte stores; an odd count's last source is padding
+                // (coordinates 0, c = -inf)
+                const float2 nc = make_float2(-cx, -cx), ncy = make_float2(-cy, -cy),
+                             ncz = make_float2(-cz, -cz), k2 = make_float2(a.sqk, a.sqk);
+                for (int j = lane; j < mp; j += 32) {
+                    const int e = 2 * j;
+                    const bool two = e + 1 < m;
+                    const float4 S0 = a.pts[sf + sb + e];
+                    const float2 L0 = a.lw[sf + sb + e];
+                    const float4 S1 = two ? a.pts[sf + sb + e + 1] : S0;
+                    const float2 L1 = two ? a.lw[sf + sb + e + 1] : L0;
+                    float2 sx = __fmul2_rn(__fadd2_rn(make_float2(S0.x, S1.x), nc), k2);
+                    float2 sy = __fmul2_rn(__fadd2_rn(make_float2(S0.y, S1.y), ncy), k2);
+                    float2 sz = __fmul2_rn(__fadd2_rn(make_float2(S0.z, S1.z), ncz), k2);
+                    float2 n2 = make_float2(0.f, 0.f);
+                    if (fast) {
+                        const float2 q = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, __fmul2_rn(sz, sz)));
+                        n2 = make_float2(-q.x, -q.y);
                     }
-                    const int j = e >> 1, h = e & 1;
-                    f[4 * j + h] = sx;
-                    f[4 * j + 2 + h] = sy;
-                    f[4 * (kNFZE + j) + h] = sz;
-                    f[4 * (kNFZE + j) + 2 + h] = cE;
-                    f[4 * (kNFZI + j) + h] = sz;
-                    f[4 * (kNFZI + j) + 2 + h] = cI;
+                    float2 cE = __fadd2_rn(n2, make_float2(L0.x, L1.x));
+                    float2 cI = __fadd2_rn(n2, make_float2(L0.y, L1.y));
+                    if (!fast) {
+                        sx = make_float2(-sx.x, -sx.y);
+                        sy = make_float2(-sy.x, -sy.y);
+                        sz = make_float2(-sz.x, -sz.y);
+                    }
+                    if (!two) {
+                        sx.y = sy.y = sz.y = 0.f;
+                        cE.y = cI.y = -INFINITY;
+                    }
+                    stw[j] = make_float4(sx.x, sx.y, sy.x, sy.y);
+                    stw[kNFZE + j] = make_float4(sz.x, sz.y, cE.x, cE.y);
+                    stw[kNFZI + j] = make_float4(sz.x, sz.y, cI.x, cI.y);
                 }
                 __syncwarp();
                 if (fast) {
