@@ -188,6 +188,10 @@ msp_status msp_direct(msp_ctx *ctx, float *u_dev, void *stream);
 
 /* Steps a11-a12: Algorithm 1 with Algorithm 2's choice at every level, a
  * per-element draw inside the chosen dendrite leaf, and request resolution.
+ * The level draws take prefix sums of the candidates' attractions in pairs
+ * of floats (hi + lo), the leaf draw in exact 64-bit fixed point; a dendrite
+ * neuron accepts, per channel, its first requests in (Philox priority,
+ * element) order up to its vacant count.
  *   step            plasticity step number, part of every Philox counter
  *   partner_dev     n_elements int32 out: the dendrite neuron drawn by each
  *                   vacant axonal element (elements ordered by neuron, then
@@ -468,7 +472,9 @@ msp_status msp_export_tree(msp_ctx *ctx, uint64_t *keys, int32_t *perm, uint8_t 
 
 /* Box pairs of the dual traversal (HOST pointers, n_pairs each; depth_start
  * has pair_depths+1 entries): kind 0 split, 1 far (translated), 2 near-field
- * leaf pair, 3 pruned; w_e / w_i the pair attraction per channel. */
+ * leaf pair, 3 pruned; w_e / w_i the pair attraction per channel (the
+ * device table holds each as a pair of floats hi + lo, about 48 significant
+ * bits, summed here in double). */
 msp_status msp_export_pairs(msp_ctx *ctx, int32_t *X, int32_t *Y, uint8_t *kind,
                             int32_t *child_first, double *w_e, double *w_i,
                             int64_t *depth_start);
