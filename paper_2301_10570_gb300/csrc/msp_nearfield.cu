@@ -96,9 +96,10 @@ struct Tgts {
 __shared__ float* s_scale;
 __shared__ float* s_fa;
 __shared__ const int32_t* s_tl;
-// per thread and target r, at [r * kNFThreads + thread]: the compensation of
-// the Kahan sum of the target's per-pair sums (kept in shared memory: the
-// kernel's registers are taken by the evaluation loop)
+// per thread and target r: the compensation of the Kahan sum of the target's
+// per-pair sums, targets 2i and 2i+1 as one float2 at [i * kNFThreads +
+// thread] (kept in shared memory: the kernel's registers are taken by the
+// evaluation loop)
 __shared__ float* s_cmp;
 
 // A warp's staged sources, in pairs: pair j (sources 2j, 2j+1) is the float4
@@ -307,15 +308,30 @@ __device__ __forceinline__ void nf_pairs(const NFArgs& a, int32_t i0, int32_t i1
             // summation (the compensation holds what the running total
             // gained by rounding)
             float v = 0.f;
+            // two targets at a time in paired FP32 (the same rounding per
+            // target); the compensations of targets k, k+1 as one float2
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                float* cp = s_cmp + k * kNFThreads + threadIdx.x;
-                const float y = __fsub_rn(part[k], *cp);
-                const float t2 = __fadd_rn(acc[k], y);
-                *cp = __fsub_rn(__fsub_rn(t2, acc[k]), y);
-                acc[k] = t2;
-                v = fmaf(s_fa[tg.slot0 + k], part[k], v);
+            for (int k = 0; k < R; k += 2) {
+                float2* cp = reinterpret_cast<float2*>(s_cmp) + (k >> 1) * kNFThreads + threadIdx.x;
+                if (k + 1 < R) {
+                    const float2 c2 = *cp, p2 = make_float2(part[k], part[k + 1]);
+                    const float2 a2 = make_float2(acc[k], acc[k + 1]);
+                    const float2 y = __fadd2_rn(p2, make_float2(-c2.x, -c2.y));
+                    const float2 t2 = __fadd2_rn(a2, y);
+                    const float2 d = __fadd2_rn(t2, make_float2(-a2.x, -a2.y));
+                    *cp = __fadd2_rn(d, make_float2(-y.x, -y.y));
+                    acc[k] = t2.x;
+                    acc[k + 1] = t2.y;
+                } else {
+                    float* cs = reinterpret_cast<float*>(cp);
+                    const float y = __fsub_rn(part[k], *cs);
+                    const float t2 = __fadd_rn(acc[k], y);
+                    *cs = __fsub_rn(__fsub_rn(t2, acc[k]), y);
+                    acc[k] = t2;
+                }
             }
+#pragma unroll
+            for (int k = 0; k < R; ++k) v = fmaf(s_fa[tg.slot0 + k], part[k], v);
             // W(X,Y) of each channel: every lane's term goes into a transposed
             // buffer; every 16 pairs the warp sums the rows (half a row per
             // lane, then one shuffle) and adds them to the pairs' slots
@@ -384,7 +400,8 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
         tg.y[r] = make_float2(f2 * hy, f2 * hy);
         tg.z[r] = make_float2(f2 * hz, f2 * hz);
         acc[r] = 0.f;
-        s_cmp[r * kNFThreads + threadIdx.x] = 0.f;
+        reinterpret_cast<float*>(reinterpret_cast<float2*>(s_cmp) + (r >> 1) * kNFThreads +
+                                 threadIdx.x)[r & 1] = 0.f;
         if (w == 0 && ksl == 0) {
             const float sc = fast ? nf_ex2(-fmaf(hx, hx, fmaf(hy, hy, hz * hz))) : 1.f;
             s_scale[slot] = sc;
@@ -397,7 +414,9 @@ __device__ __forceinline__ void nf_targets(const NFArgs& a, const int32_t* tl, i
     // warps in a fixed order
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        acc[r] = __fsub_rn(acc[r], s_cmp[r * kNFThreads + threadIdx.x]);
+        acc[r] = __fsub_rn(acc[r], reinterpret_cast<float*>(reinterpret_cast<float2*>(s_cmp) +
+                                                             (r >> 1) * kNFThreads +
+                                                             threadIdx.x)[r & 1]);
         for (int o = npr; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     }
     if (ksl == 0) {
@@ -429,7 +448,7 @@ __global__ void __launch_bounds__(kNFWarps * 32, 7) k_near_field(NFArgs a) {
     __shared__ float wt_all[kNFWarps][16][33];
     __shared__ int32_t wii_all[kNFWarps][16];
     __shared__ float scale_all[kNFMaxT], fa_all[kNFMaxT];
-    __shared__ float cmp_all[4 * kNFThreads];
+    __shared__ __align__(16) float cmp_all[4 * kNFThreads];
     s_cmp = cmp_all;
     s_wt = &wt_all[0][0][0];
     s_wii = &wii_all[0][0];
