@@ -551,16 +551,15 @@ __global__ void k_l2p(int64_t n, int64_t exp_first, int p, float inv_sigma,
     }
 }
 
-// a10: attraction of a split pair = sum over its child block (double-FP32
-// sums: no double precision instruction, which this GPU runs at 1/64 of the
-// single precision rate).  The
-// split pairs of each depth are listed once per traversal (the list keeps
-// pair order, each entry with its child block); 8 lanes take one split pair,
-// lane c summing children c, c + 8, ... (coalesced: 8 consecutive 16-byte
-// entries per step, all loaded before the sum), then a fixed butterfly over
-// the 8 lanes.  Both orders are fixed, so the table is
-// reproducible.  sb = [first, end) of the depth's entries in split; an entry
-// is (pair, first child, child count, 0).
+// a10: attraction of a split pair = sum over its child block, in double-FP32
+// (compensated FP32 sums: no double precision instruction, which this GPU
+// runs at 1/64 of the single precision rate).  The split pairs of each depth
+// are listed once per traversal (the list keeps pair order, each entry with
+// its child block); 8 lanes take one split pair, lane c summing children c,
+// c + 8, ... (coalesced: 8 consecutive 16-byte entries per step, all loaded
+// before the sum), then a fixed butterfly over the 8 lanes.  Both orders are
+// fixed, so the table is reproducible.  sb = [first, end) of the depth's
+// entries in split; an entry is (pair, first child, child count, 0).
 __global__ void k_reduce_split(const int64_t* __restrict__ sb, const int4* __restrict__ split,
                                float4* __restrict__ pw) {
     const int64_t s0 = sb[0], ns = sb[1] - sb[0];
@@ -603,6 +602,8 @@ __global__ void k_reduce_split(const int64_t* __restrict__ sb, const int4* __res
     }
 }
 
+// the split pairs in pair order (off: exclusive scan of their flags), each
+// with its child block
 __global__ void k_compact_split(const uint8_t* __restrict__ kind, const int64_t* __restrict__ n_dev,
                                 const int32_t* __restrict__ off, const int32_t* __restrict__ pcf,
                                 const uint8_t* __restrict__ pnb, int4* __restrict__ split) {

@@ -294,8 +294,10 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
 // Box aggregates, one launch for the whole octree.  A leaf sums its points;
 // an inner box combines its children, and it is computed by the warp of its
 // last child to finish: every box, once written, adds one to its parent's
-// arrival counter (after a fence), and the warp that brings the counter to the
-// parent's child count resets it and goes on with the parent, up to the root.
+// arrival counter (an acquire-release atomic: the box's results are visible
+// before the arrival, the siblings' after it), and the warp that brings the
+// counter to the parent's child count resets it and goes on with the parent,
+// up to the root.
 // Centroids are accumulated as weighted offsets from the box's geometric
 // centre so that single precision keeps them accurate (with frames, the
 // centre in the box's network's own frame: box_axis).  A leaf's lanes take its
@@ -303,8 +305,9 @@ __global__ void k_emit_children(const int64_t* __restrict__ lb, int level, int l
 // sums the lanes, then lane 0 writes the box's vacant-element sums and its
 // axon / dendrite centroids (offsets summed, then divided by the weight).  The
 // order of every sum is fixed whichever warp computes a box, so the results
-// are those of a level-by-level pass.  The counters are zero on entry (cleared
-// by the host before an eager build; every complete launch leaves them zero).
+// are those of a level-by-level pass.  The counters are zero on entry
+// (cleared by the host before an eager build and whenever their buffer is new;
+// every complete launch leaves them zero).
 __device__ __forceinline__ void aggregate_box(int64_t i, int lane, int frame_level, float ox,
                                               float oy, float oz, float side,
                                               const float4* __restrict__ pts,
