@@ -63,7 +63,7 @@ __global__ void k_graph_guard(DevCounts* dc, int64_t elem_cap) {
 __global__ void k_graph_check(DevCounts* dc, int left_slot) {
     int64_t bad = 0;
     if (dc->overflow & 1) bad |= kHaltPairs;
-    if (dc->overflow & 6) bad |= kHaltItems;
+    if (dc->overflow & 38) bad |= kHaltItems;
     if (dc->more_levels > 0 || (dc->overflow & 16) || dc->bad_pos) bad |= kHaltLevels;
     if (dc->items[left_slot] != 0) bad |= kHaltDescent;
     dc->halt |= bad;

@@ -120,7 +120,8 @@ struct DevCounts {
     int64_t draws;
     int64_t n_req, n_syn;
     int64_t interactions;
-    int64_t overflow;                        // bit 0 pairs, 1 items, 2 leaf items, 4 tree nodes
+    int64_t overflow;                        // bit 0 pairs, 1 items, 2 leaf items, 4 tree nodes,
+                                             // 5 request groups inconsistent
     int64_t need_pairs;                      // largest pair-table end asked for (before clamping)
     int64_t need_items;                      // largest descent item count asked for
     int64_t need_nodes;                      // largest octree node end asked for

@@ -139,7 +139,7 @@ __global__ void k_init_items(const int4* __restrict__ sums, const float4* __rest
     dc->n_leaf = 0;
     dc->leaf_next = 0;
     dc->draws = 0;
-    dc->overflow &= ~6ll;       // the descent's bits; bit 0 (pair table) stays
+    dc->overflow &= ~38ll;      // the selection's bits; bit 0 (pair table) stays
 }
 
 // One level step of the descent.  A warp takes four items, 8 lanes each
@@ -569,13 +569,15 @@ __global__ void k_req_count(int64_t n, const uint8_t* __restrict__ type,
 }
 
 // key = priority << 32 | group, val = element; cap bounds the slots (the
-// buffers' length) should the counts not match
+// buffers' length): a slot outside it (counts that do not match) is not
+// written and sets bit 5 of *overflow
 __global__ void k_req_scatter(int64_t n, const uint8_t* __restrict__ type,
                               const uint8_t* __restrict__ va, const int32_t* __restrict__ eoff,
                               const int32_t* __restrict__ partner, const int32_t* __restrict__ goff,
                               int32_t* __restrict__ gcnt, uint64_t seed, StepRef stp,
                               uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                              const int64_t* __restrict__ n_elem, int64_t cap) {
+                              const int64_t* __restrict__ n_elem, int64_t cap,
+                              int64_t* __restrict__ overflow) {
     const uint64_t step = stp.get();
     const int64_t ne = *n_elem;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -591,7 +593,10 @@ __global__ void k_req_scatter(int64_t n, const uint8_t* __restrict__ type,
             philox_draw(seed, (uint32_t)t, (uint32_t)k | (kTagAccept << 16), step, o);
             const int64_t g = base + s;
             const int64_t r = (int64_t)goff[g] + atomicSub(&gcnt[g], 1) - 1;
-            if (r < 0 || r >= cap) continue;
+            if (r < 0 || r >= cap) {
+                atomicOr(reinterpret_cast<unsigned long long*>(overflow), 32ull);
+                continue;
+            }
             key[r] = ((uint64_t)o[0] << 32) | (uint32_t)g;
             val[r] = e0 + k;
         }
@@ -601,11 +606,13 @@ __global__ void k_req_scatter(int64_t n, const uint8_t* __restrict__ type,
 // A dendrite neuron accepts, per channel, its first `capacity` requests in
 // (priority, element) order: the rank of request i is the number of requests
 // of its group before it in that order.  Groups are small (the requests one
-// neuron receives), so each request counts over its group directly.
+// neuron receives), so each request counts over its group directly.  A group
+// whose count the scatter did not bring back to zero sets bit 5 of *overflow.
 __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
-                         const int32_t* __restrict__ goff, const int64_t* __restrict__ nr_dev,
-                         int64_t n, const uint8_t* __restrict__ vde,
-                         const uint8_t* __restrict__ vdi, uint8_t* __restrict__ accepted) {
+                         const int32_t* __restrict__ goff, const int32_t* __restrict__ gcnt,
+                         const int64_t* __restrict__ nr_dev, int64_t n,
+                         const uint8_t* __restrict__ vde, const uint8_t* __restrict__ vdi,
+                         uint8_t* __restrict__ accepted, int64_t* __restrict__ overflow) {
     const int64_t nr = *nr_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -616,6 +623,7 @@ __global__ void k_accept(const uint64_t* __restrict__ key, const int32_t* __rest
         const bool inh = g >= n;
         const int64_t s = inh ? g - n : g;
         const int cap = inh ? vdi[s] : vde[s];
+        if (gcnt[g] != 0) atomicOr(reinterpret_cast<unsigned long long*>(overflow), 32ull);
         const int64_t j0 = goff[g], j1 = g + 1 < 2 * n ? (int64_t)goff[g + 1] : nr;
         int rank = 0;
         for (int64_t j = j0; j < j1 && rank < cap; ++j) {
@@ -813,9 +821,11 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     MSP_LAUNCH("req_count");
     scan_dev(c, gcnt, goff, &dc->n_groups, (int64_t)ng, &dc->n_req, nullptr, s);
     k_req_scatter<<<gn, B, 0, s>>>(n, type_dev, va_dev, c.elem_off.get<int32_t>(), partner, goff,
-                                   gcnt, cfg.seed, stp, k0, v0, &dc->n_elem, (int64_t)ne);
+                                   gcnt, cfg.seed, stp, k0, v0, &dc->n_elem, (int64_t)ne,
+                                   &dc->overflow);
     MSP_LAUNCH("req_scatter");
-    k_accept<<<ge, B, 0, s>>>(k0, v0, goff, &dc->n_req, n, vde_dev, vdi_dev, acc);
+    k_accept<<<ge, B, 0, s>>>(k0, v0, goff, gcnt, &dc->n_req, n, vde_dev, vdi_dev, acc,
+                              &dc->overflow);
     MSP_LAUNCH("accept");
     k_acc_flags<<<ge, B, 0, s>>>(acc, &dc->n_elem, flag);
     MSP_LAUNCH("acc_flags");
@@ -833,6 +843,7 @@ void select_partners(msp_ctx& c, uint64_t step, const uint8_t* type_dev, const u
     pull_counts(c, s);              // the one synchronisation of the selection
     const DevCounts& hc = *c.hcount;
     if (hc.overflow & 6) throw Error(MSP_ERR_CHECK, "descent item capacity exceeded");
+    if (hc.overflow & 32) throw Error(MSP_ERR_CHECK, "request groups inconsistent");
     if (hc.items[n_steps % 3] != 0) throw Error(MSP_ERR_CHECK, "descent did not terminate");
     c.n_draws = hc.draws;
     c.n_requests = hc.n_req;
