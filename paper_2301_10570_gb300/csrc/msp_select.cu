@@ -329,6 +329,23 @@ __device__ __forceinline__ uint64_t ld_weight(const float4& T, const float4& S, 
     return fixed_point(ws, shift);
 }
 
+// the weights of two sources at once: the distance, the exponent's argument
+// and the scale in paired FP32 (each element rounded as in ld_weight, so the
+// totals and the walk see the same values)
+__device__ __forceinline__ void ld_weight2(const float4& T, const float4& S0, const float4& S1,
+                                           float k2, float rc2, int shift, uint64_t& v0,
+                                           uint64_t& v1) {
+    const float2 dx = __fadd2_rn(make_float2(T.x, T.x), make_float2(-S0.x, -S1.x));
+    const float2 dy = __fadd2_rn(make_float2(T.y, T.y), make_float2(-S0.y, -S1.y));
+    const float2 dz = __fadd2_rn(make_float2(T.z, T.z), make_float2(-S0.z, -S1.z));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 e = __fmul2_rn(make_float2(-r2.x, -r2.y), make_float2(k2, k2));
+    const float2 ws =
+        __fmul2_rn(make_float2(S0.w, S1.w), make_float2(ex2_approx_sel(e.x), ex2_approx_sel(e.y)));
+    v0 = fixed_point(r2.x < rc2 ? ws.x : 0.f, shift);
+    v1 = fixed_point(r2.y < rc2 ? ws.y : 0.f, shift);
+}
+
 // per-network truncation radii (points in frames with per-network plans):
 // the squared radius of the axon leaf's network
 struct FrameRc2 {
@@ -426,21 +443,29 @@ k_leaf_draw_w(const Item* __restrict__ items, const int64_t* __restrict__ n_leaf
             const bool use_blocks = L <= 32 * kLdBlocks;
             uint64_t part = 0;
             if (nt > 0) {
+                // the sum over sources [ja, jb), two at a time
+                auto span = [&](int ja, int jb) {
+                    uint64_t sum = 0;
+                    int j = ja;
+                    for (; j + 1 < jb; j += 2) {
+                        uint64_t v0, v1;
+                        ld_weight2(T, src.get(j), src.get(j + 1), k2, rc2, shift, v0, v1);
+                        sum += (sf + j == t ? 0ull : v0) + (sf + j + 1 == t ? 0ull : v1);
+                    }
+                    if (j < jb) {
+                        const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
+                        sum += sf + j == t ? 0ull : v;
+                    }
+                    return sum;
+                };
                 if (use_blocks) {
                     for (int b = 0; j0 + 32 * b < j1; ++b) {
-                        uint64_t bsum = 0;
-                        for (int j = j0 + 32 * b; j < min(j1, j0 + 32 * b + 32); ++j) {
-                            const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
-                            bsum += sf + j == t ? 0ull : v;
-                        }
+                        const uint64_t bsum = span(j0 + 32 * b, min(j1, j0 + 32 * b + 32));
                         s_bsum[w][b][lane] = bsum;
                         part += bsum;
                     }
                 } else {
-                    for (int j = j0; j < j1; ++j) {
-                        const uint64_t v = ld_weight(T, src.get(j), k2, rc2, shift);
-                        part += sf + j == t ? 0ull : v;
-                    }
+                    part = span(j0, j1);
                 }
             }
             // inclusive scan of the slices' sums over q (offsets TS, 2 TS, ...;
